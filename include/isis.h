@@ -1,0 +1,169 @@
+/*
+ * isis.h -- C ABI of the GB300 library for the scalar-field multigrid solve
+ * of ISIS (Llinares, Mota & Winther 2013, "ISIS: a new N-body cosmological
+ * code with scalar fields based on RAMSES", arXiv:1307.6748).
+ *
+ * The paper states the problem as (Sect. 1, Eqs. (eqs_general_1)-(eqs_general_3)):
+ *     lap Phi  = (3/2) Omega_m H0^2 delta / a                 (Newtonian potential)
+ *     lap phi  = S(phi, rho, a)                               (scalar field, quasi-static)
+ *     x''      = -grad Phi / a^2 - g(phi, grad phi, a)        (particles)
+ * and this library solves them on a periodic, cell-centred N^3 grid:
+ *     isis_cic_deposit    particles -> density eta (Sect. 5.1, "CIC")
+ *     isis_poisson_solve  lap Phi = (3/2) Om H0^2 (eta - <eta>) / a (Sect. 3.1)
+ *     isis_scalar_solve   L(phi, eta) = 0 by non-linear FAS multigrid with
+ *                         Newton-Gauss-Seidel smoothing (Sect. 3.2) for the
+ *                         symmetron (Sect. 4.1) or Hu-Sawicki f(R) (Sect. 4.2)
+ *     isis_fifth_force    gradients interpolated back to particles
+ *                         (Sect. 4.1 Eq. (symmetron_geodesics_tilde_chi), Sect. 4.2)
+ *
+ * Conventions shared by every call
+ *   - Grid: N^3 cells, N a power of two, 8 <= N <= 1024, cell (i,j,k) at
+ *     index (i*N + j)*N + k (k fastest), centre at (i+1/2, j+1/2, k+1/2) h,
+ *     h = box / N, periodic in all directions.
+ *   - Units: lengths in Mpc/h, c = 1, so H0 = 1/2997.92458 per Mpc/h.
+ *   - Memory: every array argument is a DEVICE pointer owned by the caller,
+ *     contiguous, on the current CUDA device; the library never frees or
+ *     keeps it.  The library owns its level hierarchy (workspace), cached
+ *     per grid size and precision until isis_release_workspace().
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Work is stream ordered.  The solvers synchronise the
+ *     stream once per cycle to read the residual norm; deposit and force
+ *     calls do not synchronise.
+ *   - Errors: every call returns an isis_status; nothing aborts.  Calls are
+ *     not thread safe (one host thread drives the library at a time).
+ */
+#ifndef ISIS_H
+#define ISIS_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ISIS_OK = 0,
+  ISIS_EINVAL = -1,    /* bad argument: sizes, pointers, parameters */
+  ISIS_ENOCONV = -2,   /* max_cycles reached; best iterate left in phi, info filled */
+  ISIS_ENAN = -3,      /* non-finite residual or a singular coarsest Jacobian */
+  ISIS_ECUDA = -4,     /* a CUDA runtime call or launch failed */
+  ISIS_ENOMEM = -5,    /* device allocation of the workspace failed */
+  ISIS_ETIMEOUT = -6,  /* reserved: a bounded device wait gave up */
+  ISIS_EINTERNAL = -7
+} isis_status;
+
+typedef enum { ISIS_SYMMETRON = 1, ISIS_FOFR_HS = 2 } isis_model;
+
+/* Arithmetic of a solve.
+ *   ISIS_F64           eta, phi are double; every kernel computes in FP64.
+ *   ISIS_F32           eta, phi are float; every kernel computes in FP32
+ *                      (coarsest dense Newton in FP64).
+ *   ISIS_F32_REFINE64  eta, phi are double.  Outer defect correction: the
+ *                      residual r = -L(phi) and the update phi += e are FP64;
+ *                      e solves L(phi + e) - L(phi) = r by FP32 FAS V-cycles
+ *                      on the correction (coarsest dense Newton in FP64). */
+typedef enum { ISIS_F64 = 0, ISIS_F32 = 1, ISIS_F32_REFINE64 = 2 } isis_precision;
+
+typedef struct {
+  double Omega_m, Omega_L; /* density parameters */
+  double H0;               /* Hubble constant in (Mpc/h)^-1, c = 1: 1/2997.92458 */
+  double box;              /* box side in Mpc/h */
+  int N;                   /* cells per dimension */
+} isis_grid;
+
+typedef struct {
+  double lambda0, beta, a_ssb; /* symmetron (Sect. 4.1): range in Mpc/h, coupling, a at symmetry breaking */
+  int n;                       /* Hu-Sawicki exponent (Sect. 4.2), n >= 1 */
+  double fR0_abs;              /* |f_R0| */
+} isis_params;
+
+typedef struct {
+  int nu1, nu2;        /* pre- and post-smoothing sweeps (red then black) per level */
+  int n_coarsest;      /* coarsest grid size: 2 or 4 (dense Newton there) */
+  int max_cycles;      /* cap on V-cycles (inner cycles for F32_REFINE64), <= 128 */
+  isis_precision prec;
+  int inner_cycles;    /* F32 V-cycles per FP64 outer iteration (F32_REFINE64), >= 1 */
+} isis_mg_opts;
+
+typedef struct {
+  int cycles;          /* V-cycles run (FP32 inner cycles for F32_REFINE64) */
+  int outer;           /* FP64 outer iterations (F32_REFINE64), else 0 */
+  double res0;         /* RMS residual of the initial guess */
+  double res_ref;      /* reference residual (below) */
+  double res_final;    /* RMS residual on return */
+  double hist[128];    /* RMS residual after each cycle (outer iteration for F32_REFINE64) */
+} isis_solve_info;
+
+/* Convergence test of both solvers (the paper gives none): stop when
+ *     RMS over the finest grid of L(phi) <= tol * res_ref,
+ * res_ref = RMS of L(phi_bg) for the uniform background field phi_bg:
+ *   symmetron  A s chi_bg * RMS(eta - 1), chi_bg = sqrt(max(0, 1 - (a_SSB/a)^3)),
+ *              A = a^2/(2 lambda0^2), s = (a_SSB/a)^3
+ *   f(R)       Om a H0^2 * RMS(eta - 1)
+ *   Poisson    (3/2) Om H0^2 / a * RMS(eta - <eta>)
+ * and res_ref = res0 when that is 0 (uniform density, or a < a_SSB). */
+
+/* CIC density estimate (Sect. 5.1): eta[cell] = sum_p W(x_p - cell) / nbar,
+ * nbar = npart / N^3, trilinear cloud-in-cell weights, periodic.
+ *   x, y, z  device float[npart], positions in CELL units (a position is
+ *            wrapped into [0, N)); cell centres at i + 1/2.
+ *   eta      device double[N^3] (eta_f64 != 0) or float[N^3] (eta_f64 == 0),
+ *            overwritten.
+ * Accumulation is in 64-bit fixed point (2^-32 per unit weight), so the
+ * result does not depend on the order of particles.  Uses an int64 N^3
+ * scratch buffer from the workspace.  EINVAL: npart < 1, npart > 2^40 or
+ * N invalid. */
+isis_status isis_cic_deposit(const isis_grid* grid, const float* x, const float* y, const float* z, int64_t npart,
+                             void* eta, int eta_f64, void* stream);
+
+/* Newtonian potential (Sect. 3.1, Eq. (disc_lap), Eq. (explicit)):
+ *     (sum of 6 neighbours - 6 Phi)/h^2 = (3/2) Om H0^2 (eta - <eta>) / a
+ * solved by multigrid V-cycles with Gauss-Seidel smoothing (the Newton step
+ * of Sect. 3.2 reduces to Eq. (explicit) for this linear operator); the
+ * mean of Phi is set to 0 after every cycle.
+ *   eta  device double[N^3] (float for ISIS_F32), mean density 1 expected.
+ *   Phi  device double[N^3] (float for ISIS_F32): initial guess in, solution out.
+ *   opts NULL for the defaults {2, 2, 4, 100, ISIS_F64, 2}; info may be NULL. */
+isis_status isis_poisson_solve(const isis_grid* grid, double a, const void* eta, void* Phi, double tol,
+                               const isis_mg_opts* opts, isis_solve_info* info, void* stream);
+
+/* Scalar field (Sect. 3.2, FAS with implicit Newton-Gauss-Seidel):
+ *   ISIS_SYMMETRON  phi = chi:  lap chi = a^2/(2 lambda0^2) [ (a_SSB/a)^3 eta chi - chi + chi^3 ]
+ *                   (Sect. 4.1, Eq. (symmetron_dimensionles))
+ *   ISIS_FOFR_HS    phi = u, f_R = -a^-2 e^u:
+ *                   div(e^u grad u) = Om a H0^2 (eta - 1)
+ *                       - Om a^4 H0^2 (1 + 4 OL/Om)(|f_R0| a^2)^{1/(n+1)} e^{-u/(n+1)}
+ *                       + Om a H0^2 (1 + 4 a^3 OL/Om)                  (Sect. 4.2)
+ *                   discretised in flux form with face b = arithmetic mean
+ *                   (Sect. 3.4, Eq. (disc_non_canonical)).
+ *   eta  device array (double, or float for ISIS_F32) of eta = rho / mean rho.
+ *   phi  device array of the same type: initial guess in, solution out (the
+ *        symmetron's zero field is a fixed point: start from a positive guess).
+ *   On ENOCONV the last iterate is in phi and info is filled. */
+isis_status isis_scalar_solve(isis_model model, const isis_params* params, const isis_grid* grid, double a,
+                              const void* eta, void* phi, double tol, const isis_mg_opts* opts,
+                              isis_solve_info* info, void* stream);
+
+/* Per-particle acceleration in super-comoving units (Sects. 4.1, 4.2):
+ *     g = -[ grad Phi~ + F5 ],  Phi~ = a^2 Phi
+ *     ISIS_SYMMETRON  F5 = 6 Om H0^2 (beta lambda0)^2 / a_SSB^3  chi~ grad chi~,  chi~ = a chi
+ *     ISIS_FOFR_HS    F5 = (1/2) e^u grad u
+ * Gradients are 2-point central differences at cells, interpolated to the
+ * particles with the CIC weights of isis_cic_deposit.
+ *   Phi, phi    device arrays (double if fields_f64, else float); either may be
+ *               NULL to leave its term out (model is ignored when phi is NULL).
+ *   x, y, z     device float[npart], cell units.
+ *   gx, gy, gz  device float[npart], overwritten.  */
+isis_status isis_fifth_force(isis_model model, const isis_params* params, const isis_grid* grid, double a,
+                             const void* Phi, const void* phi, int fields_f64, const float* x, const float* y,
+                             const float* z, int64_t npart, float* gx, float* gy, float* gz, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* isis_strerror(isis_status status);
+
+/* Free every cached workspace buffer (synchronises the device first). */
+void isis_release_workspace(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISIS_H */

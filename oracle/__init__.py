@@ -1,0 +1,220 @@
+"""Plain FP64 CPU oracle for the ISIS scalar-field multigrid solve (arXiv:1307.6748).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` use it.  The CUDA library never imports it.
+
+The arithmetic lives in ``isis_oracle.c`` (plain C, FP64, one function per
+paper passage); this module only compiles it with gcc and marshals numpy
+arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "isis_oracle.c")
+_LIB = os.path.join(_HERE, "libisis_oracle.so")
+
+POISSON, SYMMETRON, FOFR = 0, 1, 2
+OK, EINVAL, ENOCONV, ENAN, ENOMEM = 0, -1, -2, -3, -5
+
+# c = 1 units with lengths in Mpc/h: H0 = 100 h km/s/Mpc / c
+H0_MPC = 1.0 / 2997.92458
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``libisis_oracle.so`` (gcc, OpenMP, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("model", ctypes.c_int), ("N", ctypes.c_int), ("box", ctypes.c_double), ("a", ctypes.c_double),
+        ("Omega_m", ctypes.c_double), ("Omega_L", ctypes.c_double), ("H0", ctypes.c_double),
+        ("lambda0", ctypes.c_double), ("beta", ctypes.c_double), ("a_ssb", ctypes.c_double),
+        ("n", ctypes.c_int), ("fR0_abs", ctypes.c_double),
+    ]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [
+        ("cycles", ctypes.c_int), ("coarse_newton_max", ctypes.c_int), ("res0", ctypes.c_double),
+        ("ref", ctypes.c_double), ("res_final", ctypes.c_double), ("hist", ctypes.c_double * 256),
+    ]
+
+
+@dataclass
+class Problem:
+    """Physical set-up of one solve; defaults are the paper's cosmology (Sect. 6.1)."""
+    model: int
+    N: int
+    box: float
+    a: float = 1.0
+    Omega_m: float = 0.267
+    Omega_L: float = 0.733
+    H0: float = H0_MPC
+    lambda0: float = 1.0
+    beta: float = 1.0
+    a_ssb: float = 0.5
+    n: int = 1
+    fR0_abs: float = 1e-5
+
+    def c(self) -> _Problem:
+        return _Problem(self.model, self.N, self.box, self.a, self.Omega_m, self.Omega_L, self.H0,
+                        self.lambda0, self.beta, self.a_ssb, self.n, self.fR0_abs)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        d = P(ctypes.c_double)
+        f = P(ctypes.c_float)
+        _lib.orc_solve.argtypes = [P(_Problem), d, d, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, P(_Info)]
+        _lib.orc_residual.argtypes = [P(_Problem), d, d, d, d]
+        _lib.orc_dL.argtypes = [P(_Problem), d, d, d]
+        _lib.orc_smooth.argtypes = [P(_Problem), d, d, d]
+        _lib.orc_restrict.argtypes = [ctypes.c_int, d, d]
+        _lib.orc_restrict.restype = None
+        _lib.orc_prolong_add.argtypes = [ctypes.c_int, d, d]
+        _lib.orc_prolong_add.restype = None
+        _lib.orc_dense_newton.argtypes = [P(_Problem), d, d, d, P(ctypes.c_int)]
+        _lib.orc_cic_deposit.argtypes = [ctypes.c_int, ctypes.c_int64, f, f, f, d]
+        _lib.orc_gradient.argtypes = [ctypes.c_int, ctypes.c_double, d, d, d, d]
+        _lib.orc_fifth_force.argtypes = [P(_Problem), d, d, ctypes.c_int64, f, f, f, d, d, d]
+    return _lib
+
+
+def _d(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f(a):
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+@dataclass
+class SolveResult:
+    status: int
+    phi: np.ndarray
+    cycles: int
+    res0: float
+    ref: float
+    res_final: float
+    hist: list
+    coarse_newton_max: int
+
+
+def solve(p: Problem, eta: np.ndarray, phi0: np.ndarray, tol: float = 1e-10, nu1: int = 2, nu2: int = 2,
+          ncoarse: int = 4, max_cycles: int = 100) -> SolveResult:
+    """FAS V(nu1,nu2) solve of L(phi) = 0 from the guess phi0 (Sect. 3.2)."""
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    phi = np.array(phi0, dtype=np.float64, order="C", copy=True)
+    assert eta.shape == (p.N,) * 3 and phi.shape == (p.N,) * 3
+    info = _Info()
+    pc = p.c()
+    st = lib().orc_solve(ctypes.byref(pc), _d(eta), _d(phi), tol, nu1, nu2, ncoarse, max_cycles, ctypes.byref(info))
+    return SolveResult(st, phi, info.cycles, info.res0, info.ref, info.res_final,
+                       [info.hist[i] for i in range(info.cycles)], info.coarse_newton_max)
+
+
+def residual(p: Problem, eta, phi, sigma=None) -> np.ndarray:
+    """L(phi) - Sigma on one grid."""
+    out = np.empty((p.N,) * 3)
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    sg = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64)
+    pc = p.c()
+    assert lib().orc_residual(ctypes.byref(pc), _d(eta), _d(phi), _d(sg), _d(out)) == OK
+    return out
+
+
+def dL(p: Problem, eta, phi) -> np.ndarray:
+    """Diagonal derivative dL_c/dphi_c on one grid."""
+    out = np.empty((p.N,) * 3)
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    pc = p.c()
+    assert lib().orc_dL(ctypes.byref(pc), _d(eta), _d(phi), _d(out)) == OK
+    return out
+
+
+def smooth(p: Problem, eta, phi, sigma=None) -> np.ndarray:
+    """One red-black Newton-Gauss-Seidel sweep; returns the new field."""
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    out = np.array(phi, dtype=np.float64, order="C", copy=True)
+    sg = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64)
+    pc = p.c()
+    assert lib().orc_smooth(ctypes.byref(pc), _d(eta), _d(out), _d(sg)) == OK
+    return out
+
+
+def restrict(fine: np.ndarray) -> np.ndarray:
+    fine = np.ascontiguousarray(fine, dtype=np.float64)
+    NH = fine.shape[0] // 2
+    out = np.empty((NH,) * 3)
+    lib().orc_restrict(NH, _d(fine), _d(out))
+    return out
+
+
+def prolong_add(cdelta: np.ndarray, fine: np.ndarray) -> np.ndarray:
+    cdelta = np.ascontiguousarray(cdelta, dtype=np.float64)
+    out = np.array(fine, dtype=np.float64, order="C", copy=True)
+    lib().orc_prolong_add(cdelta.shape[0], _d(cdelta), _d(out))
+    return out
+
+
+def dense_newton(p: Problem, eta, phi0, sigma=None):
+    """Dense exact-Jacobian Newton solve of L(phi) = Sigma on one small grid."""
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    phi = np.array(phi0, dtype=np.float64, order="C", copy=True)
+    sg = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64)
+    steps = ctypes.c_int(0)
+    pc = p.c()
+    st = lib().orc_dense_newton(ctypes.byref(pc), _d(eta), _d(phi), _d(sg), ctypes.byref(steps))
+    return st, phi, steps.value
+
+
+def cic_deposit(N: int, x, y, z) -> np.ndarray:
+    """CIC density eta (mean 1) from particle positions in cell units (Sect. 5.1)."""
+    x, y, z = (np.ascontiguousarray(v, dtype=np.float32) for v in (x, y, z))
+    out = np.empty((N,) * 3)
+    assert lib().orc_cic_deposit(N, x.size, _f(x), _f(y), _f(z), _d(out)) == OK
+    return out
+
+
+def gradient(f: np.ndarray, box: float):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    N = f.shape[0]
+    g = [np.empty_like(f) for _ in range(3)]
+    lib().orc_gradient(N, box, _d(f), _d(g[0]), _d(g[1]), _d(g[2]))
+    return g
+
+
+def fifth_force(p: Problem, Phi, phi, x, y, z):
+    """Per-particle acceleration -[grad Phi~ + F5] (Sects. 4.1, 4.2); Phi or phi may be None."""
+    x, y, z = (np.ascontiguousarray(v, dtype=np.float32) for v in (x, y, z))
+    Phi = None if Phi is None else np.ascontiguousarray(Phi, dtype=np.float64)
+    phi = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+    g = [np.empty(x.size) for _ in range(3)]
+    pc = p.c()
+    assert lib().orc_fifth_force(ctypes.byref(pc), _d(Phi), _d(phi), x.size, _f(x), _f(y), _f(z),
+                                 _d(g[0]), _d(g[1]), _d(g[2])) == OK
+    return g

@@ -1,0 +1,212 @@
+// isis_api.cu -- the C ABI of include/isis.h: argument checks, the model
+// constants, the workspace cache, and dispatch to the per-model drivers.
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "isis_solver.cuh"
+
+namespace isis {
+
+isis_status run_poi(const SolveArgs& A);
+isis_status run_sym(const SolveArgs& A);
+isis_status run_fofr(const SolveArgs& A);
+
+// ---------------------------------------------------------------------------
+// Workspace cache: one hierarchy per (device, N, element size, coarsest size)
+// ---------------------------------------------------------------------------
+
+static std::vector<Workspace*> g_ws;
+
+static void free_ws(Workspace* w) {
+  for (void* p : w->owned) cudaFree(p);
+  if (w->host) cudaFreeHost(w->host);
+  delete w;
+}
+
+Workspace* get_workspace(int N, int esize, int ncoarse) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  for (Workspace* w : g_ws)
+    if (w->N == N && w->esize == esize && w->device == dev && (N >> (w->nlev - 1)) == ncoarse) return w;
+  Workspace* w = new Workspace();
+  w->N = N;
+  w->esize = esize;
+  w->device = dev;
+  int nlev = 1;
+  while ((N >> (nlev - 1)) > ncoarse) ++nlev;
+  w->nlev = nlev;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    w->owned.push_back(p);
+    return p;
+  };
+  bool ok = true;
+  std::vector<void*>* arrays[6] = {&w->x, &w->x0, &w->sig, &w->eta, &w->B, &w->w};
+  for (int l = 0; l < nlev && ok; ++l) {
+    size_t nl = (size_t)(N >> l) * (N >> l) * (N >> l);
+    for (auto* a : arrays) {
+      // the finest level's buffers only serve the FP32 correction cycles
+      void* p = (l == 0 && esize != 4) ? nullptr : alloc(nl * esize);
+      if (!(l == 0 && esize != 4) && !p) ok = false;
+      a->push_back(p);
+    }
+  }
+  if (ok) {
+    w->part = (double*)alloc(kNormBlocks * sizeof(double));
+    w->part2 = (double*)alloc(kNormBlocks * sizeof(double));
+    w->scal = (double*)alloc(8 * sizeof(double));
+    w->iflags = (int*)alloc(8 * sizeof(int));
+    ok = w->part && w->part2 && w->scal && w->iflags;
+  }
+  if (ok && cudaMallocHost(&w->host, 256) != cudaSuccess) ok = false;
+  if (!ok) {
+    free_ws(w);
+    cudaGetLastError();
+    return nullptr;
+  }
+  g_ws.push_back(w);
+  return w;
+}
+
+// int64 accumulation buffer of the CIC deposit, cached per (device, N)
+struct DepositBuf {
+  int N, device;
+  unsigned long long* acc;
+};
+static std::vector<DepositBuf> g_dep;
+
+unsigned long long* get_deposit_buf(int N) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  for (auto& d : g_dep)
+    if (d.N == N && d.device == dev) return d.acc;
+  void* p = nullptr;
+  if (cudaMalloc(&p, (size_t)N * N * N * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  g_dep.push_back({N, dev, (unsigned long long*)p});
+  return (unsigned long long*)p;
+}
+
+// ---------------------------------------------------------------------------
+// Argument checks and model constants
+// ---------------------------------------------------------------------------
+
+static bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+static bool grid_ok(const isis_grid* g) {
+  return g && pow2(g->N) && g->N >= 8 && g->N <= 1024 && g->box > 0 && std::isfinite(g->box) && g->H0 > 0 &&
+         g->Omega_m > 0 && g->Omega_L >= 0;
+}
+
+static bool opts_resolve(const isis_mg_opts* o, isis_mg_opts* out, int N) {
+  isis_mg_opts d = {2, 2, 4, 100, ISIS_F64, 2};
+  if (o) d = *o;
+  if (d.nu1 < 0 || d.nu1 > 16 || d.nu2 < 0 || d.nu2 > 16) return false;
+  if (d.n_coarsest != 2 && d.n_coarsest != 4) return false;
+  if (d.n_coarsest * 2 > N) return false;
+  if (d.max_cycles < 0 || d.max_cycles > 128) return false;
+  if (d.prec != ISIS_F64 && d.prec != ISIS_F32 && d.prec != ISIS_F32_REFINE64) return false;
+  if (d.inner_cycles < 1 || d.inner_cycles > 16) return false;
+  *out = d;
+  return true;
+}
+
+static void fill_common(SolveArgs& A, const isis_grid* g, double a, const void* eta, void* phi, double tol,
+                        const isis_mg_opts& o, isis_solve_info* info, void* stream) {
+  A.N = g->N;
+  A.box = g->box;
+  A.a = a;
+  A.eta = eta;
+  A.phi = phi;
+  A.tol = tol;
+  A.nu1 = o.nu1;
+  A.nu2 = o.nu2;
+  A.ncoarse = o.n_coarsest;
+  A.max_cycles = o.max_cycles;
+  A.inner = o.inner_cycles;
+  A.prec = o.prec;
+  A.info = info;
+  A.st = (cudaStream_t)stream;
+  std::memset(&A.coef, 0, sizeof(A.coef));
+}
+
+}  // namespace isis
+
+using namespace isis;
+
+extern "C" {
+
+const char* isis_strerror(isis_status s) {
+  switch (s) {
+    case ISIS_OK: return "ok";
+    case ISIS_EINVAL: return "invalid argument";
+    case ISIS_ENOCONV: return "no convergence within max_cycles";
+    case ISIS_ENAN: return "non-finite residual or singular coarsest Jacobian";
+    case ISIS_ECUDA: return "CUDA error";
+    case ISIS_ENOMEM: return "device allocation failed";
+    case ISIS_ETIMEOUT: return "device wait timed out";
+    case ISIS_EINTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+void isis_release_workspace(void) {
+  cudaDeviceSynchronize();
+  for (Workspace* w : g_ws) free_ws(w);
+  g_ws.clear();
+  for (auto& d : g_dep) cudaFree(d.acc);
+  g_dep.clear();
+}
+
+isis_status isis_poisson_solve(const isis_grid* grid, double a, const void* eta, void* Phi, double tol,
+                               const isis_mg_opts* opts, isis_solve_info* info, void* stream) {
+  isis_mg_opts o;
+  if (!grid_ok(grid) || !eta || !Phi || !(a > 0) || !(tol >= 0) || !opts_resolve(opts, &o, grid->N))
+    return ISIS_EINVAL;
+  SolveArgs A;
+  fill_common(A, grid, a, eta, Phi, tol, o, info, stream);
+  // Sect. 3.1: lap Phi = (3/2) Om H0^2 delta / a
+  A.coef.KP = 1.5 * grid->Omega_m * grid->H0 * grid->H0 / a;
+  A.ref_scale = A.coef.KP;
+  return run_poi(A);
+}
+
+isis_status isis_scalar_solve(isis_model model, const isis_params* p, const isis_grid* grid, double a,
+                              const void* eta, void* phi, double tol, const isis_mg_opts* opts,
+                              isis_solve_info* info, void* stream) {
+  isis_mg_opts o;
+  if (!grid_ok(grid) || !p || !eta || !phi || !(a > 0) || !(tol >= 0) || !opts_resolve(opts, &o, grid->N))
+    return ISIS_EINVAL;
+  SolveArgs A;
+  fill_common(A, grid, a, eta, phi, tol, o, info, stream);
+  const double H02 = grid->H0 * grid->H0;
+  if (model == ISIS_SYMMETRON) {
+    if (!(p->lambda0 > 0) || !(p->a_ssb > 0)) return ISIS_EINVAL;
+    // Sect. 4.1, Eq. (symmetron_dimensionles)
+    A.coef.A = a * a / (2.0 * p->lambda0 * p->lambda0);
+    double q = p->a_ssb / a;
+    A.coef.s = q * q * q;
+    double chi_bg = A.coef.s < 1.0 ? std::sqrt(1.0 - A.coef.s) : 0.0;
+    A.ref_scale = A.coef.A * A.coef.s * chi_bg;
+    return run_sym(A);
+  }
+  if (model == ISIS_FOFR_HS) {
+    if (p->n < 1 || p->n > 8 || !(p->fR0_abs > 0)) return ISIS_EINVAL;
+    // Sect. 4.2, the non-canonical equation for u with b = e^u
+    double r = grid->Omega_L / grid->Omega_m, np1 = p->n + 1.0;
+    A.coef.np1 = np1;
+    A.coef.inv_np1 = 1.0 / np1;
+    A.coef.K1 = grid->Omega_m * a * H02;
+    A.coef.K2 = grid->Omega_m * a * a * a * a * H02 * (1.0 + 4.0 * r) * std::pow(p->fR0_abs * a * a, 1.0 / np1);
+    A.coef.K3 = grid->Omega_m * a * H02 * (1.0 + 4.0 * a * a * a * r);
+    A.ref_scale = A.coef.K1;
+    return run_fofr(A);
+  }
+  return ISIS_EINVAL;
+}
+
+}  // extern "C"

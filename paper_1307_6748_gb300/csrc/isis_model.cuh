@@ -1,0 +1,131 @@
+// isis_model.cuh -- per-cell operator L, its diagonal derivative and the
+// Newton-Gauss-Seidel update for the three equations of the ISIS solver
+// (Llinares, Mota & Winther 2013, arXiv:1307.6748).
+//
+//   Poisson   L(Phi) = lap Phi - KP (eta - <eta>)        Sect. 3.1, Eq. (disc_lap)
+//   symmetron L(chi) = lap chi - A[(s eta - 1) chi + chi^3]
+//                                                         Sect. 4.1, Eq. (symmetron_dimensionles)
+//   f(R)      L(u)   = h^-2 sum_f b_f (u_nb - u) - S(u),  b_f = (e^u + e^u_nb)/2
+//             S(u)   = K1 (eta - 1) - K2 e^{-u/(n+1)} + K3
+//                                                         Sect. 3.4 Eq. (disc_non_canonical), Sect. 4.2
+//   update    x <- x - (L - Sigma) / (dL/dx)              Sect. 3.2
+//   dL/dx     canonical: -6/h^2 - dS/dx                    Sect. 3.3
+//             f(R): h^-2 sum_f [-b_f + (e^u/2)(u_nb - u)] - dS/du
+//                   (Eq. (dbeq) with the exact factor 1/2 of the face average)
+//
+// Two forms of every operator:
+//   FIELD  the unknown x is the field itself (phi, chi or u).
+//   DELTA  the unknown x = e is a correction about a fixed base field B:
+//          N_B(e) = L(B + e) - L(B), written so that no large terms cancel
+//          (used by the FP32 inner cycles of the FP64 defect-correction loop).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace isis {
+
+enum Model : int { POI = 0, SYM = 1, FOFR = 2 };
+enum Form : int { FIELD = 0, DELTA = 1 };
+
+// Constants of the source terms; host code fills them from the physical
+// parameters (see isis_api.cu).
+struct Coef {
+  double A, s;          // symmetron: A = a^2/(2 lambda0^2), s = (a_SSB/a)^3
+  double K1, K2, K3;    // f(R) source constants (Sect. 4.2)
+  double np1, inv_np1;  // n + 1 and its inverse
+  double KP, eta_mean;  // Poisson: KP = 1.5 Om H0^2 / a, mean density
+};
+
+// Values of one cell and its six neighbours, in the order
+// (i+1, i-1, j+1, j-1, k+1, k-1).
+template <class T>
+struct Cell {
+  T x, xn[6];      // unknown
+  T eta, sig;      // density and FAS source
+  T B, Bn[6];      // base field (DELTA form)
+  T w, wn[6];      // e^B (f(R) DELTA form)
+};
+
+template <class T> __device__ __forceinline__ T dexp(T v);
+template <> __device__ __forceinline__ double dexp<double>(double v) { return exp(v); }
+template <> __device__ __forceinline__ float dexp<float>(float v) { return __expf(v); }
+template <class T> __device__ __forceinline__ T dexpm1(T v);
+template <> __device__ __forceinline__ double dexpm1<double>(double v) { return expm1(v); }
+template <> __device__ __forceinline__ float dexpm1<float>(float v) { return expm1f(v); }
+
+// F = L(x) - Sigma and dF = dL/dx at one cell.
+template <Model M, Form FM, class T>
+__device__ __forceinline__ void eval_cell(const Coef& c, T ih2, const Cell<T>& q, T& F, T& dF) {
+  if constexpr (M == POI) {
+    T lap = (((q.xn[0] + q.xn[1]) + (q.xn[2] + q.xn[3])) + (q.xn[4] + q.xn[5]) - T(6) * q.x) * ih2;
+    if constexpr (FM == FIELD) F = lap - T(c.KP) * (q.eta - T(c.eta_mean)) - q.sig;
+    else F = lap - q.sig;  // linear: N(e) = lap e
+    dF = T(-6) * ih2;
+  } else if constexpr (M == SYM) {
+    T lap = (((q.xn[0] + q.xn[1]) + (q.xn[2] + q.xn[3])) + (q.xn[4] + q.xn[5]) - T(6) * q.x) * ih2;
+    T A = T(c.A), sm1 = T(c.s) * q.eta - T(1);
+    if constexpr (FM == FIELD) {
+      T x2 = q.x * q.x;
+      F = lap - A * (sm1 + x2) * q.x - q.sig;
+      dF = T(-6) * ih2 - A * (sm1 + T(3) * x2);
+    } else {
+      // (B+e)^3 - B^3 = e (3B^2 + 3Be + e^2)
+      T e = q.x, B = q.B;
+      T cub = e * (T(3) * B * B + e * (T(3) * B + e));
+      F = lap - A * (sm1 * e + cub) - q.sig;
+      T u = B + e;
+      dF = T(-6) * ih2 - A * (sm1 + T(3) * u * u);
+    }
+  } else {  // FOFR
+    T K2 = T(c.K2), inp1 = T(c.inv_np1);
+    if constexpr (FM == FIELD) {
+      T bu = dexp<T>(q.x);
+      T flux = 0, dsum = 0;
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        T du = q.xn[d] - q.x;
+        T bf = T(0.5) * (bu + dexp<T>(q.xn[d]));
+        flux += bf * du;
+        dsum += T(0.5) * bu * du - bf;
+      }
+      T ex = dexp<T>(-q.x * inp1);
+      T S = T(c.K1) * (q.eta - T(1)) - K2 * ex + T(c.K3);
+      F = flux * ih2 - S - q.sig;
+      dF = dsum * ih2 - K2 * inp1 * ex;
+    } else {
+      // N_B(e) = h^-2 sum_f { (m + m_nb)/2 (B_nb - B) + (bt + bt_nb)/2 (e_nb - e) }
+      //          + K2 e^{-B/(n+1)} expm1(-e/(n+1))
+      // with m = e^B expm1(e) and bt = e^{B+e} = e^B + m.
+      T m = q.w * dexpm1<T>(q.x), bt = q.w + m;
+      T flux = 0, dsum = 0;
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        T mn = q.wn[d] * dexpm1<T>(q.xn[d]), btn = q.wn[d] + mn;
+        T dB = q.Bn[d] - q.B, de = q.xn[d] - q.x;
+        T bf = T(0.5) * (bt + btn);
+        flux += T(0.5) * (m + mn) * dB + bf * de;
+        dsum += T(0.5) * bt * (dB + de) - bf;
+      }
+      T exB = dexp<T>(-q.B * inp1);
+      F = flux * ih2 + K2 * exB * dexpm1<T>(-q.x * inp1) - q.sig;
+      dF = dsum * ih2 - K2 * inp1 * exB * dexp<T>(-q.x * inp1);
+    }
+  }
+}
+
+// Off-diagonal Jacobian entry dF_c/dx_nb for neighbour direction d (used by
+// the dense coarsest-level Newton solve).
+template <Model M, Form FM>
+__device__ __forceinline__ double eval_offdiag(const Coef& c, double ih2, const Cell<double>& q, int d) {
+  (void)c;
+  if constexpr (M == FOFR) {
+    double u = (FM == FIELD) ? q.x : q.B + q.x;
+    double un = (FM == FIELD) ? q.xn[d] : q.Bn[d] + q.xn[d];
+    double bu = exp(u), bn = exp(un);
+    return (0.5 * (bu + bn) + 0.5 * bn * (un - u)) * ih2;
+  } else {
+    return ih2;
+  }
+}
+
+}  // namespace isis

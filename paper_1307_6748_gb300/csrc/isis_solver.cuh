@@ -1,0 +1,438 @@
+// isis_solver.cuh -- host orchestration of the FAS multigrid solve
+// (Sect. 3.2 of arXiv:1307.6748): level hierarchy, V-cycles, convergence
+// test, and the FP64 defect-correction loop around FP32 correction cycles.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../include/isis.h"
+#include "isis_coarse.cuh"
+
+namespace isis {
+
+// ---------------------------------------------------------------------------
+// Device buffers
+// ---------------------------------------------------------------------------
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// One cached allocation set per (N, element size); see isis_api.cu.
+struct Workspace {
+  int N = 0, esize = 0, device = -1;
+  int nlev = 0;
+  // per level l (0 = finest): x, x0, sig, eta, B, w (element type T)
+  std::vector<void*> x, x0, sig, eta, B, w;
+  double* part = nullptr;     // kNormBlocks partial sums
+  double* part2 = nullptr;    // second set of partials
+  double* scal = nullptr;     // device scalars: [0] norm^2, [1] sum, [2] aux
+  int* iflags = nullptr;      // [0] coarse flags, [1] coarse steps max
+  void* host = nullptr;       // pinned readback area
+  std::vector<void*> owned;
+};
+
+// Returns nullptr on allocation failure.  Implemented in isis_api.cu.
+Workspace* get_workspace(int N, int esize, int ncoarse);
+
+// Common arguments of one solve.
+struct SolveArgs {
+  int N;
+  double box, a;
+  Coef coef;
+  const void* eta;
+  void* phi;
+  double tol;
+  int nu1, nu2, ncoarse, max_cycles, inner;
+  isis_precision prec;
+  isis_solve_info* info;
+  cudaStream_t st;
+  // reference residual: ref = ref_scale * RMS(eta - eta_ref) (eta_ref = <eta> for Poisson)
+  double ref_scale;
+};
+
+#define ISIS_CK(call)                              \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return ISIS_ECUDA;      \
+  } while (0)
+#define ISIS_CKL() ISIS_CK(cudaGetLastError())
+
+inline int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// V-cycle driver for one model / form / element type
+// ---------------------------------------------------------------------------
+
+template <Model M, Form FM, class T>
+struct Cycler {
+  std::vector<LevelView<T>> L;
+  Workspace* ws = nullptr;
+  Coef c;
+  int nu1 = 2, nu2 = 2;
+  cudaStream_t st = 0;
+
+  // Build level views; level 0 uses (x0_, eta0, sig0, B0, w0).
+  void setup(Workspace* w, const SolveArgs& A, T* xfine, const T* etafine, const T* sigfine) {
+    ws = w;
+    c = A.coef;
+    nu1 = A.nu1;
+    nu2 = A.nu2;
+    st = A.st;
+    L.resize(ws->nlev);
+    for (int l = 0; l < ws->nlev; ++l) {
+      int N = A.N >> l;
+      double h = A.box / N;
+      LevelView<T> v;
+      v.N = N;
+      v.lg = ilog2(N);
+      v.ih2 = (T)(1.0 / (h * h));
+      v.x = l == 0 ? xfine : (T*)ws->x[l];
+      v.eta = l == 0 ? etafine : (const T*)ws->eta[l];
+      v.sig = l == 0 ? sigfine : (const T*)ws->sig[l];
+      v.B = (const T*)ws->B[l];
+      v.w = (const T*)ws->w[l];
+      L[l] = v;
+    }
+  }
+
+  isis_status smooth(int l, int sweeps) {
+    const LevelView<T>& v = L[l];
+    size_t half = ((size_t)v.N * v.N * v.N) / 2;
+    for (int s = 0; s < sweeps; ++s)
+      for (int color = 0; color < 2; ++color) {
+        smooth_color<M, FM, T><<<nblk(half, 256), 256, 0, st>>>(v, c, color);
+        ISIS_CKL();
+      }
+    return ISIS_OK;
+  }
+
+  isis_status vcycle(int l) {
+    const int last = (int)L.size() - 1;
+    if (l == last) {
+      coarse_newton<M, FM, T><<<1, kCoarseMax, 0, st>>>(L[l], c, ws->iflags, ws->iflags + 1);
+      ISIS_CKL();
+      return ISIS_OK;
+    }
+    isis_status s = smooth(l, nu1);
+    if (s != ISIS_OK) return s;
+    LevelView<T>& C = L[l + 1];
+    size_t nc = (size_t)C.N * C.N * C.N;
+    resid_restrict<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], c, C.x, (T*)ws->x0[l + 1], (T*)ws->sig[l + 1]);
+    ISIS_CKL();
+    coarse_sigma_add<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(C, c, (T*)ws->sig[l + 1]);
+    ISIS_CKL();
+    s = vcycle(l + 1);
+    if (s != ISIS_OK) return s;
+    size_t nf = (size_t)L[l].N * L[l].N * L[l].N;
+    prolong_correct<T><<<nblk(nf, 256), 256, 0, st>>>(L[l].x, C.x, (const T*)ws->x0[l + 1], C.lg);
+    ISIS_CKL();
+    return smooth(l, nu2);
+  }
+
+  // RMS of L(x) - Sigma on the finest level (blocking: one stream sync).
+  isis_status fine_rms(double* out) {
+    norm_partial<M, FM, T><<<kNormBlocks, kNormThreads, 0, st>>>(L[0], c, ws->part);
+    ISIS_CKL();
+    reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal);
+    ISIS_CKL();
+    double* h = (double*)ws->host;
+    int* hi = (int*)(h + 4);
+    ISIS_CK(cudaMemcpyAsync(h, ws->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ISIS_CK(cudaMemcpyAsync(hi, ws->iflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    ISIS_CK(cudaStreamSynchronize(st));
+    size_t n = (size_t)L[0].N * L[0].N * L[0].N;
+    *out = std::sqrt(h[0] / (double)n);
+    if (hi[0] != 0) return ISIS_ENAN;
+    return ISIS_OK;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Reductions used by the drivers
+// ---------------------------------------------------------------------------
+
+// sum((v - shift)^2) and sum(v) over n values (blocking).
+template <class T>
+isis_status moments(Workspace* ws, const T* v, size_t n, double shift, cudaStream_t st, double* s2, double* s1) {
+  moments_partial<T><<<kNormBlocks, kNormThreads, 0, st>>>(v, n, shift, ws->part, ws->part2);
+  ISIS_CKL();
+  reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal);
+  ISIS_CKL();
+  reduce_final<<<1, kNormThreads, 0, st>>>(ws->part2, kNormBlocks, ws->scal + 1);
+  ISIS_CKL();
+  double* h = (double*)ws->host;
+  ISIS_CK(cudaMemcpyAsync(h, ws->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  ISIS_CK(cudaStreamSynchronize(st));
+  *s2 = h[0];
+  *s1 = h[1];
+  return ISIS_OK;
+}
+
+template <class T>
+__global__ void add_scalar(T* __restrict__ v, size_t n, const double* __restrict__ sum, double inv_n) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) v[t] = (T)((double)v[t] - (*sum) * inv_n);
+}
+
+// v -= mean(v), device-side (no host sync): partial sums, final sum, subtract.
+template <class T>
+isis_status remove_mean(Workspace* ws, T* v, size_t n, cudaStream_t st) {
+  moments_partial<T><<<kNormBlocks, kNormThreads, 0, st>>>(v, n, 0.0, ws->part, ws->part2);
+  ISIS_CKL();
+  reduce_final<<<1, kNormThreads, 0, st>>>(ws->part2, kNormBlocks, ws->scal + 1);
+  ISIS_CKL();
+  add_scalar<T><<<nblk(n, 256), 256, 0, st>>>(v, n, ws->scal + 1, 1.0 / (double)n);
+  ISIS_CKL();
+  return ISIS_OK;
+}
+
+template <class Tin, class Tout>
+__global__ void convert_k(const Tin* __restrict__ a, Tout* __restrict__ b, size_t n) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = (Tout)a[t];
+}
+
+template <class T>
+__global__ void exp_k(const T* __restrict__ a, T* __restrict__ b, size_t n) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = dexp<T>(a[t]);
+}
+
+template <class T>
+__global__ void fill_k(T* __restrict__ a, T v, size_t n) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) a[t] = v;
+}
+
+__global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, size_t n);
+
+// FP64 residual of the finest grid for the defect-correction loop:
+// r = -L64(phi); writes r and B = phi rounded to FP32, and block partials of r^2.
+template <Model M>
+__global__ void __launch_bounds__(kNormThreads) outer_residual(LevelView<double> L, Coef c, float* __restrict__ r32,
+                                                               float* __restrict__ B32, double* __restrict__ part) {
+  size_t n = (size_t)1 << (3 * L.lg);
+  double acc = 0.0;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    int k = (int)(t & (L.N - 1)), j = (int)((t >> L.lg) & (L.N - 1)), i = (int)(t >> (2 * L.lg));
+    Cell<double> q = gather<M, FIELD, double>(L, i, j, k);
+    double F, dF;
+    eval_cell<M, FIELD, double>(c, L.ih2, q, F, dF);
+    r32[t] = (float)(-F);
+    B32[t] = (float)q.x;
+    acc += F * F;
+  }
+  block_sum_store<double>(acc, part);
+}
+
+// ---------------------------------------------------------------------------
+// Drivers
+// ---------------------------------------------------------------------------
+
+inline void info_reset(isis_solve_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+}
+
+// Plain solve: every level in type T, field form, in place on phi.
+template <Model M, class T>
+isis_status solve_field(const SolveArgs& A) {
+  Workspace* ws = get_workspace(A.N, sizeof(T), A.ncoarse);
+  if (!ws) return ISIS_ENOMEM;
+  cudaStream_t st = A.st;
+  const size_t n = (size_t)A.N * A.N * A.N;
+  const T* eta = (const T*)A.eta;
+  T* phi = (T*)A.phi;
+  Coef c = A.coef;
+  isis_solve_info loc;
+  info_reset(&loc);
+
+  double s2, s1;
+  isis_status s = moments<T>(ws, eta, n, 1.0, st, &s2, &s1);
+  if (s != ISIS_OK) return s;
+  double eta_mean = s1 / (double)n;
+  if (M == POI) {
+    c.eta_mean = eta_mean;
+    // sum (eta - <eta>)^2 = sum (eta - 1)^2 - n (<eta> - 1)^2
+    s2 = s2 - (double)n * (eta_mean - 1.0) * (eta_mean - 1.0);
+    if (s2 < 0) s2 = 0;
+  }
+  double ref = A.ref_scale * std::sqrt(s2 / (double)n);
+
+  // density on the coarse levels
+  for (int l = 1; l < ws->nlev; ++l) {
+    int lgc = ilog2(A.N >> l);
+    const T* f = l == 1 ? eta : (const T*)ws->eta[l - 1];
+    restrict_mean<T, T><<<nblk((size_t)1 << (3 * lgc), 256), 256, 0, st>>>(f, (T*)ws->eta[l], lgc);
+    ISIS_CKL();
+  }
+  ISIS_CK(cudaMemsetAsync(ws->iflags, 0, 2 * sizeof(int), st));
+
+  Cycler<M, FIELD, T> cy;
+  SolveArgs A2 = A;
+  A2.coef = c;
+  cy.setup(ws, A2, phi, eta, nullptr);
+
+  double res;
+  s = cy.fine_rms(&res);
+  if (s != ISIS_OK) return s;
+  loc.res0 = res;
+  if (!(ref > 0.0)) ref = res;
+  loc.res_ref = ref;
+  loc.res_final = res;
+  double target = A.tol * ref;
+  isis_status out = ISIS_ENOCONV;
+  if (!std::isfinite(res)) out = ISIS_ENAN;
+  else if (res <= target) out = ISIS_OK;
+  else {
+    for (int cyc = 0; cyc < A.max_cycles; ++cyc) {
+      s = cy.vcycle(0);
+      if (s != ISIS_OK) { out = s; break; }
+      if (M == POI) {
+        s = remove_mean<T>(ws, phi, n, st);
+        if (s != ISIS_OK) { out = s; break; }
+      }
+      s = cy.fine_rms(&res);
+      loc.cycles = cyc + 1;
+      loc.hist[cyc] = res;
+      loc.res_final = res;
+      if (s != ISIS_OK) { out = s; break; }
+      if (!std::isfinite(res)) { out = ISIS_ENAN; break; }
+      if (res <= target) { out = ISIS_OK; break; }
+    }
+  }
+  if (A.info) *A.info = loc;
+  return out;
+}
+
+// FP64 defect correction with FP32 correction cycles (DELTA form).
+template <Model M>
+isis_status solve_refine(const SolveArgs& A) {
+  Workspace* ws = get_workspace(A.N, sizeof(float), A.ncoarse);
+  if (!ws) return ISIS_ENOMEM;
+  cudaStream_t st = A.st;
+  const size_t n = (size_t)A.N * A.N * A.N;
+  const double* eta64 = (const double*)A.eta;
+  double* phi64 = (double*)A.phi;
+  Coef c = A.coef;
+  isis_solve_info loc;
+  info_reset(&loc);
+
+  // FP32 buffers of the finest level: x = e, sig = r, eta, B, w
+  float* e0 = (float*)ws->x[0];
+  float* r0 = (float*)ws->sig[0];
+  float* eta0 = (float*)ws->eta[0];
+  float* B0 = (float*)ws->B[0];
+
+  double s2, s1;
+  isis_status s = moments<double>(ws, eta64, n, 1.0, st, &s2, &s1);
+  if (s != ISIS_OK) return s;
+  double eta_mean = s1 / (double)n;
+  if (M == POI) {
+    c.eta_mean = eta_mean;
+    s2 = s2 - (double)n * (eta_mean - 1.0) * (eta_mean - 1.0);
+    if (s2 < 0) s2 = 0;
+  }
+  double ref = A.ref_scale * std::sqrt(s2 / (double)n);
+
+  if (M != POI) {
+    convert_k<double, float><<<nblk(n, 256), 256, 0, st>>>(eta64, eta0, n);
+    ISIS_CKL();
+    for (int l = 1; l < ws->nlev; ++l) {
+      int lgc = ilog2(A.N >> l);
+      restrict_mean<float, float><<<nblk((size_t)1 << (3 * lgc), 256), 256, 0, st>>>(
+          (const float*)ws->eta[l - 1], (float*)ws->eta[l], lgc);
+      ISIS_CKL();
+    }
+  }
+  ISIS_CK(cudaMemsetAsync(ws->iflags, 0, 2 * sizeof(int), st));
+
+  // FP64 view of the finest level for the outer residual
+  LevelView<double> F64;
+  F64.N = A.N;
+  F64.lg = ilog2(A.N);
+  F64.ih2 = 1.0 / ((A.box / A.N) * (A.box / A.N));
+  F64.x = phi64;
+  F64.eta = eta64;
+  F64.sig = nullptr;
+  F64.B = nullptr;
+  F64.w = nullptr;
+
+  Cycler<M, DELTA, float> cy;
+  SolveArgs A2 = A;
+  A2.coef = c;
+  cy.setup(ws, A2, e0, eta0, r0);
+
+  double* h = (double*)ws->host;
+  int* hi = (int*)(h + 4);
+  isis_status out = ISIS_ENOCONV;
+  double target = 0.0;
+  for (int outer = 0;; ++outer) {
+    // r = -L64(phi64), B = fp32(phi64), RMS of r
+    outer_residual<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64, c, r0, B0, ws->part);
+    ISIS_CKL();
+    reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal);
+    ISIS_CKL();
+    ISIS_CK(cudaMemcpyAsync(h, ws->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ISIS_CK(cudaMemcpyAsync(hi, ws->iflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    ISIS_CK(cudaStreamSynchronize(st));
+    double res = std::sqrt(h[0] / (double)n);
+    if (outer == 0) {
+      loc.res0 = res;
+      if (!(ref > 0.0)) ref = res;
+      loc.res_ref = ref;
+      target = A.tol * ref;
+    } else {
+      loc.hist[outer - 1] = res;
+    }
+    loc.res_final = res;
+    loc.outer = outer;
+    if (hi[0] != 0) { out = ISIS_ENAN; break; }
+    if (!std::isfinite(res)) { out = ISIS_ENAN; break; }
+    if (res <= target) { out = ISIS_OK; break; }
+    if (loc.cycles >= A.max_cycles || outer >= 127) { out = ISIS_ENOCONV; break; }
+
+    // base field on every level (B_l = R B_{l-1}) and e^B for f(R)
+    for (int l = 1; l < ws->nlev && M != POI; ++l) {
+      int lgc = ilog2(A.N >> l);
+      restrict_mean<float, float><<<nblk((size_t)1 << (3 * lgc), 256), 256, 0, st>>>(
+          (const float*)ws->B[l - 1], (float*)ws->B[l], lgc);
+      ISIS_CKL();
+    }
+    if (M == FOFR) {
+      for (int l = 0; l < ws->nlev; ++l) {
+        size_t nl = (size_t)(A.N >> l) * (A.N >> l) * (A.N >> l);
+        exp_k<float><<<nblk(nl, 256), 256, 0, st>>>((const float*)ws->B[l], (float*)ws->w[l], nl);
+        ISIS_CKL();
+      }
+    }
+    ISIS_CK(cudaMemsetAsync(e0, 0, n * sizeof(float), st));
+    int k = A.inner;
+    if (loc.cycles + k > A.max_cycles) k = A.max_cycles - loc.cycles;
+    for (int it = 0; it < k; ++it) {
+      s = cy.vcycle(0);
+      if (s != ISIS_OK) return s;
+    }
+    loc.cycles += k;
+    update_phi64<<<nblk(n, 256), 256, 0, st>>>(phi64, e0, n);
+    ISIS_CKL();
+    if (M == POI) {
+      s = remove_mean<double>(ws, phi64, n, st);
+      if (s != ISIS_OK) return s;
+    }
+  }
+  if (A.info) *A.info = loc;
+  return out;
+}
+
+}  // namespace isis

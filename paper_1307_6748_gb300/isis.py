@@ -1,0 +1,256 @@
+"""Python binding of the C ABI in ``include/isis.h`` (ctypes over libisis_gb300.so).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+Arrays are torch CUDA tensors (contiguous, on the current device); the stream
+is torch's current stream unless one is passed.  The library must have been
+built (``paper_1307_6748_gb300.build.build()``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libisis_gb300.so")
+
+ISIS_OK, ISIS_EINVAL, ISIS_ENOCONV, ISIS_ENAN, ISIS_ECUDA, ISIS_ENOMEM, ISIS_ETIMEOUT, ISIS_EINTERNAL = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+ISIS_SYMMETRON, ISIS_FOFR_HS = 1, 2
+ISIS_F64, ISIS_F32, ISIS_F32_REFINE64 = 0, 1, 2
+
+H0_MPC = 1.0 / 2997.92458  # (Mpc/h)^-1 with c = 1
+
+# Every function the header declares (checked by the tests).
+EXPORTS = ("isis_cic_deposit", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force",
+           "isis_strerror", "isis_release_workspace")
+
+
+class isis_grid(ctypes.Structure):
+    _fields_ = [("Omega_m", ctypes.c_double), ("Omega_L", ctypes.c_double), ("H0", ctypes.c_double),
+                ("box", ctypes.c_double), ("N", ctypes.c_int)]
+
+
+class isis_params(ctypes.Structure):
+    _fields_ = [("lambda0", ctypes.c_double), ("beta", ctypes.c_double), ("a_ssb", ctypes.c_double),
+                ("n", ctypes.c_int), ("fR0_abs", ctypes.c_double)]
+
+
+class isis_mg_opts(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("n_coarsest", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("prec", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+
+
+class isis_solve_info(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("outer", ctypes.c_int), ("res0", ctypes.c_double),
+                ("res_ref", ctypes.c_double), ("res_final", ctypes.c_double), ("hist", ctypes.c_double * 128)]
+
+
+class IsisError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1307_6748_gb300.build.build() "
+                          "(the solver has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, f_p = ctypes.c_void_p, ctypes.c_void_p
+    lib.isis_cic_deposit.argtypes = [P(isis_grid), f_p, f_p, f_p, ctypes.c_int64, vp, ctypes.c_int, vp]
+    lib.isis_poisson_solve.argtypes = [P(isis_grid), ctypes.c_double, vp, vp, ctypes.c_double, P(isis_mg_opts),
+                                       P(isis_solve_info), vp]
+    lib.isis_scalar_solve.argtypes = [ctypes.c_int, P(isis_params), P(isis_grid), ctypes.c_double, vp, vp,
+                                      ctypes.c_double, P(isis_mg_opts), P(isis_solve_info), vp]
+    lib.isis_fifth_force.argtypes = [ctypes.c_int, P(isis_params), P(isis_grid), ctypes.c_double, vp, vp,
+                                     ctypes.c_int, f_p, f_p, f_p, ctypes.c_int64, f_p, f_p, f_p, vp]
+    lib.isis_strerror.argtypes = [ctypes.c_int]
+    lib.isis_strerror.restype = ctypes.c_char_p
+    lib.isis_release_workspace.argtypes = []
+    lib.isis_release_workspace.restype = None
+    for name in ("isis_cic_deposit", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------------
+# Plain-Python mirrors of the structs
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Grid:
+    N: int
+    box: float
+    Omega_m: float = 0.267
+    Omega_L: float = 0.733
+    H0: float = H0_MPC
+
+    def c(self):
+        return isis_grid(self.Omega_m, self.Omega_L, self.H0, self.box, self.N)
+
+
+@dataclass
+class Params:
+    lambda0: float = 1.0
+    beta: float = 1.0
+    a_ssb: float = 0.5
+    n: int = 1
+    fR0_abs: float = 1e-5
+
+    def c(self):
+        return isis_params(self.lambda0, self.beta, self.a_ssb, self.n, self.fR0_abs)
+
+
+@dataclass
+class Opts:
+    nu1: int = 2
+    nu2: int = 2
+    n_coarsest: int = 4
+    max_cycles: int = 100
+    prec: int = ISIS_F64
+    inner_cycles: int = 2
+
+    def c(self):
+        return isis_mg_opts(self.nu1, self.nu2, self.n_coarsest, self.max_cycles, self.prec, self.inner_cycles)
+
+
+@dataclass
+class Info:
+    status: int = 0
+    cycles: int = 0
+    outer: int = 0
+    res0: float = 0.0
+    res_ref: float = 0.0
+    res_final: float = 0.0
+    hist: list = field(default_factory=list)
+
+
+def _ptr(t: torch.Tensor | None, dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(st: int, what: str, allow=(ISIS_OK,)):
+    if st not in allow:
+        raise IsisError(st, f"{what}: {load().isis_strerror(st).decode()}")
+    return st
+
+
+def _field_dtype(prec: int):
+    return torch.float32 if prec == ISIS_F32 else torch.float64
+
+
+def strerror(status: int) -> str:
+    return load().isis_strerror(status).decode()
+
+
+def release_workspace() -> None:
+    load().isis_release_workspace()
+
+
+# ---------------------------------------------------------------------------
+# The four calls
+# ---------------------------------------------------------------------------
+
+def isis_cic_deposit(grid: Grid, x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, eta: torch.Tensor,
+                     stream=None) -> torch.Tensor:
+    """CIC density (mean 1) of particles at cell-unit positions x, y, z into eta (float64 or float32)."""
+    lib = load()
+    f64 = 1 if eta.dtype == torch.float64 else 0
+    g = grid.c()
+    st = lib.isis_cic_deposit(ctypes.byref(g), _ptr(x, torch.float32), _ptr(y, torch.float32),
+                              _ptr(z, torch.float32), x.numel(), _ptr(eta), f64, _stream(stream))
+    _check(st, "isis_cic_deposit")
+    return eta
+
+
+def _info(ci: isis_solve_info, st: int, prec: int) -> Info:
+    nh = ci.outer if prec == ISIS_F32_REFINE64 else ci.cycles
+    return Info(st, ci.cycles, ci.outer, ci.res0, ci.res_ref, ci.res_final, [ci.hist[i] for i in range(nh)])
+
+
+def isis_poisson_solve(grid: Grid, a: float, eta: torch.Tensor, Phi: torch.Tensor, tol: float = 1e-10,
+                       opts: Opts | None = None, stream=None, allow_noconv: bool = False) -> Info:
+    """Solve lap Phi = 1.5 Om H0^2 (eta - <eta>)/a in place on Phi (initial guess in)."""
+    lib = load()
+    o = opts or Opts()
+    dt = _field_dtype(o.prec)
+    g, oc, info = grid.c(), o.c(), isis_solve_info()
+    st = lib.isis_poisson_solve(ctypes.byref(g), a, _ptr(eta, dt), _ptr(Phi, dt), tol, ctypes.byref(oc),
+                                ctypes.byref(info), _stream(stream))
+    _check(st, "isis_poisson_solve", (ISIS_OK, ISIS_ENOCONV) if allow_noconv else (ISIS_OK,))
+    return _info(info, st, o.prec)
+
+
+def isis_scalar_solve(model: int, params: Params, grid: Grid, a: float, eta: torch.Tensor, phi: torch.Tensor,
+                      tol: float = 1e-10, opts: Opts | None = None, stream=None, allow_noconv: bool = False) -> Info:
+    """FAS solve of the symmetron (phi = chi) or f(R) (phi = u) equation in place on phi."""
+    lib = load()
+    o = opts or Opts()
+    dt = _field_dtype(o.prec)
+    g, p, oc, info = grid.c(), params.c(), o.c(), isis_solve_info()
+    st = lib.isis_scalar_solve(int(model), ctypes.byref(p), ctypes.byref(g), a, _ptr(eta, dt), _ptr(phi, dt),
+                               tol, ctypes.byref(oc), ctypes.byref(info), _stream(stream))
+    _check(st, "isis_scalar_solve", (ISIS_OK, ISIS_ENOCONV) if allow_noconv else (ISIS_OK,))
+    return _info(info, st, o.prec)
+
+
+def isis_fifth_force(model: int, params: Params, grid: Grid, a: float, Phi: torch.Tensor | None,
+                     phi: torch.Tensor | None, x: torch.Tensor, y: torch.Tensor, z: torch.Tensor,
+                     out=None, stream=None):
+    """Per-particle acceleration -[grad(a^2 Phi) + F5]; returns (gx, gy, gz) float32."""
+    lib = load()
+    ref = Phi if Phi is not None else phi
+    f64 = 1 if (ref is None or ref.dtype == torch.float64) else 0
+    n = x.numel()
+    if out is None:
+        out = tuple(torch.empty(n, device=x.device, dtype=torch.float32) for _ in range(3))
+    g, p = grid.c(), params.c()
+    st = lib.isis_fifth_force(int(model), ctypes.byref(p), ctypes.byref(g), a, _ptr(Phi), _ptr(phi), f64,
+                              _ptr(x, torch.float32), _ptr(y, torch.float32), _ptr(z, torch.float32), n,
+                              _ptr(out[0], torch.float32), _ptr(out[1], torch.float32),
+                              _ptr(out[2], torch.float32), _stream(stream))
+    _check(st, "isis_fifth_force")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Background fields (initial guesses)
+# ---------------------------------------------------------------------------
+
+def chi_background(a: float, a_ssb: float) -> float:
+    """Symmetron background minimum chi = sqrt(max(0, 1 - (a_SSB/a)^3)) (uniform eta = 1)."""
+    v = 1.0 - (a_ssb / a) ** 3
+    return v ** 0.5 if v > 0 else 0.0
+
+
+def u_background(a: float, fR0_abs: float, n: int = 1, Omega_m: float = 0.267, Omega_L: float = 0.733) -> float:
+    """f(R) background u = ln(a^2 |f_R(a)|), |f_R(a)| = |f_R0| [(1+4r)/(a^-3+4r)]^(n+1), r = OL/Om."""
+    import math
+    r = Omega_L / Omega_m
+    fR = fR0_abs * ((1 + 4 * r) / (a ** -3 + 4 * r)) ** (n + 1)
+    return math.log(a * a * fR)

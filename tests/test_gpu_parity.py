@@ -1,0 +1,221 @@
+"""GPU-vs-oracle parity of the CUDA path, called through the C ABI.
+
+FP64 path: same inputs, same cycle count, max-abs difference <= 1e-10 on the
+scalar field (relative to max|Phi| for the Newtonian potential).  Mixed
+precision: relative L2 <= 1e-9 against the oracle's converged solution.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1307_6748_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+L32, A1 = 64.0, 1.0
+
+
+def _prob(model, N, box, a, **kw):
+    return oracle.Problem(model, N, box, a=a, **kw)
+
+
+def _model_setup(isis, model, N, box, a, par):
+    if model == oracle.SYMMETRON:
+        return isis.ISIS_SYMMETRON, isis.chi_background(a, par.a_ssb)
+    return isis.ISIS_FOFR_HS, isis.u_background(a, par.fR0_abs, par.n)
+
+
+@pytest.mark.parametrize("model", [oracle.SYMMETRON, oracle.FOFR])
+@pytest.mark.parametrize("N,box", [(32, 64.0), (64, 128.0)])
+def test_scalar_f64_fixed_cycles(cuda_lib, model, N, box):
+    isis = cuda_lib
+    par = isis.Params()
+    eta = synth.lognormal_eta(N, box, 1.0, 1)
+    m, g0 = _model_setup(isis, model, N, box, A1, par)
+    ncyc = 3
+    phi = torch.full((N,) * 3, g0, dtype=torch.float64, device="cuda")
+    info = isis.isis_scalar_solve(m, par, isis.Grid(N, box), A1, eta.cuda(), phi, tol=0.0,
+                                  opts=isis.Opts(max_cycles=ncyc), allow_noconv=True)
+    ref = oracle.solve(_prob(model, N, box, A1), eta.numpy(), np.full((N,) * 3, g0), tol=0.0, max_cycles=ncyc)
+    assert info.status == isis.ISIS_ENOCONV and ref.status == oracle.ENOCONV
+    assert info.cycles == ref.cycles == ncyc
+    err = np.abs(phi.cpu().numpy() - ref.phi).max()
+    assert err <= 1e-10, err
+    np.testing.assert_allclose(info.hist, ref.hist, rtol=1e-6)
+    assert abs(info.res_ref - ref.ref) <= 1e-12 * ref.ref
+
+
+@pytest.mark.parametrize("model", [oracle.SYMMETRON, oracle.FOFR])
+def test_scalar_f64_converged_config1(cuda_lib, model):
+    isis = cuda_lib
+    N, box = 32, L32
+    par = isis.Params()
+    eta = synth.lognormal_eta(N, box, 1.0, 1)
+    m, g0 = _model_setup(isis, model, N, box, A1, par)
+    phi = torch.full((N,) * 3, g0, dtype=torch.float64, device="cuda")
+    info = isis.isis_scalar_solve(m, par, isis.Grid(N, box), A1, eta.cuda(), phi, tol=1e-10)
+    ref = oracle.solve(_prob(model, N, box, A1), eta.numpy(), np.full((N,) * 3, g0), tol=1e-10)
+    assert ref.status == oracle.OK and info.status == isis.ISIS_OK
+    assert info.cycles == ref.cycles
+    assert np.abs(phi.cpu().numpy() - ref.phi).max() <= 1e-10
+    if model == oracle.SYMMETRON:
+        assert phi.min().item() >= -1e-12  # positive branch
+
+
+@pytest.mark.parametrize("N,box", [(32, 64.0), (64, 64.0)])
+def test_poisson_f64(cuda_lib, N, box):
+    isis = cuda_lib
+    eta = synth.lognormal_eta(N, box, 1.0, 1)
+    Phi = torch.zeros((N,) * 3, dtype=torch.float64, device="cuda")
+    info = isis.isis_poisson_solve(isis.Grid(N, box), A1, eta.cuda(), Phi, tol=1e-10)
+    ref = oracle.solve(_prob(oracle.POISSON, N, box, A1), eta.numpy(), np.zeros((N,) * 3), tol=1e-10)
+    assert ref.status == 0 and info.cycles == ref.cycles
+    scale = np.abs(ref.phi).max()
+    assert np.abs(Phi.cpu().numpy() - ref.phi).max() <= 1e-10 * scale
+    assert abs(Phi.mean().item()) <= 1e-14 * scale
+
+
+def test_poisson_sinusoid_exact(cuda_lib):
+    """Discrete solution of a sinusoidal source: Phi = -KP delta / ((4/h^2) sin^2(pi m / N))."""
+    isis = cuda_lib
+    N, box, m = 64, 64.0, 3
+    delta = synth.sinusoid(N, m=m, amp=0.5, axis=1)
+    eta = 1.0 + delta
+    Phi = torch.zeros((N,) * 3, dtype=torch.float64, device="cuda")
+    isis.isis_poisson_solve(isis.Grid(N, box), A1, eta.cuda(), Phi, tol=1e-12)
+    h = box / N
+    KP = 1.5 * 0.267 * isis.H0_MPC ** 2 / A1
+    exact = -KP * delta.numpy() / ((4.0 / h ** 2) * np.sin(np.pi * m / N) ** 2)
+    assert np.abs(Phi.cpu().numpy() - exact).max() <= 1e-9 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("model", [oracle.SYMMETRON, oracle.FOFR, oracle.POISSON])
+def test_refine64_matches_oracle(cuda_lib, model):
+    """FP32 correction cycles + FP64 defect correction vs the converged FP64 oracle."""
+    isis = cuda_lib
+    N, box = 64, 128.0
+    par = isis.Params()
+    eta = synth.lognormal_eta(N, box, 1.0, 1)
+    opts = isis.Opts(prec=isis.ISIS_F32_REFINE64)
+    if model == oracle.POISSON:
+        phi = torch.zeros((N,) * 3, dtype=torch.float64, device="cuda")
+        info = isis.isis_poisson_solve(isis.Grid(N, box), A1, eta.cuda(), phi, tol=1e-10, opts=opts)
+        g0 = 0.0
+    else:
+        m, g0 = _model_setup(isis, model, N, box, A1, par)
+        phi = torch.full((N,) * 3, g0, dtype=torch.float64, device="cuda")
+        info = isis.isis_scalar_solve(m, par, isis.Grid(N, box), A1, eta.cuda(), phi, tol=1e-10, opts=opts)
+    assert info.status == isis.ISIS_OK and info.res_final <= 1e-10 * info.res_ref
+    # f(R) reaches its rounding floor near 1e-13 of the reference residual
+    ref = oracle.solve(_prob(model, N, box, A1), eta.numpy(), np.full((N,) * 3, g0),
+                       tol=1e-12 if model == oracle.FOFR else 1e-13)
+    assert ref.status == 0
+    got = phi.cpu().numpy()
+    if model == oracle.FOFR:
+        # relative L2 on delta f_R = f_R - fbar_R, f_R = -a^-2 e^u
+        fr_g, fr_o = -np.exp(got), -np.exp(ref.phi)
+        fbar = -np.exp(g0)
+        rel = np.linalg.norm(fr_g - fr_o) / np.linalg.norm(fr_o - fbar)
+        assert np.abs(got - ref.phi).max() <= 1e-8
+    else:
+        rel = np.linalg.norm(got - ref.phi) / np.linalg.norm(ref.phi)
+    assert rel <= 1e-9, rel
+
+
+@pytest.mark.parametrize("model", [oracle.SYMMETRON, oracle.FOFR])
+def test_plain_f32(cuda_lib, model):
+    isis = cuda_lib
+    N, box = 32, 64.0
+    par = isis.Params()
+    eta = synth.lognormal_eta(N, box, 1.0, 1)
+    m, g0 = _model_setup(isis, model, N, box, A1, par)
+    phi = torch.full((N,) * 3, g0, dtype=torch.float32, device="cuda")
+    info = isis.isis_scalar_solve(m, par, isis.Grid(N, box), A1, eta.float().cuda(), phi, tol=1e-5,
+                                  opts=isis.Opts(prec=isis.ISIS_F32))
+    assert info.status == isis.ISIS_OK
+    ref = oracle.solve(_prob(model, N, box, A1), eta.numpy(), np.full((N,) * 3, g0), tol=1e-12)
+    err = np.abs(phi.double().cpu().numpy() - ref.phi).max()
+    assert err <= 1e-4 * max(1.0, np.abs(ref.phi).max()), err
+
+
+@pytest.mark.parametrize("N", [16, 64])
+def test_cic_deposit(cuda_lib, N):
+    isis = cuda_lib
+    x, y, z = synth.zeldovich(N, float(N), seed=3)
+    eta = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
+    isis.isis_cic_deposit(isis.Grid(N, float(N)), x.cuda(), y.cuda(), z.cuda(), eta)
+    ref = oracle.cic_deposit(N, x.numpy(), y.numpy(), z.numpy())
+    assert np.abs(eta.cpu().numpy() - ref).max() <= 1e-10
+    # deterministic: same bits twice
+    eta2 = torch.empty_like(eta)
+    isis.isis_cic_deposit(isis.Grid(N, float(N)), x.cuda(), y.cuda(), z.cuda(), eta2)
+    assert torch.equal(eta, eta2)
+
+
+def test_cic_lattice_uniform(cuda_lib):
+    isis = cuda_lib
+    N = 32
+    q = (torch.arange(N, dtype=torch.float32) + 0.5)
+    X, Y, Z = torch.meshgrid(q, q, q, indexing="ij")
+    eta = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
+    isis.isis_cic_deposit(isis.Grid(N, 32.0), X.reshape(-1).cuda(), Y.reshape(-1).cuda(), Z.reshape(-1).cuda(), eta)
+    assert torch.all(eta == 1.0)
+
+
+@pytest.mark.parametrize("model", [oracle.SYMMETRON, oracle.FOFR])
+def test_fifth_force(cuda_lib, model):
+    isis = cuda_lib
+    N, box, a = 32, 64.0, 0.8
+    par = isis.Params()
+    gen = np.random.Generator(np.random.PCG64(7))
+    Phi = gen.standard_normal((N,) * 3) * 1e-6
+    if model == oracle.SYMMETRON:
+        phi = 0.9 + 0.05 * gen.standard_normal((N,) * 3)
+        m = isis.ISIS_SYMMETRON
+    else:
+        phi = -12.0 + 0.3 * gen.standard_normal((N,) * 3)
+        m = isis.ISIS_FOFR_HS
+    x, y, z = synth.zeldovich(N, box, seed=5)
+    g = isis.isis_fifth_force(m, par, isis.Grid(N, box), a, torch.from_numpy(Phi).cuda(),
+                              torch.from_numpy(phi).cuda(), x.cuda(), y.cuda(), z.cuda())
+    go = oracle.fifth_force(_prob(model, N, box, a), Phi, phi, x.numpy(), y.numpy(), z.numpy())
+    for gd, od in zip(g, go):
+        np.testing.assert_allclose(gd.cpu().numpy(), od, rtol=2e-6, atol=2e-6 * np.abs(od).max())
+
+
+def test_invalid_arguments(cuda_lib):
+    isis = cuda_lib
+    eta = torch.ones((12,) * 3, dtype=torch.float64, device="cuda")
+    phi = torch.ones_like(eta)
+    with pytest.raises(isis.IsisError) as e:
+        isis.isis_scalar_solve(isis.ISIS_SYMMETRON, isis.Params(), isis.Grid(12, 10.0), 1.0, eta, phi)
+    assert e.value.status == isis.ISIS_EINVAL
+    eta = torch.ones((16,) * 3, dtype=torch.float64, device="cuda")
+    phi = torch.ones_like(eta)
+    with pytest.raises(isis.IsisError) as e:
+        isis.isis_scalar_solve(isis.ISIS_SYMMETRON, isis.Params(lambda0=-1.0), isis.Grid(16, 10.0), 1.0, eta, phi)
+    assert e.value.status == isis.ISIS_EINVAL
+
+
+def test_nan_density_reports_enan(cuda_lib):
+    isis = cuda_lib
+    N = 16
+    eta = torch.ones((N,) * 3, dtype=torch.float64)
+    eta[3, 4, 5] = float("nan")
+    phi = torch.full((N,) * 3, 0.9, dtype=torch.float64, device="cuda")
+    with pytest.raises(isis.IsisError) as e:
+        isis.isis_scalar_solve(isis.ISIS_SYMMETRON, isis.Params(), isis.Grid(N, 32.0), 1.0, eta.cuda(), phi)
+    assert e.value.status == isis.ISIS_ENAN
+
+
+def test_uniform_density_closed_form(cuda_lib):
+    """Uniform eta: chi = sqrt(1 - (a_SSB/a)^3 eta); u from the f(R) background formula."""
+    isis = cuda_lib
+    N, box, a = 16, 32.0, 1.0
+    for etav in (0.3, 1.0, 2.5):
+        eta = torch.full((N,) * 3, etav, dtype=torch.float64, device="cuda")
+        phi = torch.full((N,) * 3, 0.5, dtype=torch.float64, device="cuda")
+        isis.isis_scalar_solve(isis.ISIS_SYMMETRON, isis.Params(), isis.Grid(N, box), a, eta, phi, tol=1e-12)
+        exact = np.sqrt(max(0.0, 1.0 - 0.125 * etav))
+        assert abs(phi.max().item() - exact) <= 1e-14 and abs(phi.min().item() - exact) <= 1e-14
