@@ -254,3 +254,26 @@ def u_background(a: float, fR0_abs: float, n: int = 1, Omega_m: float = 0.267, O
     r = Omega_L / Omega_m
     fR = fR0_abs * ((1 + 4 * r) / (a ** -3 + 4 * r)) ** (n + 1)
     return math.log(a * a * fR)
+
+
+# ---------------------------------------------------------------------------
+# Parameter presets of the paper's Table 1 (Sect. 6.1)
+# ---------------------------------------------------------------------------
+
+def fofr_range(fR0_abs: float, n: int = 1, Omega_m: float = 0.267, Omega_L: float = 0.733) -> float:
+    """Compton range of the f(R) field today in Mpc/h (Sect. 4.2):
+    lambda = 3 sqrt((n+1)/(Om + 4 OL)) sqrt(|f_R0| / 1e-6)."""
+    return 3.0 * ((n + 1) / (Omega_m + 4.0 * Omega_L)) ** 0.5 * (fR0_abs / 1e-6) ** 0.5
+
+
+PRESETS = {
+    # symmetron: lambda0 [Mpc/h], a_SSB = 1/(1+z_SSB), beta
+    "SymmA": Params(lambda0=1.0, beta=1.0, a_ssb=1.0 / 2.0),
+    "SymmB": Params(lambda0=1.0, beta=1.0, a_ssb=1.0 / 3.0),
+    "SymmC": Params(lambda0=1.0, beta=2.0, a_ssb=1.0 / 2.0),
+    "SymmD": Params(lambda0=1.0, beta=1.0, a_ssb=1.0 / 4.0),
+    # Hu-Sawicki f(R): n, |f_R0|
+    "fofr4": Params(n=1, fR0_abs=1e-4),
+    "fofr5": Params(n=1, fR0_abs=1e-5),
+    "fofr6": Params(n=1, fR0_abs=1e-6),
+}

@@ -1,0 +1,385 @@
+"""Pins of the FP64 CPU oracle to facts fixed outside it: the paper's printed
+values, closed-form solutions, FFT-exact solutions of the discrete linear
+problems, brute force and invariants.  No GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1307_6748_gb300 import synth
+
+H0 = oracle.H0_MPC
+OM, OL = 0.267, 0.733
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def lap_eigen(N, h):
+    """Eigenvalues of the periodic 7-point Laplacian on the rfft grid: -(4/h^2) sum_d sin^2(pi k_d / N)."""
+    k = np.fft.fftfreq(N) * N
+    kz = np.fft.rfftfreq(N) * N
+    s = lambda q: np.sin(np.pi * q / N) ** 2
+    return -(4.0 / h ** 2) * (s(k)[:, None, None] + s(k)[None, :, None] + s(kz)[None, None, :])
+
+
+def fft_solve(rhs, lam_shift, h):
+    """Solve (lap - lam_shift) f = rhs exactly with the discrete eigenvalues (zero mode dropped if singular)."""
+    N = rhs.shape[0]
+    lam = lap_eigen(N, h) - lam_shift
+    R = np.fft.rfftn(rhs)
+    F = np.zeros_like(R)
+    nz = np.abs(lam) > 0
+    F[nz] = R[nz] / lam[nz]
+    return np.fft.irfftn(F, s=rhs.shape, axes=(0, 1, 2))
+
+
+# ---------------------------------------------------------------------------
+# Poisson (Sect. 3.1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,axis", [(1, 0), (3, 2)])
+def test_poisson_sinusoid_closed_form(m, axis):
+    N, box, a = 32, 64.0, 0.7
+    delta = synth.sinusoid(N, m=m, amp=0.3, axis=axis).numpy()
+    r = oracle.solve(oracle.Problem(oracle.POISSON, N, box, a=a), 1.0 + delta, np.zeros((N,) * 3), tol=1e-12)
+    assert r.status == oracle.OK
+    h = box / N
+    KP = 1.5 * OM * H0 ** 2 / a
+    exact = -KP * delta / ((4.0 / h ** 2) * math.sin(math.pi * m / N) ** 2)
+    assert np.abs(r.phi - exact).max() <= 1e-10 * np.abs(exact).max()
+
+
+def test_poisson_fft_exact():
+    N, box, a = 32, 64.0, 1.0
+    eta = synth.lognormal_eta(N, box, 1.0, 11).numpy()
+    r = oracle.solve(oracle.Problem(oracle.POISSON, N, box, a=a), eta, np.zeros((N,) * 3), tol=1e-12)
+    assert r.status == oracle.OK
+    KP = 1.5 * OM * H0 ** 2 / a
+    exact = fft_solve(KP * (eta - eta.mean()), 0.0, box / N)
+    assert np.abs(r.phi - exact).max() <= 1e-9 * np.abs(exact).max()
+    assert abs(r.phi.mean()) <= 1e-13 * np.abs(exact).max()
+
+
+# ---------------------------------------------------------------------------
+# Uniform density: closed forms of the field equations
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("a,etav", [(1.0, 0.3), (1.0, 1.0), (0.8, 2.0), (0.6, 1.0), (1.0, 9.0)])
+def test_symmetron_uniform_minimum(a, etav):
+    """Sect. 4.1: uniform eta -> chi = sqrt(1 - (a_SSB/a)^3 eta) above symmetry breaking, else 0."""
+    N, box = 8, 16.0
+    r = oracle.solve(oracle.Problem(oracle.SYMMETRON, N, box, a=a, a_ssb=0.5), np.full((N,) * 3, etav),
+                     np.full((N,) * 3, 0.7), tol=1e-13)
+    v = 1.0 - (0.5 / a) ** 3 * etav
+    exact = math.sqrt(v) if v > 0 else 0.0
+    assert np.abs(r.phi - exact).max() <= 1e-12
+
+
+@pytest.mark.parametrize("a,etav,fr0", [(1.0, 1.0, 1e-5), (0.7, 1.0, 1e-6), (1.0, 0.4, 1e-5), (0.8, 5.0, 1e-4)])
+def test_fofr_uniform_background(a, etav, fr0):
+    """Sect. 4.2: the f_R equation at uniform eta gives
+    f_R = -|f_R0| [(1 + 4 OL/Om) / (eta a^-3 + 4 OL/Om)]^(n+1), and u = ln(-a^2 f_R)."""
+    N, box = 8, 16.0
+    rr = OL / OM
+    fR = -fr0 * ((1 + 4 * rr) / (etav * a ** -3 + 4 * rr)) ** 2
+    u_exact = math.log(-a * a * fR)
+    r = oracle.solve(oracle.Problem(oracle.FOFR, N, box, a=a, fR0_abs=fr0), np.full((N,) * 3, etav),
+                     np.full((N,) * 3, u_exact + 0.3), tol=1e-10)
+    assert r.status == oracle.OK
+    assert np.abs(r.phi - u_exact).max() <= 1e-10
+
+
+def test_symmetron_zero_is_fixed_point():
+    """chi = 0 solves the symmetron equation for any eta: a zero guess never moves."""
+    N, box = 16, 32.0
+    eta = synth.lognormal_eta(N, box, 1.0, 4).numpy()
+    r = oracle.solve(oracle.Problem(oracle.SYMMETRON, N, box), eta, np.zeros((N,) * 3), tol=1e-10)
+    assert r.status == oracle.OK and r.cycles == 0 and np.all(r.phi == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Linearised problems solved exactly by FFT
+# ---------------------------------------------------------------------------
+
+def test_symmetron_linearised_fft():
+    """eta = 1 + eps nu: the first-order chi - chi_bg solves lap d = A(2 chi_bg^2 d + s chi_bg eps nu)."""
+    N, box, a = 32, 32.0, 1.0
+    nu = synth.gaussian_field(N, box, 1.0, 21).numpy()
+    A, s = a * a / 2.0, (0.5 / a) ** 3
+    chib = math.sqrt(1 - s)
+    errs = []
+    for eps in (1e-4, 1e-3):
+        r = oracle.solve(oracle.Problem(oracle.SYMMETRON, N, box, a=a), 1.0 + eps * nu, np.full((N,) * 3, chib),
+                         tol=1e-12)
+        lin = fft_solve(A * s * chib * eps * nu, 2 * A * chib ** 2, box / N)
+        errs.append(np.linalg.norm(r.phi - chib - lin) / np.linalg.norm(lin))
+    assert errs[0] <= 5e-4
+    assert 5.0 < errs[1] / errs[0] < 20.0  # the difference is second order in eps
+
+
+def test_fofr_linearised_fft():
+    """eta = 1 + eps nu: e^ubar lap d - (K3/(n+1)) d = K1 eps nu (flux form and source linearised)."""
+    N, box, a, fr0 = 32, 64.0, 1.0, 1e-5
+    nu = synth.gaussian_field(N, box, 1.0, 22).numpy()
+    rr = OL / OM
+    K1 = OM * a * H0 ** 2
+    K3 = OM * a * H0 ** 2 * (1 + 4 * a ** 3 * rr)
+    ubar = math.log(a * a * fr0 * ((1 + 4 * rr) / (a ** -3 + 4 * rr)) ** 2)
+    errs = []
+    for eps in (1e-4, 1e-3):
+        r = oracle.solve(oracle.Problem(oracle.FOFR, N, box, a=a, fR0_abs=fr0), 1.0 + eps * nu,
+                         np.full((N,) * 3, ubar), tol=1e-12)
+        lin = fft_solve(K1 * eps * nu / math.exp(ubar), K3 / 2.0 / math.exp(ubar), box / N)
+        errs.append(np.linalg.norm(r.phi - ubar - lin) / np.linalg.norm(lin))
+    assert errs[0] <= 5e-4
+    assert 5.0 < errs[1] / errs[0] < 20.0
+
+
+# ---------------------------------------------------------------------------
+# Operator structure
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("model", [oracle.POISSON, oracle.SYMMETRON, oracle.FOFR])
+def test_diagonal_derivative_matches_finite_difference(model):
+    """The Newton denominator dL_c/dphi_c equals a central difference of L_c in phi_c."""
+    N, box = 8, 16.0
+    gen = np.random.Generator(np.random.PCG64(5))
+    eta = np.exp(gen.standard_normal((N,) * 3))
+    phi = (0.8 + 0.1 * gen.standard_normal((N,) * 3)) if model != oracle.FOFR else \
+        (-11.5 + 0.5 * gen.standard_normal((N,) * 3))
+    p = oracle.Problem(model, N, box)
+    d = oracle.dL(p, eta, phi)
+    for c in [(0, 0, 0), (3, 5, 7), (7, 1, 2), (4, 4, 4)]:
+        eps = 1e-5 * max(1.0, abs(phi[c]))
+        pp, pm = phi.copy(), phi.copy()
+        pp[c] += eps
+        pm[c] -= eps
+        fd = (oracle.residual(p, eta, pp)[c] - oracle.residual(p, eta, pm)[c]) / (2 * eps)
+        assert abs(fd - d[c]) <= 1e-7 * abs(d[c])
+
+
+def test_fofr_flux_is_conservative_and_second_order():
+    """The flux form of Eq. (disc_non_canonical) sums to zero over the periodic box and approaches
+    div(e^u grad u) = lap(e^u) at second order in h."""
+    a, fr0 = 1.0, 1e-5
+    rr = OL / OM
+    K1, K2 = OM * a * H0 ** 2, OM * a ** 4 * H0 ** 2 * (1 + 4 * rr) * (fr0 * a * a) ** 0.5
+    K3 = OM * a * H0 ** 2 * (1 + 4 * a ** 3 * rr)
+    box = 10.0
+    errs = []
+    for N in (16, 32, 64):
+        h = box / N
+        x = (np.arange(N) + 0.5) * h
+        X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+        kx = 2 * np.pi / box
+        u = -11.0 + 0.4 * np.sin(kx * X) * np.cos(kx * Y) + 0.2 * np.sin(kx * Z)
+        eta = np.ones((N,) * 3)
+        S = K1 * (eta - 1) - K2 * np.exp(-u / 2) + K3
+        flux = oracle.residual(oracle.Problem(oracle.FOFR, N, box, a=a, fR0_abs=fr0), eta, u) + S
+        assert abs(flux.sum()) <= 1e-9 * np.abs(flux).sum()
+        # analytic lap(e^u)
+        ux = 0.4 * kx * np.cos(kx * X) * np.cos(kx * Y)
+        uy = -0.4 * kx * np.sin(kx * X) * np.sin(kx * Y)
+        uz = 0.2 * kx * np.cos(kx * Z)
+        lapu = -0.8 * kx * kx * np.sin(kx * X) * np.cos(kx * Y) - 0.2 * kx * kx * np.sin(kx * Z)
+        exact = np.exp(u) * (ux ** 2 + uy ** 2 + uz ** 2 + lapu)
+        errs.append(np.abs(flux - exact).max())
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_restriction_and_prolongation():
+    gen = np.random.Generator(np.random.PCG64(9))
+    f = gen.standard_normal((8,) * 3)
+    c = oracle.restrict(f)
+    assert c.shape == (4,) * 3
+    assert abs(c[1, 2, 3] - f[2:4, 4:6, 6:8].mean()) <= 1e-15
+    assert abs(c.sum() * 8 - f.sum()) <= 1e-12
+    # trilinear, cell centred: a coarse field linear in I gives i/2 - 1/4 at interior fine cells
+    NH = 8
+    I = np.arange(NH, dtype=float)
+    cd = np.broadcast_to(I[:, None, None], (NH,) * 3).copy()
+    fine = oracle.prolong_add(cd, np.zeros((2 * NH,) * 3))
+    i = np.arange(2, 2 * NH - 2)
+    np.testing.assert_allclose(fine[2:-2, 5, 7], i / 2 - 0.25, atol=1e-14)
+    assert np.allclose(oracle.prolong_add(np.full((4,) * 3, 2.5), np.zeros((8,) * 3)), 2.5)
+
+
+# ---------------------------------------------------------------------------
+# FAS solution vs an independent dense Newton (brute force on 8^3)
+# ---------------------------------------------------------------------------
+
+def numpy_newton(p, eta, phi0, iters=30):
+    """Newton on F(phi) = L(phi) with a central finite-difference Jacobian (512 unknowns)."""
+    phi = phi0.copy()
+    n = phi.size
+    for _ in range(iters):
+        F = oracle.residual(p, eta, phi).ravel()
+        J = np.empty((n, n))
+        for q in range(n):
+            e = 1e-6 * max(1.0, abs(phi.flat[q]))
+            pp = phi.copy()
+            pp.flat[q] += e
+            pm = phi.copy()
+            pm.flat[q] -= e
+            J[:, q] = (oracle.residual(p, eta, pp).ravel() - oracle.residual(p, eta, pm).ravel()) / (2 * e)
+        dx = np.linalg.solve(J, -F)
+        phi = phi + dx.reshape(phi.shape)
+        if np.abs(dx).max() <= 1e-14 * max(1.0, np.abs(phi).max()):
+            break
+    return phi
+
+
+@pytest.mark.parametrize("model,ncoarse", [(oracle.SYMMETRON, 4), (oracle.SYMMETRON, 2), (oracle.FOFR, 4)])
+def test_fas_matches_dense_newton_8cubed(model, ncoarse):
+    N, box = 8, 16.0 if model == oracle.SYMMETRON else 64.0
+    eta = synth.lognormal_eta(N, box, 1.0, 13).numpy()
+    p = oracle.Problem(model, N, box, a=0.9)
+    g0 = math.sqrt(1 - (0.5 / 0.9) ** 3) if model == oracle.SYMMETRON else \
+        math.log(0.81 * 1e-5 * ((1 + 4 * OL / OM) / (0.9 ** -3 + 4 * OL / OM)) ** 2)
+    guess = np.full((N,) * 3, g0)
+    ref = numpy_newton(p, eta, guess)
+    r = oracle.solve(p, eta, guess, tol=1e-12, ncoarse=ncoarse)
+    assert r.status == oracle.OK
+    assert np.abs(r.phi - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+    st, dn, steps = oracle.dense_newton(p, eta, guess)
+    assert st == oracle.OK and np.abs(dn - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+# ---------------------------------------------------------------------------
+# Paper's static sphere test (Sect. 5.1): far-field and screened plateaus
+# ---------------------------------------------------------------------------
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+@pytest.mark.parametrize("a", [1.0, 0.5])
+def test_static_sphere_symmetron_plateaus(a):
+    row = [r for r in _golden_rows("static_sphere.txt") if r[0] == "symmetron"][0]
+    delta, R, B = float(row[1]), float(row[2]), float(row[3])
+    a_ssb, lam = 0.6, 1.0
+    N = 64
+    eta = synth.sphere_eta(N, B, R, delta).numpy()
+    eta_out = 1.0 / (1.0 + 4 * math.pi / 3 * delta * (R / B) ** 3)
+    chi_out = math.sqrt(1 - (a_ssb / a) ** 3 * eta_out)
+    p = oracle.Problem(oracle.SYMMETRON, N, B, a=a, a_ssb=a_ssb, lambda0=lam)
+    r = oracle.solve(p, eta, np.full((N,) * 3, chi_out), tol=1e-10)
+    assert r.status == oracle.OK
+    assert abs(r.phi[0, 0, 0] - chi_out) <= 1e-6          # far field (box corner)
+    assert abs(r.phi[N // 2, N // 2, N // 2]) <= 1e-2     # screened interior
+    assert r.phi.min() >= -1e-12
+
+
+def test_static_sphere_fofr_far_field():
+    row = [r for r in _golden_rows("static_sphere.txt") if r[0] == "fofr"][0]
+    delta, R, B = float(row[1]), float(row[2]), float(row[3])
+    fr0, a, N = 1e-6, 1.0, 64
+    eta = synth.sphere_eta(N, B, R, delta).numpy()
+    eta_out = 1.0 / (1.0 + 4 * math.pi / 3 * delta * (R / B) ** 3)
+    rr = OL / OM
+    fR_out = -fr0 * ((1 + 4 * rr) / (eta_out + 4 * rr)) ** 2
+    p = oracle.Problem(oracle.FOFR, N, B, a=a, fR0_abs=fr0)
+    # start from the cell-wise uniform-density solution: Newton on e^{-u/2} overshoots
+    # without bound when it starts far above the screened value inside the sphere
+    guess = np.log(a * a * fr0 * ((1 + 4 * rr) / (eta / a ** 3 + 4 * rr)) ** 2)
+    r = oracle.solve(p, eta, guess, tol=1e-9)
+    assert r.status == oracle.OK
+    assert abs(-np.exp(r.phi[0, 0, 0]) / fR_out - 1) <= 1e-6
+
+
+def test_table1_fofr_ranges():
+    """Table 1's f(R) ranges follow from |f_R0| with the range formula of Sect. 4.2."""
+    from paper_1307_6748_gb300 import isis
+    for row in _golden_rows("table1_models.txt"):
+        if row[0] != "fofr":
+            continue
+        n, fr0, lam = int(row[2]), float(row[3]), float(row[4])
+        assert abs(isis.fofr_range(fr0, n) - lam) <= 0.051 * lam / lam + 0.05 * (lam > 10)
+        assert isis.PRESETS[row[1]].fR0_abs == fr0
+    for row in _golden_rows("table1_models.txt"):
+        if row[0] == "symm":
+            p = isis.PRESETS[row[1]]
+            assert p.lambda0 == float(row[2]) and abs(p.a_ssb - 1 / (1 + float(row[3]))) < 1e-15
+            assert p.beta == float(row[4])
+
+
+# ---------------------------------------------------------------------------
+# CIC (Sect. 5.1) and gradients
+# ---------------------------------------------------------------------------
+
+def cic_brute(N, x, y, z):
+    """Brute force over every cell: weight = prod_d max(0, 1 - |x_d - c_d|) with periodic distance."""
+    eta = np.zeros((N,) * 3)
+    c = np.arange(N) + 0.5
+    for px, py, pz in zip(x, y, z):
+        w = []
+        for v in (px, py, pz):
+            d = np.abs(((v - c) + N / 2) % N - N / 2)
+            w.append(np.maximum(0.0, 1.0 - d))
+        eta += w[0][:, None, None] * w[1][None, :, None] * w[2][None, None, :]
+    return eta * (N ** 3 / len(x))
+
+
+@pytest.mark.parametrize("N", [4, 8])
+def test_cic_brute_force(N):
+    gen = np.random.Generator(np.random.PCG64(N))
+    x, y, z = (gen.uniform(0, N, 50).astype(np.float32) for _ in range(3))
+    x[0], y[0], z[0] = 0.0, N - 1e-3, 0.5  # edges and an exact centre
+    got = oracle.cic_deposit(N, x, y, z)
+    ref = cic_brute(N, x.astype(np.float64), y.astype(np.float64), z.astype(np.float64))
+    assert np.abs(got - ref).max() <= 1e-12
+
+
+def test_cic_invariants():
+    N = 16
+    q = (np.arange(N) + 0.5).astype(np.float32)
+    X, Y, Z = np.meshgrid(q, q, q, indexing="ij")
+    assert np.all(oracle.cic_deposit(N, X.ravel(), Y.ravel(), Z.ravel()) == 1.0)
+    x, y, z = (v.numpy() for v in synth.zeldovich(N, 32.0, seed=3))
+    eta = oracle.cic_deposit(N, x, y, z)
+    assert abs(eta.sum() - N ** 3) <= 1e-9
+
+
+def test_gradient_of_sinusoid():
+    N, box, m = 32, 20.0, 2
+    h = box / N
+    f = synth.sinusoid(N, m=m, amp=1.0, axis=1).numpy()
+    gx, gy, gz = oracle.gradient(f, box)
+    k = 2 * math.pi * m / box
+    y = (np.arange(N) + 0.5) * h
+    exact = (np.cos(k * y) * math.sin(k * h) / h)[None, :, None]
+    assert np.abs(gy - exact).max() <= 1e-12 and np.abs(gx).max() == 0 and np.abs(gz).max() == 0
+
+
+def test_force_at_cell_centre():
+    """A particle at a cell centre feels the grid force of that cell:
+    -[a^2 grad Phi + 6 Om H0^2 (beta lambda0)^2/a_SSB^3 a^2 chi grad chi] (Eq. (symmetron_geodesics_tilde_chi))
+    and -[a^2 grad Phi + e^u grad u / 2] for f(R) (Sect. 4.2)."""
+    N, box, a = 16, 32.0, 0.8
+    h = box / N
+    Phi = 1e-6 * synth.sinusoid(N, m=1, axis=0).numpy()
+    gPhi = oracle.gradient(Phi, box)
+    chi = 0.9 + 0.01 * synth.sinusoid(N, m=2, axis=1).numpy()
+    gchi = oracle.gradient(chi, box)
+    u = -12.0 + 0.1 * synth.sinusoid(N, m=1, axis=2).numpy()
+    gu = oracle.gradient(u, box)
+    c = (3, 7, 11)
+    x, y, z = (np.array([v + 0.5], dtype=np.float32) for v in c)
+    Cs = 6 * OM * H0 ** 2 * (1.0 * 1.0) ** 2 / 0.5 ** 3
+    assert abs(Cs - 1.42597e-6) < 1e-10
+    g = oracle.fifth_force(oracle.Problem(oracle.SYMMETRON, N, box, a=a), Phi, chi, x, y, z)
+    for d in range(3):
+        exp_d = -(a * a * gPhi[d][c] + Cs * a * a * chi[c] * gchi[d][c])
+        assert abs(g[d][0] - exp_d) <= 1e-12 * (abs(exp_d) + 1e-20)
+    g = oracle.fifth_force(oracle.Problem(oracle.FOFR, N, box, a=a), Phi, u, x, y, z)
+    for d in range(3):
+        exp_d = -(a * a * gPhi[d][c] + 0.5 * math.exp(u[c]) * gu[d][c])
+        assert abs(g[d][0] - exp_d) <= 1e-12 * (abs(exp_d) + 1e-20)
+    del h
