@@ -1,0 +1,339 @@
+"""Benchmark of the ISIS force step on one GB300 (or N independent replicas).
+
+One step is the whole hot path at 512^3 in a 256 Mpc/h box:
+  CIC deposit of 512^3 Zel'dovich-displaced particles (seeded, P(k) ~ k^-2,
+  0.5-cell rms displacement) -> Poisson solve -> symmetron FAS solve
+  (a = 1, a_SSB = 0.5, lambda0 = 1 Mpc/h, beta = 1) -> Hu-Sawicki f(R) FAS
+  solve (n = 1, |f_R0| = 1e-5) -> forces of both models on every particle.
+The three solves run the FP32 correction cycles inside the FP64 defect-
+correction loop to a relative residual of 1e-8.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "symmetron/f(R) 512³ FAS solve time to residual 1e-8; smoother HBM GB/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=512)
+    ap.add_argument("--box", type=float, default=256.0)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--inner", type=int, default=2)
+    ap.add_argument("--sample-N", type=int, default=128, help="grid of the oracle's bounded CPU sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    return {"workload": f"force step: CIC deposit of {args.N}^3 Zel'dovich particles, Poisson + symmetron + "
+                        f"f(R) FAS solves (FP32 cycles in FP64 defect correction, residual {args.tol:g}), "
+                        f"forces of both models",
+            "N": args.N, "box_mpc_h": args.box, "particles": args.N ** 3, "tol": args.tol,
+            "symmetron": {"a": 1.0, "a_ssb": 0.5, "lambda0": 1.0, "beta": 1.0},
+            "fofr": {"n": 1, "fR0_abs": 1e-5}, "cycle": "V(2,2), coarsest 4^3 dense Newton",
+            "inner_cycles": args.inner,
+            "l2": "inputs larger than L2 (each 512^3 field is 0.5-1 GB), no flush",
+            "parallelism": "replicas (one independent problem per GPU)"}
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.stop = threading.Event()
+        self.th = threading.Thread(target=self.run, daemon=True)
+
+    def run(self):
+        while not self.stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([v.strip() for v in out.split(",")])
+            except Exception:
+                return
+            self.stop.wait(0.2)
+
+    def __enter__(self):
+        self.th.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.th.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return None
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for s in self.samples for n, v in zip(names, s[4:8]) if v.strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# The oracle as CPU baseline / reference arm
+# ---------------------------------------------------------------------------
+
+def oracle_step(sample_N: int, box_full: float, N_full: int, tol: float, cache={}):
+    """One oracle force step on a sample grid with the same cell size; returns seconds."""
+    import numpy as np
+
+    import oracle
+    from paper_1307_6748_gb300 import isis, synth
+    box = box_full * sample_N / N_full
+    if sample_N not in cache:
+        cache[sample_N] = tuple(v.numpy() for v in synth.zeldovich(sample_N, box, seed=3))
+    x, y, z = cache[sample_N]
+    t0 = time.perf_counter()
+    eta = oracle.cic_deposit(sample_N, x, y, z)
+    Pp = oracle.Problem(oracle.POISSON, sample_N, box)
+    Ps = oracle.Problem(oracle.SYMMETRON, sample_N, box, a=1.0, a_ssb=0.5)
+    Pf = oracle.Problem(oracle.FOFR, sample_N, box, a=1.0, fR0_abs=1e-5)
+    shape = (sample_N,) * 3
+    rp = oracle.solve(Pp, eta, np.zeros(shape), tol=tol)
+    rs = oracle.solve(Ps, eta, np.full(shape, isis.chi_background(1.0, 0.5)), tol=tol)
+    rf = oracle.solve(Pf, eta, np.full(shape, isis.u_background(1.0, 1e-5)), tol=tol)
+    oracle.fifth_force(Ps, rp.phi, rs.phi, x, y, z)
+    oracle.fifth_force(Pf, rp.phi, rf.phi, x, y, z)
+    return time.perf_counter() - t0
+
+
+def oracle_threads() -> int:
+    n = os.environ.get("OMP_NUM_THREADS")
+    if not n:
+        n = str(os.cpu_count() or 1)
+        os.environ["OMP_NUM_THREADS"] = n  # read by libgomp when the oracle library loads
+    return int(n)
+
+
+def cpu_baseline(args, steps=1):
+    cores = oracle_threads()
+    import oracle
+    oracle.build()
+    scale = (args.N / args.sample_N) ** 3
+    times = [oracle_step(args.sample_N, args.box, args.N, args.tol) for _ in range(steps)]
+    v = statistics.median(times) * 1e3 * scale
+    return {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": f"full oracle force step (deposit, 3 FP64 FAS solves to {args.tol:g}, forces) on "
+                      f"{args.sample_N}^3 with the same recipe and cell size, x{scale:g} by cell count "
+                      f"(median of {steps})"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cores = oracle_threads()
+    import oracle
+    oracle.build()
+    scale = (args.N / args.sample_N) ** 3
+    for _ in range(args.warmup):
+        oracle_step(args.sample_N, args.box, args.N, args.tol)
+    ts = [oracle_step(args.sample_N, args.box, args.N, args.tol) for _ in range(args.steps)]
+    ms = statistics.mean(ts) * 1e3 * scale
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload(args),
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": f"oracle force step on {args.sample_N}^3 (same recipe, same cell size), "
+                                       f"x{scale:g} by cell count, mean of {args.steps}"},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    from paper_1307_6748_gb300 import build, isis, synth
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    N, box = args.N, args.box
+    grid = isis.Grid(N, box)
+    psym = isis.Params(lambda0=1.0, beta=1.0, a_ssb=0.5)
+    pfr = isis.Params(n=1, fR0_abs=1e-5)
+    a = 1.0
+    x, y, z = synth.zeldovich(N, box, seed=3 + 1000 * rank, device=dev)
+    npart = x.numel()
+    f64 = dict(dtype=torch.float64, device=dev)
+    eta = torch.empty((N,) * 3, **f64)
+    Phi = torch.empty((N,) * 3, **f64)
+    chi = torch.empty((N,) * 3, **f64)
+    u = torch.empty((N,) * 3, **f64)
+    g = [torch.empty(npart, device=dev, dtype=torch.float32) for _ in range(6)]
+    opts_bg = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=args.inner, init=isis.ISIS_INIT_BACKGROUND)
+    stream = torch.cuda.current_stream()
+    infos = {}
+
+    def step(xx, yy, zz, ev=None):
+        if ev:
+            ev[0].record(stream)
+        isis.isis_cic_deposit(grid, xx, yy, zz, eta)
+        if ev:
+            ev[1].record(stream)
+        infos["poisson"] = isis.isis_poisson_solve(grid, a, eta, Phi, tol=args.tol, opts=opts_bg)
+        if ev:
+            ev[2].record(stream)
+        infos["symmetron"] = isis.isis_scalar_solve(isis.ISIS_SYMMETRON, psym, grid, a, eta, chi, tol=args.tol,
+                                                    opts=opts_bg)
+        if ev:
+            ev[3].record(stream)
+        infos["fofr"] = isis.isis_scalar_solve(isis.ISIS_FOFR_HS, pfr, grid, a, eta, u, tol=args.tol, opts=opts_bg)
+        if ev:
+            ev[4].record(stream)
+        isis.isis_fifth_force(isis.ISIS_SYMMETRON, psym, grid, a, Phi, chi, xx, yy, zz, out=g[0:3])
+        isis.isis_fifth_force(isis.ISIS_FOFR_HS, pfr, grid, a, Phi, u, xx, yy, zz, out=g[3:6])
+        if ev:
+            ev[5].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(x, y, z)
+    barrier()
+
+    # timed region: device-resident inputs
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    isis.prof_reset()
+    isis.prof_enable(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s in range(args.steps):
+            step(x, y, z, evs[s])
+        t1.record(stream)
+        barrier()
+    isis.prof_enable(False)
+    launches = isis.launch_count()
+    prof = isis.prof_read()
+    total_ms = t0.elapsed_time(t1)
+    ms = total_ms / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    parts = ["deposit", "poisson", "symmetron", "fofr", "forces"]
+    breakdown = {p: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, p in enumerate(parts)}
+
+    # end to end: positions from pinned host memory, forces back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        hx, hy, hz = (v.cpu().pin_memory() for v in (x, y, z))
+        hg = [torch.empty(npart, dtype=torch.float32).pin_memory() for _ in range(6)]
+        dx, dy, dz = (torch.empty_like(x) for _ in range(3))
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(args.steps):
+            dx.copy_(hx, non_blocking=True)
+            dy.copy_(hy, non_blocking=True)
+            dz.copy_(hz, non_blocking=True)
+            step(dx, dy, dz)
+            for d, h in zip(g, hg):
+                h.copy_(d, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1) / args.steps
+        if dist is not None:
+            tt = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ems = float(tt.item())
+        e2e = {"value": ems, "unit": "ms", "h2d_bytes_per_step": 3 * npart * 4, "d2h_bytes_per_step": 6 * npart * 4}
+
+    # roofline of the dominant kernel kind (by summed event time)
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, kms, kbytes) = dom
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    roofline = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "launches": nl,
+                "avg_launch_us": kms * 1e3 / nl, "bytes_per_launch": kbytes / nl,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
+    kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
+                   "GBps": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None} for k, v in prof.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": workload(args),
+                "breakdown_ms": breakdown,
+                "solves": {k: {"cycles": v.cycles, "outer": v.outer, "res_rel": v.res_final / v.res_ref}
+                           for k, v in infos.items()},
+                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

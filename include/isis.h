@@ -76,12 +76,24 @@ typedef struct {
   double fR0_abs;              /* |f_R0| */
 } isis_params;
 
+/* Initial guess of a solve.
+ *   ISIS_INIT_INPUT       phi holds the guess on entry.
+ *   ISIS_INIT_BACKGROUND  phi is overwritten with the uniform background field:
+ *                         chi_bg = sqrt(max(0, 1 - (a_SSB/a)^3)), u_bg = ln(a^2 |fbar_R(a)|)
+ *                         with |fbar_R(a)| = |f_R0| [(1+4r)/(a^-3+4r)]^(n+1), r = OL/Om, Phi = 0.
+ *   ISIS_INIT_LOCAL       phi is overwritten cell by cell with the solution for a
+ *                         uniform density equal to the cell's eta (same formulas with
+ *                         (a_SSB/a)^3 eta and eta a^-3); Phi = 0.  Suits f(R) with
+ *                         dense haloes, where Newton steps from the background overshoot. */
+typedef enum { ISIS_INIT_INPUT = 0, ISIS_INIT_BACKGROUND = 1, ISIS_INIT_LOCAL = 2 } isis_init;
+
 typedef struct {
   int nu1, nu2;        /* pre- and post-smoothing sweeps (red then black) per level */
   int n_coarsest;      /* coarsest grid size: 2 or 4 (dense Newton there) */
   int max_cycles;      /* cap on V-cycles (inner cycles for F32_REFINE64), <= 128 */
   isis_precision prec;
   int inner_cycles;    /* F32 V-cycles per FP64 outer iteration (F32_REFINE64), >= 1 */
+  isis_init init;      /* initial guess */
 } isis_mg_opts;
 
 typedef struct {
@@ -108,10 +120,10 @@ typedef struct {
  *            wrapped into [0, N)); cell centres at i + 1/2.
  *   eta      device double[N^3] (eta_f64 != 0) or float[N^3] (eta_f64 == 0),
  *            overwritten.
- * Accumulation is in 64-bit fixed point (2^-32 per unit weight), so the
- * result does not depend on the order of particles.  Uses an int64 N^3
- * scratch buffer from the workspace.  EINVAL: npart < 1, npart > 2^40 or
- * N invalid. */
+ * Accumulation is in 64-bit fixed point (2^-40 per unit weight), so the
+ * result does not depend on the order of particles; a cell may collect at
+ * most 2^23 unit weights.  Uses an int64 N^3 scratch buffer cached by the
+ * library.  EINVAL: npart < 1, npart > 2^40 or N invalid. */
 isis_status isis_cic_deposit(const isis_grid* grid, const float* x, const float* y, const float* z, int64_t npart,
                              void* eta, int eta_f64, void* stream);
 
@@ -122,7 +134,7 @@ isis_status isis_cic_deposit(const isis_grid* grid, const float* x, const float*
  * mean of Phi is set to 0 after every cycle.
  *   eta  device double[N^3] (float for ISIS_F32), mean density 1 expected.
  *   Phi  device double[N^3] (float for ISIS_F32): initial guess in, solution out.
- *   opts NULL for the defaults {2, 2, 4, 100, ISIS_F64, 2}; info may be NULL. */
+ *   opts NULL for the defaults {2, 2, 4, 100, ISIS_F64, 2, ISIS_INIT_INPUT}; info may be NULL. */
 isis_status isis_poisson_solve(const isis_grid* grid, double a, const void* eta, void* Phi, double tol,
                                const isis_mg_opts* opts, isis_solve_info* info, void* stream);
 
@@ -156,6 +168,27 @@ isis_status isis_scalar_solve(isis_model model, const isis_params* params, const
 isis_status isis_fifth_force(isis_model model, const isis_params* params, const isis_grid* grid, double a,
                              const void* Phi, const void* phi, int fields_f64, const float* x, const float* y,
                              const float* z, int64_t npart, float* gx, float* gy, float* gz, void* stream);
+
+/* ---- Instrumentation (not part of the paper's method) -------------------
+ * Every kernel launch of the library is counted.  When profiling is on, each
+ * launch is also bracketed by CUDA events on its stream and its algorithmic
+ * bytes (the minimum DRAM traffic of its work) are recorded, per kernel kind. */
+typedef struct {
+  const char* name;   /* kernel kind, e.g. "smooth_fine" (static string) */
+  int64_t launches;   /* launches recorded since the last reset */
+  double ms;          /* summed event time of those launches */
+  double bytes;       /* summed algorithmic bytes of those launches */
+} isis_prof_entry;
+
+/* on != 0: record events for every launch from now on. */
+void isis_prof_enable(int on);
+/* Zero the counters and drop recorded events. */
+void isis_prof_reset(void);
+/* Synchronise the device, then fill up to max entries (one per kernel kind
+ * with at least one launch); returns the number filled. */
+int isis_prof_read(isis_prof_entry* out, int max);
+/* Kernel launches issued by the library since the last isis_prof_reset(). */
+int64_t isis_launch_count(void);
 
 /* Human-readable name of a status code (static string). */
 const char* isis_strerror(isis_status status);

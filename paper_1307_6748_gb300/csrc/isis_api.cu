@@ -103,7 +103,7 @@ static bool grid_ok(const isis_grid* g) {
 }
 
 static bool opts_resolve(const isis_mg_opts* o, isis_mg_opts* out, int N) {
-  isis_mg_opts d = {2, 2, 4, 100, ISIS_F64, 2};
+  isis_mg_opts d = {2, 2, 4, 100, ISIS_F64, 2, ISIS_INIT_INPUT};
   if (o) d = *o;
   if (d.nu1 < 0 || d.nu1 > 16 || d.nu2 < 0 || d.nu2 > 16) return false;
   if (d.n_coarsest != 2 && d.n_coarsest != 4) return false;
@@ -111,6 +111,7 @@ static bool opts_resolve(const isis_mg_opts* o, isis_mg_opts* out, int N) {
   if (d.max_cycles < 0 || d.max_cycles > 128) return false;
   if (d.prec != ISIS_F64 && d.prec != ISIS_F32 && d.prec != ISIS_F32_REFINE64) return false;
   if (d.inner_cycles < 1 || d.inner_cycles > 16) return false;
+  if (d.init != ISIS_INIT_INPUT && d.init != ISIS_INIT_BACKGROUND && d.init != ISIS_INIT_LOCAL) return false;
   *out = d;
   return true;
 }
@@ -129,9 +130,60 @@ static void fill_common(SolveArgs& A, const isis_grid* g, double a, const void* 
   A.max_cycles = o.max_cycles;
   A.inner = o.inner_cycles;
   A.prec = o.prec;
+  A.init = o.init;
   A.info = info;
   A.st = (cudaStream_t)stream;
   std::memset(&A.coef, 0, sizeof(A.coef));
+}
+
+// ---------------------------------------------------------------------------
+// Launch counting and event profiling (isis_prof.cuh)
+// ---------------------------------------------------------------------------
+
+static const char* kKindNames[KK_COUNT] = {
+    "smooth_fine",    "smooth_coarse", "resid_restrict_fine", "resid_restrict_coarse", "coarse_sigma",
+    "prolong_fine",   "prolong_coarse", "coarse_newton",      "norm_fine",             "outer_residual64",
+    "update64",       "setup",         "reduce",              "init_guess",            "cic_scatter",
+    "cic_finish",     "force_gather"};
+
+struct ProfRec {
+  int kind;
+  int ev;
+  double bytes;
+};
+static bool g_prof_on = false;
+static long long g_launches = 0;
+static std::vector<cudaEvent_t> g_events;
+static int g_next_event = 0;
+static int g_pending = -1;
+static std::vector<ProfRec> g_recs;
+
+static int take_event() {
+  if (g_next_event >= (int)g_events.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    g_events.push_back(e);
+  }
+  return g_next_event++;
+}
+
+void prof_pre(cudaStream_t st) {
+  g_pending = -1;
+  if (!g_prof_on) return;
+  int a = take_event();
+  if (a < 0) return;
+  if (cudaEventRecord(g_events[a], st) != cudaSuccess) return;
+  g_pending = a;
+}
+
+void prof_post(int kind, double bytes, cudaStream_t st) {
+  ++g_launches;
+  if (!g_prof_on || g_pending < 0) return;
+  int b = take_event();
+  if (b < 0 || b != g_pending + 1) return;
+  if (cudaEventRecord(g_events[b], st) != cudaSuccess) return;
+  g_recs.push_back({kind, g_pending, bytes});
+  g_pending = -1;
 }
 
 }  // namespace isis
@@ -160,6 +212,35 @@ void isis_release_workspace(void) {
   g_ws.clear();
   for (auto& d : g_dep) cudaFree(d.acc);
   g_dep.clear();
+}
+
+void isis_prof_enable(int on) { g_prof_on = on != 0; }
+
+void isis_prof_reset(void) {
+  g_launches = 0;
+  g_recs.clear();
+  g_next_event = 0;
+  g_pending = -1;
+}
+
+int64_t isis_launch_count(void) { return g_launches; }
+
+int isis_prof_read(isis_prof_entry* out, int max) {
+  cudaDeviceSynchronize();
+  long long cnt[KK_COUNT] = {0};
+  double ms[KK_COUNT] = {0}, by[KK_COUNT] = {0};
+  for (const ProfRec& r : g_recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, g_events[r.ev], g_events[r.ev + 1]) != cudaSuccess) continue;
+    cnt[r.kind] += 1;
+    ms[r.kind] += t;
+    by[r.kind] += r.bytes;
+  }
+  cudaGetLastError();
+  int n = 0;
+  for (int k = 0; k < KK_COUNT && n < max; ++k)
+    if (cnt[k] > 0) out[n++] = {kKindNames[k], cnt[k], ms[k], by[k]};
+  return n;
 }
 
 isis_status isis_poisson_solve(const isis_grid* grid, double a, const void* eta, void* Phi, double tol,

@@ -130,12 +130,15 @@ isis_status isis_cic_deposit(const isis_grid* grid, const float* x, const float*
   unsigned long long* acc = get_deposit_buf(N);
   if (!acc) return ISIS_ENOMEM;
   ISIS_CK(cudaMemsetAsync(acc, 0, n * sizeof(unsigned long long), st));
-  cic_scatter<<<nblk((size_t)npart, 256), 256, 0, st>>>(x, y, z, (long long)npart, lg, acc);
-  ISIS_CKL();
+  ISIS_LAUNCH(KK_CIC_SCATTER, 12.0 * npart + 8.0 * n, st,
+              (cic_scatter<<<nblk((size_t)npart, 256), 256, 0, st>>>(x, y, z, (long long)npart, lg, acc)));
   const double scale = (double)n / ((double)npart * kFix);
-  if (eta_f64) cic_finish<double><<<nblk(n, 256), 256, 0, st>>>(acc, (double*)eta, n, scale);
-  else cic_finish<float><<<nblk(n, 256), 256, 0, st>>>(acc, (float*)eta, n, scale);
-  ISIS_CKL();
+  if (eta_f64)
+    ISIS_LAUNCH(KK_CIC_FINISH, 16.0 * n, st,
+                (cic_finish<double><<<nblk(n, 256), 256, 0, st>>>(acc, (double*)eta, n, scale)));
+  else
+    ISIS_LAUNCH(KK_CIC_FINISH, 12.0 * n, st,
+                (cic_finish<float><<<nblk(n, 256), 256, 0, st>>>(acc, (float*)eta, n, scale)));
   return ISIS_OK;
 }
 
@@ -155,9 +158,12 @@ isis_status isis_fifth_force(isis_model model, const isis_params* p, const isis_
   cudaStream_t st = (cudaStream_t)stream;
   unsigned nb = nblk((size_t)npart, 256);
   int mcode = phi ? (int)model : 0;
-#define ISIS_FORCE(T, MC)                                                                                      \
-  force_gather<T, MC><<<nb, 256, 0, st>>>((const T*)Phi, (const T*)phi, x, y, z, (long long)npart, lg, a2, Cs, \
-                                          inv2h, gx, gy, gz)
+  const double fbytes = 24.0 * npart + (double)grid->N * grid->N * grid->N * (fields_f64 ? 8 : 4) *
+                                             ((Phi ? 1 : 0) + (phi ? 1 : 0));
+#define ISIS_FORCE(T, MC)                                                                                    \
+  ISIS_LAUNCH(KK_FORCE, fbytes, st,                                                                          \
+              (force_gather<T, MC><<<nb, 256, 0, st>>>((const T*)Phi, (const T*)phi, x, y, z, (long long)npart, \
+                                                       lg, a2, Cs, inv2h, gx, gy, gz)))
   if (fields_f64) {
     if (mcode == 0) ISIS_FORCE(double, 0);
     else if (mcode == ISIS_SYMMETRON) ISIS_FORCE(double, ISIS_SYMMETRON);
@@ -168,7 +174,6 @@ isis_status isis_fifth_force(isis_model model, const isis_params* p, const isis_
     else ISIS_FORCE(float, ISIS_FOFR_HS);
   }
 #undef ISIS_FORCE
-  ISIS_CKL();
   return ISIS_OK;
 }
 

@@ -1,0 +1,45 @@
+// isis_prof.cuh -- launch counting and optional per-launch CUDA-event timing.
+// Every kernel launch of the library goes through ISIS_LAUNCH, which counts
+// it and, when profiling is enabled, brackets it with events on its stream
+// and records its algorithmic bytes under a kernel kind.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace isis {
+
+enum KernelKind : int {
+  KK_SMOOTH_FINE = 0,   // smoother on the finest grid
+  KK_SMOOTH_COARSE,     // smoother on the coarser grids
+  KK_RESTRICT_FINE,     // residual + restriction from the finest grid
+  KK_RESTRICT_COARSE,
+  KK_SIGMA,             // coarse FAS source
+  KK_PROLONG_FINE,      // prolongation onto the finest grid
+  KK_PROLONG_COARSE,
+  KK_COARSE_NEWTON,
+  KK_NORM,              // residual norm of the finest grid
+  KK_OUTER_RESID,       // FP64 residual of the defect-correction loop
+  KK_UPDATE,            // FP64 solution update
+  KK_SETUP,             // density / base restriction, conversions, e^B
+  KK_REDUCE,            // final reductions, moments, mean removal
+  KK_INIT,              // initial guess
+  KK_CIC_SCATTER,
+  KK_CIC_FINISH,
+  KK_FORCE,
+  KK_COUNT
+};
+
+void prof_pre(cudaStream_t st);
+void prof_post(int kind, double bytes, cudaStream_t st);
+
+}  // namespace isis
+
+// Launch a kernel through the profiler; returns ISIS_ECUDA from the
+// enclosing function if the launch fails.
+#define ISIS_LAUNCH(kind, bytes, st, ...)        \
+  do {                                           \
+    ::isis::prof_pre(st);                        \
+    __VA_ARGS__;                                 \
+    cudaError_t le_ = cudaGetLastError();        \
+    ::isis::prof_post((kind), (bytes), (st));    \
+    if (le_ != cudaSuccess) return ISIS_ECUDA;   \
+  } while (0)

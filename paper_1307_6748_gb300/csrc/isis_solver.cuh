@@ -11,6 +11,7 @@
 
 #include "../../include/isis.h"
 #include "isis_coarse.cuh"
+#include "isis_prof.cuh"
 
 namespace isis {
 
@@ -50,6 +51,7 @@ struct SolveArgs {
   double tol;
   int nu1, nu2, ncoarse, max_cycles, inner;
   isis_precision prec;
+  isis_init init;
   isis_solve_info* info;
   cudaStream_t st;
   // reference residual: ref = ref_scale * RMS(eta - eta_ref) (eta_ref = <eta> for Poisson)
@@ -106,46 +108,59 @@ struct Cycler {
     }
   }
 
+  // per-cell input arrays read by the operator besides x (eta, B, w, Sigma)
+  static int arrays(bool has_sig) {
+    int n = has_sig ? 1 : 0;
+    if (!(M == POI && FM == DELTA)) n += 1;   // eta
+    if (FM == DELTA && M != POI) n += 1;      // B
+    if (FM == DELTA && M == FOFR) n += 1;     // w
+    return n;
+  }
+  static double cells(const LevelView<T>& v) { return (double)v.N * v.N * v.N; }
+
   isis_status smooth(int l, int sweeps) {
     const LevelView<T>& v = L[l];
     size_t half = ((size_t)v.N * v.N * v.N) / 2;
+    // a full sweep reads x and the per-cell arrays once and writes x once
+    double bytes = 0.5 * cells(v) * sizeof(T) * (2 + arrays(v.sig != nullptr));
+    int kind = l == 0 ? KK_SMOOTH_FINE : KK_SMOOTH_COARSE;
     for (int s = 0; s < sweeps; ++s)
-      for (int color = 0; color < 2; ++color) {
-        smooth_color<M, FM, T><<<nblk(half, 256), 256, 0, st>>>(v, c, color);
-        ISIS_CKL();
-      }
+      for (int color = 0; color < 2; ++color)
+        ISIS_LAUNCH(kind, bytes, st, (smooth_color<M, FM, T><<<nblk(half, 256), 256, 0, st>>>(v, c, color)));
     return ISIS_OK;
   }
 
   isis_status vcycle(int l) {
     const int last = (int)L.size() - 1;
     if (l == last) {
-      coarse_newton<M, FM, T><<<1, kCoarseMax, 0, st>>>(L[l], c, ws->iflags, ws->iflags + 1);
-      ISIS_CKL();
+      ISIS_LAUNCH(KK_COARSE_NEWTON, 0.0, st,
+                  (coarse_newton<M, FM, T><<<1, kCoarseMax, 0, st>>>(L[l], c, ws->iflags, ws->iflags + 1)));
       return ISIS_OK;
     }
     isis_status s = smooth(l, nu1);
     if (s != ISIS_OK) return s;
     LevelView<T>& C = L[l + 1];
     size_t nc = (size_t)C.N * C.N * C.N;
-    resid_restrict<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], c, C.x, (T*)ws->x0[l + 1], (T*)ws->sig[l + 1]);
-    ISIS_CKL();
-    coarse_sigma_add<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(C, c, (T*)ws->sig[l + 1]);
-    ISIS_CKL();
+    double nf = cells(L[l]), ncd = (double)nc;
+    ISIS_LAUNCH(l == 0 ? KK_RESTRICT_FINE : KK_RESTRICT_COARSE,
+                sizeof(T) * (nf * (1 + arrays(L[l].sig != nullptr)) + 3 * ncd), st,
+                (resid_restrict<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], c, C.x, (T*)ws->x0[l + 1],
+                                                                        (T*)ws->sig[l + 1])));
+    ISIS_LAUNCH(KK_SIGMA, sizeof(T) * ncd * (2 + arrays(true)), st,
+                (coarse_sigma_add<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(C, c, (T*)ws->sig[l + 1])));
     s = vcycle(l + 1);
     if (s != ISIS_OK) return s;
-    size_t nf = (size_t)L[l].N * L[l].N * L[l].N;
-    prolong_correct<T><<<nblk(nf, 256), 256, 0, st>>>(L[l].x, C.x, (const T*)ws->x0[l + 1], C.lg);
-    ISIS_CKL();
+    ISIS_LAUNCH(l == 0 ? KK_PROLONG_FINE : KK_PROLONG_COARSE, sizeof(T) * (2 * ncd + 2 * nf), st,
+                (prolong_correct<T><<<nblk((size_t)nf, 256), 256, 0, st>>>(L[l].x, C.x, (const T*)ws->x0[l + 1],
+                                                                           C.lg)));
     return smooth(l, nu2);
   }
 
   // RMS of L(x) - Sigma on the finest level (blocking: one stream sync).
   isis_status fine_rms(double* out) {
-    norm_partial<M, FM, T><<<kNormBlocks, kNormThreads, 0, st>>>(L[0], c, ws->part);
-    ISIS_CKL();
-    reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal);
-    ISIS_CKL();
+    ISIS_LAUNCH(KK_NORM, cells(L[0]) * sizeof(T) * (1 + arrays(L[0].sig != nullptr)), st,
+                (norm_partial<M, FM, T><<<kNormBlocks, kNormThreads, 0, st>>>(L[0], c, ws->part)));
+    ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
     double* h = (double*)ws->host;
     int* hi = (int*)(h + 4);
     ISIS_CK(cudaMemcpyAsync(h, ws->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -165,12 +180,11 @@ struct Cycler {
 // sum((v - shift)^2) and sum(v) over n values (blocking).
 template <class T>
 isis_status moments(Workspace* ws, const T* v, size_t n, double shift, cudaStream_t st, double* s2, double* s1) {
-  moments_partial<T><<<kNormBlocks, kNormThreads, 0, st>>>(v, n, shift, ws->part, ws->part2);
-  ISIS_CKL();
-  reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal);
-  ISIS_CKL();
-  reduce_final<<<1, kNormThreads, 0, st>>>(ws->part2, kNormBlocks, ws->scal + 1);
-  ISIS_CKL();
+  ISIS_LAUNCH(KK_REDUCE, (double)n * sizeof(T), st,
+              (moments_partial<T><<<kNormBlocks, kNormThreads, 0, st>>>(v, n, shift, ws->part, ws->part2)));
+  ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
+  ISIS_LAUNCH(KK_REDUCE, 0.0, st,
+              (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part2, kNormBlocks, ws->scal + 1)));
   double* h = (double*)ws->host;
   ISIS_CK(cudaMemcpyAsync(h, ws->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   ISIS_CK(cudaStreamSynchronize(st));
@@ -188,12 +202,12 @@ __global__ void add_scalar(T* __restrict__ v, size_t n, const double* __restrict
 // v -= mean(v), device-side (no host sync): partial sums, final sum, subtract.
 template <class T>
 isis_status remove_mean(Workspace* ws, T* v, size_t n, cudaStream_t st) {
-  moments_partial<T><<<kNormBlocks, kNormThreads, 0, st>>>(v, n, 0.0, ws->part, ws->part2);
-  ISIS_CKL();
-  reduce_final<<<1, kNormThreads, 0, st>>>(ws->part2, kNormBlocks, ws->scal + 1);
-  ISIS_CKL();
-  add_scalar<T><<<nblk(n, 256), 256, 0, st>>>(v, n, ws->scal + 1, 1.0 / (double)n);
-  ISIS_CKL();
+  ISIS_LAUNCH(KK_REDUCE, (double)n * sizeof(T), st,
+              (moments_partial<T><<<kNormBlocks, kNormThreads, 0, st>>>(v, n, 0.0, ws->part, ws->part2)));
+  ISIS_LAUNCH(KK_REDUCE, 0.0, st,
+              (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part2, kNormBlocks, ws->scal + 1)));
+  ISIS_LAUNCH(KK_REDUCE, 2.0 * n * sizeof(T), st,
+              (add_scalar<T><<<nblk(n, 256), 256, 0, st>>>(v, n, ws->scal + 1, 1.0 / (double)n)));
   return ISIS_OK;
 }
 
@@ -216,6 +230,42 @@ __global__ void fill_k(T* __restrict__ a, T v, size_t n) {
 }
 
 __global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, size_t n);
+
+// Initial guess (isis_init): the background constant, or cell by cell the
+// solution for a uniform density equal to the cell's eta (computed in FP32:
+// it is only a starting point).
+template <Model M, class T>
+__global__ void init_guess(T* __restrict__ phi, const T* __restrict__ eta, size_t n, Coef c, int mode, double bg) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  if (mode == ISIS_INIT_BACKGROUND || M == POI) { phi[t] = (T)bg; return; }
+  float e = (float)eta[t];
+  if (M == SYM) {
+    float v = 1.0f - (float)c.s * e;
+    phi[t] = (T)(v > 0.0f ? sqrtf(v) : 0.0f);
+  } else {
+    // S(u) = 0 at this eta: e^{u/(n+1)} = K2 / (K1 (eta - 1) + K3)
+    float den = (float)c.K1 * (e - 1.0f) + (float)c.K3;
+    phi[t] = (T)((float)c.np1 * logf((float)c.K2 / den));
+  }
+}
+
+// background field of the model (the ISIS_INIT_BACKGROUND value)
+template <Model M>
+inline double background_value(const Coef& c) {
+  if (M == SYM) return c.s < 1.0 ? std::sqrt(1.0 - c.s) : 0.0;
+  if (M == FOFR) return c.np1 * std::log(c.K2 / c.K3);
+  return 0.0;
+}
+
+template <Model M, class T>
+isis_status apply_init(const SolveArgs& A, const Coef& c, T* phi, const T* eta, size_t n) {
+  if (A.init == ISIS_INIT_INPUT) return ISIS_OK;
+  cudaStream_t st = A.st;
+  ISIS_LAUNCH(KK_INIT, (double)n * sizeof(T) * (A.init == ISIS_INIT_LOCAL ? 2 : 1), st,
+              (init_guess<M, T><<<nblk(n, 256), 256, 0, st>>>(phi, eta, n, c, (int)A.init, background_value<M>(c))));
+  return ISIS_OK;
+}
 
 // FP64 residual of the finest grid for the defect-correction loop:
 // r = -L64(phi); writes r and B = phi rounded to FP32, and block partials of r^2.
@@ -268,13 +318,16 @@ isis_status solve_field(const SolveArgs& A) {
     if (s2 < 0) s2 = 0;
   }
   double ref = A.ref_scale * std::sqrt(s2 / (double)n);
+  s = apply_init<M, T>(A, c, phi, eta, n);
+  if (s != ISIS_OK) return s;
 
   // density on the coarse levels
   for (int l = 1; l < ws->nlev; ++l) {
     int lgc = ilog2(A.N >> l);
     const T* f = l == 1 ? eta : (const T*)ws->eta[l - 1];
-    restrict_mean<T, T><<<nblk((size_t)1 << (3 * lgc), 256), 256, 0, st>>>(f, (T*)ws->eta[l], lgc);
-    ISIS_CKL();
+    size_t ncl = (size_t)1 << (3 * lgc);
+    ISIS_LAUNCH(KK_SETUP, 9.0 * ncl * sizeof(T), st,
+                (restrict_mean<T, T><<<nblk(ncl, 256), 256, 0, st>>>(f, (T*)ws->eta[l], lgc)));
   }
   ISIS_CK(cudaMemsetAsync(ws->iflags, 0, 2 * sizeof(int), st));
 
@@ -344,15 +397,17 @@ isis_status solve_refine(const SolveArgs& A) {
     if (s2 < 0) s2 = 0;
   }
   double ref = A.ref_scale * std::sqrt(s2 / (double)n);
+  s = apply_init<M, double>(A, c, phi64, eta64, n);
+  if (s != ISIS_OK) return s;
 
   if (M != POI) {
-    convert_k<double, float><<<nblk(n, 256), 256, 0, st>>>(eta64, eta0, n);
-    ISIS_CKL();
+    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (convert_k<double, float><<<nblk(n, 256), 256, 0, st>>>(eta64, eta0, n)));
     for (int l = 1; l < ws->nlev; ++l) {
       int lgc = ilog2(A.N >> l);
-      restrict_mean<float, float><<<nblk((size_t)1 << (3 * lgc), 256), 256, 0, st>>>(
-          (const float*)ws->eta[l - 1], (float*)ws->eta[l], lgc);
-      ISIS_CKL();
+      size_t ncl = (size_t)1 << (3 * lgc);
+      ISIS_LAUNCH(KK_SETUP, 36.0 * ncl, st,
+                  (restrict_mean<float, float><<<nblk(ncl, 256), 256, 0, st>>>((const float*)ws->eta[l - 1],
+                                                                              (float*)ws->eta[l], lgc)));
     }
   }
   ISIS_CK(cudaMemsetAsync(ws->iflags, 0, 2 * sizeof(int), st));
@@ -379,10 +434,9 @@ isis_status solve_refine(const SolveArgs& A) {
   double target = 0.0;
   for (int outer = 0;; ++outer) {
     // r = -L64(phi64), B = fp32(phi64), RMS of r
-    outer_residual<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64, c, r0, B0, ws->part);
-    ISIS_CKL();
-    reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal);
-    ISIS_CKL();
+    ISIS_LAUNCH(KK_OUTER_RESID, 24.0 * n, st,
+                (outer_residual<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64, c, r0, B0, ws->part)));
+    ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
     ISIS_CK(cudaMemcpyAsync(h, ws->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
     ISIS_CK(cudaMemcpyAsync(hi, ws->iflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     ISIS_CK(cudaStreamSynchronize(st));
@@ -405,15 +459,16 @@ isis_status solve_refine(const SolveArgs& A) {
     // base field on every level (B_l = R B_{l-1}) and e^B for f(R)
     for (int l = 1; l < ws->nlev && M != POI; ++l) {
       int lgc = ilog2(A.N >> l);
-      restrict_mean<float, float><<<nblk((size_t)1 << (3 * lgc), 256), 256, 0, st>>>(
-          (const float*)ws->B[l - 1], (float*)ws->B[l], lgc);
-      ISIS_CKL();
+      size_t ncl = (size_t)1 << (3 * lgc);
+      ISIS_LAUNCH(KK_SETUP, 36.0 * ncl, st,
+                  (restrict_mean<float, float><<<nblk(ncl, 256), 256, 0, st>>>((const float*)ws->B[l - 1],
+                                                                              (float*)ws->B[l], lgc)));
     }
     if (M == FOFR) {
       for (int l = 0; l < ws->nlev; ++l) {
         size_t nl = (size_t)(A.N >> l) * (A.N >> l) * (A.N >> l);
-        exp_k<float><<<nblk(nl, 256), 256, 0, st>>>((const float*)ws->B[l], (float*)ws->w[l], nl);
-        ISIS_CKL();
+        ISIS_LAUNCH(KK_SETUP, 8.0 * nl, st,
+                    (exp_k<float><<<nblk(nl, 256), 256, 0, st>>>((const float*)ws->B[l], (float*)ws->w[l], nl)));
       }
     }
     ISIS_CK(cudaMemsetAsync(e0, 0, n * sizeof(float), st));
@@ -424,8 +479,7 @@ isis_status solve_refine(const SolveArgs& A) {
       if (s != ISIS_OK) return s;
     }
     loc.cycles += k;
-    update_phi64<<<nblk(n, 256), 256, 0, st>>>(phi64, e0, n);
-    ISIS_CKL();
+    ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_phi64<<<nblk(n, 256), 256, 0, st>>>(phi64, e0, n)));
     if (M == POI) {
       s = remove_mean<double>(ws, phi64, n, st);
       if (s != ISIS_OK) return s;

@@ -25,7 +25,9 @@ H0_MPC = 1.0 / 2997.92458  # (Mpc/h)^-1 with c = 1
 
 # Every function the header declares (checked by the tests).
 EXPORTS = ("isis_cic_deposit", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force",
-           "isis_strerror", "isis_release_workspace")
+           "isis_strerror", "isis_release_workspace", "isis_prof_enable", "isis_prof_reset", "isis_prof_read",
+           "isis_launch_count")
+ISIS_INIT_INPUT, ISIS_INIT_BACKGROUND, ISIS_INIT_LOCAL = 0, 1, 2
 
 
 class isis_grid(ctypes.Structure):
@@ -40,7 +42,13 @@ class isis_params(ctypes.Structure):
 
 class isis_mg_opts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("n_coarsest", ctypes.c_int),
-                ("max_cycles", ctypes.c_int), ("prec", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+                ("max_cycles", ctypes.c_int), ("prec", ctypes.c_int), ("inner_cycles", ctypes.c_int),
+                ("init", ctypes.c_int)]
+
+
+class isis_prof_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 class isis_solve_info(ctypes.Structure):
@@ -79,6 +87,14 @@ def load(path: str = LIB_PATH):
     lib.isis_strerror.restype = ctypes.c_char_p
     lib.isis_release_workspace.argtypes = []
     lib.isis_release_workspace.restype = None
+    lib.isis_prof_enable.argtypes = [ctypes.c_int]
+    lib.isis_prof_enable.restype = None
+    lib.isis_prof_reset.argtypes = []
+    lib.isis_prof_reset.restype = None
+    lib.isis_prof_read.argtypes = [P(isis_prof_entry), ctypes.c_int]
+    lib.isis_prof_read.restype = ctypes.c_int
+    lib.isis_launch_count.argtypes = []
+    lib.isis_launch_count.restype = ctypes.c_int64
     for name in ("isis_cic_deposit", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -121,9 +137,11 @@ class Opts:
     max_cycles: int = 100
     prec: int = ISIS_F64
     inner_cycles: int = 2
+    init: int = ISIS_INIT_INPUT
 
     def c(self):
-        return isis_mg_opts(self.nu1, self.nu2, self.n_coarsest, self.max_cycles, self.prec, self.inner_cycles)
+        return isis_mg_opts(self.nu1, self.nu2, self.n_coarsest, self.max_cycles, self.prec, self.inner_cycles,
+                            self.init)
 
 
 @dataclass
@@ -170,6 +188,25 @@ def strerror(status: int) -> str:
 
 def release_workspace() -> None:
     load().isis_release_workspace()
+
+
+def prof_enable(on: bool = True) -> None:
+    load().isis_prof_enable(1 if on else 0)
+
+
+def prof_reset() -> None:
+    load().isis_prof_reset()
+
+
+def launch_count() -> int:
+    return int(load().isis_launch_count())
+
+
+def prof_read() -> dict:
+    """Per kernel kind: {name: (launches, ms, algorithmic bytes)} (synchronises the device)."""
+    buf = (isis_prof_entry * 64)()
+    n = load().isis_prof_read(buf, 64)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms), float(buf[i].bytes)) for i in range(n)}
 
 
 # ---------------------------------------------------------------------------

@@ -131,7 +131,9 @@ def test_plain_f32(cuda_lib, model):
     eta = synth.lognormal_eta(N, box, 1.0, 1)
     m, g0 = _model_setup(isis, model, N, box, A1, par)
     phi = torch.full((N,) * 3, g0, dtype=torch.float32, device="cuda")
-    info = isis.isis_scalar_solve(m, par, isis.Grid(N, box), A1, eta.float().cuda(), phi, tol=1e-5,
+    # FP32 u ~ -11.5 carries ~5e-7 absolute rounding: the f(R) residual floors near 1e-4 of the reference
+    tol = 1e-5 if model == oracle.SYMMETRON else 1e-3
+    info = isis.isis_scalar_solve(m, par, isis.Grid(N, box), A1, eta.float().cuda(), phi, tol=tol,
                                   opts=isis.Opts(prec=isis.ISIS_F32))
     assert info.status == isis.ISIS_OK
     ref = oracle.solve(_prob(model, N, box, A1), eta.numpy(), np.full((N,) * 3, g0), tol=1e-12)
