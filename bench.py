@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--N", type=int, default=512)
     ap.add_argument("--box", type=float, default=256.0)
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--inner", type=int, default=2)
+    ap.add_argument("--inner", type=int, default=3)
+    ap.add_argument("--ncoarse", type=int, default=2, help="coarsest grid (dense Newton): 2 or 4")
     ap.add_argument("--sample-N", type=int, default=128, help="grid of the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -53,7 +54,7 @@ def workload(args):
                         f"forces of both models",
             "N": args.N, "box_mpc_h": args.box, "particles": args.N ** 3, "tol": args.tol,
             "symmetron": {"a": 1.0, "a_ssb": 0.5, "lambda0": 1.0, "beta": 1.0},
-            "fofr": {"n": 1, "fR0_abs": 1e-5}, "cycle": "V(2,2), coarsest 4^3 dense Newton",
+            "fofr": {"n": 1, "fR0_abs": 1e-5}, "cycle": f"V(2,2), coarsest {args.ncoarse}^3 dense Newton",
             "inner_cycles": args.inner,
             "l2": "inputs larger than L2 (each 512^3 field is 0.5-1 GB), no flush",
             "parallelism": "replicas (one independent problem per GPU)"}
@@ -213,7 +214,8 @@ def main():
     chi = torch.empty((N,) * 3, **f64)
     u = torch.empty((N,) * 3, **f64)
     g = [torch.empty(npart, device=dev, dtype=torch.float32) for _ in range(6)]
-    opts_bg = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=args.inner, init=isis.ISIS_INIT_BACKGROUND)
+    opts_bg = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=args.inner, init=isis.ISIS_INIT_BACKGROUND,
+                        n_coarsest=args.ncoarse)
     stream = torch.cuda.current_stream()
     infos = {}
 

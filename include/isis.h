@@ -57,10 +57,13 @@ typedef enum { ISIS_SYMMETRON = 1, ISIS_FOFR_HS = 2 } isis_model;
  *   ISIS_F64           eta, phi are double; every kernel computes in FP64.
  *   ISIS_F32           eta, phi are float; every kernel computes in FP32
  *                      (coarsest dense Newton in FP64).
- *   ISIS_F32_REFINE64  eta, phi are double.  Outer defect correction: the
- *                      residual r = -L(phi) and the update phi += e are FP64;
- *                      e solves L(phi + e) - L(phi) = r by FP32 FAS V-cycles
- *                      on the correction (coarsest dense Newton in FP64). */
+ *   ISIS_F32_REFINE64  eta, phi are double.  First FP32 FAS V-cycles on the
+ *                      field itself until its residual is below 1e-4 of the
+ *                      reference (or stops falling); then FP64 defect
+ *                      correction: the residual r = -L(phi) and the update
+ *                      phi += e are FP64, and e solves L(phi + e) - L(phi) = r
+ *                      by FP32 FAS V-cycles on the correction (inner_cycles per
+ *                      outer iteration; coarsest dense Newton in FP64). */
 typedef enum { ISIS_F64 = 0, ISIS_F32 = 1, ISIS_F32_REFINE64 = 2 } isis_precision;
 
 typedef struct {
@@ -97,12 +100,14 @@ typedef struct {
 } isis_mg_opts;
 
 typedef struct {
-  int cycles;          /* V-cycles run (FP32 inner cycles for F32_REFINE64) */
+  int cycles;          /* V-cycles run (all FP32 cycles for F32_REFINE64) */
   int outer;           /* FP64 outer iterations (F32_REFINE64), else 0 */
-  double res0;         /* RMS residual of the initial guess */
+  int nhist;           /* entries of hist */
+  double res0;         /* RMS residual of the initial guess (FP32-evaluated for F32_REFINE64) */
   double res_ref;      /* reference residual (below) */
-  double res_final;    /* RMS residual on return */
-  double hist[128];    /* RMS residual after each cycle (outer iteration for F32_REFINE64) */
+  double res_final;    /* RMS residual on return (FP64-evaluated unless ISIS_F32) */
+  double hist[128];    /* RMS residual after each V-cycle; for F32_REFINE64 after each FP32
+                          field-form cycle, then after each FP64 outer iteration */
 } isis_solve_info;
 
 /* Convergence test of both solvers (the paper gives none): stop when
@@ -120,9 +125,10 @@ typedef struct {
  *            wrapped into [0, N)); cell centres at i + 1/2.
  *   eta      device double[N^3] (eta_f64 != 0) or float[N^3] (eta_f64 == 0),
  *            overwritten.
- * Accumulation is in 64-bit fixed point (2^-40 per unit weight), so the
- * result does not depend on the order of particles; a cell may collect at
- * most 2^23 unit weights.  Uses an int64 N^3 scratch buffer cached by the
+ * Accumulation is in 64-bit fixed point: each particle's eight weights are
+ * truncated to multiples of 2^-40 and summed as integers, so the result does
+ * not depend on the order of particles; a cell may collect at most 2^23 unit
+ * weights.  Uses an int64 N^3 scratch buffer cached by the
  * library.  EINVAL: npart < 1, npart > 2^40 or N invalid. */
 isis_status isis_cic_deposit(const isis_grid* grid, const float* x, const float* y, const float* z, int64_t npart,
                              void* eta, int eta_f64, void* stream);

@@ -47,11 +47,17 @@ Workspace* get_workspace(int N, int esize, int ncoarse) {
   for (int l = 0; l < nlev && ok; ++l) {
     size_t nl = (size_t)(N >> l) * (N >> l) * (N >> l);
     for (auto* a : arrays) {
-      // the finest level's buffers only serve the FP32 correction cycles
+      // the finest level's buffers only serve the FP32 cycles
       void* p = (l == 0 && esize != 4) ? nullptr : alloc(nl * esize);
       if (!(l == 0 && esize != 4) && !p) ok = false;
       a->push_back(p);
     }
+    void* p = nullptr;
+    if (esize == 4 && (N >> l) >= kStreamMinN) {
+      p = alloc(nl * esize);
+      if (!p) ok = false;
+    }
+    w->xalt.push_back(p);
   }
   if (ok) {
     w->part = (double*)alloc(kNormBlocks * sizeof(double));
@@ -61,6 +67,12 @@ Workspace* get_workspace(int N, int esize, int ncoarse) {
     ok = w->part && w->part2 && w->scal && w->iflags;
   }
   if (ok && cudaMallocHost(&w->host, 256) != cudaSuccess) ok = false;
+  if (ok) {
+    w->exptab = (double*)alloc(256 * sizeof(double));
+    double tab[256];
+    exp_table_fill(tab);
+    ok = w->exptab && cudaMemcpy(w->exptab, tab, sizeof(tab), cudaMemcpyHostToDevice) == cudaSuccess;
+  }
   if (!ok) {
     free_ws(w);
     cudaGetLastError();
@@ -68,6 +80,19 @@ Workspace* get_workspace(int N, int esize, int ncoarse) {
   }
   g_ws.push_back(w);
   return w;
+}
+
+bool ensure_fofr64(Workspace* w) {
+  if (w->b64) return true;
+  size_t n = (size_t)w->N * w->N * w->N;
+  void *p = nullptr, *q = nullptr;
+  if (cudaMalloc(&p, n * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return false; }
+  if (cudaMalloc(&q, n * sizeof(double)) != cudaSuccess) { cudaFree(p); cudaGetLastError(); return false; }
+  w->owned.push_back(p);
+  w->owned.push_back(q);
+  w->b64 = (double*)p;
+  w->s64 = (double*)q;
+  return true;
 }
 
 // int64 accumulation buffer of the CIC deposit, cached per (device, N)
@@ -89,6 +114,23 @@ unsigned long long* get_deposit_buf(int N) {
   }
   g_dep.push_back({N, dev, (unsigned long long*)p});
   return (unsigned long long*)p;
+}
+
+// three float N^3 arrays of the grid force, cached per (device, N)
+static std::vector<DepositBuf> g_fgrid;
+
+float* get_force_buf(int N) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  for (auto& d : g_fgrid)
+    if (d.N == N && d.device == dev) return (float*)d.acc;
+  void* p = nullptr;
+  if (cudaMalloc(&p, (size_t)3 * N * N * N * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  g_fgrid.push_back({N, dev, (unsigned long long*)p});
+  return (float*)p;
 }
 
 // ---------------------------------------------------------------------------
@@ -144,7 +186,7 @@ static const char* kKindNames[KK_COUNT] = {
     "smooth_fine",    "smooth_coarse", "resid_restrict_fine", "resid_restrict_coarse", "coarse_sigma",
     "prolong_fine",   "prolong_coarse", "coarse_newton",      "norm_fine",             "outer_residual64",
     "update64",       "setup",         "reduce",              "init_guess",            "cic_scatter",
-    "cic_finish",     "force_gather"};
+    "cic_finish",     "force_grid",    "force_gather"};
 
 struct ProfRec {
   int kind;
@@ -212,6 +254,8 @@ void isis_release_workspace(void) {
   g_ws.clear();
   for (auto& d : g_dep) cudaFree(d.acc);
   g_dep.clear();
+  for (auto& d : g_fgrid) cudaFree(d.acc);
+  g_fgrid.clear();
 }
 
 void isis_prof_enable(int on) { g_prof_on = on != 0; }

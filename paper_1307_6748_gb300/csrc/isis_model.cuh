@@ -53,6 +53,48 @@ template <class T> __device__ __forceinline__ T dexpm1(T v);
 template <> __device__ __forceinline__ double dexpm1<double>(double v) { return expm1(v); }
 template <> __device__ __forceinline__ float dexpm1<float>(float v) { return expm1f(v); }
 
+// f(R) in the field form with b = e^x of the cell and its neighbours given:
+//   F  = h^-2 sum_f b_f (x_nb - x) - S(x) - Sigma,   b_f = (b + b_nb)/2
+//   dF = h^-2 sum_f [ (b/2)(x_nb - x) - b_f ] - dS/dx
+template <class T>
+__device__ __forceinline__ void fofr_field_eval(const Coef& c, T ih2, T x, T b, const T* xn, const T* bn, T eta,
+                                                T sig, T& F, T& dF) {
+  T flux = 0, dsum = 0;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    T du = xn[d] - x;
+    T bf = T(0.5) * (b + bn[d]);
+    flux += bf * du;
+    dsum += T(0.5) * b * du - bf;
+  }
+  T K2 = T(c.K2), inp1 = T(c.inv_np1);
+  T ex = dexp<T>(-x * inp1);
+  T S = T(c.K1) * (eta - T(1)) - K2 * ex + T(c.K3);
+  F = flux * ih2 - S - sig;
+  dF = dsum * ih2 - K2 * inp1 * ex;
+}
+
+// f(R) in the correction form about the base B, with m = e^B expm1(e) and
+// bt = e^{B+e} = e^B + m of the cell and its neighbours given:
+//   N_B(e) = h^-2 sum_f { (m + m_nb)/2 (B_nb - B) + (bt + bt_nb)/2 (e_nb - e) }
+//            + K2 e^{-B/(n+1)} expm1(-e/(n+1))
+template <class T>
+__device__ __forceinline__ void fofr_delta_eval(const Coef& c, T ih2, T e, T B, T m, T bt, const T* en, const T* Bn,
+                                                const T* mn, const T* btn, T sig, T& F, T& dF) {
+  T flux = 0, dsum = 0;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    T dB = Bn[d] - B, de = en[d] - e;
+    T bf = T(0.5) * (bt + btn[d]);
+    flux += T(0.5) * (m + mn[d]) * dB + bf * de;
+    dsum += T(0.5) * bt * (dB + de) - bf;
+  }
+  T K2 = T(c.K2), inp1 = T(c.inv_np1);
+  T exB = dexp<T>(-B * inp1);
+  F = flux * ih2 + K2 * exB * dexpm1<T>(-e * inp1) - sig;
+  dF = dsum * ih2 - K2 * inp1 * exB * dexp<T>(-e * inp1);
+}
+
 // F = L(x) - Sigma and dF = dL/dx at one cell.
 template <Model M, Form FM, class T>
 __device__ __forceinline__ void eval_cell(const Coef& c, T ih2, const Cell<T>& q, T& F, T& dF) {
@@ -77,38 +119,20 @@ __device__ __forceinline__ void eval_cell(const Coef& c, T ih2, const Cell<T>& q
       dF = T(-6) * ih2 - A * (sm1 + T(3) * u * u);
     }
   } else {  // FOFR
-    T K2 = T(c.K2), inp1 = T(c.inv_np1);
     if constexpr (FM == FIELD) {
-      T bu = dexp<T>(q.x);
-      T flux = 0, dsum = 0;
+      T bn[6];
 #pragma unroll
-      for (int d = 0; d < 6; ++d) {
-        T du = q.xn[d] - q.x;
-        T bf = T(0.5) * (bu + dexp<T>(q.xn[d]));
-        flux += bf * du;
-        dsum += T(0.5) * bu * du - bf;
-      }
-      T ex = dexp<T>(-q.x * inp1);
-      T S = T(c.K1) * (q.eta - T(1)) - K2 * ex + T(c.K3);
-      F = flux * ih2 - S - q.sig;
-      dF = dsum * ih2 - K2 * inp1 * ex;
+      for (int d = 0; d < 6; ++d) bn[d] = dexp<T>(q.xn[d]);
+      fofr_field_eval<T>(c, ih2, q.x, dexp<T>(q.x), q.xn, bn, q.eta, q.sig, F, dF);
     } else {
-      // N_B(e) = h^-2 sum_f { (m + m_nb)/2 (B_nb - B) + (bt + bt_nb)/2 (e_nb - e) }
-      //          + K2 e^{-B/(n+1)} expm1(-e/(n+1))
-      // with m = e^B expm1(e) and bt = e^{B+e} = e^B + m.
-      T m = q.w * dexpm1<T>(q.x), bt = q.w + m;
-      T flux = 0, dsum = 0;
+      T mn[6], btn[6];
 #pragma unroll
       for (int d = 0; d < 6; ++d) {
-        T mn = q.wn[d] * dexpm1<T>(q.xn[d]), btn = q.wn[d] + mn;
-        T dB = q.Bn[d] - q.B, de = q.xn[d] - q.x;
-        T bf = T(0.5) * (bt + btn);
-        flux += T(0.5) * (m + mn) * dB + bf * de;
-        dsum += T(0.5) * bt * (dB + de) - bf;
+        mn[d] = q.wn[d] * dexpm1<T>(q.xn[d]);
+        btn[d] = q.wn[d] + mn[d];
       }
-      T exB = dexp<T>(-q.B * inp1);
-      F = flux * ih2 + K2 * exB * dexpm1<T>(-q.x * inp1) - q.sig;
-      dF = dsum * ih2 - K2 * inp1 * exB * dexp<T>(-q.x * inp1);
+      T m = q.w * dexpm1<T>(q.x);
+      fofr_delta_eval<T>(c, ih2, q.x, q.B, m, q.w + m, q.xn, q.Bn, mn, btn, q.sig, F, dF);
     }
   }
 }

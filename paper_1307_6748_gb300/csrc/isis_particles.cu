@@ -12,6 +12,7 @@
 namespace isis {
 
 unsigned long long* get_deposit_buf(int N);
+float* get_force_buf(int N);
 
 constexpr double kFix = 1099511627776.0;  // 2^40 fixed-point units per unit weight
 
@@ -36,23 +37,61 @@ __device__ __forceinline__ Axis cic_axis(float xf, int N) {
   return a;
 }
 
+// Exact per-axis CIC weights in units of 2^-23 for 1 <= x < N (every float
+// there is a multiple of 2^-23, so floor, the offset t and 1 - t are exact).
+// Returns false outside that range (those particles take the FP64 path).
+__device__ __forceinline__ bool cic_axis_fix(float x, int N, int& i0, unsigned& w0, unsigned& w1) {
+  if (!(x >= 1.0f && x < (float)N)) return false;
+  const float xi = floorf(x), fx = x - xi;
+  float t;
+  if (fx >= 0.5f) { i0 = (int)xi; t = fx - 0.5f; }
+  else { i0 = (int)xi - 1; t = fx + 0.5f; }
+  w1 = (unsigned)(t * 8388608.0f);  // exact: t is a multiple of 2^-23
+  w0 = 8388608u - w1;
+  return true;
+}
+
+// (a b c) 2^-69 in units of 2^-40, truncated; a, b, c <= 2^23.
+__device__ __forceinline__ unsigned long long fix3(unsigned a, unsigned b, unsigned c) {
+  const unsigned long long ab = (unsigned long long)a * b;  // <= 2^46, exact
+  const unsigned long long lo = ab * c, hi = __umul64hi(ab, (unsigned long long)c);
+  return (hi << 35) | (lo >> 29);
+}
+
 __global__ void cic_scatter(const float* __restrict__ x, const float* __restrict__ y, const float* __restrict__ z,
                             long long np, int lg, unsigned long long* __restrict__ acc) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
-  const int N = 1 << lg;
-  Axis ax = cic_axis(x[p], N), ay = cic_axis(y[p], N), az = cic_axis(z[p], N);
-  const int ii[2] = {ax.i0, ax.i1}, jj[2] = {ay.i0, ay.i1}, kk[2] = {az.i0, az.i1};
-  const double wi[2] = {ax.w0, ax.w1}, wj[2] = {ay.w0, ay.w1}, wk[2] = {az.w0, az.w1};
+  const int N = 1 << lg, m = N - 1;
+  const float px = x[p], py = y[p], pz = z[p];
+  int ii, jj, kk;
+  unsigned wi[2], wj[2], wk[2];
+  if (cic_axis_fix(px, N, ii, wi[0], wi[1]) && cic_axis_fix(py, N, jj, wj[0], wj[1]) &&
+      cic_axis_fix(pz, N, kk, wk[0], wk[1])) {
+    // all-integer path: exact weights, exact products, truncation to 2^-40
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+          const unsigned long long q = fix3(wi[a], wj[b], wk[d]);
+          if (q) atomicAdd(&acc[cidx(lg, (ii + a) & m, (jj + b) & m, (kk + d) & m)], q);
+        }
+    return;
+  }
+  // positions in [0, 1) or outside [0, N): FP64 weights, truncated to 2^-40
+  Axis ax = cic_axis(px, N), ay = cic_axis(py, N), az = cic_axis(pz, N);
+  const int is[2] = {ax.i0, ax.i1}, js[2] = {ay.i0, ay.i1}, ks[2] = {az.i0, az.i1};
+  const double wx[2] = {ax.w0, ax.w1}, wy[2] = {ay.w0, ay.w1}, wz[2] = {az.w0, az.w1};
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
-        double w = wi[a] * wj[b] * wk[d];
-        unsigned long long q = (unsigned long long)llrint(w * kFix);
-        if (q) atomicAdd(&acc[cidx(lg, ii[a], jj[b], kk[d])], q);
+        const unsigned long long q = (unsigned long long)(wx[a] * wy[b] * wz[d] * kFix);
+        if (q) atomicAdd(&acc[cidx(lg, is[a], js[b], ks[d])], q);
       }
 }
 
@@ -62,53 +101,86 @@ __global__ void cic_finish(const unsigned long long* __restrict__ acc, T* __rest
   if (t < n) eta[t] = (T)((double)acc[t] * scale);
 }
 
-// Per-particle acceleration.  Grid force at cell c along axis d:
-//   f_d(c) = a^2 D_d Phi(c) + pref(c) D_d phi(c),  D_d f(c) = (f(c+e_d) - f(c-e_d)) / (2h)
-//   pref = C_s a^2 chi(c) (symmetron), e^u(c)/2 (f(R)), 0 (no scalar field)
-// then g = -sum_cells W f.
+// Grid force at every cell (one pass):
+//   f_d(c) = [a^2 (Phi(c+e_d) - Phi(c-e_d)) + pref(c) (phi(c+e_d) - phi(c-e_d))] / (2h)
+//   pref = C_s a^2 chi(c) (symmetron, Eq. (symmetron_geodesics_tilde_chi) with chi~ = a chi),
+//          e^u(c)/2 (f(R), Sect. 4.2), 0 without a scalar field.
+// The differences are taken in the field's precision (FP64 fields lose no
+// digits to cancellation), the products in FP32 (the output is FP32).
 template <class T, int MODEL>
-__global__ void force_gather(const T* __restrict__ Phi, const T* __restrict__ phi, const float* __restrict__ x,
-                             const float* __restrict__ y, const float* __restrict__ z, long long np, int lg,
-                             double a2, double Cs, double inv2h, float* __restrict__ gx, float* __restrict__ gy,
-                             float* __restrict__ gz) {
+__global__ void force_grid(const T* __restrict__ Phi, const T* __restrict__ phi, int lg, float a2, float Cs,
+                           float inv2h, float* __restrict__ fx, float* __restrict__ fy, float* __restrict__ fz) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t n = (size_t)1 << (3 * lg);
+  if (t >= n) return;
+  const int m = (1 << lg) - 1;
+  int k = (int)(t & m), j = (int)((t >> lg) & m), i = (int)(t >> (2 * lg));
+  const size_t xp = cidx(lg, (i + 1) & m, j, k), xm = cidx(lg, (i - 1) & m, j, k);
+  const size_t yp = cidx(lg, i, (j + 1) & m, k), ym = cidx(lg, i, (j - 1) & m, k);
+  const size_t zp = cidx(lg, i, j, (k + 1) & m), zm = cidx(lg, i, j, (k - 1) & m);
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+  if (Phi) {
+    g0 = a2 * (float)(Phi[xp] - Phi[xm]);
+    g1 = a2 * (float)(Phi[yp] - Phi[ym]);
+    g2 = a2 * (float)(Phi[zp] - Phi[zm]);
+  }
+  if (MODEL != 0) {
+    float v = (float)phi[t];
+    float pref = (MODEL == ISIS_SYMMETRON) ? Cs * a2 * v : 0.5f * expf(v);
+    g0 = fmaf(pref, (float)(phi[xp] - phi[xm]), g0);
+    g1 = fmaf(pref, (float)(phi[yp] - phi[ym]), g1);
+    g2 = fmaf(pref, (float)(phi[zp] - phi[zm]), g2);
+  }
+  fx[t] = g0 * inv2h;
+  fy[t] = g1 * inv2h;
+  fz[t] = g2 * inv2h;
+}
+
+// FP32 CIC weights of one axis (exact for 1 <= x < N; to FP32 rounding elsewhere).
+__device__ __forceinline__ void cic_axis_f(float x, int N, int& i0, int& i1, float& w0, float& w1) {
+  float xs = x - 0.5f;
+  float f = floorf(xs);
+  float t = xs - f;
+  float fw = f - (float)N * floorf(f / (float)N);
+  int i = (int)fw;
+  i = i < 0 ? 0 : (i >= N ? N - 1 : i);
+  i0 = i;
+  i1 = (i + 1) & (N - 1);
+  w0 = 1.0f - t;
+  w1 = t;
+}
+
+// Per-particle acceleration g = -sum over the 8 CIC cells of W f (FP32).
+__global__ void force_gather(const float* __restrict__ fx, const float* __restrict__ fy,
+                             const float* __restrict__ fz, const float* __restrict__ x, const float* __restrict__ y,
+                             const float* __restrict__ z, long long np, int lg, float* __restrict__ gx,
+                             float* __restrict__ gy, float* __restrict__ gz) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
-  const int N = 1 << lg, m = N - 1;
-  Axis ax = cic_axis(x[p], N), ay = cic_axis(y[p], N), az = cic_axis(z[p], N);
-  const int ii[2] = {ax.i0, ax.i1}, jj[2] = {ay.i0, ay.i1}, kk[2] = {az.i0, az.i1};
-  const double wi[2] = {ax.w0, ax.w1}, wj[2] = {ay.w0, ay.w1}, wk[2] = {az.w0, az.w1};
-  double acc[3] = {0.0, 0.0, 0.0};
+  const int N = 1 << lg;
+  int ii[2], jj[2], kk[2];
+  float wi[2], wj[2], wk[2];
+  cic_axis_f(x[p], N, ii[0], ii[1], wi[0], wi[1]);
+  cic_axis_f(y[p], N, jj[0], jj[1], wj[0], wj[1]);
+  cic_axis_f(z[p], N, kk[0], kk[1], wk[0], wk[1]);
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 2; ++b) {
+      const float wab = wi[a] * wj[b];
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
-        const int i = ii[a], j = jj[b], k = kk[d];
-        const double w = wi[a] * wj[b] * wk[d];
-        const size_t xp = cidx(lg, (i + 1) & m, j, k), xm = cidx(lg, (i - 1) & m, j, k);
-        const size_t yp = cidx(lg, i, (j + 1) & m, k), ym = cidx(lg, i, (j - 1) & m, k);
-        const size_t zp = cidx(lg, i, j, (k + 1) & m), zm = cidx(lg, i, j, (k - 1) & m);
-        double f0 = 0.0, f1 = 0.0, f2 = 0.0;
-        if (Phi) {
-          f0 = a2 * ((double)Phi[xp] - (double)Phi[xm]);
-          f1 = a2 * ((double)Phi[yp] - (double)Phi[ym]);
-          f2 = a2 * ((double)Phi[zp] - (double)Phi[zm]);
-        }
-        if (MODEL != 0) {
-          double v = (double)phi[cidx(lg, i, j, k)];
-          double pref = (MODEL == ISIS_SYMMETRON) ? Cs * a2 * v : 0.5 * exp(v);
-          f0 += pref * ((double)phi[xp] - (double)phi[xm]);
-          f1 += pref * ((double)phi[yp] - (double)phi[ym]);
-          f2 += pref * ((double)phi[zp] - (double)phi[zm]);
-        }
-        acc[0] += w * f0;
-        acc[1] += w * f1;
-        acc[2] += w * f2;
+        const size_t c = cidx(lg, ii[a], jj[b], kk[d]);
+        const float w = wab * wk[d];
+        a0 = fmaf(w, __ldg(&fx[c]), a0);
+        a1 = fmaf(w, __ldg(&fy[c]), a1);
+        a2 = fmaf(w, __ldg(&fz[c]), a2);
       }
-  gx[p] = (float)(-acc[0] * inv2h);
-  gy[p] = (float)(-acc[1] * inv2h);
-  gz[p] = (float)(-acc[2] * inv2h);
+    }
+  gx[p] = -a0;
+  gy[p] = -a1;
+  gz[p] = -a2;
 }
 
 static bool grid_valid(const isis_grid* g) {
@@ -156,24 +228,31 @@ isis_status isis_fifth_force(isis_model model, const isis_params* p, const isis_
     Cs = 6.0 * grid->Omega_m * grid->H0 * grid->H0 * (p->beta * p->lambda0) * (p->beta * p->lambda0) /
          (p->a_ssb * p->a_ssb * p->a_ssb);
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned nb = nblk((size_t)npart, 256);
+  const size_t n = (size_t)grid->N * grid->N * grid->N;
+  float* fg = get_force_buf(grid->N);
+  if (!fg) return ISIS_ENOMEM;
+  float* fx = fg;
+  float* fy = fg + n;
+  float* fz = fg + 2 * n;
   int mcode = phi ? (int)model : 0;
-  const double fbytes = 24.0 * npart + (double)grid->N * grid->N * grid->N * (fields_f64 ? 8 : 4) *
-                                             ((Phi ? 1 : 0) + (phi ? 1 : 0));
-#define ISIS_FORCE(T, MC)                                                                                    \
-  ISIS_LAUNCH(KK_FORCE, fbytes, st,                                                                          \
-              (force_gather<T, MC><<<nb, 256, 0, st>>>((const T*)Phi, (const T*)phi, x, y, z, (long long)npart, \
-                                                       lg, a2, Cs, inv2h, gx, gy, gz)))
+  const double gbytes = (double)n * ((fields_f64 ? 8 : 4) * ((Phi ? 1 : 0) + (phi ? 1 : 0)) + 12);
+#define ISIS_FGRID(T, MC)                                                                                      \
+  ISIS_LAUNCH(KK_FORCE_GRID, gbytes, st,                                                                       \
+              (force_grid<T, MC><<<nblk(n, 256), 256, 0, st>>>((const T*)Phi, (const T*)phi, lg, (float)a2,    \
+                                                               (float)Cs, (float)inv2h, fx, fy, fz)))
   if (fields_f64) {
-    if (mcode == 0) ISIS_FORCE(double, 0);
-    else if (mcode == ISIS_SYMMETRON) ISIS_FORCE(double, ISIS_SYMMETRON);
-    else ISIS_FORCE(double, ISIS_FOFR_HS);
+    if (mcode == 0) ISIS_FGRID(double, 0);
+    else if (mcode == ISIS_SYMMETRON) ISIS_FGRID(double, ISIS_SYMMETRON);
+    else ISIS_FGRID(double, ISIS_FOFR_HS);
   } else {
-    if (mcode == 0) ISIS_FORCE(float, 0);
-    else if (mcode == ISIS_SYMMETRON) ISIS_FORCE(float, ISIS_SYMMETRON);
-    else ISIS_FORCE(float, ISIS_FOFR_HS);
+    if (mcode == 0) ISIS_FGRID(float, 0);
+    else if (mcode == ISIS_SYMMETRON) ISIS_FGRID(float, ISIS_SYMMETRON);
+    else ISIS_FGRID(float, ISIS_FOFR_HS);
   }
-#undef ISIS_FORCE
+#undef ISIS_FGRID
+  ISIS_LAUNCH(KK_FORCE, 24.0 * npart + 12.0 * n, st,
+              (force_gather<<<nblk((size_t)npart, 256), 256, 0, st>>>(fx, fy, fz, x, y, z, (long long)npart, lg, gx,
+                                                                      gy, gz)));
   return ISIS_OK;
 }
 

@@ -24,6 +24,7 @@ enum KernelKind : int {
   KK_INIT,              // initial guess
   KK_CIC_SCATTER,
   KK_CIC_FINISH,
+  KK_FORCE_GRID,
   KK_FORCE,
   KK_COUNT
 };

@@ -11,6 +11,8 @@
 
 #include "../../include/isis.h"
 #include "isis_coarse.cuh"
+#include "isis_stream.cuh"
+#include "isis_exp64.cuh"
 #include "isis_prof.cuh"
 
 namespace isis {
@@ -30,13 +32,20 @@ struct Workspace {
   int nlev = 0;
   // per level l (0 = finest): x, x0, sig, eta, B, w (element type T)
   std::vector<void*> x, x0, sig, eta, B, w;
+  std::vector<void*> xalt;    // second buffer of x for the streaming smoother (FP32, N >= kStreamMinN)
   double* part = nullptr;     // kNormBlocks partial sums
   double* part2 = nullptr;    // second set of partials
   double* scal = nullptr;     // device scalars: [0] norm^2, [1] sum, [2] aux
   int* iflags = nullptr;      // [0] coarse flags, [1] coarse steps max
   void* host = nullptr;       // pinned readback area
+  double* exptab = nullptr;   // 2^(j/256), j < 256, for exp_tang
+  double* b64 = nullptr;      // finest level, FP64: e^u (f(R) residual), allocated on first use
+  double* s64 = nullptr;      // finest level, FP64: S(u, eta) (f(R) residual)
   std::vector<void*> owned;
 };
+
+// FP64 scratch of the f(R) residual on the finest grid (lazily allocated).
+bool ensure_fofr64(Workspace* ws);
 
 // Returns nullptr on allocation failure.  Implemented in isis_api.cu.
 Workspace* get_workspace(int N, int esize, int ncoarse);
@@ -72,6 +81,34 @@ inline int ilog2(int n) {
 }
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Grids at least this large are smoothed by the temporally blocked streaming
+// kernel (FP32 only); smaller ones by the one-colour kernel.
+constexpr int kStreamMinN = 128;
+// Sweeps fused per streaming pass (1 or 2).
+constexpr int kStreamSweeps = 1;
+
+// One streaming pass of NSW sweeps: xin -> xout.
+template <Model M, Form FM, int NSW>
+isis_status stream_pass(const LevelView<float>& v, float* xout, const Coef& c, cudaStream_t st, double bytes,
+                        int kind) {
+  constexpr int TJ = StreamCfg<M, FM, NSW>::TJ, H = 2 * NSW;
+  constexpr size_t smem = stream_smem<M, FM, NSW>();
+  static bool attr_done = false;
+  if (!attr_done) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(smooth_stream<M, FM, NSW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+      return ISIS_ECUDA;
+    attr_done = true;
+  }
+  const int N = v.N;
+  const int TI = N >= 512 ? 64 : (N >= 256 ? 32 : 16);
+  dim3 grid((unsigned)((N + (64 - 2 * H) - 1) / (64 - 2 * H)), (unsigned)((N + (TJ - 2 * H) - 1) / (TJ - 2 * H)),
+            (unsigned)(N / TI));
+  ISIS_LAUNCH(kind, bytes, st, (smooth_stream<M, FM, NSW><<<grid, 32 * TJ, smem, st>>>(v, xout, c, TI)));
+  return ISIS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // V-cycle driver for one model / form / element type
 // ---------------------------------------------------------------------------
@@ -79,6 +116,7 @@ inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 template <Model M, Form FM, class T>
 struct Cycler {
   std::vector<LevelView<T>> L;
+  std::vector<T*> alt;  // second buffer of each level's x (streaming smoother), else nullptr
   Workspace* ws = nullptr;
   Coef c;
   int nu1 = 2, nu2 = 2;
@@ -92,7 +130,9 @@ struct Cycler {
     nu2 = A.nu2;
     st = A.st;
     L.resize(ws->nlev);
+    alt.assign(ws->nlev, nullptr);
     for (int l = 0; l < ws->nlev; ++l) {
+      if (sizeof(T) == 4) alt[l] = (T*)ws->xalt[l];
       int N = A.N >> l;
       double h = A.box / N;
       LevelView<T> v;
@@ -119,14 +159,33 @@ struct Cycler {
   static double cells(const LevelView<T>& v) { return (double)v.N * v.N * v.N; }
 
   isis_status smooth(int l, int sweeps) {
-    const LevelView<T>& v = L[l];
+    LevelView<T>& v = L[l];
     size_t half = ((size_t)v.N * v.N * v.N) / 2;
-    // a full sweep reads x and the per-cell arrays once and writes x once
-    double bytes = 0.5 * cells(v) * sizeof(T) * (2 + arrays(v.sig != nullptr));
+    // algorithmic bytes of a full sweep, and of one streaming pass of 1 or 2
+    // sweeps: read x and the per-cell arrays once, write x once
+    double bytes = cells(v) * sizeof(T) * (2 + arrays(v.sig != nullptr));
     int kind = l == 0 ? KK_SMOOTH_FINE : KK_SMOOTH_COARSE;
+    if constexpr (sizeof(T) == 4) {
+      if (v.N >= kStreamMinN && alt[l]) {
+        // one sweep per pass over HBM (fusing two costs more in redundant halo
+        // work than it saves in traffic); the field alternates between x and alt
+        int left = sweeps;
+        while (left > 0) {
+          int nsw = (left >= 2 && kStreamSweeps == 2) ? 2 : 1;
+          float* out = alt[l];
+          isis_status r = nsw == 2 ? stream_pass<M, FM, 2>(v, out, c, st, bytes, kind)
+                                   : stream_pass<M, FM, 1>(v, out, c, st, bytes, kind);
+          if (r != ISIS_OK) return r;
+          alt[l] = v.x;
+          v.x = out;
+          left -= nsw;
+        }
+        return ISIS_OK;
+      }
+    }
     for (int s = 0; s < sweeps; ++s)
       for (int color = 0; color < 2; ++color)
-        ISIS_LAUNCH(kind, bytes, st, (smooth_color<M, FM, T><<<nblk(half, 256), 256, 0, st>>>(v, c, color)));
+        ISIS_LAUNCH(kind, bytes * 0.5, st, (smooth_color<M, FM, T><<<nblk(half, 256), 256, 0, st>>>(v, c, color)));
     return ISIS_OK;
   }
 
@@ -269,6 +328,7 @@ isis_status apply_init(const SolveArgs& A, const Coef& c, T* phi, const T* eta, 
 
 // FP64 residual of the finest grid for the defect-correction loop:
 // r = -L64(phi); writes r and B = phi rounded to FP32, and block partials of r^2.
+// (Poisson and symmetron: the operator has no transcendental terms.)
 template <Model M>
 __global__ void __launch_bounds__(kNormThreads) outer_residual(LevelView<double> L, Coef c, float* __restrict__ r32,
                                                                float* __restrict__ B32, double* __restrict__ part) {
@@ -285,6 +345,19 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual(LevelView<double>
   }
   block_sum_store<double>(acc, part);
 }
+
+// f(R), first pass: per cell b = e^u and S(u, eta) = K1 (eta - 1) - K2 e^{-u/(n+1)} + K3,
+// each exponential evaluated once per cell (Sect. 4.2).
+__global__ void fofr_prep64(const double* __restrict__ u, const double* __restrict__ eta, double* __restrict__ b,
+                            double* __restrict__ S, size_t n, Coef c, const double* __restrict__ tab);
+
+// f(R), second pass: flux form of Eq. (disc_non_canonical) with face b = (b_c + b_nb)/2:
+//   sum_f b_f (u_nb - u) = [ b_c (sum u_nb - 6 u) + sum b_nb u_nb - u sum b_nb ] / 2
+__global__ void __launch_bounds__(kNormThreads) outer_residual_fofr(int lg, double ih2, const double* __restrict__ u,
+                                                                    const double* __restrict__ b,
+                                                                    const double* __restrict__ S,
+                                                                    float* __restrict__ r32, float* __restrict__ B32,
+                                                                    double* __restrict__ part);
 
 // ---------------------------------------------------------------------------
 // Drivers
@@ -352,27 +425,41 @@ isis_status solve_field(const SolveArgs& A) {
       s = cy.vcycle(0);
       if (s != ISIS_OK) { out = s; break; }
       if (M == POI) {
-        s = remove_mean<T>(ws, phi, n, st);
+        s = remove_mean<T>(ws, cy.L[0].x, n, st);
         if (s != ISIS_OK) { out = s; break; }
       }
       s = cy.fine_rms(&res);
       loc.cycles = cyc + 1;
       loc.hist[cyc] = res;
+      loc.nhist = cyc + 1;
       loc.res_final = res;
       if (s != ISIS_OK) { out = s; break; }
       if (!std::isfinite(res)) { out = ISIS_ENAN; break; }
       if (res <= target) { out = ISIS_OK; break; }
     }
   }
+  if (cy.L[0].x != phi) ISIS_CK(cudaMemcpyAsync(phi, cy.L[0].x, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
   if (A.info) *A.info = loc;
   return out;
 }
 
-// FP64 defect correction with FP32 correction cycles (DELTA form).
+// Relative residual (of the reference) below which the FP32 field-form
+// cycles hand over to the FP64 defect correction, and the per-cycle
+// reduction above which they are taken to have reached FP32 rounding.
+constexpr double kSwitchRel = 1e-4;
+constexpr double kStallRatio = 0.5;
+
+// FP32 cycles + FP64 defect correction.
+//  Phase 1: FAS V-cycles on the field itself in FP32 (psi = fp32(phi)) until
+//           the FP32-evaluated residual is below kSwitchRel * ref or stalls.
+//  Phase 2: outer loop: r = -L64(phi) in FP64; FP32 FAS V-cycles on the
+//           correction e of L(B + e) - L(B) = r, B = fp32(phi) (DELTA form);
+//           phi += e in FP64; until the FP64 residual is <= tol * ref.
 template <Model M>
 isis_status solve_refine(const SolveArgs& A) {
   Workspace* ws = get_workspace(A.N, sizeof(float), A.ncoarse);
   if (!ws) return ISIS_ENOMEM;
+  if (M == FOFR && !ensure_fofr64(ws)) return ISIS_ENOMEM;
   cudaStream_t st = A.st;
   const size_t n = (size_t)A.N * A.N * A.N;
   const double* eta64 = (const double*)A.eta;
@@ -381,7 +468,7 @@ isis_status solve_refine(const SolveArgs& A) {
   isis_solve_info loc;
   info_reset(&loc);
 
-  // FP32 buffers of the finest level: x = e, sig = r, eta, B, w
+  // FP32 buffers of the finest level: x = e, sig = r, eta, B (= psi in phase 1), w
   float* e0 = (float*)ws->x[0];
   float* r0 = (float*)ws->sig[0];
   float* eta0 = (float*)ws->eta[0];
@@ -400,19 +487,58 @@ isis_status solve_refine(const SolveArgs& A) {
   s = apply_init<M, double>(A, c, phi64, eta64, n);
   if (s != ISIS_OK) return s;
 
-  if (M != POI) {
-    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (convert_k<double, float><<<nblk(n, 256), 256, 0, st>>>(eta64, eta0, n)));
-    for (int l = 1; l < ws->nlev; ++l) {
-      int lgc = ilog2(A.N >> l);
-      size_t ncl = (size_t)1 << (3 * lgc);
-      ISIS_LAUNCH(KK_SETUP, 36.0 * ncl, st,
-                  (restrict_mean<float, float><<<nblk(ncl, 256), 256, 0, st>>>((const float*)ws->eta[l - 1],
-                                                                              (float*)ws->eta[l], lgc)));
-    }
+  ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (convert_k<double, float><<<nblk(n, 256), 256, 0, st>>>(eta64, eta0, n)));
+  for (int l = 1; l < ws->nlev; ++l) {
+    int lgc = ilog2(A.N >> l);
+    size_t ncl = (size_t)1 << (3 * lgc);
+    ISIS_LAUNCH(KK_SETUP, 36.0 * ncl, st,
+                (restrict_mean<float, float><<<nblk(ncl, 256), 256, 0, st>>>((const float*)ws->eta[l - 1],
+                                                                            (float*)ws->eta[l], lgc)));
   }
   ISIS_CK(cudaMemsetAsync(ws->iflags, 0, 2 * sizeof(int), st));
+  SolveArgs A2 = A;
+  A2.coef = c;
+  int nh = 0;  // history entries
 
-  // FP64 view of the finest level for the outer residual
+  // ---- phase 1: FP32 field-form cycles ----
+  ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (convert_k<double, float><<<nblk(n, 256), 256, 0, st>>>(phi64, B0, n)));
+  {
+    Cycler<M, FIELD, float> cy;
+    cy.setup(ws, A2, B0, eta0, nullptr);
+    double res;
+    s = cy.fine_rms(&res);
+    if (s != ISIS_OK) return s;
+    loc.res0 = res;
+    if (!(ref > 0.0)) ref = res;
+    loc.res_ref = ref;
+    double prev = res;
+    double handover = std::fmax(A.tol, kSwitchRel) * ref;
+    while (res > handover && loc.cycles < A.max_cycles && std::isfinite(res)) {
+      s = cy.vcycle(0);
+      if (s != ISIS_OK) return s;
+      s = cy.fine_rms(&res);
+      loc.cycles += 1;
+      if (nh < 128) loc.hist[nh++] = res;
+      loc.nhist = nh;
+      if (s != ISIS_OK) { if (A.info) *A.info = loc; return s; }
+      if (!(res <= kStallRatio * prev)) break;
+      prev = res;
+    }
+    if (!std::isfinite(res)) {
+      loc.res_final = res;
+      if (A.info) *A.info = loc;
+      return ISIS_ENAN;
+    }
+    const float* psi = cy.L[0].x;
+    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (convert_k<float, double><<<nblk(n, 256), 256, 0, st>>>(psi, phi64, n)));
+    // Poisson gauge: the residual does not see the mean, so it is removed once per phase
+    if (M == POI) {
+      s = remove_mean<double>(ws, phi64, n, st);
+      if (s != ISIS_OK) return s;
+    }
+  }
+
+  // ---- phase 2: FP64 defect correction around FP32 correction cycles ----
   LevelView<double> F64;
   F64.N = A.N;
   F64.lg = ilog2(A.N);
@@ -424,31 +550,31 @@ isis_status solve_refine(const SolveArgs& A) {
   F64.w = nullptr;
 
   Cycler<M, DELTA, float> cy;
-  SolveArgs A2 = A;
-  A2.coef = c;
   cy.setup(ws, A2, e0, eta0, r0);
 
   double* h = (double*)ws->host;
   int* hi = (int*)(h + 4);
   isis_status out = ISIS_ENOCONV;
-  double target = 0.0;
+  const double target = A.tol * ref;
   for (int outer = 0;; ++outer) {
     // r = -L64(phi64), B = fp32(phi64), RMS of r
-    ISIS_LAUNCH(KK_OUTER_RESID, 24.0 * n, st,
-                (outer_residual<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64, c, r0, B0, ws->part)));
+    if (M == FOFR) {
+      ISIS_LAUNCH(KK_OUTER_RESID, 32.0 * n, st,
+                  (fofr_prep64<<<nblk(n, 256), 256, 0, st>>>(phi64, eta64, ws->b64, ws->s64, n, c, ws->exptab)));
+      ISIS_LAUNCH(KK_OUTER_RESID, 32.0 * n, st,
+                  (outer_residual_fofr<<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, F64.ih2, phi64, ws->b64,
+                                                                              ws->s64, r0, B0, ws->part)));
+    } else {
+      ISIS_LAUNCH(KK_OUTER_RESID, 24.0 * n, st,
+                  (outer_residual<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64, c, r0, B0, ws->part)));
+    }
     ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
     ISIS_CK(cudaMemcpyAsync(h, ws->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
     ISIS_CK(cudaMemcpyAsync(hi, ws->iflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     ISIS_CK(cudaStreamSynchronize(st));
     double res = std::sqrt(h[0] / (double)n);
-    if (outer == 0) {
-      loc.res0 = res;
-      if (!(ref > 0.0)) ref = res;
-      loc.res_ref = ref;
-      target = A.tol * ref;
-    } else {
-      loc.hist[outer - 1] = res;
-    }
+    if (outer > 0 && nh < 128) loc.hist[nh++] = res;
+    loc.nhist = nh;
     loc.res_final = res;
     loc.outer = outer;
     if (hi[0] != 0) { out = ISIS_ENAN; break; }
@@ -471,7 +597,7 @@ isis_status solve_refine(const SolveArgs& A) {
                     (exp_k<float><<<nblk(nl, 256), 256, 0, st>>>((const float*)ws->B[l], (float*)ws->w[l], nl)));
       }
     }
-    ISIS_CK(cudaMemsetAsync(e0, 0, n * sizeof(float), st));
+    ISIS_CK(cudaMemsetAsync(cy.L[0].x, 0, n * sizeof(float), st));
     int k = A.inner;
     if (loc.cycles + k > A.max_cycles) k = A.max_cycles - loc.cycles;
     for (int it = 0; it < k; ++it) {
@@ -479,11 +605,12 @@ isis_status solve_refine(const SolveArgs& A) {
       if (s != ISIS_OK) return s;
     }
     loc.cycles += k;
-    ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_phi64<<<nblk(n, 256), 256, 0, st>>>(phi64, e0, n)));
-    if (M == POI) {
-      s = remove_mean<double>(ws, phi64, n, st);
-      if (s != ISIS_OK) return s;
-    }
+    const float* ecur = cy.L[0].x;
+    ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_phi64<<<nblk(n, 256), 256, 0, st>>>(phi64, ecur, n)));
+  }
+  if (M == POI) {
+    s = remove_mean<double>(ws, phi64, n, st);
+    if (s != ISIS_OK) return s;
   }
   if (A.info) *A.info = loc;
   return out;

@@ -52,7 +52,7 @@ class isis_prof_entry(ctypes.Structure):
 
 
 class isis_solve_info(ctypes.Structure):
-    _fields_ = [("cycles", ctypes.c_int), ("outer", ctypes.c_int), ("res0", ctypes.c_double),
+    _fields_ = [("cycles", ctypes.c_int), ("outer", ctypes.c_int), ("nhist", ctypes.c_int), ("res0", ctypes.c_double),
                 ("res_ref", ctypes.c_double), ("res_final", ctypes.c_double), ("hist", ctypes.c_double * 128)]
 
 
@@ -226,7 +226,7 @@ def isis_cic_deposit(grid: Grid, x: torch.Tensor, y: torch.Tensor, z: torch.Tens
 
 
 def _info(ci: isis_solve_info, st: int, prec: int) -> Info:
-    nh = ci.outer if prec == ISIS_F32_REFINE64 else ci.cycles
+    nh = ci.nhist
     return Info(st, ci.cycles, ci.outer, ci.res0, ci.res_ref, ci.res_final, [ci.hist[i] for i in range(nh)])
 
 
