@@ -40,7 +40,9 @@ def parse():
     ap.add_argument("--N", type=int, default=512)
     ap.add_argument("--box", type=float, default=256.0)
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--inner", type=int, default=3)
+    ap.add_argument("--inner-poisson", type=int, default=4, help="FP32 cycles per FP64 outer iteration")
+    ap.add_argument("--inner-sym", type=int, default=3)
+    ap.add_argument("--inner-fofr", type=int, default=5)
     ap.add_argument("--ncoarse", type=int, default=2, help="coarsest grid (dense Newton): 2 or 4")
     ap.add_argument("--sample-N", type=int, default=128, help="grid of the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -55,7 +57,7 @@ def workload(args):
             "N": args.N, "box_mpc_h": args.box, "particles": args.N ** 3, "tol": args.tol,
             "symmetron": {"a": 1.0, "a_ssb": 0.5, "lambda0": 1.0, "beta": 1.0},
             "fofr": {"n": 1, "fR0_abs": 1e-5}, "cycle": f"V(2,2), coarsest {args.ncoarse}^3 dense Newton",
-            "inner_cycles": args.inner,
+            "inner_cycles": {"poisson": args.inner_poisson, "symmetron": args.inner_sym, "fofr": args.inner_fofr},
             "l2": "inputs larger than L2 (each 512^3 field is 0.5-1 GB), no flush",
             "parallelism": "replicas (one independent problem per GPU)"}
 
@@ -214,8 +216,10 @@ def main():
     chi = torch.empty((N,) * 3, **f64)
     u = torch.empty((N,) * 3, **f64)
     g = [torch.empty(npart, device=dev, dtype=torch.float32) for _ in range(6)]
-    opts_bg = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=args.inner, init=isis.ISIS_INIT_BACKGROUND,
-                        n_coarsest=args.ncoarse)
+    def opts(inner):
+        return isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=inner, init=isis.ISIS_INIT_BACKGROUND,
+                         n_coarsest=args.ncoarse)
+    o_poi, o_sym, o_fr = opts(args.inner_poisson), opts(args.inner_sym), opts(args.inner_fofr)
     stream = torch.cuda.current_stream()
     infos = {}
 
@@ -225,14 +229,14 @@ def main():
         isis.isis_cic_deposit(grid, xx, yy, zz, eta)
         if ev:
             ev[1].record(stream)
-        infos["poisson"] = isis.isis_poisson_solve(grid, a, eta, Phi, tol=args.tol, opts=opts_bg)
+        infos["poisson"] = isis.isis_poisson_solve(grid, a, eta, Phi, tol=args.tol, opts=o_poi)
         if ev:
             ev[2].record(stream)
         infos["symmetron"] = isis.isis_scalar_solve(isis.ISIS_SYMMETRON, psym, grid, a, eta, chi, tol=args.tol,
-                                                    opts=opts_bg)
+                                                    opts=o_sym)
         if ev:
             ev[3].record(stream)
-        infos["fofr"] = isis.isis_scalar_solve(isis.ISIS_FOFR_HS, pfr, grid, a, eta, u, tol=args.tol, opts=opts_bg)
+        infos["fofr"] = isis.isis_scalar_solve(isis.ISIS_FOFR_HS, pfr, grid, a, eta, u, tol=args.tol, opts=o_fr)
         if ev:
             ev[4].record(stream)
         isis.isis_fifth_force(isis.ISIS_SYMMETRON, psym, grid, a, Phi, chi, xx, yy, zz, out=g[0:3])

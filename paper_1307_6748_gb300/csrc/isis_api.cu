@@ -52,12 +52,9 @@ Workspace* get_workspace(int N, int esize, int ncoarse) {
       if (!(l == 0 && esize != 4) && !p) ok = false;
       a->push_back(p);
     }
-    void* p = nullptr;
-    if (esize == 4 && (N >> l) >= kStreamMinN) {
-      p = alloc(nl * esize);
-      if (!p) ok = false;
-    }
-    w->xalt.push_back(p);
+    void* pa = alloc(nl * esize);
+    if (!pa) ok = false;
+    w->aux.push_back(pa);
   }
   if (ok) {
     w->part = (double*)alloc(kNormBlocks * sizeof(double));

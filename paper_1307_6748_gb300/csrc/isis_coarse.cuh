@@ -25,16 +25,17 @@ __global__ void __launch_bounds__(kCoarseMax) coarse_newton(LevelView<T> L, Coef
   __shared__ int done, bad;
   const int n = 1 << (3 * L.lg), N = L.N, lg = L.lg, r = threadIdx.x;
   const double ih2 = (double)L.ih2;
+  int i = r >> (2 * lg), j = (r >> lg) & (N - 1), k = r & (N - 1);
+  const size_t gr = r < n ? lidx<T>(lg, i, j, k) : 0;  // storage index of unknown r
   if (r < n) {
-    xs[r] = (double)L.x[r];
-    etas[r] = (M == POI && FM == DELTA) ? 0.0 : (double)L.eta[r];
-    sigs[r] = L.sig ? (double)L.sig[r] : 0.0;
-    Bs[r] = (FM == DELTA && M != POI) ? (double)L.B[r] : 0.0;
-    ws[r] = (FM == DELTA && M == FOFR) ? (double)L.w[r] : 0.0;
+    xs[r] = (double)L.x[gr];
+    etas[r] = (M == POI && FM == DELTA) ? 0.0 : (double)L.eta[gr];
+    sigs[r] = L.sig ? (double)L.sig[gr] : 0.0;
+    Bs[r] = (FM == DELTA && M != POI) ? (double)L.B[gr] : 0.0;
+    ws[r] = (FM == DELTA && M == FOFR) ? (double)L.w[gr] : 0.0;
   }
   if (r == 0) { done = 0; bad = 0; }
   __syncthreads();
-  int i = r >> (2 * lg), j = (r >> lg) & (N - 1), k = r & (N - 1);
   int nb[6];
   if (r < n) {
     nb[0] = (((i + 1) & (N - 1)) << (2 * lg)) | (j << lg) | k;
@@ -52,6 +53,9 @@ __global__ void __launch_bounds__(kCoarseMax) coarse_newton(LevelView<T> L, Coef
       q.x = xs[r]; q.eta = etas[r]; q.sig = sigs[r]; q.B = Bs[r]; q.w = ws[r];
 #pragma unroll
       for (int d = 0; d < 6; ++d) { q.xn[d] = xs[nb[d]]; q.Bn[d] = Bs[nb[d]]; q.wn[d] = ws[nb[d]]; }
+      q.a = aux_of<M, FM, double>(q.x, q.w);
+#pragma unroll
+      for (int d = 0; d < 6; ++d) q.an[d] = aux_of<M, FM, double>(q.xn[d], q.wn[d]);
       double F, dF;
       eval_cell<M, FM, double>(c, ih2, q, F, dF);
       double shift = (M == POI) ? 6.0 * ih2 / (double)n : 0.0;
@@ -120,7 +124,10 @@ __global__ void __launch_bounds__(kCoarseMax) coarse_newton(LevelView<T> L, Coef
     __syncthreads();
     if (done || bad) { ++it; break; }
   }
-  if (r < n) L.x[r] = (T)xs[r];
+  if (r < n) {
+    L.x[gr] = (T)xs[r];
+    if constexpr (M == FOFR) L.aux[gr] = aux_of<M, FM, T>((T)xs[r], (T)ws[r]);
+  }
   if (r == 0) {
     if (bad) atomicOr(flags, bad);
     atomicMax(steps_max, it);

@@ -24,9 +24,11 @@ __global__ void __launch_bounds__(kNormThreads) reduce_final(const double* __res
 }  // namespace isis
 
 namespace isis {
-__global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, size_t n) {
+__global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, int lg) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) phi[t] += (double)e[t];
+  if (t >= ((size_t)1 << (3 * lg))) return;
+  const int m = (1 << lg) - 1;
+  phi[t] += (double)e[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
 }
 }  // namespace isis
 
@@ -64,8 +66,9 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr(int lg, doub
     }
     double flux = 0.5 * fma(bc, fma(-6.0, uc, su), fma(-uc, sb, sbu));
     double F = fma(flux, ih2, -S[t]);
-    r32[t] = (float)(-F);
-    B32[t] = (float)uc;
+    const size_t o = lidx<float>(lg, i, j, k);
+    r32[o] = (float)(-F);
+    B32[o] = (float)uc;
     acc = fma(F, F, acc);
   }
   block_sum_store<double>(acc, part);

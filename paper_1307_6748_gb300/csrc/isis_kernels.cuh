@@ -10,6 +10,13 @@
 //
 // R = mean of the 8 children; P = cell-centred trilinear interpolation
 // (weights 3/4 and 1/4 per axis).  The paper leaves both unspecified.
+//
+// Memory layout.  FP64 grids (the caller's arrays, the FP64 solver) are
+// row-major.  FP32 grids (the workspace of the FP32 cycles) are stored
+// red/black split: red cells ((i+j+k) even) first, then black, each half in
+// row-major order of the cells of that colour, i.e. cell g = (i N + j) N + k
+// sits at colour * N^3/2 + g/2.  A one-colour half-sweep then reads the
+// other colour's half and its own half contiguously, with no wasted sectors.
 #pragma once
 #include "isis_model.cuh"
 
@@ -27,19 +34,104 @@ struct LevelView {
   const T* sig;    // FAS source, nullptr means 0
   const T* B;      // DELTA form base field
   const T* w;      // e^B (f(R) DELTA form)
+  T* aux;          // f(R): e^x (FIELD) or e^B expm1(x) (DELTA), kept in step with x
 };
 
 __device__ __forceinline__ size_t cidx(int lg, int i, int j, int k) {
   return ((((size_t)i << lg) + (size_t)j) << lg) + (size_t)k;
 }
 
-// Gather one cell and its neighbours from global memory (periodic wrap).
+// Storage index of cell (i,j,k) in a grid of element type T (see above).
+// FP32 grids have N <= 1024, so their indices fit in 32 bits.
+template <class T>
+__device__ __forceinline__ size_t lidx(int lg, int i, int j, int k) {
+  if constexpr (sizeof(T) == 4) {
+    const unsigned g = (((unsigned)i << lg | (unsigned)j) << lg) | (unsigned)k;
+    return (size_t)((((unsigned)(i + j + k) & 1u) << (3 * lg - 1)) | (g >> 1));
+  } else {
+    return cidx(lg, i, j, k);
+  }
+}
+
+// Storage indices of cell (i,j,k) and of its six neighbours (i+1, i-1, j+1,
+// j-1, k+1, k-1) with periodic wrap.  For the red/black FP32 layout the
+// neighbours all lie in the other colour's half: 32-bit arithmetic on the
+// row index and k/2.
+template <class T>
+__device__ __forceinline__ size_t stencil_idx(int lg, int i, int j, int k, size_t* nb) {
+  const int m = (1 << lg) - 1;
+  if constexpr (sizeof(T) == 4) {
+    const unsigned hN = 1u << (lg - 1), half = 1u << (3 * lg - 1);
+    const unsigned ui = (unsigned)i, uj = (unsigned)j, uk = (unsigned)k, um = (unsigned)m;
+    const unsigned col = (ui + uj + uk) & 1u, oth = col ? 0u : half;
+    const unsigned row = (ui << lg) | uj, k2 = uk >> 1;
+    nb[0] = oth + ((((ui + 1) & um) << lg | uj) << (lg - 1)) + k2;
+    nb[1] = oth + ((((ui - 1) & um) << lg | uj) << (lg - 1)) + k2;
+    nb[2] = oth + (((ui << lg) | ((uj + 1) & um)) << (lg - 1)) + k2;
+    nb[3] = oth + (((ui << lg) | ((uj - 1) & um)) << (lg - 1)) + k2;
+    nb[4] = oth + (row << (lg - 1)) + (((uk + 1) & um) >> 1);
+    nb[5] = oth + (row << (lg - 1)) + (((uk - 1) & um) >> 1);
+    (void)hN;
+    return (col ? half : 0u) + (row << (lg - 1)) + k2;
+  } else {
+    nb[0] = cidx(lg, (i + 1) & m, j, k);
+    nb[1] = cidx(lg, (i - 1) & m, j, k);
+    nb[2] = cidx(lg, i, (j + 1) & m, k);
+    nb[3] = cidx(lg, i, (j - 1) & m, k);
+    nb[4] = cidx(lg, i, j, (k + 1) & m);
+    nb[5] = cidx(lg, i, j, (k - 1) & m);
+    return cidx(lg, i, j, k);
+  }
+}
+
+// Cell (i,j,k) stored at position t of a grid of type T (inverse of lidx).
+template <class T>
+__device__ __forceinline__ void cell_of(size_t t, int lg, int& i, int& j, int& k) {
+  const int m = (1 << lg) - 1;
+  if constexpr (sizeof(T) == 4) {
+    const unsigned half = 1u << (3 * lg - 1), u = (unsigned)t;
+    const unsigned col = u >= half ? 1u : 0u, l = u - col * half;
+    const unsigned k2 = l & ((1u << (lg - 1)) - 1), row = l >> (lg - 1);
+    j = (int)(row & (unsigned)m);
+    i = (int)(row >> lg);
+    k = (int)(2 * k2 + (((unsigned)i + (unsigned)j + col) & 1u));
+  } else {
+    k = (int)(t & m);
+    j = (int)((t >> lg) & m);
+    i = (int)(t >> (2 * lg));
+  }
+}
+
+// Neighbours of the cell stored at position t (storage order), for kernels
+// whose threads run over a grid in storage order.  Red/black FP32: cell t of
+// colour col sits in row r = i N + j at place k2 of that colour; its i and j
+// neighbours are at the same place in rows r +- N, r +- 1 of the other
+// colour, its k neighbours at places k2 + par, k2 + par - 1 of its own row.
+template <class T>
+__device__ __forceinline__ void stencil_of_storage(int lg, size_t t, size_t* nb) {
+  if constexpr (sizeof(T) == 4) {
+    const unsigned half = 1u << (3 * lg - 1), hN = 1u << (lg - 1), m = (1u << lg) - 1;
+    const unsigned u = (unsigned)t, col = u >= half ? 1u : 0u, l = u - (col ? half : 0u);
+    const unsigned k2 = l & (hN - 1), row = l >> (lg - 1), j = row & m, i = row >> lg;
+    const unsigned par = (i + j + col) & 1u, oth = col ? 0u : half;
+    nb[0] = oth + ((((i + 1) & m) << lg | j) << (lg - 1)) + k2;
+    nb[1] = oth + ((((i - 1) & m) << lg | j) << (lg - 1)) + k2;
+    nb[2] = oth + (((i << lg) | ((j + 1) & m)) << (lg - 1)) + k2;
+    nb[3] = oth + (((i << lg) | ((j - 1) & m)) << (lg - 1)) + k2;
+    nb[4] = oth + (row << (lg - 1)) + ((k2 + par) & (hN - 1));
+    nb[5] = oth + (row << (lg - 1)) + ((k2 + par - 1) & (hN - 1));
+  } else {
+    int i, j, k;
+    cell_of<T>(t, lg, i, j, k);
+    stencil_idx<T>(lg, i, j, k, nb);
+  }
+}
+
+// Gather the cell stored at t and its neighbours.
 template <Model M, Form FM, class T>
-__device__ __forceinline__ Cell<T> gather(const LevelView<T>& L, int i, int j, int k) {
-  const int m = L.N - 1;
-  size_t c = cidx(L.lg, i, j, k);
-  size_t nb[6] = {cidx(L.lg, (i + 1) & m, j, k), cidx(L.lg, (i - 1) & m, j, k), cidx(L.lg, i, (j + 1) & m, k),
-                  cidx(L.lg, i, (j - 1) & m, k), cidx(L.lg, i, j, (k + 1) & m), cidx(L.lg, i, j, (k - 1) & m)};
+__device__ __forceinline__ Cell<T> gather_at(const LevelView<T>& L, size_t c) {
+  size_t nb[6];
+  stencil_of_storage<T>(L.lg, c, nb);
   Cell<T> q;
   q.x = L.x[c];
 #pragma unroll
@@ -52,12 +144,43 @@ __device__ __forceinline__ Cell<T> gather(const LevelView<T>& L, int i, int j, i
 #pragma unroll
     for (int d = 0; d < 6; ++d) { q.Bn[d] = L.B[nb[d]]; q.wn[d] = L.w[nb[d]]; }
   }
+  if constexpr (M == FOFR) {
+    q.a = L.aux[c];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) q.an[d] = L.aux[nb[d]];
+  }
+  return q;
+}
+
+// Gather one cell and its neighbours from global memory (periodic wrap).
+template <Model M, Form FM, class T>
+__device__ __forceinline__ Cell<T> gather(const LevelView<T>& L, int i, int j, int k) {
+  size_t nb[6];
+  const size_t c = stencil_idx<T>(L.lg, i, j, k, nb);
+  Cell<T> q;
+  q.x = L.x[c];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) q.xn[d] = L.x[nb[d]];
+  q.sig = L.sig ? L.sig[c] : T(0);
+  if constexpr (!(M == POI && FM == DELTA)) q.eta = L.eta[c]; else q.eta = T(0);
+  if constexpr (FM == DELTA && M != POI) q.B = L.B[c]; else q.B = T(0);
+  if constexpr (FM == DELTA && M == FOFR) {
+    q.w = L.w[c];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) { q.Bn[d] = L.B[nb[d]]; q.wn[d] = L.w[nb[d]]; }
+  }
+  if constexpr (M == FOFR) {
+    q.a = L.aux[c];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) q.an[d] = L.aux[nb[d]];
+  }
   return q;
 }
 
 // One colour (0 = red: (i+j+k) even) of a Newton-Gauss-Seidel sweep, in place.
-// Thread layout: one thread per pair of cells (k = 2p, 2p+1); it updates the
-// member of the pair that has the requested colour.
+// Thread t updates the cell of the requested colour in the pair (k = 2p, 2p+1)
+// of row t / (N/2); for FP32 grids t is also that cell's place in its colour
+// half, so a warp reads and writes 32 consecutive values of each array.
 template <Model M, Form FM, class T>
 __global__ void smooth_color(LevelView<T> L, Coef c, int color) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -70,34 +193,289 @@ __global__ void smooth_color(LevelView<T> L, Coef c, int color) {
   Cell<T> q = gather<M, FM, T>(L, i, j, k);
   T F, dF;
   eval_cell<M, FM, T>(c, L.ih2, q, F, dF);
-  L.x[cidx(L.lg, i, j, k)] = q.x - F / dF;
+  // FP32 cycles drive a correction: a 2-ulp quotient is ample there
+  T xn;
+  if constexpr (sizeof(T) == 4) xn = q.x - __fdividef(F, dF);
+  else xn = q.x - F / dF;
+  const size_t o = lidx<T>(L.lg, i, j, k);
+  L.x[o] = xn;
+  if constexpr (M == FOFR) L.aux[o] = aux_of<M, FM, T>(xn, q.w);
 }
 
-// One thread per coarse cell: residuals of its 8 children, their means.
-template <Model M, Form FM, class T>
-__global__ void resid_restrict(LevelView<T> F, Coef c, T* __restrict__ xc, T* __restrict__ x0c,
-                               T* __restrict__ sigc) {
-  int lgc = F.lg - 1;
+// One colour of a Newton-Gauss-Seidel sweep on a red/black split FP32 grid.
+// Thread t owns cell t of the colour's half: row r = t / (N/2) = i N + j,
+// k = 2 (t mod N/2) + ((i + j + colour) mod 2).  Its i and j neighbours are
+// cells of the other colour in rows r +- N and r +- 1 at the same place in
+// the row; its k neighbours are places k2 + par and k2 + par - 1 of its own
+// row in the other colour's half (par = parity of k), all in 32-bit
+// arithmetic.
+template <Model M, Form FM>
+__global__ void __launch_bounds__(256) smooth_rb(LevelView<float> L, Coef c, int color) {
+  const int lg = L.lg;
+  const unsigned half = 1u << (3 * lg - 1), hN = (unsigned)L.N >> 1, m = (unsigned)L.N - 1;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= half) return;
+  const unsigned k2 = t & (hN - 1), row = t >> (lg - 1), j = row & m, i = row >> lg;
+  const unsigned par = (i + j + (unsigned)color) & 1u;
+  const unsigned own = color ? half : 0u, oth = color ? 0u : half;
+  const unsigned rip = (((i + 1) & m) << lg | j) * hN + k2, rim = (((i - 1) & m) << lg | j) * hN + k2;
+  const unsigned rjp = ((i << lg) | ((j + 1) & m)) * hN + k2, rjm = ((i << lg) | ((j - 1) & m)) * hN + k2;
+  const unsigned rkp = row * hN + ((k2 + par) & (hN - 1)), rkm = row * hN + ((k2 + par - 1) & (hN - 1));
+  const unsigned nb[6] = {oth + rip, oth + rim, oth + rjp, oth + rjm, oth + rkp, oth + rkm};
+  const unsigned o = own + t;
+  Cell<float> q;
+  q.x = L.x[o];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) q.xn[d] = L.x[nb[d]];
+  q.sig = L.sig ? L.sig[o] : 0.f;
+  if constexpr (!(M == POI && FM == DELTA)) q.eta = L.eta[o]; else q.eta = 0.f;
+  if constexpr (FM == DELTA && M != POI) q.B = L.B[o]; else q.B = 0.f;
+  if constexpr (FM == DELTA && M == FOFR) {
+    q.w = L.w[o];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) { q.Bn[d] = L.B[nb[d]]; q.wn[d] = L.w[nb[d]]; }
+  }
+  if constexpr (M == FOFR) {
+    q.a = L.aux[o];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) q.an[d] = L.aux[nb[d]];
+  }
+  float F, dF;
+  eval_cell<M, FM, float>(c, L.ih2, q, F, dF);
+  // FP32 cycles drive a correction: a 2-ulp quotient is ample there
+  const float xn = q.x - __fdividef(F, dF);
+  L.x[o] = xn;
+  if constexpr (M == FOFR) L.aux[o] = aux_of<M, FM, float>(xn, q.w);
+}
+
+// Storage positions of the cells k = 2K-1, 2K, 2K+1, 2K+2 of row (i, j).
+template <class T>
+__device__ __forceinline__ void row4(int lg, int i, int j, int K, size_t* p) {
+  if constexpr (sizeof(T) == 4) {
+    const unsigned half = 1u << (3 * lg - 1), hm = (1u << (lg - 1)) - 1;
+    const unsigned rp = (((unsigned)i << lg) | (unsigned)j) << (lg - 1);
+    const unsigned ev = ((unsigned)(i + j) & 1u) ? half : 0u, od = ev ? 0u : half;  // colour halves of even / odd k
+    p[0] = od + rp + (((unsigned)K - 1u) & hm);
+    p[1] = ev + rp + (unsigned)K;
+    p[2] = od + rp + (unsigned)K;
+    p[3] = ev + rp + (((unsigned)K + 1u) & hm);
+  } else {
+    const int m = (1 << lg) - 1;
+    const size_t rb = (((size_t)i << lg) + (size_t)j) << lg;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) p[d] = rb + (size_t)((2 * K - 1 + d) & m);
+  }
+}
+
+// Same half-sweep, two cells of the colour per thread (places k2a, k2a + 1
+// of a row, float2 loads and stores; N >= 4).  The k neighbours of the pair
+// are the other colour's places k2a + par - 1 .. k2a + par + 1.
+template <Model M, Form FM>
+__device__ __forceinline__ unsigned rb2_gather(const LevelView<float>& L, int color, unsigned t, Cell<float>& q0,
+                                               Cell<float>& q1) {
+  const int lg = L.lg;
+  const unsigned half = 1u << (3 * lg - 1), hN = (unsigned)L.N >> 1, m = (unsigned)L.N - 1;
+  const unsigned k2a = (t & ((hN >> 1) - 1)) << 1, row = t >> (lg - 2), j = row & m, i = row >> lg;
+  const unsigned par = (i + j + (unsigned)color) & 1u;
+  const unsigned own = color ? half : 0u, oth = color ? 0u : half;
+  const unsigned o = own + row * hN + k2a;
+  const unsigned pr[4] = {oth + ((((i + 1) & m) << lg) | j) * hN + k2a, oth + ((((i - 1) & m) << lg) | j) * hN + k2a,
+                          oth + ((i << lg) | ((j + 1) & m)) * hN + k2a, oth + ((i << lg) | ((j - 1) & m)) * hN + k2a};
+  const unsigned rk = oth + row * hN;
+  const unsigned ks = par ? ((k2a + 2) & (hN - 1)) : ((k2a - 1) & (hN - 1));  // the scalar k neighbour place
+  // six neighbours of both cells from one array of the other colour
+  auto nbrs = [&](const float* __restrict__ a, float* n0, float* n1) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const float2 v = *reinterpret_cast<const float2*>(a + pr[d]);
+      n0[d] = v.x;
+      n1[d] = v.y;
+    }
+    const float2 v = *reinterpret_cast<const float2*>(a + rk + k2a);
+    const float sc = a[rk + ks];
+    if (par) { n0[4] = v.y; n0[5] = v.x; n1[4] = sc; n1[5] = v.y; }
+    else { n0[4] = v.x; n0[5] = sc; n1[4] = v.y; n1[5] = v.x; }
+  };
+  const float2 x2 = *reinterpret_cast<const float2*>(L.x + o);
+  q0.x = x2.x;
+  q1.x = x2.y;
+  nbrs(L.x, q0.xn, q1.xn);
+  if (L.sig) {
+    const float2 v = *reinterpret_cast<const float2*>(L.sig + o);
+    q0.sig = v.x;
+    q1.sig = v.y;
+  } else {
+    q0.sig = q1.sig = 0.f;
+  }
+  if constexpr (!(M == POI && FM == DELTA)) {
+    const float2 v = *reinterpret_cast<const float2*>(L.eta + o);
+    q0.eta = v.x;
+    q1.eta = v.y;
+  } else {
+    q0.eta = q1.eta = 0.f;
+  }
+  if constexpr (FM == DELTA && M != POI) {
+    const float2 v = *reinterpret_cast<const float2*>(L.B + o);
+    q0.B = v.x;
+    q1.B = v.y;
+  } else {
+    q0.B = q1.B = 0.f;
+  }
+  if constexpr (FM == DELTA && M == FOFR) {
+    const float2 v = *reinterpret_cast<const float2*>(L.w + o);
+    q0.w = v.x;
+    q1.w = v.y;
+    nbrs(L.B, q0.Bn, q1.Bn);
+    nbrs(L.w, q0.wn, q1.wn);
+  } else {
+    q0.w = q1.w = 0.f;
+  }
+  if constexpr (M == FOFR) {
+    const float2 v = *reinterpret_cast<const float2*>(L.aux + o);
+    q0.a = v.x;
+    q1.a = v.y;
+    nbrs(L.aux, q0.an, q1.an);
+  }
+  return o;
+}
+
+template <Model M, Form FM>
+__global__ void __launch_bounds__(256) smooth_rb2(LevelView<float> L, Coef c, int color) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (1u << (3 * L.lg - 2))) return;
+  Cell<float> q0, q1;
+  const unsigned o = rb2_gather<M, FM>(L, color, t, q0, q1);
+  float F0, dF0, F1, dF1;
+  eval_cell<M, FM, float>(c, L.ih2, q0, F0, dF0);
+  eval_cell<M, FM, float>(c, L.ih2, q1, F1, dF1);
+  // FP32 cycles drive a correction: a 2-ulp quotient is ample there
+  const float xn0 = q0.x - __fdividef(F0, dF0), xn1 = q1.x - __fdividef(F1, dF1);
+  *reinterpret_cast<float2*>(L.x + o) = make_float2(xn0, xn1);
+  if constexpr (M == FOFR)
+    *reinterpret_cast<float2*>(L.aux + o) =
+        make_float2(aux_of<M, FM, float>(xn0, q0.w), aux_of<M, FM, float>(xn1, q1.w));
+}
+
+// Residual r = Sigma - L(x) of every cell of a red/black FP32 grid into res
+// (two cells per thread; threads [0, N^3/4) red, then black).
+template <Model M, Form FM>
+__global__ void __launch_bounds__(256) resid_rb2(LevelView<float> L, Coef c, float* __restrict__ res) {
+  const unsigned q4 = 1u << (3 * L.lg - 2);
+  unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * q4) return;
+  const int color = t >= q4 ? 1 : 0;
+  t -= color ? q4 : 0u;
+  Cell<float> q0, q1;
+  const unsigned o = rb2_gather<M, FM>(L, color, t, q0, q1);
+  float F0, dF0, F1, dF1;
+  eval_cell<M, FM, float>(c, L.ih2, q0, F0, dF0);
+  eval_cell<M, FM, float>(c, L.ih2, q1, F1, dF1);
+  *reinterpret_cast<float2*>(res + o) = make_float2(-F0, -F1);  // Sigma is inside F
+}
+
+// x_H = R x, x0_H = x_H, Sigma_H = R res (res from resid_rb2), f(R) cache of x_H;
+// one thread per coarse cell in row-major order.
+template <Model M, Form FM>
+__global__ void restrict_xr(LevelView<float> F, const float* __restrict__ res, LevelView<float> C,
+                            float* __restrict__ x0c, float* __restrict__ sigc) {
+  const int lgc = F.lg - 1, lg = F.lg, m = F.N - 1, mc = (1 << lgc) - 1;
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ((size_t)1 << (3 * lgc))) return;
-  int Nc = 1 << lgc;
-  int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
-  T xs = 0, rs = 0;
+  const int K = (int)(t & mc), J = (int)((t >> lgc) & mc), I = (int)(t >> (2 * lgc));
+  float xs = 0.f, rs = 0.f;
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 2; ++b) {
+      size_t p[4];
+      row4<float>(lg, (2 * I + a) & m, (2 * J + b) & m, K, p);
+      xs += F.x[p[1]] + F.x[p[2]];
+      rs += res[p[1]] + res[p[2]];
+    }
+  const size_t to = lidx<float>(lgc, I, J, K);
+  const float xr = xs * 0.125f;
+  C.x[to] = xr;
+  x0c[to] = xr;
+  sigc[to] = rs * 0.125f;
+  if constexpr (M == FOFR) C.aux[to] = aux_of<M, FM, float>(xr, FM == DELTA ? C.w[to] : 0.f);
+}
+
+// One thread per coarse cell (I,J,K): residuals r = Sigma - L(x) of its 8
+// children, x_H = R x, x0_H = x_H, Sigma_H = R r.  The 32 fine cells the 8
+// stencils touch (block a, b, d = 0..3 at i = 2I-1+a, j = 2J-1+b, k = 2K-1+d,
+// without the 4 corner rows) are loaded once.
+template <Model M, Form FM, class T>
+__global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __restrict__ x0c, T* __restrict__ sigc) {
+  constexpr bool kAllB = (FM == DELTA && M == FOFR);   // neighbours' B, w, aux needed
+  constexpr bool kAux = (M == FOFR);
+  T* __restrict__ xc = C.x;
+  const int lgc = F.lg - 1, lg = F.lg, m = F.N - 1;
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ((size_t)1 << (3 * lgc))) return;
+  // threads in row-major coarse order: neighbouring threads touch neighbouring fine cells
+  const int mc = (1 << lgc) - 1;
+  const int K = (int)(t & mc), J = (int)((t >> lgc) & mc), I = (int)(t >> (2 * lgc));
+  const size_t to = lidx<T>(lgc, I, J, K);
+  T X[4][4][4], Ax[4][4][4], Bx[4][4][4], Wx[4][4][4];
+  size_t P[4][4][4];
 #pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        Cell<T> q = gather<M, FM, T>(F, 2 * I + a, 2 * J + b, 2 * K + d);
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const bool ea = (a == 0 || a == 3), eb = (b == 0 || b == 3);
+      if (ea && eb) continue;  // corner rows: not in any stencil
+      size_t p[4];
+      row4<T>(lg, (2 * I - 1 + a) & m, (2 * J - 1 + b) & m, K, p);
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        if ((ea || eb) && (d == 0 || d == 3)) continue;
+        P[a][b][d] = p[d];
+        X[a][b][d] = F.x[p[d]];
+        if constexpr (kAux) Ax[a][b][d] = F.aux[p[d]];
+        if constexpr (kAllB) { Bx[a][b][d] = F.B[p[d]]; Wx[a][b][d] = F.w[p[d]]; }
+      }
+    }
+  T xs = 0, rs = 0;
+#pragma unroll
+  for (int a = 1; a < 3; ++a)
+#pragma unroll
+    for (int b = 1; b < 3; ++b)
+#pragma unroll
+      for (int d = 1; d < 3; ++d) {
+        Cell<T> q;
+        const size_t pc = P[a][b][d];
+        q.x = X[a][b][d];
+        q.xn[0] = X[a + 1][b][d]; q.xn[1] = X[a - 1][b][d];
+        q.xn[2] = X[a][b + 1][d]; q.xn[3] = X[a][b - 1][d];
+        q.xn[4] = X[a][b][d + 1]; q.xn[5] = X[a][b][d - 1];
+        q.sig = F.sig ? F.sig[pc] : T(0);
+        if constexpr (!(M == POI && FM == DELTA)) q.eta = F.eta[pc]; else q.eta = T(0);
+        if constexpr (FM == DELTA && M != POI) q.B = F.B[pc]; else q.B = T(0);
+        if constexpr (kAllB) {
+          q.w = Wx[a][b][d];
+          q.Bn[0] = Bx[a + 1][b][d]; q.Bn[1] = Bx[a - 1][b][d]; q.Bn[2] = Bx[a][b + 1][d];
+          q.Bn[3] = Bx[a][b - 1][d]; q.Bn[4] = Bx[a][b][d + 1]; q.Bn[5] = Bx[a][b][d - 1];
+          q.wn[0] = Wx[a + 1][b][d]; q.wn[1] = Wx[a - 1][b][d]; q.wn[2] = Wx[a][b + 1][d];
+          q.wn[3] = Wx[a][b - 1][d]; q.wn[4] = Wx[a][b][d + 1]; q.wn[5] = Wx[a][b][d - 1];
+        }
+        if constexpr (kAux) {
+          q.a = Ax[a][b][d];
+          q.an[0] = Ax[a + 1][b][d]; q.an[1] = Ax[a - 1][b][d]; q.an[2] = Ax[a][b + 1][d];
+          q.an[3] = Ax[a][b - 1][d]; q.an[4] = Ax[a][b][d + 1]; q.an[5] = Ax[a][b][d - 1];
+        }
         T Fv, dF;
         eval_cell<M, FM, T>(c, F.ih2, q, Fv, dF);
         xs += q.x;
         rs -= Fv;  // r = Sigma - L(x)
       }
-  xc[t] = xs * T(0.125);
-  x0c[t] = xs * T(0.125);
-  sigc[t] = rs * T(0.125);
+  (void)Bx;
+  (void)Wx;
+  (void)Ax;
+  const T xr = xs * T(0.125);
+  xc[to] = xr;
+  x0c[to] = xr;
+  sigc[to] = rs * T(0.125);
+  if constexpr (M == FOFR) C.aux[to] = aux_of<M, FM, T>(xr, FM == DELTA ? C.w[to] : T(0));
 }
 
 // Sigma_H += L_H(x_H) (the FAS coarse source, Sect. 3.2).
@@ -105,38 +483,65 @@ template <Model M, Form FM, class T>
 __global__ void coarse_sigma_add(LevelView<T> L, Coef c, T* __restrict__ sig) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ((size_t)1 << (3 * L.lg))) return;
-  int k = (int)(t & (L.N - 1)), j = (int)((t >> L.lg) & (L.N - 1)), i = (int)(t >> (2 * L.lg));
   LevelView<T> L0 = L;
   L0.sig = nullptr;
-  Cell<T> q = gather<M, FM, T>(L0, i, j, k);
+  Cell<T> q = gather_at<M, FM, T>(L0, t);
   T F, dF;
   eval_cell<M, FM, T>(c, L.ih2, q, F, dF);
   sig[t] += F;
 }
 
-// x_h += P(x_H - x0_H), one thread per fine cell.
-template <class T>
-__global__ void prolong_correct(T* __restrict__ xf, const T* __restrict__ xc, const T* __restrict__ x0c, int lgc) {
-  int lgf = lgc + 1, Nc = 1 << lgc;
+// x_h += P(x_H - x0_H): one thread per coarse cell (I,J,K) writes its 8
+// children.  P is cell-centred trilinear, applied one axis at a time: the
+// child at offset 0 (1) along an axis takes 3/4 of the coarse value and 1/4
+// of the coarse neighbour below (above).  f(R): the cached exponential of
+// each child follows its new value.
+template <Model M, Form FM, class T>
+__global__ void prolong_correct(LevelView<T> Fv, const T* __restrict__ xc, const T* __restrict__ x0c, int lgc) {
+  T* __restrict__ xf = Fv.x;
+  const int lgf = lgc + 1, mc = (1 << lgc) - 1;
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ((size_t)1 << (3 * lgf))) return;
-  int Nf = 1 << lgf;
-  int k = (int)(t & (Nf - 1)), j = (int)((t >> lgf) & (Nf - 1)), i = (int)(t >> (2 * lgf));
-  int ci[2] = {i >> 1, ((i >> 1) + ((i & 1) ? 1 : -1)) & (Nc - 1)};
-  int cj[2] = {j >> 1, ((j >> 1) + ((j & 1) ? 1 : -1)) & (Nc - 1)};
-  int ck[2] = {k >> 1, ((k >> 1) + ((k & 1) ? 1 : -1)) & (Nc - 1)};
-  const T wt[2] = {T(0.75), T(0.25)};
-  T v = 0;
+  if (t >= ((size_t)1 << (3 * lgc))) return;
+  // threads in row-major coarse order: the 8 children of neighbouring threads are contiguous
+  const int K = (int)(t & mc), J = (int)((t >> lgc) & mc), I = (int)(t >> (2 * lgc));
+  T D[3][3][3];
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 3; ++b)
 #pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        size_t q = cidx(lgc, ci[a], cj[b], ck[d]);
-        v += wt[a] * wt[b] * wt[d] * (xc[q] - x0c[q]);
+      for (int d = 0; d < 3; ++d) {
+        const size_t q = lidx<T>(lgc, (I + a - 1) & mc, (J + b - 1) & mc, (K + d - 1) & mc);
+        D[a][b][d] = xc[q] - x0c[q];
       }
-  xf[t] += v;
+  const T w3 = T(0.75), w1 = T(0.25);
+  T Tk[3][3][2], Tj[3][2][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      Tk[a][b][0] = w3 * D[a][b][1] + w1 * D[a][b][0];
+      Tk[a][b][1] = w3 * D[a][b][1] + w1 * D[a][b][2];
+    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      Tj[a][0][d] = w3 * Tk[a][1][d] + w1 * Tk[a][0][d];
+      Tj[a][1][d] = w3 * Tk[a][1][d] + w1 * Tk[a][2][d];
+    }
+#pragma unroll
+  for (int ca = 0; ca < 2; ++ca)
+#pragma unroll
+    for (int cb = 0; cb < 2; ++cb)
+#pragma unroll
+      for (int cd = 0; cd < 2; ++cd) {
+        const T v = w3 * Tj[1][cb][cd] + w1 * Tj[ca ? 2 : 0][cb][cd];
+        const size_t o = lidx<T>(lgf, 2 * I + ca, 2 * J + cb, 2 * K + cd);
+        const T xn = xf[o] + v;
+        xf[o] = xn;
+        if constexpr (M == FOFR) Fv.aux[o] = aux_of<M, FM, T>(xn, FM == DELTA ? Fv.w[o] : T(0));
+      }
 }
 
 // coarse = mean of the 8 children of fine (plain restriction of a field).
@@ -144,16 +549,16 @@ template <class Tin, class Tout>
 __global__ void restrict_mean(const Tin* __restrict__ f, Tout* __restrict__ c, int lgc) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ((size_t)1 << (3 * lgc))) return;
-  int Nc = 1 << lgc, lgf = lgc + 1;
-  int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
+  int lgf = lgc + 1, mc = (1 << lgc) - 1;
+  const int K = (int)(t & mc), J = (int)((t >> lgc) & mc), I = (int)(t >> (2 * lgc));
   Tin s = 0;
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
-      for (int d = 0; d < 2; ++d) s += f[cidx(lgf, 2 * I + a, 2 * J + b, 2 * K + d)];
-  c[t] = (Tout)(s * Tin(0.125));
+      for (int d = 0; d < 2; ++d) s += f[lidx<Tin>(lgf, 2 * I + a, 2 * J + b, 2 * K + d)];
+  c[lidx<Tout>(lgc, I, J, K)] = (Tout)(s * Tin(0.125));
 }
 
 // Deterministic block partial sums of (L(x) - Sigma)^2 (fixed grid, fixed
@@ -178,8 +583,7 @@ __global__ void __launch_bounds__(kNormThreads) norm_partial(LevelView<T> L, Coe
   size_t n = (size_t)1 << (3 * L.lg);
   double acc = 0.0;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    int k = (int)(t & (L.N - 1)), j = (int)((t >> L.lg) & (L.N - 1)), i = (int)(t >> (2 * L.lg));
-    Cell<T> q = gather<M, FM, T>(L, i, j, k);
+    Cell<T> q = gather_at<M, FM, T>(L, t);
     T F, dF;
     eval_cell<M, FM, T>(c, L.ih2, q, F, dF);
     acc += (double)F * (double)F;

@@ -44,6 +44,7 @@ struct Cell {
   T eta, sig;      // density and FAS source
   T B, Bn[6];      // base field (DELTA form)
   T w, wn[6];      // e^B (f(R) DELTA form)
+  T a, an[6];      // f(R): cached b = e^x (FIELD) or m = e^B expm1(e) (DELTA)
 };
 
 template <class T> __device__ __forceinline__ T dexp(T v);
@@ -51,7 +52,22 @@ template <> __device__ __forceinline__ double dexp<double>(double v) { return ex
 template <> __device__ __forceinline__ float dexp<float>(float v) { return __expf(v); }
 template <class T> __device__ __forceinline__ T dexpm1(T v);
 template <> __device__ __forceinline__ double dexpm1<double>(double v) { return expm1(v); }
-template <> __device__ __forceinline__ float dexpm1<float>(float v) { return expm1f(v); }
+// FP32 e^v - 1: Taylor series to degree 9 for |v| <= 1/2 (truncation below
+// 3e-10 relative), else expf(v) - 1 (no cancellation beyond a factor 3 there).
+template <> __device__ __forceinline__ float dexpm1<float>(float v) {
+  if (fabsf(v) <= 0.5f) {
+    float p = fmaf(v, 1.0f / 362880.0f, 1.0f / 40320.0f);
+    p = fmaf(p, v, 1.0f / 5040.0f);
+    p = fmaf(p, v, 1.0f / 720.0f);
+    p = fmaf(p, v, 1.0f / 120.0f);
+    p = fmaf(p, v, 1.0f / 24.0f);
+    p = fmaf(p, v, 1.0f / 6.0f);
+    p = fmaf(p, v, 0.5f);
+    p = fmaf(p, v, 1.0f);
+    return p * v;
+  }
+  return expf(v) - 1.0f;
+}
 
 // f(R) in the field form with b = e^x of the cell and its neighbours given:
 //   F  = h^-2 sum_f b_f (x_nb - x) - S(x) - Sigma,   b_f = (b + b_nb)/2
@@ -118,23 +134,26 @@ __device__ __forceinline__ void eval_cell(const Coef& c, T ih2, const Cell<T>& q
       T u = B + e;
       dF = T(-6) * ih2 - A * (sm1 + T(3) * u * u);
     }
-  } else {  // FOFR
+  } else {  // FOFR: the per-cell exponentials come from the cached q.a, q.an
     if constexpr (FM == FIELD) {
-      T bn[6];
-#pragma unroll
-      for (int d = 0; d < 6; ++d) bn[d] = dexp<T>(q.xn[d]);
-      fofr_field_eval<T>(c, ih2, q.x, dexp<T>(q.x), q.xn, bn, q.eta, q.sig, F, dF);
+      fofr_field_eval<T>(c, ih2, q.x, q.a, q.xn, q.an, q.eta, q.sig, F, dF);
     } else {
-      T mn[6], btn[6];
+      T btn[6];
 #pragma unroll
-      for (int d = 0; d < 6; ++d) {
-        mn[d] = q.wn[d] * dexpm1<T>(q.xn[d]);
-        btn[d] = q.wn[d] + mn[d];
-      }
-      T m = q.w * dexpm1<T>(q.x);
-      fofr_delta_eval<T>(c, ih2, q.x, q.B, m, q.w + m, q.xn, q.Bn, mn, btn, q.sig, F, dF);
+      for (int d = 0; d < 6; ++d) btn[d] = q.wn[d] + q.an[d];
+      fofr_delta_eval<T>(c, ih2, q.x, q.B, q.a, q.w + q.a, q.xn, q.Bn, q.an, btn, q.sig, F, dF);
     }
   }
+}
+
+// The cached per-cell exponential of f(R) for a cell holding x (and e^B = w).
+template <Model M, Form FM, class T>
+__device__ __forceinline__ T aux_of(T x, T w) {
+  if constexpr (M == FOFR && FM == FIELD) return dexp<T>(x);
+  if constexpr (M == FOFR && FM == DELTA) return w * dexpm1<T>(x);
+  (void)x;
+  (void)w;
+  return T(0);
 }
 
 // Off-diagonal Jacobian entry dF_c/dx_nb for neighbour direction d (used by

@@ -11,7 +11,6 @@
 
 #include "../../include/isis.h"
 #include "isis_coarse.cuh"
-#include "isis_stream.cuh"
 #include "isis_exp64.cuh"
 #include "isis_prof.cuh"
 
@@ -32,7 +31,7 @@ struct Workspace {
   int nlev = 0;
   // per level l (0 = finest): x, x0, sig, eta, B, w (element type T)
   std::vector<void*> x, x0, sig, eta, B, w;
-  std::vector<void*> xalt;    // second buffer of x for the streaming smoother (FP32, N >= kStreamMinN)
+  std::vector<void*> aux;     // f(R): cached e^x / e^B expm1(x) per level (level 0 too)
   double* part = nullptr;     // kNormBlocks partial sums
   double* part2 = nullptr;    // second set of partials
   double* scal = nullptr;     // device scalars: [0] norm^2, [1] sum, [2] aux
@@ -81,34 +80,6 @@ inline int ilog2(int n) {
 }
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Grids at least this large are smoothed by the temporally blocked streaming
-// kernel (FP32 only); smaller ones by the one-colour kernel.
-constexpr int kStreamMinN = 128;
-// Sweeps fused per streaming pass (1 or 2).
-constexpr int kStreamSweeps = 1;
-
-// One streaming pass of NSW sweeps: xin -> xout.
-template <Model M, Form FM, int NSW>
-isis_status stream_pass(const LevelView<float>& v, float* xout, const Coef& c, cudaStream_t st, double bytes,
-                        int kind) {
-  constexpr int TJ = StreamCfg<M, FM, NSW>::TJ, H = 2 * NSW;
-  constexpr size_t smem = stream_smem<M, FM, NSW>();
-  static bool attr_done = false;
-  if (!attr_done) {
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(smooth_stream<M, FM, NSW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-      return ISIS_ECUDA;
-    attr_done = true;
-  }
-  const int N = v.N;
-  const int TI = N >= 512 ? 64 : (N >= 256 ? 32 : 16);
-  dim3 grid((unsigned)((N + (64 - 2 * H) - 1) / (64 - 2 * H)), (unsigned)((N + (TJ - 2 * H) - 1) / (TJ - 2 * H)),
-            (unsigned)(N / TI));
-  ISIS_LAUNCH(kind, bytes, st, (smooth_stream<M, FM, NSW><<<grid, 32 * TJ, smem, st>>>(v, xout, c, TI)));
-  return ISIS_OK;
-}
-
 // ---------------------------------------------------------------------------
 // V-cycle driver for one model / form / element type
 // ---------------------------------------------------------------------------
@@ -116,7 +87,6 @@ isis_status stream_pass(const LevelView<float>& v, float* xout, const Coef& c, c
 template <Model M, Form FM, class T>
 struct Cycler {
   std::vector<LevelView<T>> L;
-  std::vector<T*> alt;  // second buffer of each level's x (streaming smoother), else nullptr
   Workspace* ws = nullptr;
   Coef c;
   int nu1 = 2, nu2 = 2;
@@ -130,9 +100,7 @@ struct Cycler {
     nu2 = A.nu2;
     st = A.st;
     L.resize(ws->nlev);
-    alt.assign(ws->nlev, nullptr);
     for (int l = 0; l < ws->nlev; ++l) {
-      if (sizeof(T) == 4) alt[l] = (T*)ws->xalt[l];
       int N = A.N >> l;
       double h = A.box / N;
       LevelView<T> v;
@@ -144,6 +112,7 @@ struct Cycler {
       v.sig = l == 0 ? sigfine : (const T*)ws->sig[l];
       v.B = (const T*)ws->B[l];
       v.w = (const T*)ws->w[l];
+      v.aux = (T*)ws->aux[l];
       L[l] = v;
     }
   }
@@ -161,31 +130,23 @@ struct Cycler {
   isis_status smooth(int l, int sweeps) {
     LevelView<T>& v = L[l];
     size_t half = ((size_t)v.N * v.N * v.N) / 2;
-    // algorithmic bytes of a full sweep, and of one streaming pass of 1 or 2
-    // sweeps: read x and the per-cell arrays once, write x once
+    // algorithmic bytes of a full sweep: read x and the per-cell arrays once,
+    // write x once (a one-colour launch moves half of that)
     double bytes = cells(v) * sizeof(T) * (2 + arrays(v.sig != nullptr));
     int kind = l == 0 ? KK_SMOOTH_FINE : KK_SMOOTH_COARSE;
-    if constexpr (sizeof(T) == 4) {
-      if (v.N >= kStreamMinN && alt[l]) {
-        // one sweep per pass over HBM (fusing two costs more in redundant halo
-        // work than it saves in traffic); the field alternates between x and alt
-        int left = sweeps;
-        while (left > 0) {
-          int nsw = (left >= 2 && kStreamSweeps == 2) ? 2 : 1;
-          float* out = alt[l];
-          isis_status r = nsw == 2 ? stream_pass<M, FM, 2>(v, out, c, st, bytes, kind)
-                                   : stream_pass<M, FM, 1>(v, out, c, st, bytes, kind);
-          if (r != ISIS_OK) return r;
-          alt[l] = v.x;
-          v.x = out;
-          left -= nsw;
-        }
-        return ISIS_OK;
-      }
-    }
     for (int s = 0; s < sweeps; ++s)
-      for (int color = 0; color < 2; ++color)
-        ISIS_LAUNCH(kind, bytes * 0.5, st, (smooth_color<M, FM, T><<<nblk(half, 256), 256, 0, st>>>(v, c, color)));
+      for (int color = 0; color < 2; ++color) {
+        if constexpr (sizeof(T) == 4) {
+          if (v.N >= 4)
+            ISIS_LAUNCH(kind, bytes * 0.5, st,
+                        (smooth_rb2<M, FM><<<nblk(half / 2, 256), 256, 0, st>>>(v, c, color)));
+          else
+            ISIS_LAUNCH(kind, bytes * 0.5, st, (smooth_rb<M, FM><<<nblk(half, 256), 256, 0, st>>>(v, c, color)));
+        }
+        else
+          ISIS_LAUNCH(kind, bytes * 0.5, st,
+                      (smooth_color<M, FM, T><<<nblk(half, 256), 256, 0, st>>>(v, c, color)));
+      }
     return ISIS_OK;
   }
 
@@ -201,17 +162,32 @@ struct Cycler {
     LevelView<T>& C = L[l + 1];
     size_t nc = (size_t)C.N * C.N * C.N;
     double nf = cells(L[l]), ncd = (double)nc;
-    ISIS_LAUNCH(l == 0 ? KK_RESTRICT_FINE : KK_RESTRICT_COARSE,
-                sizeof(T) * (nf * (1 + arrays(L[l].sig != nullptr)) + 3 * ncd), st,
-                (resid_restrict<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], c, C.x, (T*)ws->x0[l + 1],
-                                                                        (T*)ws->sig[l + 1])));
+    const double rbytes = sizeof(T) * (nf * (1 + arrays(L[l].sig != nullptr)) + 3 * ncd);
+    bool split = false;
+    if constexpr (sizeof(T) == 4 && M == FOFR && FM == DELTA) split = (l == 0 && ws->x0[0] != nullptr);
+    if (split) {
+      // f(R) correction form on the finest grid: the stencil of 8 children holds too many
+      // per-cell inputs for one thread, so the residual goes through a scratch grid
+      if constexpr (sizeof(T) == 4) {
+        float* res = (float*)ws->x0[0];
+        ISIS_LAUNCH(KK_RESTRICT_FINE, rbytes, st,
+                    (resid_rb2<M, FM><<<nblk((size_t)nf / 2, 256), 256, 0, st>>>(L[0], c, res)));
+        ISIS_LAUNCH(KK_RESTRICT_FINE, 0.0, st,
+                    (restrict_xr<M, FM><<<nblk(nc, 256), 256, 0, st>>>(L[0], res, C, (float*)ws->x0[1],
+                                                                        (float*)ws->sig[1])));
+      }
+    } else {
+      ISIS_LAUNCH(l == 0 ? KK_RESTRICT_FINE : KK_RESTRICT_COARSE, rbytes, st,
+                  (resid_restrict<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], c, C, (T*)ws->x0[l + 1],
+                                                                          (T*)ws->sig[l + 1])));
+    }
     ISIS_LAUNCH(KK_SIGMA, sizeof(T) * ncd * (2 + arrays(true)), st,
                 (coarse_sigma_add<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(C, c, (T*)ws->sig[l + 1])));
     s = vcycle(l + 1);
     if (s != ISIS_OK) return s;
     ISIS_LAUNCH(l == 0 ? KK_PROLONG_FINE : KK_PROLONG_COARSE, sizeof(T) * (2 * ncd + 2 * nf), st,
-                (prolong_correct<T><<<nblk((size_t)nf, 256), 256, 0, st>>>(L[l].x, C.x, (const T*)ws->x0[l + 1],
-                                                                           C.lg)));
+                (prolong_correct<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], C.x, (const T*)ws->x0[l + 1],
+                                                                          C.lg)));
     return smooth(l, nu2);
   }
 
@@ -276,6 +252,22 @@ __global__ void convert_k(const Tin* __restrict__ a, Tout* __restrict__ b, size_
   if (t < n) b[t] = (Tout)a[t];
 }
 
+// Row-major (caller, FP64 or FP32) <-> red/black split FP32 workspace.
+template <class Tin>
+__global__ void to_rb(const Tin* __restrict__ a, float* __restrict__ b, int lg) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ((size_t)1 << (3 * lg))) return;
+  const int m = (1 << lg) - 1;
+  b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))] = (float)a[t];
+}
+template <class Tout>
+__global__ void from_rb(const float* __restrict__ b, Tout* __restrict__ a, int lg) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ((size_t)1 << (3 * lg))) return;
+  const int m = (1 << lg) - 1;
+  a[t] = (Tout)b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
+}
+
 template <class T>
 __global__ void exp_k(const T* __restrict__ a, T* __restrict__ b, size_t n) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,7 +280,7 @@ __global__ void fill_k(T* __restrict__ a, T v, size_t n) {
   if (t < n) a[t] = v;
 }
 
-__global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, size_t n);
+__global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, int lg);
 
 // Initial guess (isis_init): the background constant, or cell by cell the
 // solution for a uniform density equal to the cell's eta (computed in FP32:
@@ -327,7 +319,8 @@ isis_status apply_init(const SolveArgs& A, const Coef& c, T* phi, const T* eta, 
 }
 
 // FP64 residual of the finest grid for the defect-correction loop:
-// r = -L64(phi); writes r and B = phi rounded to FP32, and block partials of r^2.
+// r = -L64(phi); writes r and B = phi rounded to FP32 (red/black layout), and
+// block partials of r^2.
 // (Poisson and symmetron: the operator has no transcendental terms.)
 template <Model M>
 __global__ void __launch_bounds__(kNormThreads) outer_residual(LevelView<double> L, Coef c, float* __restrict__ r32,
@@ -339,8 +332,9 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual(LevelView<double>
     Cell<double> q = gather<M, FIELD, double>(L, i, j, k);
     double F, dF;
     eval_cell<M, FIELD, double>(c, L.ih2, q, F, dF);
-    r32[t] = (float)(-F);
-    B32[t] = (float)q.x;
+    const size_t o = lidx<float>(L.lg, i, j, k);
+    r32[o] = (float)(-F);
+    B32[o] = (float)q.x;
     acc += F * F;
   }
   block_sum_store<double>(acc, part);
@@ -394,20 +388,35 @@ isis_status solve_field(const SolveArgs& A) {
   s = apply_init<M, T>(A, c, phi, eta, n);
   if (s != ISIS_OK) return s;
 
+  // FP32 grids work in the red/black layout of the workspace; FP64 in place
+  const int lg = ilog2(A.N);
+  T* xw = phi;
+  const T* etaw = eta;
+  if constexpr (sizeof(T) == 4) {
+    xw = (T*)ws->x[0];
+    etaw = (const T*)ws->eta[0];
+    ISIS_LAUNCH(KK_SETUP, 8.0 * n, st, (to_rb<T><<<nblk(n, 256), 256, 0, st>>>(eta, (float*)ws->eta[0], lg)));
+    ISIS_LAUNCH(KK_SETUP, 8.0 * n, st, (to_rb<T><<<nblk(n, 256), 256, 0, st>>>(phi, (float*)xw, lg)));
+  }
+
   // density on the coarse levels
   for (int l = 1; l < ws->nlev; ++l) {
     int lgc = ilog2(A.N >> l);
-    const T* f = l == 1 ? eta : (const T*)ws->eta[l - 1];
+    const T* f = l == 1 ? etaw : (const T*)ws->eta[l - 1];
     size_t ncl = (size_t)1 << (3 * lgc);
     ISIS_LAUNCH(KK_SETUP, 9.0 * ncl * sizeof(T), st,
                 (restrict_mean<T, T><<<nblk(ncl, 256), 256, 0, st>>>(f, (T*)ws->eta[l], lgc)));
   }
   ISIS_CK(cudaMemsetAsync(ws->iflags, 0, 2 * sizeof(int), st));
 
+  if (M == FOFR)  // cached e^u of the finest level
+    ISIS_LAUNCH(KK_SETUP, 2.0 * n * sizeof(T), st,
+                (exp_k<T><<<nblk(n, 256), 256, 0, st>>>(xw, (T*)ws->aux[0], n)));
+
   Cycler<M, FIELD, T> cy;
   SolveArgs A2 = A;
   A2.coef = c;
-  cy.setup(ws, A2, phi, eta, nullptr);
+  cy.setup(ws, A2, xw, etaw, nullptr);
 
   double res;
   s = cy.fine_rms(&res);
@@ -438,7 +447,8 @@ isis_status solve_field(const SolveArgs& A) {
       if (res <= target) { out = ISIS_OK; break; }
     }
   }
-  if (cy.L[0].x != phi) ISIS_CK(cudaMemcpyAsync(phi, cy.L[0].x, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  if constexpr (sizeof(T) == 4)
+    ISIS_LAUNCH(KK_SETUP, 8.0 * n, st, (from_rb<T><<<nblk(n, 256), 256, 0, st>>>((const float*)xw, phi, lg)));
   if (A.info) *A.info = loc;
   return out;
 }
@@ -487,7 +497,8 @@ isis_status solve_refine(const SolveArgs& A) {
   s = apply_init<M, double>(A, c, phi64, eta64, n);
   if (s != ISIS_OK) return s;
 
-  ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (convert_k<double, float><<<nblk(n, 256), 256, 0, st>>>(eta64, eta0, n)));
+  const int lg = ilog2(A.N);
+  ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (to_rb<double><<<nblk(n, 256), 256, 0, st>>>(eta64, eta0, lg)));
   for (int l = 1; l < ws->nlev; ++l) {
     int lgc = ilog2(A.N >> l);
     size_t ncl = (size_t)1 << (3 * lgc);
@@ -501,7 +512,9 @@ isis_status solve_refine(const SolveArgs& A) {
   int nh = 0;  // history entries
 
   // ---- phase 1: FP32 field-form cycles ----
-  ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (convert_k<double, float><<<nblk(n, 256), 256, 0, st>>>(phi64, B0, n)));
+  ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (to_rb<double><<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg)));
+  if (M == FOFR)
+    ISIS_LAUNCH(KK_SETUP, 8.0 * n, st, (exp_k<float><<<nblk(n, 256), 256, 0, st>>>(B0, (float*)ws->aux[0], n)));
   {
     Cycler<M, FIELD, float> cy;
     cy.setup(ws, A2, B0, eta0, nullptr);
@@ -530,7 +543,7 @@ isis_status solve_refine(const SolveArgs& A) {
       return ISIS_ENAN;
     }
     const float* psi = cy.L[0].x;
-    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (convert_k<float, double><<<nblk(n, 256), 256, 0, st>>>(psi, phi64, n)));
+    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (from_rb<double><<<nblk(n, 256), 256, 0, st>>>(psi, phi64, lg)));
     // Poisson gauge: the residual does not see the mean, so it is removed once per phase
     if (M == POI) {
       s = remove_mean<double>(ws, phi64, n, st);
@@ -548,6 +561,7 @@ isis_status solve_refine(const SolveArgs& A) {
   F64.sig = nullptr;
   F64.B = nullptr;
   F64.w = nullptr;
+  F64.aux = nullptr;
 
   Cycler<M, DELTA, float> cy;
   cy.setup(ws, A2, e0, eta0, r0);
@@ -556,6 +570,8 @@ isis_status solve_refine(const SolveArgs& A) {
   int* hi = (int*)(h + 4);
   isis_status out = ISIS_ENOCONV;
   const double target = A.tol * ref;
+  double prev_res = 0.0;
+  int prev_k = 0;
   for (int outer = 0;; ++outer) {
     // r = -L64(phi64), B = fp32(phi64), RMS of r
     if (M == FOFR) {
@@ -598,15 +614,27 @@ isis_status solve_refine(const SolveArgs& A) {
       }
     }
     ISIS_CK(cudaMemsetAsync(cy.L[0].x, 0, n * sizeof(float), st));
+    if (M == FOFR) ISIS_CK(cudaMemsetAsync(ws->aux[0], 0, n * sizeof(float), st));  // e^B expm1(0) = 0
+    // inner_cycles FP32 cycles; after the first outer iteration, only as many
+    // as the measured contraction per cycle says reach half the target
     int k = A.inner;
+    if (prev_res > 0.0 && prev_k > 0 && res < prev_res) {
+      const double rho = std::pow(res / prev_res, 1.0 / prev_k);
+      if (rho > 0.0 && rho < 1.0) {
+        const double need = std::ceil(std::log(0.5 * target / res) / std::log(rho));
+        if (need >= 1.0 && need < (double)k) k = (int)need;
+      }
+    }
     if (loc.cycles + k > A.max_cycles) k = A.max_cycles - loc.cycles;
+    prev_res = res;
+    prev_k = k;
     for (int it = 0; it < k; ++it) {
       s = cy.vcycle(0);
       if (s != ISIS_OK) return s;
     }
     loc.cycles += k;
     const float* ecur = cy.L[0].x;
-    ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_phi64<<<nblk(n, 256), 256, 0, st>>>(phi64, ecur, n)));
+    ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_phi64<<<nblk(n, 256), 256, 0, st>>>(phi64, ecur, lg)));
   }
   if (M == POI) {
     s = remove_mean<double>(ws, phi64, n, st);
