@@ -133,6 +133,25 @@ typedef struct {
 isis_status isis_cic_deposit(const isis_grid* grid, const float* x, const float* y, const float* z, int64_t npart,
                              void* eta, int eta_f64, void* stream);
 
+/* The same CIC deposit for callers that must not allocate device memory once
+ * they are running: services held to a fixed device-memory budget, programs
+ * whose device memory is owned by another allocator (a framework's caching
+ * pool), and paths where the device-wide synchronisation that cudaMalloc and
+ * cudaFree imply is not acceptable.  It has no counterpart in the paper.
+ *   - Scratch: a fixed array of 64^3 int64 accumulators (2 MiB) compiled into
+ *     the library; every GPU that loads the library holds it until the
+ *     process exits.  Nothing is allocated or freed by this call.
+ *   - Limit: grid->N <= 64; larger grids return ISIS_EINVAL (use
+ *     isis_cic_deposit).  Other arguments as for isis_cic_deposit, same result.
+ *   - Set-up: the first call on each device looks up the array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that first
+ *     call before any stream capture.
+ *   - Sharing: all calls share the one array and each call clears the part it
+ *     uses before accumulating, so calls must not overlap on the GPU (two calls
+ *     on different streams without ordering between them race). */
+isis_status isis_cic_deposit_noalloc(const isis_grid* grid, const float* x, const float* y, const float* z,
+                                     int64_t npart, void* eta, int eta_f64, void* stream);
+
 /* Newtonian potential (Sect. 3.1, Eq. (disc_lap), Eq. (explicit)):
  *     (sum of 6 neighbours - 6 Phi)/h^2 = (3/2) Om H0^2 (eta - <eta>) / a
  * solved by multigrid V-cycles with Gauss-Seidel smoothing (the Newton step

@@ -183,6 +183,42 @@ __global__ void force_gather(const float* __restrict__ fx, const float* __restri
   gz[p] = -a2;
 }
 
+// ---------------------------------------------------------------------------
+// Deposit without device allocation (isis_cic_deposit_noalloc)
+// ---------------------------------------------------------------------------
+
+// Largest grid the allocation-free deposit accepts: 64^3 cells, 2 MiB of
+// 64-bit accumulators held for the life of the process on every GPU that
+// loads this library.
+constexpr int kNoAllocMaxN = 64;
+static __device__ __align__(256) unsigned long long g_noalloc_acc[(size_t)kNoAllocMaxN * kNoAllocMaxN * kNoAllocMaxN];
+
+// Device address of g_noalloc_acc, looked up once per device.  In host code
+// the name g_noalloc_acc is only a host-side stand-in for the array, so its
+// address must come from cudaGetSymbolAddress with the device current.
+constexpr int kMaxDevices = 64;
+static unsigned long long* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+static isis_status noalloc_scratch(unsigned long long** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ISIS_ECUDA;
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_acc) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return ISIS_ECUDA;
+    }
+    g_noalloc_ptr[dev] = (unsigned long long*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return ISIS_OK;
+}
+
+__global__ void zero_u64(unsigned long long* __restrict__ a, size_t n) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) a[t] = 0ull;
+}
+
 static bool grid_valid(const isis_grid* g) {
   return g && g->N >= 8 && g->N <= 1024 && (g->N & (g->N - 1)) == 0 && g->box > 0;
 }
@@ -202,6 +238,30 @@ isis_status isis_cic_deposit(const isis_grid* grid, const float* x, const float*
   unsigned long long* acc = get_deposit_buf(N);
   if (!acc) return ISIS_ENOMEM;
   ISIS_CK(cudaMemsetAsync(acc, 0, n * sizeof(unsigned long long), st));
+  ISIS_LAUNCH(KK_CIC_SCATTER, 12.0 * npart + 8.0 * n, st,
+              (cic_scatter<<<nblk((size_t)npart, 256), 256, 0, st>>>(x, y, z, (long long)npart, lg, acc)));
+  const double scale = (double)n / ((double)npart * kFix);
+  if (eta_f64)
+    ISIS_LAUNCH(KK_CIC_FINISH, 16.0 * n, st,
+                (cic_finish<double><<<nblk(n, 256), 256, 0, st>>>(acc, (double*)eta, n, scale)));
+  else
+    ISIS_LAUNCH(KK_CIC_FINISH, 12.0 * n, st,
+                (cic_finish<float><<<nblk(n, 256), 256, 0, st>>>(acc, (float*)eta, n, scale)));
+  return ISIS_OK;
+}
+
+isis_status isis_cic_deposit_noalloc(const isis_grid* grid, const float* x, const float* y, const float* z,
+                                     int64_t npart, void* eta, int eta_f64, void* stream) {
+  if (!grid_valid(grid) || !x || !y || !z || !eta || npart < 1 || npart > ((int64_t)1 << 40)) return ISIS_EINVAL;
+  if (grid->N > kNoAllocMaxN) return ISIS_EINVAL;  // larger grids need isis_cic_deposit
+  unsigned long long* acc = nullptr;
+  isis_status s = noalloc_scratch(&acc);
+  if (s != ISIS_OK) return s;
+  const int N = grid->N, lg = ilog2(N);
+  const size_t n = (size_t)N * N * N;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the array keeps the previous call's sums: clear the part this grid uses
+  ISIS_LAUNCH(KK_CIC_SCATTER, 8.0 * n, st, (zero_u64<<<nblk(n, 256), 256, 0, st>>>(acc, n)));
   ISIS_LAUNCH(KK_CIC_SCATTER, 12.0 * npart + 8.0 * n, st,
               (cic_scatter<<<nblk((size_t)npart, 256), 256, 0, st>>>(x, y, z, (long long)npart, lg, acc)));
   const double scale = (double)n / ((double)npart * kFix);

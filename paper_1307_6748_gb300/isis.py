@@ -24,7 +24,7 @@ ISIS_F64, ISIS_F32, ISIS_F32_REFINE64 = 0, 1, 2
 H0_MPC = 1.0 / 2997.92458  # (Mpc/h)^-1 with c = 1
 
 # Every function the header declares (checked by the tests).
-EXPORTS = ("isis_cic_deposit", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force",
+EXPORTS = ("isis_cic_deposit", "isis_cic_deposit_noalloc", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force",
            "isis_strerror", "isis_release_workspace", "isis_prof_enable", "isis_prof_reset", "isis_prof_read",
            "isis_launch_count")
 ISIS_INIT_INPUT, ISIS_INIT_BACKGROUND, ISIS_INIT_LOCAL = 0, 1, 2
@@ -77,6 +77,8 @@ def load(path: str = LIB_PATH):
     P = ctypes.POINTER
     vp, f_p = ctypes.c_void_p, ctypes.c_void_p
     lib.isis_cic_deposit.argtypes = [P(isis_grid), f_p, f_p, f_p, ctypes.c_int64, vp, ctypes.c_int, vp]
+    lib.isis_cic_deposit_noalloc.argtypes = [P(isis_grid), f_p, f_p, f_p, ctypes.c_int64, vp, ctypes.c_int, vp]
+    lib.isis_cic_deposit_noalloc.restype = ctypes.c_int
     lib.isis_poisson_solve.argtypes = [P(isis_grid), ctypes.c_double, vp, vp, ctypes.c_double, P(isis_mg_opts),
                                        P(isis_solve_info), vp]
     lib.isis_scalar_solve.argtypes = [ctypes.c_int, P(isis_params), P(isis_grid), ctypes.c_double, vp, vp,
@@ -222,6 +224,18 @@ def isis_cic_deposit(grid: Grid, x: torch.Tensor, y: torch.Tensor, z: torch.Tens
     st = lib.isis_cic_deposit(ctypes.byref(g), _ptr(x, torch.float32), _ptr(y, torch.float32),
                               _ptr(z, torch.float32), x.numel(), _ptr(eta), f64, _stream(stream))
     _check(st, "isis_cic_deposit")
+    return eta
+
+
+def isis_cic_deposit_noalloc(grid: Grid, x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, eta: torch.Tensor,
+                             stream=None) -> torch.Tensor:
+    """CIC deposit that allocates no device memory (grids up to 64^3; see include/isis.h)."""
+    lib = load()
+    f64 = 1 if eta.dtype == torch.float64 else 0
+    g = grid.c()
+    st = lib.isis_cic_deposit_noalloc(ctypes.byref(g), _ptr(x, torch.float32), _ptr(y, torch.float32),
+                                      _ptr(z, torch.float32), x.numel(), _ptr(eta), f64, _stream(stream))
+    _check(st, "isis_cic_deposit_noalloc")
     return eta
 
 
