@@ -1,0 +1,90 @@
+/*
+ * isis_unet.h -- C ABI of the learned initial guess for the scalar-field
+ * solve: the kernels of a small 3-D U-Net (convolutions on the tcgen05 tensor
+ * cores, BF16 operands, FP32 accumulation) and of its training.
+ *
+ * The paper (arXiv:1307.6748) has no learned component.  Its solver starts
+ * every FAS solve from a guess (Sect. 3.2); here a network trained on
+ * converged solutions of isis_scalar_solve proposes that guess, and the
+ * multigrid solver always finishes the solve, so the net never changes the
+ * answer, only the number of cycles.
+ *
+ * Conventions
+ *   - A grid has n = 2^lg cells per side (2 <= lg <= 10), V = n^3 voxels in
+ *     row-major order ((i n + j) n + k), periodic.
+ *   - Activations are BF16, voxel-major [v][c], with c a multiple of 16;
+ *     gradients of activations are FP32 in the same layout.  All pointers are
+ *     device pointers owned by the caller, 16-byte aligned.
+ *   - 3x3x3 convolution, tap t = (di+1)*9 + (dj+1)*3 + (dk+1) for the offset
+ *     (di, dj, dk) in {-1,0,1}^3, periodic wrap:
+ *       out[v][o] = b[o] + sum_t sum_i X[v + d_t][i] W[t][o][i],   W: BF16 [27][cout][cin]
+ *     X is the channel concatenation of src1 (c1 channels; on the grid lg1 =
+ *     lg, or lg - 1 read by nearest-neighbour upsampling) and src2 (c2
+ *     channels on grid lg, or absent with c2 = 0).  cin = c1 + c2.
+ *   - err: device int, OR-ed with 1 if a bounded wait inside a kernel gave up.
+ *   - Every call is stream ordered and returns ISIS_EINVAL for bad sizes or
+ *     pointers, ISIS_ECUDA for a failed launch.
+ */
+#ifndef ISIS_UNET_H
+#define ISIS_UNET_H
+#include <stdint.h>
+
+#include "isis.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* out (BF16 [V][cout]) = optional ReLU of the convolution plus bias (FP32 [cout]).
+ * 16 <= c1, 0 <= c2, c1 + c2 <= 128, 16 <= cout <= 64, all multiples of 16. */
+isis_status isis_unet_conv3_fwd(const void* src1, int c1, int lg1, const void* src2, int c2, int lg, const void* w,
+                                const float* bias, int cout, int relu, void* out, int* err, void* stream);
+
+/* Input gradient: din (FP32 [V][cin]) = sum_t sum_o dz[v - d_t][o] W[t][o][i],
+ * with wt = W transposed per tap (BF16 [27][cin][cout], isis_unet_transpose_w),
+ * dz BF16 [V][cout]; cin <= 128. */
+isis_status isis_unet_conv3_dgrad(const void* dz, int cout, int lg, const void* wt, int cin, float* din, int* err,
+                                  void* stream);
+
+/* Weight gradient: dw[t][o][i] += sum_v dz[v][o] X[v + d_t][i] (FP32, accumulated with
+ * atomics, so the summation order is not fixed).  Same src1/src2 convention as the forward. */
+isis_status isis_unet_conv3_wgrad(const void* src1, int c1, int lg1, const void* src2, int c2, int lg,
+                                  const void* dz, int cout, float* dw, int* err, void* stream);
+
+/* Input features of the net, BF16 [V][16]: channel 0 = (ln eta - mu) * isd,
+ * channel 1 = afeat (a normalised expansion factor), channels 2..15 = 0. */
+isis_status isis_unet_input(const double* eta, int lg, float mu, float isd, float afeat, void* x16, void* stream);
+
+/* y (grid lgc) = mean of the 8 children of x (grid lgc + 1), BF16, C channels. */
+isis_status isis_unet_pool_fwd(const void* x, int C, int lgc, void* y, void* stream);
+/* dx (grid lgc + 1, FP32) += dy (grid lgc) / 8, broadcast to the 8 children. */
+isis_status isis_unet_pool_bwd(const float* dy, int C, int lgc, float* dx, void* stream);
+/* dz (BF16) = dy where y > 0, else 0 (gradient through a ReLU whose output is y). */
+isis_status isis_unet_relu_bwd(const float* dy, const void* y, int64_t n, void* dz, void* stream);
+/* Split the FP32 gradient dx [V][c1+c2] of a concatenated input on grid lg:
+ * d1 = channels [0, c1) (summed over the 8 fine voxels of each half-resolution
+ * cell when up != 0), d2 += channels [c1, c1+c2). */
+isis_status isis_unet_split_bwd(const float* dx, int c1, int c2, int lg, int up, float* d1, float* d2,
+                                void* stream);
+/* Output head and loss: p[v] = hb[C] + sum_c hb[c] y[v][c] (into pred if not NULL);
+ * if target is not NULL: loss += mean (p - tscale target)^2, dy = d loss / d y,
+ * dhb += d loss / d hb.  hb: FP32 [C + 1] (weights, then bias). */
+isis_status isis_unet_head(const void* y, int C, int lg, const float* hb, const float* target, float tscale,
+                           float* pred, float* dy, float* dhb, double* loss, void* stream);
+/* db[o] += sum_v dz[v][o]. */
+isis_status isis_unet_bias_grad(const void* dz, int C, int lg, float* db, void* stream);
+/* Adam (Kingma & Ba) on FP32 parameters p with gradient g and moments m1, m2,
+ * step number step >= 1; writes the BF16 copy pbf16 if not NULL. */
+isis_status isis_unet_adam(float* p, const float* g, float* m1, float* m2, int64_t n, float lr, float b1, float b2,
+                           float eps, int step, void* pbf16, void* stream);
+/* wt[t][i][o] = w[t][o][i] (BF16). */
+isis_status isis_unet_transpose_w(const void* w, int cout, int cin, void* wt, void* stream);
+/* b = BF16(a). */
+isis_status isis_unet_to_bf16(const float* a, int64_t n, void* b, void* stream);
+/* phi[v] = bg + scale * pred[v] (FP64 initial guess for isis_scalar_solve). */
+isis_status isis_unet_guess(const float* pred, int lg, double bg, double scale, double* phi, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISIS_UNET_H */

@@ -36,6 +36,7 @@ def sources():
 def _headers():
     hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     hs.append(os.path.join(ROOT, "include", "isis.h"))
+    hs.append(os.path.join(ROOT, "include", "isis_unet.h"))
     return hs
 
 

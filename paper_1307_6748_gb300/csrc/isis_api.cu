@@ -183,7 +183,7 @@ static const char* kKindNames[KK_COUNT] = {
     "smooth_fine",    "smooth_coarse", "resid_restrict_fine", "resid_restrict_coarse", "coarse_sigma",
     "prolong_fine",   "prolong_coarse", "coarse_newton",      "norm_fine",             "outer_residual64",
     "update64",       "setup",         "reduce",              "init_guess",            "cic_scatter",
-    "cic_finish",     "force_grid",    "force_gather"};
+    "cic_finish",     "force_grid",    "force_gather",        "unet_conv",             "unet_elem"};
 
 struct ProfRec {
   int kind;

@@ -26,6 +26,8 @@ enum KernelKind : int {
   KK_CIC_FINISH,
   KK_FORCE_GRID,
   KK_FORCE,
+  KK_UNET_CONV,         // tcgen05 convolutions of the learned guess (bytes field: FLOPs)
+  KK_UNET_ELEM,         // its element-wise kernels
   KK_COUNT
 };
 

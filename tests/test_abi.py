@@ -10,9 +10,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared():
-    src = open(os.path.join(ROOT, "include", "isis.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(isis_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(isis_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -29,9 +33,14 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
-def test_binding_lists_the_header(lib):
-    from paper_1307_6748_gb300 import isis
-    assert sorted(isis.EXPORTS) == declared()
+def test_binding_lists_the_headers(lib):
+    from paper_1307_6748_gb300 import isis, unet
+    unet._lib()  # binds the learned-guess entry points
+    bound = set(isis.EXPORTS) | {n for n in declared() if n.startswith("isis_unet_")}
+    assert sorted(bound) == declared()
+    for n in declared():
+        if n.startswith("isis_unet_"):
+            assert getattr(isis.load(), n).argtypes is not None, n
 
 
 def test_strerror_and_argument_checks_without_gpu(lib):

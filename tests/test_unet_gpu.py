@@ -1,0 +1,127 @@
+"""Tensor-core kernels of the learned guess vs the FP64 reference (oracle/unet_ref.py),
+called through the C ABI (include/isis_unet.h).
+
+Per-kernel checks feed both sides the same BF16 values, so only the FP32
+accumulation order differs.  The whole-network gradient is checked by
+direction (cosine) because the GPU keeps activations in BF16."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import unet_ref as U
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(torch.bfloat16).cuda()
+
+
+def _np(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def lib(cuda_lib):
+    from paper_1307_6748_gb300 import unet
+    return unet._lib()
+
+
+def _p(t):
+    import ctypes
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _s():
+    import ctypes
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@pytest.mark.parametrize("c1,up,c2,cout", [(16, 0, 0, 16), (32, 1, 16, 32), (64, 0, 0, 64), (64, 1, 64, 64),
+                                           (32, 1, 16, 16)])
+def test_conv_forward(lib, c1, up, c2, cout):
+    lg = 3
+    n = 1 << lg
+    g = np.random.Generator(np.random.PCG64(c1 + cout + up))
+    n1 = n >> up
+    s1 = _bf(g.standard_normal((n1 ** 3, c1)))
+    s2 = _bf(g.standard_normal((n ** 3, c2))) if c2 else None
+    W = _bf(g.standard_normal((27, cout, c1 + c2)) * 0.1)
+    b = torch.from_numpy(g.standard_normal(cout).astype(np.float32)).cuda()
+    out = torch.empty(n ** 3 * cout, dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lib.isis_unet_conv3_fwd(_p(s1), c1, lg - up, _p(s2), c2, lg, _p(W), _p(b), cout, 1, _p(out), _p(err),
+                                   _s()) == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    X1 = _np(s1).reshape(n1, n1, n1, c1)
+    if up:
+        X1 = U.up(X1)
+    X = X1 if not c2 else np.concatenate([X1, _np(s2).reshape(n, n, n, c2)], axis=-1)
+    ref = U.relu(U.conv3_fwd(X, _np(W), b.cpu().numpy().astype(np.float64))).reshape(-1, cout)
+    got = _np(out).reshape(-1, cout)
+    assert np.abs(got - ref).max() <= 2 ** -7 * np.abs(ref).max() + 1e-6
+
+
+@pytest.mark.parametrize("cout,cin", [(16, 16), (32, 96), (64, 128), (16, 48)])
+def test_conv_input_gradient(lib, cout, cin):
+    lg = 3
+    n = 1 << lg
+    g = np.random.Generator(np.random.PCG64(cout * 7 + cin))
+    dz = _bf(g.standard_normal((n ** 3, cout)))
+    W = _bf(g.standard_normal((27, cout, cin)) * 0.1)
+    Wt = torch.empty_like(W)
+    assert lib.isis_unet_transpose_w(_p(W), cout, cin, _p(Wt), _s()) == 0
+    din = torch.empty(n ** 3 * cin, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lib.isis_unet_conv3_dgrad(_p(dz), cout, lg, _p(Wt), cin, _p(din), _p(err), _s()) == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    ref = U.conv3_dgrad(_np(dz).reshape(n, n, n, cout), _np(W)).reshape(-1, cin)
+    got = din.cpu().numpy().reshape(-1, cin)
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("c1,up,c2,cout", [(16, 0, 0, 16), (32, 1, 16, 32), (64, 1, 64, 64), (16, 0, 0, 32)])
+def test_conv_weight_gradient(lib, c1, up, c2, cout):
+    lg = 4
+    n = 1 << lg
+    g = np.random.Generator(np.random.PCG64(3 * c1 + cout + up))
+    n1 = n >> up
+    s1 = _bf(g.standard_normal((n1 ** 3, c1)))
+    s2 = _bf(g.standard_normal((n ** 3, c2))) if c2 else None
+    dz = _bf(g.standard_normal((n ** 3, cout)))
+    dw = torch.zeros(27 * cout * (c1 + c2), dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lib.isis_unet_conv3_wgrad(_p(s1), c1, lg - up, _p(s2), c2, lg, _p(dz), cout, _p(dw), _p(err), _s()) == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    X1 = _np(s1).reshape(n1, n1, n1, c1)
+    if up:
+        X1 = U.up(X1)
+    X = X1 if not c2 else np.concatenate([X1, _np(s2).reshape(n, n, n, c2)], axis=-1)
+    ref = U.conv3_wgrad(X, _np(dz).reshape(n, n, n, cout))
+    got = dw.cpu().numpy().reshape(ref.shape)
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_network_gradient_direction(cuda_lib):
+    """Gradient of one training step of the GPU net vs the FP64 reference on the same parameters."""
+    from paper_1307_6748_gb300 import synth, unet
+    lg, n = 5, 32
+    net = unet.UNet(seed=3)  # 32^3: the lowest level is 4^3
+    P = {k: v.astype(np.float64) for k, v in net.state().items() if k not in ("mu", "sd", "scale")}
+    eta = synth.lognormal_eta(n, float(n), 1.5, 9).cuda()
+    target = (0.05 * synth.gaussian_field(n, float(n), 1.0, 10)).float().cuda().reshape(-1)
+    net.features(eta, 1.0, lg)
+    X0 = _np(net.acts(lg)[1]["x0"]).reshape(n, n, n, 16)
+    _, grads, _ = U.loss_and_grads(P, X0, target.cpu().numpy().astype(np.float64).reshape(n, n, n) / net.scale)
+    net.train_step(eta, 1.0, target, lg, lr=0.0)  # lr 0: gradients only
+    torch.cuda.synchronize()
+    assert int(net.err.item()) == 0
+    for k, ref in grads.items():
+        got = net.view(net.G, k).cpu().numpy().astype(np.float64)
+        ref = ref.reshape(-1)
+        cos = got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref) + 1e-300)
+        assert cos >= 0.98, (k, cos)
+        assert abs(np.linalg.norm(got) / np.linalg.norm(ref) - 1) <= 0.1, k
