@@ -36,7 +36,10 @@ extern "C" {
 #endif
 
 /* out (BF16 [V][cout]) = optional ReLU of the convolution plus bias (FP32 [cout]).
- * 16 <= c1, 0 <= c2, c1 + c2 <= 128, 16 <= cout <= 64, all multiples of 16. */
+ * 16 <= c1, 0 <= c2, c1 + c2 <= 128, 16 <= cout <= 64, all multiples of 16.
+ * Grids of 32..512 cells per side take the line kernel (whole grid rows staged
+ * once per (di, dj), the three k taps in one MMA, the k shift in the epilogue);
+ * smaller grids the per-voxel gather kernel. */
 isis_status isis_unet_conv3_fwd(const void* src1, int c1, int lg1, const void* src2, int c2, int lg, const void* w,
                                 const float* bias, int cout, int relu, void* out, int* err, void* stream);
 
@@ -51,9 +54,18 @@ isis_status isis_unet_conv3_dgrad(const void* dz, int cout, int lg, const void* 
 isis_status isis_unet_conv3_wgrad(const void* src1, int c1, int lg1, const void* src2, int c2, int lg,
                                   const void* dz, int cout, float* dw, int* err, void* stream);
 
-/* Input features of the net, BF16 [V][16]: channel 0 = (ln eta - mu) * isd,
- * channel 1 = afeat (a normalised expansion factor), channels 2..15 = 0. */
-isis_status isis_unet_input(const double* eta, int lg, float mu, float isd, float afeat, void* x16, void* stream);
+/* Input features of the net: f0 = (ln eta - mu) * isd and f1 = afeat (a
+ * normalised expansion factor), written as x16 (BF16 [V][16]: f0, f1, then 14
+ * zero channels) and/or f2 (BF16 [V][2]: f0, f1); either may be NULL, not both. */
+isis_status isis_unet_input(const double* eta, int lg, float mu, float isd, float afeat, void* x16, void* f2,
+                            void* stream);
+
+/* First layer from the two features f2 (BF16 [V][2]): out (BF16 [V][16]) =
+ * ReLU(bias + sum_t f0(v + d_t) W[t][o][0] + f1(v + d_t) W[t][o][1]), with
+ * W BF16 [27][16][wcin] (wcin >= 2, a multiple of 8; channels >= 2 unused).
+ * Equal to isis_unet_conv3_fwd of x16 (relu = 1) up to the FP32 summation order. */
+isis_status isis_unet_stem_fwd(const void* f2, int lg, const void* w, int wcin, const float* bias, void* out,
+                               int* err, void* stream);
 
 /* y (grid lgc) = mean of the 8 children of x (grid lgc + 1), BF16, C channels. */
 isis_status isis_unet_pool_fwd(const void* x, int C, int lgc, void* y, void* stream);

@@ -101,7 +101,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ uint32_t tmem_cols(int n) { return n <= 32 ? 32u : (n <= 64 ? 64u : (n <= 128 ? 128u : 256u)); }
+// TMEM allocation (a power of two >= 32 columns) holding n columns; n <= 512.
+__host__ __device__ __forceinline__ uint32_t tmem_cols(int n) {
+  return n <= 32 ? 32u : (n <= 64 ? 64u : (n <= 128 ? 128u : (n <= 256 ? 256u : 512u)));
+}
 
 // voxel index of (i + di, j + dj, k + dk) on a grid of side 2^lg, periodic
 __device__ __forceinline__ int shift_vox(int i, int j, int k, int di, int dj, int dk, int lg) {
@@ -410,19 +413,316 @@ __global__ void __launch_bounds__(128) igemm_wgrad(WgradArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// First layer: the two input features f0 (normalised ln eta) and f1 (the
+// expansion-factor feature) to 16 channels.  One GEMM per 128 voxels with
+// K = 2 x 27 = 54 (padded to 64): A[v][t] = f0(v + d_t), A[v][27 + t] = f1(v + d_t),
+// B[o][t] = W[t][o][0], B[o][27 + t] = W[t][o][1].  The result equals the
+// 16-channel convolution of an input whose channels 2..15 are zero.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(128) stem_conv(const __nv_bfloat162* __restrict__ f2, int lg,
+                                                 const bf16* __restrict__ w, int wcin, const float* __restrict__ bias,
+                                                 bf16* __restrict__ out, int* err) {
+  __shared__ __align__(1024) unsigned char sm[128 * 128 + 16 * 128];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int V = 1 << (3 * lg), m = (1 << lg) - 1;
+  const int v = blockIdx.x * 128 + tid;
+  const bool vok = v < V;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                 "r"(32));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(&bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // K-major canonical layout, element (r, kk) at (r/8)*1024 + (kk/8)*128 + (r%8)*16 + (kk%8)*2
+  const uint32_t sa = su32(sm), sb = sa + 128 * 128;
+  {
+    __align__(16) bf16 row[64];
+#pragma unroll
+    for (int kk = 0; kk < 64; ++kk) row[kk] = __float2bfloat16(0.f);
+    if (vok) {
+      const int i = v >> (2 * lg), j = (v >> lg) & m, k = v & m;
+#pragma unroll
+      for (int t = 0; t < 27; ++t) {
+        const __nv_bfloat162 x = f2[shift_vox(i, j, k, t / 9 - 1, (t / 3) % 3 - 1, t % 3 - 1, lg)];
+        row[t] = x.x;
+        row[27 + t] = x.y;
+      }
+    }
+    const uint32_t d = sa + (tid / 8) * 1024 + (tid % 8) * 16;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint4 q = reinterpret_cast<const uint4*>(row)[c];
+      asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(d + c * 128), "r"(q.x), "r"(q.y), "r"(q.z),
+                   "r"(q.w)
+                   : "memory");
+    }
+  }
+  if (tid < 16) {
+    __align__(16) bf16 row[64];
+#pragma unroll
+    for (int kk = 0; kk < 64; ++kk) row[kk] = __float2bfloat16(0.f);
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+      row[t] = w[((size_t)t * 16 + tid) * wcin];
+      row[27 + t] = w[((size_t)t * 16 + tid) * wcin + 1];
+    }
+    const uint32_t d = sb + (tid / 8) * 1024 + (tid % 8) * 16;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint4 q = reinterpret_cast<const uint4*>(row)[c];
+      asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(d + c * 128), "r"(q.x), "r"(q.y), "r"(q.z),
+                   "r"(q.w)
+                   : "memory");
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  if (tid == 0) {
+    const uint32_t idesc = idesc_bf16(128, 16, 0, 0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      mma_bf16(tmem, sdesc(sa + q * 256, 128, 1024), sdesc(sb + q * 256, 128, 1024), idesc, q > 0 ? 1u : 0u);
+    mma_commit(&bar);
+  }
+  const bool ok = __syncthreads_and(mbar_wait(&bar, 0)) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok) {
+    if (tid == 0) atomicOr(err, 1);
+  } else {
+    float acc[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), acc);
+    if (vok) {
+      __align__(16) bf16 o[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16(fmaxf(acc[j] + bias[j], 0.f));
+      uint4* dst = reinterpret_cast<uint4*>(out + (size_t)v * 16);
+      dst[0] = reinterpret_cast<const uint4*>(o)[0];
+      dst[1] = reinterpret_cast<const uint4*>(o)[1];
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
+}
+
+// ---------------------------------------------------------------------------
+// Line convolution (forward, grids of n >= 32 cells per side).
+//
+// One CTA computes a unit of P = max(n, 128) output positions: one grid row
+// (i, j, 0..n-1) when n >= 128, else R = 128/n consecutive rows of plane i.
+// For every (di, dj) and every 16-channel slice it stages the R source rows
+// (i+di, j+r+dj), all n voxels along k, as the A operand (rows = positions,
+// no gather), and one MMA with N = 3 cout multiplies it by the weights of the
+// three taps dk = -1, 0, 1 at once:
+//     Acc[dk][u][o] += sum_c X[(i+di, j+r+dj, u)][c] W[(di,dj,dk)][o][c].
+// The k shift is applied once, in the epilogue:
+//     out[(i, j+r, k)][o] = b[o] + sum_dk Acc[dk][(k + dk) mod n][o].
+// A source read by nearest upsampling from the half-resolution grid is staged
+// at its own resolution along k (n/2 positions per row, half the MMAs); its
+// epilogue index is ((k + dk) mod n) / 2.
+// ---------------------------------------------------------------------------
+
+struct LineArgs {
+  const bf16* s1;  // c1 channels; grid lg, or lg - 1 when up1
+  const bf16* s2;  // c2 channels on grid lg, or nullptr
+  const bf16* w;   // [27][cout][c1 + c2]
+  const float* bias;
+  bf16* out;       // [V][cout]
+  int c1, up1, c2, lg, cout, relu;
+  int* err;
+};
+
+constexpr int kLS = 6;  // pipeline stages
+constexpr int kStg = 49;  // floats per staged (position, channel group): 3 x 16 + 1 (bank offset)
+
+__host__ __device__ inline int line_tiles(int lg) { return lg >= 7 ? 1 << (lg - 7) : 1; }
+__host__ __device__ inline int line_stage_bytes(int lg, int cout) { return 4096 * line_tiles(lg) + 96 * cout; }
+__host__ __device__ inline int line_tiles1(int lg, int up1) {
+  const int T = line_tiles(lg);
+  return up1 ? (T > 1 ? T / 2 : 1) : T;
+}
+__host__ __device__ inline int line_tmem_cols(int lg, int up1, int c2, int cout) {
+  return 3 * cout * (line_tiles1(lg, up1) + (c2 > 0 ? line_tiles(lg) : 0));
+}
+__host__ __device__ inline int line_smem(int lg, int up1, int c2, int cout) {
+  const int pipe = kLS * line_stage_bytes(lg, cout);
+  const int stg = 128 * (line_tiles1(lg, up1) + (c2 > 0 ? line_tiles(lg) : 0)) * kStg * 4;
+  return pipe > stg ? pipe : stg;
+}
+
+__global__ void __launch_bounds__(128) line_conv(LineArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[kLS];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lg = a.lg, n = 1 << lg, msk = n - 1;
+  const int T = line_tiles(lg), R = lg >= 7 ? 1 : 128 >> lg, P = R * n;
+  const int T1 = line_tiles1(lg, a.up1);
+  const int cout = a.cout, N3 = 3 * cout, kin = a.c1 + a.c2;
+  const int S1 = a.c1 / 16, S2 = a.c2 / 16, nst = 9 * (S1 + S2);
+  const int upp = n / R;  // units per plane
+  const int pi = blockIdx.x / upp, j0 = (blockIdx.x % upp) * R;
+  const int a_bytes = 4096 * T, stage_bytes = a_bytes + 96 * cout;
+  const uint32_t LBOA = 2048u * T, LBOB = 16u * N3;
+  const uint32_t col2 = (uint32_t)(T1 * N3);
+  const uint32_t ncols = tmem_cols(line_tmem_cols(lg, a.up1, a.c2, cout));
+  const uint32_t sbase = su32(smem);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid < kLS) mbar_init(&bars[tid]);
+  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_bf16(128, N3, 0, 0);
+  bool ok = true;
+
+  // A: position p of chunk c (channels 8c..8c+7 of the slice) at c*LBOA + p*16;
+  // B: row dk*cout + o of chunk c at c*LBOB + (dk*cout + o)*16.
+  auto load_stage = [&](int slot, int s) {
+    const int src = s < 9 * S1 ? 0 : 1;
+    const int qq = src ? s - 9 * S1 : s;
+    const int slice = qq / 9, line = qq % 9;
+    const int di = line / 3 - 1, dj = line % 3 - 1;
+    const uint32_t sa = sbase + slot * stage_bytes, sb = sa + a_bytes;
+    const int ri = (pi + di) & msk;
+    const bool up = src == 0 && a.up1;
+    const bf16* base = src ? a.s2 : a.s1;
+    const int C = src ? a.c2 : a.c1, c0 = slice * 16;
+    const int hl = up ? lg - 1 : lg;             // log2 of the staged positions per row
+    const int lv = hl + (lg >= 7 ? 0 : 7 - lg);  // log2 of the staged positions per unit
+    const int nv = 1 << lv;
+    for (int q = tid; q < 2 * nv; q += 128) {
+      const int c = q >> lv, e = q & (nv - 1);
+      const int r = e >> hl, k = e & ((1 << hl) - 1);
+      const int rj = (j0 + r + dj) & msk;
+      const int vox = up ? ((((ri >> 1) << (lg - 1)) | (rj >> 1)) << (lg - 1)) | k : (((ri << lg) | rj) << lg) | k;
+      cp16(sa + c * LBOA + (uint32_t)(r * n + k) * 16u, base + (size_t)vox * C + c0 + 8 * c);
+    }
+    const int tap0 = (di + 1) * 9 + (dj + 1) * 3;
+    const int coff = (src ? a.c1 : 0) + c0;
+    for (int q = tid; q < 2 * N3; q += 128) {
+      const int c = q / N3, nn = q - c * N3;
+      const int dki = nn / cout, o = nn - dki * cout;
+      cp16(sb + c * LBOB + (uint32_t)nn * 16u, a.w + ((size_t)(tap0 + dki) * cout + o) * kin + coff + 8 * c);
+    }
+  };
+
+  // prologue: stages 0 .. kLS-3 in flight; stage s + kLS - 2 is loaded at step s
+  // into the slot last read by the MMAs of step s - 2.
+#pragma unroll
+  for (int s = 0; s < kLS - 2; ++s) {
+    if (s < nst) load_stage(s, s);
+    cp_commit();
+  }
+  for (int s = 0; s < nst; ++s) {
+    const int sn = s + kLS - 2;
+    if (sn < nst) {
+      if (sn >= kLS && ok) ok = mbar_wait(&bars[sn % kLS], ((sn - kLS) / kLS) & 1);
+      if (ok) load_stage(sn % kLS, sn);
+    }
+    cp_commit();
+    cp_wait<kLS - 2>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int src = s < 9 * S1 ? 0 : 1;
+      const bool first = src ? s == 9 * S1 : s == 0;
+      const int Ts = src ? T : T1;
+      const uint32_t col = src ? col2 : 0u;
+      const uint32_t sa = sbase + (s % kLS) * stage_bytes, sb = sa + a_bytes;
+      const uint64_t bd = sdesc(sb, LBOB, 128);
+      for (int t = 0; t < Ts; ++t)
+        mma_bf16(tmem + col + (uint32_t)(t * N3), sdesc(sa + t * 2048, LBOA, 128), bd, idesc, first ? 0u : 1u);
+      mma_commit(&bars[s % kLS]);
+    }
+  }
+  cp_wait<0>();
+  if (ok) ok = mbar_wait(&bars[(nst - 1) % kLS], ((nst - 1) / kLS) & 1);
+  ok = __syncthreads_and(ok) != 0;  // block-uniform from here on
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok && tid == 0) atomicOr(a.err, 1);
+  // epilogue, one group of 16 output channels at a time, through shared memory
+  float* stg = reinterpret_cast<float*>(smem);
+  const int off2 = 128 * T1 * kStg;
+  for (int g = 0; g < cout / 16 && ok; ++g) {
+    for (int src = 0; src < (S2 ? 2 : 1); ++src) {
+      const int Ts = src ? T : T1;
+      const uint32_t col = src ? col2 : 0u;
+      for (int t = 0; t < Ts; ++t)
+        for (int dki = 0; dki < 3; ++dki) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + col + (uint32_t)(t * N3 + dki * cout + g * 16), v);
+          float* d = stg + (src ? off2 : 0) + (t * 128 + warp * 32 + lane) * kStg + dki * 16;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) d[j] = v[j];
+        }
+    }
+    __syncthreads();
+    for (int p = tid; p < P; p += 128) {
+      const int r = p >> lg, k = p & msk;
+      float acc[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = a.bias[g * 16 + j];
+#pragma unroll
+      for (int dki = 0; dki < 3; ++dki) {
+        const int kk = (k + dki - 1) & msk;
+        const float* s1p = stg + (r * n + (a.up1 ? kk >> 1 : kk)) * kStg + dki * 16;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] += s1p[j];
+        if (S2) {
+          const float* s2p = stg + off2 + (r * n + kk) * kStg + dki * 16;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[j] += s2p[j];
+        }
+      }
+      __align__(16) bf16 o[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16(a.relu ? fmaxf(acc[j], 0.f) : acc[j]);
+      uint4* dst = reinterpret_cast<uint4*>(a.out + ((((size_t)pi << lg | (size_t)(j0 + r)) << lg) | k) * cout +
+                                            g * 16);
+      dst[0] = reinterpret_cast<const uint4*>(o)[0];
+      dst[1] = reinterpret_cast<const uint4*>(o)[1];
+    }
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+// ---------------------------------------------------------------------------
 // Element-wise and transfer kernels
 // ---------------------------------------------------------------------------
 
 // Input features: channel 0 = (ln eta - mu) / sd, channel 1 = (a - a0) / sa, others 0.
 __global__ void input_features(const double* __restrict__ eta, int V, float mu, float isd, float afeat,
-                               bf16* __restrict__ x) {
+                               bf16* __restrict__ x, __nv_bfloat162* __restrict__ f2) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
+  const bf16 f0 = __float2bfloat16((logf((float)fmax(eta[v], 1e-30)) - mu) * isd), f1 = __float2bfloat16(afeat);
+  if (f2) f2[v] = __halves2bfloat162(f0, f1);
+  if (!x) return;
   __align__(16) bf16 o[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16(0.f);
-  o[0] = __float2bfloat16((logf((float)fmax(eta[v], 1e-30)) - mu) * isd);
-  o[1] = __float2bfloat16(afeat);
+  o[0] = f0;
+  o[1] = f1;
   uint4* dst = reinterpret_cast<uint4*>(x + (size_t)v * 16);
   dst[0] = reinterpret_cast<const uint4*>(o)[0];
   dst[1] = reinterpret_cast<const uint4*>(o)[1];
@@ -592,9 +892,26 @@ isis_status isis_unet_conv3_fwd(const void* src1, int c1, int lg1, const void* s
   if (c1 < 16 || c1 % 16 || c2 < 0 || c2 % 16 || (c2 > 0 && !src2) || cout < 16 || cout > 64 || cout % 16)
     return ISIS_EINVAL;
   if (!aligned16(src1) || (src2 && !aligned16(src2)) || !aligned16(w) || !aligned16(out)) return ISIS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t V = (size_t)1 << (3 * lg);
+  const double flops = 2.0 * 27.0 * (c1 + c2) * cout * (double)V;
+  const int up1 = lg1 != lg;
+  if (lg >= 5 && lg <= 9 && line_tmem_cols(lg, up1, c2, cout) <= 512 && line_smem(lg, up1, c2, cout) <= 200 * 1024) {
+    static bool lattr = false;
+    if (!lattr) {
+      if (cudaFuncSetAttribute(line_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+        return ISIS_ECUDA;
+      lattr = true;
+    }
+    LineArgs la{(const bf16*)src1, (const bf16*)src2, (const bf16*)w, bias, (bf16*)out, c1, up1, c2, lg, cout,
+                relu, err};
+    const int P = lg >= 7 ? 1 << lg : 128;
+    UNET_LAUNCH(isis::KK_UNET_CONV, flops, st,
+                (line_conv<<<(unsigned)(V / P), 128, line_smem(lg, up1, c2, cout), st>>>(la)));
+    return ISIS_OK;
+  }
   ConvArgs a{(const bf16*)src1, (const bf16*)src2, (const bf16*)w, bias, (bf16*)out, nullptr,
              c1, lg1, c2, lg, cout, relu, +1, err};
-  cudaStream_t st = (cudaStream_t)stream;
   const size_t smem = (size_t)kStages * conv_stage_bytes(cout);
   static bool attr = false;
   if (!attr) {
@@ -602,8 +919,6 @@ isis_status isis_unet_conv3_fwd(const void* src1, int c1, int lg1, const void* s
       return ISIS_ECUDA;
     attr = true;
   }
-  const size_t V = (size_t)1 << (3 * lg);
-  const double flops = 2.0 * 27.0 * (c1 + c2) * cout * (double)V;
   UNET_LAUNCH(isis::KK_UNET_CONV, flops, st, (igemm_conv<0><<<nb(V, 128), 128, smem, st>>>(a)));
   return ISIS_OK;
 }
@@ -656,12 +971,28 @@ isis_status isis_unet_conv3_wgrad(const void* src1, int c1, int lg1, const void*
   return ISIS_OK;
 }
 
-isis_status isis_unet_input(const double* eta, int lg, float mu, float isd, float afeat, void* x16, void* stream) {
-  if (!eta || !x16 || lg < 2 || lg > 10) return ISIS_EINVAL;
+isis_status isis_unet_input(const double* eta, int lg, float mu, float isd, float afeat, void* x16, void* f2,
+                            void* stream) {
+  if (!eta || (!x16 && !f2) || lg < 2 || lg > 10) return ISIS_EINVAL;
+  if ((x16 && !aligned16(x16)) || (f2 && ((uintptr_t)f2 & 3u))) return ISIS_EINVAL;
   const int V = 1 << (3 * lg);
   cudaStream_t st = (cudaStream_t)stream;
-  UNET_LAUNCH(isis::KK_UNET_ELEM, 40.0 * V, st,
-              (input_features<<<nb(V, 256), 256, 0, st>>>(eta, V, mu, isd, afeat, (bf16*)x16)));
+  UNET_LAUNCH(isis::KK_UNET_ELEM, (8.0 + (x16 ? 32.0 : 0.0) + (f2 ? 4.0 : 0.0)) * V, st,
+              (input_features<<<nb(V, 256), 256, 0, st>>>(eta, V, mu, isd, afeat, (bf16*)x16,
+                                                          (__nv_bfloat162*)f2)));
+  return ISIS_OK;
+}
+
+isis_status isis_unet_stem_fwd(const void* f2, int lg, const void* w, int wcin, const float* bias, void* out,
+                               int* err, void* stream) {
+  if (!f2 || !w || !bias || !out || !err || lg < 2 || lg > 10 || wcin < 2 || wcin % 8) return ISIS_EINVAL;
+  if (((uintptr_t)f2 & 3u) || !aligned16(out)) return ISIS_EINVAL;
+  const size_t V = (size_t)1 << (3 * lg);
+  cudaStream_t st = (cudaStream_t)stream;
+  const double flops = 2.0 * 27.0 * 2.0 * 16.0 * (double)V;
+  UNET_LAUNCH(isis::KK_UNET_CONV, flops, st,
+              (stem_conv<<<nb(V, 128), 128, 0, st>>>((const __nv_bfloat162*)f2, lg, (const bf16*)w, wcin, bias,
+                                                       (bf16*)out, err)));
   return ISIS_OK;
 }
 

@@ -42,7 +42,8 @@ def _lib():
         "isis_unet_conv3_fwd": [vp, i, i, vp, i, i, vp, vp, i, i, vp, vp, vp],
         "isis_unet_conv3_dgrad": [vp, i, i, vp, i, vp, vp, vp],
         "isis_unet_conv3_wgrad": [vp, i, i, vp, i, i, vp, i, vp, vp, vp],
-        "isis_unet_input": [vp, i, f, f, f, vp, vp],
+        "isis_unet_input": [vp, i, f, f, f, vp, vp, vp],
+        "isis_unet_stem_fwd": [vp, i, vp, i, vp, vp, vp, vp],
         "isis_unet_pool_fwd": [vp, i, i, vp, vp],
         "isis_unet_pool_bwd": [vp, i, i, vp, vp],
         "isis_unet_relu_bwd": [vp, vp, ctypes.c_int64, vp, vp],
@@ -155,7 +156,7 @@ class UNet:
         V = [1 << (3 * (lg - l)) for l in range(4)]
         bf = dict(device=self.dev, dtype=torch.bfloat16)
         f32 = dict(device=self.dev, dtype=torch.float32)
-        A = {"x0": torch.empty(V[0] * 16, **bf), "e0": torch.empty(V[0] * 16, **bf),
+        A = {"x0": torch.empty(V[0] * 16, **bf), "f2": torch.empty(V[0] * 2, **bf), "e0": torch.empty(V[0] * 16, **bf),
              "p0": torch.empty(V[1] * 16, **bf), "e1": torch.empty(V[1] * 32, **bf),
              "p1": torch.empty(V[2] * 32, **bf), "e2": torch.empty(V[2] * 64, **bf),
              "p2": torch.empty(V[3] * 64, **bf), "e3": torch.empty(V[3] * 64, **bf),
@@ -180,13 +181,14 @@ class UNet:
         return B
 
     # -- forward ----------------------------------------------------------
-    def features(self, eta: torch.Tensor, a: float, lg: int):
+    def features(self, eta: torch.Tensor, a: float, lg: int, x16: bool = True):
+        """The two input features (f2) and, for training, their 16-channel form (x0)."""
         V, A = self.acts(lg)
-        _ck(_lib().isis_unet_input(_p(eta), lg, self.mu, 1.0 / self.sd, (a - 0.9) / 0.1, _p(A["x0"]), _s()),
-            "unet_input")
+        _ck(_lib().isis_unet_input(_p(eta), lg, self.mu, 1.0 / self.sd, (a - 0.9) / 0.1,
+                                   _p(A["x0"]) if x16 else None, _p(A["f2"]), _s()), "unet_input")
 
     def forward(self, lg: int, pred=True):
-        """Forward pass on the features already in acts(lg)['x0']."""
+        """Forward pass on the features already in acts(lg)['f2']."""
         lib, s = _lib(), _s()
         V, A = self.acts(lg)
         P, Pb, err = self.P, self.Pb, self.err
@@ -198,7 +200,8 @@ class UNet:
         def pool(x, C, lgc, y):
             _ck(lib.isis_unet_pool_fwd(_p(x), C, lgc, _p(y), s), "pool")
 
-        conv("e0", A["x0"], 16, lg, None, 0, lg, A["e0"], 16)
+        _ck(lib.isis_unet_stem_fwd(_p(A["f2"]), lg, _p(self.view(Pb, "e0.W")), 16, _p(self.view(P, "e0.b")),
+                                   _p(A["e0"]), _p(err), s), "e0")
         pool(A["e0"], 16, lg - 1, A["p0"])
         conv("e1", A["p0"], 16, lg - 1, None, 0, lg - 1, A["e1"], 32)
         pool(A["e1"], 32, lg - 2, A["p1"])
@@ -272,7 +275,7 @@ class UNet:
         """phi = chi_bg(a) + scale * net(eta, a): FP64 initial guess for isis_scalar_solve."""
         N = eta.shape[0]
         lg = int(round(math.log2(N)))
-        self.features(eta, a, lg)
+        self.features(eta, a, lg, x16=False)
         pred = self.forward(lg)
         _ck(_lib().isis_unet_guess(_p(pred), lg, isis.chi_background(a, a_ssb), self.scale, _p(phi), _s()), "guess")
         return phi

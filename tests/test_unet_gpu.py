@@ -125,3 +125,85 @@ def test_network_gradient_direction(cuda_lib):
         cos = got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref) + 1e-300)
         assert cos >= 0.98, (k, cos)
         assert abs(np.linalg.norm(got) / np.linalg.norm(ref) - 1) <= 0.1, k
+
+
+def _sampled_conv_ref(s1, c1, up, s2, c2, lg, W, b, vs):
+    """FP64 reference of the convolution at the voxels vs only (neighbours gathered on the device)."""
+    n = 1 << lg
+    i, j, k = vs // (n * n), (vs // n) % n, vs % n
+    ref = np.zeros((len(vs), W.shape[1]))
+    for t, (di, dj, dk) in enumerate(U.TAPS):
+        ii, jj, kk = (i + di) % n, (j + dj) % n, (k + dk) % n
+        if up:
+            nc = n // 2
+            u1 = ((ii // 2) * nc + jj // 2) * nc + kk // 2
+        else:
+            u1 = (ii * n + jj) * n + kk
+        X = _np(s1.view(-1, c1)[torch.from_numpy(u1).cuda()])
+        if c2:
+            u2 = (ii * n + jj) * n + kk
+            X = np.concatenate([X, _np(s2.view(-1, c2)[torch.from_numpy(u2).cuda()])], axis=1)
+        ref += X @ W[t].T
+    return U.relu(ref + b)
+
+
+@pytest.mark.parametrize("lg,c1,up,c2,cout", [(5, 16, 0, 0, 32), (5, 64, 1, 64, 64), (6, 32, 1, 16, 16),
+                                              (6, 64, 0, 0, 64), (7, 64, 1, 32, 32), (7, 16, 0, 0, 16),
+                                              (8, 32, 1, 16, 16), (8, 16, 0, 0, 32), (9, 32, 1, 16, 16)])
+def test_line_conv_forward(lib, lg, c1, up, c2, cout):
+    """The line kernel (grids of 32..512 cells): every voxel of a plane at each end, rows at the
+    j wrap, the k wrap and random voxels, against the FP64 reference."""
+    n = 1 << lg
+    gen = torch.Generator(device="cuda").manual_seed(lg * 1000 + c1 + c2 + cout + up)
+    n1 = n >> up
+    s1 = torch.randn(n1 ** 3 * c1, generator=gen, device="cuda").to(torch.bfloat16)
+    s2 = torch.randn(n ** 3 * c2, generator=gen, device="cuda").to(torch.bfloat16) if c2 else None
+    W = (0.1 * torch.randn(27 * cout * (c1 + c2), generator=gen, device="cuda")).to(torch.bfloat16)
+    b = torch.randn(cout, generator=gen, device="cuda")
+    out = torch.empty(n ** 3 * cout, dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lib.isis_unet_conv3_fwd(_p(s1), c1, lg - up, _p(s2), c2, lg, _p(W), _p(b), cout, 1, _p(out), _p(err),
+                                   _s()) == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    rng = np.random.Generator(np.random.PCG64(lg))
+    plane0 = np.arange(n * n)
+    planeL = (n - 1) * n * n + np.arange(n * n)
+    if n > 64:
+        plane0, planeL = plane0[rng.choice(n * n, 2048, replace=False)], planeL[rng.choice(n * n, 2048, replace=False)]
+    vs = np.unique(np.concatenate([plane0, planeL, rng.integers(0, n ** 3, 4096),
+                                   (n // 2) * n * n + (n - 1) * n + np.arange(n),   # last row of a plane (j wrap)
+                                   (np.arange(n) * n + 3) * n + n - 1]))            # k = n - 1 (k wrap)
+    Wn = _np(W).reshape(27, cout, c1 + c2)
+    ref = _sampled_conv_ref(s1, c1, up, s2, c2, lg, Wn, b.cpu().numpy().astype(np.float64), vs)
+    got = _np(out.view(-1, cout)[torch.from_numpy(vs).cuda()])
+    assert np.abs(got - ref).max() <= 2 ** -7 * np.abs(ref).max() + 1e-6
+
+
+@pytest.mark.parametrize("lg", [3, 5, 7])
+def test_stem_equals_conv_of_features(lib, lg):
+    """First layer from the two features vs the FP64 convolution of the 16-channel features."""
+    from paper_1307_6748_gb300 import synth
+    n = 1 << lg
+    eta = synth.lognormal_eta(n, float(n), 1.5, 11).cuda()
+    x16 = torch.empty(n ** 3 * 16, dtype=torch.bfloat16, device="cuda")
+    f2 = torch.empty(n ** 3 * 2, dtype=torch.bfloat16, device="cuda")
+    assert lib.isis_unet_input(_p(eta), lg, -1.125, 1 / 1.5, 0.7, _p(x16), _p(f2), _s()) == 0
+    g = np.random.Generator(np.random.PCG64(lg))
+    W = _bf(g.standard_normal((27, 16, 16)) * 0.2)
+    b = torch.from_numpy(g.standard_normal(16).astype(np.float32)).cuda()
+    out = torch.empty(n ** 3 * 16, dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lib.isis_unet_stem_fwd(_p(f2), lg, _p(W), 16, _p(b), _p(out), _p(err), _s()) == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    X = _np(x16).reshape(-1, 16)
+    assert np.all(X[:, 2:] == 0) and np.array_equal(X[:, :2], _np(f2).reshape(-1, 2))
+    if lg <= 5:
+        ref = U.relu(U.conv3_fwd(X.reshape(n, n, n, 16), _np(W), b.cpu().numpy().astype(np.float64))).reshape(-1, 16)
+        got = _np(out).reshape(-1, 16)
+    else:
+        vs = np.random.Generator(np.random.PCG64(1)).integers(0, n ** 3, 8192)
+        ref = _sampled_conv_ref(x16, 16, 0, None, 0, lg, _np(W), b.cpu().numpy().astype(np.float64), vs)
+        got = _np(out.view(-1, 16)[torch.from_numpy(vs).cuda()])
+    assert np.abs(got - ref).max() <= 2 ** -7 * np.abs(ref).max() + 1e-6
