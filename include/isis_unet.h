@@ -12,9 +12,11 @@
  * Conventions
  *   - A grid has n = 2^lg cells per side (2 <= lg <= 10), V = n^3 voxels in
  *     row-major order ((i n + j) n + k), periodic.
- *   - Activations are BF16, voxel-major [v][c], with c a multiple of 16;
- *     gradients of activations are FP32 in the same layout.  All pointers are
- *     device pointers owned by the caller, 16-byte aligned.
+ *   - Activations are BF16 with C channels (a multiple of 16), stored
+ *     channel-planar in groups of 8: element (v, c) at ((c / 8) V + v) 8 + c % 8,
+ *     so that one grid row of one 8-channel group is a contiguous block of
+ *     n x 16 bytes.  Gradients of activations are FP32 in the same layout.  All
+ *     pointers are device pointers owned by the caller, 16-byte aligned.
  *   - 3x3x3 convolution, tap t = (di+1)*9 + (dj+1)*3 + (dk+1) for the offset
  *     (di, dj, dk) in {-1,0,1}^3, periodic wrap:
  *       out[v][o] = b[o] + sum_t sum_i X[v + d_t][i] W[t][o][i],   W: BF16 [27][cout][cin]
@@ -35,13 +37,30 @@
 extern "C" {
 #endif
 
-/* out (BF16 [V][cout]) = optional ReLU of the convolution plus bias (FP32 [cout]).
- * 16 <= c1, 0 <= c2, c1 + c2 <= 128, 16 <= cout <= 64, all multiples of 16.
- * Grids of 32..512 cells per side take the line kernel (whole grid rows staged
- * once per (di, dj), the three k taps in one MMA, the k shift in the epilogue);
- * smaller grids the per-voxel gather kernel. */
+/* out (BF16, cout channels) = optional ReLU of the convolution plus bias (FP32 [cout]),
+ * any grid; the A operand is gathered per voxel and tap.
+ * 16 <= c1, 0 <= c2, c1 + c2 <= 128, 16 <= cout <= 64, all multiples of 16. */
 isis_status isis_unet_conv3_fwd(const void* src1, int c1, int lg1, const void* src2, int c2, int lg, const void* w,
                                 const float* bias, int cout, int relu, void* out, int* err, void* stream);
+
+/* Weights packed for isis_unet_line_fwd: for stage s (16-channel slice s / 9 of
+ * the cin input channels, line s % 9 = (di + 1) * 3 + (dj + 1)),
+ *   wl[s][c][dk * cout + o][e] = W[3 (s % 9) + dk][o][16 (s / 9) + 8 c + e],
+ * c in {0, 1}, dk in {0, 1, 2}, e < 8; wl has the size of w. */
+isis_status isis_unet_pack_w(const void* w, int cout, int cin, void* wl, void* stream);
+
+/* 1 if isis_unet_line_fwd takes these sizes: grids of 32..512 cells per side and
+ * the accumulators and shared-memory stages fit one SM. */
+int isis_unet_line_ok(int c1, int lg1, int c2, int lg, int cout);
+
+/* The same convolution as isis_unet_conv3_fwd with weights wl packed by
+ * isis_unet_pack_w (cin = c1 + c2).  One CTA per SM computes whole grid rows:
+ * for each (di, dj) and 16-channel slice, the source rows are bulk-copied once
+ * (no per-voxel gather) and one tcgen05 MMA with N = 3 cout applies the three
+ * k taps at once; the k shift is applied in the epilogue.  An upsampled src1 is
+ * staged at its own resolution.  ISIS_EINVAL where isis_unet_line_ok is 0. */
+isis_status isis_unet_line_fwd(const void* src1, int c1, int lg1, const void* src2, int c2, int lg, const void* wl,
+                               const float* bias, int cout, int relu, void* out, int* err, void* stream);
 
 /* Input gradient: din (FP32 [V][cin]) = sum_t sum_o dz[v - d_t][o] W[t][o][i],
  * with wt = W transposed per tap (BF16 [27][cin][cout], isis_unet_transpose_w),

@@ -6,7 +6,10 @@
 // the multigrid solver always finishes the solve.
 //
 // Tensors: a grid of n = 2^lg cells per side, V = n^3 voxels in row-major
-// order, C channels (a multiple of 16), BF16, voxel-major: element [v][c].
+// order, C channels (a multiple of 16), stored channel-planar in groups of 8:
+// element (v, c) at ((c / 8) V + v) 8 + c % 8.  A grid row of one 8-channel
+// group is then one contiguous block (n x 16 bytes for BF16), which the line
+// convolution fetches with single bulk copies.
 // A 3x3x3 convolution with periodic wrap:
 //     out[v][o] = b[o] + sum_{t < 27} sum_i X[v + d_t][i] W[t][o][i]
 // tap t = (di+1)*9 + (dj+1)*3 + (dk+1), d_t = (di, dj, dk) in {-1, 0, 1}^3.
@@ -23,6 +26,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "../../include/isis_unet.h"
 #include "isis_prof.cuh"
@@ -76,6 +80,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
+// Polling wait (mbarrier.test_wait never suspends the thread), then the bounded
+// blocking wait above; false if both gave up.
+__device__ __forceinline__ bool mbar_wait_spin(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 14); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return mbar_wait(bar, parity);
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -105,6 +124,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 __host__ __device__ __forceinline__ uint32_t tmem_cols(int n) {
   return n <= 32 ? 32u : (n <= 64 ? 64u : (n <= 128 ? 128u : (n <= 256 ? 256u : 512u)));
 }
+
+// element (v, c) of a channel-planar tensor with V voxels
+__device__ __forceinline__ size_t pidx(size_t v, int c, size_t V) { return (((size_t)(c >> 3) * V + v) << 3) | (c & 7); }
 
 // voxel index of (i + di, j + dj, k + dk) on a grid of side 2^lg, periodic
 __device__ __forceinline__ int shift_vox(int i, int j, int k, int di, int dj, int dk, int lg) {
@@ -186,7 +208,7 @@ __global__ void __launch_bounds__(128) igemm_conv(ConvArgs a) {
       // A: this thread's voxel row
       const uint32_t da = sa + (tid / 8) * SBO + koff + (tid % 8) * 16;
       if (vok) {
-        const bf16* src;
+        const bf16 *src, *src8;  // channels c0..c0+7 and c0+8..c0+15 (two 8-channel planes)
         if (c0 < a.c1) {
           const int u = shift_vox(vi, vj, vk, di, dj, dk, lg);
           int uu = u;
@@ -194,13 +216,16 @@ __global__ void __launch_bounds__(128) igemm_conv(ConvArgs a) {
             const int ui = u >> (2 * lg), uj = (u >> lg) & m, uk = u & m;
             uu = (((ui >> 1) << (lg - 1) | (uj >> 1)) << (lg - 1)) | (uk >> 1);
           }
-          src = a.s1 + (size_t)uu * a.c1 + c0;
+          const size_t V1 = (size_t)1 << (3 * a.lg1);
+          src = a.s1 + pidx(uu, c0, V1);
+          src8 = a.s1 + pidx(uu, c0 + 8, V1);
         } else {
           const int u = shift_vox(vi, vj, vk, di, dj, dk, lg);
-          src = a.s2 + (size_t)u * a.c2 + (c0 - a.c1);
+          src = a.s2 + pidx(u, c0 - a.c1, (size_t)V);
+          src8 = a.s2 + pidx(u, c0 - a.c1 + 8, (size_t)V);
         }
         cp16(da, src);
-        cp16(da + 128, src + 8);
+        cp16(da + 128, src8);
       } else {
         cp_zero16(da);
         cp_zero16(da + 128);
@@ -261,13 +286,15 @@ __global__ void __launch_bounds__(128) igemm_conv(ConvArgs a) {
             if (a.relu) y = fmaxf(y, 0.f);
             o[j] = __float2bfloat16(y);
           }
-          uint4* dst = reinterpret_cast<uint4*>(a.out_bf + (size_t)v * ncol + c0);
-          dst[0] = reinterpret_cast<const uint4*>(o)[0];
-          dst[1] = reinterpret_cast<const uint4*>(o)[1];
+          *reinterpret_cast<uint4*>(a.out_bf + pidx(v, c0, (size_t)V)) = reinterpret_cast<const uint4*>(o)[0];
+          *reinterpret_cast<uint4*>(a.out_bf + pidx(v, c0 + 8, (size_t)V)) = reinterpret_cast<const uint4*>(o)[1];
         } else {
-          float4* dst = reinterpret_cast<float4*>(a.out_f + (size_t)v * ncol + c0);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) dst[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+          float4* d0 = reinterpret_cast<float4*>(a.out_f + pidx(v, c0, (size_t)V));
+          float4* d1 = reinterpret_cast<float4*>(a.out_f + pidx(v, c0 + 8, (size_t)V));
+          d0[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+          d0[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+          d1[0] = make_float4(acc[8], acc[9], acc[10], acc[11]);
+          d1[1] = make_float4(acc[12], acc[13], acc[14], acc[15]);
         }
       }
     }
@@ -349,9 +376,9 @@ __global__ void __launch_bounds__(128) igemm_wgrad(WgradArgs a) {
           const int ui = u >> (2 * lg), uj = (u >> lg) & m, uk = u & m;
           uu = (((ui >> 1) << (lg - 1) | (uj >> 1)) << (lg - 1)) | (uk >> 1);
         }
-        src = a.s1 + (size_t)uu * a.c1 + ci;
+        src = a.s1 + pidx(uu, ci, (size_t)1 << (3 * a.lg1));
       } else {
-        src = a.s2 + (size_t)u * a.c2 + (ci - a.c1);
+        src = a.s2 + pidx(u, ci - a.c1, (size_t)V);
       }
       cp16(dst, src);
     }
@@ -362,7 +389,7 @@ __global__ void __launch_bounds__(128) igemm_wgrad(WgradArgs a) {
       const uint32_t dst = sb + g * 128 + (kv / 8) * LBOB + (kv % 8) * 16;
       const int vv = vb + s * kvox + kv;
       if (vv >= ve) cp_zero16(dst);
-      else cp16(dst, a.dz + (size_t)vv * cout + g * 8);
+      else cp16(dst, a.dz + pidx(vv, g * 8, (size_t)V));
     }
   };
 
@@ -504,9 +531,8 @@ __global__ void __launch_bounds__(128) stem_conv(const __nv_bfloat162* __restric
       __align__(16) bf16 o[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16(fmaxf(acc[j] + bias[j], 0.f));
-      uint4* dst = reinterpret_cast<uint4*>(out + (size_t)v * 16);
-      dst[0] = reinterpret_cast<const uint4*>(o)[0];
-      dst[1] = reinterpret_cast<const uint4*>(o)[1];
+      *reinterpret_cast<uint4*>(out + pidx(v, 0, (size_t)V)) = reinterpret_cast<const uint4*>(o)[0];
+      *reinterpret_cast<uint4*>(out + pidx(v, 8, (size_t)V)) = reinterpret_cast<const uint4*>(o)[1];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -517,11 +543,11 @@ __global__ void __launch_bounds__(128) stem_conv(const __nv_bfloat162* __restric
 // ---------------------------------------------------------------------------
 // Line convolution (forward, grids of n >= 32 cells per side).
 //
-// One CTA computes a unit of P = max(n, 128) output positions: one grid row
-// (i, j, 0..n-1) when n >= 128, else R = 128/n consecutive rows of plane i.
-// For every (di, dj) and every 16-channel slice it stages the R source rows
-// (i+di, j+r+dj), all n voxels along k, as the A operand (rows = positions,
-// no gather), and one MMA with N = 3 cout multiplies it by the weights of the
+// A unit is P = max(n, 128) output positions: one grid row (i, j, 0..n-1)
+// when n >= 128, else R = 128/n consecutive rows of plane i.  For every
+// (di, dj) and every 16-channel slice of a source, the R source rows
+// (i+di, j+r+dj), all voxels along k, are the A operand (rows = positions, no
+// gather), and one MMA with N = 3 cout multiplies it by the weights of the
 // three taps dk = -1, 0, 1 at once:
 //     Acc[dk][u][o] += sum_c X[(i+di, j+r+dj, u)][c] W[(di,dj,dk)][o][c].
 // The k shift is applied once, in the epilogue:
@@ -529,181 +555,363 @@ __global__ void __launch_bounds__(128) stem_conv(const __nv_bfloat162* __restric
 // A source read by nearest upsampling from the half-resolution grid is staged
 // at its own resolution along k (n/2 positions per row, half the MMAs); its
 // epilogue index is ((k + dk) mod n) / 2.
+//
+// Persistent CTAs with three roles: warp 0 issues the bulk copies (a source
+// row of one 8-channel plane is one contiguous block, so a stage is 2R + 1
+// copies: the A rows of both planes of the slice and the stage's pre-packed
+// weights), warp 1 the tcgen05 MMAs, warps 2..5 the epilogue.  Accumulators
+// are double buffered in TMEM so the epilogue of one unit overlaps the MMAs
+// of the next.  Operands use the no-swizzle K-major layout: 8-channel chunk
+// planes of 16-byte rows.
 // ---------------------------------------------------------------------------
 
 struct LineArgs {
-  const bf16* s1;  // c1 channels; grid lg, or lg - 1 when up1
-  const bf16* s2;  // c2 channels on grid lg, or nullptr
-  const bf16* w;   // [27][cout][c1 + c2]
+  const bf16* s1;  // c1 channels; grid lg, or lg - 1 when up1 (channel-planar)
+  const bf16* s2;  // c2 channels on grid lg (channel-planar), or nullptr
+  const bf16* wl;  // weights packed per stage (isis_unet_pack_w)
   const float* bias;
-  bf16* out;       // [V][cout]
-  int c1, up1, c2, lg, cout, relu;
+  bf16* out;  // cout channels on grid lg (channel-planar)
+  int c1, up1, c2, lg, cout, relu, nunits, nls;
   int* err;
 };
 
-constexpr int kLS = 6;  // pipeline stages
-constexpr int kStg = 49;  // floats per staged (position, channel group): 3 x 16 + 1 (bank offset)
+#ifndef ISIS_LINE_STAGES
+#define ISIS_LINE_STAGES 4
+#endif
+constexpr int kLS = ISIS_LINE_STAGES;  // pipeline stages
+constexpr int kStg = 52;  // floats per staged (position, channel group): 3 x 16 + 4
 
 __host__ __device__ inline int line_tiles(int lg) { return lg >= 7 ? 1 << (lg - 7) : 1; }
-__host__ __device__ inline int line_stage_bytes(int lg, int cout) { return 4096 * line_tiles(lg) + 96 * cout; }
 __host__ __device__ inline int line_tiles1(int lg, int up1) {
   const int T = line_tiles(lg);
   return up1 ? (T > 1 ? T / 2 : 1) : T;
 }
-__host__ __device__ inline int line_tmem_cols(int lg, int up1, int c2, int cout) {
+// positions (16-byte rows) per chunk plane of a stage: the source rows j-1..j+1 (n >= 128) or
+// j0-1 .. j0+R of the R output rows (n < 128), n positions each
+__host__ __device__ inline int line_pa(int lg) { return lg >= 7 ? 3 << lg : 128 + (2 << lg); }
+__host__ __device__ inline int line_stage_bytes(int lg, int cout) { return 32 * line_pa(lg) + 288 * cout; }
+__host__ __device__ inline int line_unit_cols(int lg, int up1, int c2, int cout) {
   return 3 * cout * (line_tiles1(lg, up1) + (c2 > 0 ? line_tiles(lg) : 0));
 }
-__host__ __device__ inline int line_smem(int lg, int up1, int c2, int cout) {
-  const int pipe = kLS * line_stage_bytes(lg, cout);
-  const int stg = 128 * (line_tiles1(lg, up1) + (c2 > 0 ? line_tiles(lg) : 0)) * kStg * 4;
-  return pipe > stg ? pipe : stg;
+__host__ __device__ inline int line_nbuf(int lg, int up1, int c2, int cout) {
+  return 2 * line_unit_cols(lg, up1, c2, cout) <= 512 ? 2 : 1;
+}
+__host__ __device__ inline int line_stg_bytes(int lg, int up1, int c2) {
+  return 128 * (line_tiles1(lg, up1) + (c2 > 0 ? line_tiles(lg) : 0)) * kStg * 4;
+}
+__host__ __device__ inline int line_smem_n(int lg, int up1, int c2, int cout, int nls) {
+  return 1024 + nls * line_stage_bytes(lg, cout) + line_stg_bytes(lg, up1, c2);
+}
+// the most pipeline stages (2..kLS) whose shared memory fits 220 KB; 0 if none
+__host__ __device__ inline int line_nls(int lg, int up1, int c2, int cout) {
+  for (int k = kLS; k >= 2; --k)
+    if (line_smem_n(lg, up1, c2, cout, k) <= 220 * 1024) return k;
+  return 0;
 }
 
-__global__ void __launch_bounds__(128) line_conv(LineArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[kLS];
+// Bulk asynchronous copy of `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) from global to shared memory, completing on the mbarrier's tx count.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_n(uint64_t* bar, int n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(192, 1) line_conv(const __grid_constant__ LineArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[kLS], empty[kLS], accf[2], acce[2];
   __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_err, s_stop;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int lg = a.lg, n = 1 << lg, msk = n - 1;
   const int T = line_tiles(lg), R = lg >= 7 ? 1 : 128 >> lg, P = R * n;
   const int T1 = line_tiles1(lg, a.up1);
-  const int cout = a.cout, N3 = 3 * cout, kin = a.c1 + a.c2;
-  const int S1 = a.c1 / 16, S2 = a.c2 / 16, nst = 9 * (S1 + S2);
+  const int cout = a.cout, N3 = 3 * cout;
+  const int S1 = a.c1 / 16, S2 = a.c2 / 16;
   const int upp = n / R;  // units per plane
-  const int pi = blockIdx.x / upp, j0 = (blockIdx.x % upp) * R;
-  const int a_bytes = 4096 * T, stage_bytes = a_bytes + 96 * cout;
-  const uint32_t LBOA = 2048u * T, LBOB = 16u * N3;
+  const int PA = line_pa(lg), a_bytes = 32 * PA, stage_bytes = a_bytes + 288 * cout;
+  const uint32_t ucols = (uint32_t)line_unit_cols(lg, a.up1, a.c2, cout);
+  const int nbuf = line_nbuf(lg, a.up1, a.c2, cout);
+  const uint32_t ncols = tmem_cols(nbuf * ucols);
   const uint32_t col2 = (uint32_t)(T1 * N3);
-  const uint32_t ncols = tmem_cols(line_tmem_cols(lg, a.up1, a.c2, cout));
-  const uint32_t sbase = su32(smem);
+  // A: position p of chunk plane c at c * LBOA + p * 16 (source row slot q at positions q n);
+  // B: block dj (of 3), row dk * cout + o of chunk c at dj * 96 cout + c * LBOB + row * 16
+  const uint32_t LBOA = 16u * PA, LBOB = 16u * N3;
+  // 1024-byte aligned base for the swizzled stages, then the epilogue staging
+  const uint32_t sraw = su32(smem_raw), sbase = (sraw + 1023u) & ~1023u;
+  float* stg = reinterpret_cast<float*>(smem_raw + (sbase - sraw) + a.nls * stage_bytes);
+  const int nit = (a.nunits - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // units of this CTA
+  const int nls = a.nls;  // pipeline stages in use (<= kLS)
 
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid < kLS) mbar_init(&bars[tid]);
-  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (tid == 0) {
+    for (int s = 0; s < kLS; ++s) {  // all kLS barriers initialised; nls in use
+      mbar_init_n(&full[s], 1);
+      mbar_init_n(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init_n(&accf[b], 1);
+      mbar_init_n(&acce[b], 128);
+    }
+    s_err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  const uint32_t idesc = idesc_bf16(128, N3, 0, 0);
-  bool ok = true;
 
-  // A: position p of chunk c (channels 8c..8c+7 of the slice) at c*LBOA + p*16;
-  // B: row dk*cout + o of chunk c at c*LBOB + (dk*cout + o)*16.
-  auto load_stage = [&](int slot, int s) {
-    const int src = s < 9 * S1 ? 0 : 1;
-    const int qq = src ? s - 9 * S1 : s;
-    const int slice = qq / 9, line = qq % 9;
-    const int di = line / 3 - 1, dj = line % 3 - 1;
-    const uint32_t sa = sbase + slot * stage_bytes, sb = sa + a_bytes;
-    const int ri = (pi + di) & msk;
-    const bool up = src == 0 && a.up1;
-    const bf16* base = src ? a.s2 : a.s1;
-    const int C = src ? a.c2 : a.c1, c0 = slice * 16;
-    const int hl = up ? lg - 1 : lg;             // log2 of the staged positions per row
-    const int lv = hl + (lg >= 7 ? 0 : 7 - lg);  // log2 of the staged positions per unit
-    const int nv = 1 << lv;
-    for (int q = tid; q < 2 * nv; q += 128) {
-      const int c = q >> lv, e = q & (nv - 1);
-      const int r = e >> hl, k = e & ((1 << hl) - 1);
-      const int rj = (j0 + r + dj) & msk;
-      const int vox = up ? ((((ri >> 1) << (lg - 1)) | (rj >> 1)) << (lg - 1)) | k : (((ri << lg) | rj) << lg) | k;
-      cp16(sa + c * LBOA + (uint32_t)(r * n + k) * 16u, base + (size_t)vox * C + c0 + 8 * c);
-    }
-    const int tap0 = (di + 1) * 9 + (dj + 1) * 3;
-    const int coff = (src ? a.c1 : 0) + c0;
-    for (int q = tid; q < 2 * N3; q += 128) {
-      const int c = q / N3, nn = q - c * N3;
-      const int dki = nn / cout, o = nn - dki * cout;
-      cp16(sb + c * LBOB + (uint32_t)nn * 16u, a.w + ((size_t)(tap0 + dki) * cout + o) * kin + coff + 8 * c);
-    }
-  };
-
-  // prologue: stages 0 .. kLS-3 in flight; stage s + kLS - 2 is loaded at step s
-  // into the slot last read by the MMAs of step s - 2.
-#pragma unroll
-  for (int s = 0; s < kLS - 2; ++s) {
-    if (s < nst) load_stage(s, s);
-    cp_commit();
-  }
-  for (int s = 0; s < nst; ++s) {
-    const int sn = s + kLS - 2;
-    if (sn < nst) {
-      if (sn >= kLS && ok) ok = mbar_wait(&bars[sn % kLS], ((sn - kLS) / kLS) & 1);
-      if (ok) load_stage(sn % kLS, sn);
-    }
-    cp_commit();
-    cp_wait<kLS - 2>();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0 && ok) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int src = s < 9 * S1 ? 0 : 1;
-      const bool first = src ? s == 9 * S1 : s == 0;
-      const int Ts = src ? T : T1;
-      const uint32_t col = src ? col2 : 0u;
-      const uint32_t sa = sbase + (s % kLS) * stage_bytes, sb = sa + a_bytes;
-      const uint64_t bd = sdesc(sb, LBOB, 128);
-      for (int t = 0; t < Ts; ++t)
-        mma_bf16(tmem + col + (uint32_t)(t * N3), sdesc(sa + t * 2048, LBOA, 128), bd, idesc, first ? 0u : 1u);
-      mma_commit(&bars[s % kLS]);
-    }
-  }
-  cp_wait<0>();
-  if (ok) ok = mbar_wait(&bars[(nst - 1) % kLS], ((nst - 1) / kLS) & 1);
-  ok = __syncthreads_and(ok) != 0;  // block-uniform from here on
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!ok && tid == 0) atomicOr(a.err, 1);
-  // epilogue, one group of 16 output channels at a time, through shared memory
-  float* stg = reinterpret_cast<float*>(smem);
-  const int off2 = 128 * T1 * kStg;
-  for (int g = 0; g < cout / 16 && ok; ++g) {
-    for (int src = 0; src < (S2 ? 2 : 1); ++src) {
-      const int Ts = src ? T : T1;
-      const uint32_t col = src ? col2 : 0u;
-      for (int t = 0; t < Ts; ++t)
-        for (int dki = 0; dki < 3; ++dki) {
-          float v[16];
-          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + col + (uint32_t)(t * N3 + dki * cout + g * 16), v);
-          float* d = stg + (src ? off2 : 0) + (t * 128 + warp * 32 + lane) * kStg + dki * 16;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) d[j] = v[j];
-        }
-    }
-    __syncthreads();
-    for (int p = tid; p < P; p += 128) {
-      const int r = p >> lg, k = p & msk;
-      float acc[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) acc[j] = a.bias[g * 16 + j];
-#pragma unroll
-      for (int dki = 0; dki < 3; ++dki) {
-        const int kk = (k + dki - 1) & msk;
-        const float* s1p = stg + (r * n + (a.up1 ? kk >> 1 : kk)) * kStg + dki * 16;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] += s1p[j];
-        if (S2) {
-          const float* s2p = stg + off2 + (r * n + kk) * kStg + dki * 16;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) acc[j] += s2p[j];
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    // A stage is (source, 16-channel slice, di): the source rows of the three lines dj = -1, 0, 1
+    // of both 8-channel planes (consecutive grid rows are contiguous: one copy per plane, two at
+    // the periodic wrap) and the packed weights of the three lines (one copy).
+    if (lane == 0) {
+      int slot = 0, round = 0, g = 0;  // g = round * nls + slot
+      for (int it = 0; it < nit && !s_err; ++it) {
+        const int u = blockIdx.x + it * gridDim.x;
+        const int pi = u / upp, j0 = (u % upp) * R;
+        for (int src = 0; src < (S2 ? 2 : 1) && !s_err; ++src) {
+          const bool up = src == 0 && a.up1;
+          const int lgs = up ? lg - 1 : lg, nc = 1 << lgs, mc = nc - 1;
+          const size_t Vs = (size_t)1 << (3 * lgs);
+          const uint32_t rb = (uint32_t)nc * 16u;  // bytes of one source row of one plane
+          const uint32_t tx = 2u * rb * (uint32_t)(lg >= 7 ? (up ? 2 : 3) : R + 2) + 288u * (uint32_t)cout;
+          const int ns = 3 * (src ? S2 : S1), rot = (int)(blockIdx.x % (unsigned)ns);
+          const bf16* wsrc = a.wl + (size_t)(src ? 9 * S1 : 0) * 48 * cout;
+          for (int q = 0; q < ns; ++q) {
+            // per-CTA rotation of the stage order: concurrent CTAs read different weight blocks
+            int qr = q + rot;
+            if (qr >= ns) qr -= ns;
+            const int slice = qr / 3, di = qr - 3 * slice - 1;
+            if (g >= nls && !mbar_wait_spin(&empty[slot], (round - 1) & 1)) {
+              s_err = 1;
+              break;
+            }
+            const int ri = ((pi + di) & msk) >> (up ? 1 : 0);
+            const bf16* p0 = (src ? a.s2 : a.s1) + (size_t)slice * 16 * Vs + ((size_t)ri << (2 * lgs + 3));
+            const size_t p1 = 8 * Vs;  // plane 1 - plane 0
+            const uint32_t sa = sbase + slot * stage_bytes, fb = su32(&full[slot]);
+            mbar_expect_tx(&full[slot], tx);
+            // rows [r0, r0 + cnt) of the source grid plane to positions [pos, pos + cnt nc)
+            auto rows = [&](int r0, int cnt, int pos) {
+              const bf16* g0 = p0 + ((size_t)r0 << (lgs + 3));
+              bulk_g2s(sa + (uint32_t)pos * 16u, g0, rb * (uint32_t)cnt, fb);
+              bulk_g2s(sa + LBOA + (uint32_t)pos * 16u, g0 + p1, rb * (uint32_t)cnt, fb);
+            };
+            if (lg >= 7) {
+              const int j = j0;
+              if (!up) {  // fine rows j-1, j, j+1 to slots 0, 1, 2
+                if (j >= 1 && j <= n - 2) {
+                  rows(j - 1, 3, 0);
+                } else if (j == 0) {
+                  rows(n - 1, 1, 0);
+                  rows(0, 2, n);
+                } else {
+                  rows(n - 2, 2, 0);
+                  rows(0, 1, 2 * n);
+                }
+              } else {  // the two coarse rows under j-1 .. j+1, to slots 0 and 1 (nc positions each)
+                const int clo = ((j - 1) & msk) >> 1, chi = ((j + 1) & msk) >> 1;
+                if (chi == clo + 1) {
+                  rows(clo, 2, 0);
+                } else {
+                  rows(clo, 1, 0);
+                  rows(chi, 1, nc);
+                }
+              }
+            } else if (!up) {  // fine rows j0-1 .. j0+R to slots 0 .. R+1
+              if (j0 >= 1 && j0 + R <= n - 1) {
+                rows(j0 - 1, R + 2, 0);
+              } else if (j0 == 0) {
+                rows(n - 1, 1, 0);
+                rows(0, R + 1, n);
+              } else {
+                rows(j0 - 1, R + 1, 0);
+                rows(0, 1, (R + 1) * n);
+              }
+            } else {  // slot q holds the coarse row under fine row j0-1+q
+              for (int qq = 0; qq < R + 2; ++qq) rows(((j0 - 1 + qq) & msk) >> 1 & mc, 1, qq * n);
+            }
+            bulk_g2s(sa + a_bytes, wsrc + (size_t)(9 * slice + 3 * (di + 1)) * 48 * cout, 288u * (uint32_t)cout, fb);
+            ++g;
+            if (++slot == nls) {
+              slot = 0;
+              ++round;
+            }
+          }
         }
       }
-      __align__(16) bf16 o[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16(a.relu ? fmaxf(acc[j], 0.f) : acc[j]);
-      uint4* dst = reinterpret_cast<uint4*>(a.out + ((((size_t)pi << lg | (size_t)(j0 + r)) << lg) | k) * cout +
-                                            g * 16);
-      dst[0] = reinterpret_cast<const uint4*>(o)[0];
-      dst[1] = reinterpret_cast<const uint4*>(o)[1];
+      // drain: the copies of the last stages land before this CTA may exit
+      for (int h = (g > nls ? g - nls : 0); h < g; ++h)
+        if (!mbar_wait_spin(&full[h % nls], (h / nls) & 1)) s_err = 1;
     }
-    __syncthreads();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, N3, 0, 0);
+      // descriptors of slot 0; a slot or tile offset adds (bytes >> 4) to the start-address field
+      const uint64_t a0 = sdesc(sbase, LBOA, 128), b0 = sdesc(sbase + a_bytes, LBOB, 128);
+      int slot = 0, round = 0;
+      bool issued = false;
+      int last_slot = 0, last_round = 0;
+      for (int it = 0; it < nit && !s_err; ++it) {
+        const int buf = it % nbuf;
+        if (it >= nbuf && !mbar_wait_spin(&acce[buf], ((it / nbuf) - 1) & 1)) {
+          s_err = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dbase = tmem + (uint32_t)buf * ucols;
+        const int j = (blockIdx.x + it * (int)gridDim.x) % upp * R;  // the unit's (first) row
+        for (int src = 0; src < (S2 ? 2 : 1) && !s_err; ++src) {
+          const bool up = src == 0 && a.up1;
+          const int Ts = src ? T : T1, ns = 3 * (src ? S2 : S1), nc = up ? n / 2 : n;
+          const uint32_t d0 = dbase + (src ? col2 : 0u);
+          const int clo = ((j - 1) & msk) >> 1;
+          for (int q = 0; q < ns; ++q) {
+            if (!mbar_wait_spin(&full[slot], round & 1)) {
+              s_err = 1;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t so = (uint64_t)((slot * stage_bytes) >> 4);
+            for (int dji = 0; dji < 3; ++dji) {
+              // position of line dj's first source row in the stage
+              int pos = dji * n;
+              if (lg >= 7 && up) pos = (((((j + dji - 1) & msk) >> 1) == clo) ? 0 : 1) * nc;
+              const uint64_t bd = b0 + so + (uint64_t)(dji * 6 * cout);  // 96 cout bytes per line
+              for (int t = 0; t < Ts; ++t)
+                mma_bf16(d0 + (uint32_t)(t * N3), a0 + so + (uint64_t)(pos + t * 128), bd, idesc,
+                         (q == 0 && dji == 0) ? 0u : 1u);
+            }
+            mma_commit(&empty[slot]);
+            issued = true;
+            last_slot = slot;
+            last_round = round;
+            if (++slot == nls) {
+              slot = 0;
+              ++round;
+            }
+          }
+        }
+        if (s_err) break;
+        mma_commit(&accf[buf]);
+      }
+      // drain: the last MMAs complete before TMEM is released
+      if (issued && !mbar_wait_spin(&empty[last_slot], last_round & 1)) s_err = 1;
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int ew = warp & 3;  // TMEM lane quarter of this warp
+    const int et = tid - 64;  // 0..127
+    const int off2 = 128 * T1 * kStg;
+    const size_t Vout = (size_t)1 << (3 * lg);
+    for (int it = 0; it < nit; ++it) {
+      const int u = blockIdx.x + it * gridDim.x;
+      const int pi = u / upp, j0 = (u % upp) * R;
+      const int buf = it % nbuf;
+      const bool ok = !s_err && mbar_wait_spin(&accf[buf], (it / nbuf) & 1);
+      if (!ok) s_err = 1;
+      // one snapshot of the flag, so all four warps stop at the same unit
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (et == 0) s_stop = s_err;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (s_stop) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t dbase = tmem + (uint32_t)buf * ucols + ((uint32_t)(ew * 32) << 16);
+      for (int g = 0; g < cout / 16; ++g) {
+        for (int src = 0; src < (S2 ? 2 : 1); ++src) {
+          const int Ts = src ? T : T1;
+          for (int t = 0; t < Ts; ++t)
+            for (int dki = 0; dki < 3; ++dki) {
+              float v[16];
+              tmem_ld16(dbase + (src ? col2 : 0u) + (uint32_t)(t * N3 + dki * cout + g * 16), v);
+              float4* d = reinterpret_cast<float4*>(stg + (src ? off2 : 0) + (t * 128 + ew * 32 + lane) * kStg +
+                                                    dki * 16);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        }
+        if (g == cout / 16 - 1) {  // TMEM of this unit fully read
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          mbar_arrive(&acce[buf]);
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        float bb[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) bb[j] = a.bias[g * 16 + j];
+        for (int p = et; p < P; p += 128) {
+          const int r = p >> lg, k = p & msk;
+          float acc[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[j] = bb[j];
+#pragma unroll
+          for (int dki = 0; dki < 3; ++dki) {
+            const int kk = (k + dki - 1) & msk;
+            const float4* s1p =
+                reinterpret_cast<const float4*>(stg + (r * n + (a.up1 ? kk >> 1 : kk)) * kStg + dki * 16);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 x = s1p[q];
+              acc[4 * q] += x.x;
+              acc[4 * q + 1] += x.y;
+              acc[4 * q + 2] += x.z;
+              acc[4 * q + 3] += x.w;
+            }
+            if (S2) {
+              const float4* s2p = reinterpret_cast<const float4*>(stg + off2 + (r * n + kk) * kStg + dki * 16);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float4 x = s2p[q];
+                acc[4 * q] += x.x;
+                acc[4 * q + 1] += x.y;
+                acc[4 * q + 2] += x.z;
+                acc[4 * q + 3] += x.w;
+              }
+            }
+          }
+          __align__(16) bf16 o[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16(a.relu ? fmaxf(acc[j], 0.f) : acc[j]);
+          const size_t v = (((size_t)pi << lg | (size_t)(j0 + r)) << lg) | (size_t)k;
+          *reinterpret_cast<uint4*>(a.out + pidx(v, g * 16, Vout)) = reinterpret_cast<const uint4*>(o)[0];
+          *reinterpret_cast<uint4*>(a.out + pidx(v, g * 16 + 8, Vout)) = reinterpret_cast<const uint4*>(o)[1];
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      }
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+  if (tid == 0 && s_err) atomicOr(a.err, 1);
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+// Weights packed per line-convolution stage s (slice s / 9 of the concatenated
+// input channels, line s % 9 = (di + 1) * 3 + (dj + 1)), K-major no-swizzle:
+//   wl[s][c][dk * cout + o][e] = W[3 (s % 9) + dk][o][16 (s / 9) + 8 c + e].
+__global__ void pack_w(const bf16* __restrict__ w, int cout, int cin, bf16* __restrict__ wl) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte row
+  const int N3 = 3 * cout, nrow = 9 * (cin / 16) * 2 * N3;
+  if (t >= nrow) return;
+  const int nn = t % N3, c = (t / N3) & 1, s = t / (2 * N3);
+  const int dk = nn / cout, o = nn % cout;
+  const int tap = 3 * (s % 9) + dk, ch = 16 * (s / 9) + 8 * c;
+  *reinterpret_cast<uint4*>(wl + (size_t)t * 8) = *reinterpret_cast<const uint4*>(w + ((size_t)tap * cout + o) * cin + ch);
 }
 
 // ---------------------------------------------------------------------------
@@ -718,41 +926,44 @@ __global__ void input_features(const double* __restrict__ eta, int V, float mu, 
   const bf16 f0 = __float2bfloat16((logf((float)fmax(eta[v], 1e-30)) - mu) * isd), f1 = __float2bfloat16(afeat);
   if (f2) f2[v] = __halves2bfloat162(f0, f1);
   if (!x) return;
-  __align__(16) bf16 o[16];
+  __align__(16) bf16 o[8];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16(0.f);
+  for (int c = 0; c < 8; ++c) o[c] = __float2bfloat16(0.f);
+  *reinterpret_cast<uint4*>(x + pidx(v, 8, (size_t)V)) = reinterpret_cast<const uint4*>(o)[0];
   o[0] = f0;
   o[1] = f1;
-  uint4* dst = reinterpret_cast<uint4*>(x + (size_t)v * 16);
-  dst[0] = reinterpret_cast<const uint4*>(o)[0];
-  dst[1] = reinterpret_cast<const uint4*>(o)[1];
+  *reinterpret_cast<uint4*>(x + pidx(v, 0, (size_t)V)) = reinterpret_cast<const uint4*>(o)[0];
 }
 
 // Mean over the 8 children (lg: coarse grid).
 __global__ void pool_fwd(const bf16* __restrict__ x, int C, int lg, bf16* __restrict__ y) {
-  const int Vc = 1 << (3 * lg), m = (1 << lg) - 1, lgf = lg + 1;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t Vc = (size_t)1 << (3 * lg), Vf = Vc << 3;
+  const int m = (1 << lg) - 1, lgf = lg + 1;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // element of y in memory order
   if (t >= Vc * C) return;
-  const int u = t / C, c = t % C;
+  const size_t pl = t / (Vc * 8);
+  const int u = (int)((t >> 3) % Vc), e = (int)(t & 7);
   const int I = u >> (2 * lg), J = (u >> lg) & m, K = u & m;
   float s = 0.f;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int f = (((2 * I + (q >> 2)) << lgf | (2 * J + ((q >> 1) & 1))) << lgf) | (2 * K + (q & 1));
-    s += __bfloat162float(x[(size_t)f * C + c]);
+    s += __bfloat162float(x[((pl * Vf + f) << 3) | e]);
   }
   y[t] = __float2bfloat16(0.125f * s);
 }
 
 // dX[fine] += dY[parent] / 8 (lg: coarse grid).
 __global__ void pool_bwd(const float* __restrict__ dy, int C, int lg, float* __restrict__ dx) {
-  const int lgf = lg + 1, Vf = 1 << (3 * lgf), mf = (1 << lgf) - 1;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lgf = lg + 1, mf = (1 << lgf) - 1;
+  const size_t Vf = (size_t)1 << (3 * lgf), Vc = Vf >> 3;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= Vf * C) return;
-  const int f = t / C, c = t % C;
+  const size_t pl = t / (Vf * 8);
+  const int f = (int)((t >> 3) % Vf), e = (int)(t & 7);
   const int i = f >> (2 * lgf), j = (f >> lgf) & mf, k = f & mf;
   const int u = (((i >> 1) << lg | (j >> 1)) << lg) | (k >> 1);
-  dx[t] += 0.125f * dy[(size_t)u * C + c];
+  dx[t] += 0.125f * dy[((pl * Vc + u) << 3) | e];
 }
 
 // dZ = dY where the stored activation is positive (ReLU), else 0; BF16 for the GEMMs.
@@ -767,30 +978,28 @@ __global__ void relu_bwd(const float* __restrict__ dy, const bf16* __restrict__ 
 // channels [c1, c1 + c2) are added into the gradient of src2.
 __global__ void split_up_bwd(const float* __restrict__ dx, int c1, int c2, int lg, int up, float* __restrict__ d1,
                              float* __restrict__ d2) {
-  const int kin = c1 + c2, V = 1 << (3 * lg), m = (1 << lg) - 1;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t V = (size_t)1 << (3 * lg);
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // channel-planar: the planes of src1's channels come first, then those of src2
   if (up) {
-    const int lgc = lg - 1, Vc = 1 << (3 * lgc), mc = (1 << lgc) - 1;
+    const int lgc = lg - 1, mc = (1 << lgc) - 1;
+    const size_t Vc = V >> 3;
     if (t < Vc * c1) {
-      const int u = t / c1, c = t % c1;
+      const size_t pl = t / (Vc * 8);
+      const int u = (int)((t >> 3) % Vc), e = (int)(t & 7);
       const int I = u >> (2 * lgc), J = (u >> lgc) & mc, K = u & mc;
       float s = 0.f;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int f = (((2 * I + (q >> 2)) << lg | (2 * J + ((q >> 1) & 1))) << lg) | (2 * K + (q & 1));
-        s += dx[(size_t)f * kin + c];
+        s += dx[((pl * V + f) << 3) | e];
       }
       d1[t] = s;
     }
   } else if (t < V * c1) {
-    const int v = t / c1, c = t % c1;
-    d1[t] = dx[(size_t)v * kin + c];
+    d1[t] = dx[t];
   }
-  if (c2 > 0 && t < V * c2) {
-    const int v = t / c2, c = t % c2;
-    d2[t] += dx[(size_t)v * kin + c1 + c];
-  }
-  (void)m;
+  if (c2 > 0 && t < V * c2) d2[t] += dx[V * c1 + t];
 }
 
 // Output head (1x1x1 convolution to one channel) and squared-error loss:
@@ -808,7 +1017,7 @@ __global__ void head_fwd_bwd(const bf16* __restrict__ y, int C, int V, const flo
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v < V) {
     float p = hb[C];
-    for (int c = 0; c < C; ++c) p += hb[c] * __bfloat162float(y[(size_t)v * C + c]);
+    for (int c = 0; c < C; ++c) p += hb[c] * __bfloat162float(y[pidx(v, c, (size_t)V)]);
     if (pred) pred[v] = p;
     if (target) {
       const float r = p - tscale * target[v];
@@ -816,8 +1025,8 @@ __global__ void head_fwd_bwd(const bf16* __restrict__ y, int C, int V, const flo
       atomicAdd(&sl, (double)r * r / V);
       if (dy)
         for (int c = 0; c < C; ++c) {
-          dy[(size_t)v * C + c] = g * hb[c];
-          atomicAdd(&sdh[c], g * __bfloat162float(y[(size_t)v * C + c]));
+          dy[pidx(v, c, (size_t)V)] = g * hb[c];
+          atomicAdd(&sdh[c], g * __bfloat162float(y[pidx(v, c, (size_t)V)]));
         }
       atomicAdd(&sdh[C], g);
     }
@@ -832,8 +1041,9 @@ __global__ void bias_grad(const bf16* __restrict__ dz, int C, int V, float* __re
   __shared__ float s[64];
   if (threadIdx.x < C) s[threadIdx.x] = 0.f;
   __syncthreads();
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < V * C; t += gridDim.x * blockDim.x)
-    atomicAdd(&s[t % C], __bfloat162float(dz[t]));
+  const size_t n = (size_t)V * C;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    atomicAdd(&s[(int)(t / ((size_t)V * 8)) * 8 + (int)(t & 7)], __bfloat162float(dz[t]));
   __syncthreads();
   if (threadIdx.x < C) atomicAdd(&db[threadIdx.x], s[threadIdx.x]);
 }
@@ -884,6 +1094,16 @@ using namespace isis::unet;
 
 #define UNET_LAUNCH(kind, bytes, st, ...) ISIS_LAUNCH(kind, bytes, st, __VA_ARGS__)
 
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+  }
+  return n;
+}
+
 extern "C" {
 
 isis_status isis_unet_conv3_fwd(const void* src1, int c1, int lg1, const void* src2, int c2, int lg, const void* w,
@@ -895,21 +1115,6 @@ isis_status isis_unet_conv3_fwd(const void* src1, int c1, int lg1, const void* s
   cudaStream_t st = (cudaStream_t)stream;
   const size_t V = (size_t)1 << (3 * lg);
   const double flops = 2.0 * 27.0 * (c1 + c2) * cout * (double)V;
-  const int up1 = lg1 != lg;
-  if (lg >= 5 && lg <= 9 && line_tmem_cols(lg, up1, c2, cout) <= 512 && line_smem(lg, up1, c2, cout) <= 200 * 1024) {
-    static bool lattr = false;
-    if (!lattr) {
-      if (cudaFuncSetAttribute(line_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
-        return ISIS_ECUDA;
-      lattr = true;
-    }
-    LineArgs la{(const bf16*)src1, (const bf16*)src2, (const bf16*)w, bias, (bf16*)out, c1, up1, c2, lg, cout,
-                relu, err};
-    const int P = lg >= 7 ? 1 << lg : 128;
-    UNET_LAUNCH(isis::KK_UNET_CONV, flops, st,
-                (line_conv<<<(unsigned)(V / P), 128, line_smem(lg, up1, c2, cout), st>>>(la)));
-    return ISIS_OK;
-  }
   ConvArgs a{(const bf16*)src1, (const bf16*)src2, (const bf16*)w, bias, (bf16*)out, nullptr,
              c1, lg1, c2, lg, cout, relu, +1, err};
   const size_t smem = (size_t)kStages * conv_stage_bytes(cout);
@@ -920,6 +1125,48 @@ isis_status isis_unet_conv3_fwd(const void* src1, int c1, int lg1, const void* s
     attr = true;
   }
   UNET_LAUNCH(isis::KK_UNET_CONV, flops, st, (igemm_conv<0><<<nb(V, 128), 128, smem, st>>>(a)));
+  return ISIS_OK;
+}
+
+isis_status isis_unet_pack_w(const void* w, int cout, int cin, void* wl, void* stream) {
+  if (!w || !wl || cout < 16 || cout > 64 || cout % 16 || cin < 16 || cin % 16 || !aligned16(w) || !aligned16(wl))
+    return ISIS_EINVAL;
+  const int nrow = 9 * (cin / 16) * 6 * cout;
+  cudaStream_t st = (cudaStream_t)stream;
+  UNET_LAUNCH(isis::KK_UNET_ELEM, 32.0 * nrow, st,
+              (pack_w<<<nb(nrow, 256), 256, 0, st>>>((const bf16*)w, cout, cin, (bf16*)wl)));
+  return ISIS_OK;
+}
+
+int isis_unet_line_ok(int c1, int lg1, int c2, int lg, int cout) {
+  const int up1 = lg1 != lg;
+  return lg >= 5 && lg <= 9 && (lg1 == lg || lg1 == lg - 1) && c1 >= 16 && c1 % 16 == 0 && c2 >= 0 && c2 % 16 == 0 &&
+         cout >= 16 && cout <= 64 && cout % 16 == 0 && line_unit_cols(lg, up1, c2, cout) <= 512 &&
+         line_nls(lg, up1, c2, cout) >= 2;
+}
+
+isis_status isis_unet_line_fwd(const void* src1, int c1, int lg1, const void* src2, int c2, int lg, const void* wl,
+                               const float* bias, int cout, int relu, void* out, int* err, void* stream) {
+  if (!src1 || !wl || !bias || !out || !err || (c2 > 0 && !src2) || !isis_unet_line_ok(c1, lg1, c2, lg, cout))
+    return ISIS_EINVAL;
+  if (!aligned16(src1) || (src2 && !aligned16(src2)) || !aligned16(wl) || !aligned16(out)) return ISIS_EINVAL;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(line_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) != cudaSuccess)
+      return ISIS_ECUDA;
+    attr = true;
+  }
+  const int up1 = lg1 != lg, n = 1 << lg, R = lg >= 7 ? 1 : 128 >> lg;
+  const size_t V = (size_t)1 << (3 * lg);
+  const int nls = line_nls(lg, up1, c2, cout);
+  LineArgs la{(const bf16*)src1, (const bf16*)src2, (const bf16*)wl, bias, (bf16*)out, c1, up1, c2, lg, cout, relu,
+              (int)(V / (size_t)(R * n)), nls, err};
+  const int nsm = sm_count();
+  if (nsm <= 0) return ISIS_ECUDA;
+  const unsigned grid = (unsigned)(la.nunits < nsm ? la.nunits : nsm);
+  cudaStream_t st = (cudaStream_t)stream;
+  const double flops = 2.0 * 27.0 * (c1 + c2) * cout * (double)V;
+  UNET_LAUNCH(isis::KK_UNET_CONV, flops, st, (line_conv<<<grid, 192, line_smem_n(lg, up1, c2, cout, nls), st>>>(la)));
   return ISIS_OK;
 }
 

@@ -44,6 +44,9 @@ def _lib():
         "isis_unet_conv3_wgrad": [vp, i, i, vp, i, i, vp, i, vp, vp, vp],
         "isis_unet_input": [vp, i, f, f, f, vp, vp, vp],
         "isis_unet_stem_fwd": [vp, i, vp, i, vp, vp, vp, vp],
+        "isis_unet_pack_w": [vp, i, i, vp, vp],
+        "isis_unet_line_ok": [i, i, i, i, i],
+        "isis_unet_line_fwd": [vp, i, i, vp, i, i, vp, vp, i, i, vp, vp, vp],
         "isis_unet_pool_fwd": [vp, i, i, vp, vp],
         "isis_unet_pool_bwd": [vp, i, i, vp, vp],
         "isis_unet_relu_bwd": [vp, vp, ctypes.c_int64, vp, vp],
@@ -78,7 +81,9 @@ def _s():
 
 class UNet:
     """Parameters live in flat FP32 buffers (master copy, gradient, Adam
-    moments) with a BF16 copy and per-tap transposes for the convolutions."""
+    moments) with a BF16 copy, per-tap transposes (input gradient) and
+    per-stage packings (line convolution) for the convolutions.  Activations
+    are channel-planar (include/isis_unet.h)."""
 
     def __init__(self, device="cuda", seed: int = 0, mu: float = -1.125, sd: float = 1.5, scale: float = 0.1):
         self.dev = torch.device(device)
@@ -109,6 +114,8 @@ class UNet:
         self.Pb = torch.empty(off, device=self.dev, dtype=torch.bfloat16)
         self.Wt = {name: torch.empty(27 * cout * sum(pieces), device=self.dev, dtype=torch.bfloat16)
                    for name, pieces, cout in LAYERS}
+        self.Wl = {name: torch.empty(27 * cout * sum(pieces), device=self.dev, dtype=torch.bfloat16)
+                   for name, pieces, cout in LAYERS}
         self.err = torch.zeros(1, device=self.dev, dtype=torch.int32)
         self.loss = torch.zeros(1, device=self.dev, dtype=torch.float64)
         self.step = 0
@@ -121,12 +128,17 @@ class UNet:
         return buf[o:o + int(np.prod(shp))]
 
     def _refresh(self):
-        """BF16 copy of the parameters and the per-tap transposes."""
+        """BF16 copy of the parameters, then the per-tap transposes and the line-kernel packing."""
         lib, s = _lib(), _s()
         _ck(lib.isis_unet_to_bf16(_p(self.P), self.n, _p(self.Pb), s), "to_bf16")
+        self._derived()
+
+    def _derived(self):
+        lib, s = _lib(), _s()
         for name, pieces, cout in LAYERS:
-            _ck(lib.isis_unet_transpose_w(_p(self.view(self.Pb, name + ".W")), cout, sum(pieces),
-                                          _p(self.Wt[name]), s), "transpose_w")
+            w = _p(self.view(self.Pb, name + ".W"))
+            _ck(lib.isis_unet_transpose_w(w, cout, sum(pieces), _p(self.Wt[name]), s), "transpose_w")
+            _ck(lib.isis_unet_pack_w(w, cout, sum(pieces), _p(self.Wl[name]), s), "pack_w")
 
     def state(self) -> dict:
         host = self.P.cpu().numpy()
@@ -194,8 +206,13 @@ class UNet:
         P, Pb, err = self.P, self.Pb, self.err
 
         def conv(name, s1, c1, lg1, s2, c2, lgo, out, cout):
-            _ck(lib.isis_unet_conv3_fwd(_p(s1), c1, lg1, _p(s2), c2, lgo, _p(self.view(Pb, name + ".W")),
-                                        _p(self.view(P, name + ".b")), cout, 1, _p(out), _p(err), s), name)
+            b = _p(self.view(P, name + ".b"))
+            if lib.isis_unet_line_ok(c1, lg1, c2, lgo, cout):
+                _ck(lib.isis_unet_line_fwd(_p(s1), c1, lg1, _p(s2), c2, lgo, _p(self.Wl[name]), b, cout, 1, _p(out),
+                                           _p(err), s), name)
+            else:
+                _ck(lib.isis_unet_conv3_fwd(_p(s1), c1, lg1, _p(s2), c2, lgo, _p(self.view(Pb, name + ".W")), b, cout,
+                                            1, _p(out), _p(err), s), name)
 
         def pool(x, C, lgc, y):
             _ck(lib.isis_unet_pool_fwd(_p(x), C, lgc, _p(y), s), "pool")
@@ -265,9 +282,7 @@ class UNet:
         self.step += 1
         _ck(lib.isis_unet_adam(_p(P), _p(G), _p(self.M1), _p(self.M2), self.n, lr, 0.9, 0.999, 1e-8, self.step,
                                _p(Pb), s), "adam")
-        for name, pieces, cout in LAYERS:
-            _ck(lib.isis_unet_transpose_w(_p(self.view(Pb, name + ".W")), cout, sum(pieces), _p(self.Wt[name]), s),
-                "transpose_w")
+        self._derived()
         return self.loss
 
     # -- the guess ----------------------------------------------------------

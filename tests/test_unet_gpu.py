@@ -21,6 +21,22 @@ def _np(t):
     return t.float().cpu().numpy().astype(np.float64)
 
 
+def _planar(X):
+    """[V, C] -> the library's channel-planar order: element (v, c) at ((c / 8) V + v) 8 + c % 8."""
+    V, C = X.shape
+    return np.ascontiguousarray(X.reshape(V, C // 8, 8).transpose(1, 0, 2).reshape(-1))
+
+
+def _unplanar(x, C):
+    x = np.asarray(x).reshape(C // 8, -1, 8)
+    return x.transpose(1, 0, 2).reshape(-1, C)
+
+
+def _rows(t, C, idx):
+    """Rows idx ([V, C] view) of a channel-planar device tensor, FP64 on the host."""
+    return _np(t.view(C // 8, -1, 8)[:, torch.from_numpy(idx).cuda(), :]).transpose(1, 0, 2).reshape(len(idx), C)
+
+
 @pytest.fixture(scope="module")
 def lib(cuda_lib):
     from paper_1307_6748_gb300 import unet
@@ -44,8 +60,8 @@ def test_conv_forward(lib, c1, up, c2, cout):
     n = 1 << lg
     g = np.random.Generator(np.random.PCG64(c1 + cout + up))
     n1 = n >> up
-    s1 = _bf(g.standard_normal((n1 ** 3, c1)))
-    s2 = _bf(g.standard_normal((n ** 3, c2))) if c2 else None
+    s1 = _bf(_planar(g.standard_normal((n1 ** 3, c1))))
+    s2 = _bf(_planar(g.standard_normal((n ** 3, c2)))) if c2 else None
     W = _bf(g.standard_normal((27, cout, c1 + c2)) * 0.1)
     b = torch.from_numpy(g.standard_normal(cout).astype(np.float32)).cuda()
     out = torch.empty(n ** 3 * cout, dtype=torch.bfloat16, device="cuda")
@@ -54,12 +70,12 @@ def test_conv_forward(lib, c1, up, c2, cout):
                                    _s()) == 0
     torch.cuda.synchronize()
     assert int(err.item()) == 0
-    X1 = _np(s1).reshape(n1, n1, n1, c1)
+    X1 = _unplanar(_np(s1), c1).reshape(n1, n1, n1, c1)
     if up:
         X1 = U.up(X1)
-    X = X1 if not c2 else np.concatenate([X1, _np(s2).reshape(n, n, n, c2)], axis=-1)
+    X = X1 if not c2 else np.concatenate([X1, _unplanar(_np(s2), c2).reshape(n, n, n, c2)], axis=-1)
     ref = U.relu(U.conv3_fwd(X, _np(W), b.cpu().numpy().astype(np.float64))).reshape(-1, cout)
-    got = _np(out).reshape(-1, cout)
+    got = _unplanar(_np(out), cout)
     assert np.abs(got - ref).max() <= 2 ** -7 * np.abs(ref).max() + 1e-6
 
 
@@ -68,7 +84,7 @@ def test_conv_input_gradient(lib, cout, cin):
     lg = 3
     n = 1 << lg
     g = np.random.Generator(np.random.PCG64(cout * 7 + cin))
-    dz = _bf(g.standard_normal((n ** 3, cout)))
+    dz = _bf(_planar(g.standard_normal((n ** 3, cout))))
     W = _bf(g.standard_normal((27, cout, cin)) * 0.1)
     Wt = torch.empty_like(W)
     assert lib.isis_unet_transpose_w(_p(W), cout, cin, _p(Wt), _s()) == 0
@@ -77,8 +93,8 @@ def test_conv_input_gradient(lib, cout, cin):
     assert lib.isis_unet_conv3_dgrad(_p(dz), cout, lg, _p(Wt), cin, _p(din), _p(err), _s()) == 0
     torch.cuda.synchronize()
     assert int(err.item()) == 0
-    ref = U.conv3_dgrad(_np(dz).reshape(n, n, n, cout), _np(W)).reshape(-1, cin)
-    got = din.cpu().numpy().reshape(-1, cin)
+    ref = U.conv3_dgrad(_unplanar(_np(dz), cout).reshape(n, n, n, cout), _np(W)).reshape(-1, cin)
+    got = _unplanar(din.cpu().numpy(), cin)
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
@@ -88,19 +104,19 @@ def test_conv_weight_gradient(lib, c1, up, c2, cout):
     n = 1 << lg
     g = np.random.Generator(np.random.PCG64(3 * c1 + cout + up))
     n1 = n >> up
-    s1 = _bf(g.standard_normal((n1 ** 3, c1)))
-    s2 = _bf(g.standard_normal((n ** 3, c2))) if c2 else None
-    dz = _bf(g.standard_normal((n ** 3, cout)))
+    s1 = _bf(_planar(g.standard_normal((n1 ** 3, c1))))
+    s2 = _bf(_planar(g.standard_normal((n ** 3, c2)))) if c2 else None
+    dz = _bf(_planar(g.standard_normal((n ** 3, cout))))
     dw = torch.zeros(27 * cout * (c1 + c2), dtype=torch.float32, device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     assert lib.isis_unet_conv3_wgrad(_p(s1), c1, lg - up, _p(s2), c2, lg, _p(dz), cout, _p(dw), _p(err), _s()) == 0
     torch.cuda.synchronize()
     assert int(err.item()) == 0
-    X1 = _np(s1).reshape(n1, n1, n1, c1)
+    X1 = _unplanar(_np(s1), c1).reshape(n1, n1, n1, c1)
     if up:
         X1 = U.up(X1)
-    X = X1 if not c2 else np.concatenate([X1, _np(s2).reshape(n, n, n, c2)], axis=-1)
-    ref = U.conv3_wgrad(X, _np(dz).reshape(n, n, n, cout))
+    X = X1 if not c2 else np.concatenate([X1, _unplanar(_np(s2), c2).reshape(n, n, n, c2)], axis=-1)
+    ref = U.conv3_wgrad(X, _unplanar(_np(dz), cout).reshape(n, n, n, cout))
     got = dw.cpu().numpy().reshape(ref.shape)
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
 
@@ -114,7 +130,7 @@ def test_network_gradient_direction(cuda_lib):
     eta = synth.lognormal_eta(n, float(n), 1.5, 9).cuda()
     target = (0.05 * synth.gaussian_field(n, float(n), 1.0, 10)).float().cuda().reshape(-1)
     net.features(eta, 1.0, lg)
-    X0 = _np(net.acts(lg)[1]["x0"]).reshape(n, n, n, 16)
+    X0 = _unplanar(_np(net.acts(lg)[1]["x0"]), 16).reshape(n, n, n, 16)
     _, grads, _ = U.loss_and_grads(P, X0, target.cpu().numpy().astype(np.float64).reshape(n, n, n) / net.scale)
     net.train_step(eta, 1.0, target, lg, lr=0.0)  # lr 0: gradients only
     torch.cuda.synchronize()
@@ -139,20 +155,20 @@ def _sampled_conv_ref(s1, c1, up, s2, c2, lg, W, b, vs):
             u1 = ((ii // 2) * nc + jj // 2) * nc + kk // 2
         else:
             u1 = (ii * n + jj) * n + kk
-        X = _np(s1.view(-1, c1)[torch.from_numpy(u1).cuda()])
+        X = _rows(s1, c1, u1)
         if c2:
             u2 = (ii * n + jj) * n + kk
-            X = np.concatenate([X, _np(s2.view(-1, c2)[torch.from_numpy(u2).cuda()])], axis=1)
+            X = np.concatenate([X, _rows(s2, c2, u2)], axis=1)
         ref += X @ W[t].T
     return U.relu(ref + b)
 
 
 @pytest.mark.parametrize("lg,c1,up,c2,cout", [(5, 16, 0, 0, 32), (5, 64, 1, 64, 64), (6, 32, 1, 16, 16),
                                               (6, 64, 0, 0, 64), (7, 64, 1, 32, 32), (7, 16, 0, 0, 16),
-                                              (8, 32, 1, 16, 16), (8, 16, 0, 0, 32), (9, 32, 1, 16, 16)])
+                                              (8, 32, 1, 16, 16), (8, 16, 0, 0, 32), (9, 16, 0, 0, 16)])
 def test_line_conv_forward(lib, lg, c1, up, c2, cout):
-    """The line kernel (grids of 32..512 cells): every voxel of a plane at each end, rows at the
-    j wrap, the k wrap and random voxels, against the FP64 reference."""
+    """The line kernel (grids of 32..512 cells, packed weights): every voxel of a plane at each
+    end, rows at the j wrap, the k wrap and random voxels, against the FP64 reference."""
     n = 1 << lg
     gen = torch.Generator(device="cuda").manual_seed(lg * 1000 + c1 + c2 + cout + up)
     n1 = n >> up
@@ -162,8 +178,11 @@ def test_line_conv_forward(lib, lg, c1, up, c2, cout):
     b = torch.randn(cout, generator=gen, device="cuda")
     out = torch.empty(n ** 3 * cout, dtype=torch.bfloat16, device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    assert lib.isis_unet_conv3_fwd(_p(s1), c1, lg - up, _p(s2), c2, lg, _p(W), _p(b), cout, 1, _p(out), _p(err),
-                                   _s()) == 0
+    Wl = torch.empty_like(W)
+    assert lib.isis_unet_line_ok(c1, lg - up, c2, lg, cout) == 1
+    assert lib.isis_unet_pack_w(_p(W), cout, c1 + c2, _p(Wl), _s()) == 0
+    assert lib.isis_unet_line_fwd(_p(s1), c1, lg - up, _p(s2), c2, lg, _p(Wl), _p(b), cout, 1, _p(out), _p(err),
+                                  _s()) == 0
     torch.cuda.synchronize()
     assert int(err.item()) == 0
     rng = np.random.Generator(np.random.PCG64(lg))
@@ -176,7 +195,7 @@ def test_line_conv_forward(lib, lg, c1, up, c2, cout):
                                    (np.arange(n) * n + 3) * n + n - 1]))            # k = n - 1 (k wrap)
     Wn = _np(W).reshape(27, cout, c1 + c2)
     ref = _sampled_conv_ref(s1, c1, up, s2, c2, lg, Wn, b.cpu().numpy().astype(np.float64), vs)
-    got = _np(out.view(-1, cout)[torch.from_numpy(vs).cuda()])
+    got = _rows(out, cout, vs)
     assert np.abs(got - ref).max() <= 2 ** -7 * np.abs(ref).max() + 1e-6
 
 
@@ -197,13 +216,13 @@ def test_stem_equals_conv_of_features(lib, lg):
     assert lib.isis_unet_stem_fwd(_p(f2), lg, _p(W), 16, _p(b), _p(out), _p(err), _s()) == 0
     torch.cuda.synchronize()
     assert int(err.item()) == 0
-    X = _np(x16).reshape(-1, 16)
+    X = _unplanar(_np(x16), 16)
     assert np.all(X[:, 2:] == 0) and np.array_equal(X[:, :2], _np(f2).reshape(-1, 2))
     if lg <= 5:
         ref = U.relu(U.conv3_fwd(X.reshape(n, n, n, 16), _np(W), b.cpu().numpy().astype(np.float64))).reshape(-1, 16)
-        got = _np(out).reshape(-1, 16)
+        got = _unplanar(_np(out), 16)
     else:
         vs = np.random.Generator(np.random.PCG64(1)).integers(0, n ** 3, 8192)
         ref = _sampled_conv_ref(x16, 16, 0, None, 0, lg, _np(W), b.cpu().numpy().astype(np.float64), vs)
-        got = _np(out.view(-1, 16)[torch.from_numpy(vs).cuda()])
+        got = _rows(out, 16, vs)
     assert np.abs(got - ref).max() <= 2 ** -7 * np.abs(ref).max() + 1e-6
