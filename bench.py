@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--sample-N", type=int, default=128, help="grid of the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--guess", default="net", choices=["net", "background"],
+                    help="symmetron initial guess: the trained U-Net, or the background field")
+    ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1307_6748_gb300", "weights", "unet_symmetron.npz"))
     return ap.parse_args()
 
 
@@ -58,6 +61,9 @@ def workload(args):
             "symmetron": {"a": 1.0, "a_ssb": 0.5, "lambda0": 1.0, "beta": 1.0},
             "fofr": {"n": 1, "fR0_abs": 1e-5}, "cycle": f"V(2,2), coarsest {args.ncoarse}^3 dense Newton",
             "inner_cycles": {"poisson": args.inner_poisson, "symmetron": args.inner_sym, "fofr": args.inner_fofr},
+            "initial_guess": {"symmetron": "U-Net (trained at 1 Mpc/h cells) on the 8-cell mean density, "
+                                           "prolongated trilinearly" if args.guess == "net" else "background",
+                              "fofr": "background field", "poisson": "zero"},
             "l2": "inputs larger than L2 (each 512^3 field is 0.5-1 GB), no flush",
             "parallelism": "replicas (one independent problem per GPU)"}
 
@@ -194,7 +200,7 @@ def main():
 
     import torch
 
-    from paper_1307_6748_gb300 import build, isis, synth
+    from paper_1307_6748_gb300 import build, isis, synth, unet
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -220,6 +226,18 @@ def main():
         return isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=inner, init=isis.ISIS_INIT_BACKGROUND,
                          n_coarsest=args.ncoarse)
     o_poi, o_sym, o_fr = opts(args.inner_poisson), opts(args.inner_sym), opts(args.inner_fofr)
+    net, pooled = None, False
+    if args.guess == "net":
+        # the net is convolutional: it runs at its training cell size (1 Mpc/h), here on 8-cell means
+        meta = unet.UNet.meta(args.weights)
+        h, h_net = box / N, float(meta.get("h", 1.0))
+        if abs(2 * h - h_net) < 1e-9 * h_net:
+            pooled = True
+        elif abs(h - h_net) > 1e-9 * h_net:
+            raise SystemExit(f"bench: the net was trained at {h_net} Mpc/h cells; this grid has {h} Mpc/h")
+        net = unet.UNet.load(args.weights, device=dev)
+        o_sym = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=args.inner_sym, init=isis.ISIS_INIT_INPUT,
+                          n_coarsest=args.ncoarse)
     stream = torch.cuda.current_stream()
     infos = {}
 
@@ -232,6 +250,8 @@ def main():
         infos["poisson"] = isis.isis_poisson_solve(grid, a, eta, Phi, tol=args.tol, opts=o_poi)
         if ev:
             ev[2].record(stream)
+        if net is not None:
+            net.guess(eta, a, psym.a_ssb, chi, pooled=pooled)
         infos["symmetron"] = isis.isis_scalar_solve(isis.ISIS_SYMMETRON, psym, grid, a, eta, chi, tol=args.tol,
                                                     opts=o_sym)
         if ev:

@@ -112,6 +112,15 @@ isis_status isis_unet_adam(float* p, const float* g, float* m1, float* m2, int64
 isis_status isis_unet_transpose_w(const void* w, int cout, int cin, void* wt, void* stream);
 /* b = BF16(a). */
 isis_status isis_unet_to_bf16(const float* a, int64_t n, void* b, void* stream);
+/* Features of a grid twice as fine as the net's (eta on grid lg + 1): f2 (BF16 [V][2]) on
+ * grid lg from the mean density of each 8-cell block: f0 = (ln mean - mu) * isd, f1 = afeat.
+ * The net then runs at its training cell size; 2 <= lg <= 9. */
+isis_status isis_unet_input_pooled(const double* eta, int lg, float mu, float isd, float afeat, void* f2,
+                                   void* stream);
+/* phi (FP64, grid lg + 1) = bg + scale * P(pred), with pred on grid lg and P the cell-centred
+ * trilinear prolongation (per axis: 3/4 of the parent, 1/4 of the neighbour on the fine cell's
+ * side, periodic). */
+isis_status isis_unet_guess_fine(const float* pred, int lg, double bg, double scale, double* phi, void* stream);
 /* phi[v] = bg + scale * pred[v] (FP64 initial guess for isis_scalar_solve). */
 isis_status isis_unet_guess(const float* pred, int lg, double bg, double scale, double* phi, void* stream);
 

@@ -1083,6 +1083,46 @@ __global__ void guess_out(const float* __restrict__ p, int V, double bg, double 
   if (v < V) phi[v] = bg + scale * (double)p[v];
 }
 
+// Features of the mean density over each coarse cell (eta on grid lg + 1, features on grid lg):
+// f0 = (ln(mean of the 8 children) - mu) * isd, f1 = afeat.
+__global__ void input_pooled(const double* __restrict__ eta, int lg, float mu, float isd, float afeat,
+                             __nv_bfloat162* __restrict__ f2) {
+  const int V = 1 << (3 * lg), m = (1 << lg) - 1, lgf = lg + 1;
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= V) return;
+  const int I = u >> (2 * lg), J = (u >> lg) & m, K = u & m;
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    s += eta[(((2 * I + (q >> 2)) << lgf | (2 * J + ((q >> 1) & 1))) << lgf) | (2 * K + (q & 1))];
+  f2[u] = __halves2bfloat162(__float2bfloat16((logf((float)fmax(0.125 * s, 1e-30)) - mu) * isd),
+                             __float2bfloat16(afeat));
+}
+
+// Guess on the grid lg + 1 from the net's output on grid lg: phi = bg + scale * P(pred), P the
+// cell-centred trilinear interpolation (weights 3/4 and 1/4 per axis, periodic).
+__global__ void guess_fine(const float* __restrict__ p, int lg, double bg, double scale, double* __restrict__ phi) {
+  const int lgf = lg + 1, Vf = 1 << (3 * lgf), mf = (1 << lgf) - 1, m = (1 << lg) - 1;
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= Vf) return;
+  const int i = f >> (2 * lgf), j = (f >> lgf) & mf, k = f & mf;
+  // coarse neighbours along each axis: the parent and the one on the side of the fine cell
+  const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+  const int I1 = (I0 + ((i & 1) ? 1 : -1)) & m, J1 = (J0 + ((j & 1) ? 1 : -1)) & m, K1 = (K0 + ((k & 1) ? 1 : -1)) & m;
+  const int Is[2] = {I0, I1}, Js[2] = {J0, J1}, Ks[2] = {K0, K1};
+  // FP32 interpolation (the net's output is BF16-accurate); FP64 only for phi = bg + scale s
+  const float w[2] = {0.75f, 0.25f};
+  float s = 0.f;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const float* row = p + ((Is[a] << lg | Js[b]) << lg);
+      s += w[a] * w[b] * (0.75f * row[Ks[0]] + 0.25f * row[Ks[1]]);
+    }
+  phi[f] = bg + scale * (double)s;
+}
+
 inline unsigned nb(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -1325,6 +1365,24 @@ isis_status isis_unet_to_bf16(const float* a, int64_t n, void* b, void* stream) 
   cudaStream_t st = (cudaStream_t)stream;
   UNET_LAUNCH(isis::KK_UNET_ELEM, 6.0 * n, st,
               (to_bf16<<<nb((size_t)n, 256), 256, 0, st>>>(a, (bf16*)b, (size_t)n)));
+  return ISIS_OK;
+}
+
+isis_status isis_unet_input_pooled(const double* eta, int lg, float mu, float isd, float afeat, void* f2,
+                                   void* stream) {
+  if (!eta || !f2 || lg < 2 || lg > 9 || ((uintptr_t)f2 & 3u)) return ISIS_EINVAL;
+  const int V = 1 << (3 * lg);
+  cudaStream_t st = (cudaStream_t)stream;
+  UNET_LAUNCH(isis::KK_UNET_ELEM, 68.0 * V, st,
+              (input_pooled<<<nb(V, 256), 256, 0, st>>>(eta, lg, mu, isd, afeat, (__nv_bfloat162*)f2)));
+  return ISIS_OK;
+}
+
+isis_status isis_unet_guess_fine(const float* pred, int lg, double bg, double scale, double* phi, void* stream) {
+  if (!pred || !phi || lg < 2 || lg > 9) return ISIS_EINVAL;
+  const int Vf = 1 << (3 * (lg + 1));
+  cudaStream_t st = (cudaStream_t)stream;
+  UNET_LAUNCH(isis::KK_UNET_ELEM, 8.5 * Vf, st, (guess_fine<<<nb(Vf, 256), 256, 0, st>>>(pred, lg, bg, scale, phi)));
   return ISIS_OK;
 }
 

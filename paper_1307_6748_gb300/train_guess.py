@@ -123,7 +123,8 @@ def main():
     net = unet.UNet(seed=0, mu=-0.5 * SIGMA * SIGMA, sd=SIGMA)
     hist, t_train = train(net, etas, targets, avals, lg, args.epochs)
     assert int(net.err.item()) == 0
-    net.save(args.out)
+    net.save(args.out, model="symmetron", h=1.0, a_ssb=A_SSB, lambda0=1.0, beta=1.0, sigma=SIGMA,
+             pairs=args.pairs, N=args.N, epochs=args.epochs)
     del etas, targets
     torch.cuda.empty_cache()
     ev = evaluate(net, args.eval_N, [9000 + s for s in range(args.eval_seeds)], [0.8, 1.0])

@@ -57,6 +57,8 @@ def _lib():
         "isis_unet_transpose_w": [vp, i, i, vp, vp],
         "isis_unet_to_bf16": [vp, ctypes.c_int64, vp, vp],
         "isis_unet_guess": [vp, i, d, d, vp, vp],
+        "isis_unet_input_pooled": [vp, i, f, f, f, vp, vp],
+        "isis_unet_guess_fine": [vp, i, d, d, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -147,8 +149,14 @@ class UNet:
             out[k] = host[o:o + int(np.prod(shp))].reshape(shp).copy()
         return out
 
-    def save(self, path: str):
-        np.savez(path, **self.state())
+    def save(self, path: str, **meta):
+        """Parameters and input/output scalings, plus metadata (model, training cell size h, ...)."""
+        np.savez_compressed(path, **self.state(), **{"meta_" + k: v for k, v in meta.items()})
+
+    @staticmethod
+    def meta(path: str) -> dict:
+        z = np.load(path)
+        return {k[5:]: z[k].item() for k in z.files if k.startswith("meta_")}
 
     @classmethod
     def load(cls, path: str, device="cuda"):
@@ -286,13 +294,26 @@ class UNet:
         return self.loss
 
     # -- the guess ----------------------------------------------------------
-    def guess(self, eta: torch.Tensor, a: float, a_ssb: float, phi: torch.Tensor):
-        """phi = chi_bg(a) + scale * net(eta, a): FP64 initial guess for isis_scalar_solve."""
+    def guess(self, eta: torch.Tensor, a: float, a_ssb: float, phi: torch.Tensor, pooled: bool = False):
+        """phi = chi_bg(a) + scale * net(eta, a): FP64 initial guess for isis_scalar_solve.
+
+        pooled: eta's grid is twice as fine as the net's training cell size; the net runs on the
+        8-cell means and its output is prolongated (trilinear) to eta's grid."""
         N = eta.shape[0]
-        lg = int(round(math.log2(N)))
-        self.features(eta, a, lg, x16=False)
+        lg = int(round(math.log2(N))) - (1 if pooled else 0)
+        lib = _lib()
+        if pooled:
+            V, A = self.acts(lg)
+            _ck(lib.isis_unet_input_pooled(_p(eta), lg, self.mu, 1.0 / self.sd, (a - 0.9) / 0.1, _p(A["f2"]), _s()),
+                "input_pooled")
+        else:
+            self.features(eta, a, lg, x16=False)
         pred = self.forward(lg)
-        _ck(_lib().isis_unet_guess(_p(pred), lg, isis.chi_background(a, a_ssb), self.scale, _p(phi), _s()), "guess")
+        bg = isis.chi_background(a, a_ssb)
+        if pooled:
+            _ck(lib.isis_unet_guess_fine(_p(pred), lg, bg, self.scale, _p(phi), _s()), "guess_fine")
+        else:
+            _ck(lib.isis_unet_guess(_p(pred), lg, bg, self.scale, _p(phi), _s()), "guess")
         return phi
 
 

@@ -226,3 +226,81 @@ def test_stem_equals_conv_of_features(lib, lg):
         ref = _sampled_conv_ref(x16, 16, 0, None, 0, lg, _np(W), b.cpu().numpy().astype(np.float64), vs)
         got = _rows(out, 16, vs)
     assert np.abs(got - ref).max() <= 2 ** -7 * np.abs(ref).max() + 1e-6
+
+
+WEIGHTS = __import__("os").path.join(__import__("os").path.dirname(__file__), "..", "paper_1307_6748_gb300", "weights",
+                                     "unet_symmetron.npz")
+
+
+def _sym_solve(eta, a, phi, tol, init):
+    from paper_1307_6748_gb300 import isis
+    N = eta.shape[0]
+    opts = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=3, n_coarsest=2, init=init)
+    return isis.isis_scalar_solve(isis.ISIS_SYMMETRON, isis.Params(a_ssb=0.5), isis.Grid(N, float(N)), a, eta, phi,
+                                  tol=tol, opts=opts)
+
+
+def test_trained_guess_gain(cuda_lib):
+    """What the trained net gains on held-out densities (seeds outside the training range), at
+    the training cell size: a guess an order of magnitude closer to the converged field and
+    fewer V-cycles to 1e-8, with the same converged answer."""
+    from paper_1307_6748_gb300 import isis, synth, unet
+    net = unet.UNet.load(WEIGHTS)
+    assert unet.UNet.meta(WEIGHTS)["h"] == 1.0
+    N = 128
+    ref, phi_bg, phi_net = (torch.empty((N,) * 3, dtype=torch.float64, device="cuda") for _ in range(3))
+    rms = lambda x: float(torch.sqrt(torch.mean(x * x)))
+    total = {"bg": 0, "net": 0}
+    for seed in (9100, 9101):
+        eta = synth.lognormal_eta(N, float(N), 1.5, seed, device="cuda")
+        for a in (0.8, 1.0):
+            _sym_solve(eta, a, ref, 1e-10, isis.ISIS_INIT_BACKGROUND)
+            bg = isis.chi_background(a, 0.5)
+            net.guess(eta, a, 0.5, phi_net)
+            e_bg, e_net = rms(ref - bg), rms(ref - phi_net)
+            assert e_net <= 0.2 * e_bg, (seed, a, e_net, e_bg)
+            i_bg = _sym_solve(eta, a, phi_bg, 1e-8, isis.ISIS_INIT_BACKGROUND)
+            i_net = _sym_solve(eta, a, phi_net, 1e-8, isis.ISIS_INIT_INPUT)
+            assert i_net.cycles <= i_bg.cycles, (seed, a, i_net.cycles, i_bg.cycles)
+            total["bg"] += i_bg.cycles
+            total["net"] += i_net.cycles
+            assert rms(phi_net - phi_bg) <= 1e-7 * rms(ref)
+    assert total["net"] < total["bg"], total
+    assert int(net.err.item()) == 0
+
+
+def test_pooled_guess(cuda_lib):
+    """On a grid twice as fine as the training cell size the net runs on the 8-cell means and
+    its output is prolongated; the guess is still much closer than the background."""
+    from paper_1307_6748_gb300 import isis, synth, unet
+    net = unet.UNet.load(WEIGHTS)
+    N, box = 128, 64.0  # h = 0.5 Mpc/h
+    eta = synth.lognormal_eta(N, box, 1.5, 9200, device="cuda")
+    ref, phi = (torch.empty((N,) * 3, dtype=torch.float64, device="cuda") for _ in range(2))
+    opts = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=3, n_coarsest=2, init=isis.ISIS_INIT_BACKGROUND)
+    isis.isis_scalar_solve(isis.ISIS_SYMMETRON, isis.Params(a_ssb=0.5), isis.Grid(N, box), 1.0, eta, ref, tol=1e-10,
+                           opts=opts)
+    net.guess(eta, 1.0, 0.5, phi, pooled=True)
+    rms = lambda x: float(torch.sqrt(torch.mean(x * x)))
+    assert rms(ref - phi) <= 0.5 * rms(ref - isis.chi_background(1.0, 0.5))
+    assert int(net.err.item()) == 0
+
+
+def test_training_reduces_loss(cuda_lib):
+    """Adam steps of the library's own forward/backward kernels on solver-generated pairs."""
+    from paper_1307_6748_gb300 import isis, synth, unet
+    N, lg = 32, 5
+    pairs = []
+    for seed in range(6):
+        eta = synth.lognormal_eta(N, float(N), 1.5, 500 + seed, device="cuda")
+        a = 0.8 if seed % 2 == 0 else 1.0
+        phi = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
+        _sym_solve(eta, a, phi, 1e-8, isis.ISIS_INIT_BACKGROUND)
+        pairs.append((eta, a, (phi - isis.chi_background(a, 0.5)).float().reshape(-1)))
+    net = unet.UNet(seed=1, mu=-1.125, sd=1.5)
+    losses = []
+    for step in range(60):
+        eta, a, t = pairs[step % len(pairs)]
+        losses.append(float(net.train_step(eta, a, t, lg, lr=1e-3).item()))
+    assert int(net.err.item()) == 0
+    assert np.mean(losses[-10:]) < 0.6 * np.mean(losses[:10]), losses
