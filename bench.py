@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--inner-poisson", type=int, default=4, help="FP32 cycles per FP64 outer iteration")
     ap.add_argument("--inner-sym", type=int, default=3)
-    ap.add_argument("--inner-fofr", type=int, default=5)
+    ap.add_argument("--inner-fofr", type=int, default=4)
     ap.add_argument("--ncoarse", type=int, default=2, help="coarsest grid (dense Newton): 2 or 4")
     ap.add_argument("--sample-N", type=int, default=128, help="grid of the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -325,6 +325,9 @@ isis_status isis_scalar_solve(isis_model model, const isis_params* p, const isis
     A.coef.K1 = grid->Omega_m * a * H02;
     A.coef.K2 = grid->Omega_m * a * a * a * a * H02 * (1.0 + 4.0 * r) * std::pow(p->fR0_abs * a * a, 1.0 / np1);
     A.coef.K3 = grid->Omega_m * a * H02 * (1.0 + 4.0 * a * a * a * r);
+    A.coef.fscale = 1.0;  // field form in u itself; the refinement's first phase shifts it
+    A.coef.fKx = A.coef.K2;
+    A.coef.fK3x = A.coef.K3 - A.coef.K2;
     A.ref_scale = A.coef.K1;
     return run_fofr(A);
   }

@@ -32,6 +32,11 @@ enum Form : int { FIELD = 0, DELTA = 1 };
 struct Coef {
   double A, s;          // symmetron: A = a^2/(2 lambda0^2), s = (a_SSB/a)^3
   double K1, K2, K3;    // f(R) source constants (Sect. 4.2)
+  // f(R) field form in a shifted variable x = u - u0 (u0 = 0: x = u):
+  //   b = fscale e^x with fscale = e^{u0};
+  //   S = K1 (eta - 1) - fKx expm1(-x/(n+1)) + fK3x with fKx = K2 e^{-u0/(n+1)}, fK3x = K3 - fKx.
+  // With u0 the background (fK3x = 0) the two large source terms no longer cancel.
+  double fscale, fKx, fK3x;
   double np1, inv_np1;  // n + 1 and its inverse
   double KP, eta_mean;  // Poisson: KP = 1.5 Om H0^2 / a, mean density
 };
@@ -72,22 +77,24 @@ template <> __device__ __forceinline__ float dexpm1<float>(float v) {
 // f(R) in the field form with b = e^x of the cell and its neighbours given:
 //   F  = h^-2 sum_f b_f (x_nb - x) - S(x) - Sigma,   b_f = (b + b_nb)/2
 //   dF = h^-2 sum_f [ (b/2)(x_nb - x) - b_f ] - dS/dx
+// with x the shifted variable and b = fscale e^x (ex, exn: the cached e^x of the cell and its neighbours).
 template <class T>
-__device__ __forceinline__ void fofr_field_eval(const Coef& c, T ih2, T x, T b, const T* xn, const T* bn, T eta,
+__device__ __forceinline__ void fofr_field_eval(const Coef& c, T ih2, T x, T ex, const T* xn, const T* exn, T eta,
                                                 T sig, T& F, T& dF) {
+  const T bs = T(c.fscale), b = bs * ex;
   T flux = 0, dsum = 0;
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     T du = xn[d] - x;
-    T bf = T(0.5) * (b + bn[d]);
+    T bf = T(0.5) * (b + bs * exn[d]);
     flux += bf * du;
     dsum += T(0.5) * b * du - bf;
   }
-  T K2 = T(c.K2), inp1 = T(c.inv_np1);
-  T ex = dexp<T>(-x * inp1);
-  T S = T(c.K1) * (eta - T(1)) - K2 * ex + T(c.K3);
+  T Kx = T(c.fKx), inp1 = T(c.inv_np1);
+  T em = dexpm1<T>(-x * inp1);
+  T S = T(c.K1) * (eta - T(1)) - Kx * em + T(c.fK3x);
   F = flux * ih2 - S - sig;
-  dF = dsum * ih2 - K2 * inp1 * ex;
+  dF = dsum * ih2 - Kx * inp1 * (em + T(1));
 }
 
 // f(R) in the correction form about the base B, with m = e^B expm1(e) and
@@ -164,7 +171,8 @@ __device__ __forceinline__ double eval_offdiag(const Coef& c, double ih2, const 
   if constexpr (M == FOFR) {
     double u = (FM == FIELD) ? q.x : q.B + q.x;
     double un = (FM == FIELD) ? q.xn[d] : q.Bn[d] + q.xn[d];
-    double bu = exp(u), bn = exp(un);
+    const double sc = (FM == FIELD) ? c.fscale : 1.0;  // the field form's shifted variable
+    double bu = sc * exp(u), bn = sc * exp(un);
     return (0.5 * (bu + bn) + 0.5 * bn * (un - u)) * ih2;
   } else {
     return ih2;

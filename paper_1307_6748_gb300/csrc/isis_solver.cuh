@@ -268,6 +268,20 @@ __global__ void from_rb(const float* __restrict__ b, Tout* __restrict__ a, int l
   a[t] = (Tout)b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
 }
 
+// b (red/black FP32) = alpha * a + beta, a row-major FP64
+static __global__ void to_rb_affine(const double* __restrict__ a, float* __restrict__ b, int lg, double alpha, double beta) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ((size_t)1 << (3 * lg))) return;
+  const int m = (1 << lg) - 1;
+  b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))] = (float)(alpha * a[t] + beta);
+}
+// a (row-major FP64) = shift + b, b red/black FP32
+static __global__ void from_rb_shift(const float* __restrict__ b, double* __restrict__ a, int lg, double shift) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ((size_t)1 << (3 * lg))) return;
+  const int m = (1 << lg) - 1;
+  a[t] = shift + (double)b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
+}
 template <class T>
 __global__ void exp_k(const T* __restrict__ a, T* __restrict__ b, size_t n) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -460,8 +474,9 @@ constexpr double kSwitchRel = 1e-4;
 constexpr double kStallRatio = 0.5;
 
 // FP32 cycles + FP64 defect correction.
-//  Phase 1: FAS V-cycles on the field itself in FP32 (psi = fp32(phi)) until
-//           the FP32-evaluated residual is below kSwitchRel * ref or stalls.
+//  Phase 1: FAS V-cycles on the field in FP32 (psi = fp32(phi), for f(R)
+//           psi = fp32(u - u_bar)) until the FP32-evaluated residual is below
+//           kSwitchRel * ref or stalls.
 //  Phase 2: outer loop: r = -L64(phi) in FP64; FP32 FAS V-cycles on the
 //           correction e of L(B + e) - L(B) = r, B = fp32(phi) (DELTA form);
 //           phi += e in FP64; until the FP64 residual is <= tol * ref.
@@ -512,12 +527,23 @@ isis_status solve_refine(const SolveArgs& A) {
   int nh = 0;  // history entries
 
   // ---- phase 1: FP32 field-form cycles ----
-  ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (to_rb<double><<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg)));
-  if (M == FOFR)
+  // f(R) runs in the shifted variable psi = u - u_bar (u_bar the background, S(u_bar) = 0 at
+  // eta = 1): the source S = K1 (eta - 1) - K3 expm1(-psi/(n+1)) no longer cancels two large
+  // terms and psi is small, so FP32 rounding stalls the cycles far later than in u itself.
+  const double u0 = (M == FOFR) ? background_value<FOFR>(c) : 0.0;
+  SolveArgs A1 = A2;
+  if (M == FOFR) {
+    A1.coef.fscale = std::exp(u0);
+    A1.coef.fKx = c.K2 * std::exp(-u0 * c.inv_np1);
+    A1.coef.fK3x = c.K3 - A1.coef.fKx;
+    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (to_rb_affine<<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg, 1.0, -u0)));
     ISIS_LAUNCH(KK_SETUP, 8.0 * n, st, (exp_k<float><<<nblk(n, 256), 256, 0, st>>>(B0, (float*)ws->aux[0], n)));
+  } else {
+    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (to_rb<double><<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg)));
+  }
   {
     Cycler<M, FIELD, float> cy;
-    cy.setup(ws, A2, B0, eta0, nullptr);
+    cy.setup(ws, A1, B0, eta0, nullptr);
     double res;
     s = cy.fine_rms(&res);
     if (s != ISIS_OK) return s;
@@ -543,7 +569,7 @@ isis_status solve_refine(const SolveArgs& A) {
       return ISIS_ENAN;
     }
     const float* psi = cy.L[0].x;
-    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (from_rb<double><<<nblk(n, 256), 256, 0, st>>>(psi, phi64, lg)));
+    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (from_rb_shift<<<nblk(n, 256), 256, 0, st>>>(psi, phi64, lg, u0)));
     // Poisson gauge: the residual does not see the mean, so it is removed once per phase
     if (M == POI) {
       s = remove_mean<double>(ws, phi64, n, st);
