@@ -221,6 +221,12 @@ const char* isis_strerror(isis_status status);
 /* Free every cached workspace buffer (synchronises the device first). */
 void isis_release_workspace(void);
 
+/* Self-test of the float-float exponential used by the f(R) residual of the
+ * FP64 defect correction (table-driven, after Tang, ACM TOMS 1989): y[i] =
+ * exp(x[i]) evaluated in float-float from x[i] rounded to float-float, for
+ * |x| < 20.  x, y: device arrays of n doubles; stream ordered. */
+isis_status isis_selftest_exp_ff(const double* x, double* y, int n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,12 @@ Workspace* get_workspace(int N, int esize, int ncoarse) {
     exp_table_fill(tab);
     ok = w->exptab && cudaMemcpy(w->exptab, tab, sizeof(tab), cudaMemcpyHostToDevice) == cudaSuccess;
   }
+  if (ok) {
+    w->exptab_ff = (float2*)alloc(64 * sizeof(float2));
+    float2 tab[64];
+    ff_exp_table_fill(tab);
+    ok = w->exptab_ff && cudaMemcpy(w->exptab_ff, tab, sizeof(tab), cudaMemcpyHostToDevice) == cudaSuccess;
+  }
   if (!ok) {
     free_ws(w);
     cudaGetLastError();
@@ -265,6 +271,22 @@ void isis_prof_reset(void) {
 }
 
 int64_t isis_launch_count(void) { return g_launches; }
+
+isis_status isis_selftest_exp_ff(const double* x, double* y, int n, void* stream) {
+  if (!x || !y || n < 0) return ISIS_EINVAL;
+  if (n == 0) return ISIS_OK;
+  static float2* tab = nullptr;
+  if (!tab) {
+    float2 h[64];
+    ff_exp_table_fill(h);
+    if (cudaMalloc(&tab, sizeof(h)) != cudaSuccess) return ISIS_ENOMEM;
+    if (cudaMemcpy(tab, h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) return ISIS_ECUDA;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  ISIS_LAUNCH(KK_SETUP, 16.0 * n, st,
+              (selftest_exp_ff<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n, tab, ff_exp_consts())));
+  return ISIS_OK;
+}
 
 int isis_prof_read(isis_prof_entry* out, int max) {
   cudaDeviceSynchronize();

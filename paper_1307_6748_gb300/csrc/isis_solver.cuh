@@ -12,6 +12,7 @@
 #include "../../include/isis.h"
 #include "isis_coarse.cuh"
 #include "isis_exp64.cuh"
+#include "isis_ff.cuh"
 #include "isis_prof.cuh"
 
 namespace isis {
@@ -38,8 +39,9 @@ struct Workspace {
   int* iflags = nullptr;      // [0] coarse flags, [1] coarse steps max
   void* host = nullptr;       // pinned readback area
   double* exptab = nullptr;   // 2^(j/256), j < 256, for exp_tang
-  double* b64 = nullptr;      // finest level, FP64: e^u (f(R) residual), allocated on first use
-  double* s64 = nullptr;      // finest level, FP64: S(u, eta) (f(R) residual)
+  float2* exptab_ff = nullptr;  // 2^(j/64), j < 64, float-float, for exp_ff
+  double* b64 = nullptr;      // finest level, 8 bytes per cell: psi = u - u_bar (float-float), f(R) residual
+  double* s64 = nullptr;      // finest level, 8 bytes per cell: e^psi (float-float), f(R) residual
   std::vector<void*> owned;
 };
 
@@ -354,6 +356,52 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual(LevelView<double>
   block_sum_store<double>(acc, part);
 }
 
+// The same residual for Poisson and the symmetron in float-float (FP32 instruction
+// throughput; the operator of Sect. 3.1, and of Eq. (symmetron_dimensionles)).
+struct ResFF {
+  float2 ih2;          // 1/h^2
+  float2 K;            // Poisson: 1.5 Omega_m H0^2 / a; symmetron: A = a^2 / (2 lambda0^2)
+  double s, eta_mean;  // symmetron: (a_SSB/a)^3; Poisson: mean density
+};
+static __global__ void phi_to_ff(const double* __restrict__ phi, float2* __restrict__ out, size_t n) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = ff_store(ff_from_double(phi[t]));
+}
+template <Model M>
+__global__ void __launch_bounds__(kNormThreads) outer_residual_ff(int lg, ResFF c, const double* __restrict__ phi,
+                                                                  const double* __restrict__ eta,
+                                                                  const float2* __restrict__ pff,
+                                                                  float* __restrict__ r32, float* __restrict__ B32,
+                                                                  double* __restrict__ part) {
+  const size_t n = (size_t)1 << (3 * lg);
+  const int m = (1 << lg) - 1;
+  const ff ih2 = ff_load(c.ih2), K = ff_load(c.K);
+  float acc = 0.f;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    int k = (int)(t & m), j = (int)((t >> lg) & m), i = (int)(t >> (2 * lg));
+    size_t nb[6] = {cidx(lg, (i + 1) & m, j, k), cidx(lg, (i - 1) & m, j, k), cidx(lg, i, (j + 1) & m, k),
+                    cidx(lg, i, (j - 1) & m, k), cidx(lg, i, j, (k + 1) & m), cidx(lg, i, j, (k - 1) & m)};
+    const ff pc = ff_load(pff[t]);
+    ff sd = {0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < 6; ++d) sd = ff_add(sd, ff_sub(ff_load(pff[nb[d]]), pc));
+    const ff lap = ff_mul(sd, ih2);
+    ff F;
+    if constexpr (M == POI) {
+      F = ff_sub(lap, ff_mul(K, ff_from_double(eta[t] - c.eta_mean)));
+    } else {  // symmetron: L = lap - A [(s eta - 1) chi + chi^3]
+      const ff q = ff_from_double(fma(c.s, eta[t], -1.0));
+      const ff x2 = ff_mul(pc, pc);
+      F = ff_sub(lap, ff_mul(K, ff_mul(ff_add(q, x2), pc)));
+    }
+    const size_t o = lidx<float>(lg, i, j, k);
+    r32[o] = -(F.hi + F.lo);
+    B32[o] = (float)phi[t];
+    acc = fmaf(F.hi, F.hi, acc);
+  }
+  block_sum_store<double>((double)acc, part);
+}
+
 // f(R), first pass: per cell b = e^u and S(u, eta) = K1 (eta - 1) - K2 e^{-u/(n+1)} + K3,
 // each exponential evaluated once per cell (Sect. 4.2).
 __global__ void fofr_prep64(const double* __restrict__ u, const double* __restrict__ eta, double* __restrict__ b,
@@ -366,6 +414,29 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr(int lg, doub
                                                                     const double* __restrict__ S,
                                                                     float* __restrict__ r32, float* __restrict__ B32,
                                                                     double* __restrict__ part);
+
+// f(R) residual in float-float (the two passes above at FP32 instruction throughput).
+// Constants: psi = u - ub, C = e^ub, S = K1 (eta - 1) - Kx expm1(-psi/(n+1)) + dK.
+struct FofrFF {
+  double ub, inv_np1;
+  float2 Cih2, K1, Kx, minv;  // C / h^2, K1, Kx = K2 e^{-ub/(n+1)}, -1/(n+1) (float-float)
+  float dK;                   // K3 - Kx (zero up to rounding)
+  FFExp ek;
+};
+__global__ void selftest_exp_ff(const double* __restrict__ x, double* __restrict__ y, int n,
+                                const float2* __restrict__ tab, FFExp ek);
+// first pass: psi = u - ub and e^psi per cell (float-float, 8 bytes each)
+__global__ void fofr_prep_ff(const double* __restrict__ u, float2* __restrict__ psi, float2* __restrict__ E,
+                             size_t n, double ub, const float2* __restrict__ tab, FFExp ek);
+// second pass: r = -L(u) (written FP32, red/black), B = fp32(u), block partials of r^2
+__global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, FofrFF c, const double* __restrict__ u,
+                                                                       const double* __restrict__ eta,
+                                                                       const float2* __restrict__ psi,
+                                                                       const float2* __restrict__ E,
+                                                                       const float2* __restrict__ tab,
+                                                                       float* __restrict__ r32,
+                                                                       float* __restrict__ B32,
+                                                                       double* __restrict__ part);
 
 // ---------------------------------------------------------------------------
 // Drivers
@@ -484,7 +555,7 @@ template <Model M>
 isis_status solve_refine(const SolveArgs& A) {
   Workspace* ws = get_workspace(A.N, sizeof(float), A.ncoarse);
   if (!ws) return ISIS_ENOMEM;
-  if (M == FOFR && !ensure_fofr64(ws)) return ISIS_ENOMEM;
+  if (!ensure_fofr64(ws)) return ISIS_ENOMEM;  // float-float scratch of the FP64-accurate residual
   cudaStream_t st = A.st;
   const size_t n = (size_t)A.N * A.N * A.N;
   const double* eta64 = (const double*)A.eta;
@@ -591,6 +662,23 @@ isis_status solve_refine(const SolveArgs& A) {
 
   Cycler<M, DELTA, float> cy;
   cy.setup(ws, A2, e0, eta0, r0);
+  ResFF rff{};
+  rff.ih2 = ff_split_host(F64.ih2);
+  rff.K = ff_split_host(M == POI ? c.KP : c.A);
+  rff.s = c.s;
+  rff.eta_mean = c.eta_mean;
+  FofrFF ffc{};
+  if (M == FOFR) {
+    const double ub = background_value<FOFR>(c), Kx = c.K2 * std::exp(-ub * c.inv_np1);
+    ffc.ub = ub;
+    ffc.inv_np1 = c.inv_np1;
+    ffc.Cih2 = ff_split_host(std::exp(ub) * F64.ih2);
+    ffc.K1 = ff_split_host(c.K1);
+    ffc.Kx = ff_split_host(Kx);
+    ffc.minv = ff_split_host(-c.inv_np1);
+    ffc.dK = (float)(c.K3 - Kx);
+    ffc.ek = ff_exp_consts();
+  }
 
   double* h = (double*)ws->host;
   int* hi = (int*)(h + 4);
@@ -601,14 +689,19 @@ isis_status solve_refine(const SolveArgs& A) {
   for (int outer = 0;; ++outer) {
     // r = -L64(phi64), B = fp32(phi64), RMS of r
     if (M == FOFR) {
-      ISIS_LAUNCH(KK_OUTER_RESID, 32.0 * n, st,
-                  (fofr_prep64<<<nblk(n, 256), 256, 0, st>>>(phi64, eta64, ws->b64, ws->s64, n, c, ws->exptab)));
-      ISIS_LAUNCH(KK_OUTER_RESID, 32.0 * n, st,
-                  (outer_residual_fofr<<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, F64.ih2, phi64, ws->b64,
-                                                                              ws->s64, r0, B0, ws->part)));
-    } else {
+      float2* psi_ff = reinterpret_cast<float2*>(ws->b64);
+      float2* E_ff = reinterpret_cast<float2*>(ws->s64);
       ISIS_LAUNCH(KK_OUTER_RESID, 24.0 * n, st,
-                  (outer_residual<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64, c, r0, B0, ws->part)));
+                  (fofr_prep_ff<<<nblk(n, 256), 256, 0, st>>>(phi64, psi_ff, E_ff, n, ffc.ub, ws->exptab_ff, ffc.ek)));
+      ISIS_LAUNCH(KK_OUTER_RESID, 40.0 * n, st,
+                  (outer_residual_fofr_ff<<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, ffc, phi64, eta64, psi_ff, E_ff,
+                                                                                 ws->exptab_ff, r0, B0, ws->part)));
+    } else {
+      float2* pff = reinterpret_cast<float2*>(ws->b64);
+      ISIS_LAUNCH(KK_OUTER_RESID, 16.0 * n, st, (phi_to_ff<<<nblk(n, 256), 256, 0, st>>>(phi64, pff, n)));
+      ISIS_LAUNCH(KK_OUTER_RESID, 24.0 * n, st,
+                  (outer_residual_ff<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, rff, phi64, eta64, pff, r0, B0,
+                                                                              ws->part)));
     }
     ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
     ISIS_CK(cudaMemcpyAsync(h, ws->scal, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -26,7 +26,7 @@ H0_MPC = 1.0 / 2997.92458  # (Mpc/h)^-1 with c = 1
 # Every function the header declares (checked by the tests).
 EXPORTS = ("isis_cic_deposit", "isis_cic_deposit_noalloc", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force",
            "isis_strerror", "isis_release_workspace", "isis_prof_enable", "isis_prof_reset", "isis_prof_read",
-           "isis_launch_count")
+           "isis_launch_count", "isis_selftest_exp_ff")
 ISIS_INIT_INPUT, ISIS_INIT_BACKGROUND, ISIS_INIT_LOCAL = 0, 1, 2
 
 
@@ -328,3 +328,18 @@ PRESETS = {
     "fofr5": Params(n=1, fR0_abs=1e-5),
     "fofr6": Params(n=1, fR0_abs=1e-6),
 }
+
+
+def selftest_exp_ff(x: torch.Tensor) -> torch.Tensor:
+    """exp of a CUDA FP64 tensor through the library's float-float exponential (self-test)."""
+    lib = load()
+    fn = lib.isis_selftest_exp_ff
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    st = fn(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.numel(),
+            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != 0:
+        raise IsisError(st, strerror(st))
+    return y

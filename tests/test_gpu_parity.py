@@ -4,6 +4,8 @@ FP64 path: same inputs, same cycle count, max-abs difference <= 1e-10 on the
 scalar field (relative to max|Phi| for the Newtonian potential).  Mixed
 precision: relative L2 <= 1e-9 against the oracle's converged solution.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -285,3 +287,18 @@ def test_refine64_streaming_matches_oracle(cuda_lib, model, N):
     else:
         rel = np.linalg.norm(got - ref.phi) / np.linalg.norm(ref.phi)
     assert rel <= 1e-9, rel
+
+
+def test_exp_ff_accuracy(cuda_lib):
+    """The float-float exponential of the f(R) residual against CUDA's FP64 exp: relative error within
+    the float-float rounding of its argument (about 2^-48 |x|) plus a few float-float ulps."""
+    import torch
+    from paper_1307_6748_gb300 import isis
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.cat([torch.linspace(-19.9, 19.9, 1_000_001, dtype=torch.float64, device="cuda"),
+                   (torch.rand(200_000, generator=g, device="cuda", dtype=torch.float64) - 0.5) * 1e-3,
+                   torch.arange(-1400, 1400, dtype=torch.float64, device="cuda") * (math.log(2.0) / 128.0)])
+    y = isis.selftest_exp_ff(x)
+    rel = ((y - torch.exp(x)) / torch.exp(x)).abs()
+    bound = 4e-15 * x.abs() + 1e-14
+    assert bool((rel <= bound).all()), float((rel / bound).max())
