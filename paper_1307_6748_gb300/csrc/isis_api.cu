@@ -65,12 +65,6 @@ Workspace* get_workspace(int N, int esize, int ncoarse) {
   }
   if (ok && cudaMallocHost(&w->host, 256) != cudaSuccess) ok = false;
   if (ok) {
-    w->exptab = (double*)alloc(256 * sizeof(double));
-    double tab[256];
-    exp_table_fill(tab);
-    ok = w->exptab && cudaMemcpy(w->exptab, tab, sizeof(tab), cudaMemcpyHostToDevice) == cudaSuccess;
-  }
-  if (ok) {
     w->exptab_ff = (float2*)alloc(64 * sizeof(float2));
     float2 tab[64];
     ff_exp_table_fill(tab);

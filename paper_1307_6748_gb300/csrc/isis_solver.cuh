@@ -11,7 +11,6 @@
 
 #include "../../include/isis.h"
 #include "isis_coarse.cuh"
-#include "isis_exp64.cuh"
 #include "isis_ff.cuh"
 #include "isis_prof.cuh"
 
@@ -38,7 +37,6 @@ struct Workspace {
   double* scal = nullptr;     // device scalars: [0] norm^2, [1] sum, [2] aux
   int* iflags = nullptr;      // [0] coarse flags, [1] coarse steps max
   void* host = nullptr;       // pinned readback area
-  double* exptab = nullptr;   // 2^(j/256), j < 256, for exp_tang
   float2* exptab_ff = nullptr;  // 2^(j/64), j < 64, float-float, for exp_ff
   double* b64 = nullptr;      // finest level, 8 bytes per cell: psi = u - u_bar (float-float), f(R) residual
   double* s64 = nullptr;      // finest level, 8 bytes per cell: e^psi (float-float), f(R) residual
@@ -334,30 +332,10 @@ isis_status apply_init(const SolveArgs& A, const Coef& c, T* phi, const T* eta, 
   return ISIS_OK;
 }
 
-// FP64 residual of the finest grid for the defect-correction loop:
-// r = -L64(phi); writes r and B = phi rounded to FP32 (red/black layout), and
-// block partials of r^2.
-// (Poisson and symmetron: the operator has no transcendental terms.)
-template <Model M>
-__global__ void __launch_bounds__(kNormThreads) outer_residual(LevelView<double> L, Coef c, float* __restrict__ r32,
-                                                               float* __restrict__ B32, double* __restrict__ part) {
-  size_t n = (size_t)1 << (3 * L.lg);
-  double acc = 0.0;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    int k = (int)(t & (L.N - 1)), j = (int)((t >> L.lg) & (L.N - 1)), i = (int)(t >> (2 * L.lg));
-    Cell<double> q = gather<M, FIELD, double>(L, i, j, k);
-    double F, dF;
-    eval_cell<M, FIELD, double>(c, L.ih2, q, F, dF);
-    const size_t o = lidx<float>(L.lg, i, j, k);
-    r32[o] = (float)(-F);
-    B32[o] = (float)q.x;
-    acc += F * F;
-  }
-  block_sum_store<double>(acc, part);
-}
-
-// The same residual for Poisson and the symmetron in float-float (FP32 instruction
-// throughput; the operator of Sect. 3.1, and of Eq. (symmetron_dimensionles)).
+// FP64-accurate residual of the finest grid for the defect-correction loop, in
+// float-float (FP32 instruction throughput): r = -L(phi), written FP32 in the
+// red/black layout with B = fp32(phi) and block partials of r^2.  Poisson and the
+// symmetron here (the operator of Sect. 3.1, and of Eq. (symmetron_dimensionles)).
 struct ResFF {
   float2 ih2;          // 1/h^2
   float2 K;            // Poisson: 1.5 Omega_m H0^2 / a; symmetron: A = a^2 / (2 lambda0^2)
@@ -402,20 +380,7 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_ff(int lg, ResFF 
   block_sum_store<double>((double)acc, part);
 }
 
-// f(R), first pass: per cell b = e^u and S(u, eta) = K1 (eta - 1) - K2 e^{-u/(n+1)} + K3,
-// each exponential evaluated once per cell (Sect. 4.2).
-__global__ void fofr_prep64(const double* __restrict__ u, const double* __restrict__ eta, double* __restrict__ b,
-                            double* __restrict__ S, size_t n, Coef c, const double* __restrict__ tab);
-
-// f(R), second pass: flux form of Eq. (disc_non_canonical) with face b = (b_c + b_nb)/2:
-//   sum_f b_f (u_nb - u) = [ b_c (sum u_nb - 6 u) + sum b_nb u_nb - u sum b_nb ] / 2
-__global__ void __launch_bounds__(kNormThreads) outer_residual_fofr(int lg, double ih2, const double* __restrict__ u,
-                                                                    const double* __restrict__ b,
-                                                                    const double* __restrict__ S,
-                                                                    float* __restrict__ r32, float* __restrict__ B32,
-                                                                    double* __restrict__ part);
-
-// f(R) residual in float-float (the two passes above at FP32 instruction throughput).
+// f(R) residual in float-float (FP32 instruction throughput), two passes.
 // Constants: psi = u - ub, C = e^ub, S = K1 (eta - 1) - Kx expm1(-psi/(n+1)) + dK.
 struct FofrFF {
   double ub, inv_np1;
