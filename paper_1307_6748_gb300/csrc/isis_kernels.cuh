@@ -591,6 +591,26 @@ __global__ void __launch_bounds__(kNormThreads) norm_partial(LevelView<T> L, Coe
   block_sum_store<T>(acc, part);
 }
 
+// Block partial sums of (L(x) - Sigma)^2 over a red/black FP32 grid, two cells per thread
+// and iteration (the smoother's gather), a grid-stride loop over the pairs of both colours
+// with a fixed assignment: reproducible.
+template <Model M, Form FM>
+__global__ void __launch_bounds__(kNormThreads) norm_rb2(LevelView<float> L, Coef c, double* __restrict__ part) {
+  const unsigned q4 = 1u << (3 * L.lg - 2);
+  float acc = 0.f;
+  for (unsigned tt = blockIdx.x * blockDim.x + threadIdx.x; tt < 2 * q4; tt += gridDim.x * blockDim.x) {
+    const int color = tt >= q4 ? 1 : 0;
+    Cell<float> q0, q1;
+    rb2_gather<M, FM>(L, color, tt - (color ? q4 : 0u), q0, q1);
+    float F0, dF0, F1, dF1;
+    eval_cell<M, FM, float>(c, L.ih2, q0, F0, dF0);
+    eval_cell<M, FM, float>(c, L.ih2, q1, F1, dF1);
+    acc = fmaf(F0, F0, fmaf(F1, F1, acc));
+  }
+  block_sum_store<double>((double)acc, part);
+}
+
+
 // Sum of (v - shift)^2 and of v over an array (for the reference residual
 // and the Poisson mean).
 template <class T>

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/isis.h"
@@ -193,8 +194,18 @@ struct Cycler {
 
   // RMS of L(x) - Sigma on the finest level (blocking: one stream sync).
   isis_status fine_rms(double* out) {
-    ISIS_LAUNCH(KK_NORM, cells(L[0]) * sizeof(T) * (1 + arrays(L[0].sig != nullptr)), st,
-                (norm_partial<M, FM, T><<<kNormBlocks, kNormThreads, 0, st>>>(L[0], c, ws->part)));
+    if constexpr (std::is_same<T, float>::value) {
+      if (L[0].lg >= 3) {
+        ISIS_LAUNCH(KK_NORM, cells(L[0]) * sizeof(T) * (1 + arrays(L[0].sig != nullptr)), st,
+                    (norm_rb2<M, FM><<<kNormBlocks, kNormThreads, 0, st>>>(L[0], c, ws->part)));
+      } else {
+        ISIS_LAUNCH(KK_NORM, cells(L[0]) * sizeof(T) * (1 + arrays(L[0].sig != nullptr)), st,
+                    (norm_partial<M, FM, T><<<kNormBlocks, kNormThreads, 0, st>>>(L[0], c, ws->part)));
+      }
+    } else {
+      ISIS_LAUNCH(KK_NORM, cells(L[0]) * sizeof(T) * (1 + arrays(L[0].sig != nullptr)), st,
+                  (norm_partial<M, FM, T><<<kNormBlocks, kNormThreads, 0, st>>>(L[0], c, ws->part)));
+    }
     ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
     double* h = (double*)ws->host;
     int* hi = (int*)(h + 4);
