@@ -29,10 +29,10 @@ __global__ void __launch_bounds__(kCoarseMax) coarse_newton(LevelView<T> L, Coef
   const size_t gr = r < n ? lidx<T>(lg, i, j, k) : 0;  // storage index of unknown r
   if (r < n) {
     xs[r] = (double)L.x[gr];
-    etas[r] = (M == POI && FM == DELTA) ? 0.0 : (double)L.eta[gr];
+    etas[r] = uses_eta<M, FM>() ? (double)L.eta[gr] : 0.0;
     sigs[r] = L.sig ? (double)L.sig[gr] : 0.0;
     Bs[r] = (FM == DELTA && M != POI) ? (double)L.B[gr] : 0.0;
-    ws[r] = (FM == DELTA && M == FOFR) ? (double)L.w[gr] : 0.0;
+    ws[r] = (FM == DELTA && M == FOFR) ? (double)dexp<T>(L.B[gr]) : 0.0;  // e^B as the grids' kernels evaluate it
   }
   if (r == 0) { done = 0; bad = 0; }
   __syncthreads();
@@ -126,7 +126,6 @@ __global__ void __launch_bounds__(kCoarseMax) coarse_newton(LevelView<T> L, Coef
   }
   if (r < n) {
     L.x[gr] = (T)xs[r];
-    if constexpr (M == FOFR) L.aux[gr] = aux_of<M, FM, T>((T)xs[r], (T)ws[r]);
   }
   if (r == 0) {
     if (bad) atomicOr(flags, bad);

@@ -127,6 +127,28 @@ __device__ __forceinline__ void stencil_of_storage(int lg, size_t t, size_t* nb)
   }
 }
 
+// The f(R) per-cell exponentials of a gathered cell, from its values: e^x in the
+// field form; w = e^B and m = w expm1(e) in the correction form.  Evaluated where
+// they are used (one MUFU exponential each) instead of being kept in grids: the
+// sweeps then read two grids of the other colour instead of four.
+template <Model M, Form FM, class T>
+__device__ __forceinline__ void fill_exps(Cell<T>& q) {
+  if constexpr (M == FOFR) {
+    if constexpr (FM == DELTA) {
+      q.w = dexp<T>(q.B);
+#pragma unroll
+      for (int d = 0; d < 6; ++d) q.wn[d] = dexp<T>(q.Bn[d]);
+    } else {
+      q.w = T(0);
+#pragma unroll
+      for (int d = 0; d < 6; ++d) q.wn[d] = T(0);
+    }
+    q.a = aux_of<M, FM, T>(q.x, q.w);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) q.an[d] = aux_of<M, FM, T>(q.xn[d], q.wn[d]);
+  }
+}
+
 // Gather the cell stored at t and its neighbours.
 template <Model M, Form FM, class T>
 __device__ __forceinline__ Cell<T> gather_at(const LevelView<T>& L, size_t c) {
@@ -137,18 +159,13 @@ __device__ __forceinline__ Cell<T> gather_at(const LevelView<T>& L, size_t c) {
 #pragma unroll
   for (int d = 0; d < 6; ++d) q.xn[d] = L.x[nb[d]];
   q.sig = L.sig ? L.sig[c] : T(0);
-  if constexpr (!(M == POI && FM == DELTA)) q.eta = L.eta[c]; else q.eta = T(0);
+  if constexpr (uses_eta<M, FM>()) q.eta = L.eta[c]; else q.eta = T(0);
   if constexpr (FM == DELTA && M != POI) q.B = L.B[c]; else q.B = T(0);
   if constexpr (FM == DELTA && M == FOFR) {
-    q.w = L.w[c];
 #pragma unroll
-    for (int d = 0; d < 6; ++d) { q.Bn[d] = L.B[nb[d]]; q.wn[d] = L.w[nb[d]]; }
+    for (int d = 0; d < 6; ++d) q.Bn[d] = L.B[nb[d]];
   }
-  if constexpr (M == FOFR) {
-    q.a = L.aux[c];
-#pragma unroll
-    for (int d = 0; d < 6; ++d) q.an[d] = L.aux[nb[d]];
-  }
+  fill_exps<M, FM, T>(q);
   return q;
 }
 
@@ -162,18 +179,13 @@ __device__ __forceinline__ Cell<T> gather(const LevelView<T>& L, int i, int j, i
 #pragma unroll
   for (int d = 0; d < 6; ++d) q.xn[d] = L.x[nb[d]];
   q.sig = L.sig ? L.sig[c] : T(0);
-  if constexpr (!(M == POI && FM == DELTA)) q.eta = L.eta[c]; else q.eta = T(0);
+  if constexpr (uses_eta<M, FM>()) q.eta = L.eta[c]; else q.eta = T(0);
   if constexpr (FM == DELTA && M != POI) q.B = L.B[c]; else q.B = T(0);
   if constexpr (FM == DELTA && M == FOFR) {
-    q.w = L.w[c];
 #pragma unroll
-    for (int d = 0; d < 6; ++d) { q.Bn[d] = L.B[nb[d]]; q.wn[d] = L.w[nb[d]]; }
+    for (int d = 0; d < 6; ++d) q.Bn[d] = L.B[nb[d]];
   }
-  if constexpr (M == FOFR) {
-    q.a = L.aux[c];
-#pragma unroll
-    for (int d = 0; d < 6; ++d) q.an[d] = L.aux[nb[d]];
-  }
+  fill_exps<M, FM, T>(q);
   return q;
 }
 
@@ -199,7 +211,6 @@ __global__ void smooth_color(LevelView<T> L, Coef c, int color) {
   else xn = q.x - F / dF;
   const size_t o = lidx<T>(L.lg, i, j, k);
   L.x[o] = xn;
-  if constexpr (M == FOFR) L.aux[o] = aux_of<M, FM, T>(xn, q.w);
 }
 
 // One colour of a Newton-Gauss-Seidel sweep on a red/black split FP32 grid.
@@ -228,24 +239,18 @@ __global__ void __launch_bounds__(256) smooth_rb(LevelView<float> L, Coef c, int
 #pragma unroll
   for (int d = 0; d < 6; ++d) q.xn[d] = L.x[nb[d]];
   q.sig = L.sig ? L.sig[o] : 0.f;
-  if constexpr (!(M == POI && FM == DELTA)) q.eta = L.eta[o]; else q.eta = 0.f;
+  if constexpr (uses_eta<M, FM>()) q.eta = L.eta[o]; else q.eta = 0.f;
   if constexpr (FM == DELTA && M != POI) q.B = L.B[o]; else q.B = 0.f;
   if constexpr (FM == DELTA && M == FOFR) {
-    q.w = L.w[o];
 #pragma unroll
-    for (int d = 0; d < 6; ++d) { q.Bn[d] = L.B[nb[d]]; q.wn[d] = L.w[nb[d]]; }
+    for (int d = 0; d < 6; ++d) q.Bn[d] = L.B[nb[d]];
   }
-  if constexpr (M == FOFR) {
-    q.a = L.aux[o];
-#pragma unroll
-    for (int d = 0; d < 6; ++d) q.an[d] = L.aux[nb[d]];
-  }
+  fill_exps<M, FM, float>(q);
   float F, dF;
   eval_cell<M, FM, float>(c, L.ih2, q, F, dF);
   // FP32 cycles drive a correction: a 2-ulp quotient is ample there
   const float xn = q.x - __fdividef(F, dF);
   L.x[o] = xn;
-  if constexpr (M == FOFR) L.aux[o] = aux_of<M, FM, float>(xn, q.w);
 }
 
 // Storage positions of the cells k = 2K-1, 2K, 2K+1, 2K+2 of row (i, j).
@@ -307,7 +312,7 @@ __device__ __forceinline__ unsigned rb2_gather(const LevelView<float>& L, int co
   } else {
     q0.sig = q1.sig = 0.f;
   }
-  if constexpr (!(M == POI && FM == DELTA)) {
+  if constexpr (uses_eta<M, FM>()) {
     const float2 v = *reinterpret_cast<const float2*>(L.eta + o);
     q0.eta = v.x;
     q1.eta = v.y;
@@ -321,21 +326,9 @@ __device__ __forceinline__ unsigned rb2_gather(const LevelView<float>& L, int co
   } else {
     q0.B = q1.B = 0.f;
   }
-  if constexpr (FM == DELTA && M == FOFR) {
-    const float2 v = *reinterpret_cast<const float2*>(L.w + o);
-    q0.w = v.x;
-    q1.w = v.y;
-    nbrs(L.B, q0.Bn, q1.Bn);
-    nbrs(L.w, q0.wn, q1.wn);
-  } else {
-    q0.w = q1.w = 0.f;
-  }
-  if constexpr (M == FOFR) {
-    const float2 v = *reinterpret_cast<const float2*>(L.aux + o);
-    q0.a = v.x;
-    q1.a = v.y;
-    nbrs(L.aux, q0.an, q1.an);
-  }
+  if constexpr (FM == DELTA && M == FOFR) nbrs(L.B, q0.Bn, q1.Bn);
+  fill_exps<M, FM, float>(q0);
+  fill_exps<M, FM, float>(q1);
   return o;
 }
 
@@ -351,9 +344,6 @@ __global__ void __launch_bounds__(256) smooth_rb2(LevelView<float> L, Coef c, in
   // FP32 cycles drive a correction: a 2-ulp quotient is ample there
   const float xn0 = q0.x - __fdividef(F0, dF0), xn1 = q1.x - __fdividef(F1, dF1);
   *reinterpret_cast<float2*>(L.x + o) = make_float2(xn0, xn1);
-  if constexpr (M == FOFR)
-    *reinterpret_cast<float2*>(L.aux + o) =
-        make_float2(aux_of<M, FM, float>(xn0, q0.w), aux_of<M, FM, float>(xn1, q1.w));
 }
 
 // Residual r = Sigma - L(x) of every cell of a red/black FP32 grid into res
@@ -397,7 +387,6 @@ __global__ void restrict_xr(LevelView<float> F, const float* __restrict__ res, L
   C.x[to] = xr;
   x0c[to] = xr;
   sigc[to] = rs * 0.125f;
-  if constexpr (M == FOFR) C.aux[to] = aux_of<M, FM, float>(xr, FM == DELTA ? C.w[to] : 0.f);
 }
 
 // One thread per coarse cell (I,J,K): residuals r = Sigma - L(x) of its 8
@@ -406,7 +395,7 @@ __global__ void restrict_xr(LevelView<float> F, const float* __restrict__ res, L
 // without the 4 corner rows) are loaded once.
 template <Model M, Form FM, class T>
 __global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __restrict__ x0c, T* __restrict__ sigc) {
-  constexpr bool kAllB = (FM == DELTA && M == FOFR);   // neighbours' B, w, aux needed
+  constexpr bool kAllB = (FM == DELTA && M == FOFR);   // neighbours' B (and e^B) needed
   constexpr bool kAux = (M == FOFR);
   T* __restrict__ xc = C.x;
   const int lgc = F.lg - 1, lg = F.lg, m = F.N - 1;
@@ -431,8 +420,9 @@ __global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __rest
         if ((ea || eb) && (d == 0 || d == 3)) continue;
         P[a][b][d] = p[d];
         X[a][b][d] = F.x[p[d]];
-        if constexpr (kAux) Ax[a][b][d] = F.aux[p[d]];
-        if constexpr (kAllB) { Bx[a][b][d] = F.B[p[d]]; Wx[a][b][d] = F.w[p[d]]; }
+        // the f(R) exponentials of each loaded cell, once for the 8 stencils (fill_exps)
+        if constexpr (kAllB) { Bx[a][b][d] = F.B[p[d]]; Wx[a][b][d] = dexp<T>(Bx[a][b][d]); }
+        if constexpr (kAux) Ax[a][b][d] = aux_of<M, FM, T>(X[a][b][d], kAllB ? Wx[a][b][d] : T(0));
       }
     }
   T xs = 0, rs = 0;
@@ -449,7 +439,7 @@ __global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __rest
         q.xn[2] = X[a][b + 1][d]; q.xn[3] = X[a][b - 1][d];
         q.xn[4] = X[a][b][d + 1]; q.xn[5] = X[a][b][d - 1];
         q.sig = F.sig ? F.sig[pc] : T(0);
-        if constexpr (!(M == POI && FM == DELTA)) q.eta = F.eta[pc]; else q.eta = T(0);
+        if constexpr (uses_eta<M, FM>()) q.eta = F.eta[pc]; else q.eta = T(0);
         if constexpr (FM == DELTA && M != POI) q.B = F.B[pc]; else q.B = T(0);
         if constexpr (kAllB) {
           q.w = Wx[a][b][d];
@@ -475,7 +465,6 @@ __global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __rest
   xc[to] = xr;
   x0c[to] = xr;
   sigc[to] = rs * T(0.125);
-  if constexpr (M == FOFR) C.aux[to] = aux_of<M, FM, T>(xr, FM == DELTA ? C.w[to] : T(0));
 }
 
 // Sigma_H += L_H(x_H) (the FAS coarse source, Sect. 3.2).
@@ -540,7 +529,6 @@ __global__ void prolong_correct(LevelView<T> Fv, const T* __restrict__ xc, const
         const size_t o = lidx<T>(lgf, 2 * I + ca, 2 * J + cb, 2 * K + cd);
         const T xn = xf[o] + v;
         xf[o] = xn;
-        if constexpr (M == FOFR) Fv.aux[o] = aux_of<M, FM, T>(xn, FM == DELTA ? Fv.w[o] : T(0));
       }
 }
 

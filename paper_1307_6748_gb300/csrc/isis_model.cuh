@@ -153,7 +153,12 @@ __device__ __forceinline__ void eval_cell(const Coef& c, T ih2, const Cell<T>& q
   }
 }
 
-// The cached per-cell exponential of f(R) for a cell holding x (and e^B = w).
+// Whether the operator reads the density: not in the correction forms of Poisson
+// (linear) and f(R) (eta enters only its right-hand side).
+template <Model M, Form FM>
+__host__ __device__ constexpr bool uses_eta() { return !(FM == DELTA && M != SYM); }
+
+// The per-cell exponential of f(R) for a cell holding x (and e^B = w).
 template <Model M, Form FM, class T>
 __device__ __forceinline__ T aux_of(T x, T w) {
   if constexpr (M == FOFR && FM == FIELD) return dexp<T>(x);

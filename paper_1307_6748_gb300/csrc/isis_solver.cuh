@@ -118,12 +118,11 @@ struct Cycler {
     }
   }
 
-  // per-cell input arrays read by the operator besides x (eta, B, w, Sigma)
+  // per-cell input arrays read by the operator besides x (eta, B, Sigma)
   static int arrays(bool has_sig) {
     int n = has_sig ? 1 : 0;
-    if (!(M == POI && FM == DELTA)) n += 1;   // eta
-    if (FM == DELTA && M != POI) n += 1;      // B
-    if (FM == DELTA && M == FOFR) n += 1;     // w
+    if (uses_eta<M, FM>()) n += 1;        // eta
+    if (FM == DELTA && M != POI) n += 1;  // B
     return n;
   }
   static double cells(const LevelView<T>& v) { return (double)v.N * v.N * v.N; }
@@ -470,10 +469,6 @@ isis_status solve_field(const SolveArgs& A) {
   }
   ISIS_CK(cudaMemsetAsync(ws->iflags, 0, 2 * sizeof(int), st));
 
-  if (M == FOFR)  // cached e^u of the finest level
-    ISIS_LAUNCH(KK_SETUP, 2.0 * n * sizeof(T), st,
-                (exp_k<T><<<nblk(n, 256), 256, 0, st>>>(xw, (T*)ws->aux[0], n)));
-
   Cycler<M, FIELD, T> cy;
   SolveArgs A2 = A;
   A2.coef = c;
@@ -584,7 +579,6 @@ isis_status solve_refine(const SolveArgs& A) {
     A1.coef.fKx = c.K2 * std::exp(-u0 * c.inv_np1);
     A1.coef.fK3x = c.K3 - A1.coef.fKx;
     ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (to_rb_affine<<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg, 1.0, -u0)));
-    ISIS_LAUNCH(KK_SETUP, 8.0 * n, st, (exp_k<float><<<nblk(n, 256), 256, 0, st>>>(B0, (float*)ws->aux[0], n)));
   } else {
     ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (to_rb<double><<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg)));
   }
@@ -701,15 +695,7 @@ isis_status solve_refine(const SolveArgs& A) {
                   (restrict_mean<float, float><<<nblk(ncl, 256), 256, 0, st>>>((const float*)ws->B[l - 1],
                                                                               (float*)ws->B[l], lgc)));
     }
-    if (M == FOFR) {
-      for (int l = 0; l < ws->nlev; ++l) {
-        size_t nl = (size_t)(A.N >> l) * (A.N >> l) * (A.N >> l);
-        ISIS_LAUNCH(KK_SETUP, 8.0 * nl, st,
-                    (exp_k<float><<<nblk(nl, 256), 256, 0, st>>>((const float*)ws->B[l], (float*)ws->w[l], nl)));
-      }
-    }
     ISIS_CK(cudaMemsetAsync(cy.L[0].x, 0, n * sizeof(float), st));
-    if (M == FOFR) ISIS_CK(cudaMemsetAsync(ws->aux[0], 0, n * sizeof(float), st));  // e^B expm1(0) = 0
     // inner_cycles FP32 cycles; after the first outer iteration, only as many
     // as the measured contraction per cycle says reach half the target
     int k = A.inner;
