@@ -274,10 +274,9 @@ def main():
         step(x, y, z)
     barrier()
 
-    # timed region: device-resident inputs
+    # timed region: device-resident inputs, no per-launch events (they add about 6% to a step)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     isis.prof_reset()
-    isis.prof_enable(True)
     with ClockSampler(local) as clk:
         barrier()
         t0 = torch.cuda.Event(enable_timing=True)
@@ -287,8 +286,14 @@ def main():
             step(x, y, z, evs[s])
         t1.record(stream)
         barrier()
-    isis.prof_enable(False)
     launches = isis.launch_count()
+    # per-kernel durations: the same steps again, every launch bracketed by CUDA events on its stream
+    isis.prof_reset()
+    isis.prof_enable(True)
+    for s in range(args.steps):
+        step(x, y, z)
+    barrier()
+    isis.prof_enable(False)
     prof = isis.prof_read()
     total_ms = t0.elapsed_time(t1)
     ms = total_ms / args.steps
@@ -339,7 +344,9 @@ def main():
     roofline = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None, "launches": nl,
                 "avg_launch_us": kms * 1e3 / nl, "bytes_per_launch": kbytes / nl,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s",
+                "measured": f"CUDA events around every launch (on its stream) in {args.steps} steps run right after "
+                            f"the timed region; algorithmic bytes from the library's per-launch accounting"}
     kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
                    "GBps": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None} for k, v in prof.items()}
 
