@@ -57,9 +57,16 @@ template <> __device__ __forceinline__ double dexp<double>(double v) { return ex
 template <> __device__ __forceinline__ float dexp<float>(float v) { return __expf(v); }
 template <class T> __device__ __forceinline__ T dexpm1(T v);
 template <> __device__ __forceinline__ double dexpm1<double>(double v) { return expm1(v); }
-// FP32 e^v - 1: Taylor series to degree 9 for |v| <= 1/2 (truncation below
-// 3e-10 relative), else expf(v) - 1 (no cancellation beyond a factor 3 there).
+// FP32 e^v - 1: Taylor series to degree 4 for |v| <= 2^-7 (truncation v^4/120 below
+// 3e-11 relative: the corrections of the refinement loop live there), to degree 9 for
+// |v| <= 1/2 (below 3e-10 relative), else expf(v) - 1 (no cancellation beyond a factor 3).
 template <> __device__ __forceinline__ float dexpm1<float>(float v) {
+  if (fabsf(v) <= 0.0078125f) {
+    float p = fmaf(v, 1.0f / 24.0f, 1.0f / 6.0f);
+    p = fmaf(p, v, 0.5f);
+    p = fmaf(p, v, 1.0f);
+    return p * v;
+  }
   if (fabsf(v) <= 0.5f) {
     float p = fmaf(v, 1.0f / 362880.0f, 1.0f / 40320.0f);
     p = fmaf(p, v, 1.0f / 5040.0f);
@@ -81,15 +88,18 @@ template <> __device__ __forceinline__ float dexpm1<float>(float v) {
 template <class T>
 __device__ __forceinline__ void fofr_field_eval(const Coef& c, T ih2, T x, T ex, const T* xn, const T* exn, T eta,
                                                 T sig, T& F, T& dF) {
-  const T bs = T(c.fscale), b = bs * ex;
+  // sums with e^x and e^x_nb, scaled by fscale once
   T flux = 0, dsum = 0;
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     T du = xn[d] - x;
-    T bf = T(0.5) * (b + bs * exn[d]);
-    flux += bf * du;
-    dsum += T(0.5) * b * du - bf;
+    T ef = T(0.5) * (ex + exn[d]);
+    flux += ef * du;
+    dsum += T(0.5) * ex * du - ef;
   }
+  const T bs = T(c.fscale);
+  flux *= bs;
+  dsum *= bs;
   T Kx = T(c.fKx), inp1 = T(c.inv_np1);
   T em = dexpm1<T>(-x * inp1);
   T S = T(c.K1) * (eta - T(1)) - Kx * em + T(c.fK3x);
@@ -113,9 +123,9 @@ __device__ __forceinline__ void fofr_delta_eval(const Coef& c, T ih2, T e, T B, 
     dsum += T(0.5) * bt * (dB + de) - bf;
   }
   T K2 = T(c.K2), inp1 = T(c.inv_np1);
-  T exB = dexp<T>(-B * inp1);
-  F = flux * ih2 + K2 * exB * dexpm1<T>(-e * inp1) - sig;
-  dF = dsum * ih2 - K2 * inp1 * exB * dexp<T>(-e * inp1);
+  T exB = dexp<T>(-B * inp1), em = dexpm1<T>(-e * inp1);
+  F = flux * ih2 + K2 * exB * em - sig;
+  dF = dsum * ih2 - K2 * inp1 * exB * (em + T(1));
 }
 
 // F = L(x) - Sigma and dF = dL/dx at one cell.
