@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--sample-N", type=int, default=128, help="grid of the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-ref", action="store_true", help="skip the FP64-solver comparison")
     ap.add_argument("--guess", default="net", choices=["net", "background"],
                     help="symmetron initial guess: the trained U-Net, or the background field")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1307_6748_gb300", "weights", "unet_symmetron.npz"))
@@ -350,6 +351,35 @@ def main():
     kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
                    "GBps": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None} for k, v in prof.items()}
 
+    # the mixed-precision solves against the plain FP64 solver on the same GPU and density
+    # (outside the timed region; each solve once after one of its own warm-ups)
+    vs_fp64 = None
+    if not args.no_fp64_ref:
+        vs_fp64 = {}
+        for name, prec_inner in (("poisson", args.inner_poisson), ("symmetron", args.inner_sym),
+                                 ("fofr", args.inner_fofr)):
+            row = {}
+            for label, prec in (("fp64", isis.ISIS_F64), ("refine64", isis.ISIS_F32_REFINE64)):
+                o = isis.Opts(prec=prec, inner_cycles=prec_inner, init=isis.ISIS_INIT_BACKGROUND,
+                              n_coarsest=args.ncoarse, max_cycles=40)
+                out = {"poisson": Phi, "symmetron": chi, "fofr": u}[name]
+                for rep in range(2):
+                    barrier()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    if name == "poisson":
+                        info = isis.isis_poisson_solve(grid, a, eta, out, tol=args.tol, opts=o)
+                    else:
+                        m = isis.ISIS_SYMMETRON if name == "symmetron" else isis.ISIS_FOFR_HS
+                        info = isis.isis_scalar_solve(m, psym if name == "symmetron" else pfr, grid, a, eta, out,
+                                                      tol=args.tol, opts=o)
+                    e1.record(stream)
+                    barrier()
+                row[label + "_ms"] = e0.elapsed_time(e1)
+                row[label + "_cycles"] = info.cycles
+            row["speedup"] = row["fp64_ms"] / row["refine64_ms"]
+            vs_fp64[name] = row
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args)
@@ -363,6 +393,8 @@ def main():
                            for k, v in infos.items()},
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary()}
+        if vs_fp64 is not None:
+            line["vs_fp64_solver"] = vs_fp64
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(kCoarseMax) coarse_newton(LevelView<T> L, Coef
   }
   if (r < n) {
     L.x[gr] = (T)xs[r];
+    if constexpr (M == FOFR && kExpCache<T>) L.aux[gr] = aux_of<M, FM, T>((T)xs[r], T(0));
   }
   if (r == 0) {
     if (bad) atomicOr(flags, bad);

@@ -149,6 +149,26 @@ __device__ __forceinline__ void fill_exps(Cell<T>& q) {
   }
 }
 
+// FP64 grids keep e^x of every cell in L.aux (the FP64 path runs the field form only):
+// an FP64 exponential per neighbour would cost more than the extra reads.
+template <class T>
+constexpr bool kExpCache = sizeof(T) == 8;
+
+template <Model M, Form FM, class T, class IDX>
+__device__ __forceinline__ void load_or_fill_exps(const LevelView<T>& L, IDX c, const IDX* nb, Cell<T>& q) {
+  if constexpr (M == FOFR && kExpCache<T>) {
+    q.w = T(0);
+    q.a = L.aux[c];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      q.wn[d] = T(0);
+      q.an[d] = L.aux[nb[d]];
+    }
+  } else {
+    fill_exps<M, FM, T>(q);
+  }
+}
+
 // Gather the cell stored at t and its neighbours.
 template <Model M, Form FM, class T>
 __device__ __forceinline__ Cell<T> gather_at(const LevelView<T>& L, size_t c) {
@@ -165,7 +185,7 @@ __device__ __forceinline__ Cell<T> gather_at(const LevelView<T>& L, size_t c) {
 #pragma unroll
     for (int d = 0; d < 6; ++d) q.Bn[d] = L.B[nb[d]];
   }
-  fill_exps<M, FM, T>(q);
+  load_or_fill_exps<M, FM, T, size_t>(L, c, nb, q);
   return q;
 }
 
@@ -185,7 +205,7 @@ __device__ __forceinline__ Cell<T> gather(const LevelView<T>& L, int i, int j, i
 #pragma unroll
     for (int d = 0; d < 6; ++d) q.Bn[d] = L.B[nb[d]];
   }
-  fill_exps<M, FM, T>(q);
+  load_or_fill_exps<M, FM, T, size_t>(L, c, nb, q);
   return q;
 }
 
@@ -211,6 +231,7 @@ __global__ void smooth_color(LevelView<T> L, Coef c, int color) {
   else xn = q.x - F / dF;
   const size_t o = lidx<T>(L.lg, i, j, k);
   L.x[o] = xn;
+  if constexpr (M == FOFR && kExpCache<T>) L.aux[o] = aux_of<M, FM, T>(xn, q.w);
 }
 
 // One colour of a Newton-Gauss-Seidel sweep on a red/black split FP32 grid.
@@ -422,7 +443,10 @@ __global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __rest
         X[a][b][d] = F.x[p[d]];
         // the f(R) exponentials of each loaded cell, once for the 8 stencils (fill_exps)
         if constexpr (kAllB) { Bx[a][b][d] = F.B[p[d]]; Wx[a][b][d] = dexp<T>(Bx[a][b][d]); }
-        if constexpr (kAux) Ax[a][b][d] = aux_of<M, FM, T>(X[a][b][d], kAllB ? Wx[a][b][d] : T(0));
+        if constexpr (kAux) {
+          if constexpr (kExpCache<T>) Ax[a][b][d] = F.aux[p[d]];
+          else Ax[a][b][d] = aux_of<M, FM, T>(X[a][b][d], kAllB ? Wx[a][b][d] : T(0));
+        }
       }
     }
   T xs = 0, rs = 0;
@@ -465,6 +489,7 @@ __global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __rest
   xc[to] = xr;
   x0c[to] = xr;
   sigc[to] = rs * T(0.125);
+  if constexpr (M == FOFR && kExpCache<T>) C.aux[to] = aux_of<M, FM, T>(xr, T(0));
 }
 
 // Sigma_H += L_H(x_H) (the FAS coarse source, Sect. 3.2).
@@ -529,6 +554,7 @@ __global__ void prolong_correct(LevelView<T> Fv, const T* __restrict__ xc, const
         const size_t o = lidx<T>(lgf, 2 * I + ca, 2 * J + cb, 2 * K + cd);
         const T xn = xf[o] + v;
         xf[o] = xn;
+        if constexpr (M == FOFR && kExpCache<T>) Fv.aux[o] = aux_of<M, FM, T>(xn, T(0));
       }
 }
 

@@ -469,6 +469,10 @@ isis_status solve_field(const SolveArgs& A) {
   }
   ISIS_CK(cudaMemsetAsync(ws->iflags, 0, 2 * sizeof(int), st));
 
+  if (M == FOFR && kExpCache<T>)  // cached e^u of the finest level (FP64 grids)
+    ISIS_LAUNCH(KK_SETUP, 2.0 * n * sizeof(T), st,
+                (exp_k<T><<<nblk(n, 256), 256, 0, st>>>(xw, (T*)ws->aux[0], n)));
+
   Cycler<M, FIELD, T> cy;
   SolveArgs A2 = A;
   A2.coef = c;
