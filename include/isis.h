@@ -194,6 +194,20 @@ isis_status isis_fifth_force(isis_model model, const isis_params* params, const 
                              const void* Phi, const void* phi, int fields_f64, const float* x, const float* y,
                              const float* z, int64_t npart, float* gx, float* gy, float* gz, void* stream);
 
+/* One leapfrog step of the particles in super-comoving time tau (Eqs. (leap_frog_1)
+ * to (leap_frog_3)), fused kick and drift, positions and velocities in cell units:
+ *     v += kick * g / h,   x += drift * v,   x wrapped into [0, N),   h = box / N.
+ *   g       the acceleration of isis_fifth_force at the current positions (per Mpc/h).
+ *   kick    (dtau_prev + dtau) / 2: the second half-kick of the previous step merged with
+ *           the first of this one, as the paper reuses the second velocity evaluation
+ *           (dtau_prev = 0 on the first step; a last half-kick dtau/2 synchronises).
+ *   drift   dtau.  tau is measured in Mpc/h (c = 1): dtau = da / (a^3 H0 E(a)).
+ *   x, y, z, vx, vy, vz  device float[npart], updated in place; gx, gy, gz read.
+ *   EINVAL: bad grid, NULL pointers, npart < 1 or non-finite kick or drift. */
+isis_status isis_kick_drift(const isis_grid* grid, float* x, float* y, float* z, float* vx, float* vy, float* vz,
+                            const float* gx, const float* gy, const float* gz, int64_t npart, double kick,
+                            double drift, void* stream);
+
 /* ---- Instrumentation (not part of the paper's method) -------------------
  * Every kernel launch of the library is counted.  When profiling is on, each
  * launch is also bracketed by CUDA events on its stream and its algorithmic

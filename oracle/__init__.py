@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -218,3 +219,75 @@ def fifth_force(p: Problem, Phi, phi, x, y, z):
     assert lib().orc_fifth_force(ctypes.byref(pc), _d(Phi), _d(phi), x.size, _f(x), _f(y), _f(z),
                                  _d(g[0]), _d(g[1]), _d(g[2])) == OK
     return g
+
+
+# ---------------------------------------------------------------------------
+# Particle time stepping: leapfrog in super-comoving time tau
+# (Sect. 4.1, Eqs. (leap_frog_1)-(leap_frog_3); the same scheme for f(R), Sect. 4.2).
+# Positions and velocities in cell units, tau in Mpc/h (c = 1):
+#   d^2 x / dtau^2 = g = -[grad Phi~ + F5],   dtau = da / (a^3 H0 E(a)).
+# ---------------------------------------------------------------------------
+
+def tau_interval(a0: float, a1: float, Omega_m: float = 0.267, Omega_L: float = 0.733, H0: float = H0_MPC,
+                 n: int = 256) -> float:
+    """Super-comoving time from a0 to a1: the integral of da / (a^3 H0 E(a)), E(a) = sqrt(Om a^-3 + OL),
+    by the composite Simpson rule with n (even) intervals."""
+    a = np.linspace(a0, a1, n + 1)
+    f = 1.0 / (a ** 3 * H0 * np.sqrt(Omega_m / a ** 3 + Omega_L))
+    w = np.ones(n + 1)
+    w[1:-1:2] = 4.0
+    w[2:-1:2] = 2.0
+    return float((a1 - a0) / (3.0 * n) * np.dot(w, f))
+
+
+def leapfrog_kick_drift(pos, vel, g, kick: float, drift: float, N: int, h: float):
+    """One merged kick and drift (FP64, in place): v += kick g / h; x += drift v; x wrapped into [0, N).
+    kick = (dtau_{n-1} + dtau_n) / 2 joins the second half-kick of the previous step to the first of this one."""
+    for d in range(3):
+        vel[d] += kick * g[d] / h
+        pos[d] += drift * vel[d]
+        pos[d] %= N
+
+
+def background_field(model: int, a: float, Omega_m: float = 0.267, Omega_L: float = 0.733, a_ssb: float = 0.5,
+                     n: int = 1, fR0_abs: float = 1e-5) -> float:
+    """Uniform-density solution: chi = sqrt(1 - (a_SSB/a)^3) above symmetry breaking, else 0 (Sect. 4.1);
+    u = ln(a^2 |f_R|), |f_R| = |f_R0| [(1 + 4 r) / (a^-3 + 4 r)]^(n+1), r = OL/Om (Sect. 4.2)."""
+    if model == SYMMETRON:
+        v = 1.0 - (a_ssb / a) ** 3
+        return math.sqrt(v) if v > 0 else 0.0
+    if model == FOFR:
+        r = Omega_L / Omega_m
+        return math.log(a * a * fR0_abs * ((1 + 4 * r) / (a ** -3 + 4 * r)) ** (n + 1))
+    return 0.0
+
+
+def pm_run(model, N: int, box: float, pos, vel, a_steps, tol: float = 1e-10, ncoarse: int = 4, **params):
+    """Leapfrog through a_steps[0] -> ... -> a_steps[-1].  At each a_n: CIC density of the positions, the
+    Poisson field, the scalar field (model SYMMETRON or FOFR; None: gravity only), the acceleration of every
+    particle, then the merged kick and the drift by dtau_n = tau(a_n -> a_{n+1}).  pos, vel: three FP64 arrays
+    each (cell units), updated in place; returns them after the last drift (velocities at the half step)."""
+    h = box / N
+    Phi = np.zeros((N,) * 3)
+    phi = None
+    dtau_prev = 0.0
+    cos = {k: params[k] for k in ("Omega_m", "Omega_L", "H0") if k in params}
+    for a, a_next in zip(a_steps[:-1], a_steps[1:]):
+        x, y, z = (np.asarray(p, dtype=np.float32) for p in pos)
+        eta = cic_deposit(N, x, y, z)
+        pp = Problem(POISSON, N, box, a=a, **params)
+        Phi = solve(pp, eta, Phi, tol=tol, ncoarse=ncoarse).phi
+        if model is not None:
+            ps = Problem(model, N, box, a=a, **params)
+            if phi is None:
+                bg = background_field(model, a, **{k: params[k] for k in ("Omega_m", "Omega_L", "a_ssb", "n",
+                                                                          "fR0_abs") if k in params})
+                phi = np.full((N,) * 3, bg)
+            phi = solve(ps, eta, phi, tol=tol, ncoarse=ncoarse).phi
+            g = fifth_force(ps, Phi, phi, x, y, z)
+        else:
+            g = fifth_force(pp, Phi, None, x, y, z)
+        dtau = tau_interval(a, a_next, **cos)
+        leapfrog_kick_drift(pos, vel, g, 0.5 * (dtau_prev + dtau), dtau, N, h)
+        dtau_prev = dtau
+    return pos, vel

@@ -227,6 +227,30 @@ static bool grid_valid(const isis_grid* g) {
 
 using namespace isis;
 
+// Leapfrog in super-comoving time tau (Eqs. (leap_frog_1)-(leap_frog_3)): one fused
+// kick and drift per particle, positions and velocities in cell units:
+//   v += kick g / h;  x += drift v;  x wrapped into [0, N).
+// kick = (dtau_{n-1} + dtau_n)/2 merges the second half-kick of step n-1 with the
+// first of step n (the paper's reuse of the second velocity evaluation), drift = dtau_n.
+__global__ void kick_drift(float* __restrict__ x, float* __restrict__ y, float* __restrict__ z,
+                           float* __restrict__ vx, float* __restrict__ vy, float* __restrict__ vz,
+                           const float* __restrict__ gx, const float* __restrict__ gy, const float* __restrict__ gz,
+                           long long np, float kick_h, float drift, float N) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  auto wrap = [N](float v) {
+    v -= N * floorf(v / N);
+    return v >= N ? v - N : v;  // floorf rounding can leave v == N
+  };
+  const float ux = fmaf(kick_h, gx[p], vx[p]), uy = fmaf(kick_h, gy[p], vy[p]), uz = fmaf(kick_h, gz[p], vz[p]);
+  vx[p] = ux;
+  vy[p] = uy;
+  vz[p] = uz;
+  x[p] = wrap(fmaf(drift, ux, x[p]));
+  y[p] = wrap(fmaf(drift, uy, y[p]));
+  z[p] = wrap(fmaf(drift, uz, z[p]));
+}
+
 extern "C" {
 
 isis_status isis_cic_deposit(const isis_grid* grid, const float* x, const float* y, const float* z, int64_t npart,
@@ -313,6 +337,22 @@ isis_status isis_fifth_force(isis_model model, const isis_params* p, const isis_
   ISIS_LAUNCH(KK_FORCE, 24.0 * npart + 12.0 * n, st,
               (force_gather<<<nblk((size_t)npart, 256), 256, 0, st>>>(fx, fy, fz, x, y, z, (long long)npart, lg, gx,
                                                                       gy, gz)));
+  return ISIS_OK;
+}
+
+
+isis_status isis_kick_drift(const isis_grid* grid, float* x, float* y, float* z, float* vx, float* vy, float* vz,
+                            const float* gx, const float* gy, const float* gz, int64_t npart, double kick,
+                            double drift, void* stream) {
+  if (!grid_valid(grid) || !x || !y || !z || !vx || !vy || !vz || !gx || !gy || !gz || npart < 1 ||
+      !std::isfinite(kick) || !std::isfinite(drift))
+    return ISIS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double h = grid->box / grid->N;
+  ISIS_LAUNCH(KK_FORCE, 36.0 * npart, st,
+              (kick_drift<<<nblk((size_t)npart, 256), 256, 0, st>>>(x, y, z, vx, vy, vz, gx, gy, gz, (long long)npart,
+                                                                     (float)(kick / h), (float)drift,
+                                                                     (float)grid->N)));
   return ISIS_OK;
 }
 

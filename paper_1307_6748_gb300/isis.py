@@ -26,7 +26,7 @@ H0_MPC = 1.0 / 2997.92458  # (Mpc/h)^-1 with c = 1
 # Every function the header declares (checked by the tests).
 EXPORTS = ("isis_cic_deposit", "isis_cic_deposit_noalloc", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force",
            "isis_strerror", "isis_release_workspace", "isis_prof_enable", "isis_prof_reset", "isis_prof_read",
-           "isis_launch_count", "isis_selftest_exp_ff")
+           "isis_launch_count", "isis_selftest_exp_ff", "isis_kick_drift")
 ISIS_INIT_INPUT, ISIS_INIT_BACKGROUND, ISIS_INIT_LOCAL = 0, 1, 2
 
 
@@ -85,6 +85,9 @@ def load(path: str = LIB_PATH):
                                       ctypes.c_double, P(isis_mg_opts), P(isis_solve_info), vp]
     lib.isis_fifth_force.argtypes = [ctypes.c_int, P(isis_params), P(isis_grid), ctypes.c_double, vp, vp,
                                      ctypes.c_int, f_p, f_p, f_p, ctypes.c_int64, f_p, f_p, f_p, vp]
+    lib.isis_kick_drift.argtypes = [P(isis_grid), f_p, f_p, f_p, f_p, f_p, f_p, f_p, f_p, f_p, ctypes.c_int64,
+                                    ctypes.c_double, ctypes.c_double, vp]
+    lib.isis_kick_drift.restype = ctypes.c_int
     lib.isis_strerror.argtypes = [ctypes.c_int]
     lib.isis_strerror.restype = ctypes.c_char_p
     lib.isis_release_workspace.argtypes = []
@@ -287,6 +290,17 @@ def isis_fifth_force(model: int, params: Params, grid: Grid, a: float, Phi: torc
                               _ptr(out[2], torch.float32), _stream(stream))
     _check(st, "isis_fifth_force")
     return out
+
+
+def isis_kick_drift(grid: Grid, x, y, z, vx, vy, vz, g, kick: float, drift: float, stream=None) -> None:
+    """Leapfrog kick and drift in place (cell units; g = (gx, gy, gz) per Mpc/h)."""
+    lib = load()
+    gr = grid.c()
+    f = torch.float32
+    st = lib.isis_kick_drift(ctypes.byref(gr), _ptr(x, f), _ptr(y, f), _ptr(z, f), _ptr(vx, f), _ptr(vy, f),
+                             _ptr(vz, f), _ptr(g[0], f), _ptr(g[1], f), _ptr(g[2], f), x.numel(), float(kick),
+                             float(drift), _stream(stream))
+    _check(st, "isis_kick_drift")
 
 
 # ---------------------------------------------------------------------------

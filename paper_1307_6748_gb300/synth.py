@@ -125,6 +125,25 @@ def zeldovich(N: int, L: float, seed: int = 3, disp_rms: float = 0.5, device="cp
     return pos
 
 
+def zeldovich_ic(N: int, L: float, a: float, seed: int = 3, disp_rms: float = 0.5, Omega_m: float = 0.267,
+                 Omega_L: float = 0.733, H0: float = 1.0 / 2997.92458, device="cpu"):
+    """Particles and velocities of the growing mode at expansion factor a (cell units).
+
+    Positions as zeldovich(); velocities v = dx/dtau = a^2 H0 E(a) Psi in cells per unit of
+    super-comoving time (growth D proportional to a), with E(a) = sqrt(Om a^-3 + OL) and Psi
+    the displacement of each particle from its lattice site.
+    Returns (x, y, z, vx, vy, vz), float32 in [0, N) and cells per unit tau."""
+    x, y, z = zeldovich(N, L, seed, disp_rms, device)
+    q = (torch.arange(N, device=device, dtype=torch.float64) + 0.5)
+    grids = [g.reshape(-1) for g in torch.meshgrid(q, q, q, indexing="ij")]
+    fac = a * a * H0 * math.sqrt(Omega_m / a ** 3 + Omega_L)
+    vel = []
+    for p, qq in zip((x, y, z), grids):
+        psi = torch.remainder(p.double() - qq + N / 2, float(N)) - N / 2  # displacement, periodic
+        vel.append((fac * psi).to(torch.float32).contiguous())
+    return (x, y, z, *vel)
+
+
 def sphere_eta(N: int, B: float, R: float, delta: float, sub: int = 4) -> torch.Tensor:
     """Cell-averaged uniform sphere of radius R and contrast delta at the box centre (Sect. 5.1)."""
     h = B / N

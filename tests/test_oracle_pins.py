@@ -383,3 +383,95 @@ def test_force_at_cell_centre():
         exp_d = -(a * a * gPhi[d][c] + 0.5 * math.exp(u[c]) * gu[d][c])
         assert abs(g[d][0] - exp_d) <= 1e-12 * (abs(exp_d) + 1e-20)
     del h
+
+
+# ---- particle time stepping (Sect. 4.1, Eqs. (leap_frog_1)-(leap_frog_3)) ----
+
+def test_tau_interval_matches_einstein_de_sitter():
+    """Omega_m = 1, Omega_L = 0: tau(a0 -> a1) = 2 (a0^-1/2 - a1^-1/2) / H0 in closed form."""
+    H0 = oracle.H0_MPC
+    for a0, a1 in ((0.1, 0.2), (0.5, 1.0), (0.9, 0.95)):
+        got = oracle.tau_interval(a0, a1, 1.0, 0.0, H0)
+        assert abs(got / (2.0 * (a0 ** -0.5 - a1 ** -0.5) / H0) - 1.0) < 1e-10
+
+
+def test_leapfrog_constant_force_is_exact():
+    """With a constant acceleration the merged-kick leapfrog lands exactly on x0 + v0 T + g T^2 / 2 at the
+    synchronised point (after a final half-kick) for any step sizes."""
+    rng = np.random.Generator(np.random.PCG64(3))
+    N, h = 1e9, 0.5  # no wrap
+    x0 = [rng.uniform(0, 10, 5) for _ in range(3)]
+    v0 = [rng.normal(size=5) for _ in range(3)]
+    g = [np.full(5, c) for c in (0.3, -0.7, 1.1)]
+    pos, vel = [p.copy() for p in x0], [v.copy() for v in v0]
+    steps = [0.1, 0.25, 0.05, 0.3]
+    prev = 0.0
+    for dt in steps:
+        oracle.leapfrog_kick_drift(pos, vel, g, 0.5 * (prev + dt), dt, N, h)
+        prev = dt
+    for d in range(3):
+        vel[d] += 0.5 * prev * g[d] / h  # final half-kick
+    T = sum(steps)
+    for d in range(3):
+        np.testing.assert_allclose(pos[d], x0[d] + v0[d] * T + 0.5 * g[d] / h * T * T, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(vel[d], v0[d] + g[d] / h * T, rtol=0, atol=1e-12)
+
+
+def test_leapfrog_time_reversible():
+    """A position-dependent force (harmonic): steps forward, velocities reversed, the same steps back
+    return every particle to its start (the leapfrog is time-symmetric)."""
+    rng = np.random.Generator(np.random.PCG64(4))
+    N, h, w2, c = 1e9, 1.0, 0.8, 5.0
+    pos = [rng.uniform(0, 10, 7) for _ in range(3)]
+    vel = [rng.normal(size=7) for _ in range(3)]
+    x0 = [p.copy() for p in pos]
+    dt, k = 0.07, 20
+    force = lambda: [-w2 * (p - c) for p in pos]
+    # forward: half kick, (drift, full kick)^(k-1), drift, half kick
+    def run():
+        oracle.leapfrog_kick_drift(pos, vel, force(), 0.5 * dt, dt, N, h)
+        for _ in range(k - 1):
+            oracle.leapfrog_kick_drift(pos, vel, force(), dt, dt, N, h)
+        g = force()
+        for d in range(3):
+            vel[d] += 0.5 * dt * g[d] / h
+    run()
+    for d in range(3):
+        vel[d] *= -1.0
+    run()
+    for d in range(3):
+        np.testing.assert_allclose(pos[d], x0[d], rtol=0, atol=1e-11)
+
+
+def test_pm_uniform_translation_is_free_streaming():
+    """A lattice moving rigidly keeps a uniform CIC density, so every field and force vanishes and the
+    positions advance by v * (sum of dtau) exactly (mod N).  (The CIC sees FP32 positions: the velocities
+    keep their values to the force of that rounding, 1e-10 here.)"""
+    N, box = 8, 16.0
+    q = np.arange(N) + 0.5
+    X, Y, Z = np.meshgrid(q, q, q, indexing="ij")
+    pos = [X.reshape(-1).astype(np.float64), Y.reshape(-1).astype(np.float64), Z.reshape(-1).astype(np.float64)]
+    v = (2e-4, -1e-4, 3e-4)
+    vel = [np.full(N ** 3, c) for c in v]
+    a_steps = [0.8, 0.85, 0.9]
+    pos, vel = oracle.pm_run(oracle.SYMMETRON, N, box, pos, vel, a_steps, tol=1e-10)
+    T = oracle.tau_interval(0.8, 0.85) + oracle.tau_interval(0.85, 0.9)
+    for d, (grid, c) in enumerate(zip((X, Y, Z), v)):
+        np.testing.assert_allclose(pos[d], (grid.reshape(-1) + c * T) % N, rtol=0, atol=1e-9)
+        np.testing.assert_allclose(vel[d], c, rtol=0, atol=1e-10)
+
+
+def test_pm_gravity_conserves_momentum():
+    """Gravity alone: CIC deposit, the symmetric central difference and CIC interpolation with the same
+    kernel exert no net force, so the total momentum stays constant."""
+    import torch
+    N, box = 16, 32.0
+    x, y, z, vx, vy, vz = synth.zeldovich_ic(N, box, 0.8, seed=6)
+    pos = [t.double().numpy().copy() for t in (x, y, z)]
+    vel = [t.double().numpy().copy() for t in (vx, vy, vz)]
+    p0 = [v.sum() for v in vel]
+    scale = sum(np.abs(v).sum() for v in vel)
+    pos, vel = oracle.pm_run(None, N, box, pos, vel, [0.8, 0.84, 0.88, 0.92], tol=1e-11)
+    for d in range(3):
+        assert abs(vel[d].sum() - p0[d]) <= 1e-9 * scale
+    del torch
