@@ -13,8 +13,6 @@ per-particle and per-cell work runs in the library's kernels.
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 import torch
 

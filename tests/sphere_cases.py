@@ -1,0 +1,138 @@
+"""The static sphere test of Sect. 5.1 ("Potential solver"): cases, the 1D reference profiles and the
+radial-band error measure shared by the CPU (oracle) and GPU sphere tests.
+
+A sphere of radius R and contrast delta = 5000 at the centre of a periodic box of side B; the 3D density
+is the cell average of the sphere (synth.sphere_eta), the 1D reference the spherically symmetric solve of
+the same equation on a fine radial grid (oracle.sphere1d), isolated (far-field value at a large radius).
+The bands avoid the shell, where the grid does not resolve the screened layer, and stop where the
+periodic images' field is below 1e-6 of the sphere's own:
+  core [0, R/2), near [5R/4, 3R/2), mid [3R/2, 2R), far [2R, r_far).
+Error measure: symmetron |chi_3D - chi_1D|; f(R) |f_R,3D - f_R,1D| / |f_R(far)| (f_R = -e^u / a^2).
+"""
+from __future__ import annotations
+
+import functools
+import math
+import os
+
+import numpy as np
+
+import oracle
+from oracle import sphere1d as S
+from paper_1307_6748_gb300 import synth
+
+OM, OL = 0.267, 0.733
+_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "static_sphere.txt")
+
+
+def _rows():
+    with open(_GOLDEN) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def cases():
+    """name -> dict(model, a, delta, R, B, params) from the golden table (z = 0 and 1 for the symmetron)."""
+    out = {}
+    for row in _rows():
+        delta, R, B = float(row[1]), float(row[2]), float(row[3])
+        kv = dict(t.split("=") for t in row[4:] if "=" in t)
+        zs = [float(z) for z in row[-1].split("=")[1].split(",")]
+        for z in zs:
+            a = 1.0 / (1.0 + z)
+            if row[0] == "symmetron":
+                par = dict(lambda0=float(kv["lambda0"]), a_ssb=float(kv["a_SSB"]))
+                out[f"symmetron_z{z:g}"] = dict(model=oracle.SYMMETRON, a=a, delta=delta, R=R, B=B, params=par,
+                                                r_far=4.0 * R)
+            else:
+                par = dict(n=int(kv["n"]), fR0_abs=float(kv["|f_R0|"]))
+                out[f"fofr_z{z:g}"] = dict(model=oracle.FOFR, a=a, delta=delta, R=R, B=B, params=par,
+                                           r_far=6.0 * R)
+    return out
+
+
+# Max error per band on the 128^3 domain grid of Sect. 5.1 (1.5x the FP64 oracle's measured
+# discretisation error there), and the largest allowed ratio of the band RMS error when h halves
+# (symmetron: measured 0.28-0.31; f(R), first order through the face mean of e^u across the shell: 0.46-0.50).
+TOL_128 = {
+    "symmetron_z0": dict(core=1e-5, near=2.2e-2, mid=1.2e-2, far=2.5e-3),
+    "symmetron_z1": dict(core=1e-5, near=2.3e-2, mid=1.6e-2, far=7e-3),
+    "fofr_z0": dict(core=1e-8, near=0.22, mid=0.12, far=0.03),
+}
+RATIO = {"symmetron_z0": 0.6, "symmetron_z1": 0.6, "fofr_z0": 0.7}
+
+
+def far_value(c):
+    """Uniform-density solution at the exterior density (the far field of the isolated sphere)."""
+    eta_in, eta_out = S.sphere_densities(c["delta"], c["R"], c["B"])
+    a, p = c["a"], c["params"]
+    if c["model"] == oracle.SYMMETRON:
+        return math.sqrt(1.0 - (p["a_ssb"] / a) ** 3 * eta_out)
+    K1, K2, K3 = S.fofr_constants(a, OM, OL, S.H0_MPC, p["n"], p["fR0_abs"])
+    return (p["n"] + 1) * math.log(K2 / (K1 * (eta_out - 1.0) + K3))
+
+
+@functools.lru_cache(maxsize=None)
+def reference_1d(name):
+    """(r, profile) of the 1D solve, far-field value held at 20 (symmetron) or 30 (f(R)) radii."""
+    c = cases()[name]
+    eta_in, eta_out = S.sphere_densities(c["delta"], c["R"], c["B"])
+    rad = S.Radial(20000, (20.0 if c["model"] == oracle.SYMMETRON else 30.0) * c["R"])
+    eta = S.sphere_profile(rad.edges, c["R"], eta_in, eta_out)
+    a, p = c["a"], c["params"]
+    if c["model"] == oracle.SYMMETRON:
+        A, s = a * a / (2.0 * p["lambda0"] ** 2), (p["a_ssb"] / a) ** 3
+        return rad.r, S.symmetron(eta, rad, A, s, far_value(c))
+    K1, K2, K3 = S.fofr_constants(a, OM, OL, S.H0_MPC, p["n"], p["fR0_abs"])
+    return rad.r, S.fofr(eta, rad, K1, K2, K3, p["n"], far_value(c))
+
+
+def eta_3d(name, N):
+    c = cases()[name]
+    return synth.sphere_eta(N, c["B"], c["R"], c["delta"]).numpy()
+
+
+def guess_3d(name, eta):
+    """Symmetron: the far value everywhere (the z = 1 background is the unbroken chi = 0, from which the
+    iteration does not leave); f(R): the cell-wise uniform-density solution."""
+    c = cases()[name]
+    if c["model"] == oracle.SYMMETRON:
+        return np.full(eta.shape, far_value(c))
+    p, a = c["params"], c["a"]
+    K1, K2, K3 = S.fofr_constants(a, OM, OL, S.H0_MPC, p["n"], p["fR0_abs"])
+    return (p["n"] + 1) * np.log(K2 / (K1 * (eta - 1.0) + K3))
+
+
+def problem(name, N):
+    c = cases()[name]
+    return oracle.Problem(c["model"], N, c["B"], a=c["a"], **c["params"])
+
+
+def band_errors(name, field, N):
+    """band -> (max, rms) of the error of a 3D solution against the 1D profile at each cell's radius."""
+    c = cases()[name]
+    R, B = c["R"], c["B"]
+    h = B / N
+    x = (np.arange(N) + 0.5) * h - B / 2
+    r = np.sqrt(x[:, None, None] ** 2 + x[None, :, None] ** 2 + x[None, None, :] ** 2)
+    r1, p1 = reference_1d(name)
+    ref = np.interp(r, r1, p1)
+    if c["model"] == oracle.SYMMETRON:
+        err = np.abs(field - ref)
+    else:
+        err = np.abs(np.exp(field) - np.exp(ref)) / math.exp(far_value(c))
+    bands = dict(core=(0.0, 0.5 * R), near=(1.25 * R, 1.5 * R), mid=(1.5 * R, 2.0 * R), far=(2.0 * R, c["r_far"]))
+    out = {}
+    for k, (lo, hi) in bands.items():
+        m = (r >= lo) & (r < hi)
+        out[k] = (float(err[m].max()), float(np.sqrt((err[m] ** 2).mean())))
+    return out
+
+
+def check_tol(name, errs):
+    for k, tol in TOL_128[name].items():
+        assert errs[k][0] <= tol, (name, k, errs[k][0], tol)
+
+
+def check_ratio(name, coarse, fine):
+    for k in ("near", "mid", "far"):
+        assert fine[k][1] <= RATIO[name] * coarse[k][1], (name, k, coarse[k][1], fine[k][1])

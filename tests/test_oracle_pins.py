@@ -475,3 +475,59 @@ def test_pm_gravity_conserves_momentum():
     for d in range(3):
         assert abs(vel[d].sum() - p0[d]) <= 1e-9 * scale
     del torch
+
+
+# ---- the 1D radial solver of the static sphere test (Sect. 5.1) ----
+
+def _yukawa_sphere(r, R, m, q):
+    """Solution of (1/r^2)(r^2 e')' - m^2 e = q [r < R] vanishing at infinity (textbook)."""
+    mr, mR = m * r, m * R
+    inside = -(q / m ** 2) * (1.0 - (1.0 + mR) * np.exp(-mR) * np.sinh(mr) / mr)
+    outside = -(q / m ** 2) * (mR * np.cosh(mR) - np.sinh(mR)) * np.exp(-mr) / mr
+    return np.where(r < R, inside, outside)
+
+
+def test_radial_poisson_matches_uniform_sphere_potential():
+    from oracle import sphere1d as S
+    R, Rmax, K = 3.0, 20.0, 2.0
+    eta_in, eta_out = 50.0, 0.9
+    rad = S.Radial(4000, Rmax)
+    eta = S.sphere_profile(rad.edges, R, eta_in, eta_out)
+    c, D = K * (eta_out - 1.0), K * (eta_in - eta_out)
+
+    def exact(r):
+        return c * r * r / 6.0 + D * np.where(r < R, r * r / 6.0 - R * R / 2.0, -R ** 3 / (3.0 * r))
+    phi = S.poisson(eta, rad, K, 1.0, float(exact(np.array(Rmax + rad.dr / 2))))
+    err = np.abs(phi - exact(rad.r)).max()
+    assert err <= 1e-5 * np.abs(exact(rad.r)).max(), err
+
+
+def test_radial_symmetron_linear_limit_is_yukawa():
+    """A weak sphere: chi - chi_out follows the linear (Yukawa) profile with m^2 = 2 A (1 - s eta_out)."""
+    from oracle import sphere1d as S
+    A, s, R, Rmax = 0.5, 0.4, 2.0, 30.0
+    eta_out, d_eta = 1.0, 1e-4
+    chi_out = math.sqrt(1.0 - s * eta_out)
+    rad = S.Radial(6000, Rmax)
+    eta = S.sphere_profile(rad.edges, R, eta_out + d_eta, eta_out)
+    chi = S.symmetron(eta, rad, A, s, chi_out)
+    m = math.sqrt(2.0 * A * (1.0 - s * eta_out))
+    lin = _yukawa_sphere(rad.r, R, m, A * s * d_eta * chi_out)
+    assert np.abs((chi - chi_out) - lin).max() <= 2e-3 * np.abs(lin).max()
+
+
+def test_radial_fofr_linear_limit_is_yukawa():
+    """A weak sphere in f(R): u - u_out follows the Yukawa profile with m^2 = K2 e^{-u/(n+1)} / ((n+1) e^u)
+    and source K1 d_eta / e^u (the equation linearised about the uniform solution)."""
+    from oracle import sphere1d as S
+    n, fr0, a, R, Rmax = 1, 1e-5, 1.0, 2.0, 60.0
+    K1, K2, K3 = S.fofr_constants(a, OM, OL, S.H0_MPC, n, fr0)
+    u_out = (n + 1) * math.log(K2 / K3)  # S(u, eta = 1) = 0
+    d_eta = 1e-4
+    rad = S.Radial(8000, Rmax)
+    eta = S.sphere_profile(rad.edges, R, 1.0 + d_eta, 1.0)
+    u = S.fofr(eta, rad, K1, K2, K3, n, u_out)
+    b = math.exp(u_out)
+    m = math.sqrt(K2 * math.exp(-u_out / (n + 1)) / ((n + 1) * b))
+    lin = _yukawa_sphere(rad.r, R, m, K1 * d_eta / b)
+    assert np.abs((u - u_out) - lin).max() <= 2e-3 * np.abs(lin).max()
