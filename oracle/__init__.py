@@ -73,6 +73,27 @@ class Problem:
                         self.lambda0, self.beta, self.a_ssb, self.n, self.fR0_abs)
 
 
+class _Patch(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("o", ctypes.c_int * 3), ("pn", ctypes.c_int * 3),
+                ("periodic", ctypes.c_int), ("level", ctypes.c_int), ("eta_mean", ctypes.c_double)]
+
+
+@dataclass
+class Patch:
+    """A refinement patch (Sects. 3.3.1, 3.4.1): a box of n parent cells at origin o of a parent grid of dims
+    pn (periodic: the domain grid), refined by two; level >= 1 sets h = box / (N 2^level)."""
+    n: tuple
+    o: tuple
+    pn: tuple
+    periodic: bool
+    level: int = 1
+    eta_mean: float = 1.0
+
+    def c(self) -> _Patch:
+        return _Patch((ctypes.c_int * 3)(*self.n), (ctypes.c_int * 3)(*self.o), (ctypes.c_int * 3)(*self.pn),
+                      int(self.periodic), self.level, self.eta_mean)
+
+
 _lib = None
 
 
@@ -96,6 +117,11 @@ def lib():
         _lib.orc_cic_deposit.argtypes = [ctypes.c_int, ctypes.c_int64, f, f, f, d]
         _lib.orc_gradient.argtypes = [ctypes.c_int, ctypes.c_double, d, d, d, d]
         _lib.orc_fifth_force.argtypes = [P(_Problem), d, d, ctypes.c_int64, f, f, f, d, d, d]
+        u8 = P(ctypes.c_uint8)
+        _lib.orc_patch_solve.argtypes = [P(_Problem), P(_Patch), d, u8, d, d, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, P(_Info)]
+        _lib.orc_patch_eval.argtypes = [P(_Problem), P(ctypes.c_int), ctypes.c_double, d, d, d, d, d,
+                                        ctypes.c_double, d, d]
     return _lib
 
 
@@ -291,3 +317,37 @@ def pm_run(model, N: int, box: float, pos, vel, a_steps, tol: float = 1e-10, nco
         leapfrog_kick_drift(pos, vel, g, 0.5 * (dtau_prev + dtau), dtau, N, h)
         dtau_prev = dtau
     return pos, vel
+
+
+def patch_solve(p: Problem, patch: Patch, parent: np.ndarray, flags: np.ndarray, eta: np.ndarray, u0=None,
+                tol: float = 1e-10, nu1: int = 2, nu2: int = 2, max_cycles: int = 100) -> SolveResult:
+    """FAS solve on a refinement patch (P1-P7 of isis_oracle.c).  parent: the parent field (patch.pn);
+    flags: refined parent cells of the box (patch.n, uint8); eta: finest patch density (2 patch.n);
+    u0: guess at the unknowns (None: start from the interpolated parent field)."""
+    nf = tuple(2 * v for v in patch.n)
+    parent = np.ascontiguousarray(parent, dtype=np.float64)
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    assert parent.shape == tuple(patch.pn) and flags.shape == tuple(patch.n) and eta.shape == nf
+    u = np.zeros(nf) if u0 is None else np.array(u0, dtype=np.float64, order="C", copy=True)
+    assert u.shape == nf
+    info = _Info()
+    pc, bc = p.c(), patch.c()
+    st = lib().orc_patch_solve(ctypes.byref(pc), ctypes.byref(bc), _d(parent),
+                               flags.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _d(eta), _d(u), tol, nu1, nu2,
+                               max_cycles, 1 if u0 is None else 0, ctypes.byref(info))
+    return SolveResult(st, u, info.cycles, info.res0, info.ref, info.res_final,
+                       [info.hist[i] for i in range(info.cycles)], 0)
+
+
+def patch_eval(p: Problem, h: float, m, eta, u, pre, sig=None, eta_mean: float = 1.0):
+    """(L(u) - Sigma, dL/du) at the unknowns (m > 0) of one patch level, ghosts by Eq. (ueq) with u^Pre = pre."""
+    m, eta, u, pre = (np.ascontiguousarray(v, dtype=np.float64) for v in (m, eta, u, pre))
+    sig = None if sig is None else np.ascontiguousarray(sig, dtype=np.float64)
+    F, dF = np.zeros(m.shape), np.zeros(m.shape)
+    n = (ctypes.c_int * 3)(*m.shape)
+    pc = p.c()
+    st = lib().orc_patch_eval(ctypes.byref(pc), n, h, _d(m), _d(eta), _d(u), _d(pre), _d(sig), eta_mean, _d(F),
+                              _d(dF))
+    assert st == OK, st
+    return F, dF

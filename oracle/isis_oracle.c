@@ -126,10 +126,12 @@ static void make_coef(const orc_problem* p, const double* eta_fine, orc_coef* c)
   } else {
     /* Sect. 3.1: lap Phi = (3/2) Om H0^2 delta / a, delta = eta - 1 with its mean removed (R7) */
     c->KP = 1.5 * p->Omega_m * H02 / a;
-    double sum = 0.0;
-    size_t n3 = (size_t)p->N * p->N * p->N;
-    for (size_t q = 0; q < n3; ++q) sum += eta_fine[q];
-    c->eta_mean = sum / (double)n3;
+    if (eta_fine) { /* a refinement patch passes NULL and sets the domain mean itself */
+      double sum = 0.0;
+      size_t n3 = (size_t)p->N * p->N * p->N;
+      for (size_t q = 0; q < n3; ++q) sum += eta_fine[q];
+      c->eta_mean = sum / (double)n3;
+    }
   }
 }
 
@@ -723,5 +725,384 @@ int orc_fifth_force(const orc_problem* p, const double* Phi, const double* phi, 
     gz[q] = -acc[2];
   }
   for (int d = 0; d < 3; ++d) { free(f[d]); free(g[d]); }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Refinement patches: masks and ghost values (Sect. 3.3.1, 3.4.1)     */
+/* ------------------------------------------------------------------ */
+/*
+ * A patch is a box of n[0] x n[1] x n[2] cells of its parent grid, origin o[],
+ * refined by two: its finest level has 2n cells per axis and h = h_parent / 2
+ * = box / (N 2^level).  flags[] (one per parent cell of the box, same order)
+ * marks the refined parent cells, whose 8 children exist.  Readings:
+ *   P1 mask: children of flagged cells m = +1, the others m = -1 (they do not
+ *      exist); every coarser level of the patch's multigrid takes m = R(m)
+ *      (Sect. 3.4.1).  Cells with m > 0 are the unknowns; the others keep
+ *      their values.  Flags on the box's outer layer of parent cells must be
+ *      0, so unknowns never touch the edge of the box on any level.
+ *   P2 the cells that do not exist on the finest level hold u^Int, the
+ *      cell-centred trilinear interpolation (R1's P) of the parent field;
+ *      coarser levels take all values from R (full-approximation restriction).
+ *   P3 the ghost value of a neighbour nb with m_nb <= 0 of an unknown c is
+ *      Eq. (ueq): u^G = u_nb + (m_nb / m_c)(u_c - u_c^Pre), where u_nb is the
+ *      neighbour's value (u^Int or its value before the iterations) and
+ *      u_c^Pre the value of c when the smoothing phase (nu sweeps) began.
+ *      Residuals take u^Pre = u, so u^G = u_nb.  f(R): b^G = e^{u^G} and
+ *      c^G = db/du = e^{u^G} (the consistent choice of Sect. 3.4.1).
+ *   P4 dL/du_c gains, for every masked neighbour, the derivative through u^G
+ *      (Sect. 3.4.1): (m_nb/m_c)/h^2 (canonical), (m_nb/m_c)[(c^G/2)(u^G - u_c)
+ *      + b_f]/h^2 (f(R), with the factor 1/2 of the face mean as in R4).
+ *   P5 FAS on the patch levels: the residual (zero off the unknowns) and u are
+ *      restricted with R; Sigma_H = L_H(R u) + R r at the coarse unknowns; the
+ *      correction P(u_H - R u) is added at the fine unknowns, with a zero
+ *      correction for coarse cells outside the box.
+ *   P6 levels: halve while every dimension is even and the smallest is >= 8;
+ *      the coarsest level gets 64 red-black sweeps (the paper is silent).
+ *   P7 convergence: RMS of L(u) - Sigma over the finest unknowns <= tol * ref,
+ *      ref = R6's closed form over the same cells.
+ */
+
+typedef struct {
+  int n[3];         /* patch box in parent cells */
+  int o[3];         /* its origin in parent cells */
+  int pn[3];        /* parent grid dimensions */
+  int periodic;     /* 1: the parent is the periodic domain grid */
+  int level;        /* refinement level >= 1 of the patch */
+  double eta_mean;  /* Poisson: the domain's mean density */
+} orc_patch;
+
+typedef struct {
+  int n[3];
+  double h;
+  double *m, *eta, *u, *u0, *sig, *res, *pre;
+} orc_plevel;
+
+typedef struct {
+  orc_coef coef;
+  int nlev;
+  orc_plevel lev[16];
+  int nu1, nu2;
+} orc_phier;
+
+static size_t PIDX(const int* n, int i, int j, int k) { return ((size_t)i * n[1] + j) * n[2] + k; }
+static size_t PSIZE(const int* n) { return (size_t)n[0] * n[1] * n[2]; }
+
+/* P3: value of neighbour d seen by the unknown q, and its mask ratio (0 for an unknown). */
+static double patch_nb(const orc_plevel* L, size_t q, int i, int j, int k, int d, double* mu) {
+  size_t qn = PIDX(L->n, i + DI[d], j + DJ[d], k + DK[d]);
+  double mn = L->m[qn];
+  if (mn > 0.0) { *mu = 0.0; return L->u[qn]; }
+  *mu = mn / L->m[q];
+  return L->u[qn] + (*mu) * (L->u[q] - L->pre[q]);
+}
+
+/* L(u) at the unknown (i,j,k) (Eq. (gen_lap) in its general form, Eq. (disc_non_canonical)) and
+   dL/du (Sect. 3.3, Eq. (dbeq) with R4, plus P4). */
+static void patch_op(const orc_coef* c, const orc_plevel* L, int i, int j, int k, double* Lv, double* dL) {
+  size_t q = PIDX(L->n, i, j, k);
+  double h2 = L->h * L->h, u = L->u[q], eta = L->eta[q];
+  double acc = 0.0, dacc = 0.0;
+  if (c->model == ORC_FOFR) {
+    double bu = exp(u);
+    for (int d = 0; d < 6; ++d) {
+      double mu, un = patch_nb(L, q, i, j, k, d, &mu);
+      double bn = exp(un), bf = 0.5 * (bu + bn);
+      acc += bf * (un - u);
+      dacc += -bf + 0.5 * bu * (un - u);
+      dacc += mu * (0.5 * bn * (un - u) + bf);
+    }
+  } else {
+    for (int d = 0; d < 6; ++d) {
+      double mu, un = patch_nb(L, q, i, j, k, d, &mu);
+      acc += un;
+      dacc += mu;
+    }
+    acc -= 6.0 * u;
+    dacc -= 6.0;
+  }
+  *Lv = acc / h2 - source(c, u, eta);
+  *dL = dacc / h2 - dsource(c, u, eta);
+}
+
+/* One red-black Newton-Gauss-Seidel sweep over the unknowns (Sect. 3.2). */
+static void patch_sweep(const orc_coef* c, orc_plevel* L) {
+  for (int color = 0; color < 2; ++color) {
+#pragma omp parallel for schedule(static)
+    for (int i = 1; i < L->n[0] - 1; ++i)
+      for (int j = 1; j < L->n[1] - 1; ++j)
+        for (int k = 1; k < L->n[2] - 1; ++k) {
+          if (((i + j + k) & 1) != color) continue;
+          size_t q = PIDX(L->n, i, j, k);
+          if (!(L->m[q] > 0.0)) continue;
+          double Lv, dL;
+          patch_op(c, L, i, j, k, &Lv, &dL);
+          double sig = L->sig ? L->sig[q] : 0.0;
+          L->u[q] = L->u[q] - (Lv - sig) / dL;
+        }
+  }
+}
+
+/* A smoothing phase: u^Pre fixed at its start (P3), then nsweep sweeps. */
+static void patch_phase(const orc_coef* c, orc_plevel* L, int nsweep) {
+  memcpy(L->pre, L->u, PSIZE(L->n) * sizeof(double));
+  for (int s = 0; s < nsweep; ++s) patch_sweep(c, L);
+}
+
+/* res = Sigma - L(u) at the unknowns, 0 elsewhere (u^Pre = u). */
+static void patch_residual(const orc_coef* c, orc_plevel* L) {
+  memcpy(L->pre, L->u, PSIZE(L->n) * sizeof(double));
+  size_t n3 = PSIZE(L->n);
+  memset(L->res, 0, n3 * sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (int i = 1; i < L->n[0] - 1; ++i)
+    for (int j = 1; j < L->n[1] - 1; ++j)
+      for (int k = 1; k < L->n[2] - 1; ++k) {
+        size_t q = PIDX(L->n, i, j, k);
+        if (!(L->m[q] > 0.0)) continue;
+        double Lv, dL;
+        patch_op(c, L, i, j, k, &Lv, &dL);
+        L->res[q] = (L->sig ? L->sig[q] : 0.0) - Lv;
+      }
+}
+
+/* P7: RMS of the residual over the unknowns, and their number. */
+static double patch_rms(const orc_coef* c, orc_plevel* L, size_t* count) {
+  patch_residual(c, L);
+  double s = 0.0;
+  size_t cnt = 0, n3 = PSIZE(L->n);
+  for (size_t q = 0; q < n3; ++q)
+    if (L->m[q] > 0.0) { s += L->res[q] * L->res[q]; ++cnt; }
+  if (count) *count = cnt;
+  return cnt ? sqrt(s / (double)cnt) : 0.0;
+}
+
+/* R1 on a box: coarse = mean of the 8 children. */
+static void patch_restrict(const int* nc, const double* fine, double* coarse) {
+  int nf[3] = {2 * nc[0], 2 * nc[1], 2 * nc[2]};
+  for (int I = 0; I < nc[0]; ++I)
+    for (int J = 0; J < nc[1]; ++J)
+      for (int K = 0; K < nc[2]; ++K) {
+        double s = 0.0;
+        for (int di = 0; di < 2; ++di)
+          for (int dj = 0; dj < 2; ++dj)
+            for (int dk = 0; dk < 2; ++dk) s += fine[PIDX(nf, 2 * I + di, 2 * J + dj, 2 * K + dk)];
+        coarse[PIDX(nc, I, J, K)] = s / 8.0;
+      }
+}
+
+/* P5: fine unknowns += P(cdelta), coarse cells outside the box contributing 0. */
+static void patch_prolong_add(const orc_plevel* C, const double* cdelta, orc_plevel* L) {
+  for (int i = 0; i < L->n[0]; ++i)
+    for (int j = 0; j < L->n[1]; ++j)
+      for (int k = 0; k < L->n[2]; ++k) {
+        size_t q = PIDX(L->n, i, j, k);
+        if (!(L->m[q] > 0.0)) continue;
+        int ci[2] = {i / 2, i / 2 + ((i & 1) ? 1 : -1)};
+        int cj[2] = {j / 2, j / 2 + ((j & 1) ? 1 : -1)};
+        int ck[2] = {k / 2, k / 2 + ((k & 1) ? 1 : -1)};
+        double w[2] = {0.75, 0.25}, v = 0.0;
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b)
+            for (int d = 0; d < 2; ++d) {
+              if (ci[a] < 0 || ci[a] >= C->n[0] || cj[b] < 0 || cj[b] >= C->n[1] || ck[d] < 0 || ck[d] >= C->n[2])
+                continue;
+              v += w[a] * w[b] * w[d] * cdelta[PIDX(C->n, ci[a], cj[b], ck[d])];
+            }
+        L->u[q] += v;
+      }
+}
+
+/* P2: u^Int of every cell of the finest patch level from the parent field. */
+static void patch_interp(const orc_patch* P, const double* parent, const int* nf, double* out) {
+  for (int i = 0; i < nf[0]; ++i)
+    for (int j = 0; j < nf[1]; ++j)
+      for (int k = 0; k < nf[2]; ++k) {
+        int f[3] = {i, j, k}, pc[3][2];
+        for (int a = 0; a < 3; ++a) {
+          pc[a][0] = P->o[a] + f[a] / 2;
+          pc[a][1] = pc[a][0] + ((f[a] & 1) ? 1 : -1);
+          if (P->periodic) { pc[a][0] = WRAP(pc[a][0], P->pn[a]); pc[a][1] = WRAP(pc[a][1], P->pn[a]); }
+        }
+        double w[2] = {0.75, 0.25}, v = 0.0;
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b)
+            for (int d = 0; d < 2; ++d) v += w[a] * w[b] * w[d] * parent[PIDX(P->pn, pc[0][a], pc[1][b], pc[2][d])];
+        out[PIDX(nf, i, j, k)] = v;
+      }
+}
+
+static void patch_vcycle(orc_phier* H, int l) {
+  orc_plevel* L = &H->lev[l];
+  if (l == H->nlev - 1) { patch_phase(&H->coef, L, 64); return; }
+  orc_plevel* C = &H->lev[l + 1];
+  size_t nc = PSIZE(C->n);
+  patch_phase(&H->coef, L, H->nu1);
+  patch_residual(&H->coef, L);
+  patch_restrict(C->n, L->u, C->u);
+  memcpy(C->u0, C->u, nc * sizeof(double));
+  patch_restrict(C->n, L->res, C->sig);
+  memcpy(C->pre, C->u, nc * sizeof(double));
+  for (int i = 1; i < C->n[0] - 1; ++i)
+    for (int j = 1; j < C->n[1] - 1; ++j)
+      for (int k = 1; k < C->n[2] - 1; ++k) {
+        size_t q = PIDX(C->n, i, j, k);
+        if (!(C->m[q] > 0.0)) continue;
+        double Lv, dL;
+        patch_op(&H->coef, C, i, j, k, &Lv, &dL);
+        C->sig[q] += Lv;
+      }
+  patch_vcycle(H, l + 1);
+  for (size_t q = 0; q < nc; ++q) C->u0[q] = C->u[q] - C->u0[q];
+  patch_prolong_add(C, C->u0, L);
+  patch_phase(&H->coef, L, H->nu2);
+}
+
+static void free_phier(orc_phier* H) {
+  for (int l = 0; l < H->nlev; ++l) {
+    orc_plevel* L = &H->lev[l];
+    free(L->m); free(L->eta); free(L->u0); free(L->res); free(L->pre);
+    if (l > 0) { free(L->u); free(L->sig); }
+  }
+}
+
+static int patch_valid(const orc_problem* p, const orc_patch* P, const uint8_t* flags) {
+  if (!valid(p) || P->level < 1 || P->level > 12) return 0;
+  for (int a = 0; a < 3; ++a) {
+    if (P->n[a] < 4 || (P->n[a] & 1) || P->pn[a] < 1) return 0;
+    if (P->periodic) {
+      if (P->pn[a] != p->N || P->n[a] > P->pn[a]) return 0;
+    } else if (P->o[a] < 1 || P->o[a] + P->n[a] + 1 > P->pn[a]) {
+      return 0;
+    }
+  }
+  for (int i = 0; i < P->n[0]; ++i)
+    for (int j = 0; j < P->n[1]; ++j)
+      for (int k = 0; k < P->n[2]; ++k) {
+        int edge = i == 0 || j == 0 || k == 0 || i == P->n[0] - 1 || j == P->n[1] - 1 || k == P->n[2] - 1;
+        if (edge && flags[PIDX(P->n, i, j, k)]) return 0;
+      }
+  return 1;
+}
+
+/* Solve the patch (Sect. 3.3.1, 3.4.1; P1-P7).  parent: the parent field (P->pn dims); flags: refined
+   parent cells of the box; eta: density of the finest patch level (2n dims); u: the finest patch level,
+   in: the guess at the unknowns when init == 0 (init == 1: start from u^Int), out: the solution (cells
+   that are not unknowns hold u^Int). */
+int orc_patch_solve(const orc_problem* p, const orc_patch* P, const double* parent, const uint8_t* flags,
+                    const double* eta, double* u, double tol, int nu1, int nu2, int max_cycles, int init,
+                    orc_info* info) {
+  if (!patch_valid(p, P, flags) || max_cycles < 0 || max_cycles > 256 || nu1 < 0 || nu2 < 0) return ORC_EINVAL;
+  orc_phier H;
+  memset(&H, 0, sizeof(H));
+  make_coef(p, NULL, &H.coef);
+  H.coef.eta_mean = P->eta_mean;
+  H.nu1 = nu1;
+  H.nu2 = nu2;
+  int n[3] = {2 * P->n[0], 2 * P->n[1], 2 * P->n[2]};
+  double h = p->box / ((double)p->N * (double)(1 << P->level));
+  for (int l = 0;; ++l) {
+    orc_plevel* L = &H.lev[l];
+    size_t n3 = PSIZE(n);
+    memcpy(L->n, n, sizeof(n));
+    L->h = h;
+    L->m = (double*)malloc(n3 * sizeof(double));
+    L->eta = (double*)malloc(n3 * sizeof(double));
+    L->u0 = (double*)malloc(n3 * sizeof(double));
+    L->res = (double*)malloc(n3 * sizeof(double));
+    L->pre = (double*)malloc(n3 * sizeof(double));
+    if (l == 0) { L->u = u; L->sig = NULL; }
+    else { L->u = (double*)malloc(n3 * sizeof(double)); L->sig = (double*)calloc(n3, sizeof(double)); }
+    H.nlev = l + 1;
+    if (!L->m || !L->eta || !L->u0 || !L->res || !L->pre || !L->u || (l > 0 && !L->sig)) {
+      free_phier(&H);
+      return ORC_ENOMEM;
+    }
+    if (l == 0) {
+      /* P1 */
+      for (int i = 0; i < n[0]; ++i)
+        for (int j = 0; j < n[1]; ++j)
+          for (int k = 0; k < n[2]; ++k)
+            L->m[PIDX(n, i, j, k)] = flags[PIDX(P->n, i / 2, j / 2, k / 2)] ? 1.0 : -1.0;
+      memcpy(L->eta, eta, n3 * sizeof(double));
+    } else {
+      patch_restrict(n, H.lev[l - 1].m, L->m);
+      patch_restrict(n, H.lev[l - 1].eta, L->eta);
+    }
+    int mn = n[0] < n[1] ? n[0] : n[1];
+    if (n[2] < mn) mn = n[2];
+    if ((n[0] & 1) || (n[1] & 1) || (n[2] & 1) || mn < 8 || l == 15) break;
+    n[0] /= 2; n[1] /= 2; n[2] /= 2;
+    h *= 2.0;
+  }
+  orc_plevel* F = &H.lev[0];
+  size_t nf3 = PSIZE(F->n);
+  /* P2: u^Int where the cells do not exist (and everywhere for init == 1) */
+  patch_interp(P, parent, F->n, F->u0);
+  for (size_t q = 0; q < nf3; ++q)
+    if (init == 1 || !(F->m[q] > 0.0)) u[q] = F->u0[q];
+  memset(info, 0, sizeof(*info));
+  /* P7: R6's reference over the unknowns */
+  {
+    double eref = (p->model == ORC_POISSON) ? P->eta_mean : 1.0, s2 = 0.0;
+    size_t cnt = 0;
+    for (size_t q = 0; q < nf3; ++q)
+      if (F->m[q] > 0.0) { s2 += (eta[q] - eref) * (eta[q] - eref); ++cnt; }
+    double scale;
+    if (p->model == ORC_SYMMETRON) scale = H.coef.A * H.coef.s * background(p, &H.coef);
+    else if (p->model == ORC_FOFR) scale = H.coef.K1;
+    else scale = H.coef.KP;
+    info->ref = cnt ? scale * sqrt(s2 / (double)cnt) : 0.0;
+  }
+  size_t cnt = 0;
+  double res = patch_rms(&H.coef, F, &cnt);
+  info->res0 = res;
+  if (!(info->ref > 0.0)) info->ref = res;
+  info->res_final = res;
+  int st;
+  if (cnt == 0 || res <= tol * info->ref) st = ORC_OK;
+  else if (!isfinite(res)) st = ORC_ENAN;
+  else {
+    st = ORC_ENOCONV;
+    for (int cyc = 0; cyc < max_cycles; ++cyc) {
+      patch_vcycle(&H, 0);
+      res = patch_rms(&H.coef, F, NULL);
+      info->hist[cyc] = res;
+      info->cycles = cyc + 1;
+      info->res_final = res;
+      if (!isfinite(res)) { st = ORC_ENAN; break; }
+      if (res <= tol * info->ref) { st = ORC_OK; break; }
+    }
+  }
+  free_phier(&H);
+  return st;
+}
+
+/* For pins: L(u) - Sigma and dL/du at the unknowns of one patch level with mask m (0 elsewhere), u^Pre =
+   pre.  Cells with m > 0 must not lie on the outer layer of the box. */
+int orc_patch_eval(const orc_problem* p, const int* n, double h, const double* m, const double* eta,
+                   const double* u, const double* pre, const double* sig, double eta_mean, double* F, double* dF) {
+  if (!valid(p)) return ORC_EINVAL;
+  orc_coef c;
+  make_coef(p, NULL, &c);
+  c.eta_mean = eta_mean;
+  orc_plevel L;
+  memset(&L, 0, sizeof(L));
+  memcpy(L.n, n, 3 * sizeof(int));
+  L.h = h;
+  L.m = (double*)m; L.eta = (double*)eta; L.u = (double*)u; L.pre = (double*)pre; L.sig = (double*)sig;
+  size_t n3 = PSIZE(n);
+  for (size_t q = 0; q < n3; ++q) { F[q] = 0.0; dF[q] = 0.0; }
+  for (int i = 0; i < n[0]; ++i)
+    for (int j = 0; j < n[1]; ++j)
+      for (int k = 0; k < n[2]; ++k) {
+        size_t q = PIDX(n, i, j, k);
+        if (!(m[q] > 0.0)) continue;
+        if (i == 0 || j == 0 || k == 0 || i == n[0] - 1 || j == n[1] - 1 || k == n[2] - 1) return ORC_EINVAL;
+        double Lv, dL;
+        patch_op(&c, &L, i, j, k, &Lv, &dL);
+        F[q] = Lv - (sig ? sig[q] : 0.0);
+        dF[q] = dL;
+      }
   return ORC_OK;
 }
