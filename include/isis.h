@@ -87,8 +87,10 @@ typedef struct {
  *   ISIS_INIT_LOCAL       phi is overwritten cell by cell with the solution for a
  *                         uniform density equal to the cell's eta (same formulas with
  *                         (a_SSB/a)^3 eta and eta a^-3); Phi = 0.  Suits f(R) with
- *                         dense haloes, where Newton steps from the background overshoot. */
-typedef enum { ISIS_INIT_INPUT = 0, ISIS_INIT_BACKGROUND = 1, ISIS_INIT_LOCAL = 2 } isis_init;
+ *                         dense haloes, where Newton steps from the background overshoot.
+ *   ISIS_INIT_PARENT      refinement patches only: the unknowns start from the parent
+ *                         field interpolated to them. */
+typedef enum { ISIS_INIT_INPUT = 0, ISIS_INIT_BACKGROUND = 1, ISIS_INIT_LOCAL = 2, ISIS_INIT_PARENT = 3 } isis_init;
 
 typedef struct {
   int nu1, nu2;        /* pre- and post-smoothing sweeps (red then black) per level */
@@ -207,6 +209,64 @@ isis_status isis_fifth_force(isis_model model, const isis_params* params, const 
 isis_status isis_kick_drift(const isis_grid* grid, float* x, float* y, float* z, float* vx, float* vy, float* vz,
                             const float* gx, const float* gy, const float* gz, int64_t npart, double kick,
                             double drift, void* stream);
+
+/* ---- Refinement patches (Sect. 3.3.1, Sect. 3.4.1) ------------------------
+ * One refinement level over a box of its parent grid, solved with the parent
+ * field as boundary data, as the paper solves each refined level after its
+ * parent.  The box is n[0] x n[1] x n[2] parent cells at `origin`, refined by
+ * two: the patch arrays hold all (2n[0]) x (2n[1]) x (2n[2]) fine cells in
+ * row-major order (k fastest), fine cell (i,j,k) centred at parent-cell
+ * coordinates origin + (i+1/2, j+1/2, k+1/2)/2 and of size
+ * h = grid->box / (grid->N 2^level).  `flags` marks the refined parent cells;
+ * their children are the unknowns.  The other fine cells do not exist in the
+ * paper's sense: they get the parent field by cell-centred trilinear
+ * interpolation (weights 3/4, 1/4 per axis) and serve as boundary values.
+ * Masks and ghost values follow the paper: mask +1 at unknowns and -1
+ * elsewhere, restricted (mean of 8) on the patch's coarser multigrid levels,
+ * and a masked neighbour of an unknown c enters the stencil as
+ *     u_nb + (m_nb/m_c)(u_c - u_c^Pre)                         (Eq. (ueq))
+ * with u_c^Pre the value of c when the smoothing phase began, b and db/du of
+ * f(R) taken at that ghost value, and the Newton derivative gaining the terms
+ * through it.  The converged field satisfies the equation at every unknown
+ * with the boundary cells at their interpolated values.
+ *   n          each even and >= 4; the coarsest level of the patch's multigrid
+ *              (halving while all dimensions are even and the smallest >= 8)
+ *              must have at most 32768 cells.
+ *   origin     box origin in parent cells.
+ *   parent_dims, parent_periodic
+ *              level 1: the parent is the periodic domain grid (N, N, N), and the
+ *              box may wrap round it; level >= 2: the parent is the previous
+ *              patch's field (its fine dims) and 1 <= origin, origin + n + 1 <=
+ *              parent_dims (the interpolation reads one parent cell beyond the box).
+ *   eta_mean   Poisson: the domain's mean density (the source is K (eta - eta_mean)).
+ *   flags      device uint8[n0 n1 n2]; flags on the outer layer of the box are rejected.
+ *   parent     device double, parent_dims.
+ *   eta, phi   device double[(2n0)(2n1)(2n2)]: the density of the patch cells, and
+ *              the field: the guess at the unknowns in (ISIS_INIT_INPUT) or ignored
+ *              (ISIS_INIT_PARENT); out, the solution at the unknowns and the
+ *              interpolated parent elsewhere.
+ *   opts       prec must be ISIS_F64; init ISIS_INIT_INPUT or ISIS_INIT_PARENT;
+ *              n_coarsest is ignored.  The convergence test is the solvers' own
+ *              over the unknowns (res_ref from the unknowns' eta).
+ *   Workspace: allocated stream-ordered per call and freed before return.  The
+ *   call synchronises the stream once per cycle and once to check the flags. */
+typedef struct {
+  int n[3];
+  int origin[3];
+  int parent_dims[3];
+  int parent_periodic;
+  int level;
+  double eta_mean;
+} isis_patch;
+
+isis_status isis_patch_poisson_solve(const isis_grid* grid, double a, const isis_patch* box, const void* parent,
+                                     const uint8_t* flags, const void* eta, void* Phi, double tol,
+                                     const isis_mg_opts* opts, isis_solve_info* info, void* stream);
+
+isis_status isis_patch_scalar_solve(isis_model model, const isis_params* params, const isis_grid* grid, double a,
+                                    const isis_patch* box, const void* parent, const uint8_t* flags,
+                                    const void* eta, void* phi, double tol, const isis_mg_opts* opts,
+                                    isis_solve_info* info, void* stream);
 
 /* ---- Instrumentation (not part of the paper's method) -------------------
  * Every kernel launch of the library is counted.  When profiling is on, each

@@ -738,9 +738,10 @@ int orc_fifth_force(const orc_problem* p, const double* Phi, const double* phi, 
  * marks the refined parent cells, whose 8 children exist.  Readings:
  *   P1 mask: children of flagged cells m = +1, the others m = -1 (they do not
  *      exist); every coarser level of the patch's multigrid takes m = R(m)
- *      (Sect. 3.4.1).  Cells with m > 0 are the unknowns; the others keep
- *      their values.  Flags on the box's outer layer of parent cells must be
- *      0, so unknowns never touch the edge of the box on any level.
+ *      (Sect. 3.4.1), except its outer layer of cells, which stays m = -1 (it
+ *      lies outside the box's refined part; flags on the box's outer layer of
+ *      parent cells must be 0, which makes this hold on the finest level too).
+ *      Cells with m > 0 are the unknowns; the others keep their values.
  *   P2 the cells that do not exist on the finest level hold u^Int, the
  *      cell-centred trilinear interpolation (R1's P) of the parent field;
  *      coarser levels take all values from R (full-approximation restriction).
@@ -1028,6 +1029,11 @@ int orc_patch_solve(const orc_problem* p, const orc_patch* P, const double* pare
     } else {
       patch_restrict(n, H.lev[l - 1].m, L->m);
       patch_restrict(n, H.lev[l - 1].eta, L->eta);
+      for (int i = 0; i < n[0]; ++i)
+        for (int j = 0; j < n[1]; ++j)
+          for (int k = 0; k < n[2]; ++k)
+            if (i == 0 || j == 0 || k == 0 || i == n[0] - 1 || j == n[1] - 1 || k == n[2] - 1)
+              L->m[PIDX(n, i, j, k)] = -1.0;
     }
     int mn = n[0] < n[1] ? n[0] : n[1];
     if (n[2] < mn) mn = n[2];

@@ -3,7 +3,11 @@
 #include <cmath>
 #include <cstdio>
 #include <mutex>
+#include <vector>
+#include <algorithm>
+#include <cstring>
 
+#include "isis_patch.cuh"
 #include "isis_solver.cuh"
 
 namespace isis {
@@ -155,6 +159,38 @@ static bool opts_resolve(const isis_mg_opts* o, isis_mg_opts* out, int N) {
   return true;
 }
 
+// Constants of a scalar model (field form, fscale = 1) and the scale of its reference residual.
+static bool model_coef(isis_model model, const isis_params* p, const isis_grid* grid, double a, Coef* c,
+                       double* ref_scale) {
+  const double H02 = grid->H0 * grid->H0;
+  if (model == ISIS_SYMMETRON) {
+    if (!(p->lambda0 > 0) || !(p->a_ssb > 0)) return false;
+    // Sect. 4.1, Eq. (symmetron_dimensionles)
+    c->A = a * a / (2.0 * p->lambda0 * p->lambda0);
+    double q = p->a_ssb / a;
+    c->s = q * q * q;
+    double chi_bg = c->s < 1.0 ? std::sqrt(1.0 - c->s) : 0.0;
+    *ref_scale = c->A * c->s * chi_bg;
+    return true;
+  }
+  if (model == ISIS_FOFR_HS) {
+    if (p->n < 1 || p->n > 8 || !(p->fR0_abs > 0)) return false;
+    // Sect. 4.2, the non-canonical equation for u with b = e^u
+    double r = grid->Omega_L / grid->Omega_m, np1 = p->n + 1.0;
+    c->np1 = np1;
+    c->inv_np1 = 1.0 / np1;
+    c->K1 = grid->Omega_m * a * H02;
+    c->K2 = grid->Omega_m * a * a * a * a * H02 * (1.0 + 4.0 * r) * std::pow(p->fR0_abs * a * a, 1.0 / np1);
+    c->K3 = grid->Omega_m * a * H02 * (1.0 + 4.0 * a * a * a * r);
+    c->fscale = 1.0;  // field form in u itself; the refinement's first phase shifts it
+    c->fKx = c->K2;
+    c->fK3x = c->K3 - c->K2;
+    *ref_scale = c->K1;
+    return true;
+  }
+  return false;
+}
+
 static void fill_common(SolveArgs& A, const isis_grid* g, double a, const void* eta, void* phi, double tol,
                         const isis_mg_opts& o, isis_solve_info* info, void* stream) {
   A.N = g->N;
@@ -183,7 +219,8 @@ static const char* kKindNames[KK_COUNT] = {
     "smooth_fine",    "smooth_coarse", "resid_restrict_fine", "resid_restrict_coarse", "coarse_sigma",
     "prolong_fine",   "prolong_coarse", "coarse_newton",      "norm_fine",             "outer_residual64",
     "update64",       "setup",         "reduce",              "init_guess",            "cic_scatter",
-    "cic_finish",     "force_grid",    "force_gather",        "unet_conv",             "unet_elem"};
+    "cic_finish",     "force_grid",    "force_gather",        "unet_conv",             "unet_elem",
+    "patch_smooth",   "patch_other"};
 
 struct ProfRec {
   int kind;
@@ -321,33 +358,109 @@ isis_status isis_scalar_solve(isis_model model, const isis_params* p, const isis
     return ISIS_EINVAL;
   SolveArgs A;
   fill_common(A, grid, a, eta, phi, tol, o, info, stream);
-  const double H02 = grid->H0 * grid->H0;
+  if (!model_coef(model, p, grid, a, &A.coef, &A.ref_scale)) return ISIS_EINVAL;
+  return model == ISIS_SYMMETRON ? run_sym(A) : run_fofr(A);
+}
+
+// Refinement patches (Sect. 3.3.1, Sect. 3.4.1).
+static isis_status patch_common(PatchArgs& P, const isis_grid* grid, double a, const isis_patch* box,
+                                const void* parent, const uint8_t* flags, const void* eta, void* phi, double tol,
+                                const isis_mg_opts* opts, isis_solve_info* info, void* stream) {
+  if (!grid_ok(grid) || !box || !parent || !flags || !eta || !phi || !(a > 0) || !(tol >= 0)) return ISIS_EINVAL;
+  isis_mg_opts o = {2, 2, 4, 100, ISIS_F64, 2, ISIS_INIT_INPUT};
+  if (opts) o = *opts;
+  if (o.nu1 < 0 || o.nu1 > 16 || o.nu2 < 0 || o.nu2 > 16 || o.max_cycles < 0 || o.max_cycles > 128) return ISIS_EINVAL;
+  if (o.prec != ISIS_F64 || (o.init != ISIS_INIT_INPUT && o.init != ISIS_INIT_PARENT)) return ISIS_EINVAL;
+  if (box->level < 1 || box->level > 12) return ISIS_EINVAL;
+  int64_t nflag = 0;
+  for (int d = 0; d < 3; ++d) {
+    const int n = box->n[d], pn = box->parent_dims[d], o0 = box->origin[d];
+    if (n < 4 || (n & 1) || n > 2048) return ISIS_EINVAL;
+    if (box->parent_periodic) {
+      if (box->level != 1 || pn != grid->N || n > pn || o0 < 0 || o0 >= pn) return ISIS_EINVAL;
+    } else if (box->level < 2 || pn < 1 || o0 < 1 || o0 + n + 1 > pn) {
+      return ISIS_EINVAL;
+    }
+  }
+  // the coarsest patch level is relaxed by one block: keep it small
+  {
+    int m[3] = {2 * box->n[0], 2 * box->n[1], 2 * box->n[2]};
+    while (!(m[0] & 1) && !(m[1] & 1) && !(m[2] & 1) && std::min(m[0], std::min(m[1], m[2])) >= 8) {
+      m[0] /= 2; m[1] /= 2; m[2] /= 2;
+    }
+    if ((int64_t)m[0] * m[1] * m[2] > 32768) return ISIS_EINVAL;
+  }
+  // refine flags: none on the outer layer of the box; count the unknowns
+  const size_t nb = (size_t)box->n[0] * box->n[1] * box->n[2];
+  std::vector<uint8_t> hf(nb);
+  if (cudaMemcpyAsync(hf.data(), flags, nb, cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
+      cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return ISIS_ECUDA;
+  }
+  for (int i = 0; i < box->n[0]; ++i)
+    for (int j = 0; j < box->n[1]; ++j)
+      for (int k = 0; k < box->n[2]; ++k) {
+        const uint8_t f = hf[((size_t)i * box->n[1] + j) * box->n[2] + k];
+        if (!f) continue;
+        if (i == 0 || j == 0 || k == 0 || i == box->n[0] - 1 || j == box->n[1] - 1 || k == box->n[2] - 1)
+          return ISIS_EINVAL;
+        ++nflag;
+      }
+  std::memset(&P.coef, 0, sizeof(P.coef));
+  for (int d = 0; d < 3; ++d) {
+    P.n[d] = box->n[d];
+    P.origin[d] = box->origin[d];
+    P.pn[d] = box->parent_dims[d];
+  }
+  P.periodic = box->parent_periodic ? 1 : 0;
+  P.h = grid->box / ((double)grid->N * (double)(1 << box->level));
+  P.parent = (const double*)parent;
+  P.flags = flags;
+  P.eta = (const double*)eta;
+  P.phi = (double*)phi;
+  P.unknowns = 8 * nflag;
+  P.tol = tol;
+  P.nu1 = o.nu1;
+  P.nu2 = o.nu2;
+  P.max_cycles = o.max_cycles;
+  P.init_parent = o.init == ISIS_INIT_PARENT ? 1 : 0;
+  P.info = info;
+  P.st = (cudaStream_t)stream;
+  P.eref = 1.0;
+  return ISIS_OK;
+}
+
+isis_status isis_patch_poisson_solve(const isis_grid* grid, double a, const isis_patch* box, const void* parent,
+                                     const uint8_t* flags, const void* eta, void* Phi, double tol,
+                                     const isis_mg_opts* opts, isis_solve_info* info, void* stream) {
+  PatchArgs P;
+  isis_status st = patch_common(P, grid, a, box, parent, flags, eta, Phi, tol, opts, info, stream);
+  if (st != ISIS_OK) return st;
+  if (!std::isfinite(box->eta_mean)) return ISIS_EINVAL;
+  P.model = POI;
+  P.coef.KP = 1.5 * grid->Omega_m * grid->H0 * grid->H0 / a;
+  P.coef.eta_mean = box->eta_mean;
+  P.eref = box->eta_mean;
+  P.ref_scale = P.coef.KP;
+  return run_patch_poi(P);
+}
+
+isis_status isis_patch_scalar_solve(isis_model model, const isis_params* params, const isis_grid* grid, double a,
+                                    const isis_patch* box, const void* parent, const uint8_t* flags,
+                                    const void* eta, void* phi, double tol, const isis_mg_opts* opts,
+                                    isis_solve_info* info, void* stream) {
+  if (!params) return ISIS_EINVAL;
+  PatchArgs P;
+  isis_status st = patch_common(P, grid, a, box, parent, flags, eta, phi, tol, opts, info, stream);
+  if (st != ISIS_OK) return st;
+  if (!model_coef(model, params, grid, a, &P.coef, &P.ref_scale)) return ISIS_EINVAL;
   if (model == ISIS_SYMMETRON) {
-    if (!(p->lambda0 > 0) || !(p->a_ssb > 0)) return ISIS_EINVAL;
-    // Sect. 4.1, Eq. (symmetron_dimensionles)
-    A.coef.A = a * a / (2.0 * p->lambda0 * p->lambda0);
-    double q = p->a_ssb / a;
-    A.coef.s = q * q * q;
-    double chi_bg = A.coef.s < 1.0 ? std::sqrt(1.0 - A.coef.s) : 0.0;
-    A.ref_scale = A.coef.A * A.coef.s * chi_bg;
-    return run_sym(A);
+    P.model = SYM;
+    return run_patch_sym(P);
   }
-  if (model == ISIS_FOFR_HS) {
-    if (p->n < 1 || p->n > 8 || !(p->fR0_abs > 0)) return ISIS_EINVAL;
-    // Sect. 4.2, the non-canonical equation for u with b = e^u
-    double r = grid->Omega_L / grid->Omega_m, np1 = p->n + 1.0;
-    A.coef.np1 = np1;
-    A.coef.inv_np1 = 1.0 / np1;
-    A.coef.K1 = grid->Omega_m * a * H02;
-    A.coef.K2 = grid->Omega_m * a * a * a * a * H02 * (1.0 + 4.0 * r) * std::pow(p->fR0_abs * a * a, 1.0 / np1);
-    A.coef.K3 = grid->Omega_m * a * H02 * (1.0 + 4.0 * a * a * a * r);
-    A.coef.fscale = 1.0;  // field form in u itself; the refinement's first phase shifts it
-    A.coef.fKx = A.coef.K2;
-    A.coef.fK3x = A.coef.K3 - A.coef.K2;
-    A.ref_scale = A.coef.K1;
-    return run_fofr(A);
-  }
-  return ISIS_EINVAL;
+  P.model = FOFR;
+  return run_patch_fofr(P);
 }
 
 }  // extern "C"

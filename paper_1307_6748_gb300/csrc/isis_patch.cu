@@ -1,0 +1,509 @@
+// isis_patch.cu -- FAS solve on a refinement patch (Sect. 3.3.1, Sect. 3.4.1),
+// FP64, for the three models.  The readings are listed in isis_patch.cuh.
+//
+// Every level of the patch is a dense box in row-major order (k fastest);
+// kernels run one thread per cell.  The host loop synchronises once per cycle
+// to read the residual norm.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "isis_patch.cuh"
+#include "isis_prof.cuh"
+
+namespace isis {
+
+namespace {
+
+constexpr int kPT = 256;          // threads per block of the cell kernels
+constexpr int kPNormBlocks = 256;  // blocks of the norm kernels
+constexpr int kCoarseSweeps = 64;  // red/black sweeps on the coarsest patch level
+
+struct PL {  // one level of the patch
+  int n0, n1, n2;
+  double ih2;
+  const double* m;
+  const double* eta;
+  double* u;
+  const double* pre;
+  const double* sig;  // nullptr on the finest level
+};
+
+__device__ __forceinline__ size_t pidx(int n1, int n2, int i, int j, int k) {
+  return ((size_t)i * n1 + j) * n2 + k;
+}
+
+__device__ __forceinline__ void pdecode(size_t t, int n1, int n2, int& i, int& j, int& k) {
+  k = (int)(t % n2);
+  size_t r = t / n2;
+  j = (int)(r % n1);
+  i = (int)(r / n1);
+}
+
+// An unknown: m > 0 and off the outer layer (whose stencil would leave the box).
+__device__ __forceinline__ bool unknown(const PL& L, size_t t, int i, int j, int k) {
+  return L.m[t] > 0.0 && i > 0 && j > 0 && k > 0 && i < L.n0 - 1 && j < L.n1 - 1 && k < L.n2 - 1;
+}
+
+// L(u) - Sigma and dL/du at the unknown (i,j,k).  with_pre: ghosts follow Eq. (ueq) with the stored u^Pre;
+// otherwise u^Pre = u and a ghost is the neighbour's value.
+template <Model M>
+__device__ __forceinline__ void pt_eval(const Coef& c, const PL& L, int i, int j, int k, bool with_pre, double& F,
+                                        double& dF) {
+  const size_t q = pidx(L.n1, L.n2, i, j, k);
+  const double mc = L.m[q], u = L.u[q];
+  const double dpre = with_pre ? u - L.pre[q] : 0.0;
+  Cell<double> cell;
+  cell.x = u;
+  cell.eta = L.eta[q];
+  cell.sig = L.sig ? L.sig[q] : 0.0;
+  double mu[6];
+  const size_t s0 = (size_t)L.n1 * L.n2, s1 = (size_t)L.n2;
+  const size_t qn[6] = {q + s0, q - s0, q + s1, q - s1, q + 1, q - 1};
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const double mn = L.m[qn[d]];
+    double un = L.u[qn[d]];
+    mu[d] = 0.0;
+    if (!(mn > 0.0)) {
+      mu[d] = mn / mc;
+      un += mu[d] * dpre;
+    }
+    cell.xn[d] = un;
+  }
+  if constexpr (M == FOFR) {
+    cell.a = exp(u);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) cell.an[d] = exp(cell.xn[d]);
+  }
+  eval_cell<M, FIELD, double>(c, L.ih2, cell, F, dF);
+  // the derivative through the ghost values of the masked neighbours
+  double extra = 0.0;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    if constexpr (M == FOFR) {
+      extra += mu[d] * (0.5 * cell.an[d] * (cell.xn[d] - u) + 0.5 * (cell.a + cell.an[d]));
+    } else {
+      extra += mu[d];
+    }
+  }
+  dF += extra * L.ih2;
+}
+
+__global__ void pt_mask0(const uint8_t* __restrict__ flags, int b1, int b2, double* __restrict__ m, int n0, int n1,
+                         int n2) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n0 * n1 * n2) return;
+  int i, j, k;
+  pdecode(t, n1, n2, i, j, k);
+  m[t] = flags[pidx(b1, b2, i >> 1, j >> 1, k >> 1)] ? 1.0 : -1.0;
+}
+
+// coarse = mean of the 8 children (fine dims = 2 x coarse dims); edge != 0: the outer layer gets -1 (masks)
+__global__ void pt_restrict(const double* __restrict__ f, double* __restrict__ c, int n0, int n1, int n2,
+                            int edge = 0) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n0 * n1 * n2) return;
+  int I, J, K;
+  pdecode(t, n1, n2, I, J, K);
+  const int f1 = 2 * n1, f2 = 2 * n2;
+  double s = 0.0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const size_t r = pidx(f1, f2, 2 * I + a, 2 * J + b, 2 * K);
+      s += f[r] + f[r + 1];
+    }
+  c[t] = (edge && (I == 0 || J == 0 || K == 0 || I == n0 - 1 || J == n1 - 1 || K == n2 - 1)) ? -1.0 : 0.125 * s;
+}
+
+// Cell-centred trilinear interpolation of the parent at the finest patch cells: written where m <= 0,
+// or everywhere when all != 0.
+__global__ void pt_interp(const double* __restrict__ parent, int p0, int p1, int p2, int o0, int o1, int o2,
+                          int periodic, const double* __restrict__ m, double* __restrict__ u, int n0, int n1, int n2,
+                          int all) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n0 * n1 * n2) return;
+  if (!all && m[t] > 0.0) return;
+  int f[3];
+  pdecode(t, n1, n2, f[0], f[1], f[2]);
+  const int pd[3] = {p0, p1, p2}, od[3] = {o0, o1, o2};
+  int c[3][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    c[a][0] = od[a] + (f[a] >> 1);
+    c[a][1] = c[a][0] + ((f[a] & 1) ? 1 : -1);
+    if (periodic) {
+      c[a][0] = (c[a][0] % pd[a] + pd[a]) % pd[a];
+      c[a][1] = (c[a][1] % pd[a] + pd[a]) % pd[a];
+    }
+  }
+  const double w[2] = {0.75, 0.25};
+  double v = 0.0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int d = 0; d < 2; ++d) v += w[a] * w[b] * w[d] * parent[pidx(p1, p2, c[0][a], c[1][b], c[2][d])];
+  u[t] = v;
+}
+
+// One colour of a Newton-Gauss-Seidel sweep over the unknowns.
+template <Model M>
+__global__ void __launch_bounds__(kPT) pt_smooth(PL L, Coef c, int color) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)L.n0 * L.n1 * L.n2) return;
+  int i, j, k;
+  pdecode(t, L.n1, L.n2, i, j, k);
+  if (((i + j + k) & 1) != color || !unknown(L, t, i, j, k)) return;
+  double F, dF;
+  pt_eval<M>(c, L, i, j, k, true, F, dF);
+  L.u[t] -= F / dF;
+}
+
+// res = Sigma - L(u) at the unknowns, 0 elsewhere.
+template <Model M>
+__global__ void __launch_bounds__(kPT) pt_resid(PL L, Coef c, double* __restrict__ res) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)L.n0 * L.n1 * L.n2) return;
+  double r = 0.0;
+  int i, j, k;
+  pdecode(t, L.n1, L.n2, i, j, k);
+  if (unknown(L, t, i, j, k)) {
+    double F, dF;
+    pt_eval<M>(c, L, i, j, k, false, F, dF);
+    r = -F;
+  }
+  res[t] = r;
+}
+
+// Sigma_H = L_H(u_H) + R(res) at the coarse unknowns (the coarse level has sig == nullptr in L: its own
+// source is written to sig).
+template <Model M>
+__global__ void __launch_bounds__(kPT) pt_sigma(PL C, Coef c, const double* __restrict__ rf, double* __restrict__ sig) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)C.n0 * C.n1 * C.n2) return;
+  int I, J, K;
+  pdecode(t, C.n1, C.n2, I, J, K);
+  double s = 0.0;
+  if (unknown(C, t, I, J, K)) {
+    double F, dF;
+    pt_eval<M>(c, C, I, J, K, false, F, dF);  // C.sig == nullptr: F = L_H(u_H)
+    const int f1 = 2 * C.n1, f2 = 2 * C.n2;
+    double r = 0.0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const size_t q = pidx(f1, f2, 2 * I + a, 2 * J + b, 2 * K);
+        r += rf[q] + rf[q + 1];
+      }
+    s = F + 0.125 * r;
+  }
+  sig[t] = s;
+}
+
+// u += P(uc - uc0) at the fine unknowns; coarse cells outside the box contribute nothing.
+__global__ void __launch_bounds__(kPT) pt_prolong(PL L, const double* __restrict__ uc, const double* __restrict__ uc0,
+                                                  int c0, int c1, int c2) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)L.n0 * L.n1 * L.n2) return;
+  int f[3];
+  pdecode(t, L.n1, L.n2, f[0], f[1], f[2]);
+  if (!unknown(L, t, f[0], f[1], f[2])) return;
+  const int cd[3] = {c0, c1, c2};
+  int ci[3][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ci[a][0] = f[a] >> 1;
+    ci[a][1] = ci[a][0] + ((f[a] & 1) ? 1 : -1);
+  }
+  const double w[2] = {0.75, 0.25};
+  double v = 0.0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const int x = ci[0][a], y = ci[1][b], z = ci[2][d];
+        if (x < 0 || x >= cd[0] || y < 0 || y >= cd[1] || z < 0 || z >= cd[2]) continue;
+        const size_t q = pidx(c1, c2, x, y, z);
+        v += w[a] * w[b] * w[d] * (uc[q] - uc0[q]);
+      }
+  L.u[t] += v;
+}
+
+// The coarsest patch level: u^Pre = u, then kCoarseSweeps red/black sweeps, in one block.
+template <Model M>
+__global__ void __launch_bounds__(1024) pt_coarsest(PL L, Coef c, double* pre) {
+  const size_t n = (size_t)L.n0 * L.n1 * L.n2;
+  for (size_t t = threadIdx.x; t < n; t += blockDim.x) pre[t] = L.u[t];
+  __syncthreads();
+  for (int s = 0; s < kCoarseSweeps; ++s) {
+    for (int color = 0; color < 2; ++color) {
+      for (size_t t = threadIdx.x; t < n; t += blockDim.x) {
+        int i, j, k;
+        pdecode(t, L.n1, L.n2, i, j, k);
+        if (((i + j + k) & 1) != color || !unknown(L, t, i, j, k)) continue;
+        double F, dF;
+        pt_eval<M>(c, L, i, j, k, true, F, dF);
+        L.u[t] -= F / dF;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ void pt_block_sum(double v, double* out) {
+  __shared__ double red[kPT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < kPT / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+  }
+}
+
+// Block partial sums of (L(u) - Sigma)^2 over the unknowns (u^Pre = u).
+template <Model M>
+__global__ void __launch_bounds__(kPT) pt_norm(PL L, Coef c, double* __restrict__ part) {
+  const size_t n = (size_t)L.n0 * L.n1 * L.n2;
+  double acc = 0.0;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    pdecode(t, L.n1, L.n2, i, j, k);
+    if (!unknown(L, t, i, j, k)) continue;
+    double F, dF;
+    pt_eval<M>(c, L, i, j, k, false, F, dF);
+    acc += F * F;
+  }
+  pt_block_sum(acc, part);
+}
+
+// Block partial sums of (eta - eref)^2 over the unknowns.
+__global__ void __launch_bounds__(kPT) pt_ref(const double* __restrict__ m, const double* __restrict__ eta, size_t n,
+                                              double eref, double* __restrict__ part) {
+  double acc = 0.0;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    if (m[t] > 0.0) acc += (eta[t] - eref) * (eta[t] - eref);
+  pt_block_sum(acc, part);
+}
+
+inline unsigned nblk(size_t n) { return (unsigned)((n + kPT - 1) / kPT); }
+
+struct PLevel {
+  int n[3];
+  double h;
+  double *m, *eta, *u, *u0, *sig, *res, *pre;
+  size_t cells() const { return (size_t)n[0] * n[1] * n[2]; }
+  PL view(bool with_sig) const {
+    return PL{n[0], n[1], n[2], 1.0 / (h * h), m, eta, u, pre, with_sig ? sig : nullptr};
+  }
+};
+
+template <Model M>
+struct PatchSolver {
+  const PatchArgs& A;
+  std::vector<PLevel> lev;
+  double* part = nullptr;
+  double* host = nullptr;
+
+  explicit PatchSolver(const PatchArgs& a) : A(a) {}
+
+  // bytes a level-sweep kernel reads and writes once (u, m, eta, pre, sig; u written)
+  static double sweep_bytes(const PLevel& L) { return 48.0 * L.cells(); }
+
+  isis_status sum_parts(double* out) {
+    if (cudaMemcpyAsync(host, part, kPNormBlocks * sizeof(double), cudaMemcpyDeviceToHost, A.st) != cudaSuccess)
+      return ISIS_ECUDA;
+    if (cudaStreamSynchronize(A.st) != cudaSuccess) return ISIS_ECUDA;
+    double s = 0.0;
+    for (int b = 0; b < kPNormBlocks; ++b) s += host[b];
+    *out = s;
+    return ISIS_OK;
+  }
+
+  isis_status norm(double* rms) {
+    const PLevel& F = lev[0];
+    ISIS_LAUNCH(KK_PATCH_OTHER, sweep_bytes(F), A.st,
+                (pt_norm<M><<<kPNormBlocks, kPT, 0, A.st>>>(F.view(false), A.coef, part)));
+    double s = 0.0;
+    isis_status st = sum_parts(&s);
+    if (st != ISIS_OK) return st;
+    *rms = A.unknowns > 0 ? std::sqrt(s / (double)A.unknowns) : 0.0;
+    return ISIS_OK;
+  }
+
+  isis_status phase(size_t l, int nsweep) {
+    const PLevel& L = lev[l];
+    if (cudaMemcpyAsync(L.pre, L.u, L.cells() * sizeof(double), cudaMemcpyDeviceToDevice, A.st) != cudaSuccess)
+      return ISIS_ECUDA;
+    for (int s = 0; s < nsweep; ++s)
+      for (int color = 0; color < 2; ++color)
+        ISIS_LAUNCH(KK_PATCH_SMOOTH, 0.5 * sweep_bytes(L), A.st,
+                    (pt_smooth<M><<<nblk(L.cells()), kPT, 0, A.st>>>(L.view(l > 0), A.coef, color)));
+    return ISIS_OK;
+  }
+
+  isis_status vcycle(size_t l) {
+    const PLevel& L = lev[l];
+    if (l + 1 == lev.size()) {
+      ISIS_LAUNCH(KK_PATCH_SMOOTH, kCoarseSweeps * sweep_bytes(L), A.st,
+                  (pt_coarsest<M><<<1, 1024, 0, A.st>>>(L.view(l > 0), A.coef, L.pre)));
+      return ISIS_OK;
+    }
+    const PLevel& C = lev[l + 1];
+    isis_status st = phase(l, A.nu1);
+    if (st != ISIS_OK) return st;
+    ISIS_LAUNCH(KK_PATCH_OTHER, 48.0 * L.cells(), A.st,
+                (pt_resid<M><<<nblk(L.cells()), kPT, 0, A.st>>>(L.view(l > 0), A.coef, L.res)));
+    ISIS_LAUNCH(KK_PATCH_OTHER, 9.0 * C.cells() * 8.0, A.st,
+                (pt_restrict<<<nblk(C.cells()), kPT, 0, A.st>>>(L.u, C.u, C.n[0], C.n[1], C.n[2])));
+    if (cudaMemcpyAsync(C.u0, C.u, C.cells() * sizeof(double), cudaMemcpyDeviceToDevice, A.st) != cudaSuccess)
+      return ISIS_ECUDA;
+    ISIS_LAUNCH(KK_PATCH_OTHER, 48.0 * C.cells() + 64.0 * C.cells(), A.st,
+                (pt_sigma<M><<<nblk(C.cells()), kPT, 0, A.st>>>(C.view(false), A.coef, L.res, C.sig)));
+    st = vcycle(l + 1);
+    if (st != ISIS_OK) return st;
+    ISIS_LAUNCH(KK_PATCH_OTHER, 24.0 * L.cells() + 16.0 * C.cells(), A.st,
+                (pt_prolong<<<nblk(L.cells()), kPT, 0, A.st>>>(L.view(l > 0), C.u, C.u0, C.n[0], C.n[1], C.n[2])));
+    return phase(l, A.nu2);
+  }
+
+  isis_status setup() {
+    const PLevel& F = lev[0];
+    ISIS_LAUNCH(KK_PATCH_OTHER, 9.0 * F.cells(), A.st,
+                (pt_mask0<<<nblk(F.cells()), kPT, 0, A.st>>>(A.flags, A.n[1], A.n[2], F.m, F.n[0], F.n[1], F.n[2])));
+    for (size_t l = 1; l < lev.size(); ++l) {
+      const PLevel& C = lev[l];
+      const PLevel& L = lev[l - 1];
+      ISIS_LAUNCH(KK_PATCH_OTHER, 9.0 * C.cells() * 8.0, A.st,
+                  (pt_restrict<<<nblk(C.cells()), kPT, 0, A.st>>>(L.m, C.m, C.n[0], C.n[1], C.n[2], 1)));
+      ISIS_LAUNCH(KK_PATCH_OTHER, 9.0 * C.cells() * 8.0, A.st,
+                  (pt_restrict<<<nblk(C.cells()), kPT, 0, A.st>>>(L.eta, C.eta, C.n[0], C.n[1], C.n[2])));
+    }
+    ISIS_LAUNCH(KK_PATCH_OTHER, 16.0 * F.cells(), A.st,
+                (pt_interp<<<nblk(F.cells()), kPT, 0, A.st>>>(A.parent, A.pn[0], A.pn[1], A.pn[2], A.origin[0],
+                                                              A.origin[1], A.origin[2], A.periodic, F.m, F.u,
+                                                              F.n[0], F.n[1], F.n[2], A.init_parent)));
+    return ISIS_OK;
+  }
+
+  isis_status run() {
+    isis_solve_info info;
+    std::memset(&info, 0, sizeof(info));
+    isis_status st = setup();
+    if (st != ISIS_OK) return st;
+    {
+      const PLevel& F = lev[0];
+      ISIS_LAUNCH(KK_PATCH_OTHER, 17.0 * F.cells(), A.st,
+                  (pt_ref<<<kPNormBlocks, kPT, 0, A.st>>>(F.m, F.eta, F.cells(), A.eref, part)));
+      double s = 0.0;
+      st = sum_parts(&s);
+      if (st != ISIS_OK) return st;
+      info.res_ref = A.unknowns > 0 ? A.ref_scale * std::sqrt(s / (double)A.unknowns) : 0.0;
+    }
+    double res = 0.0;
+    st = norm(&res);
+    if (st != ISIS_OK) return st;
+    info.res0 = res;
+    if (!(info.res_ref > 0.0)) info.res_ref = res;
+    info.res_final = res;
+    if (A.unknowns == 0 || res <= A.tol * info.res_ref) {
+      st = ISIS_OK;
+    } else if (!std::isfinite(res)) {
+      st = ISIS_ENAN;
+    } else {
+      st = ISIS_ENOCONV;
+      for (int cyc = 0; cyc < A.max_cycles; ++cyc) {
+        isis_status vs = vcycle(0);
+        if (vs != ISIS_OK) return vs;
+        vs = norm(&res);
+        if (vs != ISIS_OK) return vs;
+        if (cyc < 128) info.hist[cyc] = res;
+        info.nhist = cyc + 1 < 128 ? cyc + 1 : 128;
+        info.cycles = cyc + 1;
+        info.res_final = res;
+        if (!std::isfinite(res)) { st = ISIS_ENAN; break; }
+        if (res <= A.tol * info.res_ref) { st = ISIS_OK; break; }
+      }
+    }
+    if (A.info) *A.info = info;
+    return st;
+  }
+};
+
+template <Model M>
+isis_status patch_solve(const PatchArgs& A) {
+  PatchSolver<M> S(A);
+  // level dimensions
+  int n[3] = {2 * A.n[0], 2 * A.n[1], 2 * A.n[2]};
+  double h = A.h;
+  size_t total = 0;
+  for (int l = 0;; ++l) {
+    PLevel L;
+    std::memcpy(L.n, n, sizeof(n));
+    L.h = h;
+    S.lev.push_back(L);
+    total += L.cells() * (l == 0 ? 4 : 7);
+    const int mn = std::min(n[0], std::min(n[1], n[2]));
+    if ((n[0] & 1) || (n[1] & 1) || (n[2] & 1) || mn < 8 || l == 15) break;
+    n[0] /= 2;
+    n[1] /= 2;
+    n[2] /= 2;
+    h *= 2.0;
+  }
+  total += kPNormBlocks;
+  double* mem = nullptr;
+  if (cudaMallocAsync((void**)&mem, total * sizeof(double), A.st) != cudaSuccess) {
+    cudaGetLastError();
+    return ISIS_ENOMEM;
+  }
+  double* p = mem;
+  for (size_t l = 0; l < S.lev.size(); ++l) {
+    PLevel& L = S.lev[l];
+    const size_t c = L.cells();
+    L.m = p; p += c;
+    L.u0 = p; p += c;
+    L.res = p; p += c;
+    L.pre = p; p += c;
+    if (l == 0) {
+      L.eta = const_cast<double*>(A.eta);
+      L.u = A.phi;
+      L.sig = nullptr;  // the finest level's Sigma is 0
+    } else {
+      L.eta = p; p += c;
+      L.u = p; p += c;
+      L.sig = p; p += c;
+    }
+  }
+  S.part = p;
+  isis_status st = ISIS_OK;
+  if (cudaMallocHost((void**)&S.host, kPNormBlocks * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    st = ISIS_ENOMEM;
+  }
+  if (st == ISIS_OK) st = S.run();
+  cudaFreeAsync(mem, A.st);
+  if (S.host) {
+    cudaStreamSynchronize(A.st);
+    cudaFreeHost(S.host);
+  }
+  if (st == ISIS_ECUDA) cudaGetLastError();
+  return st;
+}
+
+}  // namespace
+
+isis_status run_patch_poi(const PatchArgs& A) { return patch_solve<POI>(A); }
+isis_status run_patch_sym(const PatchArgs& A) { return patch_solve<SYM>(A); }
+isis_status run_patch_fofr(const PatchArgs& A) { return patch_solve<FOFR>(A); }
+
+}  // namespace isis

@@ -28,6 +28,8 @@ enum KernelKind : int {
   KK_FORCE,
   KK_UNET_CONV,         // tcgen05 convolutions of the learned guess (bytes field: FLOPs)
   KK_UNET_ELEM,         // its element-wise kernels
+  KK_PATCH_SMOOTH,      // smoother on a refinement patch
+  KK_PATCH_OTHER,       // the patch's residual, transfers, interpolation and norms
   KK_COUNT
 };
 

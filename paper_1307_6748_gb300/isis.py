@@ -26,8 +26,9 @@ H0_MPC = 1.0 / 2997.92458  # (Mpc/h)^-1 with c = 1
 # Every function the header declares (checked by the tests).
 EXPORTS = ("isis_cic_deposit", "isis_cic_deposit_noalloc", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force",
            "isis_strerror", "isis_release_workspace", "isis_prof_enable", "isis_prof_reset", "isis_prof_read",
-           "isis_launch_count", "isis_selftest_exp_ff", "isis_kick_drift")
-ISIS_INIT_INPUT, ISIS_INIT_BACKGROUND, ISIS_INIT_LOCAL = 0, 1, 2
+           "isis_launch_count", "isis_selftest_exp_ff", "isis_kick_drift", "isis_patch_poisson_solve",
+           "isis_patch_scalar_solve")
+ISIS_INIT_INPUT, ISIS_INIT_BACKGROUND, ISIS_INIT_LOCAL, ISIS_INIT_PARENT = 0, 1, 2, 3
 
 
 class isis_grid(ctypes.Structure):
@@ -44,6 +45,11 @@ class isis_mg_opts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("n_coarsest", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("prec", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("init", ctypes.c_int)]
+
+
+class isis_patch(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("origin", ctypes.c_int * 3), ("parent_dims", ctypes.c_int * 3),
+                ("parent_periodic", ctypes.c_int), ("level", ctypes.c_int), ("eta_mean", ctypes.c_double)]
 
 
 class isis_prof_entry(ctypes.Structure):
@@ -88,6 +94,13 @@ def load(path: str = LIB_PATH):
     lib.isis_kick_drift.argtypes = [P(isis_grid), f_p, f_p, f_p, f_p, f_p, f_p, f_p, f_p, f_p, ctypes.c_int64,
                                     ctypes.c_double, ctypes.c_double, vp]
     lib.isis_kick_drift.restype = ctypes.c_int
+    lib.isis_patch_poisson_solve.argtypes = [P(isis_grid), ctypes.c_double, P(isis_patch), vp, vp, vp, vp,
+                                             ctypes.c_double, P(isis_mg_opts), P(isis_solve_info), vp]
+    lib.isis_patch_scalar_solve.argtypes = [ctypes.c_int, P(isis_params), P(isis_grid), ctypes.c_double,
+                                            P(isis_patch), vp, vp, vp, vp, ctypes.c_double, P(isis_mg_opts),
+                                            P(isis_solve_info), vp]
+    lib.isis_patch_poisson_solve.restype = ctypes.c_int
+    lib.isis_patch_scalar_solve.restype = ctypes.c_int
     lib.isis_strerror.argtypes = [ctypes.c_int]
     lib.isis_strerror.restype = ctypes.c_char_p
     lib.isis_release_workspace.argtypes = []
@@ -147,6 +160,27 @@ class Opts:
     def c(self):
         return isis_mg_opts(self.nu1, self.nu2, self.n_coarsest, self.max_cycles, self.prec, self.inner_cycles,
                             self.init)
+
+
+@dataclass
+class Patch:
+    """A refinement patch: n parent cells at origin of a parent grid of dims parent_dims (periodic: the domain
+    grid, level 1), refined by two; eta_mean is the domain's mean density (Poisson)."""
+    n: tuple
+    origin: tuple
+    parent_dims: tuple
+    periodic: bool
+    level: int = 1
+    eta_mean: float = 1.0
+
+    def c(self):
+        return isis_patch((ctypes.c_int * 3)(*self.n), (ctypes.c_int * 3)(*self.origin),
+                          (ctypes.c_int * 3)(*self.parent_dims), 1 if self.periodic else 0, self.level,
+                          self.eta_mean)
+
+    @property
+    def fine_shape(self):
+        return tuple(2 * v for v in self.n)
 
 
 @dataclass
@@ -357,3 +391,32 @@ def selftest_exp_ff(x: torch.Tensor) -> torch.Tensor:
     if st != 0:
         raise IsisError(st, strerror(st))
     return y
+
+
+def isis_patch_poisson_solve(grid: Grid, a: float, patch: Patch, parent: torch.Tensor, flags: torch.Tensor,
+                             eta: torch.Tensor, Phi: torch.Tensor, tol: float = 1e-10, opts: Opts | None = None,
+                             stream=None, allow_noconv: bool = False) -> Info:
+    """Newtonian potential on a refinement patch (float64 tensors; flags uint8 of patch.n)."""
+    lib = load()
+    o = opts or Opts()
+    g, b, oc, info = grid.c(), patch.c(), o.c(), isis_solve_info()
+    st = lib.isis_patch_poisson_solve(ctypes.byref(g), a, ctypes.byref(b), _ptr(parent, torch.float64),
+                                      _ptr(flags, torch.uint8), _ptr(eta, torch.float64), _ptr(Phi, torch.float64),
+                                      tol, ctypes.byref(oc), ctypes.byref(info), _stream(stream))
+    _check(st, "isis_patch_poisson_solve", (ISIS_OK, ISIS_ENOCONV) if allow_noconv else (ISIS_OK,))
+    return _info(info, st, o.prec)
+
+
+def isis_patch_scalar_solve(model: int, params: Params, grid: Grid, a: float, patch: Patch, parent: torch.Tensor,
+                            flags: torch.Tensor, eta: torch.Tensor, phi: torch.Tensor, tol: float = 1e-10,
+                            opts: Opts | None = None, stream=None, allow_noconv: bool = False) -> Info:
+    """Symmetron or f(R) field on a refinement patch (float64 tensors; flags uint8 of patch.n)."""
+    lib = load()
+    o = opts or Opts()
+    g, p, b, oc, info = grid.c(), params.c(), patch.c(), o.c(), isis_solve_info()
+    st = lib.isis_patch_scalar_solve(int(model), ctypes.byref(p), ctypes.byref(g), a, ctypes.byref(b),
+                                     _ptr(parent, torch.float64), _ptr(flags, torch.uint8), _ptr(eta, torch.float64),
+                                     _ptr(phi, torch.float64), tol, ctypes.byref(oc), ctypes.byref(info),
+                                     _stream(stream))
+    _check(st, "isis_patch_scalar_solve", (ISIS_OK, ISIS_ENOCONV) if allow_noconv else (ISIS_OK,))
+    return _info(info, st, o.prec)
