@@ -6,8 +6,10 @@ solver and its radial profile binned, the data of the paper's Fig. of the static
 Sect. 5.1: delta = 5000; symmetron R = 3, B = 40 Mpc/h, lambda0 = 1 Mpc/h, a_SSB = 0.6 at z = 0 and 1;
 f(R) R = 5, B = 100 Mpc/h, n = 1, |f_R0| = 1e-6 at z = 0.
 
-python -m paper_1307_6748_gb300.sphere [--N 128] [--prec f64|refine] [--profile-dir DIR]
+python -m paper_1307_6748_gb300.sphere [--N 128] [--prec f64|refine] [--levels 0] [--expand 4]
+                                       [--profile-dir DIR]
 prints one JSON line per case (solve time from CUDA events after one untimed solve, cycles, residuals);
+--levels L adds L refinement levels (amr.refine, FP64) on the domain solution and times each;
 with --profile-dir, writes r, mean, min, max of the field (chi, or f_R = -e^u / a^2) per radial bin.
 """
 from __future__ import annotations
@@ -17,7 +19,7 @@ import math
 import numpy as np
 import torch
 
-from . import isis, synth
+from . import amr, isis, synth
 
 CASES = {
     "symmetron_z0": dict(model="symmetron", z=0.0, delta=5000.0, R=3.0, B=40.0, params=dict(lambda0=1.0, a_ssb=0.6)),
@@ -89,6 +91,8 @@ def main():
     ap.add_argument("--prec", default="refine", choices=["f64", "refine"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--cases", default=",".join(CASES))
+    ap.add_argument("--levels", type=int, default=0)
+    ap.add_argument("--expand", type=int, default=4)
     ap.add_argument("--profile-dir", default=None)
     args = ap.parse_args()
     isis.load()
@@ -105,6 +109,34 @@ def main():
         print(json.dumps({"case": name, "N": args.N, "prec": args.prec, "ms": round(e0.elapsed_time(e1), 3),
                           "cycles": info.cycles, "outer": info.outer, "res_final_over_ref":
                           info.res_final / info.res_ref}), flush=True)
+        if args.levels > 0:
+            a = 1.0 / (1.0 + case["z"])
+            model = isis.ISIS_SYMMETRON if case["model"] == "symmetron" else isis.ISIS_FOFR_HS
+
+            def dens(dims, corner, h, case=case):
+                return synth.sphere_eta_box(dims, corner, h, case["B"], case["R"], case["delta"])
+
+            run = lambda: amr.refine(model, isis.Params(**case["params"]), isis.Grid(args.N, case["B"]), a,
+                                     eta.cpu().numpy(), phi, dens, levels=args.levels, expand=args.expand,
+                                     tol=args.tol)
+            run()  # untimed: the flags, boxes and patch densities on the host, then the solves
+            # time each level's solve alone, on its own inputs
+            levels = run()
+            for lv in levels:
+                phi_l = torch.empty_like(lv.phi)
+                opts = isis.Opts(max_cycles=100, init=isis.ISIS_INIT_PARENT)
+                parent = phi if lv.level == 1 else levels[lv.level - 2].phi
+                torch.cuda.synchronize()
+                e0.record()
+                info = isis.isis_patch_scalar_solve(model, isis.Params(**case["params"]),
+                                                    isis.Grid(args.N, case["B"]), a, lv.patch, parent, lv.flags,
+                                                    lv.eta, phi_l, tol=args.tol, opts=opts)
+                e1.record()
+                torch.cuda.synchronize()
+                print(json.dumps({"case": name, "level": lv.level, "box": list(lv.patch.n),
+                                  "fine_cells": int(lv.phi.numel()), "unknowns": int(lv.unknowns.sum()),
+                                  "ms": round(e0.elapsed_time(e1), 3), "cycles": info.cycles,
+                                  "res_final_over_ref": info.res_final / info.res_ref}), flush=True)
         if args.profile_dir:
             os.makedirs(args.profile_dir, exist_ok=True)
             rows = radial_profile(case, phi, args.N)

@@ -18,6 +18,12 @@ Recipes
                    per-component rms displacement (default 0.5 cell).
   sphere_eta       the paper's static test density (Sect. 5.1): a uniform sphere
                    of radius R and contrast delta in a box B, cell-averaged.
+  sphere_eta_box   the same density on a box of cells of any size h (a patch).
+  refine_flags     the cells of a level to refine: mass per cell at least m_ref
+                   mean-density domain cells (RAMSES's quasi-Lagrangian rule with
+                   one particle per domain cell), dilated by `expand` cells.
+  patch_box        the box of parent cells of a patch: the flags' bounding box
+                   widened by a margin and rounded to a multiple of 4 cells.
 """
 from __future__ import annotations
 
@@ -160,6 +166,79 @@ def sphere_eta(N: int, B: float, R: float, delta: float, sub: int = 4) -> torch.
     rho_out = 1.0 / (1.0 + 4.0 * math.pi / 3.0 * delta * (R / B) ** 3)
     eta = rho_out * (1.0 + delta * frac)
     return torch.from_numpy(eta)
+
+
+def sphere_eta_box(dims, corner, h: float, B: float, R: float, delta: float, sub: int = 4) -> np.ndarray:
+    """Cell average of the Sect. 5.1 sphere (centre B/2 on each axis) on a box of dims cells of size h whose
+    first cell's lower corner sits at `corner` (Mpc/h, per axis)."""
+    s = (np.arange(sub) + 0.5) / sub
+    ax = [((np.arange(dims[a])[:, None] + s[None, :]) * h + corner[a] - B / 2) ** 2 for a in range(3)]
+    inside = np.zeros(tuple(dims))
+    for a in range(sub):
+        for b in range(sub):
+            for c in range(sub):
+                rr = ax[0][:, a][:, None, None] + ax[1][:, b][None, :, None] + ax[2][:, c][None, None, :]
+                inside += (rr < R * R)
+    rho_out = 1.0 / (1.0 + 4.0 * math.pi / 3.0 * delta * (R / B) ** 3)
+    return rho_out * (1.0 + delta * inside / sub ** 3)
+
+
+def refine_flags(eta: np.ndarray, level: int, m_ref: float = 8.0, expand: int = 1, periodic: bool = False,
+                 within: np.ndarray | None = None) -> np.ndarray:
+    """Bool flags of the cells of refinement level `level` - 1 (cell volume 8^-(level-1) of a domain cell) that
+    level `level` refines: eta 8^-(level-1) >= m_ref, dilated by `expand` cells (26-neighbourhood), and kept
+    inside `within` (the parent level's refined cells) when given."""
+    f = eta * 8.0 ** (-(level - 1)) >= m_ref
+    for _ in range(expand):
+        g = f.copy()
+        for ax in range(3):
+            for sh in (-1, 1):
+                if periodic:
+                    g |= np.roll(f, sh, axis=ax)
+                else:
+                    r = np.zeros_like(f)
+                    src = [slice(None)] * 3
+                    dst = [slice(None)] * 3
+                    src[ax] = slice(0, -1) if sh == 1 else slice(1, None)
+                    dst[ax] = slice(1, None) if sh == 1 else slice(0, -1)
+                    r[tuple(dst)] = f[tuple(src)]
+                    g |= r
+        f = g
+    if within is not None:
+        f &= within
+    return f
+
+
+def patch_box(flags: np.ndarray, margin: int = 1, multiple: int = 4, periodic: bool = False):
+    """(origin, n) of the box of parent cells holding every flag with `margin` unflagged cells round it, n
+    rounded up to a multiple of `multiple`; None without flags.  A non-periodic parent keeps one more cell
+    outside the box on each side (the interpolation's stencil); a periodic box may wrap."""
+    idx = np.argwhere(flags)
+    if len(idx) == 0:
+        return None
+    pn = flags.shape
+    origin, n = [], []
+    for a in range(3):
+        lo, hi = int(idx[:, a].min()) - margin, int(idx[:, a].max()) + margin + 1
+        size = -(-(hi - lo) // multiple) * multiple
+        lo -= (size - (hi - lo)) // 2
+        if not periodic:
+            lo = max(1, min(lo, pn[a] - 1 - size))
+            if lo < 1:
+                raise ValueError("the flagged region does not fit inside its parent")
+        elif size > pn[a]:
+            raise ValueError("the flagged region is wider than the domain")
+        origin.append(lo % pn[a] if periodic else lo)
+        n.append(size)
+    return tuple(origin), tuple(n)
+
+
+def box_flags(flags: np.ndarray, origin, n, periodic: bool) -> np.ndarray:
+    """The flags of a box's parent cells (uint8, n dims; a periodic box wraps)."""
+    pn = flags.shape
+    ix = [np.arange(origin[a], origin[a] + n[a]) % pn[a] if periodic else np.arange(origin[a], origin[a] + n[a])
+          for a in range(3)]
+    return np.ascontiguousarray(flags[np.ix_(*ix)].astype(np.uint8))
 
 
 def sinusoid(N: int, m: int = 1, amp: float = 1.0, axis: int = 0) -> torch.Tensor:

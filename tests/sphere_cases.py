@@ -136,3 +136,76 @@ def check_tol(name, errs):
 def check_ratio(name, coarse, fine):
     for k in ("near", "mid", "far"):
         assert fine[k][1] <= RATIO[name] * coarse[k][1], (name, k, coarse[k][1], fine[k][1])
+
+
+# ---- refinement levels (Sects. 3.3.1, 3.4.1): the sphere with two levels on the 128^3 domain ----
+
+EXPAND = 4  # refined region: the quasi-Lagrangian flags (8 domain-cell masses) dilated by 4 cells per level
+LEVEL_BANDS = dict(core=(0.0, 0.5), shell=(0.9, 1.1), near=(1.1, 1.5))  # in units of R
+
+
+def patch_density(name):
+    c = cases()[name]
+    return lambda dims, corner, h: synth.sphere_eta_box(dims, corner, h, c["B"], c["R"], c["delta"])
+
+
+def oracle_levels(name, N=128, levels=2, tol=1e-10):
+    """The oracle's level-by-level solve: domain, then each patch on its parent's field.
+    Returns [(phi, corner, h, unknowns or None)] for the domain and each level."""
+    c = cases()[name]
+    B = c["B"]
+    eta0 = eta_3d(name, N)
+    r0 = oracle.solve(problem(name, N), eta0, guess_3d(name, eta0), tol=tol)
+    assert r0.status == oracle.OK
+    out = [(r0.phi, (0.0, 0.0, 0.0), B / N, None)]
+    parent, peta, pdims, corner, within = r0.phi, eta0, (N, N, N), (0.0, 0.0, 0.0), None
+    dens = patch_density(name)
+    for lev in range(1, levels + 1):
+        periodic = lev == 1
+        f = synth.refine_flags(peta, lev, expand=EXPAND, periodic=periodic, within=within)
+        o, n = synth.patch_box(f, periodic=periodic)
+        hp = B / (N * 2 ** (lev - 1))
+        flags = synth.box_flags(f, o, n, periodic)
+        nf = tuple(2 * v for v in n)
+        fc = tuple(corner[a] + o[a] * hp for a in range(3))
+        eta_f = dens(nf, fc, hp / 2)
+        patch = oracle.Patch(n, o, pdims, periodic, level=lev, eta_mean=float(eta0.mean()))
+        rp = oracle.patch_solve(problem(name, N), patch, parent, flags, eta_f, tol=tol, max_cycles=100)
+        assert rp.status == oracle.OK
+        unk = np.repeat(np.repeat(np.repeat(flags, 2, 0), 2, 1), 2, 2) > 0
+        out.append((rp.phi, fc, hp / 2, unk))
+        parent, peta, pdims, corner, within = rp.phi, eta_f, nf, fc, unk
+    return out
+
+
+def level_errors(name, phi, corner, h, unknowns):
+    """band -> max error against the 1D profile over the level's unknowns (all cells for the domain)."""
+    c = cases()[name]
+    R = c["R"]
+    dims = phi.shape
+    xs = [corner[a] + (np.arange(dims[a]) + 0.5) * h - c["B"] / 2 for a in range(3)]
+    r = np.sqrt(xs[0][:, None, None] ** 2 + xs[1][None, :, None] ** 2 + xs[2][None, None, :] ** 2)
+    r1, p1 = reference_1d(name)
+    ref = np.interp(r, r1, p1)
+    if c["model"] == oracle.SYMMETRON:
+        err = np.abs(phi - ref)
+    else:
+        err = np.abs(np.exp(phi) - np.exp(ref)) / math.exp(far_value(c))
+    sel = np.ones(dims, bool) if unknowns is None else unknowns
+    out = {}
+    for k, (lo, hi) in LEVEL_BANDS.items():
+        m = sel & (r >= lo * R) & (r < hi * R)
+        out[k] = float(err[m].max()) if m.any() else None
+    return out
+
+
+def check_levels(name, errs):
+    """The paper's test: the refined levels follow the 1D solution more closely than the domain grid.
+    Shell band: each level below its parent, the second at most half the domain's; near band: the second
+    level at most 0.6 of the domain's; symmetron core: at most 0.2 of the domain's."""
+    d, l1, l2 = errs
+    assert l2["shell"] < l1["shell"] < d["shell"], (name, d, l1, l2)
+    assert l2["shell"] <= 0.5 * d["shell"], (name, d, l2)
+    assert l2["near"] <= 0.6 * d["near"], (name, d, l2)
+    if cases()[name]["model"] == oracle.SYMMETRON:
+        assert l2["core"] <= 0.2 * d["core"], (name, d, l2)

@@ -30,3 +30,11 @@ def test_sphere_cases_match_the_golden_table():
     assert abs(SC.far_value(c["symmetron_z0"]) - 0.988959) < 1e-6
     assert abs(SC.far_value(c["symmetron_z1"]) - 0.907917) < 1e-6
     assert abs(math.exp(SC.far_value(c["fofr_z0"])) / 1.13268e-6 - 1.0) < 1e-5  # |f_R| far, a = 1
+
+
+@pytest.mark.parametrize("name", sorted(SC.TOL_128))
+def test_oracle_sphere_refinement_levels(name):
+    """Two refinement levels over the 128^3 domain (the paper's set-up of Sect. 5.1): closer to the 1D profile."""
+    levels = SC.oracle_levels(name)
+    assert len(levels) == 3
+    SC.check_levels(name, [SC.level_errors(name, *lv) for lv in levels])

@@ -66,3 +66,33 @@ def test_sphere_256_error_falls(cuda_lib, name):
     e256 = SC.band_errors(name, got, 256)
     SC.check_tol(name, e256)
     SC.check_ratio(name, e128, e256)
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_levels(name):
+    return SC.oracle_levels(name)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_sphere_refinement_levels(cuda_lib, name):
+    """The level-by-level solve through amr.refine: each level equals the oracle's (max-abs 1e-10), and the
+    levels follow the 1D profile more closely than the domain grid."""
+    isis = cuda_lib
+    from paper_1307_6748_gb300 import amr
+    c = SC.cases()[name]
+    ref = _oracle_levels(name)
+    eta0 = SC.eta_3d(name, 128)
+    dom = _gpu_solve(isis, name, 128, isis.ISIS_F64, 1e-10)
+    assert np.abs(dom - ref[0][0]).max() <= 1e-10
+    model = isis.ISIS_SYMMETRON if c["model"] == oracle.SYMMETRON else isis.ISIS_FOFR_HS
+    levels = amr.refine(model, isis.Params(**c["params"]), isis.Grid(128, c["B"]), c["a"], eta0,
+                        torch.from_numpy(dom).cuda(), SC.patch_density(name), levels=2, expand=SC.EXPAND, tol=1e-10)
+    assert len(levels) == 2
+    errs = [SC.level_errors(name, dom, (0.0, 0.0, 0.0), c["B"] / 128, None)]
+    for lv, (phi_o, corner_o, h_o, unk_o) in zip(levels, ref[1:]):
+        got = lv.phi.cpu().numpy()
+        assert lv.info.status == isis.ISIS_OK and lv.h == h_o and np.allclose(lv.corner, corner_o)
+        assert np.array_equal(lv.unknowns, unk_o)
+        assert np.abs(got - phi_o).max() <= 1e-10 * max(1.0, np.abs(phi_o).max())
+        errs.append(SC.level_errors(name, got, lv.corner, lv.h, lv.unknowns))
+    SC.check_levels(name, errs)
