@@ -17,7 +17,10 @@ namespace {
 
 constexpr int kPT = 256;          // threads per block of the cell kernels
 constexpr int kPNormBlocks = 256;  // blocks of the norm kernels
-constexpr int kCoarseSweeps = 64;  // red/black sweeps on the coarsest patch level
+constexpr int kCoarseSweeps = 16;  // red/black sweeps on the coarsest patch level
+constexpr int kCoarseThreads = 256;
+constexpr size_t kCoarseSmem = 220 * 1024;  // the coarsest level in shared memory up to this many bytes
+constexpr size_t kCoarseBytesPerCell = 5 * sizeof(double) + sizeof(int);
 
 struct PL {  // one level of the patch
   int n0, n1, n2;
@@ -150,19 +153,6 @@ __global__ void pt_interp(const double* __restrict__ parent, int p0, int p1, int
   u[t] = v;
 }
 
-// One colour of a Newton-Gauss-Seidel sweep over the unknowns.
-template <Model M>
-__global__ void __launch_bounds__(kPT) pt_smooth(PL L, Coef c, int color) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)L.n0 * L.n1 * L.n2) return;
-  int i, j, k;
-  pdecode(t, L.n1, L.n2, i, j, k);
-  if (((i + j + k) & 1) != color || !unknown(L, t, i, j, k)) return;
-  double F, dF;
-  pt_eval<M>(c, L, i, j, k, true, F, dF);
-  L.u[t] -= F / dF;
-}
-
 // res = Sigma - L(u) at the unknowns, 0 elsewhere.
 template <Model M>
 __global__ void __launch_bounds__(kPT) pt_resid(PL L, Coef c, double* __restrict__ res) {
@@ -236,6 +226,78 @@ __global__ void __launch_bounds__(kPT) pt_prolong(PL L, const double* __restrict
   L.u[t] += v;
 }
 
+// The coarsest patch level held in shared memory (u, u^Pre, m, eta, Sigma of every cell, and the unknowns
+// of each colour as lists): u^Pre = u, then kCoarseSweeps red/black sweeps, in one block; u written back.
+// GB300's FP64 units are few and this is one block, so each half-sweep costs its latency: shared memory
+// and the lists keep that short.
+template <Model M>
+__global__ void __launch_bounds__(kCoarseThreads) pt_coarsest_smem(PL L, Coef c) {
+  extern __shared__ double sh[];
+  __shared__ int cnt[2];
+  const int n = L.n0 * L.n1 * L.n2;
+  double *su = sh, *spre = sh + n, *sm = sh + 2 * n, *seta = sh + 3 * n, *ssig = sh + 4 * n;
+  int* lst = reinterpret_cast<int*>(sh + 5 * n);  // red unknowns from the front, black from the back
+  if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    su[t] = L.u[t];
+    spre[t] = su[t];
+    sm[t] = L.m[t];
+    seta[t] = L.eta[t];
+    ssig[t] = L.sig ? L.sig[t] : 0.0;
+  }
+  __syncthreads();
+  PL S{L.n0, L.n1, L.n2, L.ih2, sm, seta, su, spre, ssig};
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int k = t % S.n2, j = (t / S.n2) % S.n1, i = t / (S.n1 * S.n2);
+    if (!unknown(S, t, i, j, k)) continue;
+    const int color = (i + j + k) & 1;
+    const int pos = atomicAdd(&cnt[color], 1);
+    lst[color ? n - 1 - pos : pos] = t;
+  }
+  __syncthreads();
+  for (int s = 0; s < kCoarseSweeps; ++s) {
+    for (int color = 0; color < 2; ++color) {
+      for (int q = threadIdx.x; q < cnt[color]; q += blockDim.x) {
+        const int t = lst[color ? n - 1 - q : q];
+        const int k = t % S.n2, j = (t / S.n2) % S.n1, i = t / (S.n1 * S.n2);
+        double F, dF;
+        pt_eval<M>(c, S, i, j, k, true, F, dF);
+        su[t] -= F / dF;
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < n; t += blockDim.x) L.u[t] = su[t];
+}
+
+// One colour of a sweep over a list of that colour's unknowns.
+template <Model M>
+__global__ void __launch_bounds__(kPT) pt_smooth_list(PL L, Coef c, const int* __restrict__ list, int count) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const size_t t = (size_t)list[q];
+  int i, j, k;
+  pdecode(t, L.n1, L.n2, i, j, k);
+  if (!unknown(L, t, i, j, k)) return;
+  double F, dF;
+  pt_eval<M>(c, L, i, j, k, true, F, dF);
+  L.u[t] -= F / dF;
+}
+
+// The unknowns of each colour, as lists of cell indices (in any order: cells of one colour do not read one
+// another, so the order does not change a sweep's result).
+__global__ void __launch_bounds__(kPT) pt_compact(PL L, int* __restrict__ red, int* __restrict__ black,
+                                                  int* __restrict__ counts) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)L.n0 * L.n1 * L.n2) return;
+  int i, j, k;
+  pdecode(t, L.n1, L.n2, i, j, k);
+  if (!unknown(L, t, i, j, k)) return;
+  const int color = (i + j + k) & 1;
+  const int pos = atomicAdd(&counts[color], 1);
+  (color ? black : red)[pos] = (int)t;
+}
+
 // The coarsest patch level: u^Pre = u, then kCoarseSweeps red/black sweeps, in one block.
 template <Model M>
 __global__ void __launch_bounds__(1024) pt_coarsest(PL L, Coef c, double* pre) {
@@ -302,6 +364,8 @@ struct PLevel {
   int n[3];
   double h;
   double *m, *eta, *u, *u0, *sig, *res, *pre;
+  int* list[2];  // unknowns of each colour
+  int count[2];
   size_t cells() const { return (size_t)n[0] * n[1] * n[2]; }
   PL view(bool with_sig) const {
     return PL{n[0], n[1], n[2], 1.0 / (h * h), m, eta, u, pre, with_sig ? sig : nullptr};
@@ -314,6 +378,7 @@ struct PatchSolver {
   std::vector<PLevel> lev;
   double* part = nullptr;
   double* host = nullptr;
+  int* counts = nullptr;
 
   explicit PatchSolver(const PatchArgs& a) : A(a) {}
 
@@ -346,17 +411,26 @@ struct PatchSolver {
     if (cudaMemcpyAsync(L.pre, L.u, L.cells() * sizeof(double), cudaMemcpyDeviceToDevice, A.st) != cudaSuccess)
       return ISIS_ECUDA;
     for (int s = 0; s < nsweep; ++s)
-      for (int color = 0; color < 2; ++color)
-        ISIS_LAUNCH(KK_PATCH_SMOOTH, 0.5 * sweep_bytes(L), A.st,
-                    (pt_smooth<M><<<nblk(L.cells()), kPT, 0, A.st>>>(L.view(l > 0), A.coef, color)));
+      for (int color = 0; color < 2; ++color) {
+        if (L.count[color] == 0) continue;
+        ISIS_LAUNCH(KK_PATCH_SMOOTH, 48.0 * L.count[color], A.st,
+                    (pt_smooth_list<M><<<nblk(L.count[color]), kPT, 0, A.st>>>(L.view(l > 0), A.coef,
+                                                                               L.list[color], L.count[color])));
+      }
     return ISIS_OK;
   }
 
   isis_status vcycle(size_t l) {
     const PLevel& L = lev[l];
     if (l + 1 == lev.size()) {
-      ISIS_LAUNCH(KK_PATCH_SMOOTH, kCoarseSweeps * sweep_bytes(L), A.st,
-                  (pt_coarsest<M><<<1, 1024, 0, A.st>>>(L.view(l > 0), A.coef, L.pre)));
+      const size_t smem = kCoarseBytesPerCell * L.cells();
+      if (smem <= kCoarseSmem) {
+        ISIS_LAUNCH(KK_PATCH_COARSEST, 40.0 * L.cells(), A.st,
+                    (pt_coarsest_smem<M><<<1, kCoarseThreads, smem, A.st>>>(L.view(l > 0), A.coef)));
+      } else {
+        ISIS_LAUNCH(KK_PATCH_COARSEST, kCoarseSweeps * sweep_bytes(L), A.st,
+                    (pt_coarsest<M><<<1, 1024, 0, A.st>>>(L.view(l > 0), A.coef, L.pre)));
+      }
       return ISIS_OK;
     }
     const PLevel& C = lev[l + 1];
@@ -393,6 +467,22 @@ struct PatchSolver {
                 (pt_interp<<<nblk(F.cells()), kPT, 0, A.st>>>(A.parent, A.pn[0], A.pn[1], A.pn[2], A.origin[0],
                                                               A.origin[1], A.origin[2], A.periodic, F.m, F.u,
                                                               F.n[0], F.n[1], F.n[2], A.init_parent)));
+    // the unknowns of each level and colour
+    if (cudaMemsetAsync(counts, 0, 2 * lev.size() * sizeof(int), A.st) != cudaSuccess) return ISIS_ECUDA;
+    for (size_t l = 0; l < lev.size(); ++l) {
+      const PLevel& L = lev[l];
+      ISIS_LAUNCH(KK_PATCH_OTHER, 8.0 * L.cells(), A.st,
+                  (pt_compact<<<nblk(L.cells()), kPT, 0, A.st>>>(L.view(false), L.list[0], L.list[1],
+                                                                 counts + 2 * l)));
+    }
+    std::vector<int> hc(2 * lev.size());
+    if (cudaMemcpyAsync(hc.data(), counts, hc.size() * sizeof(int), cudaMemcpyDeviceToHost, A.st) != cudaSuccess ||
+        cudaStreamSynchronize(A.st) != cudaSuccess)
+      return ISIS_ECUDA;
+    for (size_t l = 0; l < lev.size(); ++l) {
+      lev[l].count[0] = hc[2 * l];
+      lev[l].count[1] = hc[2 * l + 1];
+    }
     return ISIS_OK;
   }
 
@@ -461,6 +551,9 @@ isis_status patch_solve(const PatchArgs& A) {
     h *= 2.0;
   }
   total += kPNormBlocks;
+  size_t ints = 2 * S.lev.size();  // counts
+  for (const PLevel& L : S.lev) ints += 2 * (L.cells() / 2 + 1);
+  total += (ints + 1) / 2;
   double* mem = nullptr;
   if (cudaMallocAsync((void**)&mem, total * sizeof(double), A.st) != cudaSuccess) {
     cudaGetLastError();
@@ -485,8 +578,23 @@ isis_status patch_solve(const PatchArgs& A) {
     }
   }
   S.part = p;
+  p += kPNormBlocks;
+  int* ip = reinterpret_cast<int*>(p);
+  S.counts = ip;
+  ip += 2 * S.lev.size();
+  for (PLevel& L : S.lev) {
+    L.list[0] = ip;
+    ip += L.cells() / 2 + 1;
+    L.list[1] = ip;
+    ip += L.cells() / 2 + 1;
+  }
   isis_status st = ISIS_OK;
-  if (cudaMallocHost((void**)&S.host, kPNormBlocks * sizeof(double)) != cudaSuccess) {
+  if (cudaFuncSetAttribute(pt_coarsest_smem<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    st = ISIS_ECUDA;
+  }
+  if (st == ISIS_OK && cudaMallocHost((void**)&S.host, kPNormBlocks * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     st = ISIS_ENOMEM;
   }

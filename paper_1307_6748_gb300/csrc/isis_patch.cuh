@@ -21,7 +21,7 @@
 //     restriction of u, residual restricted with zeros off the unknowns,
 //     correction added at unknowns only, none from outside the box);
 //   - levels halve while every dimension is even and the smallest is >= 8;
-//     the coarsest level gets 64 red/black sweeps in one block;
+//     the coarsest level gets 16 red/black sweeps in one block;
 //   - flags on the box's outer layer of parent cells are rejected, so on every
 //     level the unknowns lie inside the outer layer and stencils stay in the box
 //     (the kernels also skip the outer layer whatever the mask says).

@@ -30,6 +30,7 @@ enum KernelKind : int {
   KK_UNET_ELEM,         // its element-wise kernels
   KK_PATCH_SMOOTH,      // smoother on a refinement patch
   KK_PATCH_OTHER,       // the patch's residual, transfers, interpolation and norms
+  KK_PATCH_COARSEST,    // the relaxation of a patch's coarsest level (one block)
   KK_COUNT
 };
 

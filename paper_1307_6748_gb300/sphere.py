@@ -93,6 +93,7 @@ def main():
     ap.add_argument("--cases", default=",".join(CASES))
     ap.add_argument("--levels", type=int, default=0)
     ap.add_argument("--expand", type=int, default=4)
+    ap.add_argument("--prof", action="store_true", help="per-kernel-kind event times of the level solves")
     ap.add_argument("--profile-dir", default=None)
     args = ap.parse_args()
     isis.load()
@@ -127,6 +128,9 @@ def main():
                 opts = isis.Opts(max_cycles=100, init=isis.ISIS_INIT_PARENT)
                 parent = phi if lv.level == 1 else levels[lv.level - 2].phi
                 torch.cuda.synchronize()
+                if args.prof:
+                    isis.prof_reset()
+                    isis.prof_enable(True)
                 e0.record()
                 info = isis.isis_patch_scalar_solve(model, isis.Params(**case["params"]),
                                                     isis.Grid(args.N, case["B"]), a, lv.patch, parent, lv.flags,
@@ -137,6 +141,10 @@ def main():
                                   "fine_cells": int(lv.phi.numel()), "unknowns": int(lv.unknowns.sum()),
                                   "ms": round(e0.elapsed_time(e1), 3), "cycles": info.cycles,
                                   "res_final_over_ref": info.res_final / info.res_ref}), flush=True)
+                if args.prof:
+                    isis.prof_enable(False)
+                    kinds = {k: [v[0], round(v[1], 3)] for k, v in isis.prof_read().items()}
+                    print(json.dumps({"case": name, "level": lv.level, "kinds": kinds}), flush=True)
         if args.profile_dir:
             os.makedirs(args.profile_dir, exist_ok=True)
             rows = radial_profile(case, phi, args.N)

@@ -23,7 +23,8 @@ Recipes
                    mean-density domain cells (RAMSES's quasi-Lagrangian rule with
                    one particle per domain cell), dilated by `expand` cells.
   patch_box        the box of parent cells of a patch: the flags' bounding box
-                   widened by a margin and rounded to a multiple of 4 cells.
+                   widened by a margin and rounded to a multiple of 8 cells (so
+                   the patch's multigrid halves it at least four times).
 """
 from __future__ import annotations
 
@@ -209,7 +210,7 @@ def refine_flags(eta: np.ndarray, level: int, m_ref: float = 8.0, expand: int = 
     return f
 
 
-def patch_box(flags: np.ndarray, margin: int = 1, multiple: int = 4, periodic: bool = False):
+def patch_box(flags: np.ndarray, margin: int = 1, multiple: int = 8, periodic: bool = False):
     """(origin, n) of the box of parent cells holding every flag with `margin` unflagged cells round it, n
     rounded up to a multiple of `multiple`; None without flags.  A non-periodic parent keeps one more cell
     outside the box on each side (the interpolation's stencil); a periodic box may wrap."""
