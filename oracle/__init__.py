@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "isis_oracle.c")
 _LIB = os.path.join(_HERE, "libisis_oracle.so")
 
-POISSON, SYMMETRON, FOFR = 0, 1, 2
+POISSON, SYMMETRON, FOFR, CHAMELEON = 0, 1, 2, 3
 OK, EINVAL, ENOCONV, ENAN, ENOMEM = 0, -1, -2, -3, -5
 
 # c = 1 units with lengths in Mpc/h: H0 = 100 h km/s/Mpc / c
@@ -41,7 +41,7 @@ class _Problem(ctypes.Structure):
         ("model", ctypes.c_int), ("N", ctypes.c_int), ("box", ctypes.c_double), ("a", ctypes.c_double),
         ("Omega_m", ctypes.c_double), ("Omega_L", ctypes.c_double), ("H0", ctypes.c_double),
         ("lambda0", ctypes.c_double), ("beta", ctypes.c_double), ("a_ssb", ctypes.c_double),
-        ("n", ctypes.c_int), ("fR0_abs", ctypes.c_double),
+        ("n", ctypes.c_int), ("fR0_abs", ctypes.c_double), ("cham_n", ctypes.c_double),
     ]
 
 
@@ -67,10 +67,11 @@ class Problem:
     a_ssb: float = 0.5
     n: int = 1
     fR0_abs: float = 1e-5
+    cham_n: float = 1.0
 
     def c(self) -> _Problem:
         return _Problem(self.model, self.N, self.box, self.a, self.Omega_m, self.Omega_L, self.H0,
-                        self.lambda0, self.beta, self.a_ssb, self.n, self.fR0_abs)
+                        self.lambda0, self.beta, self.a_ssb, self.n, self.fR0_abs, self.cham_n)
 
 
 class _Patch(ctypes.Structure):
@@ -276,15 +277,18 @@ def leapfrog_kick_drift(pos, vel, g, kick: float, drift: float, N: int, h: float
 
 
 def background_field(model: int, a: float, Omega_m: float = 0.267, Omega_L: float = 0.733, a_ssb: float = 0.5,
-                     n: int = 1, fR0_abs: float = 1e-5) -> float:
+                     n: int = 1, fR0_abs: float = 1e-5, cham_n: float = 1.0, **_) -> float:
     """Uniform-density solution: chi = sqrt(1 - (a_SSB/a)^3) above symmetry breaking, else 0 (Sect. 4.1);
-    u = ln(a^2 |f_R|), |f_R| = |f_R0| [(1 + 4 r) / (a^-3 + 4 r)]^(n+1), r = OL/Om (Sect. 4.2)."""
+    u = ln(a^2 |f_R|), |f_R| = |f_R0| [(1 + 4 r) / (a^-3 + 4 r)]^(n+1), r = OL/Om (Sect. 4.2);
+    chameleon u = ln psi, psi^{-(1+n)} = a^-3: u = 3 ln(a) / (1 + n)."""
     if model == SYMMETRON:
         v = 1.0 - (a_ssb / a) ** 3
         return math.sqrt(v) if v > 0 else 0.0
     if model == FOFR:
         r = Omega_L / Omega_m
         return math.log(a * a * fR0_abs * ((1 + 4 * r) / (a ** -3 + 4 * r)) ** (n + 1))
+    if model == CHAMELEON:
+        return 3.0 * math.log(a) / (1.0 + cham_n)
     return 0.0
 
 
@@ -307,7 +311,7 @@ def pm_run(model, N: int, box: float, pos, vel, a_steps, tol: float = 1e-10, nco
             ps = Problem(model, N, box, a=a, **params)
             if phi is None:
                 bg = background_field(model, a, **{k: params[k] for k in ("Omega_m", "Omega_L", "a_ssb", "n",
-                                                                          "fR0_abs") if k in params})
+                                                                          "fR0_abs", "cham_n") if k in params})
                 phi = np.full((N,) * 3, bg)
             phi = solve(ps, eta, phi, tol=tol, ncoarse=ncoarse).phi
             g = fifth_force(ps, Phi, phi, x, y, z)

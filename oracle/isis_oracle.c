@@ -60,11 +60,11 @@
 #define ORC_ENAN -3
 #define ORC_ENOMEM -5
 
-enum { ORC_POISSON = 0, ORC_SYMMETRON = 1, ORC_FOFR = 2 };
+enum { ORC_POISSON = 0, ORC_SYMMETRON = 1, ORC_FOFR = 2, ORC_CHAMELEON = 3 };
 
 /* Problem description handed in from Python (ctypes mirror). */
 typedef struct {
-  int model;     /* ORC_POISSON, ORC_SYMMETRON or ORC_FOFR */
+  int model;     /* ORC_POISSON, ORC_SYMMETRON, ORC_FOFR or ORC_CHAMELEON */
   int N;         /* finest grid size per dimension */
   double box;    /* box side in Mpc/h */
   double a;      /* expansion factor */
@@ -72,6 +72,7 @@ typedef struct {
   double lambda0, beta, a_ssb; /* symmetron, Sect. 4.1 */
   int n;                       /* Hu-Sawicki exponent, Sect. 4.2 */
   double fR0_abs;              /* |f_R0| */
+  double cham_n;               /* chameleon exponent (> -1), Sect. 6's chameleon equation */
 } orc_problem;
 
 typedef struct {
@@ -123,6 +124,21 @@ static void make_coef(const orc_problem* p, const double* eta_fine, orc_coef* c)
     c->K1 = p->Omega_m * a * H02;
     c->K2 = p->Omega_m * pow(a, 4.0) * H02 * (1.0 + 4.0 * r) * pow(p->fR0_abs * a * a, 1.0 / c->np1);
     c->K3 = p->Omega_m * a * H02 * (1.0 + 4.0 * a * a * a * r);
+  } else if (p->model == ORC_CHAMELEON) {
+    /* The chameleon equation of Sect. 6, lap phi = -M^{4+n} phi^{-(1+n)} + beta rho / M_pl, taken as a
+       free source S (Sect. 2) in comoving units (lap -> a^2 lap) with rho = rho_m0 a^-3 eta and
+       phi = phi_0 psi, phi_0 the minimum at a = 1, eta = 1:
+           lap psi = A_c [a^-3 eta - psi^{-(1+n)}],  A_c = a^2 / ((1+n) lambda0^2),
+       lambda0 the range (inverse mass) of the field in the background today.  In u = ln psi,
+       lap psi = div(e^u grad u): the non-canonical operator of Sect. 3.4 with b = e^u and
+           S(u) = K1 (eta - 1) - K2 e^{-u/np1} + K3,  K1 = K3 = A_c a^-3, K2 = A_c, np1 = 1/(1+n),
+       the form of the Hu-Sawicki source, so every f(R) step below serves it unchanged. */
+    double Ac = a * a / ((1.0 + p->cham_n) * p->lambda0 * p->lambda0);
+    c->model = ORC_FOFR;
+    c->np1 = 1.0 / (1.0 + p->cham_n);
+    c->K1 = Ac / (a * a * a);
+    c->K2 = Ac;
+    c->K3 = c->K1;
   } else {
     /* Sect. 3.1: lap Phi = (3/2) Om H0^2 delta / a, delta = eta - 1 with its mean removed (R7) */
     c->KP = 1.5 * p->Omega_m * H02 / a;
@@ -496,7 +512,7 @@ static double background(const orc_problem* p, const orc_coef* c) {
     double v = 1.0 - c->s;
     return v > 0.0 ? sqrt(v) : 0.0;
   }
-  if (p->model == ORC_FOFR) {
+  if (c->model == ORC_FOFR) {
     /* uniform eta = 1 root of S(u) = 0: e^{u/(n+1)} = K2/K3 */
     return c->np1 * log(c->K2 / c->K3);
   }
@@ -506,7 +522,8 @@ static double background(const orc_problem* p, const orc_coef* c) {
 static int valid(const orc_problem* p) {
   if (p->N < 2 || (p->N & (p->N - 1)) != 0) return 0;
   if (!(p->a > 0.0) || !(p->box > 0.0)) return 0;
-  if (p->model < 0 || p->model > 2) return 0;
+  if (p->model < 0 || p->model > 3) return 0;
+  if (p->model == ORC_CHAMELEON && (!(p->lambda0 > 0.0) || !(p->cham_n > -1.0) || !(p->cham_n <= 8.0))) return 0;
   if (p->model == ORC_SYMMETRON && !(p->lambda0 > 0.0)) return 0;
   if (p->model == ORC_FOFR && (!(p->fR0_abs > 0.0) || p->n < 1)) return 0;
   return 1;
@@ -534,7 +551,7 @@ int orc_solve(const orc_problem* p, const double* eta_in, double* phi, double to
     for (size_t q = 0; q < n3; ++q) sum2 += (eta[q] - eref) * (eta[q] - eref);
     double scale;
     if (p->model == ORC_SYMMETRON) scale = H.coef.A * H.coef.s * background(p, &H.coef);
-    else if (p->model == ORC_FOFR) scale = H.coef.K1;
+    else if (H.coef.model == ORC_FOFR) scale = H.coef.K1;
     else scale = H.coef.KP;
     info->ref = scale * sqrt(sum2 / (double)n3);
   }
@@ -698,9 +715,13 @@ int orc_fifth_force(const orc_problem* p, const double* Phi, const double* phi, 
   if (phi && p->model != ORC_POISSON) {
     orc_gradient(N, p->box, phi, g[0], g[1], g[2]);
     double Cs = 6.0 * p->Omega_m * p->H0 * p->H0 * pow(p->beta * p->lambda0, 2.0) / pow(p->a_ssb, 3.0);
+    /* chameleon: beta phi_0 / M_pl = 3 (1+n) beta^2 Om H0^2 lambda0^2, from the mass of the field at the
+       background minimum today, m0^2 = (1+n) beta rho_m0 / (M_pl phi_0) = 1/lambda0^2, rho_m0 = 3 Om H0^2 M_pl^2 */
+    double Cc = 3.0 * (1.0 + p->cham_n) * pow(p->beta, 2.0) * p->Omega_m * p->H0 * p->H0 * pow(p->lambda0, 2.0);
     for (size_t q = 0; q < n3; ++q) {
       double pref;
       if (p->model == ORC_SYMMETRON) pref = Cs * (a * phi[q]) * a; /* chi~ grad chi~ = a chi * a grad chi */
+      else if (p->model == ORC_CHAMELEON) pref = a * a * Cc * exp(phi[q]); /* a^2 grad ln A, ln A = beta phi / M_pl */
       else pref = 0.5 * exp(phi[q]);
       for (int d = 0; d < 3; ++d) f[d][q] += pref * g[d][q];
     }
@@ -1057,7 +1078,7 @@ int orc_patch_solve(const orc_problem* p, const orc_patch* P, const double* pare
       if (F->m[q] > 0.0) { s2 += (eta[q] - eref) * (eta[q] - eref); ++cnt; }
     double scale;
     if (p->model == ORC_SYMMETRON) scale = H.coef.A * H.coef.s * background(p, &H.coef);
-    else if (p->model == ORC_FOFR) scale = H.coef.K1;
+    else if (H.coef.model == ORC_FOFR) scale = H.coef.K1;
     else scale = H.coef.KP;
     info->ref = cnt ? scale * sqrt(s2 / (double)cnt) : 0.0;
   }

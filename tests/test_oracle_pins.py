@@ -531,3 +531,95 @@ def test_radial_fofr_linear_limit_is_yukawa():
     m = math.sqrt(K2 * math.exp(-u_out / (n + 1)) / ((n + 1) * b))
     lin = _yukawa_sphere(rad.r, R, m, K1 * d_eta / b)
     assert np.abs((u - u_out) - lin).max() <= 2e-3 * np.abs(lin).max()
+
+
+# ---- the chameleon through the free source (Sect. 2) and its mapping to Hu-Sawicki (Sect. 6) ----
+
+@pytest.mark.parametrize("n,a,etav", [(1.0, 1.0, 1.0), (1.0, 0.7, 3.0), (-0.5, 1.0, 0.4), (2.0, 0.5, 10.0)])
+def test_chameleon_uniform_minimum(n, a, etav):
+    """Uniform eta: the field sits at the minimum of its effective potential, psi^{-(1+n)} = a^-3 eta
+    (the chameleon equation of Sect. 6 with a zero Laplacian), u = ln psi."""
+    N, box = 8, 16.0
+    u_exact = -math.log(etav * a ** -3) / (1.0 + n)
+    p = oracle.Problem(oracle.CHAMELEON, N, box, a=a, lambda0=2.0, cham_n=n)
+    r = oracle.solve(p, np.full((N,) * 3, etav), np.full((N,) * 3, u_exact + 0.2), tol=1e-10)
+    assert r.status == oracle.OK
+    assert np.abs(r.phi - u_exact).max() <= 1e-10
+    assert abs(oracle.background_field(oracle.CHAMELEON, a, cham_n=n) + math.log(a ** -3) / (1 + n)) < 1e-15
+
+
+def test_chameleon_range_is_lambda0():
+    """eta = 1 + eps nu at a = 1: the first-order field solves lap d - d / lambda0^2 = eps nu / ((1+n) lambda0^2)
+    (psi = 1 + d): lambda0 is the range of the field in today's background."""
+    N, box, lam, n = 32, 32.0, 2.5, 1.0
+    nu = synth.gaussian_field(N, box, 1.0, 23).numpy()
+    errs = []
+    for eps in (1e-4, 1e-3):
+        r = oracle.solve(oracle.Problem(oracle.CHAMELEON, N, box, a=1.0, lambda0=lam, cham_n=n), 1.0 + eps * nu,
+                         np.zeros((N,) * 3), tol=1e-12)
+        lin = fft_solve(eps * nu / ((1 + n) * lam ** 2), 1.0 / lam ** 2, box / N)
+        errs.append(np.linalg.norm(np.expm1(r.phi) - lin) / np.linalg.norm(lin))
+    assert errs[0] <= 5e-4
+    assert 5.0 < errs[1] / errs[0] < 20.0
+
+
+def test_chameleon_n_minus_half_is_hu_sawicki_n1():
+    """Sect. 6: the Hu-Sawicki model maps to the chameleon with n = -1/2.  Without a cosmological constant
+    (OL = 0) the two equations are the same up to u_cham = u_HS + c: with K1 = Om a H0^2 and
+    K2 = Om a^4 H0^2 (|f_R0| a^2)^{1/2} of the f(R) source, A_c e^{-c} a^-3 = K1 and A_c e^{-3c/2} = K2 give c and the
+    chameleon's A_c = 2 a^2 / lambda0^2 by matching both source terms.  Both start from their backgrounds."""
+    N, box, a, fr0 = 16, 64.0, 0.8, 1e-5
+    eta = synth.lognormal_eta(N, box, 1.0, 31).numpy()
+    K1 = OM * a * H0 ** 2
+    K2 = OM * a ** 4 * H0 ** 2 * math.sqrt(fr0 * a * a)
+    # A_c e^{-c} a^-3 = K1 and A_c e^{-3c/2} = K2
+    c = 2.0 * math.log(K1 * a ** 3 / K2)
+    Ac = K1 * a ** 3 * math.exp(c)
+    lam = math.sqrt(2.0 * a * a / Ac)
+    ph = oracle.Problem(oracle.FOFR, N, box, a=a, Omega_m=OM, Omega_L=0.0, fR0_abs=fr0, n=1)
+    pc = oracle.Problem(oracle.CHAMELEON, N, box, a=a, Omega_m=OM, Omega_L=0.0, lambda0=lam, cham_n=-0.5)
+    g = np.full((N,) * 3, 2.0 * math.log(K2 / K1))  # the eta = 1 background of the f(R) source
+    rh = oracle.solve(ph, eta, g, tol=1e-12)
+    rc = oracle.solve(pc, eta, g + c, tol=1e-12)
+    assert rh.status == oracle.OK and rc.status == oracle.OK
+    assert np.abs((rc.phi - c) - rh.phi).max() <= 1e-9
+    assert np.ptp(rh.phi) > 0.5  # a non-trivial field
+
+
+def test_chameleon_derivative_and_dense_newton():
+    N, box = 8, 16.0
+    gen = np.random.Generator(np.random.PCG64(6))
+    eta = np.exp(gen.standard_normal((N,) * 3))
+    p = oracle.Problem(oracle.CHAMELEON, N, box, a=0.9, lambda0=1.5, cham_n=1.0)
+    phi = 0.3 * gen.standard_normal((N,) * 3)
+    d = oracle.dL(p, eta, phi)
+    for c in [(0, 0, 0), (3, 5, 7), (7, 1, 2)]:
+        eps = 1e-6
+        pp, pm = phi.copy(), phi.copy()
+        pp[c] += eps
+        pm[c] -= eps
+        fd = (oracle.residual(p, eta, pp)[c] - oracle.residual(p, eta, pm)[c]) / (2 * eps)
+        assert abs(fd - d[c]) <= 1e-7 * abs(d[c])
+    guess = np.zeros((N,) * 3)
+    ref = numpy_newton(p, eta, guess)
+    r = oracle.solve(p, eta, guess, tol=1e-12)
+    assert r.status == oracle.OK
+    assert np.abs(r.phi - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+
+
+def test_chameleon_force_at_cell_centre():
+    """The chameleon's fifth force is a^2 grad ln A with ln A = beta phi / M_pl = (beta phi_0 / M_pl) e^u and
+    beta phi_0 / M_pl = 3 (1+n) beta^2 Om H0^2 lambda0^2 (the background mass today, m0 = 1/lambda0)."""
+    N, box, a, lam, beta, n = 16, 32.0, 0.8, 2.0, 0.7, 1.0
+    Phi = 1e-6 * synth.sinusoid(N, m=1, axis=0).numpy()
+    gPhi = oracle.gradient(Phi, box)
+    u = 0.1 * synth.sinusoid(N, m=1, axis=2).numpy()
+    gu = oracle.gradient(u, box)
+    c = (3, 7, 11)
+    x, y, z = (np.array([v + 0.5], dtype=np.float32) for v in c)
+    Cc = 3 * (1 + n) * beta ** 2 * OM * H0 ** 2 * lam ** 2
+    g = oracle.fifth_force(oracle.Problem(oracle.CHAMELEON, N, box, a=a, lambda0=lam, beta=beta, cham_n=n),
+                           Phi, u, x, y, z)
+    for d in range(3):
+        exp_d = -(a * a * gPhi[d][c] + a * a * Cc * math.exp(u[c]) * gu[d][c])
+        assert abs(g[d][0] - exp_d) <= 1e-12 * (abs(exp_d) + 1e-20)
