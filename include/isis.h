@@ -51,7 +51,7 @@ typedef enum {
   ISIS_EINTERNAL = -7
 } isis_status;
 
-typedef enum { ISIS_SYMMETRON = 1, ISIS_FOFR_HS = 2 } isis_model;
+typedef enum { ISIS_SYMMETRON = 1, ISIS_FOFR_HS = 2, ISIS_CHAMELEON = 3 } isis_model;
 
 /* Arithmetic of a solve.
  *   ISIS_F64           eta, phi are double; every kernel computes in FP64.
@@ -77,6 +77,7 @@ typedef struct {
   double lambda0, beta, a_ssb; /* symmetron (Sect. 4.1): range in Mpc/h, coupling, a at symmetry breaking */
   int n;                       /* Hu-Sawicki exponent (Sect. 4.2), n >= 1 */
   double fR0_abs;              /* |f_R0| */
+  double cham_n;               /* chameleon exponent, -1 < n <= 8 (ISIS_CHAMELEON; lambda0 and beta as above) */
 } isis_params;
 
 /* Initial guess of a solve.
@@ -174,6 +175,13 @@ isis_status isis_poisson_solve(const isis_grid* grid, double a, const void* eta,
  *                       + Om a H0^2 (1 + 4 a^3 OL/Om)                  (Sect. 4.2)
  *                   discretised in flux form with face b = arithmetic mean
  *                   (Sect. 3.4, Eq. (disc_non_canonical)).
+ *   ISIS_CHAMELEON  the chameleon equation of Sect. 6, lap phi = -M^{4+n} phi^{-(1+n)} + beta rho / M_pl,
+ *                   as one more free source S (Sect. 2): with phi = phi_0 psi (phi_0 the minimum in
+ *                   today's background) and phi = u = ln psi,
+ *                   div(e^u grad u) = a^2 / ((1+n) lambda0^2) [a^-3 eta - e^{-(1+n) u}],
+ *                   lambda0 = params->lambda0 the range of the field in today's background and
+ *                   n = params->cham_n; the f(R) operator with other constants (n = -1/2 is the
+ *                   Hu-Sawicki n = 1 model of Sect. 6's mapping).  Background u = 3 ln(a) / (1+n).
  *   eta  device array (double, or float for ISIS_F32) of eta = rho / mean rho.
  *   phi  device array of the same type: initial guess in, solution out (the
  *        symmetron's zero field is a fixed point: start from a positive guess).
@@ -186,6 +194,7 @@ isis_status isis_scalar_solve(isis_model model, const isis_params* params, const
  *     g = -[ grad Phi~ + F5 ],  Phi~ = a^2 Phi
  *     ISIS_SYMMETRON  F5 = 6 Om H0^2 (beta lambda0)^2 / a_SSB^3  chi~ grad chi~,  chi~ = a chi
  *     ISIS_FOFR_HS    F5 = (1/2) e^u grad u
+ *     ISIS_CHAMELEON  F5 = a^2 grad(beta phi / M_pl) = a^2 3 (1+n) beta^2 Om H0^2 lambda0^2 e^u grad u
  * Gradients are 2-point central differences at cells, interpolated to the
  * particles with the CIC weights of isis_cic_deposit.
  *   Phi, phi    device arrays (double if fields_f64, else float); either may be

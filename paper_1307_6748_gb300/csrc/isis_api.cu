@@ -188,6 +188,23 @@ static bool model_coef(isis_model model, const isis_params* p, const isis_grid* 
     *ref_scale = c->K1;
     return true;
   }
+  if (model == ISIS_CHAMELEON) {
+    if (!(p->lambda0 > 0) || !(p->cham_n > -1.0) || !(p->cham_n <= 8.0)) return false;
+    // The chameleon equation of Sect. 6 as a free source (Sect. 2), in u = ln(phi / phi_0):
+    // div(e^u grad u) = A_c [a^-3 eta - e^{-(1+n) u}], A_c = a^2 / ((1+n) lambda0^2): the f(R) operator with
+    // K1 = K3 = A_c a^-3, K2 = A_c and the exponent 1/(n+1) of f(R) replaced by 1+n.
+    const double Ac = a * a / ((1.0 + p->cham_n) * p->lambda0 * p->lambda0);
+    c->inv_np1 = 1.0 + p->cham_n;
+    c->np1 = 1.0 / c->inv_np1;
+    c->K1 = Ac / (a * a * a);
+    c->K2 = Ac;
+    c->K3 = c->K1;
+    c->fscale = 1.0;
+    c->fKx = c->K2;
+    c->fK3x = c->K3 - c->K2;
+    *ref_scale = c->K1;
+    return true;
+  }
   return false;
 }
 

@@ -104,7 +104,8 @@ __global__ void cic_finish(const unsigned long long* __restrict__ acc, T* __rest
 // Grid force at every cell (one pass):
 //   f_d(c) = [a^2 (Phi(c+e_d) - Phi(c-e_d)) + pref(c) (phi(c+e_d) - phi(c-e_d))] / (2h)
 //   pref = C_s a^2 chi(c) (symmetron, Eq. (symmetron_geodesics_tilde_chi) with chi~ = a chi),
-//          e^u(c)/2 (f(R), Sect. 4.2), 0 without a scalar field.
+//          C_s e^u(c) (the b = e^u models: C_s = 1/2 for f(R), Sect. 4.2; a^2 beta phi_0 / M_pl for
+//          the chameleon), 0 without a scalar field.
 // The differences are taken in the field's precision (FP64 fields lose no
 // digits to cancellation), the products in FP32 (the output is FP32).
 template <class T, int MODEL>
@@ -126,7 +127,7 @@ __global__ void force_grid(const T* __restrict__ Phi, const T* __restrict__ phi,
   }
   if (MODEL != 0) {
     float v = (float)phi[t];
-    float pref = (MODEL == ISIS_SYMMETRON) ? Cs * a2 * v : 0.5f * expf(v);
+    float pref = (MODEL == ISIS_SYMMETRON) ? Cs * a2 * v : Cs * expf(v);
     g0 = fmaf(pref, (float)(phi[xp] - phi[xm]), g0);
     g1 = fmaf(pref, (float)(phi[yp] - phi[ym]), g1);
     g2 = fmaf(pref, (float)(phi[zp] - phi[zm]), g2);
@@ -302,8 +303,10 @@ isis_status isis_fifth_force(isis_model model, const isis_params* p, const isis_
                              const void* Phi, const void* phi, int fields_f64, const float* x, const float* y,
                              const float* z, int64_t npart, float* gx, float* gy, float* gz, void* stream) {
   if (!grid_valid(grid) || !x || !y || !z || !gx || !gy || !gz || npart < 1 || !(a > 0)) return ISIS_EINVAL;
-  if (phi && (!p || (model != ISIS_SYMMETRON && model != ISIS_FOFR_HS))) return ISIS_EINVAL;
+  if (phi && (!p || (model != ISIS_SYMMETRON && model != ISIS_FOFR_HS && model != ISIS_CHAMELEON)))
+    return ISIS_EINVAL;
   if (phi && model == ISIS_SYMMETRON && !(p->a_ssb > 0)) return ISIS_EINVAL;
+  if (phi && model == ISIS_CHAMELEON && !(p->cham_n > -1.0)) return ISIS_EINVAL;
   const int lg = ilog2(grid->N);
   const double h = grid->box / grid->N;
   const double inv2h = 1.0 / (2.0 * h), a2 = a * a;
@@ -311,6 +314,10 @@ isis_status isis_fifth_force(isis_model model, const isis_params* p, const isis_
   if (phi && model == ISIS_SYMMETRON)  // Eq. (symmetron_geodesics_tilde_chi)
     Cs = 6.0 * grid->Omega_m * grid->H0 * grid->H0 * (p->beta * p->lambda0) * (p->beta * p->lambda0) /
          (p->a_ssb * p->a_ssb * p->a_ssb);
+  if (phi && model == ISIS_FOFR_HS) Cs = 0.5;  // Sect. 4.2: (1/2) e^u grad u
+  if (phi && model == ISIS_CHAMELEON)  // a^2 grad ln A, ln A = beta phi / M_pl = (beta phi_0 / M_pl) e^u
+    Cs = a2 * 3.0 * (1.0 + p->cham_n) * p->beta * p->beta * grid->Omega_m * grid->H0 * grid->H0 * p->lambda0 *
+         p->lambda0;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t n = (size_t)grid->N * grid->N * grid->N;
   float* fg = get_force_buf(grid->N);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libisis_gb300.so")
 
 ISIS_OK, ISIS_EINVAL, ISIS_ENOCONV, ISIS_ENAN, ISIS_ECUDA, ISIS_ENOMEM, ISIS_ETIMEOUT, ISIS_EINTERNAL = (
     0, -1, -2, -3, -4, -5, -6, -7)
-ISIS_SYMMETRON, ISIS_FOFR_HS = 1, 2
+ISIS_SYMMETRON, ISIS_FOFR_HS, ISIS_CHAMELEON = 1, 2, 3
 ISIS_F64, ISIS_F32, ISIS_F32_REFINE64 = 0, 1, 2
 
 H0_MPC = 1.0 / 2997.92458  # (Mpc/h)^-1 with c = 1
@@ -38,7 +38,7 @@ class isis_grid(ctypes.Structure):
 
 class isis_params(ctypes.Structure):
     _fields_ = [("lambda0", ctypes.c_double), ("beta", ctypes.c_double), ("a_ssb", ctypes.c_double),
-                ("n", ctypes.c_int), ("fR0_abs", ctypes.c_double)]
+                ("n", ctypes.c_int), ("fR0_abs", ctypes.c_double), ("cham_n", ctypes.c_double)]
 
 
 class isis_mg_opts(ctypes.Structure):
@@ -142,9 +142,10 @@ class Params:
     a_ssb: float = 0.5
     n: int = 1
     fR0_abs: float = 1e-5
+    cham_n: float = 1.0  # chameleon exponent (ISIS_CHAMELEON uses lambda0, beta and cham_n)
 
     def c(self):
-        return isis_params(self.lambda0, self.beta, self.a_ssb, self.n, self.fR0_abs)
+        return isis_params(self.lambda0, self.beta, self.a_ssb, self.n, self.fR0_abs, self.cham_n)
 
 
 @dataclass
@@ -358,6 +359,12 @@ def u_background(a: float, fR0_abs: float, n: int = 1, Omega_m: float = 0.267, O
 # ---------------------------------------------------------------------------
 # Parameter presets of the paper's Table 1 (Sect. 6.1)
 # ---------------------------------------------------------------------------
+
+def cham_background(a: float, cham_n: float) -> float:
+    """Chameleon background u = ln(psi) with psi^{-(1+n)} = a^-3: u = 3 ln(a) / (1 + n)."""
+    import math
+    return 3.0 * math.log(a) / (1.0 + cham_n)
+
 
 def fofr_range(fR0_abs: float, n: int = 1, Omega_m: float = 0.267, Omega_L: float = 0.733) -> float:
     """Compton range of the f(R) field today in Mpc/h (Sect. 4.2):

@@ -78,8 +78,11 @@ class PM:
 
 
 def main():
-    """python -m paper_1307_6748_gb300.pm [--N 512] [--box 256] [--model symmetron|fofr|none] [--steps 10]
-    Zel'dovich particles at a0, steps of da; prints one JSON line per step (ms, cycles of each solve)."""
+    """python -m paper_1307_6748_gb300.pm [--N 512] [--box 256] [--model symmetron|fofr|chameleon|none]
+    [--steps 10] [--cham-n -0.5 --lambda0 7.5 --beta 0.408]
+    Zel'dovich particles at a0, steps of da; prints one JSON line per step (ms, cycles of each solve).
+    The chameleon defaults are the Hu-Sawicki-equivalent exponent and coupling of Sect. 6 (n = -1/2,
+    beta = 1/sqrt(6)) with the 7.5 Mpc/h range of |f_R0| = 1e-5 (Table 1)."""
     import argparse
     import json
 
@@ -87,7 +90,10 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--N", type=int, default=512)
     ap.add_argument("--box", type=float, default=256.0)
-    ap.add_argument("--model", default="symmetron", choices=["symmetron", "fofr", "none"])
+    ap.add_argument("--model", default="symmetron", choices=["symmetron", "fofr", "chameleon", "none"])
+    ap.add_argument("--cham-n", type=float, default=-0.5)
+    ap.add_argument("--lambda0", type=float, default=7.5)
+    ap.add_argument("--beta", type=float, default=6 ** -0.5)
     ap.add_argument("--a0", type=float, default=0.9)
     ap.add_argument("--da", type=float, default=0.01)
     ap.add_argument("--steps", type=int, default=10)
@@ -95,9 +101,12 @@ def main():
     ap.add_argument("--inner", type=int, default=4)
     args = ap.parse_args()
     isis.load()
-    model = {"symmetron": isis.ISIS_SYMMETRON, "fofr": isis.ISIS_FOFR_HS, "none": None}[args.model]
+    model = {"symmetron": isis.ISIS_SYMMETRON, "fofr": isis.ISIS_FOFR_HS, "chameleon": isis.ISIS_CHAMELEON,
+             "none": None}[args.model]
     ic = synth.zeldovich_ic(args.N, args.box, args.a0, seed=3, device="cuda")
-    run = PM(isis.Grid(args.N, args.box), model, isis.Params(), *ic, tol=args.tol, inner=args.inner)
+    par = isis.Params(lambda0=args.lambda0, beta=args.beta, cham_n=args.cham_n) if args.model == "chameleon" \
+        else isis.Params()
+    run = PM(isis.Grid(args.N, args.box), model, par, *ic, tol=args.tol, inner=args.inner)
     for k in range(args.steps):
         a = args.a0 + k * args.da
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
