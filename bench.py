@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-ref", action="store_true", help="skip the FP64-solver comparison")
+    ap.add_argument("--fmg", type=int, default=1, choices=[0, 1],
+                    help="start the FP32 phase of each solve with nested iteration (full multigrid)")
     ap.add_argument("--guess", default="net", choices=["net", "background"],
                     help="symmetron initial guess: the trained U-Net, or the background field")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1307_6748_gb300", "weights", "unet_symmetron.npz"))
@@ -60,7 +62,8 @@ def workload(args):
                         f"forces of both models",
             "N": args.N, "box_mpc_h": args.box, "particles": args.N ** 3, "tol": args.tol,
             "symmetron": {"a": 1.0, "a_ssb": 0.5, "lambda0": 1.0, "beta": 1.0},
-            "fofr": {"n": 1, "fR0_abs": 1e-5}, "cycle": f"V(2,2), coarsest {args.ncoarse}^3 dense Newton",
+            "fofr": {"n": 1, "fR0_abs": 1e-5}, "cycle": f"V(2,2), coarsest {args.ncoarse}^3 dense Newton"
+                                                        + (", FP32 phase started by nested iteration" if args.fmg else ""),
             "inner_cycles": {"poisson": args.inner_poisson, "symmetron": args.inner_sym, "fofr": args.inner_fofr},
             "initial_guess": {"symmetron": "U-Net (trained at 1 Mpc/h cells) on the 8-cell mean density, "
                                            "prolongated trilinearly" if args.guess == "net" else "background",
@@ -225,7 +228,7 @@ def main():
     g = [torch.empty(npart, device=dev, dtype=torch.float32) for _ in range(6)]
     def opts(inner):
         return isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=inner, init=isis.ISIS_INIT_BACKGROUND,
-                         n_coarsest=args.ncoarse)
+                         n_coarsest=args.ncoarse, fmg=args.fmg)
     o_poi, o_sym, o_fr = opts(args.inner_poisson), opts(args.inner_sym), opts(args.inner_fofr)
     net, pooled = None, False
     if args.guess == "net":
@@ -238,7 +241,7 @@ def main():
             raise SystemExit(f"bench: the net was trained at {h_net} Mpc/h cells; this grid has {h} Mpc/h")
         net = unet.UNet.load(args.weights, device=dev)
         o_sym = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=args.inner_sym, init=isis.ISIS_INIT_INPUT,
-                          n_coarsest=args.ncoarse)
+                          n_coarsest=args.ncoarse, fmg=args.fmg)
     stream = torch.cuda.current_stream()
     infos = {}
 
@@ -361,7 +364,8 @@ def main():
             row = {}
             for label, prec in (("fp64", isis.ISIS_F64), ("refine64", isis.ISIS_F32_REFINE64)):
                 o = isis.Opts(prec=prec, inner_cycles=prec_inner, init=isis.ISIS_INIT_BACKGROUND,
-                              n_coarsest=args.ncoarse, max_cycles=40)
+                              n_coarsest=args.ncoarse, max_cycles=40,
+                              fmg=args.fmg if prec == isis.ISIS_F32_REFINE64 else 0)
                 out = {"poisson": Phi, "symmetron": chi, "fofr": u}[name]
                 for rep in range(2):
                     barrier()

@@ -58,7 +58,7 @@ typedef enum { ISIS_SYMMETRON = 1, ISIS_FOFR_HS = 2, ISIS_CHAMELEON = 3 } isis_m
  *   ISIS_F32           eta, phi are float; every kernel computes in FP32
  *                      (coarsest dense Newton in FP64).
  *   ISIS_F32_REFINE64  eta, phi are double.  First FP32 FAS V-cycles on the
- *                      field itself until its residual is below 1e-4 of the
+ *                      field itself until its residual is below 2e-4 of the
  *                      reference (or stops falling); then FP64 defect
  *                      correction: the residual r = -L(phi) and the update
  *                      phi += e are FP64, and e solves L(phi + e) - L(phi) = r
@@ -100,6 +100,11 @@ typedef struct {
   isis_precision prec;
   int inner_cycles;    /* F32 V-cycles per FP64 outer iteration (F32_REFINE64), >= 1 */
   isis_init init;      /* initial guess */
+  int fmg;             /* ISIS_F32_REFINE64: 1 starts the FP32 phase with nested iteration (full multigrid):
+                          the guess restricted to every level, the coarsest level's own problem solved,
+                          then on each finer level the coarse correction prolongated onto the restricted
+                          guess and one V-cycle; counted as one cycle.  0: plain V-cycles.  Not in the paper
+                          (its solver starts each level's V-cycles from a guess, Sect. 3.2). */
 } isis_mg_opts;
 
 typedef struct {
@@ -162,7 +167,7 @@ isis_status isis_cic_deposit_noalloc(const isis_grid* grid, const float* x, cons
  * mean of Phi is set to 0 after every cycle.
  *   eta  device double[N^3] (float for ISIS_F32), mean density 1 expected.
  *   Phi  device double[N^3] (float for ISIS_F32): initial guess in, solution out.
- *   opts NULL for the defaults {2, 2, 4, 100, ISIS_F64, 2, ISIS_INIT_INPUT}; info may be NULL. */
+ *   opts NULL for the defaults {2, 2, 4, 100, ISIS_F64, 2, ISIS_INIT_INPUT, 0}; info may be NULL. */
 isis_status isis_poisson_solve(const isis_grid* grid, double a, const void* eta, void* Phi, double tol,
                                const isis_mg_opts* opts, isis_solve_info* info, void* stream);
 

@@ -146,7 +146,7 @@ static bool grid_ok(const isis_grid* g) {
 }
 
 static bool opts_resolve(const isis_mg_opts* o, isis_mg_opts* out, int N) {
-  isis_mg_opts d = {2, 2, 4, 100, ISIS_F64, 2, ISIS_INIT_INPUT};
+  isis_mg_opts d = {2, 2, 4, 100, ISIS_F64, 2, ISIS_INIT_INPUT, 0};
   if (o) d = *o;
   if (d.nu1 < 0 || d.nu1 > 16 || d.nu2 < 0 || d.nu2 > 16) return false;
   if (d.n_coarsest != 2 && d.n_coarsest != 4) return false;
@@ -155,6 +155,7 @@ static bool opts_resolve(const isis_mg_opts* o, isis_mg_opts* out, int N) {
   if (d.prec != ISIS_F64 && d.prec != ISIS_F32 && d.prec != ISIS_F32_REFINE64) return false;
   if (d.inner_cycles < 1 || d.inner_cycles > 16) return false;
   if (d.init != ISIS_INIT_INPUT && d.init != ISIS_INIT_BACKGROUND && d.init != ISIS_INIT_LOCAL) return false;
+  if (d.fmg != 0 && d.fmg != 1) return false;
   *out = d;
   return true;
 }
@@ -223,6 +224,7 @@ static void fill_common(SolveArgs& A, const isis_grid* g, double a, const void* 
   A.inner = o.inner_cycles;
   A.prec = o.prec;
   A.init = o.init;
+  A.fmg = o.fmg;
   A.info = info;
   A.st = (cudaStream_t)stream;
   std::memset(&A.coef, 0, sizeof(A.coef));
@@ -384,7 +386,7 @@ static isis_status patch_common(PatchArgs& P, const isis_grid* grid, double a, c
                                 const void* parent, const uint8_t* flags, const void* eta, void* phi, double tol,
                                 const isis_mg_opts* opts, isis_solve_info* info, void* stream) {
   if (!grid_ok(grid) || !box || !parent || !flags || !eta || !phi || !(a > 0) || !(tol >= 0)) return ISIS_EINVAL;
-  isis_mg_opts o = {2, 2, 4, 100, ISIS_F64, 2, ISIS_INIT_INPUT};
+  isis_mg_opts o = {2, 2, 4, 100, ISIS_F64, 2, ISIS_INIT_INPUT, 0};
   if (opts) o = *opts;
   if (o.nu1 < 0 || o.nu1 > 16 || o.nu2 < 0 || o.nu2 > 16 || o.max_cycles < 0 || o.max_cycles > 128) return ISIS_EINVAL;
   if (o.prec != ISIS_F64 || (o.init != ISIS_INIT_INPUT && o.init != ISIS_INIT_PARENT)) return ISIS_EINVAL;

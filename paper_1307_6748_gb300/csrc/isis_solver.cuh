@@ -61,6 +61,7 @@ struct SolveArgs {
   int nu1, nu2, ncoarse, max_cycles, inner;
   isis_precision prec;
   isis_init init;
+  int fmg;  // nested-iteration start of the FP32 phase (ISIS_F32_REFINE64)
   isis_solve_info* info;
   cudaStream_t st;
   // reference residual: ref = ref_scale * RMS(eta - eta_ref) (eta_ref = <eta> for Poisson)
@@ -189,6 +190,34 @@ struct Cycler {
                 (prolong_correct<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], C.x, (const T*)ws->x0[l + 1],
                                                                           C.lg)));
     return smooth(l, nu2);
+  }
+
+  // Nested iteration (full multigrid start): the guess on level 0 is restricted to every level (R, the
+  // full-approximation restriction); the coarsest level's own problem (Sigma = 0) is solved; then on each
+  // finer level the coarse correction P(x_{l+1} - R x_l) is added to the restricted guess and one V-cycle
+  // is run on that level's own problem.  Level 0 must be the finest level with no Sigma.
+  isis_status fmg() {
+    const int last = (int)L.size() - 1;
+    for (int l = 1; l <= last; ++l) {
+      LevelView<T>& C = L[l];
+      size_t nc = (size_t)C.N * C.N * C.N;
+      ISIS_LAUNCH(KK_SETUP, 9.0 * nc * sizeof(T), st,
+                  (restrict_mean<T, T><<<nblk(nc, 256), 256, 0, st>>>(L[l - 1].x, C.x, C.lg)));
+      ISIS_CK(cudaMemcpyAsync(ws->x0[l], C.x, nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      ISIS_CK(cudaMemsetAsync(ws->sig[l], 0, nc * sizeof(T), st));
+    }
+    isis_status s = vcycle(last);
+    if (s != ISIS_OK) return s;
+    for (int l = last - 1; l >= 0; --l) {
+      LevelView<T>& C = L[l + 1];
+      size_t nc = (size_t)C.N * C.N * C.N;
+      ISIS_LAUNCH(l == 0 ? KK_PROLONG_FINE : KK_PROLONG_COARSE, sizeof(T) * (2 * (double)nc + 2 * cells(L[l])), st,
+                  (prolong_correct<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], C.x, (const T*)ws->x0[l + 1],
+                                                                            C.lg)));
+      s = vcycle(l);
+      if (s != ISIS_OK) return s;
+    }
+    return ISIS_OK;
   }
 
   // RMS of L(x) - Sigma on the finest level (blocking: one stream sync).
@@ -516,7 +545,7 @@ isis_status solve_field(const SolveArgs& A) {
 // Relative residual (of the reference) below which the FP32 field-form
 // cycles hand over to the FP64 defect correction, and the per-cycle
 // reduction above which they are taken to have reached FP32 rounding.
-constexpr double kSwitchRel = 1e-4;
+constexpr double kSwitchRel = 2e-4;
 constexpr double kStallRatio = 0.5;
 
 // FP32 cycles + FP64 defect correction.
@@ -597,8 +626,10 @@ isis_status solve_refine(const SolveArgs& A) {
     loc.res_ref = ref;
     double prev = res;
     double handover = std::fmax(A.tol, kSwitchRel) * ref;
+    bool nested = A.fmg != 0;
     while (res > handover && loc.cycles < A.max_cycles && std::isfinite(res)) {
-      s = cy.vcycle(0);
+      s = nested ? cy.fmg() : cy.vcycle(0);
+      nested = false;
       if (s != ISIS_OK) return s;
       s = cy.fine_rms(&res);
       loc.cycles += 1;

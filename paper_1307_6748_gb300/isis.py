@@ -44,7 +44,7 @@ class isis_params(ctypes.Structure):
 class isis_mg_opts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("n_coarsest", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("prec", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-                ("init", ctypes.c_int)]
+                ("init", ctypes.c_int), ("fmg", ctypes.c_int)]
 
 
 class isis_patch(ctypes.Structure):
@@ -157,10 +157,11 @@ class Opts:
     prec: int = ISIS_F64
     inner_cycles: int = 2
     init: int = ISIS_INIT_INPUT
+    fmg: int = 0  # ISIS_F32_REFINE64: nested-iteration start of the FP32 phase
 
     def c(self):
         return isis_mg_opts(self.nu1, self.nu2, self.n_coarsest, self.max_cycles, self.prec, self.inner_cycles,
-                            self.init)
+                            self.init, self.fmg)
 
 
 @dataclass

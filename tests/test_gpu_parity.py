@@ -92,14 +92,16 @@ def test_poisson_sinusoid_exact(cuda_lib):
     assert np.abs(Phi.cpu().numpy() - exact).max() <= 1e-9 * np.abs(exact).max()
 
 
+@pytest.mark.parametrize("fmg", [0, 1])
 @pytest.mark.parametrize("model", [oracle.SYMMETRON, oracle.FOFR, oracle.POISSON])
-def test_refine64_matches_oracle(cuda_lib, model):
-    """FP32 correction cycles + FP64 defect correction vs the converged FP64 oracle."""
+def test_refine64_matches_oracle(cuda_lib, model, fmg):
+    """FP32 correction cycles + FP64 defect correction vs the converged FP64 oracle, with and without the
+    nested-iteration start of the FP32 phase."""
     isis = cuda_lib
     N, box = 64, 128.0
     par = isis.Params()
     eta = synth.lognormal_eta(N, box, 1.0, 1)
-    opts = isis.Opts(prec=isis.ISIS_F32_REFINE64)
+    opts = isis.Opts(prec=isis.ISIS_F32_REFINE64, fmg=fmg)
     if model == oracle.POISSON:
         phi = torch.zeros((N,) * 3, dtype=torch.float64, device="cuda")
         info = isis.isis_poisson_solve(isis.Grid(N, box), A1, eta.cuda(), phi, tol=1e-10, opts=opts)
@@ -259,14 +261,15 @@ def test_streaming_f32_fixed_cycles_128(cuda_lib, model):
         assert err <= (2e-6 if model == oracle.SYMMETRON else 2e-5), err
 
 
-@pytest.mark.parametrize("model,N", [(oracle.SYMMETRON, 128), (oracle.FOFR, 128), (oracle.POISSON, 128),
-                                     (oracle.SYMMETRON, 256)])
-def test_refine64_streaming_matches_oracle(cuda_lib, model, N):
+@pytest.mark.parametrize("model,N,fmg", [(oracle.SYMMETRON, 128, 0), (oracle.FOFR, 128, 0), (oracle.POISSON, 128, 0),
+                                         (oracle.SYMMETRON, 256, 0), (oracle.FOFR, 128, 1), (oracle.POISSON, 128, 1),
+                                         (oracle.SYMMETRON, 256, 1)])
+def test_refine64_streaming_matches_oracle(cuda_lib, model, N, fmg):
     isis = cuda_lib
     box = float(N)
     par = isis.Params()
     eta = synth.lognormal_eta(N, box, 1.0, 2)
-    opts = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=3)
+    opts = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=3, fmg=fmg)
     if model == oracle.POISSON:
         phi = torch.zeros((N,) * 3, dtype=torch.float64, device="cuda")
         info = isis.isis_poisson_solve(isis.Grid(N, box), A1, eta.cuda(), phi, tol=1e-10, opts=opts)
