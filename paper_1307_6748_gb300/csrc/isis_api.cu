@@ -67,7 +67,8 @@ Workspace* get_workspace(int N, int esize, int ncoarse) {
     w->iflags = (int*)alloc(8 * sizeof(int));
     ok = w->part && w->part2 && w->scal && w->iflags;
   }
-  if (ok && cudaMallocHost(&w->host, 256) != cudaSuccess) ok = false;
+  if (ok && cudaHostAlloc(&w->host, 256, cudaHostAllocMapped) != cudaSuccess) ok = false;
+  if (ok && cudaHostGetDevicePointer((void**)&w->host_dev, w->host, 0) != cudaSuccess) ok = false;
   if (ok) {
     w->exptab_ff = (float2*)alloc(64 * sizeof(float2));
     float2 tab[64];

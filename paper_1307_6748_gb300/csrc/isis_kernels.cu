@@ -23,6 +23,13 @@ __global__ void __launch_bounds__(kNormThreads) reduce_final(const double* __res
   }
 }
 
+__global__ void publish_scalars(const double* __restrict__ scal, int ns, const int* __restrict__ iflags, int ni,
+                                double* hd, int* hi) {
+  const int t = threadIdx.x;
+  if (t < ns) hd[t] = scal[t];
+  if (t < ni) hi[t] = iflags[t];
+}
+
 }  // namespace isis
 
 namespace isis {

@@ -644,5 +644,10 @@ __global__ void __launch_bounds__(kNormThreads) moments_partial(const T* __restr
 
 // One block sums nparts partials in a fixed order into *out.
 __global__ void reduce_final(const double* __restrict__ part, int nparts, double* __restrict__ out);
+// Scalars and flags for the host, written by a kernel into mapped pinned memory (hd, hi: its device
+// addresses): the per-cycle readback of the solvers uses no copy engine, so it never queues behind the
+// caller's bulk host<->device copies on other streams.
+__global__ void publish_scalars(const double* __restrict__ scal, int ns, const int* __restrict__ iflags, int ni,
+                                double* hd, int* hi);
 
 }  // namespace isis

@@ -37,7 +37,8 @@ struct Workspace {
   double* part2 = nullptr;    // second set of partials
   double* scal = nullptr;     // device scalars: [0] norm^2, [1] sum, [2] aux
   int* iflags = nullptr;      // [0] coarse flags, [1] coarse steps max
-  void* host = nullptr;       // pinned readback area
+  void* host = nullptr;       // mapped pinned readback area: [0..3] doubles, then ints at (int*)(host + 4)
+  double* host_dev = nullptr;  // its device address
   float2* exptab_ff = nullptr;  // 2^(j/64), j < 64, float-float, for exp_ff
   double* b64 = nullptr;      // finest level, 8 bytes per cell: psi = u - u_bar (float-float), f(R) residual
   double* s64 = nullptr;      // finest level, 8 bytes per cell: e^psi (float-float), f(R) residual
@@ -237,8 +238,8 @@ struct Cycler {
     ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
     double* h = (double*)ws->host;
     int* hi = (int*)(h + 4);
-    ISIS_CK(cudaMemcpyAsync(h, ws->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
-    ISIS_CK(cudaMemcpyAsync(hi, ws->iflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    ISIS_LAUNCH(KK_REDUCE, 0.0, st,
+                (publish_scalars<<<1, 32, 0, st>>>(ws->scal, 1, ws->iflags, 2, ws->host_dev, (int*)(ws->host_dev + 4))));
     ISIS_CK(cudaStreamSynchronize(st));
     size_t n = (size_t)L[0].N * L[0].N * L[0].N;
     *out = std::sqrt(h[0] / (double)n);
@@ -260,7 +261,8 @@ isis_status moments(Workspace* ws, const T* v, size_t n, double shift, cudaStrea
   ISIS_LAUNCH(KK_REDUCE, 0.0, st,
               (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part2, kNormBlocks, ws->scal + 1)));
   double* h = (double*)ws->host;
-  ISIS_CK(cudaMemcpyAsync(h, ws->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  ISIS_LAUNCH(KK_REDUCE, 0.0, st,
+              (publish_scalars<<<1, 32, 0, st>>>(ws->scal, 2, ws->iflags, 0, ws->host_dev, (int*)(ws->host_dev + 4))));
   ISIS_CK(cudaStreamSynchronize(st));
   *s2 = h[0];
   *s1 = h[1];
@@ -709,8 +711,8 @@ isis_status solve_refine(const SolveArgs& A) {
                                                                               ws->part)));
     }
     ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
-    ISIS_CK(cudaMemcpyAsync(h, ws->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
-    ISIS_CK(cudaMemcpyAsync(hi, ws->iflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    ISIS_LAUNCH(KK_REDUCE, 0.0, st,
+                (publish_scalars<<<1, 32, 0, st>>>(ws->scal, 1, ws->iflags, 2, ws->host_dev, (int*)(ws->host_dev + 4))));
     ISIS_CK(cudaStreamSynchronize(st));
     double res = std::sqrt(h[0] / (double)n);
     if (outer > 0 && nh < 128) loc.hist[nh++] = res;
