@@ -46,6 +46,14 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
   s.lo += t.lo;
   return ff_quick_two_sum(s.hi, s.lo);
 }
+// Dekker's addition: one exact sum of the high parts, the low parts added in FP32.  Its error is about
+// ulp of the low parts, 2^-48 of the larger input: absolute accuracy, which is what the stencil
+// differences and their sums need (ff_add keeps relative accuracy under cancellation, at twice the cost).
+__device__ __forceinline__ ff ff_add_abs(ff a, ff b) {
+  ff s = ff_two_sum(a.hi, b.hi);
+  s.lo += a.lo + b.lo;
+  return ff_quick_two_sum(s.hi, s.lo);
+}
 __device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
 __device__ __forceinline__ ff ff_add_f(ff a, float b) {
@@ -69,6 +77,30 @@ __device__ __forceinline__ ff ff_ldexp(ff a, int m) { return {ldexpf(a.hi, m), l
 __device__ __forceinline__ ff ff_from_double(double d) {
   const float hi = __double2float_rn(d);
   return {hi, __double2float_rn(d - (double)hi)};
+}
+// FP64 -> float-float without the FP64 units, for the bulk conversions of the FP64 residual (GB300 runs
+// FP64<->FP32 conversions on its few FP64 units): by integer operations on the bit pattern, hi = d with its
+// significand cut to 24 bits and lo = the remaining 29 bits cut to 24 significant bits, so
+// |d - (hi + lo)| < 2^-47 |d|, hi and lo of d's sign.  |d| < 2^-70 (zero included) gives a signed zero,
+// |d| >= 2^127 gives +-Inf and NaN stays NaN (so a non-finite field still shows in the residual norm).
+// No FP64 instruction, not even on a branch the compiler might predicate.
+__device__ __forceinline__ ff ff_split_bits(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
+  const unsigned sgn = h & 0x80000000u;
+  const int ef = (int)((h >> 20) & 0x7FFu), e = ef - 1023;
+  if (e > 126) {
+    const bool nan = ef == 0x7FF && (((h & 0xFFFFFu) | l) != 0u);
+    return {__uint_as_float(sgn | 0x7F800000u | (nan ? 0x400000u : 0u)), 0.0f};
+  }
+  if (e < -70) return {__uint_as_float(sgn), 0.0f};
+  const float hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29));
+  const unsigned rem = l & 0x1FFFFFFFu;  // the significand bits below hi's, in units of 2^(e - 52)
+  if (rem == 0u) return {hi, 0.0f};
+  const int top = 31 - __clz(rem);  // position of the leading one, 0..28
+  const unsigned man = top >= 23 ? (rem >> (top - 23)) : (rem << (23 - top));
+  const float lo = __uint_as_float(sgn | ((unsigned)(e - 52 + top + 127) << 23) | (man & 0x7FFFFFu));
+  return {hi, lo};
 }
 __device__ __forceinline__ ff ff_load(const float2& v) { return {v.x, v.y}; }
 __device__ __forceinline__ float2 ff_store(ff a) { return make_float2(a.hi, a.lo); }

@@ -86,17 +86,16 @@ __global__ void selftest_exp_ff(const double* __restrict__ x, double* __restrict
 }
 
 __global__ void fofr_prep_ff(const double* __restrict__ u, float2* __restrict__ psi, float2* __restrict__ E,
-                             size_t n, double ub, const float2* __restrict__ tab, FFExp ek) {
+                             size_t n, float2 ubff, const float2* __restrict__ tab, FFExp ek) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const double d = u[t] - ub;
-  const ff p = ff_from_double(d);
+  const ff p = ff_sub(ff_split_bits(u[t]), ff_load(ubff));
   psi[t] = ff_store(p);
   // exp_ff covers |psi| < 22; beyond (no physical field gets there) the FP64 library exp
-  E[t] = ff_store(fabs(d) < 20.0 ? exp_ff(p, tab, ek) : ff_from_double(exp(d)));
+  E[t] = ff_store(fabsf(p.hi) < 20.0f ? exp_ff(p, tab, ek) : ff_from_double(exp((double)p.hi + (double)p.lo)));
 }
 
-__global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, FofrFF c, const double* __restrict__ u,
+__global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, FofrFF c,
                                                                        const double* __restrict__ eta,
                                                                        const float2* __restrict__ psi,
                                                                        const float2* __restrict__ E,
@@ -119,21 +118,21 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, F
     ff sd = {0.f, 0.f}, se = {0.f, 0.f};
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
-      const ff dp = ff_sub(ff_load(psi[nb[d]]), pc);
-      sd = ff_add(sd, dp);
-      se = ff_add(se, ff_mul(ff_load(E[nb[d]]), dp));
+      const ff dp = ff_add_abs(ff_load(psi[nb[d]]), ff_neg(pc));
+      sd = ff_add_abs(sd, dp);
+      se = ff_add_abs(se, ff_mul(ff_load(E[nb[d]]), dp));
     }
     ff flux = ff_add(ff_mul(ec, sd), se);
     flux = {0.5f * flux.hi, 0.5f * flux.lo};
-    const double dpsi = (double)pc.hi + (double)pc.lo;
-    const ff em = fabs(dpsi) < 20.0 ? ff_add_f(exp_ff(ff_mul(pc, minv), stab, c.ek), -1.0f)
-                                     : ff_from_double(expm1(-dpsi * c.inv_np1));
-    ff S = ff_sub(ff_mul(K1, ff_from_double(eta[t] - 1.0)), ff_mul(Kx, em));
+    const ff em = fabsf(pc.hi) < 20.0f
+                      ? ff_add_f(exp_ff(ff_mul(pc, minv), stab, c.ek), -1.0f)
+                      : ff_from_double(expm1(-((double)pc.hi + (double)pc.lo) * c.inv_np1));
+    ff S = ff_sub(ff_mul(K1, ff_add_f(ff_split_bits(eta[t]), -1.0f)), ff_mul(Kx, em));
     S = ff_add_f(S, c.dK);
     const ff F = ff_sub(ff_mul(flux, Cih2), S);
     const size_t o = lidx<float>(lg, i, j, k);
     r32[o] = -(F.hi + F.lo);
-    B32[o] = (float)u[t];
+    B32[o] = ff_add(pc, ff_load(c.ubff)).hi;  // fp32(u), u = psi + ub
     acc = fmaf(F.hi, F.hi, acc);
   }
   block_sum_store<double>((double)acc, part);

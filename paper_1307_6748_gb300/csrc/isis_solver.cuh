@@ -380,15 +380,15 @@ isis_status apply_init(const SolveArgs& A, const Coef& c, T* phi, const T* eta, 
 struct ResFF {
   float2 ih2;          // 1/h^2
   float2 K;            // Poisson: 1.5 Omega_m H0^2 / a; symmetron: A = a^2 / (2 lambda0^2)
-  double s, eta_mean;  // symmetron: (a_SSB/a)^3; Poisson: mean density
+  float2 s, eta_mean;  // symmetron: (a_SSB/a)^3; Poisson: mean density (float-float)
 };
 static __global__ void phi_to_ff(const double* __restrict__ phi, float2* __restrict__ out, size_t n) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) out[t] = ff_store(ff_from_double(phi[t]));
+  if (t < n) out[t] = ff_store(ff_split_bits(phi[t]));
 }
+// r = -L(phi) in float-float from phi's float-float copy pff; B = the copy's high part (fp32 phi).
 template <Model M>
-__global__ void __launch_bounds__(kNormThreads) outer_residual_ff(int lg, ResFF c, const double* __restrict__ phi,
-                                                                  const double* __restrict__ eta,
+__global__ void __launch_bounds__(kNormThreads) outer_residual_ff(int lg, ResFF c, const double* __restrict__ eta,
                                                                   const float2* __restrict__ pff,
                                                                   float* __restrict__ r32, float* __restrict__ B32,
                                                                   double* __restrict__ part) {
@@ -403,19 +403,20 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_ff(int lg, ResFF 
     const ff pc = ff_load(pff[t]);
     ff sd = {0.f, 0.f};
 #pragma unroll
-    for (int d = 0; d < 6; ++d) sd = ff_add(sd, ff_sub(ff_load(pff[nb[d]]), pc));
+    for (int d = 0; d < 6; ++d) sd = ff_add_abs(sd, ff_add_abs(ff_load(pff[nb[d]]), ff_neg(pc)));
     const ff lap = ff_mul(sd, ih2);
     ff F;
+    const ff et = ff_split_bits(eta[t]);
     if constexpr (M == POI) {
-      F = ff_sub(lap, ff_mul(K, ff_from_double(eta[t] - c.eta_mean)));
+      F = ff_sub(lap, ff_mul(K, ff_sub(et, ff_load(c.eta_mean))));
     } else {  // symmetron: L = lap - A [(s eta - 1) chi + chi^3]
-      const ff q = ff_from_double(fma(c.s, eta[t], -1.0));
+      const ff q = ff_add_f(ff_mul(ff_load(c.s), et), -1.0f);
       const ff x2 = ff_mul(pc, pc);
       F = ff_sub(lap, ff_mul(K, ff_mul(ff_add(q, x2), pc)));
     }
     const size_t o = lidx<float>(lg, i, j, k);
     r32[o] = -(F.hi + F.lo);
-    B32[o] = (float)phi[t];
+    B32[o] = pc.hi;
     acc = fmaf(F.hi, F.hi, acc);
   }
   block_sum_store<double>((double)acc, part);
@@ -426,6 +427,7 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_ff(int lg, ResFF 
 struct FofrFF {
   double ub, inv_np1;
   float2 Cih2, K1, Kx, minv;  // C / h^2, K1, Kx = K2 e^{-ub/(n+1)}, -1/(n+1) (float-float)
+  float2 ubff;                // ub (float-float)
   float dK;                   // K3 - Kx (zero up to rounding)
   FFExp ek;
 };
@@ -433,9 +435,9 @@ __global__ void selftest_exp_ff(const double* __restrict__ x, double* __restrict
                                 const float2* __restrict__ tab, FFExp ek);
 // first pass: psi = u - ub and e^psi per cell (float-float, 8 bytes each)
 __global__ void fofr_prep_ff(const double* __restrict__ u, float2* __restrict__ psi, float2* __restrict__ E,
-                             size_t n, double ub, const float2* __restrict__ tab, FFExp ek);
+                             size_t n, float2 ubff, const float2* __restrict__ tab, FFExp ek);
 // second pass: r = -L(u) (written FP32, red/black), B = fp32(u), block partials of r^2
-__global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, FofrFF c, const double* __restrict__ u,
+__global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, FofrFF c,
                                                                        const double* __restrict__ eta,
                                                                        const float2* __restrict__ psi,
                                                                        const float2* __restrict__ E,
@@ -672,8 +674,8 @@ isis_status solve_refine(const SolveArgs& A) {
   ResFF rff{};
   rff.ih2 = ff_split_host(F64.ih2);
   rff.K = ff_split_host(M == POI ? c.KP : c.A);
-  rff.s = c.s;
-  rff.eta_mean = c.eta_mean;
+  rff.s = ff_split_host(c.s);
+  rff.eta_mean = ff_split_host(c.eta_mean);
   FofrFF ffc{};
   if (M == FOFR) {
     const double ub = background_value<FOFR>(c), Kx = c.K2 * std::exp(-ub * c.inv_np1);
@@ -683,6 +685,7 @@ isis_status solve_refine(const SolveArgs& A) {
     ffc.K1 = ff_split_host(c.K1);
     ffc.Kx = ff_split_host(Kx);
     ffc.minv = ff_split_host(-c.inv_np1);
+    ffc.ubff = ff_split_host(ub);
     ffc.dK = (float)(c.K3 - Kx);
     ffc.ek = ff_exp_consts();
   }
@@ -699,15 +702,16 @@ isis_status solve_refine(const SolveArgs& A) {
       float2* psi_ff = reinterpret_cast<float2*>(ws->b64);
       float2* E_ff = reinterpret_cast<float2*>(ws->s64);
       ISIS_LAUNCH(KK_OUTER_RESID, 24.0 * n, st,
-                  (fofr_prep_ff<<<nblk(n, 256), 256, 0, st>>>(phi64, psi_ff, E_ff, n, ffc.ub, ws->exptab_ff, ffc.ek)));
-      ISIS_LAUNCH(KK_OUTER_RESID, 40.0 * n, st,
-                  (outer_residual_fofr_ff<<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, ffc, phi64, eta64, psi_ff, E_ff,
+                  (fofr_prep_ff<<<nblk(n, 256), 256, 0, st>>>(phi64, psi_ff, E_ff, n, ffc.ubff, ws->exptab_ff,
+                                                               ffc.ek)));
+      ISIS_LAUNCH(KK_OUTER_RESID, 32.0 * n, st,
+                  (outer_residual_fofr_ff<<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, ffc, eta64, psi_ff, E_ff,
                                                                                  ws->exptab_ff, r0, B0, ws->part)));
     } else {
       float2* pff = reinterpret_cast<float2*>(ws->b64);
       ISIS_LAUNCH(KK_OUTER_RESID, 16.0 * n, st, (phi_to_ff<<<nblk(n, 256), 256, 0, st>>>(phi64, pff, n)));
-      ISIS_LAUNCH(KK_OUTER_RESID, 24.0 * n, st,
-                  (outer_residual_ff<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, rff, phi64, eta64, pff, r0, B0,
+      ISIS_LAUNCH(KK_OUTER_RESID, 16.0 * n, st,
+                  (outer_residual_ff<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, rff, eta64, pff, r0, B0,
                                                                               ws->part)));
     }
     ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
