@@ -102,6 +102,15 @@ __device__ __forceinline__ ff ff_split_bits(double d) {
   const float lo = __uint_as_float(sgn | ((unsigned)(e - 52 + top + 127) << 23) | (man & 0x7FFFFFu));
   return {hi, lo};
 }
+// FP32 -> FP64, exact, by integer operations (no FP64 unit): zero and subnormal floats give a signed
+// zero, Inf and NaN stay Inf and NaN.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sgn = u & 0x80000000u, ef = (u >> 23) & 0xFFu, man = u & 0x7FFFFFu;
+  if (ef == 0u) return __hiloint2double((int)sgn, 0);
+  const unsigned e = ef == 0xFFu ? 0x7FFu : ef - 127u + 1023u;
+  return __hiloint2double((int)(sgn | (e << 20) | (man >> 3)), (int)(man << 29));
+}
 __device__ __forceinline__ ff ff_load(const float2& v) { return {v.x, v.y}; }
 __device__ __forceinline__ float2 ff_store(ff a) { return make_float2(a.hi, a.lo); }
 

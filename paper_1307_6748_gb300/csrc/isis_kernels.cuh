@@ -18,6 +18,7 @@
 // sits at colour * N^3/2 + g/2.  A one-colour half-sweep then reads the
 // other colour's half and its own half contiguously, with no wasted sectors.
 #pragma once
+#include "isis_ff.cuh"
 #include "isis_model.cuh"
 
 namespace isis {
@@ -627,15 +628,31 @@ __global__ void __launch_bounds__(kNormThreads) norm_rb2(LevelView<float> L, Coe
 
 // Sum of (v - shift)^2 and of v over an array (for the reference residual
 // and the Poisson mean).
-template <class T>
+template <class T, bool kFast = false>
 __global__ void __launch_bounds__(kNormThreads) moments_partial(const T* __restrict__ v, size_t n, double shift,
                                                                 double* __restrict__ part2,
                                                                 double* __restrict__ part1) {
   double a2 = 0.0, a1 = 0.0;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    double d = (double)v[t] - shift;
-    a2 += d * d;
-    a1 += (double)v[t];
+  if constexpr (sizeof(T) == 8 && kFast) {
+    // FP64 fields without the FP64 units (the mixed-precision solves): the sum in float-float (Poisson needs
+    // the mean to ~1e-14), the square sum (a scale for the tolerance) in FP32 per thread
+    ff s1 = {0.f, 0.f};
+    float s2 = 0.f;
+    const float sh = (float)shift;  // 0 or 1: exact
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+      const ff x = ff_split_bits((double)v[t]);
+      s1 = ff_add(s1, x);
+      const float d = ff_add_f(x, -sh).hi;
+      s2 = fmaf(d, d, s2);
+    }
+    a1 = (double)s1.hi + (double)s1.lo;
+    a2 = (double)s2;
+  } else {
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+      double d = (double)v[t] - shift;
+      a2 += d * d;
+      a1 += (double)v[t];
+    }
   }
   block_sum_store<T>(a2, part2);
   __syncthreads();

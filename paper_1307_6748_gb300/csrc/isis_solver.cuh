@@ -253,10 +253,10 @@ struct Cycler {
 // ---------------------------------------------------------------------------
 
 // sum((v - shift)^2) and sum(v) over n values (blocking).
-template <class T>
+template <class T, bool kFast = false>
 isis_status moments(Workspace* ws, const T* v, size_t n, double shift, cudaStream_t st, double* s2, double* s1) {
   ISIS_LAUNCH(KK_REDUCE, (double)n * sizeof(T), st,
-              (moments_partial<T><<<kNormBlocks, kNormThreads, 0, st>>>(v, n, shift, ws->part, ws->part2)));
+              (moments_partial<T, kFast><<<kNormBlocks, kNormThreads, 0, st>>>(v, n, shift, ws->part, ws->part2)));
   ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
   ISIS_LAUNCH(KK_REDUCE, 0.0, st,
               (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part2, kNormBlocks, ws->scal + 1)));
@@ -276,10 +276,10 @@ __global__ void add_scalar(T* __restrict__ v, size_t n, const double* __restrict
 }
 
 // v -= mean(v), device-side (no host sync): partial sums, final sum, subtract.
-template <class T>
+template <class T, bool kFast = false>
 isis_status remove_mean(Workspace* ws, T* v, size_t n, cudaStream_t st) {
   ISIS_LAUNCH(KK_REDUCE, (double)n * sizeof(T), st,
-              (moments_partial<T><<<kNormBlocks, kNormThreads, 0, st>>>(v, n, 0.0, ws->part, ws->part2)));
+              (moments_partial<T, kFast><<<kNormBlocks, kNormThreads, 0, st>>>(v, n, 0.0, ws->part, ws->part2)));
   ISIS_LAUNCH(KK_REDUCE, 0.0, st,
               (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part2, kNormBlocks, ws->scal + 1)));
   ISIS_LAUNCH(KK_REDUCE, 2.0 * n * sizeof(T), st,
@@ -299,29 +299,36 @@ __global__ void to_rb(const Tin* __restrict__ a, float* __restrict__ b, int lg) 
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ((size_t)1 << (3 * lg))) return;
   const int m = (1 << lg) - 1;
-  b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))] = (float)a[t];
+  float v;
+  if constexpr (sizeof(Tin) == 8) v = ff_split_bits((double)a[t]).hi;  // no FP64 unit (truncated to 24 bits)
+  else v = (float)a[t];
+  b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))] = v;
 }
 template <class Tout>
 __global__ void from_rb(const float* __restrict__ b, Tout* __restrict__ a, int lg) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ((size_t)1 << (3 * lg))) return;
   const int m = (1 << lg) - 1;
-  a[t] = (Tout)b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
+  const float v = b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
+  if constexpr (sizeof(Tout) == 8) a[t] = f2d_bits(v);
+  else a[t] = (Tout)v;
 }
 
-// b (red/black FP32) = alpha * a + beta, a row-major FP64
-static __global__ void to_rb_affine(const double* __restrict__ a, float* __restrict__ b, int lg, double alpha, double beta) {
+// b (red/black FP32) = a - shift, a row-major FP64, shift float-float (FP32 arithmetic only)
+static __global__ void to_rb_shift(const double* __restrict__ a, float* __restrict__ b, int lg, float2 shift) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ((size_t)1 << (3 * lg))) return;
   const int m = (1 << lg) - 1;
-  b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))] = (float)(alpha * a[t] + beta);
+  b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))] =
+      ff_add(ff_split_bits(a[t]), ff_neg(ff_load(shift))).hi;
 }
-// a (row-major FP64) = shift + b, b red/black FP32
+// a (row-major FP64) = shift + b, b red/black FP32 (one FP64 addition only when shift != 0)
 static __global__ void from_rb_shift(const float* __restrict__ b, double* __restrict__ a, int lg, double shift) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ((size_t)1 << (3 * lg))) return;
   const int m = (1 << lg) - 1;
-  a[t] = shift + (double)b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
+  const double v = f2d_bits(b[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))]);
+  a[t] = shift != 0.0 ? shift + v : v;
 }
 template <class T>
 __global__ void exp_k(const T* __restrict__ a, T* __restrict__ b, size_t n) {
@@ -579,7 +586,7 @@ isis_status solve_refine(const SolveArgs& A) {
   float* B0 = (float*)ws->B[0];
 
   double s2, s1;
-  isis_status s = moments<double>(ws, eta64, n, 1.0, st, &s2, &s1);
+  isis_status s = moments<double, true>(ws, eta64, n, 1.0, st, &s2, &s1);
   if (s != ISIS_OK) return s;
   double eta_mean = s1 / (double)n;
   if (M == POI) {
@@ -615,7 +622,8 @@ isis_status solve_refine(const SolveArgs& A) {
     A1.coef.fscale = std::exp(u0);
     A1.coef.fKx = c.K2 * std::exp(-u0 * c.inv_np1);
     A1.coef.fK3x = c.K3 - A1.coef.fKx;
-    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (to_rb_affine<<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg, 1.0, -u0)));
+    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st,
+                (to_rb_shift<<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg, ff_split_host(u0))));
   } else {
     ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (to_rb<double><<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg)));
   }
@@ -652,7 +660,7 @@ isis_status solve_refine(const SolveArgs& A) {
     ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (from_rb_shift<<<nblk(n, 256), 256, 0, st>>>(psi, phi64, lg, u0)));
     // Poisson gauge: the residual does not see the mean, so it is removed once per phase
     if (M == POI) {
-      s = remove_mean<double>(ws, phi64, n, st);
+      s = remove_mean<double, true>(ws, phi64, n, st);
       if (s != ISIS_OK) return s;
     }
   }
@@ -759,7 +767,7 @@ isis_status solve_refine(const SolveArgs& A) {
     ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_phi64<<<nblk(n, 256), 256, 0, st>>>(phi64, ecur, lg)));
   }
   if (M == POI) {
-    s = remove_mean<double>(ws, phi64, n, st);
+    s = remove_mean<double, true>(ws, phi64, n, st);
     if (s != ISIS_OK) return s;
   }
   if (A.info) *A.info = loc;
