@@ -41,9 +41,11 @@ def parse():
     ap.add_argument("--box", type=float, default=256.0)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--inner-poisson", type=int, default=4, help="FP32 cycles per FP64 outer iteration")
-    ap.add_argument("--inner-sym", type=int, default=3)
+    ap.add_argument("--inner-sym", type=int, default=4)
     ap.add_argument("--inner-fofr", type=int, default=4)
     ap.add_argument("--ncoarse", type=int, default=2, help="coarsest grid (dense Newton): 2 or 4")
+    ap.add_argument("--nu1", type=int, default=2, help="pre-smoothing sweeps per level")
+    ap.add_argument("--nu2", type=int, default=1, help="post-smoothing sweeps per level")
     ap.add_argument("--sample-N", type=int, default=128, help="grid of the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -62,7 +64,7 @@ def workload(args):
                         f"forces of both models",
             "N": args.N, "box_mpc_h": args.box, "particles": args.N ** 3, "tol": args.tol,
             "symmetron": {"a": 1.0, "a_ssb": 0.5, "lambda0": 1.0, "beta": 1.0},
-            "fofr": {"n": 1, "fR0_abs": 1e-5}, "cycle": f"V(2,2), coarsest {args.ncoarse}^3 dense Newton"
+            "fofr": {"n": 1, "fR0_abs": 1e-5}, "cycle": f"V({args.nu1},{args.nu2}), coarsest {args.ncoarse}^3 dense Newton"
                                                         + (", FP32 phase started by nested iteration" if args.fmg else ""),
             "inner_cycles": {"poisson": args.inner_poisson, "symmetron": args.inner_sym, "fofr": args.inner_fofr},
             "initial_guess": {"symmetron": "U-Net (trained at 1 Mpc/h cells) on the 8-cell mean density, "
@@ -228,7 +230,7 @@ def main():
     g = [torch.empty(npart, device=dev, dtype=torch.float32) for _ in range(6)]
     def opts(inner):
         return isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=inner, init=isis.ISIS_INIT_BACKGROUND,
-                         n_coarsest=args.ncoarse, fmg=args.fmg)
+                         n_coarsest=args.ncoarse, fmg=args.fmg, nu1=args.nu1, nu2=args.nu2)
     o_poi, o_sym, o_fr = opts(args.inner_poisson), opts(args.inner_sym), opts(args.inner_fofr)
     net, pooled = None, False
     if args.guess == "net":
@@ -241,7 +243,7 @@ def main():
             raise SystemExit(f"bench: the net was trained at {h_net} Mpc/h cells; this grid has {h} Mpc/h")
         net = unet.UNet.load(args.weights, device=dev)
         o_sym = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=args.inner_sym, init=isis.ISIS_INIT_INPUT,
-                          n_coarsest=args.ncoarse, fmg=args.fmg)
+                          n_coarsest=args.ncoarse, fmg=args.fmg, nu1=args.nu1, nu2=args.nu2)
     stream = torch.cuda.current_stream()
     infos = {}
 
@@ -424,7 +426,9 @@ def main():
             for label, prec in (("fp64", isis.ISIS_F64), ("refine64", isis.ISIS_F32_REFINE64)):
                 o = isis.Opts(prec=prec, inner_cycles=prec_inner, init=isis.ISIS_INIT_BACKGROUND,
                               n_coarsest=args.ncoarse, max_cycles=40,
-                              fmg=args.fmg if prec == isis.ISIS_F32_REFINE64 else 0)
+                              fmg=args.fmg if prec == isis.ISIS_F32_REFINE64 else 0,
+                              nu1=args.nu1 if prec == isis.ISIS_F32_REFINE64 else 2,
+                              nu2=args.nu2 if prec == isis.ISIS_F32_REFINE64 else 2)
                 out = {"poisson": Phi, "symmetron": chi, "fofr": u}[name]
                 for rep in range(2):
                     barrier()
