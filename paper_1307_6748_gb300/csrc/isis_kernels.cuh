@@ -297,7 +297,7 @@ __device__ __forceinline__ void row4(int lg, int i, int j, int K, size_t* p) {
 // Same half-sweep, two cells of the colour per thread (places k2a, k2a + 1
 // of a row, float2 loads and stores; N >= 4).  The k neighbours of the pair
 // are the other colour's places k2a + par - 1 .. k2a + par + 1.
-template <Model M, Form FM>
+template <Model M, Form FM, bool kFill = true>
 __device__ __forceinline__ unsigned rb2_gather(const LevelView<float>& L, int color, unsigned t, Cell<float>& q0,
                                                Cell<float>& q1) {
   const int lg = L.lg;
@@ -349,9 +349,113 @@ __device__ __forceinline__ unsigned rb2_gather(const LevelView<float>& L, int co
     q0.B = q1.B = 0.f;
   }
   if constexpr (FM == DELTA && M == FOFR) nbrs(L.B, q0.Bn, q1.Bn);
-  fill_exps<M, FM, float>(q0);
-  fill_exps<M, FM, float>(q1);
+  if constexpr (kFill) {
+    fill_exps<M, FM, float>(q0);
+    fill_exps<M, FM, float>(q1);
+  }
   return o;
+}
+
+// ---- f(R) on the pair of cells of an rb2 thread, in packed FP32x2 arithmetic ----
+// Both cells go through the same operations, so they run as the two lanes of float2 instructions (one
+// fused multiply-add, add or multiply for a pair of FP32 operations; sm_100 family).  The f(R) sweeps are
+// bound by instruction issue, and this halves the issue count of their arithmetic.  The exponentials
+// remain one MUFU operation per lane.
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc(-1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 exp_2(float2 v) { return pk(__expf(v.x), __expf(v.y)); }
+
+// e^v - 1 of both lanes, the series of dexpm1<float> with its degree set by the larger |v|.
+__device__ __forceinline__ float2 expm1_2(float2 v) {
+  const float mx = fmaxf(fabsf(v.x), fabsf(v.y));
+  if (mx <= 0.0078125f) {
+    float2 p = fma2(v, bc(1.0f / 24.0f), bc(1.0f / 6.0f));
+    p = fma2(p, v, bc(0.5f));
+    p = fma2(p, v, bc(1.0f));
+    return mul2(p, v);
+  }
+  if (mx <= 0.5f) {
+    float2 p = fma2(v, bc(1.0f / 362880.0f), bc(1.0f / 40320.0f));
+    p = fma2(p, v, bc(1.0f / 5040.0f));
+    p = fma2(p, v, bc(1.0f / 720.0f));
+    p = fma2(p, v, bc(1.0f / 120.0f));
+    p = fma2(p, v, bc(1.0f / 24.0f));
+    p = fma2(p, v, bc(1.0f / 6.0f));
+    p = fma2(p, v, bc(0.5f));
+    p = fma2(p, v, bc(1.0f));
+    return mul2(p, v);
+  }
+  return pk(expf(v.x) - 1.0f, expf(v.y) - 1.0f);
+}
+
+// F = L(x) - Sigma and dF = dL/dx of both cells (the f(R) operators of fofr_field_eval and fofr_delta_eval),
+// from cells gathered without their exponentials.
+template <Form FM>
+__device__ __forceinline__ void fofr_pair_eval(const Coef& c, float ih2, const Cell<float>& q0,
+                                               const Cell<float>& q1, float2& F, float2& dF) {
+  const float2 half = bc(0.5f);
+  const float2 x = pk(q0.x, q1.x), sig = pk(q0.sig, q1.sig);
+  float2 flux = bc(0.0f), dsum = bc(0.0f);
+  if constexpr (FM == DELTA) {
+    const float2 B = pk(q0.B, q1.B);
+    const float2 w = exp_2(B);
+    const float2 m = mul2(w, expm1_2(x));
+    const float2 hbt = mul2(half, add2(w, m));
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const float2 Bn = pk(q0.Bn[d], q1.Bn[d]), en = pk(q0.xn[d], q1.xn[d]);
+      const float2 wn = exp_2(Bn);
+      const float2 mn = mul2(wn, expm1_2(en));
+      const float2 dB = sub2(Bn, B), de = sub2(en, x);
+      const float2 bf = fma2(half, add2(wn, mn), hbt);  // (bt + bt_nb) / 2
+      flux = fma2(mul2(half, add2(m, mn)), dB, fma2(bf, de, flux));
+      dsum = sub2(fma2(hbt, add2(dB, de), dsum), bf);
+    }
+    const float2 minv = bc(-(float)c.inv_np1);
+    const float2 exB = exp_2(mul2(B, minv)), em = expm1_2(mul2(x, minv));
+    const float2 K2 = bc((float)c.K2);
+    F = sub2(fma2(flux, bc(ih2), mul2(K2, mul2(exB, em))), sig);
+    dF = sub2(mul2(dsum, bc(ih2)), mul2(mul2(K2, bc((float)c.inv_np1)), mul2(exB, add2(em, bc(1.0f)))));
+  } else {
+    const float2 ex = exp_2(x), hex = mul2(half, ex);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const float2 xn = pk(q0.xn[d], q1.xn[d]);
+      const float2 du = sub2(xn, x);
+      const float2 ef = fma2(half, exp_2(xn), hex);
+      flux = fma2(ef, du, flux);
+      dsum = sub2(fma2(hex, du, dsum), ef);
+    }
+    const float2 fs = bc((float)c.fscale);
+    flux = mul2(flux, fs);
+    dsum = mul2(dsum, fs);
+    const float2 inp1 = bc((float)c.inv_np1), Kx = bc((float)c.fKx);
+    const float2 em = expm1_2(mul2(x, bc(-(float)c.inv_np1)));
+    const float2 S = add2(sub2(mul2(bc((float)c.K1), sub2(pk(q0.eta, q1.eta), bc(1.0f))), mul2(Kx, em)),
+                          bc((float)c.fK3x));
+    F = sub2(sub2(mul2(flux, bc(ih2)), S), sig);
+    dF = sub2(mul2(dsum, bc(ih2)), mul2(mul2(Kx, inp1), add2(em, bc(1.0f))));
+  }
+}
+
+// Gather and evaluate the two cells of an rb2 thread: the packed path for f(R), two eval_cell otherwise.
+template <Model M, Form FM>
+__device__ __forceinline__ unsigned rb2_eval(const LevelView<float>& L, const Coef& c, int color, unsigned t,
+                                             Cell<float>& q0, Cell<float>& q1, float2& F, float2& dF) {
+  if constexpr (M == FOFR) {
+    const unsigned o = rb2_gather<M, FM, false>(L, color, t, q0, q1);
+    fofr_pair_eval<FM>(c, L.ih2, q0, q1, F, dF);
+    return o;
+  } else {
+    const unsigned o = rb2_gather<M, FM>(L, color, t, q0, q1);
+    eval_cell<M, FM, float>(c, L.ih2, q0, F.x, dF.x);
+    eval_cell<M, FM, float>(c, L.ih2, q1, F.y, dF.y);
+    return o;
+  }
 }
 
 template <Model M, Form FM>
@@ -359,12 +463,10 @@ __global__ void __launch_bounds__(256) smooth_rb2(LevelView<float> L, Coef c, in
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (1u << (3 * L.lg - 2))) return;
   Cell<float> q0, q1;
-  const unsigned o = rb2_gather<M, FM>(L, color, t, q0, q1);
-  float F0, dF0, F1, dF1;
-  eval_cell<M, FM, float>(c, L.ih2, q0, F0, dF0);
-  eval_cell<M, FM, float>(c, L.ih2, q1, F1, dF1);
+  float2 F, dF;
+  const unsigned o = rb2_eval<M, FM>(L, c, color, t, q0, q1, F, dF);
   // FP32 cycles drive a correction: a 2-ulp quotient is ample there
-  const float xn0 = q0.x - __fdividef(F0, dF0), xn1 = q1.x - __fdividef(F1, dF1);
+  const float xn0 = q0.x - __fdividef(F.x, dF.x), xn1 = q1.x - __fdividef(F.y, dF.y);
   *reinterpret_cast<float2*>(L.x + o) = make_float2(xn0, xn1);
 }
 
@@ -378,11 +480,9 @@ __global__ void __launch_bounds__(256) resid_rb2(LevelView<float> L, Coef c, flo
   const int color = t >= q4 ? 1 : 0;
   t -= color ? q4 : 0u;
   Cell<float> q0, q1;
-  const unsigned o = rb2_gather<M, FM>(L, color, t, q0, q1);
-  float F0, dF0, F1, dF1;
-  eval_cell<M, FM, float>(c, L.ih2, q0, F0, dF0);
-  eval_cell<M, FM, float>(c, L.ih2, q1, F1, dF1);
-  *reinterpret_cast<float2*>(res + o) = make_float2(-F0, -F1);  // Sigma is inside F
+  float2 F, dF;
+  const unsigned o = rb2_eval<M, FM>(L, c, color, t, q0, q1, F, dF);
+  *reinterpret_cast<float2*>(res + o) = make_float2(-F.x, -F.y);  // Sigma is inside F
 }
 
 // x_H = R x, x0_H = x_H, Sigma_H = R res (res from resid_rb2), f(R) cache of x_H;
@@ -616,11 +716,9 @@ __global__ void __launch_bounds__(kNormThreads) norm_rb2(LevelView<float> L, Coe
   for (unsigned tt = blockIdx.x * blockDim.x + threadIdx.x; tt < 2 * q4; tt += gridDim.x * blockDim.x) {
     const int color = tt >= q4 ? 1 : 0;
     Cell<float> q0, q1;
-    rb2_gather<M, FM>(L, color, tt - (color ? q4 : 0u), q0, q1);
-    float F0, dF0, F1, dF1;
-    eval_cell<M, FM, float>(c, L.ih2, q0, F0, dF0);
-    eval_cell<M, FM, float>(c, L.ih2, q1, F1, dF1);
-    acc = fmaf(F0, F0, fmaf(F1, F1, acc));
+    float2 F, dF;
+    rb2_eval<M, FM>(L, c, color, tt - (color ? q4 : 0u), q0, q1, F, dF);
+    acc = fmaf(F.x, F.x, fmaf(F.y, F.y, acc));
   }
   block_sum_store<double>((double)acc, part);
 }
