@@ -103,7 +103,8 @@ typedef struct {
   int fmg;             /* ISIS_F32_REFINE64: 1 starts the FP32 phase with nested iteration (full multigrid):
                           the guess restricted to every level, the coarsest level's own problem solved,
                           then on each finer level the coarse correction prolongated onto the restricted
-                          guess and one V-cycle; counted as one cycle.  0: plain V-cycles.  Not in the paper
+                          guess and one V-cycle; counted as one cycle, and followed by a plain V-cycle
+                          before the first residual norm.  0: plain V-cycles.  Not in the paper
                           (its solver starts each level's V-cycles from a guess, Sect. 3.2). */
 } isis_mg_opts;
 

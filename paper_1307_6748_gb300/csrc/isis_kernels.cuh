@@ -367,18 +367,27 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc(-1.0f), a); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 exp_2(float2 v) { return pk(__expf(v.x), __expf(v.y)); }
+// e^v = 2^(v log2 e): one packed multiply, then the hardware base-2 exponential (MUFU) of each lane.
+__device__ __forceinline__ float ex2_approx(float t) {
+  float r;
+  asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(t));
+  return r;
+}
+__device__ __forceinline__ float2 exp_2(float2 v) {
+  const float2 t = mul2(v, bc(1.4426950408889634f));
+  return pk(ex2_approx(t.x), ex2_approx(t.y));
+}
 
-// e^v - 1 of both lanes, the series of dexpm1<float> with its degree set by the larger |v|.
-__device__ __forceinline__ float2 expm1_2(float2 v) {
-  const float mx = fmaxf(fabsf(v.x), fabsf(v.y));
-  if (mx <= 0.0078125f) {
+// e^v - 1 of both lanes by the series of dexpm1<float> of a fixed degree: DEG 4 for |v| <= 2^-7, DEG 9 for
+// |v| <= 1/2, DEG 0 for expf(v) - 1.
+template <int DEG>
+__device__ __forceinline__ float2 expm1_2d(float2 v) {
+  if constexpr (DEG == 4) {
     float2 p = fma2(v, bc(1.0f / 24.0f), bc(1.0f / 6.0f));
     p = fma2(p, v, bc(0.5f));
     p = fma2(p, v, bc(1.0f));
     return mul2(p, v);
-  }
-  if (mx <= 0.5f) {
+  } else if constexpr (DEG == 9) {
     float2 p = fma2(v, bc(1.0f / 362880.0f), bc(1.0f / 40320.0f));
     p = fma2(p, v, bc(1.0f / 5040.0f));
     p = fma2(p, v, bc(1.0f / 720.0f));
@@ -388,8 +397,36 @@ __device__ __forceinline__ float2 expm1_2(float2 v) {
     p = fma2(p, v, bc(0.5f));
     p = fma2(p, v, bc(1.0f));
     return mul2(p, v);
+  } else {
+    return pk(expf(v.x) - 1.0f, expf(v.y) - 1.0f);
   }
-  return pk(expf(v.x) - 1.0f, expf(v.y) - 1.0f);
+}
+// The same with the degree set by the larger |v| of the two lanes.
+__device__ __forceinline__ float2 expm1_2(float2 v) {
+  const float mx = fmaxf(fabsf(v.x), fabsf(v.y));
+  if (mx <= 0.0078125f) return expm1_2d<4>(v);
+  if (mx <= 0.5f) return expm1_2d<9>(v);
+  return expm1_2d<0>(v);
+}
+
+// The correction-form flux sums of both cells with every e^e - 1 of one degree.
+template <int DEG>
+__device__ __forceinline__ void fofr_delta_flux2(const Cell<float>& q0, const Cell<float>& q1, float2 x, float2 B,
+                                                 float2& m, float2& flux, float2& dsum) {
+  const float2 half = bc(0.5f);
+  const float2 w = exp_2(B);
+  m = mul2(w, expm1_2d<DEG>(x));
+  const float2 hbt = mul2(half, add2(w, m));
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const float2 Bn = pk(q0.Bn[d], q1.Bn[d]), en = pk(q0.xn[d], q1.xn[d]);
+    const float2 wn = exp_2(Bn);
+    const float2 mn = mul2(wn, expm1_2d<DEG>(en));
+    const float2 dB = sub2(Bn, B), de = sub2(en, x);
+    const float2 bf = fma2(half, add2(wn, mn), hbt);  // (bt + bt_nb) / 2
+    flux = fma2(mul2(half, add2(m, mn)), dB, fma2(bf, de, flux));
+    dsum = sub2(fma2(hbt, add2(dB, de), dsum), bf);
+  }
 }
 
 // F = L(x) - Sigma and dF = dL/dx of both cells (the f(R) operators of fofr_field_eval and fofr_delta_eval),
@@ -402,19 +439,14 @@ __device__ __forceinline__ void fofr_pair_eval(const Coef& c, float ih2, const C
   float2 flux = bc(0.0f), dsum = bc(0.0f);
   if constexpr (FM == DELTA) {
     const float2 B = pk(q0.B, q1.B);
-    const float2 w = exp_2(B);
-    const float2 m = mul2(w, expm1_2(x));
-    const float2 hbt = mul2(half, add2(w, m));
+    // one series degree for the corrections of both cells and their neighbours
+    float mx = fmaxf(fabsf(x.x), fabsf(x.y));
 #pragma unroll
-    for (int d = 0; d < 6; ++d) {
-      const float2 Bn = pk(q0.Bn[d], q1.Bn[d]), en = pk(q0.xn[d], q1.xn[d]);
-      const float2 wn = exp_2(Bn);
-      const float2 mn = mul2(wn, expm1_2(en));
-      const float2 dB = sub2(Bn, B), de = sub2(en, x);
-      const float2 bf = fma2(half, add2(wn, mn), hbt);  // (bt + bt_nb) / 2
-      flux = fma2(mul2(half, add2(m, mn)), dB, fma2(bf, de, flux));
-      dsum = sub2(fma2(hbt, add2(dB, de), dsum), bf);
-    }
+    for (int d = 0; d < 6; ++d) mx = fmaxf(mx, fmaxf(fabsf(q0.xn[d]), fabsf(q1.xn[d])));
+    float2 m;
+    if (mx <= 0.0078125f) fofr_delta_flux2<4>(q0, q1, x, B, m, flux, dsum);
+    else if (mx <= 0.5f) fofr_delta_flux2<9>(q0, q1, x, B, m, flux, dsum);
+    else fofr_delta_flux2<0>(q0, q1, x, B, m, flux, dsum);
     const float2 minv = bc(-(float)c.inv_np1);
     const float2 exB = exp_2(mul2(B, minv)), em = expm1_2(mul2(x, minv));
     const float2 K2 = bc((float)c.K2);

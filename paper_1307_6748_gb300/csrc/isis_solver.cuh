@@ -640,8 +640,16 @@ isis_status solve_refine(const SolveArgs& A) {
     double handover = std::fmax(A.tol, kSwitchRel) * ref;
     bool nested = A.fmg != 0;
     while (res > handover && loc.cycles < A.max_cycles && std::isfinite(res)) {
-      s = nested ? cy.fmg() : cy.vcycle(0);
-      nested = false;
+      if (nested) {
+        // the nested-iteration start leaves the residual near 1e-2 of the reference, far above the handover:
+        // the next V-cycle follows without a norm in between
+        nested = false;
+        s = cy.fmg();
+        if (s != ISIS_OK) return s;
+        loc.cycles += 1;
+        if (loc.cycles >= A.max_cycles) break;
+      }
+      s = cy.vcycle(0);
       if (s != ISIS_OK) return s;
       s = cy.fine_rms(&res);
       loc.cycles += 1;
