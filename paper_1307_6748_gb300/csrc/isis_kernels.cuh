@@ -691,6 +691,60 @@ __global__ void prolong_correct(LevelView<T> Fv, const T* __restrict__ xc, const
       }
 }
 
+// The same correction for FP32 red/black grids with at least 32 coarse cells per side, tiled: a block of
+// 2 x 4 x 32 coarse cells first stages the coarse correction D = xc - x0c of its tile and a one-cell halo
+// (4 x 6 x 34 values) in shared memory, so each D is read from global memory once per block instead of by
+// 27 threads, and each thread then updates the 8 children of its coarse cell (consecutive threads write
+// consecutive places of one colour half).
+constexpr int kPTI = 2, kPTJ = 4, kPTK = 32;
+template <Model M, Form FM>
+__global__ void __launch_bounds__(kPTI * kPTJ * kPTK) prolong_tiled(LevelView<float> Fv, const float* __restrict__ xc,
+                                                                   const float* __restrict__ x0c, int lgc) {
+  __shared__ float D[kPTI + 2][kPTJ + 2][kPTK + 2];
+  float* __restrict__ xf = Fv.x;
+  const int Nc = 1 << lgc, mc = Nc - 1, lgf = lgc + 1;
+  const int tk_blocks = Nc / kPTK, tj_blocks = Nc / kPTJ;
+  const int b = blockIdx.x;
+  const int K0 = (b % tk_blocks) * kPTK, J0 = ((b / tk_blocks) % tj_blocks) * kPTJ,
+            I0 = (b / (tk_blocks * tj_blocks)) * kPTI;
+  constexpr int kHalo = (kPTI + 2) * (kPTJ + 2) * (kPTK + 2);
+  for (int e = threadIdx.x; e < kHalo; e += blockDim.x) {
+    const int d = e % (kPTK + 2), r = e / (kPTK + 2), bb = r % (kPTJ + 2), a = r / (kPTJ + 2);
+    const size_t q = lidx<float>(lgc, (I0 + a - 1) & mc, (J0 + bb - 1) & mc, (K0 + d - 1) & mc);
+    D[a][bb][d] = xc[q] - x0c[q];
+  }
+  __syncthreads();
+  const int tk = threadIdx.x % kPTK, tj = (threadIdx.x / kPTK) % kPTJ, ti = threadIdx.x / (kPTK * kPTJ);
+  const float w3 = 0.75f, w1 = 0.25f;
+  float Tk[3][3][2], Tj[3][2][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb) {
+      const float c0 = D[ti + a][tj + bb][tk], c1 = D[ti + a][tj + bb][tk + 1], c2 = D[ti + a][tj + bb][tk + 2];
+      Tk[a][bb][0] = w3 * c1 + w1 * c0;
+      Tk[a][bb][1] = w3 * c1 + w1 * c2;
+    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      Tj[a][0][d] = w3 * Tk[a][1][d] + w1 * Tk[a][0][d];
+      Tj[a][1][d] = w3 * Tk[a][1][d] + w1 * Tk[a][2][d];
+    }
+  const int I = I0 + ti, J = J0 + tj, K = K0 + tk;
+#pragma unroll
+  for (int ca = 0; ca < 2; ++ca)
+#pragma unroll
+    for (int cb = 0; cb < 2; ++cb)
+#pragma unroll
+      for (int cd = 0; cd < 2; ++cd) {
+        const float v = w3 * Tj[1][cb][cd] + w1 * Tj[ca ? 2 : 0][cb][cd];
+        const size_t o = lidx<float>(lgf, 2 * I + ca, 2 * J + cb, 2 * K + cd);
+        xf[o] += v;
+      }
+}
+
 // coarse = mean of the 8 children of fine (plain restriction of a field).
 template <class Tin, class Tout>
 __global__ void restrict_mean(const Tin* __restrict__ f, Tout* __restrict__ c, int lgc) {

@@ -152,6 +152,27 @@ struct Cycler {
     return ISIS_OK;
   }
 
+  // x_l += P(x_{l+1} - x0_{l+1})
+  isis_status prolong(int l) {
+    LevelView<T>& C = L[l + 1];
+    const size_t nc = (size_t)C.N * C.N * C.N;
+    const double bytes = sizeof(T) * (2 * (double)nc + 2 * cells(L[l]));
+    const int kind = l == 0 ? KK_PROLONG_FINE : KK_PROLONG_COARSE;
+    if constexpr (sizeof(T) == 4) {
+      if (C.N >= kPTK) {
+        const unsigned blocks = (unsigned)(nc / (kPTI * kPTJ * kPTK));
+        ISIS_LAUNCH(kind, bytes, st,
+                    (prolong_tiled<M, FM><<<blocks, kPTI * kPTJ * kPTK, 0, st>>>(L[l], C.x, (const T*)ws->x0[l + 1],
+                                                                                  C.lg)));
+        return ISIS_OK;
+      }
+    }
+    ISIS_LAUNCH(kind, bytes, st,
+                (prolong_correct<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], C.x, (const T*)ws->x0[l + 1],
+                                                                          C.lg)));
+    return ISIS_OK;
+  }
+
   isis_status vcycle(int l) {
     const int last = (int)L.size() - 1;
     if (l == last) {
@@ -187,9 +208,8 @@ struct Cycler {
                 (coarse_sigma_add<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(C, c, (T*)ws->sig[l + 1])));
     s = vcycle(l + 1);
     if (s != ISIS_OK) return s;
-    ISIS_LAUNCH(l == 0 ? KK_PROLONG_FINE : KK_PROLONG_COARSE, sizeof(T) * (2 * ncd + 2 * nf), st,
-                (prolong_correct<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], C.x, (const T*)ws->x0[l + 1],
-                                                                          C.lg)));
+    s = prolong(l);
+    if (s != ISIS_OK) return s;
     return smooth(l, nu2);
   }
 
@@ -212,9 +232,9 @@ struct Cycler {
     for (int l = last - 1; l >= 0; --l) {
       LevelView<T>& C = L[l + 1];
       size_t nc = (size_t)C.N * C.N * C.N;
-      ISIS_LAUNCH(l == 0 ? KK_PROLONG_FINE : KK_PROLONG_COARSE, sizeof(T) * (2 * (double)nc + 2 * cells(L[l])), st,
-                  (prolong_correct<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], C.x, (const T*)ws->x0[l + 1],
-                                                                            C.lg)));
+      (void)nc;
+      s = prolong(l);
+      if (s != ISIS_OK) return s;
       s = vcycle(l);
       if (s != ISIS_OK) return s;
     }
