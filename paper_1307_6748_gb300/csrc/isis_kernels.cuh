@@ -745,6 +745,82 @@ __global__ void __launch_bounds__(kPTI * kPTJ * kPTK) prolong_tiled(LevelView<fl
       }
 }
 
+// The tiled prolongation with two coarse cells per thread along k (tile 2 x 4 x 64): the children of cells
+// K and K+1 at the same (ca, cb, cd) are neighbours in one colour half, so every fine access is a float2
+// and all 8 loads are issued before the 8 stores.
+constexpr int kP2K = 64;
+template <Model M, Form FM>
+__global__ void __launch_bounds__(kPTI * kPTJ * kPTK) prolong_tiled2(LevelView<float> Fv, const float* __restrict__ xc,
+                                                                    const float* __restrict__ x0c, int lgc) {
+  __shared__ float D[kPTI + 2][kPTJ + 2][kP2K + 2];
+  float* __restrict__ xf = Fv.x;
+  const int Nc = 1 << lgc, mc = Nc - 1, lgf = lgc + 1;
+  const int tk_blocks = Nc / kP2K, tj_blocks = Nc / kPTJ;
+  const int b = blockIdx.x;
+  const int K0 = (b % tk_blocks) * kP2K, J0 = ((b / tk_blocks) % tj_blocks) * kPTJ,
+            I0 = (b / (tk_blocks * tj_blocks)) * kPTI;
+  constexpr int kHalo = (kPTI + 2) * (kPTJ + 2) * (kP2K + 2);
+  for (int e = threadIdx.x; e < kHalo; e += blockDim.x) {
+    const int d = e % (kP2K + 2), r = e / (kP2K + 2), bb = r % (kPTJ + 2), a = r / (kPTJ + 2);
+    const size_t q = lidx<float>(lgc, (I0 + a - 1) & mc, (J0 + bb - 1) & mc, (K0 + d - 1) & mc);
+    D[a][bb][d] = xc[q] - x0c[q];
+  }
+  __syncthreads();
+  const int tk = threadIdx.x % kPTK, tj = (threadIdx.x / kPTK) % kPTJ, ti = threadIdx.x / (kPTK * kPTJ);
+  const float w3 = 0.75f, w1 = 0.25f;
+  // values of the 8 children of coarse cell K0 + 2 tk + s (s = 0, 1), index [ca][cb][cd]
+  float V[2][2][2][2];
+#pragma unroll
+  for (int sidx = 0; sidx < 2; ++sidx) {
+    const int kk = 2 * tk + sidx;
+    float Tk[3][3][2], Tj[3][2][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 3; ++bb) {
+        const float c0 = D[ti + a][tj + bb][kk], c1 = D[ti + a][tj + bb][kk + 1], c2 = D[ti + a][tj + bb][kk + 2];
+        Tk[a][bb][0] = w3 * c1 + w1 * c0;
+        Tk[a][bb][1] = w3 * c1 + w1 * c2;
+      }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        Tj[a][0][d] = w3 * Tk[a][1][d] + w1 * Tk[a][0][d];
+        Tj[a][1][d] = w3 * Tk[a][1][d] + w1 * Tk[a][2][d];
+      }
+#pragma unroll
+    for (int ca = 0; ca < 2; ++ca)
+#pragma unroll
+      for (int cb = 0; cb < 2; ++cb)
+#pragma unroll
+        for (int cd = 0; cd < 2; ++cd) V[sidx][ca][cb][cd] = w3 * Tj[1][cb][cd] + w1 * Tj[ca ? 2 : 0][cb][cd];
+  }
+  const int I = I0 + ti, J = J0 + tj, K = K0 + 2 * tk;
+  // children (2I+ca, 2J+cb, 2K+cd) and (2I+ca, 2J+cb, 2K+2+cd): places g/2 and g/2 + 1 of one colour half
+  size_t o[2][2][2];
+  float2 xv[2][2][2];
+#pragma unroll
+  for (int ca = 0; ca < 2; ++ca)
+#pragma unroll
+    for (int cb = 0; cb < 2; ++cb)
+#pragma unroll
+      for (int cd = 0; cd < 2; ++cd) {
+        o[ca][cb][cd] = lidx<float>(lgf, 2 * I + ca, 2 * J + cb, 2 * K + cd);
+        xv[ca][cb][cd] = *reinterpret_cast<const float2*>(xf + o[ca][cb][cd]);
+      }
+#pragma unroll
+  for (int ca = 0; ca < 2; ++ca)
+#pragma unroll
+    for (int cb = 0; cb < 2; ++cb)
+#pragma unroll
+      for (int cd = 0; cd < 2; ++cd) {
+        const float2 v = xv[ca][cb][cd];
+        *reinterpret_cast<float2*>(xf + o[ca][cb][cd]) =
+            make_float2(v.x + V[0][ca][cb][cd], v.y + V[1][ca][cb][cd]);
+      }
+}
+
 // coarse = mean of the 8 children of fine (plain restriction of a field).
 template <class Tin, class Tout>
 __global__ void restrict_mean(const Tin* __restrict__ f, Tout* __restrict__ c, int lgc) {

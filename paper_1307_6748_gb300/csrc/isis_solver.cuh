@@ -159,6 +159,13 @@ struct Cycler {
     const double bytes = sizeof(T) * (2 * (double)nc + 2 * cells(L[l]));
     const int kind = l == 0 ? KK_PROLONG_FINE : KK_PROLONG_COARSE;
     if constexpr (sizeof(T) == 4) {
+      if (C.N >= kP2K) {
+        const unsigned blocks = (unsigned)(nc / (kPTI * kPTJ * kP2K));
+        ISIS_LAUNCH(kind, bytes, st,
+                    (prolong_tiled2<M, FM><<<blocks, kPTI * kPTJ * kPTK, 0, st>>>(L[l], C.x, (const T*)ws->x0[l + 1],
+                                                                                   C.lg)));
+        return ISIS_OK;
+      }
       if (C.N >= kPTK) {
         const unsigned blocks = (unsigned)(nc / (kPTI * kPTJ * kPTK));
         ISIS_LAUNCH(kind, bytes, st,
