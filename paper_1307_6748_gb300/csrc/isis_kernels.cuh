@@ -625,6 +625,104 @@ __global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __rest
   if constexpr (M == FOFR && kExpCache<T>) C.aux[to] = aux_of<M, FM, T>(xr, T(0));
 }
 
+// resid_restrict for FP32 red/black grids of the canonical models (Poisson, symmetron), two coarse cells
+// (K, K+1; K even) per thread: each fine row of the 16 children's stencils, k = 2K-1 .. 2K+4, comes in as one
+// float2 per colour half (k = 2K, 2K+2 and k = 2K+1, 2K+3) and two scalars, and the per-cell arrays of the
+// children as float2 likewise.  Coarse side >= 4.
+template <Model M, Form FM>
+__global__ void __launch_bounds__(256) resid_restrict2(LevelView<float> F, Coef c, LevelView<float> C,
+                                                       float* __restrict__ x0c, float* __restrict__ sigc) {
+  static_assert(M != FOFR, "the f(R) operators keep the one-cell kernel");
+  const int lg = F.lg, lgc = lg - 1, m = F.N - 1;
+  const unsigned hN = (unsigned)F.N >> 1, half = 1u << (3 * lg - 1);
+  const unsigned long long npairs = 1ull << (3 * lgc - 1);
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npairs) return;
+  const int mc = (1 << lgc) - 1;
+  const int K = (int)((t << 1) & mc), J = (int)((t >> (lgc - 1)) & mc), I = (int)(t >> (2 * lgc - 1));
+  // X[a][b][d]: fine (2I-1+a, 2J-1+b, 2K-1+d); corner rows (a, b both in {0, 3}) unused
+  float X[4][4][6];
+  auto row = [&](int a, int b, bool halo) {
+    const int fi = (2 * I - 1 + a) & m, fj = (2 * J - 1 + b) & m;
+    const unsigned rb = (((unsigned)fi << lg) | (unsigned)fj) * hN;
+    const unsigned c0 = ((unsigned)(fi + fj) & 1u) ? half : 0u, c1 = c0 ? 0u : half;
+    const float2 v0 = *reinterpret_cast<const float2*>(F.x + c0 + rb + (unsigned)K);  // k = 2K, 2K+2
+    const float2 v1 = *reinterpret_cast<const float2*>(F.x + c1 + rb + (unsigned)K);  // k = 2K+1, 2K+3
+    X[a][b][1] = v0.x;
+    X[a][b][2] = v1.x;
+    X[a][b][3] = v0.y;
+    X[a][b][4] = v1.y;
+    if (halo) {
+      X[a][b][0] = F.x[c1 + rb + (((unsigned)K - 1u) & (hN - 1u))];  // k = 2K-1
+      X[a][b][5] = F.x[c0 + rb + (((unsigned)K + 2u) & (hN - 1u))];  // k = 2K+4
+    }
+  };
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const bool ea = (a == 0 || a == 3), eb = (b == 0 || b == 3);
+      if (ea && eb) continue;
+      row(a, b, !(ea || eb));
+    }
+  // the children's own arrays (a, b in {1, 2}; d = 1..4), same float2 pattern
+  float E[2][2][4], S[2][2][4], Bv[2][2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int fi = (2 * I + a) & m, fj = (2 * J + b) & m;
+      const unsigned rb = (((unsigned)fi << lg) | (unsigned)fj) * hN;
+      const unsigned c0 = ((unsigned)(fi + fj) & 1u) ? half : 0u, c1 = c0 ? 0u : half;
+      auto get4 = [&](const float* __restrict__ arr, float* out) {
+        const float2 v0 = *reinterpret_cast<const float2*>(arr + c0 + rb + (unsigned)K);
+        const float2 v1 = *reinterpret_cast<const float2*>(arr + c1 + rb + (unsigned)K);
+        out[0] = v0.x;
+        out[1] = v1.x;
+        out[2] = v0.y;
+        out[3] = v1.y;
+      };
+      if (F.sig) get4(F.sig, S[a][b]);
+      else S[a][b][0] = S[a][b][1] = S[a][b][2] = S[a][b][3] = 0.f;
+      if constexpr (uses_eta<M, FM>()) get4(F.eta, E[a][b]);
+      if constexpr (FM == DELTA && M != POI) get4(F.B, Bv[a][b]);
+    }
+  float xs[2] = {0.f, 0.f}, rs[2] = {0.f, 0.f};
+#pragma unroll
+  for (int a = 1; a < 3; ++a)
+#pragma unroll
+    for (int b = 1; b < 3; ++b)
+#pragma unroll
+      for (int d = 1; d < 5; ++d) {
+        Cell<float> q;
+        q.x = X[a][b][d];
+        q.xn[0] = X[a + 1][b][d];
+        q.xn[1] = X[a - 1][b][d];
+        q.xn[2] = X[a][b + 1][d];
+        q.xn[3] = X[a][b - 1][d];
+        q.xn[4] = X[a][b][d + 1];
+        q.xn[5] = X[a][b][d - 1];
+        q.sig = S[a - 1][b - 1][d - 1];
+        if constexpr (uses_eta<M, FM>()) q.eta = E[a - 1][b - 1][d - 1]; else q.eta = 0.f;
+        if constexpr (FM == DELTA && M != POI) q.B = Bv[a - 1][b - 1][d - 1]; else q.B = 0.f;
+        float Fv, dF;
+        eval_cell<M, FM, float>(c, F.ih2, q, Fv, dF);
+        const int s = (d - 1) >> 1;  // children of K (d = 1, 2) or of K+1 (d = 3, 4)
+        xs[s] += q.x;
+        rs[s] -= Fv;
+      }
+  (void)E;
+  (void)Bv;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const size_t to = lidx<float>(lgc, I, J, K + s);
+    const float xr = xs[s] * 0.125f;
+    C.x[to] = xr;
+    x0c[to] = xr;
+    sigc[to] = rs[s] * 0.125f;
+  }
+}
+
 // Sigma_H += L_H(x_H) (the FAS coarse source, Sect. 3.2).
 template <Model M, Form FM, class T>
 __global__ void coarse_sigma_add(LevelView<T> L, Coef c, T* __restrict__ sig) {

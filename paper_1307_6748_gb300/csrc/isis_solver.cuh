@@ -207,9 +207,19 @@ struct Cycler {
                                                                         (float*)ws->sig[1])));
       }
     } else {
-      ISIS_LAUNCH(l == 0 ? KK_RESTRICT_FINE : KK_RESTRICT_COARSE, rbytes, st,
-                  (resid_restrict<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], c, C, (T*)ws->x0[l + 1],
-                                                                          (T*)ws->sig[l + 1])));
+      bool done = false;
+      if constexpr (sizeof(T) == 4 && M != FOFR) {
+        if (C.N >= 4) {
+          ISIS_LAUNCH(l == 0 ? KK_RESTRICT_FINE : KK_RESTRICT_COARSE, rbytes, st,
+                      (resid_restrict2<M, FM><<<nblk(nc / 2, 256), 256, 0, st>>>(L[l], c, C, (float*)ws->x0[l + 1],
+                                                                                 (float*)ws->sig[l + 1])));
+          done = true;
+        }
+      }
+      if (!done)
+        ISIS_LAUNCH(l == 0 ? KK_RESTRICT_FINE : KK_RESTRICT_COARSE, rbytes, st,
+                    (resid_restrict<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], c, C, (T*)ws->x0[l + 1],
+                                                                            (T*)ws->sig[l + 1])));
     }
     ISIS_LAUNCH(KK_SIGMA, sizeof(T) * ncd * (2 + arrays(true)), st,
                 (coarse_sigma_add<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(C, c, (T*)ws->sig[l + 1])));
