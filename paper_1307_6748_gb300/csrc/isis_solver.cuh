@@ -324,11 +324,6 @@ isis_status remove_mean(Workspace* ws, T* v, size_t n, cudaStream_t st) {
   return ISIS_OK;
 }
 
-template <class Tin, class Tout>
-__global__ void convert_k(const Tin* __restrict__ a, Tout* __restrict__ b, size_t n) {
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) b[t] = (Tout)a[t];
-}
 
 // Row-major (caller, FP64 or FP32) <-> red/black split FP32 workspace.
 template <class Tin>
@@ -373,11 +368,6 @@ __global__ void exp_k(const T* __restrict__ a, T* __restrict__ b, size_t n) {
   if (t < n) b[t] = dexp<T>(a[t]);
 }
 
-template <class T>
-__global__ void fill_k(T* __restrict__ a, T v, size_t n) {
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) a[t] = v;
-}
 
 __global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, int lg);
 
