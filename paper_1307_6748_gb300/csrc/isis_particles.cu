@@ -106,8 +106,26 @@ __global__ void cic_finish(const unsigned long long* __restrict__ acc, T* __rest
 //   pref = C_s a^2 chi(c) (symmetron, Eq. (symmetron_geodesics_tilde_chi) with chi~ = a chi),
 //          C_s e^u(c) (the b = e^u models: C_s = 1/2 for f(R), Sect. 4.2; a^2 beta phi_0 / M_pl for
 //          the chameleon), 0 without a scalar field.
-// The differences are taken in the field's precision (FP64 fields lose no
-// digits to cancellation), the products in FP32 (the output is FP32).
+// The differences keep the field's digits (FP64 fields through their float-float
+// splits, see fdiff), the products are FP32 (the output is FP32).
+// a - b rounded to FP32.  FP64 fields: from the float-float splits of a and b by integer operations, so no
+// FP64 instruction runs (GB300 has few FP64 units); (a.hi - b.hi) + (a.lo - b.lo) carries the difference to
+// FP32 accuracy.
+template <class T>
+__device__ __forceinline__ float fdiff(T a, T b) {
+  if constexpr (sizeof(T) == 8) {
+    const ff A = ff_split_bits((double)a), B = ff_split_bits((double)b);
+    return (A.hi - B.hi) + (A.lo - B.lo);
+  } else {
+    return (float)(a - b);
+  }
+}
+template <class T>
+__device__ __forceinline__ float to_f32(T a) {
+  if constexpr (sizeof(T) == 8) return ff_split_bits((double)a).hi;
+  else return (float)a;
+}
+
 template <class T, int MODEL>
 __global__ void force_grid(const T* __restrict__ Phi, const T* __restrict__ phi, int lg, float a2, float Cs,
                            float inv2h, float* __restrict__ fx, float* __restrict__ fy, float* __restrict__ fz) {
@@ -121,16 +139,16 @@ __global__ void force_grid(const T* __restrict__ Phi, const T* __restrict__ phi,
   const size_t zp = cidx(lg, i, j, (k + 1) & m), zm = cidx(lg, i, j, (k - 1) & m);
   float g0 = 0.f, g1 = 0.f, g2 = 0.f;
   if (Phi) {
-    g0 = a2 * (float)(Phi[xp] - Phi[xm]);
-    g1 = a2 * (float)(Phi[yp] - Phi[ym]);
-    g2 = a2 * (float)(Phi[zp] - Phi[zm]);
+    g0 = a2 * fdiff<T>(Phi[xp], Phi[xm]);
+    g1 = a2 * fdiff<T>(Phi[yp], Phi[ym]);
+    g2 = a2 * fdiff<T>(Phi[zp], Phi[zm]);
   }
   if (MODEL != 0) {
-    float v = (float)phi[t];
+    float v = to_f32<T>(phi[t]);
     float pref = (MODEL == ISIS_SYMMETRON) ? Cs * a2 * v : Cs * expf(v);
-    g0 = fmaf(pref, (float)(phi[xp] - phi[xm]), g0);
-    g1 = fmaf(pref, (float)(phi[yp] - phi[ym]), g1);
-    g2 = fmaf(pref, (float)(phi[zp] - phi[zm]), g2);
+    g0 = fmaf(pref, fdiff<T>(phi[xp], phi[xm]), g0);
+    g1 = fmaf(pref, fdiff<T>(phi[yp], phi[ym]), g1);
+    g2 = fmaf(pref, fdiff<T>(phi[zp], phi[zm]), g2);
   }
   fx[t] = g0 * inv2h;
   fy[t] = g1 * inv2h;
