@@ -187,8 +187,8 @@ def sphere_eta_box(dims, corner, h: float, B: float, R: float, delta: float, sub
 def refine_flags(eta: np.ndarray, level: int, m_ref: float = 8.0, expand: int = 1, periodic: bool = False,
                  within: np.ndarray | None = None) -> np.ndarray:
     """Bool flags of the cells of refinement level `level` - 1 (cell volume 8^-(level-1) of a domain cell) that
-    level `level` refines: eta 8^-(level-1) >= m_ref, dilated by `expand` cells (26-neighbourhood), and kept
-    inside `within` (the parent level's refined cells) when given."""
+    level `level` refines: eta 8^-(level-1) >= m_ref, dilated `expand` times by the six face neighbours, and
+    kept inside `within` (the parent level's refined cells) when given."""
     f = eta * 8.0 ** (-(level - 1)) >= m_ref
     for _ in range(expand):
         g = f.copy()
@@ -221,6 +221,15 @@ def patch_box(flags: np.ndarray, margin: int = 1, multiple: int = 8, periodic: b
     origin, n = [], []
     for a in range(3):
         lo, hi = int(idx[:, a].min()) - margin, int(idx[:, a].max()) + margin + 1
+        if periodic:
+            # the flagged coordinates may wrap round the domain: start after the largest circular gap
+            occ = np.unique(idx[:, a])
+            gaps = np.diff(np.concatenate([occ, occ[:1] + pn[a]]))
+            g = int(np.argmax(gaps))
+            start = int(occ[(g + 1) % len(occ)])
+            span = int(occ[g]) - start
+            span = span + pn[a] if span < 0 else span
+            lo, hi = start - margin, start + span + margin + 1
         size = -(-(hi - lo) // multiple) * multiple
         lo -= (size - (hi - lo)) // 2
         if not periodic:
