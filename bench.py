@@ -31,7 +31,7 @@ METRIC = "symmetron/f(R) 512³ FAS solve time to residual 1e-8; smoother HBM GB/
 L2_BYTES = 129 * 2 ** 20
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--guess", default="net", choices=["net", "background"],
                     help="symmetron initial guess: the trained U-Net, or the background field")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1307_6748_gb300", "weights", "unet_symmetron.npz"))
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload(args):
@@ -72,6 +72,75 @@ def workload(args):
                               "fofr": "background field", "poisson": "zero"},
             "l2": "inputs larger than L2 (each 512^3 field is 0.5-1 GB), no flush",
             "parallelism": "replicas (one independent problem per GPU)"}
+
+
+# ---------------------------------------------------------------------------
+# The timed step
+# ---------------------------------------------------------------------------
+
+class ForceStep:
+    """One force step on device-resident particles: CIC deposit, the Poisson, symmetron and f(R) solves (FP32
+    cycles in FP64 defect correction), the forces of both models.  The solver options here are the launch
+    configuration the benchmark times; the full-size GPU test runs the same object."""
+
+    def __init__(self, args, dev, npart: int):
+        import torch
+
+        from paper_1307_6748_gb300 import isis, unet
+        self.isis = isis
+        N, box = args.N, args.box
+        self.tol = args.tol
+        self.grid = isis.Grid(N, box)
+        self.psym = isis.Params(lambda0=1.0, beta=1.0, a_ssb=0.5)
+        self.pfr = isis.Params(n=1, fR0_abs=1e-5)
+        self.a = 1.0
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.eta, self.Phi, self.chi, self.u = (torch.empty((N,) * 3, **f64) for _ in range(4))
+        self.g = [torch.empty(npart, device=dev, dtype=torch.float32) for _ in range(6)]
+
+        def opts(inner, init=isis.ISIS_INIT_BACKGROUND):
+            return isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=inner, init=init, n_coarsest=args.ncoarse,
+                             fmg=args.fmg, nu1=args.nu1, nu2=args.nu2)
+        self.o_poi, self.o_sym, self.o_fr = opts(args.inner_poisson), opts(args.inner_sym), opts(args.inner_fofr)
+        self.net, self.pooled = None, False
+        if args.guess == "net":
+            # the net is convolutional: it runs at its training cell size (1 Mpc/h), here on 8-cell means
+            meta = unet.UNet.meta(args.weights)
+            h, h_net = box / N, float(meta.get("h", 1.0))
+            if abs(2 * h - h_net) < 1e-9 * h_net:
+                self.pooled = True
+            elif abs(h - h_net) > 1e-9 * h_net:
+                raise SystemExit(f"bench: the net was trained at {h_net} Mpc/h cells; this grid has {h} Mpc/h")
+            self.net = unet.UNet.load(args.weights, device=dev)
+            self.o_sym = opts(args.inner_sym, isis.ISIS_INIT_INPUT)
+        self.stream = torch.cuda.current_stream()
+        self.infos = {}
+
+    def __call__(self, xx, yy, zz, ev=None):
+        isis, st, infos = self.isis, self.stream, self.infos
+        grid, a, eta, Phi, chi, u, g = self.grid, self.a, self.eta, self.Phi, self.chi, self.u, self.g
+        if ev:
+            ev[0].record(st)
+        isis.isis_cic_deposit(grid, xx, yy, zz, eta)
+        if ev:
+            ev[1].record(st)
+        infos["poisson"] = isis.isis_poisson_solve(grid, a, eta, Phi, tol=self.tol, opts=self.o_poi)
+        if ev:
+            ev[2].record(st)
+        if self.net is not None:
+            self.net.guess(eta, a, self.psym.a_ssb, chi, pooled=self.pooled)
+        infos["symmetron"] = isis.isis_scalar_solve(isis.ISIS_SYMMETRON, self.psym, grid, a, eta, chi, tol=self.tol,
+                                                    opts=self.o_sym)
+        if ev:
+            ev[3].record(st)
+        infos["fofr"] = isis.isis_scalar_solve(isis.ISIS_FOFR_HS, self.pfr, grid, a, eta, u, tol=self.tol,
+                                               opts=self.o_fr)
+        if ev:
+            ev[4].record(st)
+        isis.isis_fifth_force(isis.ISIS_SYMMETRON, self.psym, grid, a, Phi, chi, xx, yy, zz, out=g[0:3])
+        isis.isis_fifth_force(isis.ISIS_FOFR_HS, self.pfr, grid, a, Phi, u, xx, yy, zz, out=g[3:6])
+        if ev:
+            ev[5].record(st)
 
 
 # ---------------------------------------------------------------------------
@@ -206,7 +275,7 @@ def main():
 
     import torch
 
-    from paper_1307_6748_gb300 import build, isis, synth, unet
+    from paper_1307_6748_gb300 import build, isis, synth
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -216,59 +285,13 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     N, box = args.N, args.box
-    grid = isis.Grid(N, box)
-    psym = isis.Params(lambda0=1.0, beta=1.0, a_ssb=0.5)
-    pfr = isis.Params(n=1, fR0_abs=1e-5)
-    a = 1.0
     x, y, z = synth.zeldovich(N, box, seed=3 + 1000 * rank, device=dev)
     npart = x.numel()
-    f64 = dict(dtype=torch.float64, device=dev)
-    eta = torch.empty((N,) * 3, **f64)
-    Phi = torch.empty((N,) * 3, **f64)
-    chi = torch.empty((N,) * 3, **f64)
-    u = torch.empty((N,) * 3, **f64)
-    g = [torch.empty(npart, device=dev, dtype=torch.float32) for _ in range(6)]
-    def opts(inner):
-        return isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=inner, init=isis.ISIS_INIT_BACKGROUND,
-                         n_coarsest=args.ncoarse, fmg=args.fmg, nu1=args.nu1, nu2=args.nu2)
-    o_poi, o_sym, o_fr = opts(args.inner_poisson), opts(args.inner_sym), opts(args.inner_fofr)
-    net, pooled = None, False
-    if args.guess == "net":
-        # the net is convolutional: it runs at its training cell size (1 Mpc/h), here on 8-cell means
-        meta = unet.UNet.meta(args.weights)
-        h, h_net = box / N, float(meta.get("h", 1.0))
-        if abs(2 * h - h_net) < 1e-9 * h_net:
-            pooled = True
-        elif abs(h - h_net) > 1e-9 * h_net:
-            raise SystemExit(f"bench: the net was trained at {h_net} Mpc/h cells; this grid has {h} Mpc/h")
-        net = unet.UNet.load(args.weights, device=dev)
-        o_sym = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=args.inner_sym, init=isis.ISIS_INIT_INPUT,
-                          n_coarsest=args.ncoarse, fmg=args.fmg, nu1=args.nu1, nu2=args.nu2)
-    stream = torch.cuda.current_stream()
-    infos = {}
-
-    def step(xx, yy, zz, ev=None):
-        if ev:
-            ev[0].record(stream)
-        isis.isis_cic_deposit(grid, xx, yy, zz, eta)
-        if ev:
-            ev[1].record(stream)
-        infos["poisson"] = isis.isis_poisson_solve(grid, a, eta, Phi, tol=args.tol, opts=o_poi)
-        if ev:
-            ev[2].record(stream)
-        if net is not None:
-            net.guess(eta, a, psym.a_ssb, chi, pooled=pooled)
-        infos["symmetron"] = isis.isis_scalar_solve(isis.ISIS_SYMMETRON, psym, grid, a, eta, chi, tol=args.tol,
-                                                    opts=o_sym)
-        if ev:
-            ev[3].record(stream)
-        infos["fofr"] = isis.isis_scalar_solve(isis.ISIS_FOFR_HS, pfr, grid, a, eta, u, tol=args.tol, opts=o_fr)
-        if ev:
-            ev[4].record(stream)
-        isis.isis_fifth_force(isis.ISIS_SYMMETRON, psym, grid, a, Phi, chi, xx, yy, zz, out=g[0:3])
-        isis.isis_fifth_force(isis.ISIS_FOFR_HS, pfr, grid, a, Phi, u, xx, yy, zz, out=g[3:6])
-        if ev:
-            ev[5].record(stream)
+    S = ForceStep(args, dev, npart)
+    grid, psym, pfr, a = S.grid, S.psym, S.pfr, S.a
+    eta, Phi, chi, u, g = S.eta, S.Phi, S.chi, S.u, S.g
+    o_poi, o_sym, o_fr, net, pooled = S.o_poi, S.o_sym, S.o_fr, S.net, S.pooled
+    stream, infos, step = S.stream, S.infos, S
 
     def barrier():
         torch.cuda.synchronize()

@@ -368,9 +368,12 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 // e^v = 2^(v log2 e): one packed multiply, then the hardware base-2 exponential (MUFU) of each lane.
+// The .ftz form flushes subnormal inputs and results to zero (PTX ISA, ex2): it spares the subnormal
+// handling around the MUFU operation.  A subnormal input gives 1 either way; a subnormal result needs
+// v < -87, far outside the exponents of these fields (|u|, |B| and |u|/(n+1) stay below about 30).
 __device__ __forceinline__ float ex2_approx(float t) {
   float r;
-  asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(t));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
   return r;
 }
 __device__ __forceinline__ float2 exp_2(float2 v) {
