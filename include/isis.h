@@ -260,11 +260,19 @@ isis_status isis_kick_drift(const isis_grid* grid, float* x, float* y, float* z,
  *              the field: the guess at the unknowns in (ISIS_INIT_INPUT) or ignored
  *              (ISIS_INIT_PARENT); out, the solution at the unknowns and the
  *              interpolated parent elsewhere.
- *   opts       prec must be ISIS_F64; init ISIS_INIT_INPUT or ISIS_INIT_PARENT;
+ *   opts       prec ISIS_F64, or ISIS_F32_REFINE64: the FP64 residual r = -L(u)
+ *              at the unknowns, then inner_cycles FP32 V-cycles of the same patch
+ *              FAS on the correction e about B = fp32(u), L(B + e) - L(B) = r,
+ *              with masked neighbours entering as B_nb + e_nb + (m_nb/m_c)
+ *              (e_c - e_c^Pre), then u += e; repeated until the FP64 residual
+ *              meets the test (cycles counts the FP32 V-cycles, outer the FP64
+ *              iterations, hist the FP64 residual after each; fmg is ignored).
+ *              ISIS_F32 is rejected.  init ISIS_INIT_INPUT or ISIS_INIT_PARENT;
  *              n_coarsest is ignored.  The convergence test is the solvers' own
  *              over the unknowns (res_ref from the unknowns' eta).
  *   Workspace: allocated stream-ordered per call and freed before return.  The
- *   call synchronises the stream once per cycle and once to check the flags. */
+ *   call synchronises the stream once to check the flags, then once per cycle
+ *   (ISIS_F64) or per outer iteration (ISIS_F32_REFINE64). */
 typedef struct {
   int n[3];
   int origin[3];

@@ -35,13 +35,15 @@ class Level:
 
 def refine(model, params: isis.Params | None, grid: isis.Grid, a: float, eta_domain: np.ndarray,
            phi_domain: torch.Tensor, eta_box, levels: int = 2, m_ref: float = 8.0, expand: int = 1,
-           tol: float = 1e-10, max_cycles: int = 100, nu1: int = 2, nu2: int = 2, stream=None) -> list[Level]:
+           tol: float = 1e-10, max_cycles: int = 100, nu1: int = 2, nu2: int = 2, prec: int = isis.ISIS_F64,
+           inner_cycles: int = 4, stream=None) -> list[Level]:
     """Solve up to `levels` refinement levels on top of a converged domain field.
 
     model: isis.ISIS_SYMMETRON, isis.ISIS_FOFR_HS, or None for the Newtonian potential.
     eta_domain: host array (N^3) of the domain density; phi_domain: the domain field on the device (float64).
     eta_box(dims, corner, h) -> host array: the density of a box of cells of size h whose first cell's lower
-    corner is `corner`.  Stops early when a level has nothing to refine."""
+    corner is `corner`.  prec: isis.ISIS_F64, or isis.ISIS_F32_REFINE64 (FP32 correction cycles, inner_cycles
+    per FP64 outer iteration).  Stops early when a level has nothing to refine."""
     N, B = grid.N, grid.box
     out: list[Level] = []
     parent, peta, pdims = phi_domain, np.asarray(eta_domain), (N, N, N)
@@ -65,7 +67,8 @@ def refine(model, params: isis.Params | None, grid: isis.Grid, a: float, eta_dom
         tf = torch.from_numpy(flags).to(dev)
         te = torch.from_numpy(eta_f).to(dev)
         phi = torch.empty(nf, dtype=torch.float64, device=dev)
-        opts = isis.Opts(nu1=nu1, nu2=nu2, max_cycles=max_cycles, init=isis.ISIS_INIT_PARENT)
+        opts = isis.Opts(nu1=nu1, nu2=nu2, max_cycles=max_cycles, init=isis.ISIS_INIT_PARENT, prec=prec,
+                         inner_cycles=inner_cycles)
         if model is None:
             info = isis.isis_patch_poisson_solve(grid, a, patch, parent, tf, te, phi, tol=tol, opts=opts,
                                                  stream=stream)

@@ -390,7 +390,9 @@ static isis_status patch_common(PatchArgs& P, const isis_grid* grid, double a, c
   isis_mg_opts o = {2, 2, 4, 100, ISIS_F64, 2, ISIS_INIT_INPUT, 0};
   if (opts) o = *opts;
   if (o.nu1 < 0 || o.nu1 > 16 || o.nu2 < 0 || o.nu2 > 16 || o.max_cycles < 0 || o.max_cycles > 128) return ISIS_EINVAL;
-  if (o.prec != ISIS_F64 || (o.init != ISIS_INIT_INPUT && o.init != ISIS_INIT_PARENT)) return ISIS_EINVAL;
+  if ((o.prec != ISIS_F64 && o.prec != ISIS_F32_REFINE64) || (o.init != ISIS_INIT_INPUT && o.init != ISIS_INIT_PARENT))
+    return ISIS_EINVAL;
+  if (o.prec == ISIS_F32_REFINE64 && (o.inner_cycles < 1 || o.inner_cycles > 16)) return ISIS_EINVAL;
   if (box->level < 1 || box->level > 12) return ISIS_EINVAL;
   int64_t nflag = 0;
   for (int d = 0; d < 3; ++d) {
@@ -444,6 +446,8 @@ static isis_status patch_common(PatchArgs& P, const isis_grid* grid, double a, c
   P.nu1 = o.nu1;
   P.nu2 = o.nu2;
   P.max_cycles = o.max_cycles;
+  P.prec = o.prec;
+  P.inner = o.inner_cycles;
   P.init_parent = o.init == ISIS_INIT_PARENT ? 1 : 0;
   P.info = info;
   P.st = (cudaStream_t)stream;

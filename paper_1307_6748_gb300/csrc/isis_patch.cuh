@@ -20,6 +20,10 @@
 //   - FAS between the patch levels as on the domain grid (full-approximation
 //     restriction of u, residual restricted with zeros off the unknowns,
 //     correction added at unknowns only, none from outside the box);
+//   - mixed precision (ISIS_F32_REFINE64): the FP64 residual r = -L(u) at
+//     the unknowns, then FP32 V-cycles of the same patch FAS on the correction
+//     e about B = fp32(u), L(B + e) - L(B) = r (masked neighbours enter as
+//     B_nb + e_nb + (m_nb/m_c)(e_c - e_c^Pre)), then u += e, as on the domain;
 //   - levels halve while every dimension is even and the smallest is >= 8;
 //     the coarsest level gets 16 red/black sweeps in one block;
 //   - flags on the box's outer layer of parent cells are rejected, so on every
@@ -47,6 +51,8 @@ struct PatchArgs {
   int64_t unknowns;        // 8 * number of flagged cells
   double tol;
   int nu1, nu2, max_cycles;
+  int prec;                // ISIS_F64, or ISIS_F32_REFINE64: FP32 correction cycles in FP64 defect correction
+  int inner;               // FP32 V-cycles per FP64 outer iteration (ISIS_F32_REFINE64)
   int init_parent;         // 1: unknowns start from the interpolated parent
   isis_solve_info* info;
   cudaStream_t st;

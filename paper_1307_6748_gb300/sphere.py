@@ -9,7 +9,7 @@ f(R) R = 5, B = 100 Mpc/h, n = 1, |f_R0| = 1e-6 at z = 0.
 python -m paper_1307_6748_gb300.sphere [--N 128] [--prec f64|refine] [--levels 0] [--expand 4]
                                        [--profile-dir DIR]
 prints one JSON line per case (solve time from CUDA events after one untimed solve, cycles, residuals);
---levels L adds L refinement levels (amr.refine, FP64) on the domain solution and times each;
+--levels L adds L refinement levels (amr.refine, in --prec as the domain) on the domain solution and times each;
 with --profile-dir, writes r, mean, min, max of the field (chi, or f_R = -e^u / a^2) per radial bin.
 """
 from __future__ import annotations
@@ -119,13 +119,13 @@ def main():
 
             run = lambda: amr.refine(model, isis.Params(**case["params"]), isis.Grid(args.N, case["B"]), a,
                                      eta.cpu().numpy(), phi, dens, levels=args.levels, expand=args.expand,
-                                     tol=args.tol)
+                                     tol=args.tol, prec=prec)
             run()  # untimed: the flags, boxes and patch densities on the host, then the solves
             # time each level's solve alone, on its own inputs
             levels = run()
             for lv in levels:
                 phi_l = torch.empty_like(lv.phi)
-                opts = isis.Opts(max_cycles=100, init=isis.ISIS_INIT_PARENT)
+                opts = isis.Opts(max_cycles=100, init=isis.ISIS_INIT_PARENT, prec=prec, inner_cycles=4)
                 parent = phi if lv.level == 1 else levels[lv.level - 2].phi
                 torch.cuda.synchronize()
                 if args.prof:
@@ -137,9 +137,9 @@ def main():
                                                     lv.eta, phi_l, tol=args.tol, opts=opts)
                 e1.record()
                 torch.cuda.synchronize()
-                print(json.dumps({"case": name, "level": lv.level, "box": list(lv.patch.n),
+                print(json.dumps({"case": name, "level": lv.level, "prec": args.prec, "box": list(lv.patch.n),
                                   "fine_cells": int(lv.phi.numel()), "unknowns": int(lv.unknowns.sum()),
-                                  "ms": round(e0.elapsed_time(e1), 3), "cycles": info.cycles,
+                                  "ms": round(e0.elapsed_time(e1), 3), "cycles": info.cycles, "outer": info.outer,
                                   "res_final_over_ref": info.res_final / info.res_ref}), flush=True)
                 if args.prof:
                     isis.prof_enable(False)

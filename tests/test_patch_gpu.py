@@ -2,7 +2,10 @@
 
 Same parent, flags and density on both sides: a level-1 patch over the periodic domain grid (its box
 wrapping round the domain along one axis) and a level-2 patch over the level-1 patch.  FP64: max-abs
-1e-10 after a fixed number of cycles and after convergence (same cycle count)."""
+1e-10 after a fixed number of cycles and after convergence (same cycle count).  FP32 correction cycles in
+FP64 defect correction (ISIS_F32_REFINE64): relative L2 over the unknowns within 1e-9 of the oracle's
+solution, both converged (the library to 1e-11, the oracle to 5e-12: its FP64 floor on the f(R) level-2
+patch is 2.9e-12 of ref)."""
 import numpy as np
 import pytest
 import torch
@@ -48,14 +51,17 @@ def _fine_eta(shape, seed):
     return np.ascontiguousarray(e[:shape[0], :shape[1], :shape[2]])
 
 
-def _run_both(isis, model, patch_o, parent, flags, eta_f, tol, max_cycles, init_parent=True):
+def _run_both(isis, model, patch_o, parent, flags, eta_f, tol, max_cycles, init_parent=True, prec=None,
+              tol_oracle=None):
     # oracle
-    ro = oracle.patch_solve(_prob(model), patch_o, parent, flags, eta_f, tol=tol, max_cycles=max_cycles)
+    ro = oracle.patch_solve(_prob(model), patch_o, parent, flags, eta_f, tol=tol if tol_oracle is None else tol_oracle,
+                            max_cycles=max_cycles)
     # GPU
     patch = isis.Patch(patch_o.n, patch_o.o, patch_o.pn, patch_o.periodic, level=patch_o.level,
                        eta_mean=patch_o.eta_mean)
     phi = torch.zeros(patch.fine_shape, dtype=torch.float64, device="cuda")
-    opts = isis.Opts(max_cycles=max_cycles, init=isis.ISIS_INIT_PARENT if init_parent else isis.ISIS_INIT_INPUT)
+    opts = isis.Opts(max_cycles=max_cycles, init=isis.ISIS_INIT_PARENT if init_parent else isis.ISIS_INIT_INPUT,
+                     prec=isis.ISIS_F64 if prec is None else prec, inner_cycles=4)
     args = (isis.Grid(N, BOX), A1, patch, torch.from_numpy(parent).cuda(), torch.from_numpy(flags).cuda(),
             torch.from_numpy(eta_f).cuda(), phi)
     if model == oracle.POISSON:
@@ -108,6 +114,37 @@ def test_patch_levels_1_and_2_converged(cuda_lib, model):
     assert np.abs(got2 - ro2.phi).max() <= 1e-10 * max(1.0, np.abs(ro2.phi).max())
 
 
+def _rel_l2(got, ref, unk):
+    return float(np.linalg.norm(got[unk] - ref[unk]) / np.linalg.norm(ref[unk]))
+
+
+def _unknowns(flags):
+    return np.repeat(np.repeat(np.repeat(flags, 2, 0), 2, 1), 2, 2) > 0
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_patch_refine64_levels_1_and_2(cuda_lib, model):
+    isis = cuda_lib
+    patch, parent, flags, eta_f = _level1(model)
+    ro, info, got = _run_both(isis, model, patch, parent, flags, eta_f, tol=1e-11, max_cycles=60,
+                              prec=isis.ISIS_F32_REFINE64, tol_oracle=5e-12)
+    assert ro.status == oracle.OK and info.status == isis.ISIS_OK and info.outer >= 1
+    assert info.res_final <= 1e-11 * info.res_ref and info.cycles <= 4 * info.outer
+    assert _rel_l2(got, ro.phi, _unknowns(flags)) <= 1e-9
+    # the cells that are not unknowns hold the interpolated parent on both sides
+    assert np.abs(got[~_unknowns(flags)] - ro.phi[~_unknowns(flags)]).max() <= 1e-12 * max(1.0, np.abs(ro.phi).max())
+    # level 2 inside level 1, with the oracle's level-1 field as parent
+    nf = tuple(2 * v for v in patch.n)
+    o2, n2 = (4, 3, 6), (14, 12, 14)
+    e1 = eta_f[o2[0]:o2[0] + n2[0], o2[1]:o2[1] + n2[1], o2[2]:o2[2] + n2[2]]
+    flags2 = _flags(e1, 1.2)
+    p2 = oracle.Patch(n2, o2, nf, False, level=2, eta_mean=patch.eta_mean)
+    ro2, info2, got2 = _run_both(isis, model, p2, ro.phi, flags2, _fine_eta(tuple(2 * v for v in n2), 12),
+                                 tol=1e-11, max_cycles=60, prec=isis.ISIS_F32_REFINE64, tol_oracle=5e-12)
+    assert ro2.status == oracle.OK and info2.status == isis.ISIS_OK and info2.outer >= 1
+    assert _rel_l2(got2, ro2.phi, _unknowns(flags2)) <= 1e-9
+
+
 def test_patch_input_guess_and_argument_checks(cuda_lib):
     isis = cuda_lib
     patch, parent, flags, eta_f = _level1(oracle.SYMMETRON)
@@ -135,3 +172,6 @@ def test_patch_input_guess_and_argument_checks(cuda_lib):
     with pytest.raises(isis.IsisError):
         isis.isis_patch_scalar_solve(isis.ISIS_SYMMETRON, isis.Params(), *args, phi,
                                      opts=isis.Opts(prec=isis.ISIS_F32))
+    with pytest.raises(isis.IsisError):
+        isis.isis_patch_scalar_solve(isis.ISIS_SYMMETRON, isis.Params(), *args, phi,
+                                     opts=isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=0))

@@ -96,3 +96,34 @@ def test_sphere_refinement_levels(cuda_lib, name):
         assert np.abs(got - phi_o).max() <= 1e-10 * max(1.0, np.abs(phi_o).max())
         errs.append(SC.level_errors(name, got, lv.corner, lv.h, lv.unknowns))
     SC.check_levels(name, errs)
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_levels_tight(name):
+    return SC.oracle_levels(name, tol=1e-12)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_sphere_refinement_levels_refine64(cuda_lib, name):
+    """The same two levels with FP32 correction cycles in FP64 defect correction (ISIS_F32_REFINE64) to 1e-11,
+    on the FP64 domain field at 1e-12: each level within 1e-9 relative L2 (over its unknowns) of the oracle's
+    levels at 1e-12, and the levels still beat the domain grid against the 1D profile."""
+    isis = cuda_lib
+    from paper_1307_6748_gb300 import amr
+    c = SC.cases()[name]
+    ref = _oracle_levels_tight(name)
+    eta0 = SC.eta_3d(name, 128)
+    dom = _gpu_solve(isis, name, 128, isis.ISIS_F64, 1e-12)
+    model = isis.ISIS_SYMMETRON if c["model"] == oracle.SYMMETRON else isis.ISIS_FOFR_HS
+    levels = amr.refine(model, isis.Params(**c["params"]), isis.Grid(128, c["B"]), c["a"], eta0,
+                        torch.from_numpy(dom).cuda(), SC.patch_density(name), levels=2, expand=SC.EXPAND, tol=1e-11,
+                        prec=isis.ISIS_F32_REFINE64)
+    assert len(levels) == 2
+    errs = [SC.level_errors(name, dom, (0.0, 0.0, 0.0), c["B"] / 128, None)]
+    for lv, (phi_o, corner_o, h_o, unk_o) in zip(levels, ref[1:]):
+        got = lv.phi.cpu().numpy()
+        assert lv.info.status == isis.ISIS_OK and lv.info.outer >= 1 and np.array_equal(lv.unknowns, unk_o)
+        u = lv.unknowns
+        assert np.linalg.norm(got[u] - phi_o[u]) <= 1e-9 * np.linalg.norm(phi_o[u])
+        errs.append(SC.level_errors(name, got, lv.corner, lv.h, lv.unknowns))
+    SC.check_levels(name, errs)
