@@ -335,7 +335,7 @@ isis_status isis_selftest_exp_ff(const double* x, double* y, int n, void* stream
   }
   cudaStream_t st = (cudaStream_t)stream;
   ISIS_LAUNCH(KK_SETUP, 16.0 * n, st,
-              (selftest_exp_ff<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n, tab, ff_exp_consts())));
+              (selftest_exp_ff<<<(unsigned)((n / 2 + 256) / 256), 256, 0, st>>>(x, y, n, tab, ff_exp_consts())));
   return ISIS_OK;
 }
 

@@ -114,37 +114,103 @@ __device__ __forceinline__ double f2d_bits(float f) {
 __device__ __forceinline__ ff ff_load(const float2& v) { return {v.x, v.y}; }
 __device__ __forceinline__ float2 ff_store(ff a) { return make_float2(a.hi, a.lo); }
 
-// Constants of exp_ff, filled on the host (ff_exp_consts).
+// ---- two float-float values at once, in packed FP32x2 instructions (sm_100 family) ----
+// ff2 holds the high parts of two values in one float2 and their low parts in another.  Each operation is
+// the scalar one of the same name done lane by lane: __fadd2_rn, __fmul2_rn and __ffma2_rn round each lane
+// as an FP32 add, multiply and fused multiply-add do, and a subtraction a - b is the exact fma b * (-1) + a,
+// so both lanes give the scalar results bit for bit at half the instruction count.
+struct ff2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2_bc(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ ff2 ff2_two_sum(float2 a, float2 b) {
+  const float2 s = f2_add(a, b);
+  const float2 bb = f2_sub(s, a);
+  return {s, f2_add(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb))};
+}
+__device__ __forceinline__ ff2 ff2_quick_two_sum(float2 a, float2 b) {
+  const float2 s = f2_add(a, b);
+  return {s, f2_sub(b, f2_sub(s, a))};
+}
+__device__ __forceinline__ ff2 ff2_two_prod(float2 a, float2 b) {
+  const float2 p = f2_mul(a, b);
+  return {p, f2_fma(a, b, make_float2(-p.x, -p.y))};
+}
+__device__ __forceinline__ ff2 ff2_add(ff2 a, ff2 b) {
+  ff2 s = ff2_two_sum(a.hi, b.hi);
+  const ff2 t = ff2_two_sum(a.lo, b.lo);
+  s.lo = f2_add(s.lo, t.hi);
+  s = ff2_quick_two_sum(s.hi, s.lo);
+  s.lo = f2_add(s.lo, t.lo);
+  return ff2_quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff2 ff2_add_abs(ff2 a, ff2 b) {
+  ff2 s = ff2_two_sum(a.hi, b.hi);
+  s.lo = f2_add(s.lo, f2_add(a.lo, b.lo));
+  return ff2_quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff2 ff2_neg(ff2 a) {
+  return {make_float2(-a.hi.x, -a.hi.y), make_float2(-a.lo.x, -a.lo.y)};
+}
+__device__ __forceinline__ ff2 ff2_sub(ff2 a, ff2 b) { return ff2_add(a, ff2_neg(b)); }
+__device__ __forceinline__ ff2 ff2_add_f(ff2 a, float2 b) {
+  ff2 s = ff2_two_sum(a.hi, b);
+  s.lo = f2_add(s.lo, a.lo);
+  return ff2_quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b) {
+  ff2 p = ff2_two_prod(a.hi, b.hi);
+  p.lo = f2_fma(a.hi, b.lo, f2_fma(a.lo, b.hi, p.lo));
+  return ff2_quick_two_sum(p.hi, p.lo);
+}
+// both lanes the same float-float constant
+__device__ __forceinline__ ff2 ff2_bc(float2 v) { return {f2_bc(v.x), f2_bc(v.y)}; }
+// the float-float values x (lane 0) and y (lane 1)
+__device__ __forceinline__ ff2 ff2_pack(ff x, ff y) { return {make_float2(x.hi, y.hi), make_float2(x.lo, y.lo)}; }
+
+// Constants of exp_ff2, filled on the host (ff_exp_consts).
 struct FFExp {
   float invL;        // 64 / ln 2
   float L1, L2, L3;  // ln2/64 = L1 + L2 + L3, L1 with 13 significant bits (n L1 exact for |n| < 2^11)
 };
 
-// e^x for |x| < 22 (|n| < 2^11); tab: 64 float-float values 2^(j/64) (shared or global memory).
-__device__ __forceinline__ ff exp_ff(ff x, const float2* tab, const FFExp& k) {
-  const float nf = rintf(x.hi * k.invL);
-  const int n = (int)nf;
-  // r = x - n L: n L1 is exact and x.hi - n L1 is exact (Sterbenz), so one fma gives it exactly
-  ff r = ff_two_sum(fmaf(-nf, k.L1, x.hi), x.lo);
-  r = ff_add(r, ff_two_prod(-nf, k.L2));
-  r = ff_add_f(r, -nf * k.L3);
-  // e^r - 1
-  ff r2 = ff_two_prod(r.hi, r.hi);
-  r2.lo = fmaf(2.0f * r.hi, r.lo, r2.lo);
-  const float c = r2.hi * r.hi * fmaf(r.hi, fmaf(r.hi, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f);
-  ff p = ff_add(r, ff{0.5f * r2.hi, 0.5f * r2.lo});
-  p = ff_add_f(p, c);
-  const ff T = ff_load(tab[n & 63]);
-  return ff_ldexp(ff_add(T, ff_mul(T, p)), n >> 6);
-}
-
-// Host: the 64-entry table 2^(j/64) and the constants of exp_ff, from extended precision.
+// Host: the 64-entry table 2^(j/64) and the constants of exp_ff2, from extended precision.
 void ff_exp_table_fill(float2* host64);
 FFExp ff_exp_consts();
 // Host: split an FP64 value into float-float (hi = FP32 rounding, lo = FP32 rounding of the rest).
 inline float2 ff_split_host(double v) {
   const float hi = (float)v;
   return make_float2(hi, (float)(v - (double)hi));
+}
+
+// e^x of both lanes, for |x| < 22 (|n| < 2^11) per lane; a lane outside that range gives an unspecified
+// value.  tab: 64 float-float values 2^(j/64) (shared or global memory).  The steps are Tang's, in packed
+// arithmetic; the rounding to n, the table reads and the final scaling by 2^(n >> 6) are per lane, the
+// scaling an exact multiply by a power of two built from its bits.
+__device__ __forceinline__ ff2 exp_ff2(ff2 x, const float2* tab, const FFExp& k) {
+  const float2 t = f2_mul(x.hi, f2_bc(k.invL));
+  const float2 nf = make_float2(rintf(t.x), rintf(t.y));
+  const int n0 = (int)nf.x, n1 = (int)nf.y;
+  const float2 mnf = make_float2(-nf.x, -nf.y);
+  ff2 r = ff2_two_sum(f2_fma(mnf, f2_bc(k.L1), x.hi), x.lo);
+  r = ff2_add(r, ff2_two_prod(mnf, f2_bc(k.L2)));
+  r = ff2_add_f(r, f2_mul(mnf, f2_bc(k.L3)));
+  ff2 r2 = ff2_two_prod(r.hi, r.hi);
+  r2.lo = f2_fma(f2_mul(f2_bc(2.0f), r.hi), r.lo, r2.lo);
+  const float2 c = f2_mul(f2_mul(r2.hi, r.hi),
+                          f2_fma(r.hi, f2_fma(r.hi, f2_bc(1.0f / 120.0f), f2_bc(1.0f / 24.0f)), f2_bc(1.0f / 6.0f)));
+  ff2 p = ff2_add(r, ff2{f2_mul(f2_bc(0.5f), r2.hi), f2_mul(f2_bc(0.5f), r2.lo)});
+  p = ff2_add_f(p, c);
+  const ff2 T = ff2_pack(ff_load(tab[n0 & 63]), ff_load(tab[n1 & 63]));
+  const ff2 v = ff2_add(T, ff2_mul(T, p));
+  const int m0 = min(max(n0 >> 6, -126), 127), m1 = min(max(n1 >> 6, -126), 127);
+  const float2 sc = make_float2(__int_as_float((m0 + 127) << 23), __int_as_float((m1 + 127) << 23));
+  return {f2_mul(v.hi, sc), f2_mul(v.lo, sc)};
 }
 
 }  // namespace isis

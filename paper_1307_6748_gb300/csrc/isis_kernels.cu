@@ -77,24 +77,47 @@ FFExp ff_exp_consts() {
   return k;
 }
 
+// e^x of x[2t] and x[2t+1] as the two lanes of exp_ff2 (one thread per pair).
 __global__ void selftest_exp_ff(const double* __restrict__ x, double* __restrict__ y, int n,
                                 const float2* __restrict__ tab, FFExp ek) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const ff v = exp_ff(ff_from_double(x[t]), tab, ek);
-  y[t] = (double)v.hi + (double)v.lo;
+  if (2 * t >= n) return;
+  const bool two = 2 * t + 1 < n;
+  const ff2 v = exp_ff2(ff2_pack(ff_from_double(x[2 * t]), ff_from_double(x[two ? 2 * t + 1 : 2 * t])), tab, ek);
+  y[2 * t] = (double)v.hi.x + (double)v.lo.x;
+  if (two) y[2 * t + 1] = (double)v.hi.y + (double)v.lo.y;
 }
 
+// Two cells per thread (n even): psi = u - ub and e^psi as packed float-float pairs, 16-byte stores.
 __global__ void fofr_prep_ff(const double* __restrict__ u, float2* __restrict__ psi, float2* __restrict__ E,
                              size_t n, float2 ubff, const float2* __restrict__ tab, FFExp ek) {
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const ff p = ff_sub(ff_split_bits(u[t]), ff_load(ubff));
-  psi[t] = ff_store(p);
-  // exp_ff covers |psi| < 22; beyond (no physical field gets there) the FP64 library exp
-  E[t] = ff_store(fabsf(p.hi) < 20.0f ? exp_ff(p, tab, ek) : ff_from_double(exp((double)p.hi + (double)p.lo)));
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * t >= n) return;
+  const size_t q = 2 * t;
+  const ff2 p = ff2_sub(ff2_pack(ff_split_bits(u[q]), ff_split_bits(u[q + 1])), ff2_bc(ubff));
+  reinterpret_cast<float4*>(psi)[t] = make_float4(p.hi.x, p.lo.x, p.hi.y, p.lo.y);
+  // exp_ff2 covers |psi| < 22; beyond (no physical field gets there) the FP64 library exp
+  ff2 e = exp_ff2(p, tab, ek);
+  if (!(fabsf(p.hi.x) < 20.0f)) {
+    const ff v = ff_from_double(exp((double)p.hi.x + (double)p.lo.x));
+    e.hi.x = v.hi;
+    e.lo.x = v.lo;
+  }
+  if (!(fabsf(p.hi.y) < 20.0f)) {
+    const ff v = ff_from_double(exp((double)p.hi.y + (double)p.lo.y));
+    e.hi.y = v.hi;
+    e.lo.y = v.lo;
+  }
+  reinterpret_cast<float4*>(E)[t] = make_float4(e.hi.x, e.lo.x, e.hi.y, e.lo.y);
 }
 
+// The pair (k, k+1) of a float-float grid starting at cell q (q even): one 16-byte load.
+__device__ __forceinline__ ff2 ff2_pair(const float2* __restrict__ a, size_t q) {
+  const float4 v = *reinterpret_cast<const float4*>(a + q);
+  return ff2{make_float2(v.x, v.z), make_float2(v.y, v.w)};
+}
+
+// Two cells per thread, (k, k+1) with k even, in packed float-float arithmetic (see outer_residual_ff).
 __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, FofrFF c,
                                                                        const double* __restrict__ eta,
                                                                        const float2* __restrict__ psi,
@@ -106,34 +129,61 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, F
   __shared__ float2 stab[64];
   if (threadIdx.x < 64) stab[threadIdx.x] = tab[threadIdx.x];
   __syncthreads();
-  const size_t n = (size_t)1 << (3 * lg);
-  const int N = 1 << lg, m = N - 1;
-  const ff Cih2 = ff_load(c.Cih2), K1 = ff_load(c.K1), Kx = ff_load(c.Kx), minv = ff_load(c.minv);
+  const size_t np = (size_t)1 << (3 * lg - 1), half = np;
+  const int m = (1 << lg) - 1;
+  const ff2 Cih2 = ff2_bc(c.Cih2), K1 = ff2_bc(c.K1), Kx = ff2_bc(c.Kx), minv = ff2_bc(c.minv);
   float acc = 0.f;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    int k = (int)(t & m), j = (int)((t >> lg) & m), i = (int)(t >> (2 * lg));
-    size_t nb[6] = {cidx(lg, (i + 1) & m, j, k), cidx(lg, (i - 1) & m, j, k), cidx(lg, i, (j + 1) & m, k),
-                    cidx(lg, i, (j - 1) & m, k), cidx(lg, i, j, (k + 1) & m), cidx(lg, i, j, (k - 1) & m)};
-    const ff pc = ff_load(psi[t]), ec = ff_load(E[t]);
-    ff sd = {0.f, 0.f}, se = {0.f, 0.f};
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t q = 2 * t;
+    const int k = (int)(q & m), j = (int)((q >> lg) & m), i = (int)(q >> (2 * lg));
+    const size_t pq[4] = {cidx(lg, (i + 1) & m, j, k), cidx(lg, (i - 1) & m, j, k), cidx(lg, i, (j + 1) & m, k),
+                          cidx(lg, i, (j - 1) & m, k)};
+    const size_t qm = cidx(lg, i, j, (k - 1) & m), qp = cidx(lg, i, j, (k + 2) & m);
+    const ff2 pc = ff2_pair(psi, q), ec = ff2_pair(E, q);
+    // the six neighbour pairs (i+1, i-1, j+1, j-1, k+1, k-1) of psi and of e^psi
+    auto nbr = [&](const float2* __restrict__ a, const ff2& own, int d) -> ff2 {
+      if (d < 4) return ff2_pair(a, pq[d]);
+      if (d == 4) {
+        const float2 v = a[qp];
+        return ff2{make_float2(own.hi.y, v.x), make_float2(own.lo.y, v.y)};
+      }
+      const float2 v = a[qm];
+      return ff2{make_float2(v.x, own.hi.x), make_float2(v.y, own.lo.x)};
+    };
+    ff2 sd = {f2_bc(0.f), f2_bc(0.f)}, se = sd;
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
-      const ff dp = ff_add_abs(ff_load(psi[nb[d]]), ff_neg(pc));
-      sd = ff_add_abs(sd, dp);
-      se = ff_add_abs(se, ff_mul(ff_load(E[nb[d]]), dp));
+      const ff2 dp = ff2_add_abs(nbr(psi, pc, d), ff2_neg(pc));
+      sd = ff2_add_abs(sd, dp);
+      se = ff2_add_abs(se, ff2_mul(nbr(E, ec, d), dp));
     }
-    ff flux = ff_add(ff_mul(ec, sd), se);
-    flux = {0.5f * flux.hi, 0.5f * flux.lo};
-    const ff em = fabsf(pc.hi) < 20.0f
-                      ? ff_add_f(exp_ff(ff_mul(pc, minv), stab, c.ek), -1.0f)
-                      : ff_from_double(expm1(-((double)pc.hi + (double)pc.lo) * c.inv_np1));
-    ff S = ff_sub(ff_mul(K1, ff_add_f(ff_split_bits(eta[t]), -1.0f)), ff_mul(Kx, em));
-    S = ff_add_f(S, c.dK);
-    const ff F = ff_sub(ff_mul(flux, Cih2), S);
-    const size_t o = lidx<float>(lg, i, j, k);
-    r32[o] = -(F.hi + F.lo);
-    B32[o] = ff_add(pc, ff_load(c.ubff)).hi;  // fp32(u), u = psi + ub
-    acc = fmaf(F.hi, F.hi, acc);
+    ff2 flux = ff2_add(ff2_mul(ec, sd), se);
+    flux = {f2_mul(f2_bc(0.5f), flux.hi), f2_mul(f2_bc(0.5f), flux.lo)};
+    ff2 em = ff2_add_f(exp_ff2(ff2_mul(pc, minv), stab, c.ek), f2_bc(-1.0f));
+    if (!(fabsf(pc.hi.x) < 20.0f)) {
+      const ff v = ff_from_double(expm1(-((double)pc.hi.x + (double)pc.lo.x) * c.inv_np1));
+      em.hi.x = v.hi;
+      em.lo.x = v.lo;
+    }
+    if (!(fabsf(pc.hi.y) < 20.0f)) {
+      const ff v = ff_from_double(expm1(-((double)pc.hi.y + (double)pc.lo.y) * c.inv_np1));
+      em.hi.y = v.hi;
+      em.lo.y = v.lo;
+    }
+    const ff2 et = ff2_pack(ff_split_bits(eta[q]), ff_split_bits(eta[q + 1]));  // the caller's array
+    ff2 S = ff2_sub(ff2_mul(K1, ff2_add_f(et, f2_bc(-1.0f))), ff2_mul(Kx, em));
+    S = ff2_add_f(S, f2_bc(c.dK));
+    const ff2 F = ff2_sub(ff2_mul(flux, Cih2), S);
+    const float2 r = f2_add(F.hi, F.lo);
+    const float2 B = ff2_add(pc, ff2_bc(c.ubff)).hi;  // fp32(u), u = psi + ub
+    // cell k has colour (i + j + k) & 1, cell k + 1 the other; both at place q / 2 of their half
+    const size_t o0 = (((size_t)(i + j) & 1u) ? half : 0) + t, o1 = (((size_t)(i + j) & 1u) ? 0 : half) + t;
+    r32[o0] = -r.x;
+    r32[o1] = -r.y;
+    B32[o0] = B.x;
+    B32[o1] = B.y;
+    acc = fmaf(F.hi.x, F.hi.x, acc);
+    acc = fmaf(F.hi.y, F.hi.y, acc);
   }
   block_sum_store<double>((double)acc, part);
 }

@@ -39,7 +39,7 @@ struct Workspace {
   int* iflags = nullptr;      // [0] coarse flags, [1] coarse steps max
   void* host = nullptr;       // mapped pinned readback area: [0..3] doubles, then ints at (int*)(host + 4)
   double* host_dev = nullptr;  // its device address
-  float2* exptab_ff = nullptr;  // 2^(j/64), j < 64, float-float, for exp_ff
+  float2* exptab_ff = nullptr;  // 2^(j/64), j < 64, float-float, for exp_ff2
   double* b64 = nullptr;      // finest level, 8 bytes per cell: psi = u - u_bar (float-float), f(R) residual
   double* s64 = nullptr;      // finest level, 8 bytes per cell: e^psi (float-float), f(R) residual
   std::vector<void*> owned;
@@ -421,37 +421,54 @@ static __global__ void phi_to_ff(const double* __restrict__ phi, float2* __restr
   if (t < n) out[t] = ff_store(ff_split_bits(phi[t]));
 }
 // r = -L(phi) in float-float from phi's float-float copy pff; B = the copy's high part (fp32 phi).
+// Two cells per thread, (k, k+1) with k even, as the lanes of packed FP32x2 float-float arithmetic (ff2):
+// the pair's own values and its i and j neighbours are 16-byte loads, the k neighbours outside the pair two
+// 8-byte loads.  In the red/black output the pair's two cells sit at the same place of the two halves.
 template <Model M>
 __global__ void __launch_bounds__(kNormThreads) outer_residual_ff(int lg, ResFF c, const double* __restrict__ eta,
                                                                   const float2* __restrict__ pff,
                                                                   float* __restrict__ r32, float* __restrict__ B32,
                                                                   double* __restrict__ part) {
-  const size_t n = (size_t)1 << (3 * lg);
+  const size_t np = (size_t)1 << (3 * lg - 1);
   const int m = (1 << lg) - 1;
-  const ff ih2 = ff_load(c.ih2), K = ff_load(c.K);
+  const size_t half = np;
+  const ff2 ih2 = ff2_bc(c.ih2), K = ff2_bc(c.K);
   float acc = 0.f;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    int k = (int)(t & m), j = (int)((t >> lg) & m), i = (int)(t >> (2 * lg));
-    size_t nb[6] = {cidx(lg, (i + 1) & m, j, k), cidx(lg, (i - 1) & m, j, k), cidx(lg, i, (j + 1) & m, k),
-                    cidx(lg, i, (j - 1) & m, k), cidx(lg, i, j, (k + 1) & m), cidx(lg, i, j, (k - 1) & m)};
-    const ff pc = ff_load(pff[t]);
-    ff sd = {0.f, 0.f};
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t q = 2 * t;
+    const int k = (int)(q & m), j = (int)((q >> lg) & m), i = (int)(q >> (2 * lg));
+    auto pair = [&](size_t at) {
+      const float4 v = *reinterpret_cast<const float4*>(pff + at);
+      return ff2{make_float2(v.x, v.z), make_float2(v.y, v.w)};
+    };
+    const ff2 pc = pair(q);
+    const float2 km = pff[cidx(lg, i, j, (k - 1) & m)], kp = pff[cidx(lg, i, j, (k + 2) & m)];
+    const ff2 nb[6] = {pair(cidx(lg, (i + 1) & m, j, k)), pair(cidx(lg, (i - 1) & m, j, k)),
+                       pair(cidx(lg, i, (j + 1) & m, k)), pair(cidx(lg, i, (j - 1) & m, k)),
+                       ff2{make_float2(pc.hi.y, kp.x), make_float2(pc.lo.y, kp.y)},   // k + 1
+                       ff2{make_float2(km.x, pc.hi.x), make_float2(km.y, pc.lo.x)}};  // k - 1
+    ff2 sd = {f2_bc(0.f), f2_bc(0.f)};
 #pragma unroll
-    for (int d = 0; d < 6; ++d) sd = ff_add_abs(sd, ff_add_abs(ff_load(pff[nb[d]]), ff_neg(pc)));
-    const ff lap = ff_mul(sd, ih2);
-    ff F;
-    const ff et = ff_split_bits(eta[t]);
+    for (int d = 0; d < 6; ++d) sd = ff2_add_abs(sd, ff2_add_abs(nb[d], ff2_neg(pc)));
+    const ff2 lap = ff2_mul(sd, ih2);
+    const ff2 et = ff2_pack(ff_split_bits(eta[q]), ff_split_bits(eta[q + 1]));  // the caller's array: 8-byte loads
+    ff2 F;
     if constexpr (M == POI) {
-      F = ff_sub(lap, ff_mul(K, ff_sub(et, ff_load(c.eta_mean))));
+      F = ff2_sub(lap, ff2_mul(K, ff2_sub(et, ff2_bc(c.eta_mean))));
     } else {  // symmetron: L = lap - A [(s eta - 1) chi + chi^3]
-      const ff q = ff_add_f(ff_mul(ff_load(c.s), et), -1.0f);
-      const ff x2 = ff_mul(pc, pc);
-      F = ff_sub(lap, ff_mul(K, ff_mul(ff_add(q, x2), pc)));
+      const ff2 qv = ff2_add_f(ff2_mul(ff2_bc(c.s), et), f2_bc(-1.0f));
+      const ff2 x2 = ff2_mul(pc, pc);
+      F = ff2_sub(lap, ff2_mul(K, ff2_mul(ff2_add(qv, x2), pc)));
     }
-    const size_t o = lidx<float>(lg, i, j, k);
-    r32[o] = -(F.hi + F.lo);
-    B32[o] = pc.hi;
-    acc = fmaf(F.hi, F.hi, acc);
+    const float2 r = f2_add(F.hi, F.lo);
+    // cell k has colour (i + j + k) & 1, cell k + 1 the other; both at place q / 2 of their half
+    const size_t o0 = (((size_t)(i + j) & 1u) ? half : 0) + t, o1 = (((size_t)(i + j) & 1u) ? 0 : half) + t;
+    r32[o0] = -r.x;
+    r32[o1] = -r.y;
+    B32[o0] = pc.hi.x;
+    B32[o1] = pc.hi.y;
+    acc = fmaf(F.hi.x, F.hi.x, acc);
+    acc = fmaf(F.hi.y, F.hi.y, acc);
   }
   block_sum_store<double>((double)acc, part);
 }
@@ -467,7 +484,7 @@ struct FofrFF {
 };
 __global__ void selftest_exp_ff(const double* __restrict__ x, double* __restrict__ y, int n,
                                 const float2* __restrict__ tab, FFExp ek);
-// first pass: psi = u - ub and e^psi per cell (float-float, 8 bytes each)
+// first pass: psi = u - ub and e^psi per cell (float-float, 8 bytes each), two cells per thread (n even)
 __global__ void fofr_prep_ff(const double* __restrict__ u, float2* __restrict__ psi, float2* __restrict__ E,
                              size_t n, float2 ubff, const float2* __restrict__ tab, FFExp ek);
 // second pass: r = -L(u) (written FP32, red/black), B = fp32(u), block partials of r^2
@@ -745,7 +762,7 @@ isis_status solve_refine(const SolveArgs& A) {
       float2* psi_ff = reinterpret_cast<float2*>(ws->b64);
       float2* E_ff = reinterpret_cast<float2*>(ws->s64);
       ISIS_LAUNCH(KK_OUTER_RESID, 24.0 * n, st,
-                  (fofr_prep_ff<<<nblk(n, 256), 256, 0, st>>>(phi64, psi_ff, E_ff, n, ffc.ubff, ws->exptab_ff,
+                  (fofr_prep_ff<<<nblk(n / 2, 256), 256, 0, st>>>(phi64, psi_ff, E_ff, n, ffc.ubff, ws->exptab_ff,
                                                                ffc.ek)));
       ISIS_LAUNCH(KK_OUTER_RESID, 32.0 * n, st,
                   (outer_residual_fofr_ff<<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, ffc, eta64, psi_ff, E_ff,
