@@ -66,13 +66,6 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
   p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
   return ff_quick_two_sum(p.hi, p.lo);
 }
-__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
-  ff p = ff_two_prod(a.hi, b);
-  p.lo = fmaf(a.lo, b, p.lo);
-  return ff_quick_two_sum(p.hi, p.lo);
-}
-// exact scaling by a power of two
-__device__ __forceinline__ ff ff_ldexp(ff a, int m) { return {ldexpf(a.hi, m), ldexpf(a.lo, m)}; }
 // FP64 -> float-float (one FP64 subtraction) and back
 __device__ __forceinline__ ff ff_from_double(double d) {
   const float hi = __double2float_rn(d);
