@@ -75,6 +75,25 @@ def workload(args):
 
 
 # ---------------------------------------------------------------------------
+# Ranks (one process per GPU): each rank solves its own seeded problem (replicas)
+# ---------------------------------------------------------------------------
+
+def replica_seed(rank: int) -> int:
+    """Seed of rank `rank`'s Zel'dovich particles: every replica solves its own problem."""
+    return 3 + 1000 * rank
+
+
+def max_over_ranks(v: float, dist, dev) -> float:
+    """The largest v over all ranks (v itself without a process group)."""
+    if dist is None:
+        return v
+    import torch
+    tt = torch.tensor([v], device=dev, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+# ---------------------------------------------------------------------------
 # The timed step
 # ---------------------------------------------------------------------------
 
@@ -285,7 +304,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     N, box = args.N, args.box
-    x, y, z = synth.zeldovich(N, box, seed=3 + 1000 * rank, device=dev)
+    x, y, z = synth.zeldovich(N, box, seed=replica_seed(rank), device=dev)
     npart = x.numel()
     S = ForceStep(args, dev, npart)
     grid, psym, pfr, a = S.grid, S.psym, S.pfr, S.a
@@ -325,11 +344,7 @@ def main():
     isis.prof_enable(False)
     prof = isis.prof_read()
     total_ms = t0.elapsed_time(t1)
-    ms = total_ms / args.steps
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(total_ms / args.steps, dist, dev)
     parts = ["deposit", "poisson", "symmetron", "fofr", "forces"]
     breakdown = {p: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, p in enumerate(parts)}
 
@@ -340,13 +355,6 @@ def main():
         hg = [torch.empty(npart, dtype=torch.float32).pin_memory() for _ in range(6)]
         pos = [tuple(torch.empty_like(x) for _ in range(3)) for _ in range(2)]
         gb = [g, [torch.empty_like(t) for t in g]]
-
-        def reduce_max(v):
-            if dist is None:
-                return v
-            tt = torch.tensor([v], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            return float(tt.item())
 
         # serial: every copy on the compute stream, before and after its step
         barrier()
@@ -360,7 +368,7 @@ def main():
                 h.copy_(d, non_blocking=True)
         e1.record(stream)
         barrier()
-        serial = reduce_max(e0.elapsed_time(e1) / args.steps)
+        serial = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
 
         # pipelined: copies on a second stream, positions and forces double-buffered; step s's positions
         # arrive while step s-1 computes, and each model's forces leave as soon as they exist
@@ -412,7 +420,7 @@ def main():
         stream.wait_stream(cs)
         e1.record(stream)
         barrier()
-        ems = reduce_max(e0.elapsed_time(e1) / args.steps)
+        ems = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
         e2e = {"value": ems, "unit": "ms", "h2d_bytes_per_step": 3 * npart * 4, "d2h_bytes_per_step": 6 * npart * 4,
                "copies": "on a second stream, positions and forces double-buffered: step s's positions are copied "
                          "while step s-1 computes, each model's forces are read back while the next solve runs",
