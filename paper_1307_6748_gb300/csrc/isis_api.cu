@@ -272,6 +272,10 @@ void prof_pre(cudaStream_t st) {
   g_pending = a;
 }
 
+bool prof_enabled() { return g_prof_on; }
+long long prof_launches() { return g_launches; }
+void prof_add_launches(long long n) { g_launches += n; }
+
 void prof_post(int kind, double bytes, cudaStream_t st) {
   ++g_launches;
   if (!g_prof_on || g_pending < 0) return;

@@ -265,10 +265,10 @@ constexpr size_t coarse_bytes_per_cell() {
   return (FM == DELTA ? 6 : 5) * sizeof(T) + sizeof(int);
 }
 
-// The coarsest patch level held in shared memory (u, u^Pre, m, eta, Sigma, B of every cell, and the unknowns
-// of each colour as lists): u^Pre = u, then kCoarseSweeps red/black sweeps, in one block; u written back.
-// GB300's FP64 units are few and this is one block, so each half-sweep costs its latency: shared memory
-// and the lists keep that short.
+// The coarsest patch level held in shared memory (u, u^Pre, m, eta, Sigma, and B in the DELTA form, of every
+// cell, and the unknowns of each colour as lists): u^Pre = u, then kCoarseSweeps red/black sweeps, in one
+// block; u written back.  One block pays each half-sweep's latency (in FP64 on GB300's few FP64 units):
+// shared memory and the lists keep that short.
 template <Model M, Form FM, class T>
 __global__ void __launch_bounds__(kCoarseThreads) pt_coarsest_smem(PL<T> L, Coef c) {
   extern __shared__ __align__(16) unsigned char pt_smem[];
@@ -465,16 +465,61 @@ struct PatchSolver {
   double* part = nullptr;
   double* host = nullptr;
   int* counts = nullptr;
+  cudaStream_t strm;  // the caller's stream; a private one while a V-cycle is captured into a graph
+  // one V-cycle (vcycle or vcycle32 from the finest level) as a CUDA graph: the same launches, captured once
+  // per solve and replayed for every cycle, which takes the host's launch overhead off these small grids
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_launches = 0;
+  bool try_graph = true;
 
-  explicit PatchSolver(const PatchArgs& a) : A(a) {}
+  explicit PatchSolver(const PatchArgs& a) : A(a), strm(a.st) {}
+  ~PatchSolver() {
+    if (graph) {
+      cudaStreamSynchronize(A.st);
+      cudaGraphExecDestroy(graph);
+    }
+    if (cap) cudaStreamDestroy(cap);
+  }
+
+  // One V-cycle from the finest level: through the graph, captured at the first call on a private stream (the
+  // caller's stream may be the legacy default stream, which cannot be captured) and launched on the caller's;
+  // launch by launch while per-launch events are on or if the capture fails.
+  template <class Cycle>
+  isis_status cycle_graphed(Cycle cycle) {
+    if (!graph && try_graph && !prof_enabled()) {
+      try_graph = false;
+      if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess &&
+          cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const long long before = prof_launches();
+        strm = cap;
+        const isis_status s = cycle();
+        strm = A.st;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cap, &g);
+        graph_launches = prof_launches() - before;
+        prof_add_launches(-graph_launches);  // recorded, not run
+        if (s != ISIS_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&graph, g, 0) != cudaSuccess)
+          graph = nullptr;
+        if (g) cudaGraphDestroy(g);
+      }
+      cudaGetLastError();  // a capture that failed leaves no error behind: the cycle then runs launch by launch
+    }
+    if (graph) {
+      if (cudaGraphLaunch(graph, A.st) != cudaSuccess) return ISIS_ECUDA;
+      prof_add_launches(graph_launches);
+      return ISIS_OK;
+    }
+    return cycle();
+  }
 
   // bytes a level-sweep kernel reads and writes once (u, m, eta, pre, sig; u written)
   static double sweep_bytes(const PLevel& L) { return 48.0 * L.cells(); }
 
   isis_status sum_parts(double* out) {
-    if (cudaMemcpyAsync(host, part, kPNormBlocks * sizeof(double), cudaMemcpyDeviceToHost, A.st) != cudaSuccess)
+    if (cudaMemcpyAsync(host, part, kPNormBlocks * sizeof(double), cudaMemcpyDeviceToHost, strm) != cudaSuccess)
       return ISIS_ECUDA;
-    if (cudaStreamSynchronize(A.st) != cudaSuccess) return ISIS_ECUDA;
+    if (cudaStreamSynchronize(strm) != cudaSuccess) return ISIS_ECUDA;
     double s = 0.0;
     for (int b = 0; b < kPNormBlocks; ++b) s += host[b];
     *out = s;
@@ -483,8 +528,8 @@ struct PatchSolver {
 
   isis_status norm(double* rms) {
     const PLevel& F = lev[0];
-    ISIS_LAUNCH(KK_PATCH_OTHER, sweep_bytes(F), A.st,
-                (pt_norm<M><<<kPNormBlocks, kPT, 0, A.st>>>(F.view(false), A.coef, part)));
+    ISIS_LAUNCH(KK_PATCH_OTHER, sweep_bytes(F), strm,
+                (pt_norm<M><<<kPNormBlocks, kPT, 0, strm>>>(F.view(false), A.coef, part)));
     double s = 0.0;
     isis_status st = sum_parts(&s);
     if (st != ISIS_OK) return st;
@@ -497,8 +542,8 @@ struct PatchSolver {
     for (int s = 0; s < nsweep; ++s)
       for (int color = 0; color < 2; ++color) {
         if (L.count[color] == 0) continue;
-        ISIS_LAUNCH(KK_PATCH_SMOOTH, 48.0 * L.count[color], A.st,
-                    (pt_smooth_list<M, FIELD, double><<<nblk(L.count[color]), kPT, 0, A.st>>>(
+        ISIS_LAUNCH(KK_PATCH_SMOOTH, 48.0 * L.count[color], strm,
+                    (pt_smooth_list<M, FIELD, double><<<nblk(L.count[color]), kPT, 0, strm>>>(
                         L.view(l > 0), A.coef, L.list[color], L.count[color], s == 0 ? L.pre : nullptr)));
       }
     return ISIS_OK;
@@ -509,27 +554,27 @@ struct PatchSolver {
     if (l + 1 == lev.size()) {
       const size_t smem = coarse_bytes_per_cell<FIELD, double>() * L.cells();
       if (smem <= kCoarseSmem) {
-        ISIS_LAUNCH(KK_PATCH_COARSEST, 40.0 * L.cells(), A.st,
-                    (pt_coarsest_smem<M, FIELD, double><<<1, kCoarseThreads, smem, A.st>>>(L.view(l > 0), A.coef)));
+        ISIS_LAUNCH(KK_PATCH_COARSEST, 40.0 * L.cells(), strm,
+                    (pt_coarsest_smem<M, FIELD, double><<<1, kCoarseThreads, smem, strm>>>(L.view(l > 0), A.coef)));
       } else {
-        ISIS_LAUNCH(KK_PATCH_COARSEST, kCoarseSweeps * sweep_bytes(L), A.st,
-                    (pt_coarsest<M, FIELD, double><<<1, 1024, 0, A.st>>>(L.view(l > 0), A.coef, L.pre)));
+        ISIS_LAUNCH(KK_PATCH_COARSEST, kCoarseSweeps * sweep_bytes(L), strm,
+                    (pt_coarsest<M, FIELD, double><<<1, 1024, 0, strm>>>(L.view(l > 0), A.coef, L.pre)));
       }
       return ISIS_OK;
     }
     const PLevel& C = lev[l + 1];
     isis_status st = phase(l, A.nu1);
     if (st != ISIS_OK) return st;
-    ISIS_LAUNCH(KK_PATCH_OTHER, 48.0 * L.cells(), A.st,
-                (pt_resid<M, FIELD, double><<<nblk(L.cells()), kPT, 0, A.st>>>(L.view(l > 0), A.coef, L.res)));
-    ISIS_LAUNCH(KK_PATCH_OTHER, 10.0 * C.cells() * 8.0, A.st,
-                (pt_restrict<double><<<nblk(C.cells()), kPT, 0, A.st>>>(L.u, C.u, C.n[0], C.n[1], C.n[2], 0, C.u0)));
-    ISIS_LAUNCH(KK_PATCH_OTHER, 48.0 * C.cells() + 64.0 * C.cells(), A.st,
-                (pt_sigma<M, FIELD, double><<<nblk(C.cells()), kPT, 0, A.st>>>(C.view(false), A.coef, L.res, C.sig)));
+    ISIS_LAUNCH(KK_PATCH_OTHER, 48.0 * L.cells(), strm,
+                (pt_resid<M, FIELD, double><<<nblk(L.cells()), kPT, 0, strm>>>(L.view(l > 0), A.coef, L.res)));
+    ISIS_LAUNCH(KK_PATCH_OTHER, 10.0 * C.cells() * 8.0, strm,
+                (pt_restrict<double><<<nblk(C.cells()), kPT, 0, strm>>>(L.u, C.u, C.n[0], C.n[1], C.n[2], 0, C.u0)));
+    ISIS_LAUNCH(KK_PATCH_OTHER, 48.0 * C.cells() + 64.0 * C.cells(), strm,
+                (pt_sigma<M, FIELD, double><<<nblk(C.cells()), kPT, 0, strm>>>(C.view(false), A.coef, L.res, C.sig)));
     st = vcycle(l + 1);
     if (st != ISIS_OK) return st;
-    ISIS_LAUNCH(KK_PATCH_OTHER, 24.0 * L.cells() + 16.0 * C.cells(), A.st,
-                (pt_prolong<double><<<nblk(L.cells()), kPT, 0, A.st>>>(L.view(l > 0), C.u, C.u0, C.n[0], C.n[1],
+    ISIS_LAUNCH(KK_PATCH_OTHER, 24.0 * L.cells() + 16.0 * C.cells(), strm,
+                (pt_prolong<double><<<nblk(L.cells()), kPT, 0, strm>>>(L.view(l > 0), C.u, C.u0, C.n[0], C.n[1],
                                                                        C.n[2])));
     return phase(l, A.nu2);
   }
@@ -540,8 +585,8 @@ struct PatchSolver {
     for (int s = 0; s < nsweep; ++s)
       for (int color = 0; color < 2; ++color) {
         if (L.count[color] == 0) continue;
-        ISIS_LAUNCH(KK_PATCH_SMOOTH, 28.0 * L.count[color], A.st,
-                    (pt_smooth_list<M, DELTA, float><<<nblk(L.count[color]), kPT, 0, A.st>>>(
+        ISIS_LAUNCH(KK_PATCH_SMOOTH, 28.0 * L.count[color], strm,
+                    (pt_smooth_list<M, DELTA, float><<<nblk(L.count[color]), kPT, 0, strm>>>(
                         L.view32(true), A.coef, L.list[color], L.count[color], s == 0 ? L.pre32 : nullptr)));
       }
     return ISIS_OK;
@@ -552,70 +597,70 @@ struct PatchSolver {
     if (l + 1 == lev.size()) {
       const size_t smem = coarse_bytes_per_cell<DELTA, float>() * L.cells();
       if (smem <= kCoarseSmem) {
-        ISIS_LAUNCH(KK_PATCH_COARSEST, 24.0 * L.cells(), A.st,
-                    (pt_coarsest_smem<M, DELTA, float><<<1, kCoarseThreads, smem, A.st>>>(L.view32(true), A.coef)));
+        ISIS_LAUNCH(KK_PATCH_COARSEST, 24.0 * L.cells(), strm,
+                    (pt_coarsest_smem<M, DELTA, float><<<1, kCoarseThreads, smem, strm>>>(L.view32(true), A.coef)));
       } else {
-        ISIS_LAUNCH(KK_PATCH_COARSEST, kCoarseSweeps * 28.0 * L.cells(), A.st,
-                    (pt_coarsest<M, DELTA, float><<<1, 1024, 0, A.st>>>(L.view32(true), A.coef, L.pre32)));
+        ISIS_LAUNCH(KK_PATCH_COARSEST, kCoarseSweeps * 28.0 * L.cells(), strm,
+                    (pt_coarsest<M, DELTA, float><<<1, 1024, 0, strm>>>(L.view32(true), A.coef, L.pre32)));
       }
       return ISIS_OK;
     }
     const PLevel& C = lev[l + 1];
     isis_status st = phase32(l, A.nu1);
     if (st != ISIS_OK) return st;
-    ISIS_LAUNCH(KK_PATCH_OTHER, 28.0 * L.cells(), A.st,
-                (pt_resid<M, DELTA, float><<<nblk(L.cells()), kPT, 0, A.st>>>(L.view32(true), A.coef, L.res32)));
-    ISIS_LAUNCH(KK_PATCH_OTHER, 5.0 * C.cells() * 8.0, A.st,
-                (pt_restrict<float><<<nblk(C.cells()), kPT, 0, A.st>>>(L.e, C.e, C.n[0], C.n[1], C.n[2], 0, C.e0)));
-    ISIS_LAUNCH(KK_PATCH_OTHER, 24.0 * C.cells() + 32.0 * C.cells(), A.st,
-                (pt_sigma<M, DELTA, float><<<nblk(C.cells()), kPT, 0, A.st>>>(C.view32(false), A.coef, L.res32,
+    ISIS_LAUNCH(KK_PATCH_OTHER, 28.0 * L.cells(), strm,
+                (pt_resid<M, DELTA, float><<<nblk(L.cells()), kPT, 0, strm>>>(L.view32(true), A.coef, L.res32)));
+    ISIS_LAUNCH(KK_PATCH_OTHER, 5.0 * C.cells() * 8.0, strm,
+                (pt_restrict<float><<<nblk(C.cells()), kPT, 0, strm>>>(L.e, C.e, C.n[0], C.n[1], C.n[2], 0, C.e0)));
+    ISIS_LAUNCH(KK_PATCH_OTHER, 24.0 * C.cells() + 32.0 * C.cells(), strm,
+                (pt_sigma<M, DELTA, float><<<nblk(C.cells()), kPT, 0, strm>>>(C.view32(false), A.coef, L.res32,
                                                                              C.sig32)));
     st = vcycle32(l + 1);
     if (st != ISIS_OK) return st;
-    ISIS_LAUNCH(KK_PATCH_OTHER, 12.0 * L.cells() + 8.0 * C.cells(), A.st,
-                (pt_prolong<float><<<nblk(L.cells()), kPT, 0, A.st>>>(L.view32(true), C.e, C.e0, C.n[0], C.n[1],
+    ISIS_LAUNCH(KK_PATCH_OTHER, 12.0 * L.cells() + 8.0 * C.cells(), strm,
+                (pt_prolong<float><<<nblk(L.cells()), kPT, 0, strm>>>(L.view32(true), C.e, C.e0, C.n[0], C.n[1],
                                                                       C.n[2])));
     return phase32(l, A.nu2);
   }
 
   isis_status setup() {
     const PLevel& F = lev[0];
-    ISIS_LAUNCH(KK_PATCH_OTHER, 9.0 * F.cells(), A.st,
-                (pt_mask0<<<nblk(F.cells()), kPT, 0, A.st>>>(A.flags, A.n[1], A.n[2], F.m, F.n[0], F.n[1], F.n[2])));
+    ISIS_LAUNCH(KK_PATCH_OTHER, 9.0 * F.cells(), strm,
+                (pt_mask0<<<nblk(F.cells()), kPT, 0, strm>>>(A.flags, A.n[1], A.n[2], F.m, F.n[0], F.n[1], F.n[2])));
     for (size_t l = 1; l < lev.size(); ++l) {
       const PLevel& C = lev[l];
       const PLevel& L = lev[l - 1];
-      ISIS_LAUNCH(KK_PATCH_OTHER, 9.0 * C.cells() * 8.0, A.st,
-                  (pt_restrict<double><<<nblk(C.cells()), kPT, 0, A.st>>>(L.m, C.m, C.n[0], C.n[1], C.n[2], 1)));
-      ISIS_LAUNCH(KK_PATCH_OTHER, 9.0 * C.cells() * 8.0, A.st,
-                  (pt_restrict<double><<<nblk(C.cells()), kPT, 0, A.st>>>(L.eta, C.eta, C.n[0], C.n[1], C.n[2])));
+      ISIS_LAUNCH(KK_PATCH_OTHER, 9.0 * C.cells() * 8.0, strm,
+                  (pt_restrict<double><<<nblk(C.cells()), kPT, 0, strm>>>(L.m, C.m, C.n[0], C.n[1], C.n[2], 1)));
+      ISIS_LAUNCH(KK_PATCH_OTHER, 9.0 * C.cells() * 8.0, strm,
+                  (pt_restrict<double><<<nblk(C.cells()), kPT, 0, strm>>>(L.eta, C.eta, C.n[0], C.n[1], C.n[2])));
     }
-    ISIS_LAUNCH(KK_PATCH_OTHER, 16.0 * F.cells(), A.st,
-                (pt_interp<<<nblk(F.cells()), kPT, 0, A.st>>>(A.parent, A.pn[0], A.pn[1], A.pn[2], A.origin[0],
+    ISIS_LAUNCH(KK_PATCH_OTHER, 16.0 * F.cells(), strm,
+                (pt_interp<<<nblk(F.cells()), kPT, 0, strm>>>(A.parent, A.pn[0], A.pn[1], A.pn[2], A.origin[0],
                                                               A.origin[1], A.origin[2], A.periodic, F.m, F.u,
                                                               F.n[0], F.n[1], F.n[2], A.init_parent)));
     // the unknowns of each level and colour
-    if (cudaMemsetAsync(counts, 0, 2 * lev.size() * sizeof(int), A.st) != cudaSuccess) return ISIS_ECUDA;
+    if (cudaMemsetAsync(counts, 0, 2 * lev.size() * sizeof(int), strm) != cudaSuccess) return ISIS_ECUDA;
     for (size_t l = 0; l < lev.size(); ++l) {
       const PLevel& L = lev[l];
-      ISIS_LAUNCH(KK_PATCH_OTHER, 8.0 * L.cells(), A.st,
-                  (pt_compact<<<nblk(L.cells()), kPT, 0, A.st>>>(L.view(false), L.list[0], L.list[1],
+      ISIS_LAUNCH(KK_PATCH_OTHER, 8.0 * L.cells(), strm,
+                  (pt_compact<<<nblk(L.cells()), kPT, 0, strm>>>(L.view(false), L.list[0], L.list[1],
                                                                  counts + 2 * l)));
     }
     // FP32 copies of the masks (exact: means of +-1 over 8^l cells) and of the symmetron's density
     if (A.prec == ISIS_F32_REFINE64) {
       for (size_t l = 0; l < lev.size(); ++l) {
         const PLevel& L = lev[l];
-        ISIS_LAUNCH(KK_PATCH_OTHER, 12.0 * L.cells(), A.st,
-                    (pt_to_f32<<<nblk(L.cells()), kPT, 0, A.st>>>(L.m, L.m32, L.cells())));
+        ISIS_LAUNCH(KK_PATCH_OTHER, 12.0 * L.cells(), strm,
+                    (pt_to_f32<<<nblk(L.cells()), kPT, 0, strm>>>(L.m, L.m32, L.cells())));
         if (L.eta32)
-          ISIS_LAUNCH(KK_PATCH_OTHER, 12.0 * L.cells(), A.st,
-                      (pt_to_f32<<<nblk(L.cells()), kPT, 0, A.st>>>(L.eta, L.eta32, L.cells())));
+          ISIS_LAUNCH(KK_PATCH_OTHER, 12.0 * L.cells(), strm,
+                      (pt_to_f32<<<nblk(L.cells()), kPT, 0, strm>>>(L.eta, L.eta32, L.cells())));
       }
     }
     std::vector<int> hc(2 * lev.size());
-    if (cudaMemcpyAsync(hc.data(), counts, hc.size() * sizeof(int), cudaMemcpyDeviceToHost, A.st) != cudaSuccess ||
-        cudaStreamSynchronize(A.st) != cudaSuccess)
+    if (cudaMemcpyAsync(hc.data(), counts, hc.size() * sizeof(int), cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
+        cudaStreamSynchronize(strm) != cudaSuccess)
       return ISIS_ECUDA;
     for (size_t l = 0; l < lev.size(); ++l) {
       lev[l].count[0] = hc[2 * l];
@@ -626,8 +671,8 @@ struct PatchSolver {
 
   isis_status reference(isis_solve_info& info) {
     const PLevel& F = lev[0];
-    ISIS_LAUNCH(KK_PATCH_OTHER, 17.0 * F.cells(), A.st,
-                (pt_ref<<<kPNormBlocks, kPT, 0, A.st>>>(F.m, F.eta, F.cells(), A.eref, part)));
+    ISIS_LAUNCH(KK_PATCH_OTHER, 17.0 * F.cells(), strm,
+                (pt_ref<<<kPNormBlocks, kPT, 0, strm>>>(F.m, F.eta, F.cells(), A.eref, part)));
     double s = 0.0;
     isis_status st = sum_parts(&s);
     if (st != ISIS_OK) return st;
@@ -660,7 +705,7 @@ struct PatchSolver {
     } else {
       st = ISIS_ENOCONV;
       for (int cyc = 0; cyc < A.max_cycles; ++cyc) {
-        isis_status vs = vcycle(0);
+        isis_status vs = cycle_graphed([&] { return vcycle(0); });
         if (vs != ISIS_OK) return vs;
         vs = norm(&res);
         if (vs != ISIS_OK) return vs;
@@ -686,9 +731,9 @@ struct PatchSolver {
     double prev_res = 0.0;
     int prev_k = 0;
     for (int outer = 0;; ++outer) {
-      ISIS_LAUNCH(KK_PATCH_OTHER, 48.0 * n, A.st,
-                  (pt_resid<M, FIELD, double><<<nblk(n), kPT, 0, A.st>>>(F.view(false), A.coef, F.res)));
-      ISIS_LAUNCH(KK_PATCH_OTHER, 8.0 * n, A.st, (pt_sumsq<<<kPNormBlocks, kPT, 0, A.st>>>(F.res, n, part)));
+      ISIS_LAUNCH(KK_PATCH_OTHER, 48.0 * n, strm,
+                  (pt_resid<M, FIELD, double><<<nblk(n), kPT, 0, strm>>>(F.view(false), A.coef, F.res)));
+      ISIS_LAUNCH(KK_PATCH_OTHER, 8.0 * n, strm, (pt_sumsq<<<kPNormBlocks, kPT, 0, strm>>>(F.res, n, part)));
       double s = 0.0;
       st = sum_parts(&s);
       if (st != ISIS_OK) return st;
@@ -704,12 +749,12 @@ struct PatchSolver {
       if (A.unknowns == 0 || res <= A.tol * info.res_ref) { st = ISIS_OK; break; }
       if (!std::isfinite(res)) { st = ISIS_ENAN; break; }
       if (info.cycles >= A.max_cycles) { st = ISIS_ENOCONV; break; }
-      ISIS_LAUNCH(KK_PATCH_OTHER, 28.0 * n, A.st,
-                  (pt_prep32<<<nblk(n), kPT, 0, A.st>>>(F.u, F.res, F.B, F.e, F.sig32, n)));
+      ISIS_LAUNCH(KK_PATCH_OTHER, 28.0 * n, strm,
+                  (pt_prep32<<<nblk(n), kPT, 0, strm>>>(F.u, F.res, F.B, F.e, F.sig32, n)));
       for (size_t l = 1; l < lev.size(); ++l) {
         const PLevel& C = lev[l];
-        ISIS_LAUNCH(KK_PATCH_OTHER, 4.5 * C.cells() * 8.0, A.st,
-                    (pt_restrict<float><<<nblk(C.cells()), kPT, 0, A.st>>>(lev[l - 1].B, C.B, C.n[0], C.n[1],
+        ISIS_LAUNCH(KK_PATCH_OTHER, 4.5 * C.cells() * 8.0, strm,
+                    (pt_restrict<float><<<nblk(C.cells()), kPT, 0, strm>>>(lev[l - 1].B, C.B, C.n[0], C.n[1],
                                                                           C.n[2])));
       }
       // inner cycles; after the first outer iteration, only as many as the measured contraction per cycle
@@ -726,10 +771,10 @@ struct PatchSolver {
       prev_res = res;
       prev_k = k;
       for (int c = 0; c < k; ++c) {
-        st = vcycle32(0);
+        st = cycle_graphed([&] { return vcycle32(0); });
         if (st != ISIS_OK) return st;
       }
-      ISIS_LAUNCH(KK_PATCH_OTHER, 20.0 * n, A.st, (pt_add_correction<<<nblk(n), kPT, 0, A.st>>>(F.u, F.e, n)));
+      ISIS_LAUNCH(KK_PATCH_OTHER, 20.0 * n, strm, (pt_add_correction<<<nblk(n), kPT, 0, strm>>>(F.u, F.e, n)));
       info.cycles += k;
       info.outer = outer + 1;
     }

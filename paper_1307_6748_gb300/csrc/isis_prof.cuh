@@ -36,6 +36,11 @@ enum KernelKind : int {
 
 void prof_pre(cudaStream_t st);
 void prof_post(int kind, double bytes, cudaStream_t st);
+// Whether per-launch events are on; the launches counted so far; count n launches run through a CUDA graph
+// (n < 0 takes back the count of launches recorded into one while it was captured).
+bool prof_enabled();
+long long prof_launches();
+void prof_add_launches(long long n);
 
 }  // namespace isis
 
