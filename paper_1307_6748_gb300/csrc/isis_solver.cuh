@@ -770,7 +770,8 @@ isis_status solve_refine(const SolveArgs& A) {
     } else {
       float2* pff = reinterpret_cast<float2*>(ws->b64);
       ISIS_LAUNCH(KK_OUTER_RESID, 16.0 * n, st, (phi_to_ff<<<nblk(n, 256), 256, 0, st>>>(phi64, pff, n)));
-      ISIS_LAUNCH(KK_OUTER_RESID, 16.0 * n, st,
+      // phi_ff and eta read, r and B written: 24 bytes per cell
+      ISIS_LAUNCH(KK_OUTER_RESID, 24.0 * n, st,
                   (outer_residual_ff<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, rff, eta64, pff, r0, B0,
                                                                               ws->part)));
     }
