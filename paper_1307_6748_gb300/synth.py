@@ -212,8 +212,9 @@ def refine_flags(eta: np.ndarray, level: int, m_ref: float = 8.0, expand: int = 
 
 def patch_box(flags: np.ndarray, margin: int = 1, multiple: int = 8, periodic: bool = False):
     """(origin, n) of the box of parent cells holding every flag with `margin` unflagged cells round it, n
-    rounded up to a multiple of `multiple`; None without flags.  A non-periodic parent keeps one more cell
-    outside the box on each side (the interpolation's stencil); a periodic box may wrap."""
+    rounded up to a multiple of `multiple` (to the next even size where a non-periodic parent has no room for
+    that); None without flags.  A non-periodic parent keeps one more cell outside the box on each side (the
+    interpolation's stencil); a periodic box may wrap."""
     idx = np.argwhere(flags)
     if len(idx) == 0:
         return None
@@ -230,11 +231,15 @@ def patch_box(flags: np.ndarray, margin: int = 1, multiple: int = 8, periodic: b
             span = int(occ[g]) - start
             span = span + pn[a] if span < 0 else span
             lo, hi = start - margin, start + span + margin + 1
-        size = -(-(hi - lo) // multiple) * multiple
-        lo -= (size - (hi - lo)) // 2
+        need = hi - lo
+        size = -(-need // multiple) * multiple
+        if not periodic and size > pn[a] - 2:
+            size = need + (need & 1)
+        lo0, hi0 = lo, hi
+        lo -= (size - need) // 2
         if not periodic:
             lo = max(1, min(lo, pn[a] - 1 - size))
-            if lo < 1:
+            if lo > lo0 or lo + size < hi0 or lo + size + 1 > pn[a]:
                 raise ValueError("the flagged region does not fit inside its parent")
         elif size > pn[a]:
             raise ValueError("the flagged region is wider than the domain")

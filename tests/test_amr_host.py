@@ -88,3 +88,53 @@ def test_oracle_rejects_bad_patches():
     r = oracle.patch_solve(p, oracle.Patch((8, 8, 8), (0, 2, 2), (16, 16, 16), False, level=2), parent, good, eta,
                            tol=1e-8)
     assert r.status == oracle.EINVAL
+
+
+def test_refine_builds_nested_levels_and_passes_the_precision(monkeypatch):
+    """amr.refine's host flow with the library's patch solve replaced by a recorder: level 2 lies inside level 1,
+    its parent is level 1's field, and the options carry the precision, inner cycles and parent start."""
+    import torch
+
+    from paper_1307_6748_gb300 import amr, isis
+    calls = []
+
+    def fake_solve(model, params, grid, a, patch, parent, flags, eta, phi, tol, opts, stream=None):
+        calls.append(dict(patch=patch, parent=parent, flags=flags.clone(), opts=opts, model=model, tol=tol))
+        phi.fill_(float(len(calls)))  # level l's field is l everywhere
+        return isis.Info(isis.ISIS_OK, 1, 1, 0.0, 1.0, 0.0, [])
+
+    monkeypatch.setattr(isis, "isis_patch_scalar_solve", fake_solve)
+    N, B = 32, 64.0
+    eta = np.ones((N, N, N))
+    eta[14:18, 14:18, 14:18] = 600.0  # above 8 domain-cell masses at level 1 and 64 at level 2
+    phi0 = torch.zeros((N, N, N), dtype=torch.float64)
+    dens = lambda dims, corner, h: np.full(dims, 600.0)
+    levels = amr.refine(isis.ISIS_SYMMETRON, isis.Params(), isis.Grid(N, B), 1.0, eta, phi0, dens, levels=2,
+                        expand=1, tol=1e-9, prec=isis.ISIS_F32_REFINE64, inner_cycles=3)
+    assert [lv.level for lv in levels] == [1, 2] and len(calls) == 2
+    for c in calls:
+        assert c["opts"].prec == isis.ISIS_F32_REFINE64 and c["opts"].inner_cycles == 3
+        assert c["opts"].init == isis.ISIS_INIT_PARENT and c["tol"] == 1e-9
+    p1, p2 = calls[0]["patch"], calls[1]["patch"]
+    assert p1.periodic and p1.level == 1 and tuple(p1.parent_dims) == (N, N, N)
+    assert not p2.periodic and p2.level == 2 and tuple(p2.parent_dims) == tuple(2 * v for v in p1.n)
+    assert calls[1]["parent"] is levels[0].phi and calls[0]["parent"] is phi0
+    # level 2's cells lie inside level 1's unknowns, and its fine cells are half the size
+    assert levels[1].h == levels[0].h / 2
+    o2 = np.array(p2.origin)
+    inner = levels[0].unknowns[o2[0]:o2[0] + p2.n[0], o2[1]:o2[1] + p2.n[1], o2[2]:o2[2] + p2.n[2]]
+    assert not (calls[1]["flags"].numpy().astype(bool) & ~inner).any()
+
+
+def test_patch_box_without_room_for_the_rounding():
+    """A non-periodic parent of 16 cells with flags at 2..13: the multiple of 8 (16) leaves no cell on each
+    side, so the box takes the next even size (14) at origin 1; flags that reach the parent's edge raise."""
+    f = np.zeros((16, 16, 16), bool)
+    f[2:14, 2:14, 2:14] = True
+    o, n = synth.patch_box(f, periodic=False)
+    assert o == (1, 1, 1) and n == (14, 14, 14)
+    assert synth.box_flags(f, o, n, False).sum() == f.sum()
+    g = np.zeros((16, 16, 16), bool)
+    g[0:5, 4:6, 4:6] = True
+    with pytest.raises(ValueError):
+        synth.patch_box(g, periodic=False)
