@@ -1,0 +1,54 @@
+"""Host-side helpers of the package (no GPU): the background fields the solves start from, against the
+oracle's uniform-density solutions; the sphere workload's densities and radial profile; the density
+recipes' normalisation."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import sphere1d
+from paper_1307_6748_gb300 import isis, sphere, synth
+
+
+@pytest.mark.parametrize("a", [0.3, 0.5, 0.8, 1.0])
+def test_background_fields_match_the_oracle(a):
+    assert isis.chi_background(a, 0.5) == pytest.approx(oracle.background_field(oracle.SYMMETRON, a, a_ssb=0.5),
+                                                        abs=1e-15)
+    for n, f in ((1, 1e-5), (2, 1e-6)):
+        assert isis.u_background(a, f, n) == pytest.approx(
+            oracle.background_field(oracle.FOFR, a, n=n, fR0_abs=f), rel=1e-14)
+    for cn in (-0.5, 1.0, 2.0):
+        assert isis.cham_background(a, cn) == pytest.approx(
+            oracle.background_field(oracle.CHAMELEON, a, cham_n=cn), abs=1e-15)
+
+
+def test_sphere_exterior_density_keeps_the_mean():
+    for delta, R, B in ((5000.0, 3.0, 40.0), (5000.0, 5.0, 100.0), (10.0, 1.0, 8.0)):
+        eta_in, eta_out = sphere1d.sphere_densities(delta, R, B)
+        assert sphere.exterior_density(delta, R, B) == pytest.approx(eta_out, rel=1e-15)
+        v = 4.0 * math.pi / 3.0 * R ** 3
+        assert (eta_in * v + eta_out * (B ** 3 - v)) / B ** 3 == pytest.approx(1.0, rel=1e-13)
+
+
+@pytest.mark.parametrize("name", ["symmetron_z0", "fofr_z0"])
+def test_radial_profile_of_a_constant_field(name):
+    case = sphere.CASES[name]
+    N, nbins, c = 16, 8, -0.75
+    rows = sphere.radial_profile(case, torch.full((N,) * 3, c, dtype=torch.float64), nbins)
+    want = c if case["model"] == "symmetron" else -math.exp(c) * (1.0 + case["z"]) ** 2
+    assert np.allclose(rows[:, 1:], want, rtol=1e-14, atol=0.0)
+    w = case["B"] / (2 * nbins)
+    assert np.allclose(np.diff(rows[:, 0]) % w, 0.0, atol=1e-12) and rows[0, 0] >= 0.5 * w
+
+
+def test_density_recipes_have_mean_one():
+    e = synth.lognormal_eta(16, 32.0, 1.0, 5)
+    assert float(e.mean()) == pytest.approx(1.0, rel=1e-12) and float(e.min()) > 0.0
+    h1 = synth.nfw_eta(16, 32.0, 0.5, 5, nhalo=4)
+    h2 = synth.nfw_eta(16, 32.0, 0.5, 5, nhalo=4)
+    assert torch.equal(h1, h2)
+    assert float(h1.mean()) == pytest.approx(1.0, rel=1e-12) and float(h1.min()) > 0.0
+    # the haloes add mass concentrations beyond the lognormal field's
+    assert float(h1.max()) > float(synth.lognormal_eta(16, 32.0, 0.5, 5).max())
