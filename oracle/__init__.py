@@ -29,11 +29,18 @@ H0_MPC = 1.0 / 2997.92458
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``libisis_oracle.so`` (gcc, OpenMP, no FP contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
+    """Compile the oracle into ``libisis_oracle.so`` (gcc, OpenMP, no FP contraction).
+
+    With ISIS_ORACLE_SRC set, that C file is compiled next to itself and loaded instead: the mutation tests
+    plant one mistake in a copy of the oracle and check that the pins catch it."""
+    src, out = _SRC, _LIB
+    if os.environ.get("ISIS_ORACLE_SRC"):
+        src = os.environ["ISIS_ORACLE_SRC"]
+        out = os.path.splitext(src)[0] + ".so"
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", out, src, "-lm"]
         subprocess.run(cmd, check=True)
-    return _LIB
+    return out
 
 
 class _Problem(ctypes.Structure):

@@ -1,0 +1,96 @@
+"""Mutation tests of the oracle's pins: each case plants one plausible mistake in a copy of the oracle (a
+dropped or wrong factor, a flipped sign, a wrong neighbour or offset, a wrong constant) and runs the pin
+tests against that copy, which must fail.  The oracle stays pinned to facts outside itself only if every
+such mistake is caught.  CPU only; the copy is compiled in a temporary directory."""
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "isis_oracle.c")
+
+PINS = "tests/test_oracle_pins.py"
+PATCH_PINS = "tests/test_patch_pins.py"
+
+# (name, exact text in the oracle, its planted replacement, the pin file that must catch it)
+MUTATIONS = [
+    ("symmetron cubic term sign",
+     "c->A * ((c->s * eta - 1.0) * phi + phi * phi * phi)", "c->A * ((c->s * eta - 1.0) * phi - phi * phi * phi)",
+     PINS),
+    ("symmetron derivative factor",
+     "c->A * (c->s * eta - 1.0 + 3.0 * phi * phi)", "c->A * (c->s * eta - 1.0 + 2.0 * phi * phi)", PINS),
+    ("Poisson source sign", "return c->KP * (eta - c->eta_mean);", "return -c->KP * (eta - c->eta_mean);", PINS),
+    ("f(R) K3 power of a", "(1.0 + 4.0 * a * a * a * r)", "(1.0 + 4.0 * a * a * r)", PINS),
+    ("f(R) face value: the cell's b instead of the face mean", "div += bf * (un - u);", "div += bu * (un - u);",
+     PINS),
+    ("f(R) derivative factor 1/2", "acc += -bf + 0.5 * bu * (un - u);\n    }\n    return acc / h2",
+     "acc += -bf + bu * (un - u);\n    }\n    return acc / h2", PINS),
+    ("f(R) source exponent", "c->K2 * exp(-phi / c->np1) + c->K3", "c->K2 * exp(-phi * c->np1) + c->K3", PINS),
+    ("chameleon exponent", "c->np1 = 1.0 / (1.0 + p->cham_n);", "c->np1 = 1.0 + p->cham_n;", PINS),
+    ("restriction weight", "coarse[IDX(NH, I, J, K)] = s / 8.0;", "coarse[IDX(NH, I, J, K)] = s / 4.0;", PINS),
+    ("prolongation neighbour", "ci[1] = WRAP(i / 2 + ((i & 1) ? 1 : -1), NH);",
+     "ci[1] = WRAP(i / 2 + ((i & 1) ? -1 : 1), NH);", PINS),
+    ("CIC cell-centre offset", "double xs = x - 0.5;", "double xs = x;", PINS),
+    ("gradient spacing",
+     "gx[q] = (f[IDX(N, WRAP(i + 1, N), j, k)] - f[IDX(N, WRAP(i - 1, N), j, k)]) / (2.0 * h);",
+     "gx[q] = (f[IDX(N, WRAP(i + 1, N), j, k)] - f[IDX(N, WRAP(i - 1, N), j, k)]) / h;", PINS),
+    ("symmetron force constant power of a_SSB", "/ pow(p->a_ssb, 3.0);", "/ pow(p->a_ssb, 2.0);", PINS),
+    ("patch ghost: mask ratio sign", "*mu = mn / L->m[q];", "*mu = -mn / L->m[q];", PATCH_PINS),
+    ("patch ghost: the neighbour's u^Pre", "(*mu) * (L->u[q] - L->pre[q]);", "(*mu) * (L->u[qn] - L->pre[qn]);",
+     PATCH_PINS),
+    ("patch f(R) ghost derivative factor", "dacc += mu * (0.5 * bn * (un - u) + bf);",
+     "dacc += mu * (bn * (un - u) + bf);", PATCH_PINS),
+    ("patch f(R) derivative factor 1/2", "dacc += -bf + 0.5 * bu * (un - u);", "dacc += -bf + bu * (un - u);",
+     PATCH_PINS),
+]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """Every mutant's pin run, four at a time: name -> (occurrences of the mutated text, pytest exit, output)."""
+    with open(SRC) as f:
+        src = f.read()
+    d = tmp_path_factory.mktemp("mutants")
+
+    def run(i, m):
+        name, old, new, pins = m
+        if src.count(old) != 1:
+            return src.count(old), None, ""
+        mutant = d / f"isis_oracle_mutant{i}.c"
+        mutant.write_text(src.replace(old, new))
+        # the copy must compile: a build error would fail the pins for the wrong reason
+        cc = subprocess.run(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o",
+                             str(mutant.with_suffix(".so")), str(mutant), "-lm"], capture_output=True, text=True)
+        if cc.returncode != 0:
+            return 1, None, cc.stderr[-3000:]
+        env = dict(os.environ, ISIS_ORACLE_SRC=str(mutant), OMP_NUM_THREADS="2")
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider",
+                            pins], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+        return 1, r.returncode, r.stdout[-3000:]
+
+    runs = MUTATIONS + [CONTROL(PINS), CONTROL(PATCH_PINS)]
+    with ThreadPoolExecutor(max_workers=4) as ex:
+        res = list(ex.map(lambda im: run(*im), enumerate(runs)))
+    return {m[0]: r for m, r in zip(runs, res)}
+
+
+def CONTROL(pins):
+    """The copy without a planted mistake, through the same mechanism: the pins must pass."""
+    return (f"control {pins}", "int orc_solve(", "int orc_solve(", pins)
+
+
+@pytest.mark.parametrize("pins", [PINS, PATCH_PINS])
+def test_unmutated_copy_passes(outcomes, pins):
+    count, code, out = outcomes[f"control {pins}"]
+    assert count == 1 and code == 0, out
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(outcomes, name):
+    count, code, out = outcomes[name]
+    assert count == 1, f"{name}: the text to mutate must occur exactly once (found {count})"
+    assert code is not None, f"{name}: the copy does not compile\n{out}"
+    assert code == 1, f"{name}: no pin failed (pytest exit {code})\n{out}"
