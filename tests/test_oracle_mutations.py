@@ -38,6 +38,29 @@ MUTATIONS = [
      "gx[q] = (f[IDX(N, WRAP(i + 1, N), j, k)] - f[IDX(N, WRAP(i - 1, N), j, k)]) / (2.0 * h);",
      "gx[q] = (f[IDX(N, WRAP(i + 1, N), j, k)] - f[IDX(N, WRAP(i - 1, N), j, k)]) / h;", PINS),
     ("symmetron force constant power of a_SSB", "/ pow(p->a_ssb, 3.0);", "/ pow(p->a_ssb, 2.0);", PINS),
+    ("FAS coarse source without L_H(R phi)",
+     "C->sigma[IDX(C->N, i, j, k)] += op_L(&H->coef, C, C->phi, i, j, k);", "C->sigma[IDX(C->N, i, j, k)] += 0.0;",
+     PINS),
+    ("coarse correction without R phi", "C->phi0[q] = C->phi[q] - C->phi0[q];", "C->phi0[q] = C->phi[q];", PINS),
+    ("Newton step sign", "L->phi[q] = L->phi[q] - F / dF;", "L->phi[q] = L->phi[q] + F / dF;", PINS),
+    ("Poisson mean kept", "if (p->model == ORC_POISSON) remove_mean(p->N, phi);", "if (0) remove_mean(p->N, phi);",
+     PINS),
+    ("symmetron reference residual without s",
+     "scale = H.coef.A * H.coef.s * background(p, &H.coef);\n    else if (H.coef.model == ORC_FOFR) scale = H.coef.K1;"
+     "\n    else scale = H.coef.KP;\n    info->ref = scale * sqrt(sum2 / (double)n3);",
+     "scale = H.coef.A * background(p, &H.coef);\n    else if (H.coef.model == ORC_FOFR) scale = H.coef.K1;"
+     "\n    else scale = H.coef.KP;\n    info->ref = scale * sqrt(sum2 / (double)n3);", PINS),
+    ("f(R) reference residual constant",
+     "scale = H.coef.K1;\n    else scale = H.coef.KP;\n    info->ref = scale * sqrt(sum2 / (double)n3);",
+     "scale = H.coef.K3;\n    else scale = H.coef.KP;\n    info->ref = scale * sqrt(sum2 / (double)n3);", PINS),
+    ("CIC normalisation", "for (size_t q = 0; q < n3; ++q) eta[q] /= nbar;",
+     "for (size_t q = 0; q < n3; ++q) eta[q] *= nbar;", PINS),
+    ("f(R) K2 exponent", "pow(p->fR0_abs * a * a, 1.0 / c->np1)", "pow(p->fR0_abs * a * a, c->np1)", PINS),
+    ("symmetron A", "c->A = a * a / (2.0 * p->lambda0 * p->lambda0);", "c->A = a * a / (p->lambda0 * p->lambda0);",
+     PINS),
+    ("chameleon force constant", "double Cc = 3.0 * (1.0 + p->cham_n)", "double Cc = 3.0 * (2.0 + p->cham_n)", PINS),
+    ("f(R) force factor", "else pref = 0.5 * exp(phi[q]);", "else pref = exp(phi[q]);", PINS),
+    ("force sign", "gx[q] = -acc[0];", "gx[q] = acc[0];", PINS),
     ("patch ghost: mask ratio sign", "*mu = mn / L->m[q];", "*mu = -mn / L->m[q];", PATCH_PINS),
     ("patch ghost: the neighbour's u^Pre", "(*mu) * (L->u[q] - L->pre[q]);", "(*mu) * (L->u[qn] - L->pre[qn]);",
      PATCH_PINS),
@@ -50,7 +73,8 @@ MUTATIONS = [
 
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
-    """Every mutant's pin run, four at a time: name -> (occurrences of the mutated text, pytest exit, output)."""
+    """Every mutant's pin run, one per core at a time.
+    name -> (occurrences of the mutated text, pytest exit, output)."""
     with open(SRC) as f:
         src = f.read()
     d = tmp_path_factory.mktemp("mutants")
@@ -66,13 +90,13 @@ def outcomes(tmp_path_factory):
                              str(mutant.with_suffix(".so")), str(mutant), "-lm"], capture_output=True, text=True)
         if cc.returncode != 0:
             return 1, None, cc.stderr[-3000:]
-        env = dict(os.environ, ISIS_ORACLE_SRC=str(mutant), OMP_NUM_THREADS="2")
+        env = dict(os.environ, ISIS_ORACLE_SRC=str(mutant), OMP_NUM_THREADS="1")
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider",
                             pins], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
         return 1, r.returncode, r.stdout[-3000:]
 
     runs = MUTATIONS + [CONTROL(PINS), CONTROL(PATCH_PINS)]
-    with ThreadPoolExecutor(max_workers=4) as ex:
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         res = list(ex.map(lambda im: run(*im), enumerate(runs)))
     return {m[0]: r for m, r in zip(runs, res)}
 

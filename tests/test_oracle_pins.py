@@ -627,3 +627,23 @@ def test_chameleon_force_at_cell_centre():
     for d in range(3):
         exp_d = -(a * a * gPhi[d][c] + a * a * Cc * math.exp(u[c]) * gu[d][c])
         assert abs(g[d][0] - exp_d) <= 1e-12 * (abs(exp_d) + 1e-20)
+
+
+# ---------------------------------------------------------------------------
+# The convergence test's reference residual (reading R6)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("model,a", [(oracle.POISSON, 0.7), (oracle.SYMMETRON, 1.0), (oracle.SYMMETRON, 0.8),
+                                     (oracle.FOFR, 1.0), (oracle.FOFR, 0.6), (oracle.CHAMELEON, 0.9)])
+def test_reference_residual_is_the_background_residual(model, a):
+    """R6 defines ref as the RMS of L(phi_bg) for the uniform background field phi_bg; the solver computes it in
+    closed form from the density.  The two must agree: L of the uniform background, evaluated by the operator
+    itself (pinned above), against the ref the solve reports (no cycles run)."""
+    N, box = 8, 16.0
+    eta = synth.lognormal_eta(N, box, 0.8, 11).numpy()
+    p = oracle.Problem(model, N, box, a=a, a_ssb=0.5, cham_n=1.0)
+    bg = oracle.background_field(model, a, a_ssb=0.5, cham_n=1.0)
+    phi = np.full((N,) * 3, bg)
+    rms = float(np.sqrt(np.mean(oracle.residual(p, eta, phi) ** 2)))
+    r = oracle.solve(p, eta, phi, tol=1.0, max_cycles=0)
+    assert rms > 0 and r.ref == pytest.approx(rms, rel=1e-12)
