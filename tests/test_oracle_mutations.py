@@ -62,6 +62,13 @@ MUTATIONS = [
     ("f(R) force factor", "else pref = 0.5 * exp(phi[q]);", "else pref = exp(phi[q]);", PINS),
     ("force sign", "gx[q] = -acc[0];", "gx[q] = acc[0];", PINS),
     ("patch ghost: mask ratio sign", "*mu = mn / L->m[q];", "*mu = -mn / L->m[q];", PATCH_PINS),
+    ("patch reference residual without s",
+     "scale = H.coef.A * H.coef.s * background(p, &H.coef);\n    else if (H.coef.model == ORC_FOFR) scale = H.coef.K1;"
+     "\n    else scale = H.coef.KP;\n    info->ref = cnt",
+     "scale = H.coef.A * background(p, &H.coef);\n    else if (H.coef.model == ORC_FOFR) scale = H.coef.K1;"
+     "\n    else scale = H.coef.KP;\n    info->ref = cnt", PATCH_PINS),
+    ("patch Poisson reference density", "double eref = (p->model == ORC_POISSON) ? P->eta_mean : 1.0, s2 = 0.0;",
+     "double eref = 1.0, s2 = 0.0;", PATCH_PINS),
     ("patch ghost: the neighbour's u^Pre", "(*mu) * (L->u[q] - L->pre[q]);", "(*mu) * (L->u[qn] - L->pre[qn]);",
      PATCH_PINS),
     ("patch f(R) ghost derivative factor", "dacc += mu * (0.5 * bn * (un - u) + bf);",

@@ -225,3 +225,27 @@ def test_patch_fixed_point_matches_dense_newton(model):
     assert len(idx) == 40
     assert np.abs(r.phi[m] - v).max() <= 1e-10 * max(1.0, np.abs(v).max())
     assert np.abs(r.phi[~m] - uint[~m]).max() <= 1e-13 * max(1.0, np.abs(uint).max())
+
+
+@pytest.mark.parametrize("model,a", [(oracle.POISSON, 0.7), (oracle.SYMMETRON, 0.9), (oracle.FOFR, 0.8),
+                                     (oracle.CHAMELEON, 1.0)])
+def test_patch_reference_residual_is_the_background_residual(model, a):
+    """P7: the patch's ref is R6's closed form over its unknowns.  It must equal the RMS over the unknowns of L
+    at the uniform background field, evaluated by the patch operator, with the domain mean for Poisson."""
+    rng = np.random.default_rng(21 + model)
+    n = (8, 6, 10)
+    flags = (rng.uniform(size=n) < 0.5).astype(np.uint8)
+    flags[0, :, :] = flags[-1, :, :] = 0
+    flags[:, 0, :] = flags[:, -1, :] = 0
+    flags[:, :, 0] = flags[:, :, -1] = 0
+    nf = tuple(2 * v for v in n)
+    eta = rng.uniform(0.2, 4.0, nf)
+    p = oracle.Problem(model, 16, 16.0, a=a, a_ssb=0.5, cham_n=1.0)
+    bg = oracle.background_field(model, a, a_ssb=0.5, cham_n=1.0)
+    patch = oracle.Patch(n, (3, 4, 2), (16, 16, 16), True, level=1, eta_mean=1.3)
+    r = oracle.patch_solve(p, patch, np.full((16, 16, 16), bg), flags, eta, tol=1.0, max_cycles=0)
+    m = np.where(np.repeat(np.repeat(np.repeat(flags, 2, 0), 2, 1), 2, 2) > 0, 1.0, -1.0)
+    u = np.full(nf, bg)
+    F, _ = oracle.patch_eval(p, 16.0 / 32, m, eta, u, u, eta_mean=patch.eta_mean)
+    rms = float(np.sqrt(np.mean(F[m > 0] ** 2)))
+    assert rms > 0 and r.ref == pytest.approx(rms, rel=1e-12)
