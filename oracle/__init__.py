@@ -130,6 +130,7 @@ def lib():
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, P(_Info)]
         _lib.orc_patch_eval.argtypes = [P(_Problem), P(ctypes.c_int), ctypes.c_double, d, d, d, d, d,
                                         ctypes.c_double, d, d]
+        _lib.orc_patch_prolong_add.argtypes = [P(ctypes.c_int), d, d, d]
     return _lib
 
 
@@ -362,3 +363,14 @@ def patch_eval(p: Problem, h: float, m, eta, u, pre, sig=None, eta_mean: float =
                               _d(dF))
     assert st == OK, st
     return F, dF
+
+
+def patch_prolong_add(cdelta, m_fine, fine) -> np.ndarray:
+    """fine + P(cdelta) at the fine cells with m > 0 of one patch level (P5); returns the new fine array."""
+    cdelta = np.ascontiguousarray(cdelta, dtype=np.float64)
+    m_fine = np.ascontiguousarray(m_fine, dtype=np.float64)
+    out = np.array(fine, dtype=np.float64, order="C", copy=True)
+    assert m_fine.shape == out.shape == tuple(2 * v for v in cdelta.shape)
+    nc = (ctypes.c_int * 3)(*cdelta.shape)
+    assert lib().orc_patch_prolong_add(nc, _d(cdelta), _d(m_fine), _d(out)) == OK
+    return out

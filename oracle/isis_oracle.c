@@ -1134,3 +1134,20 @@ int orc_patch_eval(const orc_problem* p, const int* n, double h, const double* m
       }
   return ORC_OK;
 }
+
+/* fine += P(cdelta) at the fine cells with m > 0 of a patch level (P5), coarse cells outside the box
+   contributing 0; nc: coarse dims (the fine level has 2 nc).  Exposed for the pins. */
+int orc_patch_prolong_add(const int* nc, const double* cdelta, const double* m_fine, double* fine) {
+  if (nc[0] < 1 || nc[1] < 1 || nc[2] < 1) return ORC_EINVAL;
+  orc_plevel C, L;
+  memset(&C, 0, sizeof(C));
+  memset(&L, 0, sizeof(L));
+  for (int a = 0; a < 3; ++a) {
+    C.n[a] = nc[a];
+    L.n[a] = 2 * nc[a];
+  }
+  L.m = (double*)m_fine;
+  L.u = fine;
+  patch_prolong_add(&C, cdelta, &L);
+  return ORC_OK;
+}

@@ -62,6 +62,17 @@ MUTATIONS = [
     ("f(R) force factor", "else pref = 0.5 * exp(phi[q]);", "else pref = exp(phi[q]);", PINS),
     ("force sign", "gx[q] = -acc[0];", "gx[q] = acc[0];", PINS),
     ("patch ghost: mask ratio sign", "*mu = mn / L->m[q];", "*mu = -mn / L->m[q];", PATCH_PINS),
+    ("patch interpolation neighbour", "pc[a][1] = pc[a][0] + ((f[a] & 1) ? 1 : -1);",
+     "pc[a][1] = pc[a][0] + ((f[a] & 1) ? -1 : 1);", PATCH_PINS),
+    ("patch restriction weight", "coarse[PIDX(nc, I, J, K)] = s / 8.0;", "coarse[PIDX(nc, I, J, K)] = s / 4.0;",
+     PATCH_PINS),
+    ("patch prolongation neighbour", "int ci[2] = {i / 2, i / 2 + ((i & 1) ? 1 : -1)};",
+     "int ci[2] = {i / 2, i / 2 + ((i & 1) ? -1 : 1)};", PATCH_PINS),
+    ("patch prolongation weights",
+     "double w[2] = {0.75, 0.25}, v = 0.0;\n        for (int a = 0; a < 2; ++a)\n          for (int b = 0; b < 2; ++b)"
+     "\n            for (int d = 0; d < 2; ++d) {",
+     "double w[2] = {0.5, 0.5}, v = 0.0;\n        for (int a = 0; a < 2; ++a)\n          for (int b = 0; b < 2; ++b)"
+     "\n            for (int d = 0; d < 2; ++d) {", PATCH_PINS),
     ("patch reference residual without s",
      "scale = H.coef.A * H.coef.s * background(p, &H.coef);\n    else if (H.coef.model == ORC_FOFR) scale = H.coef.K1;"
      "\n    else scale = H.coef.KP;\n    info->ref = cnt",

@@ -249,3 +249,38 @@ def test_patch_reference_residual_is_the_background_residual(model, a):
     F, _ = oracle.patch_eval(p, 16.0 / 32, m, eta, u, u, eta_mean=patch.eta_mean)
     rms = float(np.sqrt(np.mean(F[m > 0] ** 2)))
     assert rms > 0 and r.ref == pytest.approx(rms, rel=1e-12)
+
+
+def test_patch_prolongation_reproduces_a_linear_correction():
+    """P5: the cell-centred trilinear prolongation of a linear coarse correction is the same linear function at
+    every fine unknown whose coarse stencil lies in the box; cells that are not unknowns are left alone, and at
+    the box's edge the missing coarse cells contribute nothing (their weights are not redistributed)."""
+    rng = np.random.default_rng(5)
+    nc = (5, 4, 6)
+    H = 1.0  # coarse cell size; fine h = 1/2
+    g = rng.normal(size=3)
+    ctr = [(np.arange(n) + 0.5) * H for n in nc]
+    cdelta = 0.3 + g[0] * ctr[0][:, None, None] + g[1] * ctr[1][None, :, None] + g[2] * ctr[2][None, None, :]
+    nf = tuple(2 * n for n in nc)
+    m = np.where(rng.uniform(size=nf) < 0.7, 1.0, -0.5)
+    out = oracle.patch_prolong_add(cdelta, m, np.zeros(nf))
+    f = [(np.arange(n) + 0.5) * (H / 2) for n in nf]
+    lin = 0.3 + g[0] * f[0][:, None, None] + g[1] * f[1][None, :, None] + g[2] * f[2][None, None, :]
+    inside = np.ones(nf, bool)
+    for ax, n in enumerate(nf):
+        edge = np.zeros(n, bool)
+        edge[0] = edge[-1] = True  # the first and last fine cells reach a coarse cell outside the box
+        shape = [1, 1, 1]
+        shape[ax] = n
+        inside &= ~edge.reshape(shape)
+    sel = inside & (m > 0)
+    assert sel.sum() > 100
+    assert np.abs(out[sel] - lin[sel]).max() <= 1e-13
+    assert np.all(out[m <= 0] == 0.0)
+    # at a corner unknown only the in-box coarse cell of each axis contributes: weight (3/4)^3
+    c = (0, 0, 0)
+    m2 = np.full(nf, -1.0)
+    m2[c] = 1.0
+    one = np.zeros(nc)
+    one[0, 0, 0] = 1.0
+    assert oracle.patch_prolong_add(one, m2, np.zeros(nf))[c] == 0.75 ** 3
