@@ -6,6 +6,10 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+# mutation tests (test_oracle_mutations.py): a directory holding a copy of the oracle package with one planted
+# mistake comes first, so that `import oracle` loads the copy
+if os.environ.get("ISIS_ORACLE_PKG_DIR"):
+    sys.path.insert(0, os.environ["ISIS_ORACLE_PKG_DIR"])
 
 
 def pytest_configure(config):

@@ -647,3 +647,73 @@ def test_reference_residual_is_the_background_residual(model, a):
     rms = float(np.sqrt(np.mean(oracle.residual(p, eta, phi) ** 2)))
     r = oracle.solve(p, eta, phi, tol=1.0, max_cycles=0)
     assert rms > 0 and r.ref == pytest.approx(rms, rel=1e-12)
+
+
+# ---- pins found missing by planting mistakes in the Python parts of the oracle ----
+
+def test_radial_flux_form_is_second_order():
+    """The 1D finite-volume operator with per-cell b (the f(R) form, face mean of b) approaches
+    (1/r^2)(r^2 b u')' at second order in dr, away from r = 0 and the far boundary."""
+    from oracle import sphere1d as S
+    Rmax = 10.0
+    u_f = lambda r: -1.0 + 0.3 * np.sin(0.5 * r) + 0.05 * r
+    up = lambda r: 0.15 * np.cos(0.5 * r) + 0.05
+    upp = lambda r: -0.075 * np.sin(0.5 * r)
+
+    def exact(r):
+        b = np.exp(u_f(r))
+        return b * (up(r) ** 2 + upp(r) + 2.0 * up(r) / r)  # (1/r^2)(r^2 e^u u')'
+    errs = []
+    for M in (200, 400, 800):
+        rad = S.Radial(M, Rmax)
+        u = u_f(rad.r)
+        L, _, _ = rad.div_flux(u, float(u_f(np.array(Rmax + rad.dr / 2))), np.exp(u))
+        sel = (rad.r > 2.0) & (rad.r < 8.0)
+        errs.append(np.abs(L[sel] - exact(rad.r[sel])).max())
+    assert errs[1] / errs[0] < 0.3 and errs[2] / errs[1] < 0.3, errs
+
+
+def test_radial_sphere_profile_conserves_mass():
+    """The cell-averaged sphere profile holds the sphere's mass: sum of eta V over the radial cells equals
+    eta_in R^3/3 + eta_out (R_max^3 - R^3)/3 (per unit solid angle) for R between cell edges."""
+    from oracle import sphere1d as S
+    rad = S.Radial(97, 10.0)
+    R, eta_in, eta_out = 3.3, 40.0, 0.7
+    eta = S.sphere_profile(rad.edges, R, eta_in, eta_out)
+    mass = float(np.sum(eta * rad.vol))
+    want = eta_in * R ** 3 / 3.0 + eta_out * (10.0 ** 3 - R ** 3) / 3.0
+    assert abs(mass - want) <= 1e-12 * want
+    assert eta[0] == eta_in and eta[-1] == eta_out
+
+
+def test_sphere_densities_contrast_and_mean():
+    """Sect. 5.1: the sphere is delta times denser than its surroundings in contrast (eta_in = (1 + delta)
+    eta_out) and the box mean is 1."""
+    from oracle import sphere1d as S
+    for delta, R, B in ((5000.0, 3.0, 40.0), (10.0, 1.0, 8.0)):
+        eta_in, eta_out = S.sphere_densities(delta, R, B)
+        assert eta_in / eta_out - 1.0 == pytest.approx(delta, rel=1e-14)
+        v = 4.0 * math.pi / 3.0 * R ** 3
+        assert (eta_in * v + eta_out * (B ** 3 - v)) / B ** 3 == pytest.approx(1.0, rel=1e-13)
+
+
+@pytest.mark.parametrize("a,n,fr0", [(0.5, 1, 1e-5), (0.8, 2, 1e-6)])
+def test_radial_fofr_constants_uniform_solution(a, n, fr0):
+    """The 1D solve's K1, K2, K3 give, at eta = 1, the uniform solution u = ln(a^2 |f_R|) with
+    |f_R| = |f_R0| [(1 + 4r)/(a^-3 + 4r)]^(n+1) (Sect. 4.2), at a != 1 where every power of a shows."""
+    from oracle import sphere1d as S
+    K1, K2, K3 = S.fofr_constants(a, OM, OL, S.H0_MPC, n, fr0)
+    r = OL / OM
+    u = math.log(a * a * fr0 * ((1 + 4 * r) / (a ** -3 + 4 * r)) ** (n + 1))
+    assert (n + 1) * math.log(K2 / K3) == pytest.approx(u, abs=1e-12)
+    assert K1 == pytest.approx(OM * a * S.H0_MPC ** 2, rel=1e-15)
+
+
+def test_leapfrog_wraps_into_the_box():
+    """Positions are periodic: a particle drifting across x = N re-enters at x - N, one drifting below 0 at
+    x + N."""
+    N, h = 16, 1.0
+    pos = [np.array([15.5, 0.25]), np.array([3.0, 3.0]), np.array([3.0, 3.0])]
+    vel = [np.array([1.0, -0.5]), np.zeros(2), np.zeros(2)]
+    oracle.leapfrog_kick_drift(pos, vel, [np.zeros(2)] * 3, 0.0, 1.0, N, h)
+    np.testing.assert_allclose(pos[0], [0.5, 15.75], rtol=0, atol=1e-15)
