@@ -15,8 +15,9 @@ ORACLE_DIR = os.path.join(ROOT, "oracle")
 
 PINS = "tests/test_oracle_pins.py"
 PATCH_PINS = "tests/test_patch_pins.py"
+NET_PINS = "tests/test_unet_ref.py"
 
-C, PY, SPH = "isis_oracle.c", "__init__.py", "sphere1d.py"
+C, PY, SPH, NET = "isis_oracle.c", "__init__.py", "sphere1d.py", "unet_ref.py"
 
 # (name, oracle file, exact text in it, its planted replacement, the pin file that must catch it)
 MUTATIONS = [
@@ -131,6 +132,22 @@ MUTATIONS = [
     ("background chameleon", PY,
      "return 3.0 * math.log(a) / (1.0 + cham_n)",
      "return 3.0 * math.log(a) / (2.0 + cham_n)", PINS),
+    ("net: ReLU derivative", NET, "dZ = dY * (Y > 0)", "dZ = dY", NET_PINS),
+    ("net: pooling adjoint weight", NET, "return np.repeat(np.repeat(np.repeat(dY, 2, 0), 2, 1), 2, 2) / 8.0",
+     "return np.repeat(np.repeat(np.repeat(dY, 2, 0), 2, 1), 2, 2) / 4.0", NET_PINS),
+    ("net: upsampling adjoint as a mean", NET, "return dY.reshape(n, 2, n, 2, n, 2, -1).sum(axis=(1, 3, 5))",
+     "return dY.reshape(n, 2, n, 2, n, 2, -1).mean(axis=(1, 3, 5))", NET_PINS),
+    ("net: data gradient shift", NET, "dX += shift(dZ, (-d[0], -d[1], -d[2])) @ W[t]", "dX += shift(dZ, d) @ W[t]",
+     NET_PINS),
+    ("net: weight gradient shift", NET, "return np.stack([Z.T @ shift(X, d).reshape(n3, -1) for d in TAPS])",
+     "return np.stack([Z.T @ shift(X, (-d[0], -d[1], -d[2])).reshape(n3, -1) for d in TAPS])", NET_PINS),
+    ("net: head bias gradient", NET, "[dpred.sum()]", "[0.0]", NET_PINS),
+    ("net: loss gradient factor", NET, "dpred = 2.0 * r / V", "dpred = r / V", NET_PINS),
+    ("net: tap order", NET,
+     "TAPS = [(di, dj, dk) for di in (-1, 0, 1) for dj in (-1, 0, 1) for dk in (-1, 0, 1)]",
+     "TAPS = [(di, dj, dk) for dk in (-1, 0, 1) for dj in (-1, 0, 1) for di in (-1, 0, 1)]", NET_PINS),
+    ("net: skip split in the backward pass", NET, "dd1, de0 = up_bwd(dx[..., :32]), dx[..., 32:]",
+     "dd1, de0 = up_bwd(dx[..., 16:]), dx[..., :16]", NET_PINS),
 ]
 
 
