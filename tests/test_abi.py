@@ -58,3 +58,38 @@ def test_strerror_and_argument_checks_without_gpu(lib):
     assert st == isis.ISIS_EINVAL
     st = L.isis_cic_deposit(ctypes.byref(g), None, None, None, 10, None, 1, None)
     assert st == isis.ISIS_EINVAL
+
+
+def test_patch_argument_checks_without_gpu(lib):
+    """The refinement-patch entry points reject bad boxes and options on the host, before any device call."""
+    from paper_1307_6748_gb300 import isis
+    L = isis.load()
+    g = isis.isis_grid(0.267, 0.733, isis.H0_MPC, 64.0, 16)
+    p = isis.isis_params(1.0, 1.0, 0.5, 1, 1e-5, 1.0)
+    dev = ctypes.c_void_p(16)  # never dereferenced: every case fails its host checks first
+
+    def call(box, opts=None, a=1.0, tol=1e-10):
+        o = None if opts is None else ctypes.byref(opts.c())
+        return L.isis_patch_scalar_solve(isis.ISIS_SYMMETRON, ctypes.byref(p), ctypes.byref(g), a, ctypes.byref(box),
+                                         dev, dev, dev, dev, tol, o, None, None)
+
+    def box(n=(8, 8, 8), o=(0, 0, 0), pn=(16, 16, 16), periodic=1, level=1):
+        return isis.Patch(n, o, pn, bool(periodic), level=level).c()
+
+    E = isis.ISIS_EINVAL
+    assert call(box(), isis.Opts(prec=isis.ISIS_F32)) == E  # FP32 fields: not offered on patches
+    assert call(box(), isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=0)) == E
+    assert call(box(), isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=17)) == E
+    assert call(box(), isis.Opts(nu1=17)) == E
+    assert call(box(), isis.Opts(max_cycles=129)) == E
+    assert call(box(), isis.Opts(init=isis.ISIS_INIT_BACKGROUND)) == E
+    assert call(box(), a=0.0) == E and call(box(), tol=-1.0) == E
+    assert call(box(n=(7, 8, 8))) == E and call(box(n=(2, 8, 8))) == E  # odd, too small
+    assert call(box(level=0)) == E and call(box(level=2)) == E  # a periodic parent is the domain: level 1
+    assert call(box(n=(18, 8, 8))) == E  # wider than the periodic parent
+    # a non-periodic parent keeps one cell on each side
+    assert call(box(o=(0, 1, 1), pn=(20, 20, 20), periodic=0, level=2)) == E
+    assert call(box(o=(12, 1, 1), pn=(20, 20, 20), periodic=0, level=2)) == E
+    # the coarsest patch level (one block) holds at most 32768 cells: 2 x 66 -> 66 -> 33 (odd) is 35937
+    g.N = 128
+    assert call(box(n=(66, 66, 66), pn=(128, 128, 128))) == E
