@@ -93,3 +93,30 @@ def test_patch_argument_checks_without_gpu(lib):
     # the coarsest patch level (one block) holds at most 32768 cells: 2 x 66 -> 66 -> 33 (odd) is 35937
     g.N = 128
     assert call(box(n=(66, 66, 66), pn=(128, 128, 128))) == E
+
+
+def test_solver_option_and_parameter_checks_without_gpu(lib):
+    """The grid, the options and the model parameters of the domain solves are checked on the host."""
+    from paper_1307_6748_gb300 import isis
+    L = isis.load()
+    dev = ctypes.c_void_p(16)  # never dereferenced
+    E = isis.ISIS_EINVAL
+
+    def solve(model=isis.ISIS_SYMMETRON, N=16, box=32.0, opts=None, params=None, a=1.0, Om=0.267):
+        g = isis.isis_grid(Om, 0.733, isis.H0_MPC, box, N)
+        p = (params or isis.Params()).c()
+        o = None if opts is None else ctypes.byref(opts.c())
+        return L.isis_scalar_solve(model, ctypes.byref(p), ctypes.byref(g), a, dev, dev, 1e-8, o, None, None)
+
+    for N in (4, 12, 2048):
+        assert solve(N=N) == E  # a power of two in [8, 1024]
+    assert solve(box=0.0) == E and solve(Om=0.0) == E and solve(a=-1.0) == E
+    for o in (isis.Opts(n_coarsest=3), isis.Opts(nu1=17), isis.Opts(nu2=-1), isis.Opts(max_cycles=129),
+              isis.Opts(prec=5), isis.Opts(inner_cycles=0), isis.Opts(inner_cycles=17), isis.Opts(init=9),
+              isis.Opts(fmg=2), isis.Opts(init=isis.ISIS_INIT_PARENT)):
+        assert solve(opts=o) == E, o
+    assert solve(params=isis.Params(lambda0=0.0)) == E
+    assert solve(params=isis.Params(a_ssb=-0.5)) == E
+    assert solve(model=isis.ISIS_FOFR_HS, params=isis.Params(fR0_abs=0.0)) == E
+    assert solve(model=isis.ISIS_FOFR_HS, params=isis.Params(n=0)) == E
+    assert solve(model=isis.ISIS_CHAMELEON, params=isis.Params(cham_n=-1.0)) == E
