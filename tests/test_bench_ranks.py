@@ -51,3 +51,23 @@ def test_reference_arm_prints_on_rank_0_only():
     with contextlib.redirect_stdout(buf):
         bench.run_reference(args, 1, 2)
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_line_has_the_contract_keys():
+    """The reference arm (the oracle on the host cores) prints one JSON line with the contract's keys, on a
+    tiny sample so that the test stays short."""
+    import json
+    args = bench.parse(["--impl", "reference", "--steps", "1", "--warmup", "0", "--sample-N", "16"])
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(args, 0, 1)
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is False
+    assert line["config"]["workload"].startswith("force step")
+    assert set(line["cpu_baseline"]) >= {"value", "unit", "cores", "kind", "sample"}
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
