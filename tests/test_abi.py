@@ -58,6 +58,10 @@ def test_strerror_and_argument_checks_without_gpu(lib):
     assert st == isis.ISIS_EINVAL
     st = L.isis_cic_deposit(ctypes.byref(g), None, None, None, 10, None, 1, None)
     assert st == isis.ISIS_EINVAL
+    # no particles, or more than 2^40, are rejected before any device work
+    dev = ctypes.c_void_p(16)
+    for npart in (0, -1, (1 << 40) + 1):
+        assert L.isis_cic_deposit(ctypes.byref(g), dev, dev, dev, npart, dev, 1, None) == isis.ISIS_EINVAL
 
 
 def test_patch_argument_checks_without_gpu(lib):
