@@ -105,6 +105,9 @@ MUTATIONS = [
     ("patch f(R) derivative factor 1/2", C,
      "dacc += -bf + 0.5 * bu * (un - u);",
      "dacc += -bf + bu * (un - u);", PATCH_PINS),
+    ("CIC weights swapped", C, "*w0 = 1.0 - t;\n  *w1 = t;", "*w0 = t;\n  *w1 = 1.0 - t;", PINS),
+    ("symmetron force without a^2", C, "pref = Cs * (a * phi[q]) * a;", "pref = Cs * phi[q];", PINS),
+    ("force gather weight", C, "double w = wx[aa] * wy[b] * wz[d];", "double w = wx[aa] * wy[b] * wz[1 - d];", PINS),
     ("1D face area", SPH,
      "area = self.edges[1:] ** 2  # outer face of cell i",
      "area = self.edges[1:] ** 1  # outer face of cell i", PINS),
