@@ -43,7 +43,8 @@ extern "C" {
 typedef enum {
   ISIS_OK = 0,
   ISIS_EINVAL = -1,    /* bad argument: sizes, pointers, parameters */
-  ISIS_ENOCONV = -2,   /* max_cycles reached; best iterate left in phi, info filled */
+  ISIS_ENOCONV = -2,   /* max_cycles reached, or a coarsest-grid Newton solve met no stop within its 50
+                          steps (that cycle then ends the solve); last iterate left in phi, info filled */
   ISIS_ENAN = -3,      /* non-finite residual or a singular coarsest Jacobian */
   ISIS_ECUDA = -4,     /* a CUDA runtime call or launch failed */
   ISIS_ENOMEM = -5,    /* device allocation of the workspace failed */

@@ -122,6 +122,9 @@ def lib():
         _lib.orc_prolong_add.argtypes = [ctypes.c_int, d, d]
         _lib.orc_prolong_add.restype = None
         _lib.orc_dense_newton.argtypes = [P(_Problem), d, d, d, P(ctypes.c_int)]
+        _lib.orc_jacobian.argtypes = [P(_Problem), d, d, d]
+        _lib.orc_rms_residual.argtypes = [P(_Problem), d, d, d]
+        _lib.orc_rms_residual.restype = ctypes.c_double
         _lib.orc_cic_deposit.argtypes = [ctypes.c_int, ctypes.c_int64, f, f, f, d]
         _lib.orc_gradient.argtypes = [ctypes.c_int, ctypes.c_double, d, d, d, d]
         _lib.orc_fifth_force.argtypes = [P(_Problem), d, d, ctypes.c_int64, f, f, f, d, d, d]
@@ -226,6 +229,27 @@ def dense_newton(p: Problem, eta, phi0, sigma=None):
     pc = p.c()
     st = lib().orc_dense_newton(ctypes.byref(pc), _d(eta), _d(phi), _d(sg), ctypes.byref(steps))
     return st, phi, steps.value
+
+
+def jacobian(p: Problem, eta, phi) -> np.ndarray:
+    """The dense Jacobian dF_r/dphi_c (N^3 x N^3) of the coarsest-level Newton solve at phi.  Poisson's
+    carries the shift -(6/h^2)/N^3 in every entry, which removes the periodic Laplacian's null space."""
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    n = p.N ** 3
+    out = np.empty((n, n))
+    pc = p.c()
+    assert lib().orc_jacobian(ctypes.byref(pc), _d(eta), _d(phi), _d(out)) == OK
+    return out
+
+
+def rms_residual(p: Problem, eta, phi, sigma=None) -> float:
+    """RMS of L(phi) - Sigma over one grid: the norm of the convergence test."""
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    sg = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64)
+    pc = p.c()
+    return float(lib().orc_rms_residual(ctypes.byref(pc), _d(eta), _d(phi), _d(sg)))
 
 
 def cic_deposit(N: int, x, y, z) -> np.ndarray:

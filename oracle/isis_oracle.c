@@ -388,7 +388,8 @@ static int coarse_newton(const orc_coef* c, orc_level* L, int* steps) {
   double* J = (double*)malloc(sizeof(double) * (size_t)n * n);
   double* F = (double*)malloc(sizeof(double) * (size_t)n);
   if (!J || !F) { free(J); free(F); return ORC_ENOMEM; }
-  int st = ORC_OK, it;
+  /* ENOCONV unless a step meets the stop rule within 50 steps */
+  int st = ORC_ENOCONV, it;
   for (it = 0; it < 50; ++it) {
     for (int i = 0; i < N; ++i)
       for (int j = 0; j < N; ++j)
@@ -411,7 +412,7 @@ static int coarse_newton(const orc_coef* c, orc_level* L, int* steps) {
       if (fabs(L->phi[q]) > pmax) pmax = fabs(L->phi[q]);
     }
     if (!isfinite(dmax)) { st = ORC_ENAN; break; }
-    if (dmax <= 1e-13 * (pmax > 1.0 ? pmax : 1.0)) { ++it; break; }
+    if (dmax <= 1e-13 * (pmax > 1.0 ? pmax : 1.0)) { st = ORC_OK; ++it; break; }
   }
   if (steps) *steps = it;
   free(J);
@@ -626,6 +627,26 @@ int orc_smooth(const orc_problem* p, const double* eta, double* phi, const doubl
 
 void orc_restrict(int NH, const double* fine, double* coarse) { restrict_mean(NH, fine, coarse); }
 void orc_prolong_add(int NH, const double* cdelta, double* fine) { prolong_add(NH, cdelta, fine); }
+
+/* The dense Jacobian of the coarsest solve, dF_r/dphi_c (row-major n x n, n = N^3), at phi; for pins.
+   Poisson's carries the shift -(6/h^2)/n in every entry that removes the periodic Laplacian's null space. */
+int orc_jacobian(const orc_problem* p, const double* eta, const double* phi, double* J) {
+  if (!valid(p)) return ORC_EINVAL;
+  orc_coef c;
+  make_coef(p, eta, &c);
+  orc_level L = {p->N, p->box / p->N, (double*)eta, (double*)phi, NULL, NULL, NULL};
+  jacobian(&c, &L, J);
+  return ORC_OK;
+}
+
+/* RMS of L(phi) - Sigma over one grid, the norm of the convergence test; for pins. */
+double orc_rms_residual(const orc_problem* p, const double* eta, const double* phi, const double* sigma) {
+  if (!valid(p)) return NAN;
+  orc_coef c;
+  make_coef(p, eta, &c);
+  orc_level L = {p->N, p->box / p->N, (double*)eta, (double*)phi, NULL, (double*)sigma, NULL};
+  return rms_residual(&c, &L);
+}
 
 /* Dense-Newton solve of L(phi) = Sigma on one (small) grid; for pins. */
 int orc_dense_newton(const orc_problem* p, const double* eta, double* phi, const double* sigma, int* steps) {

@@ -14,7 +14,8 @@ namespace isis {
 
 constexpr int kCoarseMax = 64;
 
-// status bits written to *flags (OR-ed): 1 = singular pivot, 2 = non-finite step
+// status bits written to *flags (OR-ed): 1 = singular pivot, 2 = non-finite step, 4 = no step met the stop
+// rule within the 50 steps
 template <Model M, Form FM, class T>
 __global__ void __launch_bounds__(kCoarseMax) coarse_newton(LevelView<T> L, Coef c, int* flags, int* steps_max) {
   __shared__ double J[kCoarseMax][kCoarseMax + 1];
@@ -129,7 +130,8 @@ __global__ void __launch_bounds__(kCoarseMax) coarse_newton(LevelView<T> L, Coef
     if constexpr (M == FOFR && kExpCache<T>) L.aux[gr] = aux_of<M, FM, T>((T)xs[r], T(0));
   }
   if (r == 0) {
-    if (bad) atomicOr(flags, bad);
+    const int f = bad ? bad : (done ? 0 : 4);
+    if (f) atomicOr(flags, f);
     atomicMax(steps_max, it);
   }
 }

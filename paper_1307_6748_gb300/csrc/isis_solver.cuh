@@ -83,6 +83,14 @@ inline int ilog2(int n) {
 }
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Status of the solve from the coarsest Newton solve's flags: a singular pivot or a non-finite step is
+// ISIS_ENAN; a solve that did not meet its stop rule in 50 steps ends the solve with ISIS_ENOCONV.
+inline isis_status coarse_status(int flags) {
+  if (flags & 3) return ISIS_ENAN;
+  if (flags & 4) return ISIS_ENOCONV;
+  return ISIS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // V-cycle driver for one model / form / element type
 // ---------------------------------------------------------------------------
@@ -280,8 +288,7 @@ struct Cycler {
     ISIS_CK(cudaStreamSynchronize(st));
     size_t n = (size_t)L[0].N * L[0].N * L[0].N;
     *out = std::sqrt(h[0] / (double)n);
-    if (hi[0] != 0) return ISIS_ENAN;
-    return ISIS_OK;
+    return coarse_status(hi[0]);
   }
 };
 
@@ -784,7 +791,7 @@ isis_status solve_refine(const SolveArgs& A) {
     loc.nhist = nh;
     loc.res_final = res;
     loc.outer = outer;
-    if (hi[0] != 0) { out = ISIS_ENAN; break; }
+    if (hi[0] != 0) { out = coarse_status(hi[0]); break; }
     if (!std::isfinite(res)) { out = ISIS_ENAN; break; }
     if (res <= target) { out = ISIS_OK; break; }
     if (loc.cycles >= A.max_cycles || outer >= 127) { out = ISIS_ENOCONV; break; }

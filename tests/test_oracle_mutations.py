@@ -105,6 +105,19 @@ MUTATIONS = [
     ("patch f(R) derivative factor 1/2", C,
      "dacc += -bf + 0.5 * bu * (un - u);",
      "dacc += -bf + bu * (un - u);", PATCH_PINS),
+    ("coarsest Jacobian: f(R) off-diagonal derivative factor", C,
+     "J[row * n + col] += (bf + 0.5 * bn * (un - u)) / h2;",
+     "J[row * n + col] += (bf + bn * (un - u)) / h2;", PINS),
+    ("coarsest Jacobian: f(R) off-diagonal without the face mean", C,
+     "J[row * n + col] += (bf + 0.5 * bn * (un - u)) / h2;",
+     "J[row * n + col] += (0.5 * bn + 0.5 * bn * (un - u)) / h2;", PINS),
+    ("coarsest Jacobian: Poisson null-space shift", C,
+     "double shift = 6.0 / h2 / (double)n;",
+     "double shift = 12.0 / h2 / (double)n;", PINS),
+    ("coarsest Newton: OK without meeting the stop rule", C,
+     "int st = ORC_ENOCONV, it;", "int st = ORC_OK, it;", PINS),
+    ("RMS residual normalisation", C,
+     "return sqrt(tot / ((double)N * N * N));", "return sqrt(tot / ((double)N * N));", PINS),
     ("CIC weights swapped", C, "*w0 = 1.0 - t;\n  *w1 = t;", "*w0 = t;\n  *w1 = 1.0 - t;", PINS),
     ("symmetron force without a^2", C, "pref = Cs * (a * phi[q]) * a;", "pref = Cs * phi[q];", PINS),
     ("force gather weight", C, "double w = wx[aa] * wy[b] * wz[d];", "double w = wx[aa] * wy[b] * wz[1 - d];", PINS),

@@ -231,13 +231,20 @@ def numpy_newton(p, eta, phi0, iters=30):
     return phi
 
 
-@pytest.mark.parametrize("model,ncoarse", [(oracle.SYMMETRON, 4), (oracle.SYMMETRON, 2), (oracle.FOFR, 4)])
+@pytest.mark.parametrize("model,ncoarse", [(oracle.SYMMETRON, 4), (oracle.SYMMETRON, 2), (oracle.FOFR, 4),
+                                           (oracle.CHAMELEON, 4)])
 def test_fas_matches_dense_newton_8cubed(model, ncoarse):
-    N, box = 8, 16.0 if model == oracle.SYMMETRON else 64.0
+    """The FAS fixed point and the oracle's own dense Newton solve (the coarsest-level solver run on the whole
+    8^3 grid) both equal a numpy Newton solve with a finite-difference Jacobian.  The dense Newton solve,
+    started from the background field, converges quadratically (exact Jacobian): it meets its stop rule
+    (max|dx| <= 1e-13 max(1, max|phi|)) within 8 steps, where a Jacobian off by a few per cent converges only
+    linearly and needs more."""
+    N, box = 8, 16.0 if model in (oracle.SYMMETRON, oracle.CHAMELEON) else 64.0
     eta = synth.lognormal_eta(N, box, 1.0, 13).numpy()
-    p = oracle.Problem(model, N, box, a=0.9)
+    p = oracle.Problem(model, N, box, a=0.9, lambda0=1.5, cham_n=1.0)
     g0 = math.sqrt(1 - (0.5 / 0.9) ** 3) if model == oracle.SYMMETRON else \
-        math.log(0.81 * 1e-5 * ((1 + 4 * OL / OM) / (0.9 ** -3 + 4 * OL / OM)) ** 2)
+        math.log(0.81 * 1e-5 * ((1 + 4 * OL / OM) / (0.9 ** -3 + 4 * OL / OM)) ** 2) if model == oracle.FOFR else \
+        3.0 * math.log(0.9) / 2.0  # chameleon n = 1: u = 3 ln(a) / (1 + n) at eta = 1
     guess = np.full((N,) * 3, g0)
     ref = numpy_newton(p, eta, guess)
     r = oracle.solve(p, eta, guess, tol=1e-12, ncoarse=ncoarse)
@@ -245,6 +252,81 @@ def test_fas_matches_dense_newton_8cubed(model, ncoarse):
     assert np.abs(r.phi - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
     st, dn, steps = oracle.dense_newton(p, eta, guess)
     assert st == oracle.OK and np.abs(dn - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+    assert 2 <= steps <= 8, steps
+
+
+def test_dense_newton_reports_no_convergence():
+    """A Newton solve that does not meet its stop rule within its 50 steps reports ENOCONV, not OK.  On a
+    uniform symmetron grid with eta = 0 the equation L(chi) = Sigma reads chi^3 - chi + Sigma/A = 0 in every
+    cell, and for Sigma/A = 1/sqrt(2) Newton's method from chi = 0 cycles exactly between 0 and 1/sqrt(2)
+    (N(0) = 1/sqrt(2), N(1/sqrt(2)) = 0; the cycle is superattracting, N'(0) = 0), so every step has
+    max|dx| = 1/sqrt(2)."""
+    N, box = 4, 4.0
+    p = oracle.Problem(oracle.SYMMETRON, N, box, a=1.0, a_ssb=0.5, lambda0=1.0)
+    A = 0.5  # a^2 / (2 lambda0^2)
+    eta = np.zeros((N,) * 3)
+    sigma = np.full((N,) * 3, A / math.sqrt(2.0))
+    for start in (0.0, 0.3):
+        st, phi, steps = oracle.dense_newton(p, eta, np.full((N,) * 3, start), sigma)
+        assert st == oracle.ENOCONV and steps == 50, (st, steps)
+        # 50 steps (even) end on the cycle's point reached from the start
+        assert np.abs(phi - (0.0 if start == 0.0 else 1 / math.sqrt(2.0))).max() < 1e-12
+
+
+@pytest.mark.parametrize("model", [oracle.POISSON, oracle.SYMMETRON, oracle.FOFR, oracle.CHAMELEON])
+def test_jacobian_matches_finite_difference(model):
+    """The coarsest solve's dense Jacobian (every entry, all 64 columns of a 4^3 grid) against a central
+    difference of the residual L(phi) in each phi_c.  The f(R) and chameleon off-diagonal entries
+    (b_f + (b_nb/2)(u_nb - u))/h^2 carry the face average's derivative of Sect. 3.4; Poisson's entries carry the
+    shift -(6/h^2)/n that removes the constant null space of the periodic Laplacian."""
+    N, box = 4, 8.0
+    h = box / N
+    gen = np.random.Generator(np.random.PCG64(17))
+    eta = np.exp(0.5 * gen.standard_normal((N,) * 3))
+    if model == oracle.FOFR:
+        phi = -11.5 + 0.6 * gen.standard_normal((N,) * 3)
+    elif model == oracle.CHAMELEON:
+        phi = 0.4 * gen.standard_normal((N,) * 3)
+    elif model == oracle.POISSON:
+        phi = 1e-5 * gen.standard_normal((N,) * 3)
+    else:
+        phi = 0.8 + 0.2 * gen.standard_normal((N,) * 3)
+    p = oracle.Problem(model, N, box, a=0.9, lambda0=1.5, cham_n=1.0)
+    J = oracle.jacobian(p, eta, phi)
+    n = N ** 3
+    if model == oracle.POISSON:
+        J = J + (6.0 / h ** 2) / n
+    Jfd = np.empty((n, n))
+    for q in range(n):
+        e = 1e-5 * max(1.0, abs(phi.flat[q]))
+        pp, pm = phi.copy(), phi.copy()
+        pp.flat[q] += e
+        pm.flat[q] -= e
+        Jfd[:, q] = (oracle.residual(p, eta, pp).ravel() - oracle.residual(p, eta, pm).ravel()) / (2 * e)
+    scale = np.abs(Jfd).max()
+    assert np.abs(J - Jfd).max() <= 1e-8 * scale, np.abs(J - Jfd).max() / scale
+    # the sparsity: the diagonal and the six neighbours of each row (4^3: all distinct)
+    assert np.count_nonzero(np.abs(Jfd) > 1e-12 * scale) == 7 * n
+
+
+@pytest.mark.parametrize("model", [oracle.POISSON, oracle.SYMMETRON, oracle.FOFR])
+def test_rms_residual_is_the_root_mean_square(model):
+    """The convergence test's norm is sqrt(mean((L(phi) - Sigma)^2)) over the N^3 cells of the grid, here
+    computed in numpy from the residual field; the solve reports the same value as its starting residual."""
+    N, box = 8, 16.0
+    gen = np.random.Generator(np.random.PCG64(23))
+    eta = np.exp(gen.standard_normal((N,) * 3))
+    phi = (-11.5 + 0.3 * gen.standard_normal((N,) * 3)) if model == oracle.FOFR else \
+        (0.8 + 0.1 * gen.standard_normal((N,) * 3))
+    p = oracle.Problem(model, N, box)
+    sig = 1e-3 * gen.standard_normal((N,) * 3) * np.abs(oracle.residual(p, eta, phi)).max()
+    for sigma in (None, sig):
+        r = oracle.residual(p, eta, phi, sigma)
+        want = math.sqrt(float(np.sum(r * r)) / N ** 3)
+        assert oracle.rms_residual(p, eta, phi, sigma) == pytest.approx(want, rel=1e-13)
+    res = oracle.solve(p, eta, phi, tol=0.0, max_cycles=0)
+    r = oracle.residual(p, eta, phi)
+    assert res.res0 == pytest.approx(math.sqrt(float(np.mean(r * r))), rel=1e-13)
 
 
 # ---------------------------------------------------------------------------
