@@ -228,8 +228,8 @@ def oracle_step(sample_N: int, box_full: float, N_full: int, tol: float, cache={
     Pf = oracle.Problem(oracle.FOFR, sample_N, box, a=1.0, fR0_abs=1e-5)
     shape = (sample_N,) * 3
     rp = oracle.solve(Pp, eta, np.zeros(shape), tol=tol)
-    rs = oracle.solve(Ps, eta, np.full(shape, isis.chi_background(1.0, 0.5)), tol=tol)
-    rf = oracle.solve(Pf, eta, np.full(shape, isis.u_background(1.0, 1e-5)), tol=tol)
+    rs = oracle.solve(Ps, eta, np.full(shape, oracle.background_field(oracle.SYMMETRON, 1.0, a_ssb=0.5)), tol=tol)
+    rf = oracle.solve(Pf, eta, np.full(shape, oracle.background_field(oracle.FOFR, 1.0, fR0_abs=1e-5)), tol=tol)
     oracle.fifth_force(Ps, rp.phi, rs.phi, x, y, z)
     oracle.fifth_force(Pf, rp.phi, rf.phi, x, y, z)
     return time.perf_counter() - t0

@@ -173,6 +173,18 @@ isis_status isis_cic_deposit_noalloc(const isis_grid* grid, const float* x, cons
 isis_status isis_poisson_solve(const isis_grid* grid, double a, const void* eta, void* Phi, double tol,
                                const isis_mg_opts* opts, isis_solve_info* info, void* stream);
 
+/* Uniform background field of a scalar model at expansion factor a: the solution at eta = 1 everywhere, the
+ * value ISIS_INIT_BACKGROUND writes as the initial guess.
+ *   ISIS_SYMMETRON  chi_bg = sqrt(max(0, 1 - (a_SSB/a)^3))      (Sect. 4.1: the minimum of the effective
+ *                   potential at the background density; 0 before symmetry breaking)
+ *   ISIS_FOFR_HS    u_bar = ln(a^2 |fbar_R(a)|), |fbar_R(a)| = |f_R0| [(1 + 4r)/(a^-3 + 4r)]^(n+1),
+ *                   r = Omega_L/Omega_m                         (Sect. 4.2, the f_R equation at eta = 1)
+ *   ISIS_CHAMELEON  u = 3 ln(a) / (1 + n)                       (Sect. 6, the minimum at a^-3 eta = psi^-(1+n))
+ *   out  host double, written on ISIS_OK.  Host arithmetic only: no device work, no stream.
+ *   Returns ISIS_EINVAL for a NULL pointer, a <= 0 or parameters outside the solver's range. */
+isis_status isis_background_field(isis_model model, const isis_params* params, const isis_grid* grid, double a,
+                                  double* out);
+
 /* Scalar field (Sect. 3.2, FAS with implicit Newton-Gauss-Seidel):
  *   ISIS_SYMMETRON  phi = chi:  lap chi = a^2/(2 lambda0^2) [ (a_SSB/a)^3 eta chi - chi + chi^3 ]
  *                   (Sect. 4.1, Eq. (symmetron_dimensionles))

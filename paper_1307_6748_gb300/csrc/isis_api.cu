@@ -386,6 +386,19 @@ isis_status isis_scalar_solve(isis_model model, const isis_params* p, const isis
   return model == ISIS_SYMMETRON ? run_sym(A) : run_fofr(A);
 }
 
+isis_status isis_background_field(isis_model model, const isis_params* p, const isis_grid* grid, double a,
+                                  double* out) {
+  if (!p || !grid || !out || !(a > 0) || !std::isfinite(a) || !(grid->H0 > 0) || !(grid->Omega_m > 0) ||
+      !(grid->Omega_L >= 0))
+    return ISIS_EINVAL;
+  Coef c;
+  double ref_scale = 0.0;
+  std::memset(&c, 0, sizeof(c));
+  if (!model_coef(model, p, grid, a, &c, &ref_scale)) return ISIS_EINVAL;
+  *out = model == ISIS_SYMMETRON ? background_value<SYM>(c) : background_value<FOFR>(c);
+  return ISIS_OK;
+}
+
 // Refinement patches (Sect. 3.3.1, Sect. 3.4.1).
 static isis_status patch_common(PatchArgs& P, const isis_grid* grid, double a, const isis_patch* box,
                                 const void* parent, const uint8_t* flags, const void* eta, void* phi, double tol,

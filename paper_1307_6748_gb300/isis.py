@@ -27,7 +27,7 @@ H0_MPC = 1.0 / 2997.92458  # (Mpc/h)^-1 with c = 1
 EXPORTS = ("isis_cic_deposit", "isis_cic_deposit_noalloc", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force",
            "isis_strerror", "isis_release_workspace", "isis_prof_enable", "isis_prof_reset", "isis_prof_read",
            "isis_launch_count", "isis_selftest_exp_ff", "isis_kick_drift", "isis_patch_poisson_solve",
-           "isis_patch_scalar_solve")
+           "isis_patch_scalar_solve", "isis_background_field")
 ISIS_INIT_INPUT, ISIS_INIT_BACKGROUND, ISIS_INIT_LOCAL, ISIS_INIT_PARENT = 0, 1, 2, 3
 
 
@@ -101,6 +101,9 @@ def load(path: str = LIB_PATH):
                                             P(isis_solve_info), vp]
     lib.isis_patch_poisson_solve.restype = ctypes.c_int
     lib.isis_patch_scalar_solve.restype = ctypes.c_int
+    lib.isis_background_field.argtypes = [ctypes.c_int, P(isis_params), P(isis_grid), ctypes.c_double,
+                                          P(ctypes.c_double)]
+    lib.isis_background_field.restype = ctypes.c_int
     lib.isis_strerror.argtypes = [ctypes.c_int]
     lib.isis_strerror.restype = ctypes.c_char_p
     lib.isis_release_workspace.argtypes = []
@@ -340,31 +343,18 @@ def isis_kick_drift(grid: Grid, x, y, z, vx, vy, vz, g, kick: float, drift: floa
 
 
 # ---------------------------------------------------------------------------
-# Background fields (initial guesses)
+# Background fields (initial guesses) and the paper's parameter presets (Table 1, Sect. 6.1)
 # ---------------------------------------------------------------------------
 
-def chi_background(a: float, a_ssb: float) -> float:
-    """Symmetron background minimum chi = sqrt(max(0, 1 - (a_SSB/a)^3)) (uniform eta = 1)."""
-    v = 1.0 - (a_ssb / a) ** 3
-    return v ** 0.5 if v > 0 else 0.0
-
-
-def u_background(a: float, fR0_abs: float, n: int = 1, Omega_m: float = 0.267, Omega_L: float = 0.733) -> float:
-    """f(R) background u = ln(a^2 |f_R(a)|), |f_R(a)| = |f_R0| [(1+4r)/(a^-3+4r)]^(n+1), r = OL/Om."""
-    import math
-    r = Omega_L / Omega_m
-    fR = fR0_abs * ((1 + 4 * r) / (a ** -3 + 4 * r)) ** (n + 1)
-    return math.log(a * a * fR)
-
-
-# ---------------------------------------------------------------------------
-# Parameter presets of the paper's Table 1 (Sect. 6.1)
-# ---------------------------------------------------------------------------
-
-def cham_background(a: float, cham_n: float) -> float:
-    """Chameleon background u = ln(psi) with psi^{-(1+n)} = a^-3: u = 3 ln(a) / (1 + n)."""
-    import math
-    return 3.0 * math.log(a) / (1.0 + cham_n)
+def isis_background_field(model: int, params: Params, a: float, grid: Grid | None = None) -> float:
+    """The model's uniform background field at expansion factor a (the library's ISIS_INIT_BACKGROUND value)."""
+    lib = load()
+    g = (grid or Grid(8, 1.0)).c()
+    p = params.c()
+    out = ctypes.c_double(0.0)
+    st = lib.isis_background_field(int(model), ctypes.byref(p), ctypes.byref(g), float(a), ctypes.byref(out))
+    _check(st, "isis_background_field")
+    return out.value
 
 
 def fofr_range(fR0_abs: float, n: int = 1, Omega_m: float = 0.267, Omega_L: float = 0.733) -> float:

@@ -44,7 +44,7 @@ def make_pairs(n_pairs, N, seed0=1000):
         eta = synth.lognormal_eta(N, float(N), SIGMA, seed0 + s, device="cuda")
         solve(eta, a, phi, 1e-8, isis.ISIS_INIT_BACKGROUND)
         etas.append(eta)
-        targets.append((phi - isis.chi_background(a, A_SSB)).float().reshape(-1))
+        targets.append((phi - isis.isis_background_field(isis.ISIS_SYMMETRON, isis.Params(a_ssb=A_SSB), a)).float().reshape(-1))
         avals.append(a)
     torch.cuda.synchronize()
     return etas, targets, avals, lg, time.time() - t0
@@ -104,7 +104,7 @@ def evaluate(net, N, seeds, avals, tol=1e-8):
                              "rel_l2_vs_converged": rms(phi - ref) / rms(ref)}
             net.guess(eta, a, A_SSB, phi)
             row["net"]["guess_rms_error"] = rms(phi - ref)
-            row["background"]["guess_rms_error"] = rms(ref - isis.chi_background(a, A_SSB))
+            row["background"]["guess_rms_error"] = rms(ref - isis.isis_background_field(isis.ISIS_SYMMETRON, isis.Params(a_ssb=A_SSB), a))
             out.append(row)
     return out
 

@@ -309,7 +309,7 @@ class UNet:
         else:
             self.features(eta, a, lg, x16=False)
         pred = self.forward(lg)
-        bg = isis.chi_background(a, a_ssb)
+        bg = isis.isis_background_field(isis.ISIS_SYMMETRON, isis.Params(a_ssb=a_ssb), a)
         if pooled:
             _ck(lib.isis_unet_guess_fine(_p(pred), lg, bg, self.scale, _p(phi), _s()), "guess_fine")
         else:

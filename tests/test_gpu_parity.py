@@ -23,9 +23,10 @@ def _prob(model, N, box, a, **kw):
 
 
 def _model_setup(isis, model, N, box, a, par):
+    """The library's model id and the initial guess both sides start from: the oracle's background field."""
     if model == oracle.SYMMETRON:
-        return isis.ISIS_SYMMETRON, isis.chi_background(a, par.a_ssb)
-    return isis.ISIS_FOFR_HS, isis.u_background(a, par.fR0_abs, par.n)
+        return isis.ISIS_SYMMETRON, oracle.background_field(oracle.SYMMETRON, a, a_ssb=par.a_ssb)
+    return isis.ISIS_FOFR_HS, oracle.background_field(oracle.FOFR, a, n=par.n, fR0_abs=par.fR0_abs)
 
 
 @pytest.mark.parametrize("model", [oracle.SYMMETRON, oracle.FOFR])
@@ -228,13 +229,13 @@ def test_uniform_density_closed_form(cuda_lib):
 
 
 # ---------------------------------------------------------------------------
-# Grids large enough for the temporally blocked streaming smoother (N >= 128):
-# several tiles in every direction and a ragged last tile along k.
+# Larger grids (N >= 128): the two-cells-per-thread smoother, the tiled prolongation and the fused
+# residual + restriction all run with many blocks per level.
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("model", [oracle.SYMMETRON, oracle.FOFR, oracle.POISSON])
-def test_streaming_f32_fixed_cycles_128(cuda_lib, model):
-    """Plain FP32 cycles (streaming smoother on 128^3) track the FP64 oracle's cycles to FP32 rounding."""
+def test_f32_fixed_cycles_128(cuda_lib, model):
+    """Plain FP32 cycles on 128^3 track the FP64 oracle's cycles to FP32 rounding."""
     isis = cuda_lib
     N, box = 128, 128.0
     par = isis.Params()
@@ -264,7 +265,7 @@ def test_streaming_f32_fixed_cycles_128(cuda_lib, model):
 @pytest.mark.parametrize("model,N,fmg", [(oracle.SYMMETRON, 128, 0), (oracle.FOFR, 128, 0), (oracle.POISSON, 128, 0),
                                          (oracle.SYMMETRON, 256, 0), (oracle.FOFR, 128, 1), (oracle.POISSON, 128, 1),
                                          (oracle.SYMMETRON, 256, 1)])
-def test_refine64_streaming_matches_oracle(cuda_lib, model, N, fmg):
+def test_refine64_large_matches_oracle(cuda_lib, model, N, fmg):
     isis = cuda_lib
     box = float(N)
     par = isis.Params()

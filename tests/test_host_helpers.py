@@ -12,15 +12,19 @@ from oracle import sphere1d
 from paper_1307_6748_gb300 import isis, sphere, synth
 
 
+@pytest.mark.gpu
 @pytest.mark.parametrize("a", [0.3, 0.5, 0.8, 1.0])
-def test_background_fields_match_the_oracle(a):
-    assert isis.chi_background(a, 0.5) == pytest.approx(oracle.background_field(oracle.SYMMETRON, a, a_ssb=0.5),
-                                                        abs=1e-15)
+def test_background_fields_match_the_oracle(cuda_lib, a):
+    """The library's background fields (isis_background_field, the ISIS_INIT_BACKGROUND values) against the
+    oracle's uniform-density solutions."""
+    bgf = isis.isis_background_field
+    assert bgf(isis.ISIS_SYMMETRON, isis.Params(a_ssb=0.5), a) == pytest.approx(
+        oracle.background_field(oracle.SYMMETRON, a, a_ssb=0.5), abs=1e-15)
     for n, f in ((1, 1e-5), (2, 1e-6)):
-        assert isis.u_background(a, f, n) == pytest.approx(
+        assert bgf(isis.ISIS_FOFR_HS, isis.Params(n=n, fR0_abs=f), a) == pytest.approx(
             oracle.background_field(oracle.FOFR, a, n=n, fR0_abs=f), rel=1e-14)
     for cn in (-0.5, 1.0, 2.0):
-        assert isis.cham_background(a, cn) == pytest.approx(
+        assert bgf(isis.ISIS_CHAMELEON, isis.Params(cham_n=cn, lambda0=2.0), a) == pytest.approx(
             oracle.background_field(oracle.CHAMELEON, a, cham_n=cn), abs=1e-15)
 
 
@@ -52,3 +56,12 @@ def test_density_recipes_have_mean_one():
     assert float(h1.mean()) == pytest.approx(1.0, rel=1e-12) and float(h1.min()) > 0.0
     # the haloes add mass concentrations beyond the lognormal field's
     assert float(h1.max()) > float(synth.lognormal_eta(16, 32.0, 0.5, 5).max())
+
+
+def test_halo_density_recipe_is_high_contrast():
+    """The halo workload's density (lognormal sigma = 1.5 plus 32 NFW haloes, 1 Mpc/h cells) has mean 1 and
+    peaks above 1e3 in the haloes, with voids below 0.05."""
+    eta = synth.nfw_eta(64, 64.0, 1.5, 1).numpy()
+    assert abs(eta.mean() - 1.0) <= 1e-12
+    assert eta.max() >= 1e3 and eta.min() < 0.05
+    assert (eta > 0).all()

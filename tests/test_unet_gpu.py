@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from oracle import unet_ref as U
 
 pytestmark = pytest.mark.gpu
@@ -255,7 +256,7 @@ def test_trained_guess_gain(cuda_lib):
         eta = synth.lognormal_eta(N, float(N), 1.5, seed, device="cuda")
         for a in (0.8, 1.0):
             _sym_solve(eta, a, ref, 1e-10, isis.ISIS_INIT_BACKGROUND)
-            bg = isis.chi_background(a, 0.5)
+            bg = oracle.background_field(oracle.SYMMETRON, a, a_ssb=0.5)
             net.guess(eta, a, 0.5, phi_net)
             e_bg, e_net = rms(ref - bg), rms(ref - phi_net)
             assert e_net <= 0.2 * e_bg, (seed, a, e_net, e_bg)
@@ -282,7 +283,7 @@ def test_pooled_guess(cuda_lib):
                            opts=opts)
     net.guess(eta, 1.0, 0.5, phi, pooled=True)
     rms = lambda x: float(torch.sqrt(torch.mean(x * x)))
-    assert rms(ref - phi) <= 0.5 * rms(ref - isis.chi_background(1.0, 0.5))
+    assert rms(ref - phi) <= 0.5 * rms(ref - oracle.background_field(oracle.SYMMETRON, 1.0, a_ssb=0.5))
     assert int(net.err.item()) == 0
 
 
@@ -296,7 +297,7 @@ def test_training_reduces_loss(cuda_lib):
         a = 0.8 if seed % 2 == 0 else 1.0
         phi = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
         _sym_solve(eta, a, phi, 1e-8, isis.ISIS_INIT_BACKGROUND)
-        pairs.append((eta, a, (phi - isis.chi_background(a, 0.5)).float().reshape(-1)))
+        pairs.append((eta, a, (phi - oracle.background_field(oracle.SYMMETRON, a, a_ssb=0.5)).float().reshape(-1)))
     net = unet.UNet(seed=1, mu=-1.125, sd=1.5)
     losses = []
     for step in range(60):
