@@ -27,6 +27,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "symmetron/f(R) 512³ FAS solve time to residual 1e-8; smoother HBM GB/s"
+# The arithmetic of the step: FP32 V-cycles; the fine-grid residual of the defect correction in float-float
+# (pairs of FP32 numbers, about 48 significant bits; FP32 instructions); the solution accumulated in FP64.
+DTYPE = "f32 (V-cycles) + float-float ~48-bit (outer residual) + f64 (accumulation, coarsest Newton)"
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -62,6 +65,8 @@ def workload(args):
                         f"f(R) FAS solves (FP32 cycles in FP64 defect correction, residual {args.tol:g}), "
                         f"forces of both models",
             "N": args.N, "box_mpc_h": args.box, "particles": args.N ** 3, "tol": args.tol,
+            "residual_floor": "float-float residual: about 1e-9 of ref for f(R) (u held to 48 bits), far below "
+                              "for Poisson and the symmetron",
             "symmetron": {"a": 1.0, "a_ssb": 0.5, "lambda0": 1.0, "beta": 1.0},
             "fofr": {"n": 1, "fR0_abs": 1e-5}, "cycle": f"V({args.nu1},{args.nu2}), coarsest {args.ncoarse}^3 dense Newton"
                                                         + (", FP32 phase started by nested iteration" if args.fmg else ""),
@@ -147,18 +152,20 @@ class ForceStep:
             ev[2].record(st)
         if self.net is not None:
             self.net.guess(eta, a, self.psym.a_ssb, chi, pooled=self.pooled)
+        if ev:
+            ev[3].record(st)
         infos["symmetron"] = isis.isis_scalar_solve(isis.ISIS_SYMMETRON, self.psym, grid, a, eta, chi, tol=self.tol,
                                                     opts=self.o_sym)
         if ev:
-            ev[3].record(st)
+            ev[4].record(st)
         infos["fofr"] = isis.isis_scalar_solve(isis.ISIS_FOFR_HS, self.pfr, grid, a, eta, u, tol=self.tol,
                                                opts=self.o_fr)
         if ev:
-            ev[4].record(st)
+            ev[5].record(st)
         isis.isis_fifth_force(isis.ISIS_SYMMETRON, self.psym, grid, a, Phi, chi, xx, yy, zz, out=g[0:3])
         isis.isis_fifth_force(isis.ISIS_FOFR_HS, self.pfr, grid, a, Phi, u, xx, yy, zz, out=g[3:6])
         if ev:
-            ev[5].record(st)
+            ev[6].record(st)
 
 
 # ---------------------------------------------------------------------------
@@ -251,9 +258,9 @@ def cpu_baseline(args, steps=1):
     times = [oracle_step(args.sample_N, args.box, args.N, args.tol) for _ in range(steps)]
     v = statistics.median(times) * 1e3 * scale
     return {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
-            "sample": f"full oracle force step (deposit, 3 FP64 FAS solves to {args.tol:g}, forces) on "
-                      f"{args.sample_N}^3 with the same recipe and cell size, x{scale:g} by cell count "
-                      f"(median of {steps})"}
+            "sample": f"estimate: {args.sample_N}^3 sample x {scale:g}. The full oracle force step (deposit, "
+                      f"3 FP64 FAS solves to {args.tol:g}, forces) timed on {args.sample_N}^3 with the same "
+                      f"recipe and cell size (median of {steps}), scaled by cell count to {args.N}^3"}
 
 
 def run_reference(args, rank, world):
@@ -272,10 +279,120 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload(args),
             "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
-                             "sample": f"oracle force step on {args.sample_N}^3 (same recipe, same cell size), "
-                                       f"x{scale:g} by cell count, mean of {args.steps}"},
+                             "sample": f"estimate: {args.sample_N}^3 sample x {scale:g}. Each step runs the oracle "
+                                       f"force step on {args.sample_N}^3 (same recipe, same cell size); value = "
+                                       f"mean of {args.steps} x {scale:g} by cell count",
+                             "sample_ms_per_step": ms / scale},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def copy_rates(h_src, d_dst, h_dst, d_src, stream) -> dict:
+    """This box's pinned-host link, measured with the step's own buffers (one particle coordinate, one force
+    component): GB/s host-to-device, device-to-host, and both directions at once on two streams."""
+    import torch
+    nb = d_dst.numel() * d_dst.element_size()
+    other = torch.cuda.Stream()
+
+    def timed(fn, reps=3):
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3
+            best = t if best is None else min(best, t)
+        return best
+
+    def both():
+        other.wait_stream(stream)
+        with torch.cuda.stream(other):
+            h_dst.copy_(d_src, non_blocking=True)
+        d_dst.copy_(h_src, non_blocking=True)
+        stream.wait_stream(other)
+
+    h2d = timed(lambda: d_dst.copy_(h_src, non_blocking=True))
+    d2h = timed(lambda: h_dst.copy_(d_src, non_blocking=True))
+    bo = timed(both)
+    return {"h2d": nb / h2d / 1e9, "d2h": nb / d2h / 1e9, "both": 2 * nb / bo / 1e9, "bytes": nb}
+
+
+# ---------------------------------------------------------------------------
+# Roofline figures
+# ---------------------------------------------------------------------------
+
+# Sources of the fine-grid smoother and its operators: the DRAM traffic recorded in profiles/ holds only while
+# they are unchanged.
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1307_6748_gb300", "csrc", f) for f in ("isis_kernels.cuh", "isis_model.cuh")]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_smooth_fine_512.md")
+
+
+def sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kind: str):
+    """DRAM bytes per launch of `kind` at 512^3 from the committed ncu summary, or None when the summary has no
+    figure for it or the kernel sources changed since it was taken.  The summary's machine-readable lines read
+    `traffic: <kind> <bytes per launch> <sources sha>`."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            lines = [ln.split() for ln in f if ln.startswith("traffic: ")]
+    except OSError:
+        return None
+    sha = sources_sha()
+    for parts in lines:
+        if len(parts) == 4 and parts[1] == kind and parts[3] == sha:
+            return float(parts[2])
+    return None
+
+
+def roofline_line(prof: dict, peak: float, peak_source: str, steps: int) -> dict:
+    """The dominant kernel (by summed event time, each model and form apart) against the HBM peak, and every
+    instantiation of the fine-grid smoother beside it.  achieved = algorithmic bytes / event time."""
+    name, (nl, kms, kbytes) = max(prof.items(), key=lambda kv: kv[1][1])
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    per = {}
+    for k, (n, ms, by) in sorted(prof.items()):
+        if k.startswith("smooth_fine[") and ms > 0:
+            a = by / (ms * 1e-3) / 1e9
+            per[k] = {"achieved": a, "frac": a / peak, "launches_per_step": n / steps, "ms_per_step": ms / steps,
+                      "avg_launch_us": ms * 1e3 / n, "bytes_per_launch": by / n,
+                      "traffic": recorded_traffic(k)}
+    allf = [v for k, v in prof.items() if k.startswith("smooth_fine[")]
+    agg = None
+    if allf:
+        ms = sum(v[1] for v in allf)
+        by = sum(v[2] for v in allf)
+        agg = {"achieved": by / (ms * 1e-3) / 1e9, "frac": by / (ms * 1e-3) / 1e9 / peak}
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": recorded_traffic(name), "launches": nl,
+            "avg_launch_us": kms * 1e3 / nl, "bytes_per_launch": kbytes / nl, "peak_source": peak_source,
+            "measured": f"CUDA events around every launch (on its stream) in {steps} steps run right after the timed "
+                        f"region; algorithmic bytes from the library's per-launch accounting",
+            "smooth_fine_by_instantiation": per, "smooth_fine_all": agg}
+
+
+def solve_fractions(N: int, infos: dict, breakdown: dict, peak: float) -> dict:
+    """Solve-level roofline: the algorithmic minimum of a V-cycle in FP32 (two fused passes per level visit, each
+    reading x and eta and writing x: 6 x 4 bytes per cell, x 8/7 over the levels) times the cycles, over the
+    solve's time (CUDA events in the timed region) times the HBM peak.  The FP64 outer residual and update
+    passes are not in the minimum, so they count against the fraction."""
+    per_cycle = 6 * 4 * (8.0 / 7.0) * N ** 3
+    out = {}
+    for k, info in infos.items():
+        t = breakdown[k] * 1e-3
+        out[k] = {"cycles": info.cycles, "bytes_per_cycle": per_cycle, "ms": breakdown[k],
+                  "frac": per_cycle * info.cycles / (t * peak * 1e9)}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -322,7 +439,7 @@ def main():
     barrier()
 
     # timed region: device-resident inputs, no per-launch events (they add about 6% to a step)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
     isis.prof_reset()
     with ClockSampler(local) as clk:
         barrier()
@@ -344,7 +461,7 @@ def main():
     prof = isis.prof_read()
     total_ms = t0.elapsed_time(t1)
     ms = max_over_ranks(total_ms / args.steps, dist, dev)
-    parts = ["deposit", "poisson", "symmetron", "fofr", "forces"]
+    parts = ["deposit", "poisson", "guess", "symmetron", "fofr", "forces"]
     breakdown = {p: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, p in enumerate(parts)}
 
     # end to end: positions from pinned host memory, forces back to pinned host memory, every step
@@ -423,11 +540,9 @@ def main():
         e2e = {"value": ems, "unit": "ms", "h2d_bytes_per_step": 3 * npart * 4, "d2h_bytes_per_step": 6 * npart * 4,
                "copies": "on a second stream, positions and forces double-buffered: step s's positions are copied "
                          "while step s-1 computes, each model's forces are read back while the next solve runs",
-               "serial_value": serial}
+               "serial_value": serial, "copy_rates_gbs": copy_rates(hx, x, hg[0], g[0], stream)}
 
-    # roofline of the dominant kernel kind (by summed event time)
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (nl, kms, kbytes) = dom
+    # roofline of the dominant kernel (kind and instantiation, by summed event time)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -435,30 +550,29 @@ def main():
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = kbytes / (kms * 1e-3) / 1e9
-    roofline = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "launches": nl,
-                "avg_launch_us": kms * 1e3 / nl, "bytes_per_launch": kbytes / nl,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s",
-                "measured": f"CUDA events around every launch (on its stream) in {args.steps} steps run right after "
-                            f"the timed region; algorithmic bytes from the library's per-launch accounting"}
+    roofline = roofline_line(prof, hbm_peak, "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks
+                             else "fallback 6800 GB/s", args.steps)
+    roofline["solve_frac"] = solve_fractions(args.N, infos, breakdown, hbm_peak)
     kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
                    "GBps": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None} for k, v in prof.items()}
 
-    # the mixed-precision solves against the plain FP64 solver on the same GPU and density
-    # (outside the timed region; each solve once after one of its own warm-ups)
+    # the mixed-precision solves against the plain FP64 solver on the same GPU and density (outside the timed
+    # region; each solve once after one of its own warm-ups).  Arms: the FP64 solver in V(2,2) and in the
+    # benchmark's own cycle shape V(nu1,nu2); the mixed path in that shape without and with the nested-iteration
+    # start.  speedup_same_cycle compares the FP64 and mixed arms of one cycle shape, neither with nested
+    # iteration (which only the mixed path has); speedup is the FP64 V(2,2) arm against the benchmarked setting.
     vs_fp64 = None
     if not args.no_fp64_ref:
-        vs_fp64 = {}
+        vs_fp64 = {"cycle": f"V({args.nu1},{args.nu2})"}
+        arms = (("fp64_v22", isis.ISIS_F64, 2, 2, 0), ("fp64", isis.ISIS_F64, args.nu1, args.nu2, 0),
+                ("refine64_nofmg", isis.ISIS_F32_REFINE64, args.nu1, args.nu2, 0),
+                ("refine64", isis.ISIS_F32_REFINE64, args.nu1, args.nu2, args.fmg))
         for name, prec_inner in (("poisson", args.inner_poisson), ("symmetron", args.inner_sym),
                                  ("fofr", args.inner_fofr)):
             row = {}
-            for label, prec in (("fp64", isis.ISIS_F64), ("refine64", isis.ISIS_F32_REFINE64)):
+            for label, prec, nu1, nu2, fmg in arms:
                 o = isis.Opts(prec=prec, inner_cycles=prec_inner, init=isis.ISIS_INIT_BACKGROUND,
-                              n_coarsest=args.ncoarse, max_cycles=40,
-                              fmg=args.fmg if prec == isis.ISIS_F32_REFINE64 else 0,
-                              nu1=args.nu1 if prec == isis.ISIS_F32_REFINE64 else 2,
-                              nu2=args.nu2 if prec == isis.ISIS_F32_REFINE64 else 2)
+                              n_coarsest=args.ncoarse, max_cycles=60, fmg=fmg, nu1=nu1, nu2=nu2)
                 out = {"poisson": Phi, "symmetron": chi, "fofr": u}[name]
                 for rep in range(2):
                     barrier()
@@ -474,7 +588,8 @@ def main():
                     barrier()
                 row[label + "_ms"] = e0.elapsed_time(e1)
                 row[label + "_cycles"] = info.cycles
-            row["speedup"] = row["fp64_ms"] / row["refine64_ms"]
+            row["speedup"] = row["fp64_v22_ms"] / row["refine64_ms"]
+            row["speedup_same_cycle"] = row["fp64_ms"] / row["refine64_nofmg_ms"]
             vs_fp64[name] = row
 
     cpu = None
@@ -484,7 +599,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": workload(args),
+                "vs_baseline": None, "dtype": DTYPE, "data": "synthetic", "config": workload(args),
                 "breakdown_ms": breakdown,
                 "solves": {k: {"cycles": v.cycles, "outer": v.outer, "res_rel": v.res_final / v.res_ref}
                            for k, v in infos.items()},

@@ -309,7 +309,9 @@ isis_status isis_patch_scalar_solve(isis_model model, const isis_params* params,
  * launch is also bracketed by CUDA events on its stream and its algorithmic
  * bytes (the minimum DRAM traffic of its work) are recorded, per kernel kind. */
 typedef struct {
-  const char* name;   /* kernel kind, e.g. "smooth_fine" (static string) */
+  const char* name;   /* kernel kind, e.g. "smooth_fine"; the multigrid kernels' kinds carry the model
+                         and form of their instantiation, e.g. "smooth_fine[fofr/delta]" (a string owned
+                         by the library, valid until it is unloaded) */
   int64_t launches;   /* launches recorded since the last reset */
   double ms;          /* summed event time of those launches */
   double bytes;       /* summed algorithmic bytes of those launches */
@@ -319,8 +321,9 @@ typedef struct {
 void isis_prof_enable(int on);
 /* Zero the counters and drop recorded events. */
 void isis_prof_reset(void);
-/* Synchronise the device, then fill up to max entries (one per kernel kind
- * with at least one launch); returns the number filled. */
+/* Synchronise the device, then fill up to max entries (one per kernel kind,
+ * and per model and form for the multigrid kernels, with at least one
+ * launch); returns the number filled. */
 int isis_prof_read(isis_prof_entry* out, int max);
 /* Kernel launches issued by the library since the last isis_prof_reset(). */
 int64_t isis_launch_count(void);

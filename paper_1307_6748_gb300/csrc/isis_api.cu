@@ -6,6 +6,7 @@
 #include <vector>
 #include <algorithm>
 #include <cstring>
+#include <string>
 
 #include "isis_patch.cuh"
 #include "isis_solver.cuh"
@@ -345,10 +346,20 @@ isis_status isis_selftest_exp_ff(const double* x, double* y, int n, void* stream
 
 int isis_prof_read(isis_prof_entry* out, int max) {
   cudaDeviceSynchronize();
-  long long cnt[KK_COUNT] = {0};
-  double ms[KK_COUNT] = {0}, by[KK_COUNT] = {0};
+  constexpr int kAll = KK_COUNT * kKindTags;
+  // names "kind" or "kind[model/form]", built once
+  static std::vector<std::string> names;
+  if (names.empty()) {
+    static const char* kTag[kKindTags] = {"", "[poisson/field]", "[poisson/delta]", "[symmetron/field]",
+                                          "[symmetron/delta]", "[fofr/field]", "[fofr/delta]"};
+    for (int t = 0; t < kKindTags; ++t)
+      for (int k = 0; k < KK_COUNT; ++k) names.push_back(std::string(kKindNames[k]) + kTag[t]);
+  }
+  std::vector<long long> cnt(kAll, 0);
+  std::vector<double> ms(kAll, 0.0), by(kAll, 0.0);
   for (const ProfRec& r : g_recs) {
     float t = 0.f;
+    if (r.kind < 0 || r.kind >= kAll) continue;
     if (cudaEventElapsedTime(&t, g_events[r.ev], g_events[r.ev + 1]) != cudaSuccess) continue;
     cnt[r.kind] += 1;
     ms[r.kind] += t;
@@ -356,8 +367,8 @@ int isis_prof_read(isis_prof_entry* out, int max) {
   }
   cudaGetLastError();
   int n = 0;
-  for (int k = 0; k < KK_COUNT && n < max; ++k)
-    if (cnt[k] > 0) out[n++] = {kKindNames[k], cnt[k], ms[k], by[k]};
+  for (int k = 0; k < kAll && n < max; ++k)
+    if (cnt[k] > 0) out[n++] = {names[k].c_str(), cnt[k], ms[k], by[k]};
   return n;
 }
 

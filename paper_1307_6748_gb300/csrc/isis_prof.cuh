@@ -34,6 +34,12 @@ enum KernelKind : int {
   KK_COUNT
 };
 
+// A launch of the multigrid kernels also records the instantiation it runs: the recorded kind is
+// kind + KK_COUNT * tag with tag = 1 + 2 * model + form (model 0 Poisson, 1 symmetron, 2 f(R) and the
+// chameleon; form 0 field, 1 correction), tag 0 for the other kernels.
+constexpr int kKindTags = 7;
+constexpr int kind_tag(int kind, int model, int form) { return kind + KK_COUNT * (1 + 2 * model + form); }
+
 void prof_pre(cudaStream_t st);
 void prof_post(int kind, double bytes, cudaStream_t st);
 // Whether per-launch events are on; the launches counted so far; count n launches run through a CUDA graph

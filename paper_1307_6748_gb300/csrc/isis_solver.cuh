@@ -136,6 +136,8 @@ struct Cycler {
     return n;
   }
   static double cells(const LevelView<T>& v) { return (double)v.N * v.N * v.N; }
+  // kernel kind of a launch, with this instantiation's model and form
+  static constexpr int tk(int kind) { return kind_tag(kind, (int)M, (int)FM); }
 
   isis_status smooth(int l, int sweeps) {
     LevelView<T>& v = L[l];
@@ -143,7 +145,7 @@ struct Cycler {
     // algorithmic bytes of a full sweep: read x and the per-cell arrays once,
     // write x once (a one-colour launch moves half of that)
     double bytes = cells(v) * sizeof(T) * (2 + arrays(v.sig != nullptr));
-    int kind = l == 0 ? KK_SMOOTH_FINE : KK_SMOOTH_COARSE;
+    const int kind = tk(l == 0 ? KK_SMOOTH_FINE : KK_SMOOTH_COARSE);
     for (int s = 0; s < sweeps; ++s)
       for (int color = 0; color < 2; ++color) {
         if constexpr (sizeof(T) == 4) {
@@ -165,7 +167,7 @@ struct Cycler {
     LevelView<T>& C = L[l + 1];
     const size_t nc = (size_t)C.N * C.N * C.N;
     const double bytes = sizeof(T) * (2 * (double)nc + 2 * cells(L[l]));
-    const int kind = l == 0 ? KK_PROLONG_FINE : KK_PROLONG_COARSE;
+    const int kind = tk(l == 0 ? KK_PROLONG_FINE : KK_PROLONG_COARSE);
     if constexpr (sizeof(T) == 4) {
       if (C.N >= kP2K) {
         const unsigned blocks = (unsigned)(nc / (kPTI * kPTJ * kP2K));
@@ -191,7 +193,7 @@ struct Cycler {
   isis_status vcycle(int l) {
     const int last = (int)L.size() - 1;
     if (l == last) {
-      ISIS_LAUNCH(KK_COARSE_NEWTON, 0.0, st,
+      ISIS_LAUNCH(tk(KK_COARSE_NEWTON), 0.0, st,
                   (coarse_newton<M, FM, T><<<1, kCoarseMax, 0, st>>>(L[l], c, ws->iflags, ws->iflags + 1)));
       return ISIS_OK;
     }
@@ -208,9 +210,9 @@ struct Cycler {
       // per-cell inputs for one thread, so the residual goes through a scratch grid
       if constexpr (sizeof(T) == 4) {
         float* res = (float*)ws->x0[0];
-        ISIS_LAUNCH(KK_RESTRICT_FINE, rbytes, st,
+        ISIS_LAUNCH(tk(KK_RESTRICT_FINE), rbytes, st,
                     (resid_rb2<M, FM><<<nblk((size_t)nf / 2, 256), 256, 0, st>>>(L[0], c, res)));
-        ISIS_LAUNCH(KK_RESTRICT_FINE, 0.0, st,
+        ISIS_LAUNCH(tk(KK_RESTRICT_FINE), 0.0, st,
                     (restrict_xr<M, FM><<<nblk(nc, 256), 256, 0, st>>>(L[0], res, C, (float*)ws->x0[1],
                                                                         (float*)ws->sig[1])));
       }
@@ -218,18 +220,18 @@ struct Cycler {
       bool done = false;
       if constexpr (sizeof(T) == 4 && M != FOFR) {
         if (C.N >= 4) {
-          ISIS_LAUNCH(l == 0 ? KK_RESTRICT_FINE : KK_RESTRICT_COARSE, rbytes, st,
+          ISIS_LAUNCH(tk(l == 0 ? KK_RESTRICT_FINE : KK_RESTRICT_COARSE), rbytes, st,
                       (resid_restrict2<M, FM><<<nblk(nc / 2, 256), 256, 0, st>>>(L[l], c, C, (float*)ws->x0[l + 1],
                                                                                  (float*)ws->sig[l + 1])));
           done = true;
         }
       }
       if (!done)
-        ISIS_LAUNCH(l == 0 ? KK_RESTRICT_FINE : KK_RESTRICT_COARSE, rbytes, st,
+        ISIS_LAUNCH(tk(l == 0 ? KK_RESTRICT_FINE : KK_RESTRICT_COARSE), rbytes, st,
                     (resid_restrict<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], c, C, (T*)ws->x0[l + 1],
                                                                             (T*)ws->sig[l + 1])));
     }
-    ISIS_LAUNCH(KK_SIGMA, sizeof(T) * ncd * (2 + arrays(true)), st,
+    ISIS_LAUNCH(tk(KK_SIGMA), sizeof(T) * ncd * (2 + arrays(true)), st,
                 (coarse_sigma_add<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(C, c, (T*)ws->sig[l + 1])));
     s = vcycle(l + 1);
     if (s != ISIS_OK) return s;
@@ -270,14 +272,14 @@ struct Cycler {
   isis_status fine_rms(double* out) {
     if constexpr (std::is_same<T, float>::value) {
       if (L[0].lg >= 3) {
-        ISIS_LAUNCH(KK_NORM, cells(L[0]) * sizeof(T) * (1 + arrays(L[0].sig != nullptr)), st,
+        ISIS_LAUNCH(tk(KK_NORM), cells(L[0]) * sizeof(T) * (1 + arrays(L[0].sig != nullptr)), st,
                     (norm_rb2<M, FM><<<kNormBlocks, kNormThreads, 0, st>>>(L[0], c, ws->part)));
       } else {
-        ISIS_LAUNCH(KK_NORM, cells(L[0]) * sizeof(T) * (1 + arrays(L[0].sig != nullptr)), st,
+        ISIS_LAUNCH(tk(KK_NORM), cells(L[0]) * sizeof(T) * (1 + arrays(L[0].sig != nullptr)), st,
                     (norm_partial<M, FM, T><<<kNormBlocks, kNormThreads, 0, st>>>(L[0], c, ws->part)));
       }
     } else {
-      ISIS_LAUNCH(KK_NORM, cells(L[0]) * sizeof(T) * (1 + arrays(L[0].sig != nullptr)), st,
+      ISIS_LAUNCH(tk(KK_NORM), cells(L[0]) * sizeof(T) * (1 + arrays(L[0].sig != nullptr)), st,
                   (norm_partial<M, FM, T><<<kNormBlocks, kNormThreads, 0, st>>>(L[0], c, ws->part)));
     }
     ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
@@ -768,17 +770,17 @@ isis_status solve_refine(const SolveArgs& A) {
     if (M == FOFR) {
       float2* psi_ff = reinterpret_cast<float2*>(ws->b64);
       float2* E_ff = reinterpret_cast<float2*>(ws->s64);
-      ISIS_LAUNCH(KK_OUTER_RESID, 24.0 * n, st,
+      ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), 24.0 * n, st,
                   (fofr_prep_ff<<<nblk(n / 2, 256), 256, 0, st>>>(phi64, psi_ff, E_ff, n, ffc.ubff, ws->exptab_ff,
                                                                ffc.ek)));
-      ISIS_LAUNCH(KK_OUTER_RESID, 32.0 * n, st,
+      ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), 32.0 * n, st,
                   (outer_residual_fofr_ff<<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, ffc, eta64, psi_ff, E_ff,
                                                                                  ws->exptab_ff, r0, B0, ws->part)));
     } else {
       float2* pff = reinterpret_cast<float2*>(ws->b64);
-      ISIS_LAUNCH(KK_OUTER_RESID, 16.0 * n, st, (phi_to_ff<<<nblk(n, 256), 256, 0, st>>>(phi64, pff, n)));
+      ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), 16.0 * n, st, (phi_to_ff<<<nblk(n, 256), 256, 0, st>>>(phi64, pff, n)));
       // phi_ff and eta read, r and B written: 24 bytes per cell
-      ISIS_LAUNCH(KK_OUTER_RESID, 24.0 * n, st,
+      ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), 24.0 * n, st,
                   (outer_residual_ff<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, rff, eta64, pff, r0, B0,
                                                                               ws->part)));
     }

@@ -247,9 +247,10 @@ def launch_count() -> int:
 
 
 def prof_read() -> dict:
-    """Per kernel kind: {name: (launches, ms, algorithmic bytes)} (synchronises the device)."""
-    buf = (isis_prof_entry * 64)()
-    n = load().isis_prof_read(buf, 64)
+    """Per kernel kind, and for the multigrid kernels per model and form ("smooth_fine[fofr/delta]"):
+    {name: (launches, ms, algorithmic bytes)} (synchronises the device)."""
+    buf = (isis_prof_entry * 256)()
+    n = load().isis_prof_read(buf, 256)
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms), float(buf[i].bytes)) for i in range(n)}
 
 
