@@ -136,9 +136,12 @@ typedef struct {
  *   eta      device double[N^3] (eta_f64 != 0) or float[N^3] (eta_f64 == 0),
  *            overwritten.
  * Accumulation is in 64-bit fixed point: each particle's eight weights are
- * truncated to multiples of 2^-40 and summed as integers, so the result does
- * not depend on the order of particles; a cell may collect at most 2^23 unit
- * weights.  Uses an int64 N^3 scratch buffer cached by the
+ * truncated to multiples of 2^-40 and summed as unsigned integers, so the
+ * result does not depend on the order of particles.  A cell's accumulator
+ * holds less than 2^24 unit weights (2^64 / 2^40): the weights a cell
+ * collects, (npart / N^3) times its overdensity eta, must stay below 2^24
+ * (16.7 million particles), or that cell wraps silently; npart < 2^24 rules
+ * it out for any clustering.  Uses an int64 N^3 scratch buffer cached by the
  * library.  EINVAL: npart < 1, npart > 2^40 or N invalid. */
 isis_status isis_cic_deposit(const isis_grid* grid, const float* x, const float* y, const float* z, int64_t npart,
                              void* eta, int eta_f64, void* stream);
@@ -151,8 +154,13 @@ isis_status isis_cic_deposit(const isis_grid* grid, const float* x, const float*
  *   - Scratch: a fixed array of 64^3 int64 accumulators (2 MiB) compiled into
  *     the library; every GPU that loads the library holds it until the
  *     process exits.  Nothing is allocated or freed by this call.
- *   - Limit: grid->N <= 64; larger grids return ISIS_EINVAL (use
+ *   - Limits: grid->N <= 64 and npart < 2^24 (then no cell can collect the
+ *     2^24 unit weights that would wrap its accumulator, however the particles
+ *     cluster); larger grids or more particles return ISIS_EINVAL (use
  *     isis_cic_deposit).  Other arguments as for isis_cic_deposit, same result.
+ *   - Device contexts: the array's address is cached per device for the life
+ *     of the process; a device reset (cudaDeviceReset) invalidates it and is
+ *     not supported between calls.
  *   - Set-up: the first call on each device looks up the array's device
  *     address (cudaGetSymbolAddress) with that device current; make that first
  *     call before any stream capture.

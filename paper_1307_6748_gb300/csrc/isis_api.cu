@@ -241,7 +241,7 @@ static const char* kKindNames[KK_COUNT] = {
     "prolong_fine",   "prolong_coarse", "coarse_newton",      "norm_fine",             "outer_residual64",
     "update64",       "setup",         "reduce",              "init_guess",            "cic_scatter",
     "cic_finish",     "force_grid",    "force_gather",        "unet_conv",             "unet_elem",
-    "patch_smooth",   "patch_other",   "patch_coarsest"};
+    "patch_smooth",   "patch_other",   "patch_coarsest",      "coarse_cycle"};
 
 struct ProfRec {
   int kind;

@@ -6,6 +6,7 @@
 // cell floor(x - 1/2) and t to the next cell, t = (x - 1/2) - floor(x - 1/2);
 // periodic wrap.  The 3-D weight is the product of the three.
 #include <cmath>
+#include <mutex>
 
 #include "isis_solver.cuh"
 
@@ -215,12 +216,18 @@ static __device__ __align__(256) unsigned long long g_noalloc_acc[(size_t)kNoAll
 // Device address of g_noalloc_acc, looked up once per device.  In host code
 // the name g_noalloc_acc is only a host-side stand-in for the array, so its
 // address must come from cudaGetSymbolAddress with the device current.
+// The table is filled under a mutex, so host threads that make their first calls at once are safe.  The
+// cached address outlives nothing but the device's context: a device reset between calls is not supported.
 constexpr int kMaxDevices = 64;
 static unsigned long long* g_noalloc_ptr[kMaxDevices] = {nullptr};
+static std::mutex g_noalloc_mu;
+// Fewer particles than this cannot wrap a 64-bit accumulator of 2^-40 units in any cell.
+constexpr int64_t kNoAllocMaxParticles = (int64_t)1 << 24;
 
 static isis_status noalloc_scratch(unsigned long long** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ISIS_ECUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_acc) != cudaSuccess || !p) {
@@ -296,7 +303,7 @@ isis_status isis_cic_deposit(const isis_grid* grid, const float* x, const float*
 isis_status isis_cic_deposit_noalloc(const isis_grid* grid, const float* x, const float* y, const float* z,
                                      int64_t npart, void* eta, int eta_f64, void* stream) {
   if (!grid_valid(grid) || !x || !y || !z || !eta || npart < 1 || npart > ((int64_t)1 << 40)) return ISIS_EINVAL;
-  if (grid->N > kNoAllocMaxN) return ISIS_EINVAL;  // larger grids need isis_cic_deposit
+  if (grid->N > kNoAllocMaxN || npart >= kNoAllocMaxParticles) return ISIS_EINVAL;  // use isis_cic_deposit
   unsigned long long* acc = nullptr;
   isis_status s = noalloc_scratch(&acc);
   if (s != ISIS_OK) return s;
@@ -304,7 +311,7 @@ isis_status isis_cic_deposit_noalloc(const isis_grid* grid, const float* x, cons
   const size_t n = (size_t)N * N * N;
   cudaStream_t st = (cudaStream_t)stream;
   // the array keeps the previous call's sums: clear the part this grid uses
-  ISIS_LAUNCH(KK_CIC_SCATTER, 8.0 * n, st, (zero_u64<<<nblk(n, 256), 256, 0, st>>>(acc, n)));
+  ISIS_LAUNCH(KK_SETUP, 8.0 * n, st, (zero_u64<<<nblk(n, 256), 256, 0, st>>>(acc, n)));
   ISIS_LAUNCH(KK_CIC_SCATTER, 12.0 * npart + 8.0 * n, st,
               (cic_scatter<<<nblk((size_t)npart, 256), 256, 0, st>>>(x, y, z, (long long)npart, lg, acc)));
   const double scale = (double)n / ((double)npart * kFix);

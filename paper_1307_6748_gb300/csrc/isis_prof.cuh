@@ -31,6 +31,7 @@ enum KernelKind : int {
   KK_PATCH_SMOOTH,      // smoother on a refinement patch
   KK_PATCH_OTHER,       // the patch's residual, transfers, interpolation and norms
   KK_PATCH_COARSEST,    // the relaxation of a patch's coarsest level (one block)
+  KK_COARSE_CYCLE,      // the levels of a V-cycle from 16^3 down, in one block
   KK_COUNT
 };
 

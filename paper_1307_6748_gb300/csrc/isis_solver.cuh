@@ -12,6 +12,7 @@
 
 #include "../../include/isis.h"
 #include "isis_coarse.cuh"
+#include "isis_fofr_staged.cuh"
 #include "isis_ff.cuh"
 #include "isis_prof.cuh"
 
@@ -146,6 +147,25 @@ struct Cycler {
     // write x once (a one-colour launch moves half of that)
     double bytes = cells(v) * sizeof(T) * (2 + arrays(v.sig != nullptr));
     const int kind = tk(l == 0 ? KK_SMOOTH_FINE : KK_SMOOTH_COARSE);
+    if constexpr (sizeof(T) == 4 && M == FOFR) {
+      if (v.N >= 128) {
+        // the other colour's exponentials staged in shared memory (isis_fofr_staged.cuh)
+        const size_t smem = staged_smem_bytes<FM>(v.N);
+        static bool attr[64] = {};
+        const int dev = ws->device >= 0 && ws->device < 64 ? ws->device : 0;
+        if (!attr[dev]) {
+          ISIS_CK(cudaFuncSetAttribute(fofr_smooth_staged<FM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)staged_smem_bytes<FM>(1024)));
+          attr[dev] = true;
+        }
+        const unsigned blocks = (unsigned)((v.N / kSTRows) * (v.N / kSTChunk));
+        for (int s = 0; s < sweeps; ++s)
+          for (int color = 0; color < 2; ++color)
+            ISIS_LAUNCH(kind, bytes * 0.5, st,
+                        (fofr_smooth_staged<FM><<<blocks, kSTThreads, smem, st>>>(v, c, color)));
+        return ISIS_OK;
+      }
+    }
     for (int s = 0; s < sweeps; ++s)
       for (int color = 0; color < 2; ++color) {
         if constexpr (sizeof(T) == 4) {
@@ -190,8 +210,39 @@ struct Cycler {
     return ISIS_OK;
   }
 
+  // Every level from l (N <= 16) down in one CTA (FP32 grids): see coarse_cycle.
+  isis_status coarse_fused(int l) {
+    if constexpr (sizeof(T) == 4) {
+      const int last = (int)L.size() - 1;
+      CoarseCycle cc;
+      cc.nlev = last - l + 1;
+      cc.nu1 = nu1;
+      cc.nu2 = nu2;
+      double bytes = 0.0;
+      for (int q = 0; q < cc.nlev; ++q) {
+        cc.L[q] = L[l + q];
+        bytes += cells(L[l + q]) * sizeof(float) * (arrays(false) + (q == 0 ? 3 : 0));
+      }
+      const size_t smem = coarse_cycle_floats(L[l].N, L[last].N) * sizeof(float);
+      // the largest cycle's shared memory, allowed once per instantiation and device
+      static bool attr[64] = {};
+      const int dev = ws->device >= 0 && ws->device < 64 ? ws->device : 0;
+      if (!attr[dev]) {
+        const size_t most = coarse_cycle_floats(kCVMaxN, 2) * sizeof(float);
+        ISIS_CK(cudaFuncSetAttribute(coarse_cycle<M, FM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most));
+        attr[dev] = true;
+      }
+      ISIS_LAUNCH(tk(KK_COARSE_CYCLE), bytes, st,
+                  (coarse_cycle<M, FM><<<1, kCVThreads, smem, st>>>(cc, c, ws->iflags, ws->iflags + 1)));
+    }
+    return ISIS_OK;
+  }
+
   isis_status vcycle(int l) {
     const int last = (int)L.size() - 1;
+    if constexpr (sizeof(T) == 4) {
+      if (L[l].N <= kCVMaxN && last - l + 1 <= kCVMaxLev) return coarse_fused(l);
+    }
     if (l == last) {
       ISIS_LAUNCH(tk(KK_COARSE_NEWTON), 0.0, st,
                   (coarse_newton<M, FM, T><<<1, kCoarseMax, 0, st>>>(L[l], c, ws->iflags, ws->iflags + 1)));
@@ -210,8 +261,24 @@ struct Cycler {
       // per-cell inputs for one thread, so the residual goes through a scratch grid
       if constexpr (sizeof(T) == 4) {
         float* res = (float*)ws->x0[0];
-        ISIS_LAUNCH(tk(KK_RESTRICT_FINE), rbytes, st,
-                    (resid_rb2<M, FM><<<nblk((size_t)nf / 2, 256), 256, 0, st>>>(L[0], c, res)));
+        if (L[0].N >= 128) {
+          // two one-colour passes with the other colour's exponentials staged in shared memory
+          const unsigned blocks = (unsigned)((L[0].N / kSTRows) * (L[0].N / kSTChunk));
+          const size_t smem = staged_smem_bytes<FM>(L[0].N);
+          static bool attr[64] = {};
+          const int dev = ws->device >= 0 && ws->device < 64 ? ws->device : 0;
+          if (!attr[dev]) {
+            ISIS_CK(cudaFuncSetAttribute(fofr_smooth_staged<FM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)staged_smem_bytes<FM>(1024)));
+            attr[dev] = true;
+          }
+          for (int color = 0; color < 2; ++color)
+            ISIS_LAUNCH(tk(KK_RESTRICT_FINE), rbytes * 0.5, st,
+                        (fofr_smooth_staged<FM, true><<<blocks, kSTThreads, smem, st>>>(L[0], c, color, res)));
+        } else {
+          ISIS_LAUNCH(tk(KK_RESTRICT_FINE), rbytes, st,
+                      (resid_rb2<M, FM><<<nblk((size_t)nf / 2, 256), 256, 0, st>>>(L[0], c, res)));
+        }
         ISIS_LAUNCH(tk(KK_RESTRICT_FINE), 0.0, st,
                     (restrict_xr<M, FM><<<nblk(nc, 256), 256, 0, st>>>(L[0], res, C, (float*)ws->x0[1],
                                                                         (float*)ws->sig[1])));
