@@ -48,53 +48,92 @@ inline size_t staged_smem_bytes(int N) {
   return 3 * (size_t)(kSTRows + 2) * (size_t)(N / 2) * sizeof(typename StagedVal<FM>::T);
 }
 
-// Blocks: (N / TJ) slabs in j times (N / kSTChunk) chunks in i.  N >= 128, a power of two.
+// Blocks: (N / TJ) slabs in j times (N / kSTChunk) chunks in i; N = 2^LG >= 128.
 // kResid: instead of updating x, write the residual r = Sigma - L(x) of the colour's cells into res (same
 // layout as x); two launches (colour 0, 1) give the residual of the grid.
-template <Form FM, bool kResid = false>
+// The global loads of plane i + 2 (to be staged) and of the own cells of plane i + 1 are issued into registers
+// before plane i is updated, so their latency overlaps the update and the block barriers.
+template <Form FM, bool kResid, int LG>
 __global__ void __launch_bounds__(kSTThreads) fofr_smooth_staged(LevelView<float> L, Coef c, int color,
-                                                                 float* __restrict__ res = nullptr) {
+                                                                 float* __restrict__ res) {
   using V = typename StagedVal<FM>::T;
+  constexpr unsigned N = 1u << LG, m = N - 1, hN = N >> 1, half = 1u << (3 * LG - 1);
+  constexpr unsigned kR = kSTRows + 2;        // staged rows: j0 - 1 .. j0 + TJ
+  constexpr unsigned plane_vals = kR * hN;    // values per staged plane
+  constexpr unsigned kFill = (plane_vals + kSTThreads - 1) / kSTThreads;  // staged values per thread
+  constexpr unsigned kOwn = kSTRows * hN / kSTThreads;                    // own cells per thread and plane
+  static_assert(kSTRows * hN % kSTThreads == 0, "own cells must divide evenly among the threads");
   extern __shared__ float4 st_dyn[];
   V* ring = reinterpret_cast<V*>(st_dyn);
-  const int lg = L.lg;
-  const unsigned N = 1u << lg, m = N - 1, hN = N >> 1, half = 1u << (3 * lg - 1);
   const unsigned own = color ? half : 0u, oth = color ? 0u : half;
-  const unsigned nslab = N / kSTRows;
+  constexpr unsigned nslab = N / kSTRows;
   const unsigned j0 = (blockIdx.x % nslab) * kSTRows, i0 = (blockIdx.x / nslab) * kSTChunk;
-  constexpr unsigned kR = kSTRows + 2;   // staged rows: j0 - 1 .. j0 + TJ
-  const unsigned plane_vals = kR * hN;  // values per staged plane
 
-  // stage the other colour's rows of plane p (wrapped) into ring slot s
-  auto fill = [&](unsigned p, unsigned s) {
+  // raw values (x, B) of the other colour's staged rows of plane p
+  float rx[kFill], rB[kFill];
+  auto load_raw = [&](unsigned p) {
+#pragma unroll
+    for (unsigned u = 0; u < kFill; ++u) {
+      const unsigned t = threadIdx.x + u * kSTThreads;
+      if (t < plane_vals) {
+        const unsigned r = t / hN, k2 = t - r * hN, jj = (j0 + r - 1) & m;
+        const unsigned g = oth + ((((p & m) << LG) | jj) << (LG - 1)) + k2;
+        rx[u] = L.x[g];
+        rB[u] = (FM == DELTA) ? L.B[g] : 0.f;
+      }
+    }
+  };
+  auto store_raw = [&](unsigned s) {
     V* dst = ring + s * plane_vals;
-    for (unsigned t = threadIdx.x; t < plane_vals; t += blockDim.x) {
-      const unsigned r = t / hN, k2 = t - r * hN, jj = (j0 + r - 1) & m;
-      const unsigned g = oth + ((((p & m) << lg) | jj) << (lg - 1)) + k2;
-      const float x = L.x[g];
-      const float B = (FM == DELTA) ? L.B[g] : 0.f;
-      dst[t] = st_values<FM>(x, B);
+#pragma unroll
+    for (unsigned u = 0; u < kFill; ++u) {
+      const unsigned t = threadIdx.x + u * kSTThreads;
+      if (t < plane_vals) dst[t] = st_values<FM>(rx[u], rB[u]);
+    }
+  };
+  // the own cells of plane i: x, Sigma and eta (field form) or B (correction form)
+  float ox[kOwn], osig[kOwn], oe[kOwn];
+  auto load_own = [&](unsigned i) {
+#pragma unroll
+    for (unsigned u = 0; u < kOwn; ++u) {
+      const unsigned t = threadIdx.x + u * kSTThreads, r = t / hN, k2 = t - r * hN, j = j0 + r;
+      const unsigned o = own + (((i << LG) | j) << (LG - 1)) + k2;
+      ox[u] = L.x[o];
+      osig[u] = L.sig ? L.sig[o] : 0.f;
+      oe[u] = (FM == FIELD) ? L.eta[o] : L.B[o];
     }
   };
 
   const float ih2 = L.ih2;
-  fill(i0 - 1, 0);
-  fill(i0, 1);
+  load_raw(i0 - 1);
+  store_raw(0);
+  load_raw(i0);
+  store_raw(1);
+  load_raw(i0 + 1);
+  load_own(i0);
   for (unsigned q = 1; q <= kSTChunk; ++q) {
     const unsigned i = i0 + q - 1;
-    fill(i + 1, (q + 1) % 3);
+    store_raw((q + 1) % 3);  // plane i + 1
+    float cx[kOwn], csig[kOwn], ce[kOwn];
+#pragma unroll
+    for (unsigned u = 0; u < kOwn; ++u) { cx[u] = ox[u]; csig[u] = osig[u]; ce[u] = oe[u]; }
+    if (q < kSTChunk) {
+      load_raw(i + 2);
+      load_own(i + 1);
+    }
     __syncthreads();
     const V* pm = ring + ((q + 2) % 3) * plane_vals;  // plane i - 1
     const V* pc = ring + (q % 3) * plane_vals;        // plane i
     const V* pp = ring + ((q + 1) % 3) * plane_vals;  // plane i + 1
-    for (unsigned t = threadIdx.x; t < kSTRows * hN; t += blockDim.x) {
-      const unsigned r = t / hN, k2 = t - r * hN, j = j0 + r;
+#pragma unroll
+    for (unsigned u = 0; u < kOwn; ++u) {
+      const unsigned t = threadIdx.x + u * kSTThreads, r = t / hN, k2 = t - r * hN, j = j0 + r;
       const unsigned par = (i + j + (unsigned)color) & 1u;
-      const unsigned o = own + (((i << lg) | j) << (lg - 1)) + k2;
+      const unsigned o = own + (((i << LG) | j) << (LG - 1)) + k2;
       const unsigned rc = (r + 1) * hN;  // the own row in the staged planes
       const V nb[6] = {pp[rc + k2], pm[rc + k2], pc[rc + hN + k2], pc[rc - hN + k2],
                        pc[rc + ((k2 + par) & (hN - 1))], pc[rc + ((k2 + par - 1) & (hN - 1))]};
-      const float x = L.x[o], sig = L.sig ? L.sig[o] : 0.f;
+      const float x = cx[u], sig = csig[u];
       float F, dF;
       if constexpr (FM == FIELD) {
         const float ex = st_exp(x);
@@ -112,11 +151,11 @@ __global__ void __launch_bounds__(kSTThreads) fofr_smooth_staged(LevelView<float
         const float dsum = fs * 0.5f * (fmaf(ex, sdu, -6.0f * ex) - sex);
         const float inp1 = (float)c.inv_np1, Kx = (float)c.fKx;
         const float em = dexpm1<float>(-x * inp1);
-        const float S = (float)c.K1 * (L.eta[o] - 1.0f) - Kx * em + (float)c.fK3x;
+        const float S = (float)c.K1 * (ce[u] - 1.0f) - Kx * em + (float)c.fK3x;
         F = flux * ih2 - S - sig;
         dF = dsum * ih2 - Kx * inp1 * (em + 1.0f);
       } else {
-        const float B = L.B[o];
+        const float B = ce[u];
         const float w = st_exp(B), mm = w * dexpm1<float>(x), bt = w + mm;
         float sdB = 0.f, sde = 0.f, smn = 0.f, sbn = 0.f, sbt = 0.f;
 #pragma unroll
@@ -142,6 +181,37 @@ __global__ void __launch_bounds__(kSTThreads) fofr_smooth_staged(LevelView<float
     }
     __syncthreads();
   }
+}
+
+// Launch one colour on grids of side 128 .. 1024.
+template <Form FM, bool kResid>
+inline cudaError_t launch_fofr_staged(const LevelView<float>& L, const Coef& c, int color, float* res,
+                                      cudaStream_t st) {
+  const unsigned blocks = (unsigned)((L.N / kSTRows) * (L.N / kSTChunk));
+  const size_t smem = staged_smem_bytes<FM>(L.N);
+  switch (L.lg) {
+    case 7: fofr_smooth_staged<FM, kResid, 7><<<blocks, kSTThreads, smem, st>>>(L, c, color, res); break;
+    case 8: fofr_smooth_staged<FM, kResid, 8><<<blocks, kSTThreads, smem, st>>>(L, c, color, res); break;
+    case 9: fofr_smooth_staged<FM, kResid, 9><<<blocks, kSTThreads, smem, st>>>(L, c, color, res); break;
+    case 10: fofr_smooth_staged<FM, kResid, 10><<<blocks, kSTThreads, smem, st>>>(L, c, color, res); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Allow each instantiation its largest shared memory (called once per device).
+template <Form FM, bool kResid>
+inline cudaError_t allow_fofr_staged_smem() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](auto kern, int lg) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged_smem_bytes<FM>(1 << lg));
+  };
+  set(fofr_smooth_staged<FM, kResid, 7>, 7);
+  set(fofr_smooth_staged<FM, kResid, 8>, 8);
+  set(fofr_smooth_staged<FM, kResid, 9>, 9);
+  set(fofr_smooth_staged<FM, kResid, 10>, 10);
+  return e;
 }
 
 }  // namespace isis

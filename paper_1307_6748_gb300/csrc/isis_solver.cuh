@@ -150,19 +150,15 @@ struct Cycler {
     if constexpr (sizeof(T) == 4 && M == FOFR) {
       if (v.N >= 128) {
         // the other colour's exponentials staged in shared memory (isis_fofr_staged.cuh)
-        const size_t smem = staged_smem_bytes<FM>(v.N);
         static bool attr[64] = {};
         const int dev = ws->device >= 0 && ws->device < 64 ? ws->device : 0;
         if (!attr[dev]) {
-          ISIS_CK(cudaFuncSetAttribute(fofr_smooth_staged<FM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)staged_smem_bytes<FM>(1024)));
+          ISIS_CK((allow_fofr_staged_smem<FM, false>()));
           attr[dev] = true;
         }
-        const unsigned blocks = (unsigned)((v.N / kSTRows) * (v.N / kSTChunk));
         for (int s = 0; s < sweeps; ++s)
           for (int color = 0; color < 2; ++color)
-            ISIS_LAUNCH(kind, bytes * 0.5, st,
-                        (fofr_smooth_staged<FM><<<blocks, kSTThreads, smem, st>>>(v, c, color)));
+            ISIS_LAUNCH(kind, bytes * 0.5, st, (launch_fofr_staged<FM, false>(v, c, color, nullptr, st)));
         return ISIS_OK;
       }
     }
@@ -263,18 +259,14 @@ struct Cycler {
         float* res = (float*)ws->x0[0];
         if (L[0].N >= 128) {
           // two one-colour passes with the other colour's exponentials staged in shared memory
-          const unsigned blocks = (unsigned)((L[0].N / kSTRows) * (L[0].N / kSTChunk));
-          const size_t smem = staged_smem_bytes<FM>(L[0].N);
           static bool attr[64] = {};
           const int dev = ws->device >= 0 && ws->device < 64 ? ws->device : 0;
           if (!attr[dev]) {
-            ISIS_CK(cudaFuncSetAttribute(fofr_smooth_staged<FM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)staged_smem_bytes<FM>(1024)));
+            ISIS_CK((allow_fofr_staged_smem<FM, true>()));
             attr[dev] = true;
           }
           for (int color = 0; color < 2; ++color)
-            ISIS_LAUNCH(tk(KK_RESTRICT_FINE), rbytes * 0.5, st,
-                        (fofr_smooth_staged<FM, true><<<blocks, kSTThreads, smem, st>>>(L[0], c, color, res)));
+            ISIS_LAUNCH(tk(KK_RESTRICT_FINE), rbytes * 0.5, st, (launch_fofr_staged<FM, true>(L[0], c, color, res, st)));
         } else {
           ISIS_LAUNCH(tk(KK_RESTRICT_FINE), rbytes, st,
                       (resid_rb2<M, FM><<<nblk((size_t)nf / 2, 256), 256, 0, st>>>(L[0], c, res)));
@@ -742,11 +734,18 @@ isis_status solve_refine(const SolveArgs& A) {
     A1.coef.fscale = std::exp(u0);
     A1.coef.fKx = c.K2 * std::exp(-u0 * c.inv_np1);
     A1.coef.fK3x = c.K3 - A1.coef.fKx;
-    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st,
-                (to_rb_shift<<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg, ff_split_host(u0))));
-  } else {
-    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (to_rb<double><<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg)));
   }
+  // the FP32 field of phase 1 from the caller's FP64 field (phi64 is not written until the phase ends)
+  auto start_field = [&]() -> isis_status {
+    if (M == FOFR)
+      ISIS_LAUNCH(KK_SETUP, 12.0 * n, st,
+                  (to_rb_shift<<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg, ff_split_host(u0))));
+    else
+      ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (to_rb<double><<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg)));
+    return ISIS_OK;
+  };
+  s = start_field();
+  if (s != ISIS_OK) return s;
   {
     Cycler<M, FIELD, float> cy;
     cy.setup(ws, A1, B0, eta0, nullptr);
@@ -758,12 +757,13 @@ isis_status solve_refine(const SolveArgs& A) {
     loc.res_ref = ref;
     double prev = res;
     double handover = std::fmax(A.tol, kSwitchRel) * ref;
-    bool nested = A.fmg != 0;
+    bool nested = A.fmg != 0, after_nested = false;
     while (res > handover && loc.cycles < A.max_cycles && std::isfinite(res)) {
       if (nested) {
         // the nested-iteration start leaves the residual near 1e-2 of the reference, far above the handover:
         // the next V-cycle follows without a norm in between
         nested = false;
+        after_nested = true;
         s = cy.fmg();
         if (s != ISIS_OK) return s;
         loc.cycles += 1;
@@ -775,6 +775,21 @@ isis_status solve_refine(const SolveArgs& A) {
       loc.cycles += 1;
       if (nh < 128) loc.hist[nh++] = res;
       loc.nhist = nh;
+      if (after_nested) {
+        after_nested = false;
+        if (s != ISIS_OK || !std::isfinite(res) || res > loc.res0) {
+          // The nested start solves each coarse grid's own problem from the restricted density.  Where a coarse
+          // cell is wide against the field's range (6/h^2 below the source's slope), its Newton-Gauss-Seidel
+          // denominator can change sign and the start diverges (the symmetron near symmetry breaking on
+          // strongly clustered densities).  It is only an acceleration: the phase restarts from the caller's
+          // field with plain V-cycles, and the fixed point is unchanged.
+          ISIS_CK(cudaMemsetAsync(ws->iflags, 0, 2 * sizeof(int), st));
+          s = start_field();
+          if (s != ISIS_OK) return s;
+          res = prev = loc.res0;
+          continue;
+        }
+      }
       if (s != ISIS_OK) { if (A.info) *A.info = loc; return s; }
       if (!(res <= kStallRatio * prev)) break;
       prev = res;

@@ -5,6 +5,8 @@ started from the U-Net guess).  The oracle checks what it can compute at this si
 - the CIC density of every cell (the oracle deposits all 512^3 particles, Sect. 5.1);
 - each solve's convergence (Sect. 3.2): the oracle's FP64 RMS residual of the returned field, over its reference
   residual, is at most the tolerance and equals the ratio the library reports;
+- each returned field against the oracle continued from it to a tighter tolerance: relative L2 <= 1e-9 (the
+  accuracy target at this size);
 - the accelerations of both models at a seeded sample of 65 536 particles, from the returned fields
   (Sects. 4.1, 4.2).
 Host memory: about 12 GB at the peak (the oracle's grids at 512^3)."""
@@ -69,6 +71,36 @@ def test_full_size_convergence(step, name):
     agree = 5e-2 if name == "fofr" else 1e-3
     assert r.res0 <= args.tol * r.ref, (name, r.res0 / r.ref)
     assert abs(r.res0 - info.res_final) <= agree * r.res0, (name, r.res0, info.res_final)
+
+
+# The oracle continued from the returned field to well below the library's error: tolerances it reaches at 512^3
+# (its FP64 floors there are about 3e-13 for the symmetron, 3e-12 for Poisson and 3e-11 for f(R), where u = -11.5
+# holds 1e-16 relative and each face flux cancels terms e^u / h^2 times larger than the residual).
+ORACLE_TOL = {"poisson": 1e-11, "symmetron": 1e-12, "fofr": 1e-10}
+
+
+@pytest.mark.parametrize("name", ["poisson", "symmetron", "fofr"])
+def test_full_size_fields_match_converged_oracle(step, name):
+    """The accuracy statement at full size, field by field: the benchmark's 512^3 fields (mixed precision to a
+    residual of 1e-8, the symmetron from the learned guess) against the FP64 oracle continued from them to the
+    tolerances above (a few of its V(2,2) cycles): relative L2 <= 1e-9 on Phi and chi, on delta f_R = f_R - fbar_R
+    for f(R) (and max-abs <= 1e-8 on u)."""
+    import math
+    args, S, _ = step
+    model = {"poisson": oracle.POISSON, "symmetron": oracle.SYMMETRON, "fofr": oracle.FOFR}[name]
+    got = _host({"poisson": S.Phi, "symmetron": S.chi, "fofr": S.u}[name])
+    P = oracle.Problem(model, args.N, args.box, a=S.a, lambda0=S.psym.lambda0, beta=S.psym.beta,
+                       a_ssb=S.psym.a_ssb, n=S.pfr.n, fR0_abs=S.pfr.fR0_abs)
+    r = oracle.solve(P, _host(S.eta), got, tol=ORACLE_TOL[name], max_cycles=30)
+    assert r.status == oracle.OK, (name, r.status, r.res_final / r.ref)
+    if name == "fofr":
+        fbar = -math.exp(oracle.background_field(oracle.FOFR, S.a, n=S.pfr.n, fR0_abs=S.pfr.fR0_abs)) / S.a ** 2
+        dref = -np.exp(r.phi) / S.a ** 2 - fbar
+        rel = np.linalg.norm((np.exp(got) - np.exp(r.phi)) / S.a ** 2) / np.linalg.norm(dref)
+        assert np.abs(got - r.phi).max() <= 1e-8
+    else:
+        rel = np.linalg.norm(got - r.phi) / np.linalg.norm(r.phi)
+    assert rel <= 1e-9, (name, rel)
 
 
 @pytest.mark.parametrize("name", ["symmetron", "fofr"])
