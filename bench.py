@@ -54,8 +54,11 @@ def parse(argv=None):
     ap.add_argument("--no-fp64-ref", action="store_true", help="skip the FP64-solver comparison")
     ap.add_argument("--fmg", type=int, default=1, choices=[0, 1],
                     help="start the FP32 phase of each solve with nested iteration (full multigrid)")
-    ap.add_argument("--guess", default="net", choices=["net", "background"],
-                    help="symmetron initial guess: the trained U-Net, or the background field")
+    ap.add_argument("--guess", default="background", choices=["net", "background"],
+                    help="symmetron initial guess of the timed step: the background field (the faster start on this "
+                         "density, see the learned_guess record) or the trained U-Net")
+    ap.add_argument("--no-guess-record", action="store_true",
+                    help="skip the learned guess's record (net start against background start)")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1307_6748_gb300", "weights", "unet_symmetron.npz"))
     return ap.parse_args(argv)
 
@@ -318,6 +321,49 @@ def copy_rates(h_src, d_dst, h_dst, d_src, stream) -> dict:
     d2h = timed(lambda: h_dst.copy_(d_src, non_blocking=True))
     bo = timed(both)
     return {"h2d": nb / h2d / 1e9, "d2h": nb / d2h / 1e9, "both": 2 * nb / bo / 1e9, "bytes": nb}
+
+
+def learned_guess(args, dev, S, barrier) -> dict:
+    """The step's symmetron solve started from the trained U-Net's guess against the background start, on the
+    step's own density and solver options, outside the timed region (CUDA events, one warm-up of each): the
+    inference time, and the cycles and solve time of each start."""
+    import torch
+
+    from paper_1307_6748_gb300 import isis, unet
+    meta = unet.UNet.meta(args.weights)
+    h, h_net = args.box / args.N, float(meta.get("h", 1.0))
+    pooled = abs(2 * h - h_net) < 1e-9 * h_net
+    if not pooled and abs(h - h_net) > 1e-9 * h_net:
+        return {"skipped": f"the net was trained at {h_net} Mpc/h cells; this grid has {h} Mpc/h"}
+    net = unet.UNet.load(args.weights, device=dev)
+    st = S.stream
+
+    def opts(init):
+        return isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=args.inner_sym, init=init,
+                         n_coarsest=args.ncoarse, fmg=args.fmg, nu1=args.nu1, nu2=args.nu2)
+    rec = {}
+    for rep in range(2):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        barrier()
+        ev[0].record(st)
+        net.guess(S.eta, S.a, S.psym.a_ssb, S.chi, pooled=pooled)
+        ev[1].record(st)
+        i_net = isis.isis_scalar_solve(isis.ISIS_SYMMETRON, S.psym, S.grid, S.a, S.eta, S.chi, tol=S.tol,
+                                       opts=opts(isis.ISIS_INIT_INPUT))
+        ev[2].record(st)
+        barrier()
+        ev[3].record(st)
+        i_bg = isis.isis_scalar_solve(isis.ISIS_SYMMETRON, S.psym, S.grid, S.a, S.eta, S.chi, tol=S.tol,
+                                      opts=opts(isis.ISIS_INIT_BACKGROUND))
+        ev[4].record(st)
+        barrier()
+        rec = {"inference_ms": ev[0].elapsed_time(ev[1]), "net_solve_ms": ev[1].elapsed_time(ev[2]),
+               "net_cycles": i_net.cycles, "background_solve_ms": ev[3].elapsed_time(ev[4]),
+               "background_cycles": i_bg.cycles}
+    rec["net_total_ms"] = rec["inference_ms"] + rec["net_solve_ms"]
+    rec["net_saves_ms"] = rec["background_solve_ms"] - rec["net_total_ms"]
+    rec["cycles_saved"] = rec["background_cycles"] - rec["net_cycles"]
+    return rec
 
 
 # ---------------------------------------------------------------------------
@@ -592,6 +638,10 @@ def main():
             row["speedup_same_cycle"] = row["fp64_ms"] / row["refine64_nofmg_ms"]
             vs_fp64[name] = row
 
+    guess_rec = None
+    if not args.no_guess_record and os.path.exists(args.weights):
+        guess_rec = learned_guess(args, dev, S, barrier)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args)
@@ -607,6 +657,8 @@ def main():
                 "gpu_launches": launches, "clocks": clk.summary()}
         if vs_fp64 is not None:
             line["vs_fp64_solver"] = vs_fp64
+        if guess_rec is not None:
+            line["learned_guess"] = guess_rec
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -85,6 +85,22 @@ Workspace* get_workspace(int N, int esize, int ncoarse) {
   return w;
 }
 
+float* get_xalt(Workspace* w, int l) {
+  if (l < 0 || l >= w->nlev || w->esize != 4) return nullptr;
+  if ((int)w->xalt.size() < w->nlev) w->xalt.resize(w->nlev, nullptr);
+  if (!w->xalt[l]) {
+    const size_t nl = (size_t)(w->N >> l) * (w->N >> l) * (w->N >> l);
+    void* p = nullptr;
+    if (cudaMalloc(&p, nl * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    w->owned.push_back(p);
+    w->xalt[l] = p;
+  }
+  return (float*)w->xalt[l];
+}
+
 bool ensure_fofr64(Workspace* w) {
   if (w->b64) return true;
   size_t n = (size_t)w->N * w->N * w->N;

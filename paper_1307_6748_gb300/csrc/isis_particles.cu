@@ -156,6 +156,97 @@ __global__ void force_grid(const T* __restrict__ Phi, const T* __restrict__ phi,
   fz[t] = g2 * inv2h;
 }
 
+// The same grid force, streamed: a block takes a tile of 8 x 32 cells in (j, k) through 32 planes in i and keeps
+// three planes of both fields (tile plus a one-cell halo) in shared memory as float-float pairs, so each FP64
+// value is split once per block instead of once per stencil that reads it (seven times); the next plane's
+// values are loaded into registers while the current one is differenced.  Same arithmetic as force_grid.
+// N >= 32.
+constexpr int kFGTJ = 8, kFGTK = 32, kFGCh = 32;
+constexpr int kFGHalo = (kFGTJ + 2) * (kFGTK + 2);
+
+template <class T>
+__device__ __forceinline__ float2 split_pair(T a) {
+  if constexpr (sizeof(T) == 8) {
+    const ff v = ff_split_bits((double)a);
+    return make_float2(v.hi, v.lo);
+  } else {
+    return make_float2((float)a, 0.0f);
+  }
+}
+
+template <class T, int MODEL>
+__global__ void __launch_bounds__(kFGTJ * kFGTK) force_grid_st(const T* __restrict__ Phi, const T* __restrict__ phi,
+                                                               int lg, float a2, float Cs, float inv2h,
+                                                               float* __restrict__ fx, float* __restrict__ fy,
+                                                               float* __restrict__ fz) {
+  __shared__ float2 sP[3][kFGHalo], sF[3][kFGHalo];
+  const int N = 1 << lg, m = N - 1, ntk = N / kFGTK, ntj = N / kFGTJ;
+  int b = blockIdx.x;
+  const int k0 = (b % ntk) * kFGTK;
+  b /= ntk;
+  const int j0 = (b % ntj) * kFGTJ;
+  const int i0 = (b / ntj) * kFGCh;
+  const bool hasP = Phi != nullptr;
+  constexpr int kU = (kFGHalo + kFGTJ * kFGTK - 1) / (kFGTJ * kFGTK);
+  T rP[kU], rF[kU];
+  auto load = [&](int p) {
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = threadIdx.x + u * kFGTJ * kFGTK;
+      if (e < kFGHalo) {
+        const int r = e / (kFGTK + 2), col = e - r * (kFGTK + 2);
+        const size_t g = cidx(lg, p & m, (j0 + r - 1) & m, (k0 + col - 1) & m);
+        if (hasP) rP[u] = Phi[g];
+        if (MODEL != 0) rF[u] = phi[g];
+      }
+    }
+  };
+  auto store = [&](int s) {
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = threadIdx.x + u * kFGTJ * kFGTK;
+      if (e < kFGHalo) {
+        if (hasP) sP[s][e] = split_pair<T>(rP[u]);
+        if (MODEL != 0) sF[s][e] = split_pair<T>(rF[u]);
+      }
+    }
+  };
+  auto diff = [](float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); };
+  const int tj = threadIdx.x / kFGTK, tk = threadIdx.x - tj * kFGTK;
+  const int c = (tj + 1) * (kFGTK + 2) + tk + 1;  // this thread's cell in the halo tile
+  constexpr int kRow = kFGTK + 2;
+  load(i0 - 1);
+  store(0);
+  load(i0);
+  store(1);
+  load(i0 + 1);
+  for (int q = 1; q <= kFGCh; ++q) {
+    const int i = i0 + q - 1;
+    store((q + 1) % 3);  // plane i + 1
+    if (q < kFGCh) load(i + 2);
+    __syncthreads();
+    const int sm = (q + 2) % 3, sc = q % 3, sp = (q + 1) % 3;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (hasP) {
+      g0 = a2 * diff(sP[sp][c], sP[sm][c]);
+      g1 = a2 * diff(sP[sc][c + kRow], sP[sc][c - kRow]);
+      g2 = a2 * diff(sP[sc][c + 1], sP[sc][c - 1]);
+    }
+    if (MODEL != 0) {
+      const float v = sF[sc][c].x;
+      const float pref = (MODEL == ISIS_SYMMETRON) ? Cs * a2 * v : Cs * expf(v);
+      g0 = fmaf(pref, diff(sF[sp][c], sF[sm][c]), g0);
+      g1 = fmaf(pref, diff(sF[sc][c + kRow], sF[sc][c - kRow]), g1);
+      g2 = fmaf(pref, diff(sF[sc][c + 1], sF[sc][c - 1]), g2);
+    }
+    const size_t o = cidx(lg, i, j0 + tj, k0 + tk);
+    fx[o] = g0 * inv2h;
+    fy[o] = g1 * inv2h;
+    fz[o] = g2 * inv2h;
+    __syncthreads();
+  }
+}
+
 // FP32 CIC weights of one axis (exact for 1 <= x < N; to FP32 rounding elsewhere).
 __device__ __forceinline__ void cic_axis_f(float x, int N, int& i0, int& i1, float& w0, float& w1) {
   float xs = x - 0.5f;
@@ -352,10 +443,18 @@ isis_status isis_fifth_force(isis_model model, const isis_params* p, const isis_
   float* fz = fg + 2 * n;
   int mcode = phi ? (int)model : 0;
   const double gbytes = (double)n * ((fields_f64 ? 8 : 4) * ((Phi ? 1 : 0) + (phi ? 1 : 0)) + 12);
+  const int Ng = grid->N;
+  const unsigned st_blocks = (unsigned)((Ng / kFGTK) * (Ng / kFGTJ) * (Ng / kFGCh));
 #define ISIS_FGRID(T, MC)                                                                                      \
-  ISIS_LAUNCH(KK_FORCE_GRID, gbytes, st,                                                                       \
-              (force_grid<T, MC><<<nblk(n, 256), 256, 0, st>>>((const T*)Phi, (const T*)phi, lg, (float)a2,    \
-                                                               (float)Cs, (float)inv2h, fx, fy, fz)))
+  if (Ng >= 32)                                                                                                \
+    ISIS_LAUNCH(KK_FORCE_GRID, gbytes, st,                                                                     \
+                (force_grid_st<T, MC><<<st_blocks, kFGTJ * kFGTK, 0, st>>>((const T*)Phi, (const T*)phi, lg,    \
+                                                                          (float)a2, (float)Cs, (float)inv2h,   \
+                                                                          fx, fy, fz)));                        \
+  else                                                                                                         \
+    ISIS_LAUNCH(KK_FORCE_GRID, gbytes, st,                                                                     \
+                (force_grid<T, MC><<<nblk(n, 256), 256, 0, st>>>((const T*)Phi, (const T*)phi, lg, (float)a2,  \
+                                                                 (float)Cs, (float)inv2h, fx, fy, fz)))
   if (fields_f64) {
     if (mcode == 0) ISIS_FGRID(double, 0);
     else if (mcode == ISIS_SYMMETRON) ISIS_FGRID(double, ISIS_SYMMETRON);

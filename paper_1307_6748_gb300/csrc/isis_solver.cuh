@@ -12,7 +12,6 @@
 
 #include "../../include/isis.h"
 #include "isis_coarse.cuh"
-#include "isis_fofr_staged.cuh"
 #include "isis_ff.cuh"
 #include "isis_prof.cuh"
 
@@ -43,8 +42,12 @@ struct Workspace {
   float2* exptab_ff = nullptr;  // 2^(j/64), j < 64, float-float, for exp_ff2
   double* b64 = nullptr;      // finest level, 8 bytes per cell: psi = u - u_bar (float-float), f(R) residual
   double* s64 = nullptr;      // finest level, 8 bytes per cell: e^psi (float-float), f(R) residual
+  std::vector<void*> xalt;    // FP32 levels: a scratch grid of the level's size (lazy), see get_xalt
   std::vector<void*> owned;
 };
+
+// A scratch FP32 grid of level l's size (allocated at first use; nullptr on failure).  Implemented in isis_api.cu.
+float* get_xalt(Workspace* ws, int l);
 
 // FP64 scratch of the f(R) residual on the finest grid (lazily allocated).
 bool ensure_fofr64(Workspace* ws);
@@ -147,21 +150,6 @@ struct Cycler {
     // write x once (a one-colour launch moves half of that)
     double bytes = cells(v) * sizeof(T) * (2 + arrays(v.sig != nullptr));
     const int kind = tk(l == 0 ? KK_SMOOTH_FINE : KK_SMOOTH_COARSE);
-    if constexpr (sizeof(T) == 4 && M == FOFR) {
-      if (v.N >= 128) {
-        // the other colour's exponentials staged in shared memory (isis_fofr_staged.cuh)
-        static bool attr[64] = {};
-        const int dev = ws->device >= 0 && ws->device < 64 ? ws->device : 0;
-        if (!attr[dev]) {
-          ISIS_CK((allow_fofr_staged_smem<FM, false>()));
-          attr[dev] = true;
-        }
-        for (int s = 0; s < sweeps; ++s)
-          for (int color = 0; color < 2; ++color)
-            ISIS_LAUNCH(kind, bytes * 0.5, st, (launch_fofr_staged<FM, false>(v, c, color, nullptr, st)));
-        return ISIS_OK;
-      }
-    }
     for (int s = 0; s < sweeps; ++s)
       for (int color = 0; color < 2; ++color) {
         if constexpr (sizeof(T) == 4) {
@@ -251,29 +239,19 @@ struct Cycler {
     double nf = cells(L[l]), ncd = (double)nc;
     const double rbytes = sizeof(T) * (nf * (1 + arrays(L[l].sig != nullptr)) + 3 * ncd);
     bool split = false;
-    if constexpr (sizeof(T) == 4 && M == FOFR && FM == DELTA) split = (l == 0 && ws->x0[0] != nullptr);
+    if constexpr (sizeof(T) == 4 && M == FOFR) split = L[l].N >= 64;
     if (split) {
-      // f(R) correction form on the finest grid: the stencil of 8 children holds too many
-      // per-cell inputs for one thread, so the residual goes through a scratch grid
+      // f(R) on grids of side >= 64: the stencils of 8 children hold too many per-cell inputs and exponentials
+      // for one thread, so the residual of every cell goes through a scratch grid of the level (the packed pair
+      // evaluation of the smoother), then the restriction reads it
       if constexpr (sizeof(T) == 4) {
-        float* res = (float*)ws->x0[0];
-        if (L[0].N >= 128) {
-          // two one-colour passes with the other colour's exponentials staged in shared memory
-          static bool attr[64] = {};
-          const int dev = ws->device >= 0 && ws->device < 64 ? ws->device : 0;
-          if (!attr[dev]) {
-            ISIS_CK((allow_fofr_staged_smem<FM, true>()));
-            attr[dev] = true;
-          }
-          for (int color = 0; color < 2; ++color)
-            ISIS_LAUNCH(tk(KK_RESTRICT_FINE), rbytes * 0.5, st, (launch_fofr_staged<FM, true>(L[0], c, color, res, st)));
-        } else {
-          ISIS_LAUNCH(tk(KK_RESTRICT_FINE), rbytes, st,
-                      (resid_rb2<M, FM><<<nblk((size_t)nf / 2, 256), 256, 0, st>>>(L[0], c, res)));
-        }
-        ISIS_LAUNCH(tk(KK_RESTRICT_FINE), 0.0, st,
-                    (restrict_xr<M, FM><<<nblk(nc, 256), 256, 0, st>>>(L[0], res, C, (float*)ws->x0[1],
-                                                                        (float*)ws->sig[1])));
+        float* res = l == 0 ? (float*)ws->x0[0] : get_xalt(ws, l);
+        if (!res) return ISIS_ENOMEM;
+        const int kind = tk(l == 0 ? KK_RESTRICT_FINE : KK_RESTRICT_COARSE);
+        ISIS_LAUNCH(kind, rbytes, st, (resid_rb2<M, FM><<<nblk((size_t)nf / 2, 256), 256, 0, st>>>(L[l], c, res)));
+        ISIS_LAUNCH(kind, 0.0, st,
+                    (restrict_xr<M, FM><<<nblk(nc, 256), 256, 0, st>>>(L[l], res, C, (float*)ws->x0[l + 1],
+                                                                        (float*)ws->sig[l + 1])));
       }
     } else {
       bool done = false;

@@ -1,7 +1,7 @@
 """The force step at full size, in the launch configuration the benchmark times (bench.ForceStep with the
 benchmark's default options: 512^3 Zel'dovich particles on a 512^3 grid of a 256 Mpc/h box, FP32 cycles in
-FP64 defect correction to a residual of 1e-8, V(2,1), nested-iteration start, coarsest 2^3, the symmetron
-started from the U-Net guess).  The oracle checks what it can compute at this size:
+FP64 defect correction to a residual of 1e-8, V(2,1), nested-iteration start, coarsest 2^3, every solve
+started from its background field).  The oracle checks what it can compute at this size:
 - the CIC density of every cell (the oracle deposits all 512^3 particles, Sect. 5.1);
 - each solve's convergence (Sect. 3.2): the oracle's FP64 RMS residual of the returned field, over its reference
   residual, is at most the tolerance and equals the ratio the library reports;
@@ -82,7 +82,7 @@ ORACLE_TOL = {"poisson": 1e-11, "symmetron": 1e-12, "fofr": 1e-10}
 @pytest.mark.parametrize("name", ["poisson", "symmetron", "fofr"])
 def test_full_size_fields_match_converged_oracle(step, name):
     """The accuracy statement at full size, field by field: the benchmark's 512^3 fields (mixed precision to a
-    residual of 1e-8, the symmetron from the learned guess) against the FP64 oracle continued from them to the
+    residual of 1e-8) against the FP64 oracle continued from them to the
     tolerances above (a few of its V(2,2) cycles): relative L2 <= 1e-9 on Phi and chi, on delta f_R = f_R - fbar_R
     for f(R) (and max-abs <= 1e-8 on u)."""
     import math
