@@ -85,6 +85,17 @@ Workspace* get_workspace(int N, int esize, int ncoarse) {
   return w;
 }
 
+__global__ void fill_f32(float* __restrict__ a, size_t n, float v) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) a[t] = v;
+}
+
+isis_status sum_f32(Workspace* ws, const float* v, size_t n, cudaStream_t st) {
+  ISIS_LAUNCH(KK_REDUCE, 4.0 * n, st, (sum_f32_partial<<<kNormBlocks, kNormThreads, 0, st>>>(v, n, ws->part2)));
+  ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part2, kNormBlocks, ws->scal + 1)));
+  return ISIS_OK;
+}
+
 float* get_xalt(Workspace* w, int l) {
   if (l < 0 || l >= w->nlev || w->esize != 4) return nullptr;
   if ((int)w->xalt.size() < w->nlev) w->xalt.resize(w->nlev, nullptr);

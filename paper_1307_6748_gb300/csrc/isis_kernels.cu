@@ -33,11 +33,45 @@ __global__ void publish_scalars(const double* __restrict__ scal, int ns, const i
 }  // namespace isis
 
 namespace isis {
-__global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, int lg) {
+__global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, int lg,
+                             const float* __restrict__ emean) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ((size_t)1 << (3 * lg))) return;
   const int m = (1 << lg) - 1;
-  phi[t] += (double)e[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
+  float v = e[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
+  if (emean) v -= *emean;  // Poisson: the correction's mean removed (in FP32, as e is)
+  phi[t] += (double)v;
+}
+
+__global__ void mean_to_f32(const double* __restrict__ sum, double inv_n, float* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = (float)(*sum * inv_n);
+}
+
+__global__ void __launch_bounds__(kNormThreads) moments_to_rb(const double* __restrict__ v, float* __restrict__ rb,
+                                                              int lg, double* __restrict__ part2,
+                                                              double* __restrict__ part1) {
+  const size_t n = (size_t)1 << (3 * lg);
+  const int m = (1 << lg) - 1;
+  ff s1 = {0.f, 0.f};
+  float s2 = 0.f;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const ff x = ff_split_bits(v[t]);
+    s1 = ff_add(s1, x);
+    const float d = ff_add_f(x, -1.0f).hi;
+    s2 = fmaf(d, d, s2);
+    rb[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))] = x.hi;
+  }
+  block_sum_store<double>((double)s2, part2);
+  __syncthreads();
+  block_sum_store<double>((double)s1.hi + (double)s1.lo, part1);
+}
+
+__global__ void __launch_bounds__(kNormThreads) sum_f32_partial(const float* __restrict__ v, size_t n,
+                                                                double* __restrict__ part) {
+  ff s = {0.f, 0.f};
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    s = ff_add_f(s, v[t]);
+  block_sum_store<double>((double)s.hi + (double)s.lo, part);
 }
 }  // namespace isis
 

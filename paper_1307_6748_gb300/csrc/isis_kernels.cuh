@@ -1035,6 +1035,15 @@ __global__ void __launch_bounds__(kNormThreads) moments_partial(const T* __restr
   block_sum_store<T>(a1, part1);
 }
 
+// moments_partial<double, true> of the density (shift 1) and, in the same pass, its FP32 copy in the
+// red/black layout (the value truncated to 24 bits, as to_rb writes it): the density is read once.
+__global__ void __launch_bounds__(kNormThreads) moments_to_rb(const double* __restrict__ v, float* __restrict__ rb,
+                                                              int lg, double* __restrict__ part2,
+                                                              double* __restrict__ part1);
+// Sum (float-float per thread) of an FP32 array, block partials: the Poisson mean of the FP32 grids.
+__global__ void __launch_bounds__(kNormThreads) sum_f32_partial(const float* __restrict__ v, size_t n,
+                                                                double* __restrict__ part);
+
 // One block sums nparts partials in a fixed order into *out.
 __global__ void reduce_final(const double* __restrict__ part, int nparts, double* __restrict__ out);
 // Scalars and flags for the host, written by a kernel into mapped pinned memory (hd, hi: its device

@@ -239,11 +239,13 @@ struct Cycler {
     double nf = cells(L[l]), ncd = (double)nc;
     const double rbytes = sizeof(T) * (nf * (1 + arrays(L[l].sig != nullptr)) + 3 * ncd);
     bool split = false;
-    if constexpr (sizeof(T) == 4 && M == FOFR) split = L[l].N >= 64;
+    if constexpr (sizeof(T) == 4 && M == FOFR && FM == DELTA) split = L[l].N >= 64;
     if (split) {
-      // f(R) on grids of side >= 64: the stencils of 8 children hold too many per-cell inputs and exponentials
-      // for one thread, so the residual of every cell goes through a scratch grid of the level (the packed pair
-      // evaluation of the smoother), then the restriction reads it
+      // f(R) correction form on grids of side >= 64: the stencils of 8 children hold too many per-cell inputs
+      // and exponentials for one thread, so the residual of every cell goes through a scratch grid of the level
+      // (the packed pair evaluation of the smoother), then the restriction reads it (measured at 512^3: 0.7
+      // against 2.9 ms per force step on the coarse grids; the field form keeps the one-pass kernel, faster for
+      // it)
       if constexpr (sizeof(T) == 4) {
         float* res = l == 0 ? (float*)ws->x0[0] : get_xalt(ws, l);
         if (!res) return ISIS_ENOMEM;
@@ -415,7 +417,28 @@ __global__ void exp_k(const T* __restrict__ a, T* __restrict__ b, size_t n) {
 }
 
 
-__global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, int lg);
+// phi += e (e in the red/black FP32 layout); with emean, e minus its mean *emean (the Poisson gauge).
+__global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, int lg,
+                             const float* __restrict__ emean);
+// *out = (float)(*sum * inv_n), one thread: the FP32 mean for update_phi64 (its threads then run no FP64
+// arithmetic for it).
+__global__ void mean_to_f32(const double* __restrict__ sum, double inv_n, float* __restrict__ out);
+
+// The FP32 value to_rb writes for an FP64 value (the significand cut to 24 bits, as ff_split_bits' high part;
+// normal values).
+inline float f32_cut(double d) {
+  unsigned long long b;
+  std::memcpy(&b, &d, sizeof b);
+  b &= ~((1ull << 29) - 1ull);
+  double t;
+  std::memcpy(&t, &b, sizeof t);
+  return (float)t;  // exact: 24 significant bits
+}
+
+__global__ void fill_f32(float* __restrict__ a, size_t n, float v);
+
+// Sum of an FP32 array on the device, left in ws->scal[1] (no host sync).
+isis_status sum_f32(Workspace* ws, const float* v, size_t n, cudaStream_t st);
 
 // Initial guess (isis_init): the background constant, or cell by cell the
 // solution for a uniform density equal to the cell's eta (computed in FP32:
@@ -675,9 +698,23 @@ isis_status solve_refine(const SolveArgs& A) {
   float* eta0 = (float*)ws->eta[0];
   float* B0 = (float*)ws->B[0];
 
+  const int lg = ilog2(A.N);
   double s2, s1;
-  isis_status s = moments<double, true>(ws, eta64, n, 1.0, st, &s2, &s1);
-  if (s != ISIS_OK) return s;
+  // the density's moments and its FP32 red/black copy in one pass
+  {
+    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st,
+                (moments_to_rb<<<kNormBlocks, kNormThreads, 0, st>>>(eta64, eta0, lg, ws->part, ws->part2)));
+    ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
+    ISIS_LAUNCH(KK_REDUCE, 0.0, st,
+                (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part2, kNormBlocks, ws->scal + 1)));
+    ISIS_LAUNCH(KK_REDUCE, 0.0, st,
+                (publish_scalars<<<1, 32, 0, st>>>(ws->scal, 2, ws->iflags, 0, ws->host_dev,
+                                                   (int*)(ws->host_dev + 4))));
+    ISIS_CK(cudaStreamSynchronize(st));
+    s2 = ((double*)ws->host)[0];
+    s1 = ((double*)ws->host)[1];
+  }
+  isis_status s = ISIS_OK;
   double eta_mean = s1 / (double)n;
   if (M == POI) {
     c.eta_mean = eta_mean;
@@ -685,11 +722,12 @@ isis_status solve_refine(const SolveArgs& A) {
     if (s2 < 0) s2 = 0;
   }
   double ref = A.ref_scale * std::sqrt(s2 / (double)n);
-  s = apply_init<M, double>(A, c, phi64, eta64, n);
-  if (s != ISIS_OK) return s;
-
-  const int lg = ilog2(A.N);
-  ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (to_rb<double><<<nblk(n, 256), 256, 0, st>>>(eta64, eta0, lg)));
+  // a background start is written straight into the FP32 field of phase 1 (phi64 is written when it ends)
+  const bool bg_start = A.init == ISIS_INIT_BACKGROUND;
+  if (!bg_start) {
+    s = apply_init<M, double>(A, c, phi64, eta64, n);
+    if (s != ISIS_OK) return s;
+  }
   for (int l = 1; l < ws->nlev; ++l) {
     int lgc = ilog2(A.N >> l);
     size_t ncl = (size_t)1 << (3 * lgc);
@@ -715,6 +753,12 @@ isis_status solve_refine(const SolveArgs& A) {
   }
   // the FP32 field of phase 1 from the caller's FP64 field (phi64 is not written until the phase ends)
   auto start_field = [&]() -> isis_status {
+    if (bg_start) {
+      // f(R) and Poisson start at psi = 0 (u = u_bar, Phi = 0); the symmetron at fp32(chi_bg)
+      const float v = M == SYM ? f32_cut(background_value<SYM>(c)) : 0.0f;
+      ISIS_LAUNCH(KK_INIT, 4.0 * n, st, (fill_f32<<<nblk(n, 256), 256, 0, st>>>(B0, n, v)));
+      return ISIS_OK;
+    }
     if (M == FOFR)
       ISIS_LAUNCH(KK_SETUP, 12.0 * n, st,
                   (to_rb_shift<<<nblk(n, 256), 256, 0, st>>>(phi64, B0, lg, ff_split_host(u0))));
@@ -778,11 +822,20 @@ isis_status solve_refine(const SolveArgs& A) {
       return ISIS_ENAN;
     }
     const float* psi = cy.L[0].x;
-    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (from_rb_shift<<<nblk(n, 256), 256, 0, st>>>(psi, phi64, lg, u0)));
-    // Poisson gauge: the residual does not see the mean, so it is removed once per phase
+    // Poisson gauge: the residual does not see the mean, so it is removed once per phase; here from the FP32
+    // field's mean, in the conversion to FP64
     if (M == POI) {
-      s = remove_mean<double, true>(ws, phi64, n, st);
+      s = sum_f32(ws, psi, n, st);
       if (s != ISIS_OK) return s;
+      // read through the mapped readback area, as the norms are (no copy engine)
+      ISIS_LAUNCH(KK_REDUCE, 0.0, st,
+                  (publish_scalars<<<1, 32, 0, st>>>(ws->scal, 2, ws->iflags, 0, ws->host_dev,
+                                                     (int*)(ws->host_dev + 4))));
+      ISIS_CK(cudaStreamSynchronize(st));
+      const double mean = ((double*)ws->host)[1] / (double)n;
+      ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (from_rb_shift<<<nblk(n, 256), 256, 0, st>>>(psi, phi64, lg, -mean)));
+    } else {
+      ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (from_rb_shift<<<nblk(n, 256), 256, 0, st>>>(psi, phi64, lg, u0)));
     }
   }
 
@@ -886,11 +939,15 @@ isis_status solve_refine(const SolveArgs& A) {
     }
     loc.cycles += k;
     const float* ecur = cy.L[0].x;
-    ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_phi64<<<nblk(n, 256), 256, 0, st>>>(phi64, ecur, lg)));
-  }
-  if (M == POI) {
-    s = remove_mean<double, true>(ws, phi64, n, st);
-    if (s != ISIS_OK) return s;
+    const float* emean = nullptr;
+    if (M == POI) {  // the gauge: each correction enters with its mean removed
+      s = sum_f32(ws, ecur, n, st);
+      if (s != ISIS_OK) return s;
+      float* mf = reinterpret_cast<float*>(ws->scal + 2);
+      ISIS_LAUNCH(KK_REDUCE, 0.0, st, (mean_to_f32<<<1, 32, 0, st>>>(ws->scal + 1, 1.0 / (double)n, mf)));
+      emean = mf;
+    }
+    ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_phi64<<<nblk(n, 256), 256, 0, st>>>(phi64, ecur, lg, emean)));
   }
   if (A.info) *A.info = loc;
   return out;
