@@ -27,9 +27,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "symmetron/f(R) 512³ FAS solve time to residual 1e-8; smoother HBM GB/s"
-# The arithmetic of the step: FP32 V-cycles; the fine-grid residual of the defect correction in float-float
-# (pairs of FP32 numbers, about 48 significant bits; FP32 instructions); the solution accumulated in FP64.
-DTYPE = "f32 (V-cycles) + float-float ~48-bit (outer residual) + f64 (accumulation, coarsest Newton)"
+# The arithmetic of the step: FP32 V-cycles; the fine-grid residual of the defect correction and the field it
+# carries in float-float (pairs of FP32 numbers, about 48 significant bits; FP32 instructions); the coarsest
+# Newton solves and the returned fields in FP64.
+DTYPE = "f32 (V-cycles) + float-float ~48-bit (outer residual, carried field) + f64 (coarsest Newton, returned field)"
 L2_BYTES = 129 * 2 ** 20
 
 

@@ -60,11 +60,13 @@ typedef enum { ISIS_SYMMETRON = 1, ISIS_FOFR_HS = 2, ISIS_CHAMELEON = 3 } isis_m
  *                      (coarsest dense Newton in FP64).
  *   ISIS_F32_REFINE64  eta, phi are double.  First FP32 FAS V-cycles on the
  *                      field itself until its residual is below 2e-4 of the
- *                      reference (or stops falling); then FP64 defect
- *                      correction: the residual r = -L(phi) and the update
- *                      phi += e are FP64, and e solves L(phi + e) - L(phi) = r
- *                      by FP32 FAS V-cycles on the correction (inner_cycles per
- *                      outer iteration; coarsest dense Newton in FP64). */
+ *                      reference (or stops falling); then defect correction to
+ *                      FP64 accuracy: the residual r = -L(phi) and the update
+ *                      phi += e in float-float (two floats per value, about 48
+ *                      significant bits, the field carried in that form), and e
+ *                      solves L(phi + e) - L(phi) = r by FP32 FAS V-cycles on the
+ *                      correction (inner_cycles per outer iteration; coarsest
+ *                      dense Newton in FP64).  phi is written in FP64 on return. */
 typedef enum { ISIS_F64 = 0, ISIS_F32 = 1, ISIS_F32_REFINE64 = 2 } isis_precision;
 
 typedef struct {

@@ -33,14 +33,52 @@ __global__ void publish_scalars(const double* __restrict__ scal, int ns, const i
 }  // namespace isis
 
 namespace isis {
-__global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, int lg,
-                             const float* __restrict__ emean) {
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+
+__global__ void rb_to_ff(const float* __restrict__ psi, float2* __restrict__ pff, int lg, float2 shift) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ((size_t)1 << (3 * lg))) return;
+  const int m = (1 << lg) - 1;
+  const float v = psi[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
+  pff[t] = ff_store(ff_add_f(ff_load(shift), v));
+}
+
+__global__ void update_ff(float2* __restrict__ pff, const float* __restrict__ e, int lg,
+                          const float* __restrict__ emean) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ((size_t)1 << (3 * lg))) return;
   const int m = (1 << lg) - 1;
   float v = e[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
   if (emean) v -= *emean;  // Poisson: the correction's mean removed (in FP32, as e is)
-  phi[t] += (double)v;
+  pff[t] = ff_store(ff_add_f(ff_load(pff[t]), v));
+}
+
+__global__ void ff_to_f64(const float2* __restrict__ pff, double* __restrict__ phi, size_t n, double base) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const float2 v = pff[t];
+  const double d = f2d_bits(v.x) + f2d_bits(v.y);  // the float-float value (one rounding at most)
+  phi[t] = base != 0.0 ? base + d : d;
+}
+
+__global__ void fofr_exp_ff(const float2* __restrict__ psi, float2* __restrict__ E, size_t n,
+                            const float2* __restrict__ tab, FFExp ek) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * t >= n) return;
+  const float4 pv = reinterpret_cast<const float4*>(psi)[t];
+  const ff2 p = ff2{make_float2(pv.x, pv.z), make_float2(pv.y, pv.w)};
+  // exp_ff2 covers |psi| < 22; beyond (no physical field gets there) the FP64 library exp
+  ff2 e = exp_ff2(p, tab, ek);
+  if (!(fabsf(p.hi.x) < 20.0f)) {
+    const ff v = ff_from_double(exp((double)p.hi.x + (double)p.lo.x));
+    e.hi.x = v.hi;
+    e.lo.x = v.lo;
+  }
+  if (!(fabsf(p.hi.y) < 20.0f)) {
+    const ff v = ff_from_double(exp((double)p.hi.y + (double)p.lo.y));
+    e.hi.y = v.hi;
+    e.lo.y = v.lo;
+  }
+  reinterpret_cast<float4*>(E)[t] = make_float4(e.hi.x, e.lo.x, e.hi.y, e.lo.y);
 }
 
 __global__ void mean_to_f32(const double* __restrict__ sum, double inv_n, float* __restrict__ out) {
@@ -120,29 +158,6 @@ __global__ void selftest_exp_ff(const double* __restrict__ x, double* __restrict
   const ff2 v = exp_ff2(ff2_pack(ff_from_double(x[2 * t]), ff_from_double(x[two ? 2 * t + 1 : 2 * t])), tab, ek);
   y[2 * t] = (double)v.hi.x + (double)v.lo.x;
   if (two) y[2 * t + 1] = (double)v.hi.y + (double)v.lo.y;
-}
-
-// Two cells per thread (n even): psi = u - ub and e^psi as packed float-float pairs, 16-byte stores.
-__global__ void fofr_prep_ff(const double* __restrict__ u, float2* __restrict__ psi, float2* __restrict__ E,
-                             size_t n, float2 ubff, const float2* __restrict__ tab, FFExp ek) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (2 * t >= n) return;
-  const size_t q = 2 * t;
-  const ff2 p = ff2_sub(ff2_pack(ff_split_bits(u[q]), ff_split_bits(u[q + 1])), ff2_bc(ubff));
-  reinterpret_cast<float4*>(psi)[t] = make_float4(p.hi.x, p.lo.x, p.hi.y, p.lo.y);
-  // exp_ff2 covers |psi| < 22; beyond (no physical field gets there) the FP64 library exp
-  ff2 e = exp_ff2(p, tab, ek);
-  if (!(fabsf(p.hi.x) < 20.0f)) {
-    const ff v = ff_from_double(exp((double)p.hi.x + (double)p.lo.x));
-    e.hi.x = v.hi;
-    e.lo.x = v.lo;
-  }
-  if (!(fabsf(p.hi.y) < 20.0f)) {
-    const ff v = ff_from_double(exp((double)p.hi.y + (double)p.lo.y));
-    e.hi.y = v.hi;
-    e.lo.y = v.lo;
-  }
-  reinterpret_cast<float4*>(E)[t] = make_float4(e.hi.x, e.lo.x, e.hi.y, e.lo.y);
 }
 
 // The pair (k, k+1) of a float-float grid starting at cell q (q even): one 16-byte load.

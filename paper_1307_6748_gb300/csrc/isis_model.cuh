@@ -179,15 +179,18 @@ __device__ __forceinline__ T aux_of(T x, T w) {
 }
 
 // Off-diagonal Jacobian entry dF_c/dx_nb for neighbour direction d (used by
-// the dense coarsest-level Newton solve).
+// the dense coarsest-level Newton solve).  f(R): b = e^u of the cell and of its
+// neighbour from the cell's cached exponentials (q.a, q.an: e^x in the field
+// form, with b = fscale e^x; e^B expm1(e) in the correction form, with
+// b = e^B + e^B expm1(e) = e^{B+e}), which the caller has filled.
 template <Model M, Form FM>
 __device__ __forceinline__ double eval_offdiag(const Coef& c, double ih2, const Cell<double>& q, int d) {
   (void)c;
   if constexpr (M == FOFR) {
     double u = (FM == FIELD) ? q.x : q.B + q.x;
     double un = (FM == FIELD) ? q.xn[d] : q.Bn[d] + q.xn[d];
-    const double sc = (FM == FIELD) ? c.fscale : 1.0;  // the field form's shifted variable
-    double bu = sc * exp(u), bn = sc * exp(un);
+    const double bu = (FM == FIELD) ? c.fscale * q.a : q.w + q.a;
+    const double bn = (FM == FIELD) ? c.fscale * q.an[d] : q.wn[d] + q.an[d];
     return (0.5 * (bu + bn) + 0.5 * bn * (un - u)) * ih2;
   } else {
     return ih2;

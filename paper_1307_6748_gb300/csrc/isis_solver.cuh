@@ -417,13 +417,6 @@ __global__ void exp_k(const T* __restrict__ a, T* __restrict__ b, size_t n) {
 }
 
 
-// phi += e (e in the red/black FP32 layout); with emean, e minus its mean *emean (the Poisson gauge).
-__global__ void update_phi64(double* __restrict__ phi, const float* __restrict__ e, int lg,
-                             const float* __restrict__ emean);
-// *out = (float)(*sum * inv_n), one thread: the FP32 mean for update_phi64 (its threads then run no FP64
-// arithmetic for it).
-__global__ void mean_to_f32(const double* __restrict__ sum, double inv_n, float* __restrict__ out);
-
 // The FP32 value to_rb writes for an FP64 value (the significand cut to 24 bits, as ff_split_bits' high part;
 // normal values).
 inline float f32_cut(double d) {
@@ -436,6 +429,21 @@ inline float f32_cut(double d) {
 }
 
 __global__ void fill_f32(float* __restrict__ a, size_t n, float v);
+
+// The field of the defect-correction loop, carried in float-float (row-major, 8 bytes per cell):
+//   rb_to_ff   pff = shift + psi, psi the FP32 red/black field of the first phase (one exact float-float add);
+//   update_ff  pff += e (minus its mean *emean for Poisson), FP32 instructions only;
+//   ff_to_f64  phi = base + (hi + lo), the FP64 field returned to the caller.
+__global__ void rb_to_ff(const float* __restrict__ psi, float2* __restrict__ pff, int lg, float2 shift);
+__global__ void update_ff(float2* __restrict__ pff, const float* __restrict__ e, int lg,
+                          const float* __restrict__ emean);
+__global__ void ff_to_f64(const float2* __restrict__ pff, double* __restrict__ phi, size_t n, double base);
+// f(R): e^psi (float-float) of the carried psi = u - u_bar, two cells per thread (n even)
+__global__ void fofr_exp_ff(const float2* __restrict__ psi, float2* __restrict__ E, size_t n,
+                            const float2* __restrict__ tab, FFExp ek);
+// *out = (float)(*sum * inv_n), one thread: the FP32 mean for the update (its threads then run no FP64
+// arithmetic for it).
+__global__ void mean_to_f32(const double* __restrict__ sum, double inv_n, float* __restrict__ out);
 
 // Sum of an FP32 array on the device, left in ws->scal[1] (no host sync).
 isis_status sum_f32(Workspace* ws, const float* v, size_t n, cudaStream_t st);
@@ -485,10 +493,6 @@ struct ResFF {
   float2 K;            // Poisson: 1.5 Omega_m H0^2 / a; symmetron: A = a^2 / (2 lambda0^2)
   float2 s, eta_mean;  // symmetron: (a_SSB/a)^3; Poisson: mean density (float-float)
 };
-static __global__ void phi_to_ff(const double* __restrict__ phi, float2* __restrict__ out, size_t n) {
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) out[t] = ff_store(ff_split_bits(phi[t]));
-}
 // r = -L(phi) in float-float from phi's float-float copy pff; B = the copy's high part (fp32 phi).
 // Two cells per thread, (k, k+1) with k even, as the lanes of packed FP32x2 float-float arithmetic (ff2):
 // the pair's own values and its i and j neighbours are 16-byte loads, the k neighbours outside the pair two
@@ -553,9 +557,6 @@ struct FofrFF {
 };
 __global__ void selftest_exp_ff(const double* __restrict__ x, double* __restrict__ y, int n,
                                 const float2* __restrict__ tab, FFExp ek);
-// first pass: psi = u - ub and e^psi per cell (float-float, 8 bytes each), two cells per thread (n even)
-__global__ void fofr_prep_ff(const double* __restrict__ u, float2* __restrict__ psi, float2* __restrict__ E,
-                             size_t n, float2 ubff, const float2* __restrict__ tab, FFExp ek);
 // second pass: r = -L(u) (written FP32, red/black), B = fp32(u), block partials of r^2
 __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, FofrFF c,
                                                                        const double* __restrict__ eta,
@@ -722,7 +723,8 @@ isis_status solve_refine(const SolveArgs& A) {
     if (s2 < 0) s2 = 0;
   }
   double ref = A.ref_scale * std::sqrt(s2 / (double)n);
-  // a background start is written straight into the FP32 field of phase 1 (phi64 is written when it ends)
+  // a background start is written straight into the FP32 field of phase 1 (phi64 is written when the solve
+  // ends)
   const bool bg_start = A.init == ISIS_INIT_BACKGROUND;
   if (!bg_start) {
     s = apply_init<M, double>(A, c, phi64, eta64, n);
@@ -751,7 +753,7 @@ isis_status solve_refine(const SolveArgs& A) {
     A1.coef.fKx = c.K2 * std::exp(-u0 * c.inv_np1);
     A1.coef.fK3x = c.K3 - A1.coef.fKx;
   }
-  // the FP32 field of phase 1 from the caller's FP64 field (phi64 is not written until the phase ends)
+  // the FP32 field of phase 1 from the caller's FP64 field (phi64 is not written until the solve ends)
   auto start_field = [&]() -> isis_status {
     if (bg_start) {
       // f(R) and Poisson start at psi = 0 (u = u_bar, Phi = 0); the symmetron at fp32(chi_bg)
@@ -812,7 +814,13 @@ isis_status solve_refine(const SolveArgs& A) {
           continue;
         }
       }
-      if (s != ISIS_OK) { if (A.info) *A.info = loc; return s; }
+      if (s != ISIS_OK) {
+        // the last iterate to the caller (from the FP32 field of this phase)
+        ISIS_LAUNCH(KK_SETUP, 12.0 * n, st,
+                    (from_rb_shift<<<nblk(n, 256), 256, 0, st>>>(cy.L[0].x, phi64, lg, u0)));
+        if (A.info) *A.info = loc;
+        return s;
+      }
       if (!(res <= kStallRatio * prev)) break;
       prev = res;
     }
@@ -822,8 +830,10 @@ isis_status solve_refine(const SolveArgs& A) {
       return ISIS_ENAN;
     }
     const float* psi = cy.L[0].x;
-    // Poisson gauge: the residual does not see the mean, so it is removed once per phase; here from the FP32
-    // field's mean, in the conversion to FP64
+    // The field of phase 2 is carried in float-float (ws->b64): phi for Poisson and the symmetron, psi = u - u_bar
+    // for f(R).  Poisson gauge: the residual does not see the mean, so it is removed once per phase; here from
+    // the FP32 field's mean, in the conversion.
+    float2 shift = make_float2(0.f, 0.f);
     if (M == POI) {
       s = sum_f32(ws, psi, n, st);
       if (s != ISIS_OK) return s;
@@ -832,11 +842,10 @@ isis_status solve_refine(const SolveArgs& A) {
                   (publish_scalars<<<1, 32, 0, st>>>(ws->scal, 2, ws->iflags, 0, ws->host_dev,
                                                      (int*)(ws->host_dev + 4))));
       ISIS_CK(cudaStreamSynchronize(st));
-      const double mean = ((double*)ws->host)[1] / (double)n;
-      ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (from_rb_shift<<<nblk(n, 256), 256, 0, st>>>(psi, phi64, lg, -mean)));
-    } else {
-      ISIS_LAUNCH(KK_SETUP, 12.0 * n, st, (from_rb_shift<<<nblk(n, 256), 256, 0, st>>>(psi, phi64, lg, u0)));
+      shift = ff_split_host(-((double*)ws->host)[1] / (double)n);
     }
+    ISIS_LAUNCH(KK_SETUP, 12.0 * n, st,
+                (rb_to_ff<<<nblk(n, 256), 256, 0, st>>>(psi, reinterpret_cast<float2*>(ws->b64), lg, shift)));
   }
 
   // ---- phase 2: FP64 defect correction around FP32 correction cycles ----
@@ -879,22 +888,19 @@ isis_status solve_refine(const SolveArgs& A) {
   double prev_res = 0.0;
   int prev_k = 0;
   for (int outer = 0;; ++outer) {
-    // r = -L64(phi64), B = fp32(phi64), RMS of r
+    // r = -L(phi) to FP64 accuracy from the carried float-float field, B = its FP32 value, RMS of r
+    float2* carry = reinterpret_cast<float2*>(ws->b64);
     if (M == FOFR) {
-      float2* psi_ff = reinterpret_cast<float2*>(ws->b64);
       float2* E_ff = reinterpret_cast<float2*>(ws->s64);
-      ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), 24.0 * n, st,
-                  (fofr_prep_ff<<<nblk(n / 2, 256), 256, 0, st>>>(phi64, psi_ff, E_ff, n, ffc.ubff, ws->exptab_ff,
-                                                               ffc.ek)));
+      ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), 16.0 * n, st,
+                  (fofr_exp_ff<<<nblk(n / 2, 256), 256, 0, st>>>(carry, E_ff, n, ws->exptab_ff, ffc.ek)));
       ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), 32.0 * n, st,
-                  (outer_residual_fofr_ff<<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, ffc, eta64, psi_ff, E_ff,
+                  (outer_residual_fofr_ff<<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, ffc, eta64, carry, E_ff,
                                                                                  ws->exptab_ff, r0, B0, ws->part)));
     } else {
-      float2* pff = reinterpret_cast<float2*>(ws->b64);
-      ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), 16.0 * n, st, (phi_to_ff<<<nblk(n, 256), 256, 0, st>>>(phi64, pff, n)));
       // phi_ff and eta read, r and B written: 24 bytes per cell
       ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), 24.0 * n, st,
-                  (outer_residual_ff<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, rff, eta64, pff, r0, B0,
+                  (outer_residual_ff<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, rff, eta64, carry, r0, B0,
                                                                               ws->part)));
     }
     ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
@@ -947,8 +953,12 @@ isis_status solve_refine(const SolveArgs& A) {
       ISIS_LAUNCH(KK_REDUCE, 0.0, st, (mean_to_f32<<<1, 32, 0, st>>>(ws->scal + 1, 1.0 / (double)n, mf)));
       emean = mf;
     }
-    ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_phi64<<<nblk(n, 256), 256, 0, st>>>(phi64, ecur, lg, emean)));
+    ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_ff<<<nblk(n, 256), 256, 0, st>>>(carry, ecur, lg, emean)));
   }
+  // the carried field to the caller: phi = hi + lo (f(R): u = u_bar + psi), in FP64
+  ISIS_LAUNCH(KK_UPDATE, 16.0 * n, st,
+              (ff_to_f64<<<nblk(n, 256), 256, 0, st>>>(reinterpret_cast<const float2*>(ws->b64), phi64, n,
+                                                       M == FOFR ? u0 : 0.0)));
   if (A.info) *A.info = loc;
   return out;
 }

@@ -29,3 +29,7 @@ def test_profile_commands_name_committed_code():
         for names in re.findall(r"from paper_1307_6748_gb300 import ([a-z_, ]+)", text):
             for n in (x.strip() for x in names.split(",")):
                 assert os.path.exists(os.path.join(ROOT, "paper_1307_6748_gb300", n + ".py")), (f, n)
+        # the package attributes a command calls exist (isis.X, synth.X)
+        from paper_1307_6748_gb300 import isis, synth
+        for mod, name in re.findall(r"\b(isis|synth)\.([A-Za-z_][A-Za-z0-9_]*)", text):
+            assert hasattr({"isis": isis, "synth": synth}[mod], name), (f, mod, name)
