@@ -411,14 +411,30 @@ __device__ __forceinline__ float2 expm1_2(float2 v) {
   if (mx <= 0.5f) return expm1_2d<9>(v);
   return expm1_2d<0>(v);
 }
+// The largest of a non-negative float over the warp's lanes in `lanes` (non-negative floats order as their bits).
+__device__ __forceinline__ float warp_max_nonneg(unsigned lanes, float v) {
+  return __uint_as_float(__reduce_max_sync(lanes, __float_as_uint(v)));
+}
+// expm1_2 with the low degree taken only when every lane of the warp allows it: the threads of a warp then
+// run one series rather than both in turn.  Degree 9 holds its bound for every |v| <= 1/2, the small ones
+// included, so only lanes with |v| > 1/2 (rare) leave it for expf.
+__device__ __forceinline__ float2 expm1_2w(unsigned lanes, float2 v) {
+  const float mx = fmaxf(fabsf(v.x), fabsf(v.y));
+  if (warp_max_nonneg(lanes, mx) <= 0.0078125f) return expm1_2d<4>(v);
+  if (mx <= 0.5f) return expm1_2d<9>(v);
+  return expm1_2d<0>(v);
+}
 
 // The correction-form flux sums of both cells with every e^e - 1 of one degree.  The face terms
 // (1/2)(m + m_nb) dB + (1/2)(bt + bt_nb) de and (1/2) bt (dB + de) - (bt + bt_nb)/2 are summed through the
 // five neighbour sums of dB, de, m_nb dB, bt_nb de and bt_nb, each term of which is of the size of the
 // correction (no large terms cancel), at fewer operations per neighbour.
+// em = e^{-e/(n+1)} - 1 of both cells comes with it, of the same degree (|e|/(n+1) <= |e|); the expf form
+// (DEG 0) picks its own degree per lane.
 template <int DEG>
 __device__ __forceinline__ void fofr_delta_flux2(const Cell<float>& q0, const Cell<float>& q1, float2 x, float2 B,
-                                                 float2& m, float2& flux, float2& dsum) {
+                                                 float2 xm, float2& m, float2& flux, float2& dsum, float2& em) {
+  em = DEG == 0 ? expm1_2(xm) : expm1_2d<DEG>(xm);
   const float2 w = exp_2(B);
   m = mul2(w, expm1_2d<DEG>(x));
   const float2 bt = add2(w, m);
@@ -445,8 +461,9 @@ __device__ __forceinline__ void fofr_delta_flux2(const Cell<float>& q0, const Ce
 
 // F = L(x) - Sigma and dF = dL/dx of both cells (the f(R) operators of fofr_field_eval and fofr_delta_eval),
 // from cells gathered without their exponentials.
+// `lanes`: the warp's lanes that evaluate a pair here (the series degree is chosen per warp).
 template <Form FM>
-__device__ __forceinline__ void fofr_pair_eval(const Coef& c, float ih2, const Cell<float>& q0,
+__device__ __forceinline__ void fofr_pair_eval(const Coef& c, float ih2, unsigned lanes, const Cell<float>& q0,
                                                const Cell<float>& q1, float2& F, float2& dF) {
   const float2 half = bc(0.5f);
   const float2 x = pk(q0.x, q1.x), sig = pk(q0.sig, q1.sig);
@@ -457,12 +474,13 @@ __device__ __forceinline__ void fofr_pair_eval(const Coef& c, float ih2, const C
     float mx = fmaxf(fabsf(x.x), fabsf(x.y));
 #pragma unroll
     for (int d = 0; d < 6; ++d) mx = fmaxf(mx, fmaxf(fabsf(q0.xn[d]), fabsf(q1.xn[d])));
-    float2 m;
-    if (mx <= 0.0078125f) fofr_delta_flux2<4>(q0, q1, x, B, m, flux, dsum);
-    else if (mx <= 0.5f) fofr_delta_flux2<9>(q0, q1, x, B, m, flux, dsum);
-    else fofr_delta_flux2<0>(q0, q1, x, B, m, flux, dsum);
-    const float2 minv = bc(-(float)c.inv_np1);
-    const float2 exB = exp_2(mul2(B, minv)), em = expm1_2(mul2(x, minv));
+    // one degree for the whole warp unless a lane needs expf (|e| > 1/2): then degree 9 or expf per lane
+    const float2 minv = bc(-(float)c.inv_np1), xm = mul2(x, minv);
+    float2 m, em;
+    if (warp_max_nonneg(lanes, mx) <= 0.0078125f) fofr_delta_flux2<4>(q0, q1, x, B, xm, m, flux, dsum, em);
+    else if (mx <= 0.5f) fofr_delta_flux2<9>(q0, q1, x, B, xm, m, flux, dsum, em);
+    else fofr_delta_flux2<0>(q0, q1, x, B, xm, m, flux, dsum, em);
+    const float2 exB = exp_2(mul2(B, minv));
     const float2 K2 = bc((float)c.K2);
     F = sub2(fma2(flux, bc(ih2), mul2(K2, mul2(exB, em))), sig);
     dF = sub2(mul2(dsum, bc(ih2)), mul2(mul2(K2, bc((float)c.inv_np1)), mul2(exB, add2(em, bc(1.0f)))));
@@ -484,7 +502,7 @@ __device__ __forceinline__ void fofr_pair_eval(const Coef& c, float ih2, const C
     flux = mul2(flux, fs);
     dsum = mul2(dsum, fs);
     const float2 inp1 = bc((float)c.inv_np1), Kx = bc((float)c.fKx);
-    const float2 em = expm1_2(mul2(x, bc(-(float)c.inv_np1)));
+    const float2 em = expm1_2w(lanes, mul2(x, bc(-(float)c.inv_np1)));
     const float2 S = add2(sub2(mul2(bc((float)c.K1), sub2(pk(q0.eta, q1.eta), bc(1.0f))), mul2(Kx, em)),
                           bc((float)c.fK3x));
     F = sub2(sub2(mul2(flux, bc(ih2)), S), sig);
@@ -493,14 +511,17 @@ __device__ __forceinline__ void fofr_pair_eval(const Coef& c, float ih2, const C
 }
 
 // Gather and evaluate the two cells of an rb2 thread: the packed path for f(R), two eval_cell otherwise.
+// `lanes`: the lanes of the calling warp that are here (all of them call with the same mask).
 template <Model M, Form FM>
 __device__ __forceinline__ unsigned rb2_eval(const LevelView<float>& L, const Coef& c, int color, unsigned t,
-                                             Cell<float>& q0, Cell<float>& q1, float2& F, float2& dF) {
+                                             unsigned lanes, Cell<float>& q0, Cell<float>& q1, float2& F,
+                                             float2& dF) {
   if constexpr (M == FOFR) {
     const unsigned o = rb2_gather<M, FM, false>(L, color, t, q0, q1);
-    fofr_pair_eval<FM>(c, L.ih2, q0, q1, F, dF);
+    fofr_pair_eval<FM>(c, L.ih2, lanes, q0, q1, F, dF);
     return o;
   } else {
+    (void)lanes;
     const unsigned o = rb2_gather<M, FM>(L, color, t, q0, q1);
     eval_cell<M, FM, float>(c, L.ih2, q0, F.x, dF.x);
     eval_cell<M, FM, float>(c, L.ih2, q1, F.y, dF.y);
@@ -511,10 +532,11 @@ __device__ __forceinline__ unsigned rb2_eval(const LevelView<float>& L, const Co
 template <Model M, Form FM>
 __global__ void __launch_bounds__(256) smooth_rb2(LevelView<float> L, Coef c, int color) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lanes = __ballot_sync(0xffffffffu, t < (1u << (3 * L.lg - 2)));  // blocks of whole warps
   if (t >= (1u << (3 * L.lg - 2))) return;
   Cell<float> q0, q1;
   float2 F, dF;
-  const unsigned o = rb2_eval<M, FM>(L, c, color, t, q0, q1, F, dF);
+  const unsigned o = rb2_eval<M, FM>(L, c, color, t, lanes, q0, q1, F, dF);
   // FP32 cycles drive a correction: a 2-ulp quotient is ample there
   const float xn0 = q0.x - __fdividef(F.x, dF.x), xn1 = q1.x - __fdividef(F.y, dF.y);
   *reinterpret_cast<float2*>(L.x + o) = make_float2(xn0, xn1);
@@ -526,12 +548,13 @@ template <Model M, Form FM>
 __global__ void __launch_bounds__(256) resid_rb2(LevelView<float> L, Coef c, float* __restrict__ res) {
   const unsigned q4 = 1u << (3 * L.lg - 2);
   unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lanes = __ballot_sync(0xffffffffu, t < 2 * q4);  // blocks of whole warps
   if (t >= 2 * q4) return;
   const int color = t >= q4 ? 1 : 0;
   t -= color ? q4 : 0u;
   Cell<float> q0, q1;
   float2 F, dF;
-  const unsigned o = rb2_eval<M, FM>(L, c, color, t, q0, q1, F, dF);
+  const unsigned o = rb2_eval<M, FM>(L, c, color, t, lanes, q0, q1, F, dF);
   *reinterpret_cast<float2*>(res + o) = make_float2(-F.x, -F.y);  // Sigma is inside F
 }
 
@@ -991,12 +1014,17 @@ template <Model M, Form FM>
 __global__ void __launch_bounds__(kNormThreads) norm_rb2(LevelView<float> L, Coef c, double* __restrict__ part) {
   const unsigned q4 = 1u << (3 * L.lg - 2);
   float acc = 0.f;
-  for (unsigned tt = blockIdx.x * blockDim.x + threadIdx.x; tt < 2 * q4; tt += gridDim.x * blockDim.x) {
-    const int color = tt >= q4 ? 1 : 0;
-    Cell<float> q0, q1;
-    float2 F, dF;
-    rb2_eval<M, FM>(L, c, color, tt - (color ? q4 : 0u), q0, q1, F, dF);
-    acc = fmaf(F.x, F.x, fmaf(F.y, F.y, acc));
+  // the loop runs while any lane of the warp has a pair (warp-uniform trip count, blocks of whole warps)
+  for (unsigned tt = blockIdx.x * blockDim.x + threadIdx.x; __any_sync(0xffffffffu, tt < 2 * q4);
+       tt += gridDim.x * blockDim.x) {
+    const unsigned lanes = __ballot_sync(0xffffffffu, tt < 2 * q4);
+    if (tt < 2 * q4) {
+      const int color = tt >= q4 ? 1 : 0;
+      Cell<float> q0, q1;
+      float2 F, dF;
+      rb2_eval<M, FM>(L, c, color, tt - (color ? q4 : 0u), lanes, q0, q1, F, dF);
+      acc = fmaf(F.x, F.x, fmaf(F.y, F.y, acc));
+    }
   }
   block_sum_store<double>((double)acc, part);
 }
