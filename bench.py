@@ -291,6 +291,23 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def copy_times(cev: dict, steps: int) -> dict:
+    """Per loop (serial, pipelined) and direction: the copies' event time per step (mean) and the slowest step's.
+    Against the step time they show whether the link, not the schedule, set the end-to-end figure: a copy that
+    outlasts a step cannot hide behind it."""
+    out = {}
+    for loop, evs in cev.items():
+        for kind in ("h2d", "d2h"):
+            ts = [a.elapsed_time(b) for k, a, b in evs if k == kind]
+            if not ts:
+                continue
+            # the d2h of one step is two groups in the pipelined loop (each model's forces)
+            per = len(ts) / steps
+            steps_ms = [sum(ts[i:i + round(per)]) for i in range(0, len(ts), max(1, round(per)))]
+            out[f"{loop}_{kind}"] = {"mean": sum(ts) / steps, "max_step": max(steps_ms)}
+    return out
+
+
 def copy_rates(h_src, d_dst, h_dst, d_src, stream) -> dict:
     """This box's pinned-host link, measured with the step's own buffers (one particle coordinate, one force
     component): GB/s host-to-device, device-to-host, and both directions at once on two streams."""
@@ -514,21 +531,44 @@ def main():
     # end to end: positions from pinned host memory, forces back to pinned host memory, every step
     e2e = None
     if not args.no_e2e:
-        hx, hy, hz = (v.cpu().pin_memory() for v in (x, y, z))
-        hg = [torch.empty(npart, dtype=torch.float32).pin_memory() for _ in range(6)]
+        # the library's page-locked host buffers (huge-page backed where the kernel grants it)
+        hx, hy, hz = (isis.host_empty(npart) for _ in range(3))
+        for h, v in zip((hx, hy, hz), (x, y, z)):
+            h.copy_(v)
+        hg = [isis.host_empty(npart) for _ in range(6)]
         pos = [tuple(torch.empty_like(x) for _ in range(3)) for _ in range(2)]
         gb = [g, [torch.empty_like(t) for t in g]]
 
+        def tev():
+            return torch.cuda.Event(enable_timing=True)
+
+        # copy groups of each loop, bracketed by events on the copying stream: (kind, start, end)
+        cev = {"serial": [], "pipelined": []}
+
+        def copies(loop, kind, st, pairs):
+            a, b = tev(), tev()
+            a.record(st)
+            for dst, src in pairs:
+                dst.copy_(src, non_blocking=True)
+            b.record(st)
+            cev[loop].append((kind, a, b))
+
+        # one untimed pass of every copy first: the first DMA to or from a freshly pinned buffer runs slow
+        for bufs in pos:
+            for dst, src in zip(bufs, (hx, hy, hz)):
+                dst.copy_(src, non_blocking=True)
+        for bufs in gb:
+            for dst, src in zip(hg, bufs):
+                dst.copy_(src, non_blocking=True)
+
         # serial: every copy on the compute stream, before and after its step
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = tev(), tev()
         e0.record(stream)
         for s in range(args.steps):
-            for d, h in zip(pos[0], (hx, hy, hz)):
-                d.copy_(h, non_blocking=True)
+            copies("serial", "h2d", stream, zip(pos[0], (hx, hy, hz)))
             step(*pos[0])
-            for d, h in zip(g, hg):
-                h.copy_(d, non_blocking=True)
+            copies("serial", "d2h", stream, zip(hg, g))
         e1.record(stream)
         barrier()
         serial = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
@@ -543,8 +583,7 @@ def main():
         e0.record(stream)
         cs.wait_stream(stream)
         with torch.cuda.stream(cs):
-            for d, h in zip(pos[0], (hx, hy, hz)):
-                d.copy_(h, non_blocking=True)
+            copies("pipelined", "h2d", cs, zip(pos[0], (hx, hy, hz)))
             h2d[0].record(cs)
         for s in range(args.steps):
             b = s % 2
@@ -552,8 +591,7 @@ def main():
                 with torch.cuda.stream(cs):
                     if s >= 1:
                         cs.wait_event(pos_free[1 - b])
-                    for d, h in zip(pos[1 - b], (hx, hy, hz)):
-                        d.copy_(h, non_blocking=True)
+                    copies("pipelined", "h2d", cs, zip(pos[1 - b], (hx, hy, hz)))
                     h2d[1 - b].record(cs)
             stream.wait_event(h2d[b])
             if s >= 2:
@@ -570,15 +608,13 @@ def main():
             ev.record(stream)
             with torch.cuda.stream(cs):
                 cs.wait_event(ev)
-                for d, h in zip(gb[b][0:3], hg[0:3]):
-                    h.copy_(d, non_blocking=True)
+                copies("pipelined", "d2h", cs, zip(hg[0:3], gb[b][0:3]))
             infos["fofr"] = isis.isis_scalar_solve(isis.ISIS_FOFR_HS, pfr, grid, a, eta, u, tol=args.tol, opts=o_fr)
             isis.isis_fifth_force(isis.ISIS_FOFR_HS, pfr, grid, a, Phi, u, xx, yy, zz, out=gb[b][3:6])
             pos_free[b].record(stream)
             with torch.cuda.stream(cs):
                 cs.wait_event(pos_free[b])
-                for d, h in zip(gb[b][3:6], hg[3:6]):
-                    h.copy_(d, non_blocking=True)
+                copies("pipelined", "d2h", cs, zip(hg[3:6], gb[b][3:6]))
                 g_free[b].record(cs)
         stream.wait_stream(cs)
         e1.record(stream)
@@ -586,8 +622,10 @@ def main():
         ems = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
         e2e = {"value": ems, "unit": "ms", "h2d_bytes_per_step": 3 * npart * 4, "d2h_bytes_per_step": 6 * npart * 4,
                "copies": "on a second stream, positions and forces double-buffered: step s's positions are copied "
-                         "while step s-1 computes, each model's forces are read back while the next solve runs",
-               "serial_value": serial, "copy_rates_gbs": copy_rates(hx, x, hg[0], g[0], stream)}
+                         "while step s-1 computes, each model's forces are read back while the next solve runs; "
+                         "host buffers from isis_host_alloc (page-locked, huge-page backed)",
+               "serial_value": serial, "copy_ms_per_step": copy_times(cev, args.steps),
+               "copy_rates_gbs": copy_rates(hx, x, hg[0], g[0], stream)}
 
     # roofline of the dominant kernel (kind and instantiation, by summed event time)
     peaks = {}

@@ -34,6 +34,7 @@
  */
 #ifndef ISIS_H
 #define ISIS_H
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -343,6 +344,20 @@ const char* isis_strerror(isis_status status);
 
 /* Free every cached workspace buffer (synchronises the device first). */
 void isis_release_workspace(void);
+
+/* Page-locked HOST memory for the arrays that cross the host link every step (the particle positions given
+ * to isis_cic_deposit and isis_fifth_force, the forces read back), so that their copies run as asynchronous
+ * DMA on a stream.  bytes > 0; on success *out is a buffer of at least `bytes` bytes, zero-filled, owned by
+ * the caller until isis_host_free(*out).  A buffer of at least one transparent huge page starts on a huge-page
+ * boundary and is advised MADV_HUGEPAGE before its pages are touched (the copy engines' address translations
+ * then cover it with a few entries); smaller buffers, or a kernel that grants no huge pages, get base pages.
+ * Returns ISIS_EINVAL for out == NULL or bytes == 0, ISIS_ENOMEM when the mapping fails and ISIS_ECUDA when
+ * the CUDA driver refuses to page-lock it (nothing is left allocated then).  Thread safe. */
+isis_status isis_host_alloc(size_t bytes, void** out);
+/* Unlock and unmap a buffer of isis_host_alloc; NULL is a no-op.  Returns ISIS_EINVAL for a pointer that
+ * isis_host_alloc did not return (or that was freed already), ISIS_ECUDA when the driver's unregistration
+ * fails (the buffer is unmapped all the same).  Thread safe. */
+isis_status isis_host_free(void* ptr);
 
 /* Self-test of the float-float exponential used by the f(R) residual of the
  * FP64 defect correction (table-driven, after Tang, ACM TOMS 1989): y[i] =

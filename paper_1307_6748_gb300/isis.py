@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 from dataclasses import dataclass, field
 
 import torch
@@ -27,7 +28,7 @@ H0_MPC = 1.0 / 2997.92458  # (Mpc/h)^-1 with c = 1
 EXPORTS = ("isis_cic_deposit", "isis_cic_deposit_noalloc", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force",
            "isis_strerror", "isis_release_workspace", "isis_prof_enable", "isis_prof_reset", "isis_prof_read",
            "isis_launch_count", "isis_selftest_exp_ff", "isis_kick_drift", "isis_patch_poisson_solve",
-           "isis_patch_scalar_solve", "isis_background_field")
+           "isis_patch_scalar_solve", "isis_background_field", "isis_host_alloc", "isis_host_free")
 ISIS_INIT_INPUT, ISIS_INIT_BACKGROUND, ISIS_INIT_LOCAL, ISIS_INIT_PARENT = 0, 1, 2, 3
 
 
@@ -116,6 +117,10 @@ def load(path: str = LIB_PATH):
     lib.isis_prof_read.restype = ctypes.c_int
     lib.isis_launch_count.argtypes = []
     lib.isis_launch_count.restype = ctypes.c_int64
+    lib.isis_host_alloc.argtypes = [ctypes.c_size_t, P(ctypes.c_void_p)]
+    lib.isis_host_alloc.restype = ctypes.c_int
+    lib.isis_host_free.argtypes = [ctypes.c_void_p]
+    lib.isis_host_free.restype = ctypes.c_int
     for name in ("isis_cic_deposit", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -232,6 +237,20 @@ def strerror(status: int) -> str:
 
 def release_workspace() -> None:
     load().isis_release_workspace()
+
+
+def host_empty(n: int, dtype=torch.float32) -> torch.Tensor:
+    """A CPU tensor of n elements in page-locked host memory from isis_host_alloc (huge-page backed where the
+    kernel grants it), for the arrays copied every step; isis_host_free runs when the last tensor viewing it is
+    released.  Zero-filled."""
+    lib = load()
+    esize = torch.empty((), dtype=dtype).element_size()
+    nbytes = int(n) * esize
+    ptr = ctypes.c_void_p()
+    _check(lib.isis_host_alloc(nbytes, ctypes.byref(ptr)), "isis_host_alloc")
+    buf = (ctypes.c_ubyte * nbytes).from_address(ptr.value)
+    weakref.finalize(buf, lib.isis_host_free, ptr.value)
+    return torch.frombuffer(buf, dtype=dtype, count=int(n))
 
 
 def prof_enable(on: bool = True) -> None:

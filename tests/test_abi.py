@@ -124,3 +124,18 @@ def test_solver_option_and_parameter_checks_without_gpu(lib):
     assert solve(model=isis.ISIS_FOFR_HS, params=isis.Params(fR0_abs=0.0)) == E
     assert solve(model=isis.ISIS_FOFR_HS, params=isis.Params(n=0)) == E
     assert solve(model=isis.ISIS_CHAMELEON, params=isis.Params(cham_n=-1.0)) == E
+
+
+def test_host_buffer_argument_checks_without_gpu(lib):
+    """isis_host_alloc / isis_host_free reject what they must before any driver call."""
+    from paper_1307_6748_gb300 import isis
+    L = isis.load()
+    out = ctypes.c_void_p()
+    assert L.isis_host_alloc(0, ctypes.byref(out)) == isis.ISIS_EINVAL
+    assert out.value is None
+    assert L.isis_host_alloc(64, None) == isis.ISIS_EINVAL
+    assert L.isis_host_alloc((1 << 64) - 1, ctypes.byref(out)) == isis.ISIS_EINVAL
+    assert L.isis_host_free(None) == isis.ISIS_OK
+    # a pointer the allocator did not return
+    buf = (ctypes.c_ubyte * 64)()
+    assert L.isis_host_free(ctypes.addressof(buf)) == isis.ISIS_EINVAL
