@@ -213,7 +213,7 @@ __device__ __forceinline__ Cell<float> cv_gather(const SmemLevel& S, int i, int 
 
 // One colour of a Newton-Gauss-Seidel sweep (the update of smooth_rb).
 template <Model M, Form FM>
-__device__ void cv_smooth(const SmemLevel& S, const Coef& c, int color) {
+__device__ void cv_smooth(const SmemLevel& S, const CoefT<float>& c, int color) {
   const int lg = S.lg, half = 1 << (3 * lg - 1), m = (1 << lg) - 1;
   for (int t = threadIdx.x; t < half; t += blockDim.x) {
     const int k2 = t & ((1 << (lg - 1)) - 1), row = t >> (lg - 1), j = row & m, i = row >> lg;
@@ -225,8 +225,10 @@ __device__ void cv_smooth(const SmemLevel& S, const Coef& c, int color) {
   }
 }
 
+// c: the constants of the FP64 Newton solve; cf: the same rounded to FP32 for the FP32 levels.
 template <Model M, Form FM>
-__global__ void __launch_bounds__(kCVThreads) coarse_cycle(CoarseCycle cc, Coef c, int* flags, int* steps_max) {
+__global__ void __launch_bounds__(kCVThreads, 1) coarse_cycle(CoarseCycle cc, Coef c, CoefT<float> cf, int* flags,
+                                                           int* steps_max) {
   extern __shared__ float4 cv_dyn[];
   __shared__ NewtonScratch NS;
   float* sm = reinterpret_cast<float*>(cv_dyn);
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(kCVThreads) coarse_cycle(CoarseCycle cc, Coef 
   for (int l = 0; l < last; ++l) {
     for (int s = 0; s < cc.nu1; ++s)
       for (int color = 0; color < 2; ++color) {
-        cv_smooth<M, FM>(S[l], c, color);
+        cv_smooth<M, FM>(S[l], cf, color);
         __syncthreads();
       }
     const SmemLevel &F = S[l], &C = S[l + 1];
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(kCVThreads) coarse_cycle(CoarseCycle cc, Coef 
           for (int d = 0; d < 2; ++d) {
             Cell<float> q = cv_gather<M, FM>(F, 2 * I + a, 2 * J + b, 2 * K + d);
             float Fv, dF;
-            eval_cell<M, FM, float>(c, F.ih2, q, Fv, dF);
+            eval_cell<M, FM, float>(cf, F.ih2, q, Fv, dF);
             xs += q.x;
             rs -= Fv;  // r = Sigma - L(x)
           }
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(kCVThreads) coarse_cycle(CoarseCycle cc, Coef 
       Cell<float> q = cv_gather<M, FM>(C, I, J, K);
       q.sig = 0.f;
       float Fv, dF;
-      eval_cell<M, FM, float>(c, C.ih2, q, Fv, dF);
+      eval_cell<M, FM, float>(cf, C.ih2, q, Fv, dF);
       C.sig[t] += Fv;  // Sigma_H = L_H(R x) + R r
     }
     __syncthreads();
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(kCVThreads) coarse_cycle(CoarseCycle cc, Coef 
     __syncthreads();
     for (int s = 0; s < cc.nu2; ++s)
       for (int color = 0; color < 2; ++color) {
-        cv_smooth<M, FM>(S[l], c, color);
+        cv_smooth<M, FM>(S[l], cf, color);
         __syncthreads();
       }
   }

@@ -215,7 +215,7 @@ __device__ __forceinline__ Cell<T> gather(const LevelView<T>& L, int i, int j, i
 // of row t / (N/2); for FP32 grids t is also that cell's place in its colour
 // half, so a warp reads and writes 32 consecutive values of each array.
 template <Model M, Form FM, class T>
-__global__ void smooth_color(LevelView<T> L, Coef c, int color) {
+__global__ void smooth_color(LevelView<T> L, CoefT<T> c, int color) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t half = (size_t)1 << (3 * L.lg - 1);
   if (t >= half) return;
@@ -243,7 +243,7 @@ __global__ void smooth_color(LevelView<T> L, Coef c, int color) {
 // row in the other colour's half (par = parity of k), all in 32-bit
 // arithmetic.
 template <Model M, Form FM>
-__global__ void __launch_bounds__(256) smooth_rb(LevelView<float> L, Coef c, int color) {
+__global__ void __launch_bounds__(256) smooth_rb(LevelView<float> L, CoefT<float> c, int color) {
   const int lg = L.lg;
   const unsigned half = 1u << (3 * lg - 1), hN = (unsigned)L.N >> 1, m = (unsigned)L.N - 1;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -381,18 +381,16 @@ __device__ __forceinline__ float2 exp_2(float2 v) {
   return pk(ex2_approx(t.x), ex2_approx(t.y));
 }
 
-// e^v - 1 of both lanes by the series of dexpm1<float> of a fixed degree: DEG 4 for |v| <= 2^-7, DEG 9 for
+// e^v - 1 of both lanes by the series of dexpm1<float> of a fixed degree: DEG 3 for |v| <= 2^-7, DEG 8 for
 // |v| <= 1/2, DEG 0 for expf(v) - 1.
 template <int DEG>
 __device__ __forceinline__ float2 expm1_2d(float2 v) {
-  if constexpr (DEG == 4) {
-    float2 p = fma2(v, bc(1.0f / 24.0f), bc(1.0f / 6.0f));
-    p = fma2(p, v, bc(0.5f));
+  if constexpr (DEG == 3) {
+    float2 p = fma2(v, bc(1.0f / 6.0f), bc(0.5f));
     p = fma2(p, v, bc(1.0f));
     return mul2(p, v);
-  } else if constexpr (DEG == 9) {
-    float2 p = fma2(v, bc(1.0f / 362880.0f), bc(1.0f / 40320.0f));
-    p = fma2(p, v, bc(1.0f / 5040.0f));
+  } else if constexpr (DEG == 8) {
+    float2 p = fma2(v, bc(1.0f / 40320.0f), bc(1.0f / 5040.0f));
     p = fma2(p, v, bc(1.0f / 720.0f));
     p = fma2(p, v, bc(1.0f / 120.0f));
     p = fma2(p, v, bc(1.0f / 24.0f));
@@ -407,8 +405,8 @@ __device__ __forceinline__ float2 expm1_2d(float2 v) {
 // The same with the degree set by the larger |v| of the two lanes.
 __device__ __forceinline__ float2 expm1_2(float2 v) {
   const float mx = fmaxf(fabsf(v.x), fabsf(v.y));
-  if (mx <= 0.0078125f) return expm1_2d<4>(v);
-  if (mx <= 0.5f) return expm1_2d<9>(v);
+  if (mx <= 0.0078125f) return expm1_2d<3>(v);
+  if (mx <= 0.5f) return expm1_2d<8>(v);
   return expm1_2d<0>(v);
 }
 // The largest of a non-negative float over the warp's lanes in `lanes` (non-negative floats order as their bits).
@@ -416,12 +414,12 @@ __device__ __forceinline__ float warp_max_nonneg(unsigned lanes, float v) {
   return __uint_as_float(__reduce_max_sync(lanes, __float_as_uint(v)));
 }
 // expm1_2 with the low degree taken only when every lane of the warp allows it: the threads of a warp then
-// run one series rather than both in turn.  Degree 9 holds its bound for every |v| <= 1/2, the small ones
+// run one series rather than both in turn.  Degree 8 holds its bound for every |v| <= 1/2, the small ones
 // included, so only lanes with |v| > 1/2 (rare) leave it for expf.
 __device__ __forceinline__ float2 expm1_2w(unsigned lanes, float2 v) {
   const float mx = fmaxf(fabsf(v.x), fabsf(v.y));
-  if (warp_max_nonneg(lanes, mx) <= 0.0078125f) return expm1_2d<4>(v);
-  if (mx <= 0.5f) return expm1_2d<9>(v);
+  if (warp_max_nonneg(lanes, mx) <= 0.0078125f) return expm1_2d<3>(v);
+  if (mx <= 0.5f) return expm1_2d<8>(v);
   return expm1_2d<0>(v);
 }
 
@@ -463,7 +461,7 @@ __device__ __forceinline__ void fofr_delta_flux2(const Cell<float>& q0, const Ce
 // from cells gathered without their exponentials.
 // `lanes`: the warp's lanes that evaluate a pair here (the series degree is chosen per warp).
 template <Form FM>
-__device__ __forceinline__ void fofr_pair_eval(const Coef& c, float ih2, unsigned lanes, const Cell<float>& q0,
+__device__ __forceinline__ void fofr_pair_eval(const CoefT<float>& c, float ih2, unsigned lanes, const Cell<float>& q0,
                                                const Cell<float>& q1, float2& F, float2& dF) {
   const float2 half = bc(0.5f);
   const float2 x = pk(q0.x, q1.x), sig = pk(q0.sig, q1.sig);
@@ -474,16 +472,16 @@ __device__ __forceinline__ void fofr_pair_eval(const Coef& c, float ih2, unsigne
     float mx = fmaxf(fabsf(x.x), fabsf(x.y));
 #pragma unroll
     for (int d = 0; d < 6; ++d) mx = fmaxf(mx, fmaxf(fabsf(q0.xn[d]), fabsf(q1.xn[d])));
-    // one degree for the whole warp unless a lane needs expf (|e| > 1/2): then degree 9 or expf per lane
-    const float2 minv = bc(-(float)c.inv_np1), xm = mul2(x, minv);
+    // one degree for the whole warp unless a lane needs expf (|e| > 1/2): then degree 8 or expf per lane
+    const float2 minv = bc(-c.inv_np1), xm = mul2(x, minv);
     float2 m, em;
-    if (warp_max_nonneg(lanes, mx) <= 0.0078125f) fofr_delta_flux2<4>(q0, q1, x, B, xm, m, flux, dsum, em);
-    else if (mx <= 0.5f) fofr_delta_flux2<9>(q0, q1, x, B, xm, m, flux, dsum, em);
+    if (warp_max_nonneg(lanes, mx) <= 0.0078125f) fofr_delta_flux2<3>(q0, q1, x, B, xm, m, flux, dsum, em);
+    else if (mx <= 0.5f) fofr_delta_flux2<8>(q0, q1, x, B, xm, m, flux, dsum, em);
     else fofr_delta_flux2<0>(q0, q1, x, B, xm, m, flux, dsum, em);
     const float2 exB = exp_2(mul2(B, minv));
-    const float2 K2 = bc((float)c.K2);
+    const float2 K2 = bc(c.K2);
     F = sub2(fma2(flux, bc(ih2), mul2(K2, mul2(exB, em))), sig);
-    dF = sub2(mul2(dsum, bc(ih2)), mul2(mul2(K2, bc((float)c.inv_np1)), mul2(exB, add2(em, bc(1.0f)))));
+    dF = sub2(mul2(dsum, bc(ih2)), mul2(mul2(K2, bc(c.inv_np1)), mul2(exB, add2(em, bc(1.0f)))));
   } else {
     // flux = (1/2) [ex sum du + sum ex_nb du], dsum = (1/2) ex sum du - (6 ex + sum ex_nb) / 2
     const float2 ex = exp_2(x), hex = mul2(half, ex);
@@ -498,13 +496,13 @@ __device__ __forceinline__ void fofr_pair_eval(const Coef& c, float ih2, unsigne
     }
     flux = fma2(hex, sdu, mul2(half, sexdu));
     dsum = sub2(mul2(hex, sdu), mul2(half, fma2(bc(6.0f), ex, sex)));
-    const float2 fs = bc((float)c.fscale);
+    const float2 fs = bc(c.fscale);
     flux = mul2(flux, fs);
     dsum = mul2(dsum, fs);
-    const float2 inp1 = bc((float)c.inv_np1), Kx = bc((float)c.fKx);
-    const float2 em = expm1_2w(lanes, mul2(x, bc(-(float)c.inv_np1)));
-    const float2 S = add2(sub2(mul2(bc((float)c.K1), sub2(pk(q0.eta, q1.eta), bc(1.0f))), mul2(Kx, em)),
-                          bc((float)c.fK3x));
+    const float2 inp1 = bc(c.inv_np1), Kx = bc(c.fKx);
+    const float2 em = expm1_2w(lanes, mul2(x, bc(-c.inv_np1)));
+    const float2 S = add2(sub2(mul2(bc(c.K1), sub2(pk(q0.eta, q1.eta), bc(1.0f))), mul2(Kx, em)),
+                          bc(c.fK3x));
     F = sub2(sub2(mul2(flux, bc(ih2)), S), sig);
     dF = sub2(mul2(dsum, bc(ih2)), mul2(mul2(Kx, inp1), add2(em, bc(1.0f))));
   }
@@ -513,7 +511,7 @@ __device__ __forceinline__ void fofr_pair_eval(const Coef& c, float ih2, unsigne
 // Gather and evaluate the two cells of an rb2 thread: the packed path for f(R), two eval_cell otherwise.
 // `lanes`: the lanes of the calling warp that are here (all of them call with the same mask).
 template <Model M, Form FM>
-__device__ __forceinline__ unsigned rb2_eval(const LevelView<float>& L, const Coef& c, int color, unsigned t,
+__device__ __forceinline__ unsigned rb2_eval(const LevelView<float>& L, const CoefT<float>& c, int color, unsigned t,
                                              unsigned lanes, Cell<float>& q0, Cell<float>& q1, float2& F,
                                              float2& dF) {
   if constexpr (M == FOFR) {
@@ -530,7 +528,7 @@ __device__ __forceinline__ unsigned rb2_eval(const LevelView<float>& L, const Co
 }
 
 template <Model M, Form FM>
-__global__ void __launch_bounds__(256) smooth_rb2(LevelView<float> L, Coef c, int color) {
+__global__ void __launch_bounds__(256) smooth_rb2(LevelView<float> L, CoefT<float> c, int color) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lanes = __ballot_sync(0xffffffffu, t < (1u << (3 * L.lg - 2)));  // blocks of whole warps
   if (t >= (1u << (3 * L.lg - 2))) return;
@@ -545,7 +543,7 @@ __global__ void __launch_bounds__(256) smooth_rb2(LevelView<float> L, Coef c, in
 // Residual r = Sigma - L(x) of every cell of a red/black FP32 grid into res
 // (two cells per thread; threads [0, N^3/4) red, then black).
 template <Model M, Form FM>
-__global__ void __launch_bounds__(256) resid_rb2(LevelView<float> L, Coef c, float* __restrict__ res) {
+__global__ void __launch_bounds__(256) resid_rb2(LevelView<float> L, CoefT<float> c, float* __restrict__ res) {
   const unsigned q4 = 1u << (3 * L.lg - 2);
   unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lanes = __ballot_sync(0xffffffffu, t < 2 * q4);  // blocks of whole warps
@@ -588,8 +586,12 @@ __global__ void restrict_xr(LevelView<float> F, const float* __restrict__ res, L
 // children, x_H = R x, x0_H = x_H, Sigma_H = R r.  The 32 fine cells the 8
 // stencils touch (block a, b, d = 0..3 at i = 2I-1+a, j = 2J-1+b, k = 2K-1+d,
 // without the 4 corner rows) are loaded once.
+// FP32 (but the f(R) correction form, whose neighbours' B and e^B need more): at least three blocks of 256 per
+// SM (at most 85 registers); the compiler would otherwise keep every loaded cell and exponential in flight at
+// once (89 registers, two blocks, 1.35x the time at 512^3 for the f(R) field form).
 template <Model M, Form FM, class T>
-__global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __restrict__ x0c, T* __restrict__ sigc) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && !(M == FOFR && FM == DELTA)) ? 3 : 1)
+    resid_restrict(LevelView<T> F, CoefT<T> c, LevelView<T> C, T* __restrict__ x0c, T* __restrict__ sigc) {
   constexpr bool kAllB = (FM == DELTA && M == FOFR);   // neighbours' B (and e^B) needed
   constexpr bool kAux = (M == FOFR);
   T* __restrict__ xc = C.x;
@@ -601,7 +603,9 @@ __global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __rest
   const int K = (int)(t & mc), J = (int)((t >> lgc) & mc), I = (int)(t >> (2 * lgc));
   const size_t to = lidx<T>(lgc, I, J, K);
   T X[4][4][4], Ax[4][4][4], Bx[4][4][4], Wx[4][4][4];
-  size_t P[4][4][4];
+  // storage positions of the loaded cells (FP32 grids: N <= 1024, 32-bit positions, half the registers)
+  using Idx = std::conditional_t<sizeof(T) == 4, unsigned, size_t>;
+  Idx P[4][4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -613,7 +617,7 @@ __global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __rest
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
         if ((ea || eb) && (d == 0 || d == 3)) continue;
-        P[a][b][d] = p[d];
+        P[a][b][d] = (Idx)p[d];
         X[a][b][d] = F.x[p[d]];
         // the f(R) exponentials of each loaded cell, once for the 8 stencils (fill_exps)
         if constexpr (kAllB) { Bx[a][b][d] = F.B[p[d]]; Wx[a][b][d] = dexp<T>(Bx[a][b][d]); }
@@ -631,7 +635,7 @@ __global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __rest
 #pragma unroll
       for (int d = 1; d < 3; ++d) {
         Cell<T> q;
-        const size_t pc = P[a][b][d];
+        const Idx pc = P[a][b][d];
         q.x = X[a][b][d];
         q.xn[0] = X[a + 1][b][d]; q.xn[1] = X[a - 1][b][d];
         q.xn[2] = X[a][b + 1][d]; q.xn[3] = X[a][b - 1][d];
@@ -671,7 +675,7 @@ __global__ void resid_restrict(LevelView<T> F, Coef c, LevelView<T> C, T* __rest
 // float2 per colour half (k = 2K, 2K+2 and k = 2K+1, 2K+3) and two scalars, and the per-cell arrays of the
 // children as float2 likewise.  Coarse side >= 4.
 template <Model M, Form FM>
-__global__ void __launch_bounds__(256) resid_restrict2(LevelView<float> F, Coef c, LevelView<float> C,
+__global__ void __launch_bounds__(256) resid_restrict2(LevelView<float> F, CoefT<float> c, LevelView<float> C,
                                                        float* __restrict__ x0c, float* __restrict__ sigc) {
   static_assert(M != FOFR, "the f(R) operators keep the one-cell kernel");
   const int lg = F.lg, lgc = lg - 1, m = F.N - 1;
@@ -766,7 +770,7 @@ __global__ void __launch_bounds__(256) resid_restrict2(LevelView<float> F, Coef 
 
 // Sigma_H += L_H(x_H) (the FAS coarse source, Sect. 3.2).
 template <Model M, Form FM, class T>
-__global__ void coarse_sigma_add(LevelView<T> L, Coef c, T* __restrict__ sig) {
+__global__ void coarse_sigma_add(LevelView<T> L, CoefT<T> c, T* __restrict__ sig) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ((size_t)1 << (3 * L.lg))) return;
   LevelView<T> L0 = L;
@@ -995,7 +999,7 @@ __device__ __forceinline__ void block_sum_store(double v, double* out) {
 }
 
 template <Model M, Form FM, class T>
-__global__ void __launch_bounds__(kNormThreads) norm_partial(LevelView<T> L, Coef c, double* __restrict__ part) {
+__global__ void __launch_bounds__(kNormThreads) norm_partial(LevelView<T> L, CoefT<T> c, double* __restrict__ part) {
   size_t n = (size_t)1 << (3 * L.lg);
   double acc = 0.0;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
@@ -1011,7 +1015,7 @@ __global__ void __launch_bounds__(kNormThreads) norm_partial(LevelView<T> L, Coe
 // and iteration (the smoother's gather), a grid-stride loop over the pairs of both colours
 // with a fixed assignment: reproducible.
 template <Model M, Form FM>
-__global__ void __launch_bounds__(kNormThreads) norm_rb2(LevelView<float> L, Coef c, double* __restrict__ part) {
+__global__ void __launch_bounds__(kNormThreads) norm_rb2(LevelView<float> L, CoefT<float> c, double* __restrict__ part) {
   const unsigned q4 = 1u << (3 * L.lg - 2);
   float acc = 0.f;
   // the loop runs while any lane of the warp has a pair (warp-uniform trip count, blocks of whole warps)

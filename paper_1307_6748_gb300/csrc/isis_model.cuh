@@ -41,6 +41,18 @@ struct Coef {
   double KP, eta_mean;  // Poisson: KP = 1.5 Om H0^2 / a, mean density
 };
 
+// The same constants in a kernel's own precision.  The FP32 kernels receive them rounded to FP32 once on the host
+// (the launch converts a Coef argument): converted per thread, each would be an FP64-to-FP32 conversion on the
+// narrow FP64 pipe of this part.  CoefT<double> holds the values unchanged.
+template <class T>
+struct CoefT {
+  T A, s, K1, K2, K3, fscale, fKx, fK3x, np1, inv_np1, KP, eta_mean;
+  CoefT() = default;
+  __host__ __device__ CoefT(const Coef& c)
+      : A((T)c.A), s((T)c.s), K1((T)c.K1), K2((T)c.K2), K3((T)c.K3), fscale((T)c.fscale), fKx((T)c.fKx),
+        fK3x((T)c.fK3x), np1((T)c.np1), inv_np1((T)c.inv_np1), KP((T)c.KP), eta_mean((T)c.eta_mean) {}
+};
+
 // Values of one cell and its six neighbours, in the order
 // (i+1, i-1, j+1, j-1, k+1, k-1).
 template <class T>
@@ -57,19 +69,18 @@ template <> __device__ __forceinline__ double dexp<double>(double v) { return ex
 template <> __device__ __forceinline__ float dexp<float>(float v) { return __expf(v); }
 template <class T> __device__ __forceinline__ T dexpm1(T v);
 template <> __device__ __forceinline__ double dexpm1<double>(double v) { return expm1(v); }
-// FP32 e^v - 1: Taylor series to degree 4 for |v| <= 2^-7 (truncation v^4/120 below
-// 3e-11 relative: the corrections of the refinement loop live there), to degree 9 for
-// |v| <= 1/2 (below 3e-10 relative), else expf(v) - 1 (no cancellation beyond a factor 3).
+// FP32 e^v - 1: Taylor series to degree 3 for |v| <= 2^-7 (truncation below 2.0e-8
+// relative, a third of an FP32 ulp: the corrections of the refinement loop live there), to
+// degree 8 for |v| <= 1/2 (below 1.4e-8 relative), else expf(v) - 1 (no cancellation beyond
+// a factor 3).
 template <> __device__ __forceinline__ float dexpm1<float>(float v) {
   if (fabsf(v) <= 0.0078125f) {
-    float p = fmaf(v, 1.0f / 24.0f, 1.0f / 6.0f);
-    p = fmaf(p, v, 0.5f);
+    float p = fmaf(v, 1.0f / 6.0f, 0.5f);
     p = fmaf(p, v, 1.0f);
     return p * v;
   }
   if (fabsf(v) <= 0.5f) {
-    float p = fmaf(v, 1.0f / 362880.0f, 1.0f / 40320.0f);
-    p = fmaf(p, v, 1.0f / 5040.0f);
+    float p = fmaf(v, 1.0f / 40320.0f, 1.0f / 5040.0f);
     p = fmaf(p, v, 1.0f / 720.0f);
     p = fmaf(p, v, 1.0f / 120.0f);
     p = fmaf(p, v, 1.0f / 24.0f);
@@ -85,8 +96,8 @@ template <> __device__ __forceinline__ float dexpm1<float>(float v) {
 //   F  = h^-2 sum_f b_f (x_nb - x) - S(x) - Sigma,   b_f = (b + b_nb)/2
 //   dF = h^-2 sum_f [ (b/2)(x_nb - x) - b_f ] - dS/dx
 // with x the shifted variable and b = fscale e^x (ex, exn: the cached e^x of the cell and its neighbours).
-template <class T>
-__device__ __forceinline__ void fofr_field_eval(const Coef& c, T ih2, T x, T ex, const T* xn, const T* exn, T eta,
+template <class T, class CT>
+__device__ __forceinline__ void fofr_field_eval(const CT& c, T ih2, T x, T ex, const T* xn, const T* exn, T eta,
                                                 T sig, T& F, T& dF) {
   // sums with e^x and e^x_nb, scaled by fscale once
   T flux = 0, dsum = 0;
@@ -111,8 +122,8 @@ __device__ __forceinline__ void fofr_field_eval(const Coef& c, T ih2, T x, T ex,
 // bt = e^{B+e} = e^B + m of the cell and its neighbours given:
 //   N_B(e) = h^-2 sum_f { (m + m_nb)/2 (B_nb - B) + (bt + bt_nb)/2 (e_nb - e) }
 //            + K2 e^{-B/(n+1)} expm1(-e/(n+1))
-template <class T>
-__device__ __forceinline__ void fofr_delta_eval(const Coef& c, T ih2, T e, T B, T m, T bt, const T* en, const T* Bn,
+template <class T, class CT>
+__device__ __forceinline__ void fofr_delta_eval(const CT& c, T ih2, T e, T B, T m, T bt, const T* en, const T* Bn,
                                                 const T* mn, const T* btn, T sig, T& F, T& dF) {
   T flux = 0, dsum = 0;
 #pragma unroll
@@ -128,9 +139,9 @@ __device__ __forceinline__ void fofr_delta_eval(const Coef& c, T ih2, T e, T B, 
   dF = dsum * ih2 - K2 * inp1 * exB * (em + T(1));
 }
 
-// F = L(x) - Sigma and dF = dL/dx at one cell.
-template <Model M, Form FM, class T>
-__device__ __forceinline__ void eval_cell(const Coef& c, T ih2, const Cell<T>& q, T& F, T& dF) {
+// F = L(x) - Sigma and dF = dL/dx at one cell (c: Coef or CoefT).
+template <Model M, Form FM, class T, class CT>
+__device__ __forceinline__ void eval_cell(const CT& c, T ih2, const Cell<T>& q, T& F, T& dF) {
   if constexpr (M == POI) {
     T lap = (((q.xn[0] + q.xn[1]) + (q.xn[2] + q.xn[3])) + (q.xn[4] + q.xn[5]) - T(6) * q.x) * ih2;
     if constexpr (FM == FIELD) F = lap - T(c.KP) * (q.eta - T(c.eta_mean)) - q.sig;

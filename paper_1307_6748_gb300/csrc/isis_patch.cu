@@ -59,7 +59,7 @@ __device__ __forceinline__ bool unknown(const PL<T>& L, size_t t, int i, int j, 
 // ghost of a masked neighbour is B_nb + e_nb + (m_nb/m_c)(e_c - e_c^Pre): B_c cancels from u_c - u_c^Pre, so the
 // correction enters the ghost as the field does in Eq. (ueq).
 template <Model M, Form FM, class T>
-__device__ __forceinline__ void pt_eval(const Coef& c, const PL<T>& L, int i, int j, int k, bool with_pre, T& F,
+__device__ __forceinline__ void pt_eval(const CoefT<T>& c, const PL<T>& L, int i, int j, int k, bool with_pre, T& F,
                                         T& dF) {
   const size_t q = pidx(L.n1, L.n2, i, j, k);
   const T mc = L.m[q], u = L.u[q];
@@ -187,7 +187,7 @@ __global__ void pt_interp(const double* __restrict__ parent, int p0, int p1, int
 
 // res = Sigma - L(u) at the unknowns, 0 elsewhere.
 template <Model M, Form FM, class T>
-__global__ void __launch_bounds__(kPT) pt_resid(PL<T> L, Coef c, T* __restrict__ res) {
+__global__ void __launch_bounds__(kPT) pt_resid(PL<T> L, CoefT<T> c, T* __restrict__ res) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)L.n0 * L.n1 * L.n2) return;
   T r = T(0);
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kPT) pt_resid(PL<T> L, Coef c, T* __restrict__
 // Sigma_H = L_H(u_H) + R(res) at the coarse unknowns (the coarse level has sig == nullptr in L: its own
 // source is written to sig).
 template <Model M, Form FM, class T>
-__global__ void __launch_bounds__(kPT) pt_sigma(PL<T> C, Coef c, const T* __restrict__ rf, T* __restrict__ sig) {
+__global__ void __launch_bounds__(kPT) pt_sigma(PL<T> C, CoefT<T> c, const T* __restrict__ rf, T* __restrict__ sig) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)C.n0 * C.n1 * C.n2) return;
   int I, J, K;
@@ -270,7 +270,7 @@ constexpr size_t coarse_bytes_per_cell() {
 // block; u written back.  One block pays each half-sweep's latency (in FP64 on GB300's few FP64 units):
 // shared memory and the lists keep that short.
 template <Model M, Form FM, class T>
-__global__ void __launch_bounds__(kCoarseThreads) pt_coarsest_smem(PL<T> L, Coef c) {
+__global__ void __launch_bounds__(kCoarseThreads) pt_coarsest_smem(PL<T> L, CoefT<T> c) {
   extern __shared__ __align__(16) unsigned char pt_smem[];
   __shared__ int cnt[2];
   const int n = L.n0 * L.n1 * L.n2;
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kCoarseThreads) pt_coarsest_smem(PL<T> L, Coef
 // colour): u^Pre = u is stored first, for this colour's unknowns, the only cells whose u^Pre a ghost reads; the
 // other colour's sweeps have not moved them since the phase began.  Then u - u^Pre = 0 in this sweep.
 template <Model M, Form FM, class T>
-__global__ void __launch_bounds__(kPT) pt_smooth_list(PL<T> L, Coef c, const int* __restrict__ list, int count,
+__global__ void __launch_bounds__(kPT) pt_smooth_list(PL<T> L, CoefT<T> c, const int* __restrict__ list, int count,
                                                       T* __restrict__ pre_out) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= count) return;
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kPT) pt_compact(PL<double> L, int* __restrict_
 
 // The coarsest patch level: u^Pre = u, then kCoarseSweeps red/black sweeps, in one block.
 template <Model M, Form FM, class T>
-__global__ void __launch_bounds__(1024) pt_coarsest(PL<T> L, Coef c, T* pre) {
+__global__ void __launch_bounds__(1024) pt_coarsest(PL<T> L, CoefT<T> c, T* pre) {
   const size_t n = (size_t)L.n0 * L.n1 * L.n2;
   for (size_t t = threadIdx.x; t < n; t += blockDim.x) pre[t] = L.u[t];
   __syncthreads();
@@ -382,7 +382,7 @@ __device__ __forceinline__ void pt_block_sum(double v, double* out) {
 
 // Block partial sums of (L(u) - Sigma)^2 over the unknowns (u^Pre = u).
 template <Model M>
-__global__ void __launch_bounds__(kPT) pt_norm(PL<double> L, Coef c, double* __restrict__ part) {
+__global__ void __launch_bounds__(kPT) pt_norm(PL<double> L, CoefT<double> c, double* __restrict__ part) {
   const size_t n = (size_t)L.n0 * L.n1 * L.n2;
   double acc = 0.0;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {

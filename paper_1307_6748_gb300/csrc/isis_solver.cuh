@@ -217,7 +217,7 @@ struct Cycler {
         attr[dev] = true;
       }
       ISIS_LAUNCH(tk(KK_COARSE_CYCLE), bytes, st,
-                  (coarse_cycle<M, FM><<<1, kCVThreads, smem, st>>>(cc, c, ws->iflags, ws->iflags + 1)));
+                  (coarse_cycle<M, FM><<<1, kCVThreads, smem, st>>>(cc, c, CoefT<float>(c), ws->iflags, ws->iflags + 1)));
     }
     return ISIS_OK;
   }
@@ -452,18 +452,19 @@ isis_status sum_f32(Workspace* ws, const float* v, size_t n, cudaStream_t st);
 // solution for a uniform density equal to the cell's eta (computed in FP32:
 // it is only a starting point).
 template <Model M, class T>
-__global__ void init_guess(T* __restrict__ phi, const T* __restrict__ eta, size_t n, Coef c, int mode, double bg) {
+__global__ void init_guess(T* __restrict__ phi, const T* __restrict__ eta, size_t n, CoefT<float> c, int mode,
+                           double bg) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   if (mode == ISIS_INIT_BACKGROUND || M == POI) { phi[t] = (T)bg; return; }
   float e = (float)eta[t];
   if (M == SYM) {
-    float v = 1.0f - (float)c.s * e;
+    float v = 1.0f - c.s * e;
     phi[t] = (T)(v > 0.0f ? sqrtf(v) : 0.0f);
   } else {
     // S(u) = 0 at this eta: e^{u/(n+1)} = K2 / (K1 (eta - 1) + K3)
-    float den = (float)c.K1 * (e - 1.0f) + (float)c.K3;
-    phi[t] = (T)((float)c.np1 * logf((float)c.K2 / den));
+    float den = c.K1 * (e - 1.0f) + c.K3;
+    phi[t] = (T)(c.np1 * logf(c.K2 / den));
   }
 }
 
