@@ -85,9 +85,10 @@ Workspace* get_workspace(int N, int esize, int ncoarse) {
   return w;
 }
 
+// a[0 .. n) = v, four values per thread (a 16-byte aligned workspace grid, n a multiple of 4).
 __global__ void fill_f32(float* __restrict__ a, size_t n, float v) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) a[t] = v;
+  if (4 * t < n) reinterpret_cast<float4*>(a)[t] = make_float4(v, v, v, v);
 }
 
 isis_status sum_f32(Workspace* ws, const float* v, size_t n, cudaStream_t st) {

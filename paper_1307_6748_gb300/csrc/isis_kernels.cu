@@ -34,30 +34,68 @@ __global__ void publish_scalars(const double* __restrict__ scal, int ns, const i
 
 namespace isis {
 
+// Four cells k = 4q .. 4q+3 of a row (i, j), row-major position g0 = 4q' (a multiple of 4; N >= 8): in the
+// red/black FP32 layout, (k, k+2) sit side by side at place g0/2 of the half of colour (i + j) & 1, and
+// (k+1, k+3) at the same place of the other half.  pe and po receive those two places.
+__device__ __forceinline__ void rb_quad(int lg, size_t g0, unsigned& pe, unsigned& po) {
+  const unsigned row = (unsigned)(g0 >> lg), m = (1u << lg) - 1u;
+  const unsigned half = 1u << (3 * lg - 1), base = (unsigned)(g0 >> 1);
+  const bool odd = (((row >> lg) + (row & m)) & 1u) != 0u;
+  pe = (odd ? half : 0u) + base;
+  po = (odd ? 0u : half) + base;
+}
+
+// One thread per four cells (row-major quads): 16-byte and 8-byte accesses, every cell's bytes moved once.
 __global__ void rb_to_ff(const float* __restrict__ psi, float2* __restrict__ pff, int lg, float2 shift) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ((size_t)1 << (3 * lg))) return;
-  const int m = (1 << lg) - 1;
-  const float v = psi[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
-  pff[t] = ff_store(ff_add_f(ff_load(shift), v));
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ((size_t)1 << (3 * lg - 2))) return;
+  unsigned pe, po;
+  rb_quad(lg, 4 * q, pe, po);
+  const float2 ve = *reinterpret_cast<const float2*>(psi + pe), vo = *reinterpret_cast<const float2*>(psi + po);
+  const ff sh = ff_load(shift);
+  const float2 a = ff_store(ff_add_f(sh, ve.x)), b = ff_store(ff_add_f(sh, vo.x));
+  const float2 c = ff_store(ff_add_f(sh, ve.y)), d = ff_store(ff_add_f(sh, vo.y));
+  float4* o = reinterpret_cast<float4*>(pff + 4 * q);
+  o[0] = make_float4(a.x, a.y, b.x, b.y);
+  o[1] = make_float4(c.x, c.y, d.x, d.y);
 }
 
 __global__ void update_ff(float2* __restrict__ pff, const float* __restrict__ e, int lg,
                           const float* __restrict__ emean) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ((size_t)1 << (3 * lg))) return;
-  const int m = (1 << lg) - 1;
-  float v = e[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))];
-  if (emean) v -= *emean;  // Poisson: the correction's mean removed (in FP32, as e is)
-  pff[t] = ff_store(ff_add_f(ff_load(pff[t]), v));
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ((size_t)1 << (3 * lg - 2))) return;
+  unsigned pe, po;
+  rb_quad(lg, 4 * q, pe, po);
+  float2 ve = *reinterpret_cast<const float2*>(e + pe), vo = *reinterpret_cast<const float2*>(e + po);
+  if (emean) {  // Poisson: the correction's mean removed (in FP32, as e is)
+    const float mu = *emean;
+    ve.x -= mu; ve.y -= mu; vo.x -= mu; vo.y -= mu;
+  }
+  float4* io = reinterpret_cast<float4*>(pff + 4 * q);
+  const float4 u0 = io[0], u1 = io[1];
+  const float2 a = ff_store(ff_add_f(ff{u0.x, u0.y}, ve.x)), b = ff_store(ff_add_f(ff{u0.z, u0.w}, vo.x));
+  const float2 c = ff_store(ff_add_f(ff{u1.x, u1.y}, ve.y)), d = ff_store(ff_add_f(ff{u1.z, u1.w}, vo.y));
+  io[0] = make_float4(a.x, a.y, b.x, b.y);
+  io[1] = make_float4(c.x, c.y, d.x, d.y);
 }
 
+// Two cells per thread (n even): one 16-byte load, one 16-byte store.
 __global__ void ff_to_f64(const float2* __restrict__ pff, double* __restrict__ phi, size_t n, double base) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const float2 v = pff[t];
-  const double d = f2d_bits(v.x) + f2d_bits(v.y);  // the float-float value (one rounding at most)
-  phi[t] = base != 0.0 ? base + d : d;
+  if (2 * t >= n) return;
+  const float4 v = reinterpret_cast<const float4*>(pff)[t];
+  // the float-float values (one rounding at most)
+  double d0 = f2d_bits(v.x) + f2d_bits(v.y), d1 = f2d_bits(v.z) + f2d_bits(v.w);
+  if (base != 0.0) {
+    d0 += base;
+    d1 += base;
+  }
+  if ((reinterpret_cast<uintptr_t>(phi) & 15u) == 0) {  // the caller's array: 8-byte alignment is all it promises
+    reinterpret_cast<double2*>(phi)[t] = make_double2(d0, d1);
+  } else {
+    phi[2 * t] = d0;
+    phi[2 * t + 1] = d1;
+  }
 }
 
 __global__ void fofr_exp_ff(const float2* __restrict__ psi, float2* __restrict__ E, size_t n,
@@ -88,16 +126,29 @@ __global__ void mean_to_f32(const double* __restrict__ sum, double inv_n, float*
 __global__ void __launch_bounds__(kNormThreads) moments_to_rb(const double* __restrict__ v, float* __restrict__ rb,
                                                               int lg, double* __restrict__ part2,
                                                               double* __restrict__ part1) {
-  const size_t n = (size_t)1 << (3 * lg);
-  const int m = (1 << lg) - 1;
+  // four cells per iteration (two 16-byte loads in flight per thread), fixed assignment: reproducible
+  const size_t nq = (size_t)1 << (3 * lg - 2);
   ff s1 = {0.f, 0.f};
   float s2 = 0.f;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const ff x = ff_split_bits(v[t]);
-    s1 = ff_add(s1, x);
-    const float d = ff_add_f(x, -1.0f).hi;
-    s2 = fmaf(d, d, s2);
-    rb[lidx<float>(lg, (int)(t >> (2 * lg)), (int)((t >> lg) & m), (int)(t & m))] = x.hi;
+  const bool al = (reinterpret_cast<uintptr_t>(v) & 15u) == 0;  // the caller's array: 16-byte loads if aligned
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (size_t)gridDim.x * blockDim.x) {
+    double2 a, b;
+    if (al) {
+      a = reinterpret_cast<const double2*>(v)[2 * q];
+      b = reinterpret_cast<const double2*>(v)[2 * q + 1];
+    } else {
+      a = make_double2(v[4 * q], v[4 * q + 1]);
+      b = make_double2(v[4 * q + 2], v[4 * q + 3]);
+    }
+    const ff x0 = ff_split_bits(a.x), x1 = ff_split_bits(a.y), x2 = ff_split_bits(b.x), x3 = ff_split_bits(b.y);
+    s1 = ff_add(s1, ff_add(ff_add(x0, x1), ff_add(x2, x3)));
+    const float d0 = ff_add_f(x0, -1.0f).hi, d1 = ff_add_f(x1, -1.0f).hi;
+    const float d2 = ff_add_f(x2, -1.0f).hi, d3 = ff_add_f(x3, -1.0f).hi;
+    s2 = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, s2))));
+    unsigned pe, po;
+    rb_quad(lg, 4 * q, pe, po);
+    *reinterpret_cast<float2*>(rb + pe) = make_float2(x0.hi, x2.hi);
+    *reinterpret_cast<float2*>(rb + po) = make_float2(x1.hi, x3.hi);
   }
   block_sum_store<double>((double)s2, part2);
   __syncthreads();
@@ -106,9 +157,13 @@ __global__ void __launch_bounds__(kNormThreads) moments_to_rb(const double* __re
 
 __global__ void __launch_bounds__(kNormThreads) sum_f32_partial(const float* __restrict__ v, size_t n,
                                                                 double* __restrict__ part) {
+  // four values per iteration (one 16-byte load; n a multiple of 4)
   ff s = {0.f, 0.f};
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-    s = ff_add_f(s, v[t]);
+  const size_t n4 = n >> 2;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += (size_t)gridDim.x * blockDim.x) {
+    const float4 a = reinterpret_cast<const float4*>(v)[t];
+    s = ff_add(s, ff_add(ff_two_sum(a.x, a.y), ff_two_sum(a.z, a.w)));
+  }
   block_sum_store<double>((double)s.hi + (double)s.lo, part);
 }
 }  // namespace isis

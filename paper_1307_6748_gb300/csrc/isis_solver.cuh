@@ -434,6 +434,7 @@ __global__ void fill_f32(float* __restrict__ a, size_t n, float v);
 //   rb_to_ff   pff = shift + psi, psi the FP32 red/black field of the first phase (one exact float-float add);
 //   update_ff  pff += e (minus its mean *emean for Poisson), FP32 instructions only;
 //   ff_to_f64  phi = base + (hi + lo), the FP64 field returned to the caller.
+// rb_to_ff and update_ff take one thread per four cells of a row (N^3/4 threads), ff_to_f64 one per two.
 __global__ void rb_to_ff(const float* __restrict__ psi, float2* __restrict__ pff, int lg, float2 shift);
 __global__ void update_ff(float2* __restrict__ pff, const float* __restrict__ e, int lg,
                           const float* __restrict__ emean);
@@ -759,7 +760,7 @@ isis_status solve_refine(const SolveArgs& A) {
     if (bg_start) {
       // f(R) and Poisson start at psi = 0 (u = u_bar, Phi = 0); the symmetron at fp32(chi_bg)
       const float v = M == SYM ? f32_cut(background_value<SYM>(c)) : 0.0f;
-      ISIS_LAUNCH(KK_INIT, 4.0 * n, st, (fill_f32<<<nblk(n, 256), 256, 0, st>>>(B0, n, v)));
+      ISIS_LAUNCH(KK_INIT, 4.0 * n, st, (fill_f32<<<nblk(n / 4, 256), 256, 0, st>>>(B0, n, v)));
       return ISIS_OK;
     }
     if (M == FOFR)
@@ -846,7 +847,7 @@ isis_status solve_refine(const SolveArgs& A) {
       shift = ff_split_host(-((double*)ws->host)[1] / (double)n);
     }
     ISIS_LAUNCH(KK_SETUP, 12.0 * n, st,
-                (rb_to_ff<<<nblk(n, 256), 256, 0, st>>>(psi, reinterpret_cast<float2*>(ws->b64), lg, shift)));
+                (rb_to_ff<<<nblk(n / 4, 256), 256, 0, st>>>(psi, reinterpret_cast<float2*>(ws->b64), lg, shift)));
   }
 
   // ---- phase 2: FP64 defect correction around FP32 correction cycles ----
@@ -954,11 +955,11 @@ isis_status solve_refine(const SolveArgs& A) {
       ISIS_LAUNCH(KK_REDUCE, 0.0, st, (mean_to_f32<<<1, 32, 0, st>>>(ws->scal + 1, 1.0 / (double)n, mf)));
       emean = mf;
     }
-    ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_ff<<<nblk(n, 256), 256, 0, st>>>(carry, ecur, lg, emean)));
+    ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_ff<<<nblk(n / 4, 256), 256, 0, st>>>(carry, ecur, lg, emean)));
   }
   // the carried field to the caller: phi = hi + lo (f(R): u = u_bar + psi), in FP64
   ISIS_LAUNCH(KK_UPDATE, 16.0 * n, st,
-              (ff_to_f64<<<nblk(n, 256), 256, 0, st>>>(reinterpret_cast<const float2*>(ws->b64), phi64, n,
+              (ff_to_f64<<<nblk(n / 2, 256), 256, 0, st>>>(reinterpret_cast<const float2*>(ws->b64), phi64, n,
                                                        M == FOFR ? u0 : 0.0)));
   if (A.info) *A.info = loc;
   return out;
