@@ -20,21 +20,32 @@ namespace isis {
 
 constexpr int kCoarseMax = 64;
 
-// Shared scratch of the dense Newton solve.
-struct NewtonScratch {
-  double J[kCoarseMax][kCoarseMax + 1];
-  double b[kCoarseMax], xs[kCoarseMax], Bs[kCoarseMax], ws[kCoarseMax], etas[kCoarseMax], sigs[kCoarseMax];
-  double wmax[2];
+// Shared scratch of the dense Newton solve.  LU: the type of the Jacobian, the step and its factorisation; the
+// iterate and the residual are FP64 whatever LU is.
+template <class LU>
+struct NewtonScratchT {
+  LU J[kCoarseMax][kCoarseMax + 1];
+  LU b[kCoarseMax];
+  double xs[kCoarseMax], Bs[kCoarseMax], ws[kCoarseMax], etas[kCoarseMax], sigs[kCoarseMax];
+  double as[kCoarseMax];  // f(R): the per-cell exponential of the iterate (aux_of), once per cell and step
+  LU wmax[2];
   int wpiv[2];
   int done, bad;
 };
+using NewtonScratch = NewtonScratchT<double>;
 
 // Dense Newton on the n = N^3 unknowns held in S.xs (with S.etas, S.sigs, S.Bs, S.ws = e^B); every thread of
 // the block calls it, threads 0..n-1 own the rows (blockDim.x >= n, at most kCoarseMax rows).  Row-major
 // unknown r = (i N + j) N + k.  On return S.xs holds the solution, S.bad the flags 1 (singular pivot) and
 // 2 (non-finite step), S.done whether the stop rule was met; the return value is the number of steps.
-template <Model M, Form FM>
-__device__ int dense_newton_block(NewtonScratch& S, int lg, double ih2, const Coef& c) {
+// LU = float (the FP32 V-cycles): F(x) and x stay FP64, so the stop rule means the same, while the step comes
+// from an FP32 factorisation of the FP32-rounded Jacobian.  That makes each step a Newton step with an
+// inexact linear solve (the error contracts by about cond(J) 2^-24 per step on top of Newton's quadratic
+// rate; an FP64 iterative refinement of the step, in effect) at FP32 instruction cost: FP64 instructions run
+// on a narrow pipe on this part, and the FP64 factorisation took about 30 us per step of an 8-unknown
+// system in one CTA.
+template <Model M, Form FM, class LU = double>
+__device__ int dense_newton_block(NewtonScratchT<LU>& S, int lg, double ih2, const Coef& c) {
   const int n = 1 << (3 * lg), N = 1 << lg, r = threadIdx.x;
   const int i = r >> (2 * lg), j = (r >> lg) & (N - 1), k = r & (N - 1);
   if (r == 0) { S.done = 0; S.bad = 0; }
@@ -50,52 +61,62 @@ __device__ int dense_newton_block(NewtonScratch& S, int lg, double ih2, const Co
   }
   int it = 0;
   for (; it < 50; ++it) {
+    if constexpr (M == FOFR) {  // each cell's exponential once (FP64 exponentials are costly here)
+      if (r < n) S.as[r] = aux_of<M, FM, double>(S.xs[r], S.ws[r]);
+      __syncthreads();
+    }
     // Jacobian row r and right-hand side -F_r
     if (r < n) {
       Cell<double> q;
       q.x = S.xs[r]; q.eta = S.etas[r]; q.sig = S.sigs[r]; q.B = S.Bs[r]; q.w = S.ws[r];
 #pragma unroll
       for (int d = 0; d < 6; ++d) { q.xn[d] = S.xs[nb[d]]; q.Bn[d] = S.Bs[nb[d]]; q.wn[d] = S.ws[nb[d]]; }
-      q.a = aux_of<M, FM, double>(q.x, q.w);
+      if constexpr (M == FOFR) {
+        q.a = S.as[r];
 #pragma unroll
-      for (int d = 0; d < 6; ++d) q.an[d] = aux_of<M, FM, double>(q.xn[d], q.wn[d]);
+        for (int d = 0; d < 6; ++d) q.an[d] = S.as[nb[d]];
+      } else {
+        q.a = 0.0;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) q.an[d] = 0.0;
+      }
       double F, dF;
       eval_cell<M, FM, double>(c, ih2, q, F, dF);
-      double shift = (M == POI) ? 6.0 * ih2 / (double)n : 0.0;
-      for (int cc = 0; cc < n; ++cc) S.J[r][cc] = -shift;
-      S.J[r][r] += dF;
+      const double shift = (M == POI) ? 6.0 * ih2 / (double)n : 0.0;
+      for (int cc = 0; cc < n; ++cc) S.J[r][cc] = (LU)(-shift);
+      S.J[r][r] = (LU)(dF - shift);
 #pragma unroll
-      for (int d = 0; d < 6; ++d) S.J[r][nb[d]] += eval_offdiag<M, FM>(c, ih2, q, d);
-      S.b[r] = -F;
+      for (int d = 0; d < 6; ++d) S.J[r][nb[d]] += (LU)eval_offdiag<M, FM>(c, ih2, q, d);
+      S.b[r] = (LU)(-F);
     }
     __syncthreads();
     // LU with partial pivoting; the pivot is the first largest |J[p][kk]|, p >= kk (warps 0 and 1)
     for (int kk = 0; kk < n; ++kk) {
-      double v = (r >= kk && r < n) ? fabs(S.J[r][kk]) : -1.0;
+      LU v = (r >= kk && r < n) ? (LU)fabs(S.J[r][kk]) : (LU)(-1);
       int p = r;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        double v2 = __shfl_down_sync(0xffffffffu, v, o);
+        LU v2 = __shfl_down_sync(0xffffffffu, v, o);
         int p2 = __shfl_down_sync(0xffffffffu, p, o);
         if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
       }
       if (r < kCoarseMax && (r & 31) == 0) { S.wmax[r >> 5] = v; S.wpiv[r >> 5] = p; }
       __syncthreads();
       int piv = S.wpiv[0];
-      double best = S.wmax[0];
+      LU best = S.wmax[0];
       if (n > 32 && (S.wmax[1] > best)) { best = S.wmax[1]; piv = S.wpiv[1]; }
-      if (!(best > 0.0)) {
+      if (!(best > (LU)0)) {
         if (r == 0) S.bad |= 1;
         __syncthreads();
         break;
       }
       if (piv != kk && r < n) {
-        double t = S.J[kk][r]; S.J[kk][r] = S.J[piv][r]; S.J[piv][r] = t;
-        if (r == 0) { double tb = S.b[kk]; S.b[kk] = S.b[piv]; S.b[piv] = tb; }
+        LU t = S.J[kk][r]; S.J[kk][r] = S.J[piv][r]; S.J[piv][r] = t;
+        if (r == 0) { LU tb = S.b[kk]; S.b[kk] = S.b[piv]; S.b[piv] = tb; }
       }
       __syncthreads();
       if (r > kk && r < n) {
-        double m = S.J[r][kk] / S.J[kk][kk];
+        LU m = S.J[r][kk] / S.J[kk][kk];
         S.J[r][kk] = m;
         for (int cc = kk + 1; cc < n; ++cc) S.J[r][cc] -= m * S.J[kk][cc];
         S.b[r] -= m * S.b[kk];
@@ -105,20 +126,20 @@ __device__ int dense_newton_block(NewtonScratch& S, int lg, double ih2, const Co
     if (S.bad) break;
     if (r == 0) {
       for (int rr = n - 1; rr >= 0; --rr) {
-        double s = S.b[rr];
+        LU s = S.b[rr];
         for (int cc = rr + 1; cc < n; ++cc) s -= S.J[rr][cc] * S.b[cc];
         S.b[rr] = s / S.J[rr][rr];
       }
       if (M == POI) {
-        double m = 0.0;
+        LU m = 0;
         for (int rr = 0; rr < n; ++rr) m += S.b[rr];
-        m /= (double)n;
+        m /= (LU)n;
         for (int rr = 0; rr < n; ++rr) S.b[rr] -= m;
       }
       double dmax = 0.0, xmax = 0.0;
       for (int rr = 0; rr < n; ++rr) {
-        S.xs[rr] += S.b[rr];
-        dmax = fmax(dmax, fabs(S.b[rr]));
+        S.xs[rr] += (double)S.b[rr];
+        dmax = fmax(dmax, fabs((double)S.b[rr]));
         xmax = fmax(xmax, fabs(S.xs[rr]));
       }
       if (!isfinite(dmax) || !isfinite(xmax)) S.bad |= 2;
@@ -131,7 +152,8 @@ __device__ int dense_newton_block(NewtonScratch& S, int lg, double ih2, const Co
 }
 
 // Status of a dense Newton solve in the flag bits below.
-__device__ __forceinline__ int newton_flags(const NewtonScratch& S) { return S.bad ? S.bad : (S.done ? 0 : 4); }
+template <class LU>
+__device__ __forceinline__ int newton_flags(const NewtonScratchT<LU>& S) { return S.bad ? S.bad : (S.done ? 0 : 4); }
 
 // status bits written to *flags (OR-ed): 1 = singular pivot, 2 = non-finite step, 4 = no step met the stop
 // rule within the 50 steps
@@ -230,7 +252,7 @@ template <Model M, Form FM>
 __global__ void __launch_bounds__(kCVThreads, 1) coarse_cycle(CoarseCycle cc, Coef c, CoefT<float> cf, int* flags,
                                                            int* steps_max) {
   extern __shared__ float4 cv_dyn[];
-  __shared__ NewtonScratch NS;
+  __shared__ NewtonScratchT<float> NS;
   float* sm = reinterpret_cast<float*>(cv_dyn);
   SmemLevel S[kCVMaxLev];
   for (int l = 0; l < cc.nlev; ++l) {
@@ -308,7 +330,7 @@ __global__ void __launch_bounds__(kCVThreads, 1) coarse_cycle(CoarseCycle cc, Co
       NS.Bs[r] = (FM == DELTA && M != POI) ? (double)C.B[r] : 0.0;
       NS.ws[r] = (FM == DELTA && M == FOFR) ? (double)dexp<float>(C.B[r]) : 0.0;
     }
-    const int it = dense_newton_block<M, FM>(NS, C.lg, (double)C.ih2, c);
+    const int it = dense_newton_block<M, FM, float>(NS, C.lg, (double)C.ih2, c);
     if (r < n) C.x[r] = (float)NS.xs[r];
     if (r == 0) {
       const int f = newton_flags(NS);

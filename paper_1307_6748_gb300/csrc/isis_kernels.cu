@@ -233,16 +233,18 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, F
   __shared__ float2 stab[64];
   if (threadIdx.x < 64) stab[threadIdx.x] = tab[threadIdx.x];
   __syncthreads();
-  const size_t np = (size_t)1 << (3 * lg - 1), half = np;
-  const int m = (1 << lg) - 1;
+  // 32-bit positions: N <= 1024, so N^3 <= 2^30
+  const unsigned np = 1u << (3 * lg - 1), half = np, m = (1u << lg) - 1u;
   const ff2 Cih2 = ff2_bc(c.Cih2), K1 = ff2_bc(c.K1), Kx = ff2_bc(c.Kx), minv = ff2_bc(c.minv);
+  const float2 ub = c.ubff;
   float acc = 0.f;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t q = 2 * t;
-    const int k = (int)(q & m), j = (int)((q >> lg) & m), i = (int)(q >> (2 * lg));
-    const size_t pq[4] = {cidx(lg, (i + 1) & m, j, k), cidx(lg, (i - 1) & m, j, k), cidx(lg, i, (j + 1) & m, k),
-                          cidx(lg, i, (j - 1) & m, k)};
-    const size_t qm = cidx(lg, i, j, (k - 1) & m), qp = cidx(lg, i, j, (k + 2) & m);
+  auto cid = [&](unsigned i, unsigned j, unsigned k) { return (((i << lg) | j) << lg) | k; };
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < np; t += gridDim.x * blockDim.x) {
+    const unsigned q = 2 * t;
+    const unsigned k = q & m, j = (q >> lg) & m, i = q >> (2 * lg);
+    const unsigned pq[4] = {cid((i + 1) & m, j, k), cid((i - 1) & m, j, k), cid(i, (j + 1) & m, k),
+                            cid(i, (j - 1) & m, k)};
+    const unsigned qm = cid(i, j, (k - 1) & m), qp = cid(i, j, (k + 2) & m);
     const ff2 pc = ff2_pair(psi, q), ec = ff2_pair(E, q);
     // the six neighbour pairs (i+1, i-1, j+1, j-1, k+1, k-1) of psi and of e^psi
     auto nbr = [&](const float2* __restrict__ a, const ff2& own, int d) -> ff2 {
@@ -254,14 +256,25 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, F
       const float2 v = a[qm];
       return ff2{make_float2(v.x, own.hi.x), make_float2(v.y, own.lo.x)};
     };
+    // sd = sum dp, se = sum e^psi_nb dp with dp = psi_nb - psi: every high part goes through an exact two-sum
+    // (or two-product), the low parts and rounding errors are summed in FP32, and each sum is normalised once
+    // at the end.  Absolute accuracy about 2^-48 of the terms, as the residual needs (its terms cancel).
     ff2 sd = {f2_bc(0.f), f2_bc(0.f)}, se = sd;
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
-      const ff2 dp = ff2_add_abs(nbr(psi, pc, d), ff2_neg(pc));
-      sd = ff2_add_abs(sd, dp);
-      se = ff2_add_abs(se, ff2_mul(nbr(E, ec, d), dp));
+      const ff2 pn = nbr(psi, pc, d), en = nbr(E, ec, d);
+      ff2 dp = ff2_two_sum(pn.hi, make_float2(-pc.hi.x, -pc.hi.y));
+      dp.lo = f2_add(dp.lo, f2_sub(pn.lo, pc.lo));
+      const ff2 ts = ff2_two_sum(sd.hi, dp.hi);
+      sd = {ts.hi, f2_add(f2_add(sd.lo, dp.lo), ts.lo)};
+      ff2 pr = ff2_two_prod(en.hi, dp.hi);
+      pr.lo = f2_fma(en.hi, dp.lo, f2_fma(en.lo, dp.hi, pr.lo));
+      const ff2 te = ff2_two_sum(se.hi, pr.hi);
+      se = {te.hi, f2_add(f2_add(se.lo, pr.lo), te.lo)};
     }
-    ff2 flux = ff2_add(ff2_mul(ec, sd), se);
+    sd = ff2_quick_two_sum(sd.hi, sd.lo);
+    se = ff2_quick_two_sum(se.hi, se.lo);
+    ff2 flux = ff2_add_abs(ff2_mul(ec, sd), se);
     flux = {f2_mul(f2_bc(0.5f), flux.hi), f2_mul(f2_bc(0.5f), flux.lo)};
     ff2 em = ff2_add_f(exp_ff2(ff2_mul(pc, minv), stab, c.ek), f2_bc(-1.0f));
     if (!(fabsf(pc.hi.x) < 20.0f)) {
@@ -275,13 +288,16 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, F
       em.lo.y = v.lo;
     }
     const ff2 et = ff2_pack(ff_split_bits(eta[q]), ff_split_bits(eta[q + 1]));  // the caller's array
-    ff2 S = ff2_sub(ff2_mul(K1, ff2_add_f(et, f2_bc(-1.0f))), ff2_mul(Kx, em));
+    // S and F = flux C - S by Dekker's addition (absolute accuracy: F is small against its terms)
+    ff2 S = ff2_add_abs(ff2_mul(K1, ff2_add_f(et, f2_bc(-1.0f))), ff2_neg(ff2_mul(Kx, em)));
     S = ff2_add_f(S, f2_bc(c.dK));
-    const ff2 F = ff2_sub(ff2_mul(flux, Cih2), S);
+    const ff2 F = ff2_add_abs(ff2_mul(flux, Cih2), ff2_neg(S));
     const float2 r = f2_add(F.hi, F.lo);
-    const float2 B = ff2_add(pc, ff2_bc(c.ubff)).hi;  // fp32(u), u = psi + ub
+    // the base field of the correction cycles: u = psi + ub to FP32 (within an FP32 ulp of u; the cycles'
+    // linearisation point, not part of the residual)
+    const float2 B = f2_add(f2_add(pc.hi, f2_bc(ub.x)), f2_add(pc.lo, f2_bc(ub.y)));
     // cell k has colour (i + j + k) & 1, cell k + 1 the other; both at place q / 2 of their half
-    const size_t o0 = (((size_t)(i + j) & 1u) ? half : 0) + t, o1 = (((size_t)(i + j) & 1u) ? 0 : half) + t;
+    const unsigned o0 = (((i + j) & 1u) ? half : 0u) + t, o1 = (((i + j) & 1u) ? 0u : half) + t;
     r32[o0] = -r.x;
     r32[o1] = -r.y;
     B32[o0] = B.x;
