@@ -104,6 +104,53 @@ __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned e = ef == 0xFFu ? 0x7FFu : ef - 127u + 1023u;
   return __hiloint2double((int)(sgn | (e << 20) | (man >> 3)), (int)(man << 29));
 }
+// A normalised float-float value hi + lo (|lo| <= ulp(hi)/2) to FP64, rounded to nearest even as one FP64
+// addition of the two would round it, by integer operations (an FP64 addition runs on the narrow FP64 pipe).
+// The exact sum is formed in a 64-bit integer in units of 2^(e_hi - 189): |hi| at bits 39..62, |lo| shifted by
+// the exponent gap (bits shifted out only set a sticky flag), then cut to 53 bits.  hi zero, subnormal, Inf or
+// NaN, and lo zero or subnormal, give f2d_bits(hi) (the flush of f2d_bits); a pair that is not normalised
+// (exponent gap < 24) takes the FP64 addition.
+__device__ __forceinline__ double ff_to_double_bits(float hi, float lo) {
+  const unsigned uh = __float_as_uint(hi), ul = __float_as_uint(lo);
+  const int eh = (int)((uh >> 23) & 0xFFu), el = (int)((ul >> 23) & 0xFFu);
+  if (eh == 0 || eh == 0xFF || el == 0) return f2d_bits(hi);
+  const int gap = eh - el;
+  if (gap < 24) return f2d_bits(hi) + f2d_bits(lo);
+  const unsigned long long H = (unsigned long long)((uh & 0x7FFFFFu) | 0x800000u);
+  const unsigned long long L = (unsigned long long)((ul & 0x7FFFFFu) | 0x800000u);
+  unsigned long long A = H << 39, Lp;
+  bool sticky;
+  const int sh = 39 - gap;  // <= 15
+  if (sh >= 0) {
+    Lp = L << sh;
+    sticky = false;
+  } else if (sh > -24) {
+    Lp = L >> (-sh);
+    sticky = (L & ((1ull << (-sh)) - 1ull)) != 0ull;
+  } else {
+    Lp = 0ull;
+    sticky = true;
+  }
+  if ((uh ^ ul) & 0x80000000u) {
+    A -= Lp;
+    if (sticky) A -= 1ull;  // the exact value lies strictly between A and A + 1
+  } else {
+    A += Lp;
+  }
+  // A in [2^61, 2^63): keep 53 bits
+  const int shift = (A >> 62) ? 10 : 9;
+  unsigned long long M = A >> shift;
+  const unsigned long long rem = A & ((1ull << shift) - 1ull), halfu = 1ull << (shift - 1);
+  if (rem > halfu || (rem == halfu && (sticky || (M & 1ull)))) ++M;
+  int E = eh - 127 + (shift - 10);  // unbiased exponent of the result
+  if (M >> 53) {
+    M >>= 1;
+    ++E;
+  }
+  const unsigned long long bits = ((unsigned long long)(uh & 0x80000000u) << 32) |
+                                  ((unsigned long long)(E + 1023) << 52) | (M & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
 __device__ __forceinline__ ff ff_load(const float2& v) { return {v.x, v.y}; }
 __device__ __forceinline__ float2 ff_store(ff a) { return make_float2(a.hi, a.lo); }
 

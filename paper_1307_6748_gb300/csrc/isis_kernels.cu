@@ -79,14 +79,16 @@ __global__ void update_ff(float2* __restrict__ pff, const float* __restrict__ e,
   io[1] = make_float4(c.x, c.y, d.x, d.y);
 }
 
-// Two cells per thread (n even): one 16-byte load, one 16-byte store.
-__global__ void ff_to_f64(const float2* __restrict__ pff, double* __restrict__ phi, size_t n, double base) {
+// Two cells per thread (n even): one 16-byte load, one 16-byte store.  The float-float value goes to FP64 by
+// integer operations (ff_to_double_bits, the rounding of one FP64 addition); f(R) then adds its background in
+// one FP64 addition (has_base).
+__global__ void ff_to_f64(const float2* __restrict__ pff, double* __restrict__ phi, size_t n, double base,
+                          int has_base) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * t >= n) return;
   const float4 v = reinterpret_cast<const float4*>(pff)[t];
-  // the float-float values (one rounding at most)
-  double d0 = f2d_bits(v.x) + f2d_bits(v.y), d1 = f2d_bits(v.z) + f2d_bits(v.w);
-  if (base != 0.0) {
+  double d0 = ff_to_double_bits(v.x, v.y), d1 = ff_to_double_bits(v.z, v.w);
+  if (has_base) {
     d0 += base;
     d1 += base;
   }

@@ -438,7 +438,8 @@ __global__ void fill_f32(float* __restrict__ a, size_t n, float v);
 __global__ void rb_to_ff(const float* __restrict__ psi, float2* __restrict__ pff, int lg, float2 shift);
 __global__ void update_ff(float2* __restrict__ pff, const float* __restrict__ e, int lg,
                           const float* __restrict__ emean);
-__global__ void ff_to_f64(const float2* __restrict__ pff, double* __restrict__ phi, size_t n, double base);
+__global__ void ff_to_f64(const float2* __restrict__ pff, double* __restrict__ phi, size_t n, double base,
+                          int has_base);
 // f(R): e^psi (float-float) of the carried psi = u - u_bar, two cells per thread (n even)
 __global__ void fofr_exp_ff(const float2* __restrict__ psi, float2* __restrict__ E, size_t n,
                             const float2* __restrict__ tab, FFExp ek);
@@ -504,40 +505,51 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_ff(int lg, ResFF 
                                                                   const float2* __restrict__ pff,
                                                                   float* __restrict__ r32, float* __restrict__ B32,
                                                                   double* __restrict__ part) {
-  const size_t np = (size_t)1 << (3 * lg - 1);
-  const int m = (1 << lg) - 1;
-  const size_t half = np;
+  // 32-bit positions: N <= 1024, so N^3 <= 2^30
+  const unsigned np = 1u << (3 * lg - 1), half = np, m = (1u << lg) - 1u;
   const ff2 ih2 = ff2_bc(c.ih2), K = ff2_bc(c.K);
   float acc = 0.f;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < np; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t q = 2 * t;
-    const int k = (int)(q & m), j = (int)((q >> lg) & m), i = (int)(q >> (2 * lg));
-    auto pair = [&](size_t at) {
+  auto cid = [&](unsigned i, unsigned j, unsigned k) { return (((i << lg) | j) << lg) | k; };
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < np; t += gridDim.x * blockDim.x) {
+    const unsigned q = 2 * t;
+    const unsigned k = q & m, j = (q >> lg) & m, i = q >> (2 * lg);
+    auto pair = [&](unsigned at) {
       const float4 v = *reinterpret_cast<const float4*>(pff + at);
       return ff2{make_float2(v.x, v.z), make_float2(v.y, v.w)};
     };
     const ff2 pc = pair(q);
-    const float2 km = pff[cidx(lg, i, j, (k - 1) & m)], kp = pff[cidx(lg, i, j, (k + 2) & m)];
-    const ff2 nb[6] = {pair(cidx(lg, (i + 1) & m, j, k)), pair(cidx(lg, (i - 1) & m, j, k)),
-                       pair(cidx(lg, i, (j + 1) & m, k)), pair(cidx(lg, i, (j - 1) & m, k)),
+    const float2 km = pff[cid(i, j, (k - 1) & m)], kp = pff[cid(i, j, (k + 2) & m)];
+    const ff2 nb[6] = {pair(cid((i + 1) & m, j, k)), pair(cid((i - 1) & m, j, k)),
+                       pair(cid(i, (j + 1) & m, k)), pair(cid(i, (j - 1) & m, k)),
                        ff2{make_float2(pc.hi.y, kp.x), make_float2(pc.lo.y, kp.y)},   // k + 1
                        ff2{make_float2(km.x, pc.hi.x), make_float2(km.y, pc.lo.x)}};  // k - 1
+    // sd = sum (phi_nb - phi): each difference's high parts by an exact two-sum, the sum's high parts by
+    // two-sums, low parts and rounding errors summed in FP32, normalised once (absolute accuracy about 2^-48
+    // of the differences)
     ff2 sd = {f2_bc(0.f), f2_bc(0.f)};
+    const float2 mh = make_float2(-pc.hi.x, -pc.hi.y);
 #pragma unroll
-    for (int d = 0; d < 6; ++d) sd = ff2_add_abs(sd, ff2_add_abs(nb[d], ff2_neg(pc)));
+    for (int d = 0; d < 6; ++d) {
+      ff2 dp = ff2_two_sum(nb[d].hi, mh);
+      dp.lo = f2_add(dp.lo, f2_sub(nb[d].lo, pc.lo));
+      const ff2 ts = ff2_two_sum(sd.hi, dp.hi);
+      sd = {ts.hi, f2_add(f2_add(sd.lo, dp.lo), ts.lo)};
+    }
+    sd = ff2_quick_two_sum(sd.hi, sd.lo);
     const ff2 lap = ff2_mul(sd, ih2);
     const ff2 et = ff2_pack(ff_split_bits(eta[q]), ff_split_bits(eta[q + 1]));  // the caller's array: 8-byte loads
+    // F by Dekker's addition: absolute accuracy, F being small against its terms
     ff2 F;
     if constexpr (M == POI) {
-      F = ff2_sub(lap, ff2_mul(K, ff2_sub(et, ff2_bc(c.eta_mean))));
+      F = ff2_add_abs(lap, ff2_neg(ff2_mul(K, ff2_add_abs(et, ff2_neg(ff2_bc(c.eta_mean))))));
     } else {  // symmetron: L = lap - A [(s eta - 1) chi + chi^3]
       const ff2 qv = ff2_add_f(ff2_mul(ff2_bc(c.s), et), f2_bc(-1.0f));
       const ff2 x2 = ff2_mul(pc, pc);
-      F = ff2_sub(lap, ff2_mul(K, ff2_mul(ff2_add(qv, x2), pc)));
+      F = ff2_add_abs(lap, ff2_neg(ff2_mul(K, ff2_mul(ff2_add_abs(qv, x2), pc))));
     }
     const float2 r = f2_add(F.hi, F.lo);
     // cell k has colour (i + j + k) & 1, cell k + 1 the other; both at place q / 2 of their half
-    const size_t o0 = (((size_t)(i + j) & 1u) ? half : 0) + t, o1 = (((size_t)(i + j) & 1u) ? 0 : half) + t;
+    const unsigned o0 = (((i + j) & 1u) ? half : 0u) + t, o1 = (((i + j) & 1u) ? 0u : half) + t;
     r32[o0] = -r.x;
     r32[o1] = -r.y;
     B32[o0] = pc.hi.x;
@@ -960,7 +972,7 @@ isis_status solve_refine(const SolveArgs& A) {
   // the carried field to the caller: phi = hi + lo (f(R): u = u_bar + psi), in FP64
   ISIS_LAUNCH(KK_UPDATE, 16.0 * n, st,
               (ff_to_f64<<<nblk(n / 2, 256), 256, 0, st>>>(reinterpret_cast<const float2*>(ws->b64), phi64, n,
-                                                       M == FOFR ? u0 : 0.0)));
+                                                           M == FOFR ? u0 : 0.0, M == FOFR ? 1 : 0)));
   if (A.info) *A.info = loc;
   return out;
 }
