@@ -768,6 +768,26 @@ __global__ void __launch_bounds__(256) resid_restrict2(LevelView<float> F, CoefT
   }
 }
 
+// Sigma_H += L_H(x_H) on a red/black FP32 level (the FAS coarse source, Sect. 3.2): two cells per thread through
+// the smoother's gather and evaluation (threads [0, N^3/4) red, then black; N >= 4).  sig is the level's own
+// Sigma array, read and written here only.
+template <Model M, Form FM>
+__global__ void __launch_bounds__(256) sigma_rb2(LevelView<float> L, CoefT<float> c, float* __restrict__ sig) {
+  const unsigned q4 = 1u << (3 * L.lg - 2);
+  unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lanes = __ballot_sync(0xffffffffu, t < 2 * q4);  // blocks of whole warps
+  if (t >= 2 * q4) return;
+  const int color = t >= q4 ? 1 : 0;
+  t -= color ? q4 : 0u;
+  L.sig = nullptr;  // L(x) itself
+  Cell<float> q0, q1;
+  float2 F, dF;
+  const unsigned o = rb2_eval<M, FM>(L, c, color, t, lanes, q0, q1, F, dF);
+  float2* sp = reinterpret_cast<float2*>(sig + o);
+  const float2 v = *sp;
+  *sp = make_float2(v.x + F.x, v.y + F.y);
+}
+
 // Sigma_H += L_H(x_H) (the FAS coarse source, Sect. 3.2).
 template <Model M, Form FM, class T>
 __global__ void coarse_sigma_add(LevelView<T> L, CoefT<T> c, T* __restrict__ sig) {

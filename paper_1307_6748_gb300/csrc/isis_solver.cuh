@@ -270,8 +270,13 @@ struct Cycler {
                     (resid_restrict<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], c, C, (T*)ws->x0[l + 1],
                                                                             (T*)ws->sig[l + 1])));
     }
-    ISIS_LAUNCH(tk(KK_SIGMA), sizeof(T) * ncd * (2 + arrays(true)), st,
-                (coarse_sigma_add<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(C, c, (T*)ws->sig[l + 1])));
+    if constexpr (sizeof(T) == 4) {
+      ISIS_LAUNCH(tk(KK_SIGMA), sizeof(T) * ncd * (2 + arrays(true)), st,
+                  (sigma_rb2<M, FM><<<nblk(nc / 2, 256), 256, 0, st>>>(C, c, (float*)ws->sig[l + 1])));
+    } else {
+      ISIS_LAUNCH(tk(KK_SIGMA), sizeof(T) * ncd * (2 + arrays(true)), st,
+                  (coarse_sigma_add<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(C, c, (T*)ws->sig[l + 1])));
+    }
     s = vcycle(l + 1);
     if (s != ISIS_OK) return s;
     s = prolong(l);
@@ -806,6 +811,14 @@ isis_status solve_refine(const SolveArgs& A) {
         if (s != ISIS_OK) return s;
         loc.cycles += 1;
         if (loc.cycles >= A.max_cycles) break;
+        if (handover < 1e-3 * ref) {
+          // and a V(2,1) cycle contracts it by about 0.1: a second V-cycle follows without a norm as well (the
+          // check of the start below then comes one cycle later)
+          s = cy.vcycle(0);
+          if (s != ISIS_OK) return s;
+          loc.cycles += 1;
+          if (loc.cycles >= A.max_cycles) break;
+        }
       }
       s = cy.vcycle(0);
       if (s != ISIS_OK) return s;
