@@ -597,6 +597,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !(M == FOFR && FM == D
   T* __restrict__ xc = C.x;
   const int lgc = F.lg - 1, lg = F.lg, m = F.N - 1;
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lanes = __ballot_sync(0xffffffffu, t < ((size_t)1 << (3 * lgc)));  // blocks of whole warps
   if (t >= ((size_t)1 << (3 * lgc))) return;
   // threads in row-major coarse order: neighbouring threads touch neighbouring fine cells
   const int mc = (1 << lgc) - 1;
@@ -628,6 +629,42 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !(M == FOFR && FM == D
       }
     }
   T xs = 0, rs = 0;
+  if constexpr (M == FOFR && FM == FIELD && sizeof(T) == 4) {
+    // the f(R) field form in packed FP32x2: the children k = 2K, 2K+1 of each (i, j) row as the two lanes
+    // (the algebra of fofr_pair_eval, with the loaded cells' exponentials)
+    const float2 half = bc(0.5f), fs = bc(c.fscale), ih2 = bc(F.ih2);
+    float2 xs2 = bc(0.f), rs2 = bc(0.f);
+#pragma unroll
+    for (int a = 1; a < 3; ++a)
+#pragma unroll
+      for (int b = 1; b < 3; ++b) {
+        const float2 x2 = pk(X[a][b][1], X[a][b][2]), ex2 = pk(Ax[a][b][1], Ax[a][b][2]);
+        const float2 xn[6] = {pk(X[a + 1][b][1], X[a + 1][b][2]), pk(X[a - 1][b][1], X[a - 1][b][2]),
+                              pk(X[a][b + 1][1], X[a][b + 1][2]), pk(X[a][b - 1][1], X[a][b - 1][2]),
+                              pk(X[a][b][2], X[a][b][3]), pk(X[a][b][0], X[a][b][1])};
+        const float2 en[6] = {pk(Ax[a + 1][b][1], Ax[a + 1][b][2]), pk(Ax[a - 1][b][1], Ax[a - 1][b][2]),
+                              pk(Ax[a][b + 1][1], Ax[a][b + 1][2]), pk(Ax[a][b - 1][1], Ax[a][b - 1][2]),
+                              pk(Ax[a][b][2], Ax[a][b][3]), pk(Ax[a][b][0], Ax[a][b][1])};
+        float2 sdu = bc(0.f), sexdu = bc(0.f);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+          const float2 du = sub2(xn[d], x2);
+          sdu = add2(sdu, du);
+          sexdu = fma2(en[d], du, sexdu);
+        }
+        const float2 flux = mul2(fs, fma2(mul2(half, ex2), sdu, mul2(half, sexdu)));
+        const float2 em = expm1_2w(lanes, mul2(x2, bc(-c.inv_np1)));
+        const float2 eta2 = pk(F.eta[P[a][b][1]], F.eta[P[a][b][2]]);
+        const float2 sig2 = F.sig ? pk(F.sig[P[a][b][1]], F.sig[P[a][b][2]]) : bc(0.f);
+        const float2 S = add2(sub2(mul2(bc(c.K1), sub2(eta2, bc(1.0f))), mul2(bc(c.fKx), em)), bc(c.fK3x));
+        const float2 Fv = sub2(sub2(mul2(flux, ih2), S), sig2);
+        xs2 = add2(xs2, x2);
+        rs2 = sub2(rs2, Fv);  // r = Sigma - L(x)
+      }
+    xs = xs2.x + xs2.y;
+    rs = rs2.x + rs2.y;
+  } else {
+  (void)lanes;
 #pragma unroll
   for (int a = 1; a < 3; ++a)
 #pragma unroll
@@ -660,6 +697,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !(M == FOFR && FM == D
         xs += q.x;
         rs -= Fv;  // r = Sigma - L(x)
       }
+  }
   (void)Bx;
   (void)Wx;
   (void)Ax;
