@@ -365,6 +365,14 @@ isis_status isis_host_free(void* ptr);
  * |x| < 20.  x, y: device arrays of n doubles; stream ordered. */
 isis_status isis_selftest_exp_ff(const double* x, double* y, int n, void* stream);
 
+/* Self-test of the conversion that writes the carried float-float field back to FP64 at the end of a mixed
+ * solve: out[i] = hl[2i] + hl[2i+1] rounded to nearest even, as one FP64 addition of the two floats would give
+ * it, formed by integer operations; zero, subnormal, Inf and NaN high parts, and subnormal low parts, are
+ * flushed as the library's FP32-to-FP64 conversion flushes them (zero, subnormal: a signed zero).  The pair
+ * must be normalised (|lo| <= ulp(hi)/2) for the integer path; other pairs take an FP64 addition.  hl: device
+ * array of 2n floats, out: device array of n doubles; stream ordered. */
+isis_status isis_selftest_ff_to_f64(const float* hl, double* out, int n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -372,6 +372,15 @@ isis_status isis_selftest_exp_ff(const double* x, double* y, int n, void* stream
   return ISIS_OK;
 }
 
+isis_status isis_selftest_ff_to_f64(const float* hl, double* out, int n, void* stream) {
+  if (!hl || !out || n < 0) return ISIS_EINVAL;
+  if (n == 0) return ISIS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  ISIS_LAUNCH(KK_SETUP, 16.0 * n, st,
+              (selftest_ff_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(hl, out, n)));
+  return ISIS_OK;
+}
+
 int isis_prof_read(isis_prof_entry* out, int max) {
   cudaDeviceSynchronize();
   constexpr int kAll = KK_COUNT * kKindTags;

@@ -206,6 +206,12 @@ FFExp ff_exp_consts() {
   return k;
 }
 
+// out[t] = ff_to_double_bits(hl[2t], hl[2t+1]) (self-test of the FP64 write-back's conversion).
+__global__ void selftest_ff_to_f64(const float* __restrict__ hl, double* __restrict__ out, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = ff_to_double_bits(hl[2 * t], hl[2 * t + 1]);
+}
+
 // e^x of x[2t] and x[2t+1] as the two lanes of exp_ff2 (one thread per pair).
 __global__ void selftest_exp_ff(const double* __restrict__ x, double* __restrict__ y, int n,
                                 const float2* __restrict__ tab, FFExp ek) {

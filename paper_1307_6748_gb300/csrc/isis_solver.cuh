@@ -576,6 +576,7 @@ struct FofrFF {
 };
 __global__ void selftest_exp_ff(const double* __restrict__ x, double* __restrict__ y, int n,
                                 const float2* __restrict__ tab, FFExp ek);
+__global__ void selftest_ff_to_f64(const float* __restrict__ hl, double* __restrict__ out, int n);
 // second pass: r = -L(u) (written FP32, red/black), B = fp32(u), block partials of r^2
 __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, FofrFF c,
                                                                        const double* __restrict__ eta,

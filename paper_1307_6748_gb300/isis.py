@@ -27,7 +27,7 @@ H0_MPC = 1.0 / 2997.92458  # (Mpc/h)^-1 with c = 1
 # Every function the header declares (checked by the tests).
 EXPORTS = ("isis_cic_deposit", "isis_cic_deposit_noalloc", "isis_poisson_solve", "isis_scalar_solve", "isis_fifth_force",
            "isis_strerror", "isis_release_workspace", "isis_prof_enable", "isis_prof_reset", "isis_prof_read",
-           "isis_launch_count", "isis_selftest_exp_ff", "isis_kick_drift", "isis_patch_poisson_solve",
+           "isis_launch_count", "isis_selftest_exp_ff", "isis_selftest_ff_to_f64", "isis_kick_drift", "isis_patch_poisson_solve",
            "isis_patch_scalar_solve", "isis_background_field", "isis_host_alloc", "isis_host_free")
 ISIS_INIT_INPUT, ISIS_INIT_BACKGROUND, ISIS_INIT_LOCAL, ISIS_INIT_PARENT = 0, 1, 2, 3
 
@@ -409,6 +409,22 @@ def selftest_exp_ff(x: torch.Tensor) -> torch.Tensor:
     if st != 0:
         raise IsisError(st, strerror(st))
     return y
+
+
+def selftest_ff_to_f64(hl: torch.Tensor) -> torch.Tensor:
+    """FP64 values of float-float pairs (a CUDA float32 tensor of shape (n, 2): high, low) through the
+    library's integer conversion (self-test)."""
+    lib = load()
+    fn = lib.isis_selftest_ff_to_f64
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    hl = hl.contiguous()
+    out = torch.empty(hl.shape[0], dtype=torch.float64, device=hl.device)
+    st = fn(ctypes.c_void_p(hl.data_ptr()), ctypes.c_void_p(out.data_ptr()), hl.shape[0],
+            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != 0:
+        raise IsisError(st, strerror(st))
+    return out
 
 
 def isis_patch_poisson_solve(grid: Grid, a: float, patch: Patch, parent: torch.Tensor, flags: torch.Tensor,

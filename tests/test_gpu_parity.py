@@ -293,6 +293,41 @@ def test_refine64_large_matches_oracle(cuda_lib, model, N, fmg):
     assert rel <= 1e-9, rel
 
 
+def _ff_pairs(n, seed):
+    """Normalised float-float pairs (hi, lo) of random doubles over 60 decades, pairs whose exact sum needs more
+    than 53 bits (remainders below, at and above half a double ulp, both signs), and pairs with lo = 0."""
+    rng = np.random.default_rng(seed)
+    d = rng.standard_normal(n) * 10.0 ** rng.uniform(-30, 30, n)
+    hi = d.astype(np.float32)
+    lo = (d - hi.astype(np.float64)).astype(np.float32)
+    h2 = (rng.standard_normal(n) * 10.0 ** rng.uniform(-20, 20, n)).astype(np.float32)
+    k = rng.integers(-4, 5, n).astype(np.float64)
+    # lo = hi 2^-53 (1 + k 2^-20): around half an ulp of hi's FP64 value, k = 0 the exact tie
+    l2 = (h2.astype(np.float64) * 2.0 ** -53 * (1.0 + k * 2.0 ** -20)).astype(np.float32)
+    sgn = np.where(rng.random(n) < 0.5, -1.0, 1.0).astype(np.float32)
+    l2 = l2 * sgn
+    h3 = (rng.standard_normal(1000) * 1e3).astype(np.float32)
+    hl = np.concatenate([np.stack([hi, lo], 1), np.stack([h2, l2], 1),
+                         np.stack([h3, np.zeros_like(h3)], 1)]).astype(np.float32)
+    keep = np.abs(hl[:, 1].astype(np.float64)) <= np.spacing(np.abs(hl[:, 0])).astype(np.float64) / 2
+    return hl[keep]
+
+
+def test_ff_to_f64_matches_one_fp64_addition(cuda_lib):
+    """The integer FP64 write-back of a float-float value equals one FP64 addition of its two floats, bit for
+    bit (round to nearest even, ties included), with subnormal low parts flushed as the library flushes them."""
+    import torch
+    from paper_1307_6748_gb300 import isis
+    hl = _ff_pairs(400_000, 11)
+    assert len(hl) > 700_000
+    got = isis.selftest_ff_to_f64(torch.from_numpy(hl).cuda()).cpu().numpy()
+    lo = hl[:, 1].astype(np.float64)
+    lo = np.where(np.abs(lo) < 2.0 ** -126, 0.0, lo)
+    want = hl[:, 0].astype(np.float64) + lo
+    bad = got.view(np.int64) != want.view(np.int64)
+    assert not bad.any(), (int(bad.sum()), hl[bad][:3], got[bad][:3], want[bad][:3])
+
+
 def test_exp_ff_accuracy(cuda_lib):
     """The float-float exponential of the f(R) residual against CUDA's FP64 exp: relative error within
     the float-float rounding of its argument (about 2^-48 |x|) plus a few float-float ulps."""
