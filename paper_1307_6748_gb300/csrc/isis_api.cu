@@ -156,7 +156,7 @@ float* get_force_buf(int N) {
   for (auto& d : g_fgrid)
     if (d.N == N && d.device == dev) return (float*)d.acc;
   void* p = nullptr;
-  if (cudaMalloc(&p, (size_t)3 * N * N * N * sizeof(float)) != cudaSuccess) {
+  if (cudaMalloc(&p, (size_t)4 * N * N * N * sizeof(float)) != cudaSuccess) {  // float4 per cell
     cudaGetLastError();
     return nullptr;
   }

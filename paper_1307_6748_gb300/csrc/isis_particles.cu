@@ -96,10 +96,47 @@ __global__ void cic_scatter(const float* __restrict__ x, const float* __restrict
       }
 }
 
+// u 2^e2 rounded to FP64 as (double)u * 2^e2 rounds it (to nearest even, the power-of-two product exact), by
+// integer operations: the conversion and the multiply would run on the narrow FP64 pipe.  Normal results only
+// (e2 > -960 for the densities here).
+__device__ __forceinline__ double u64_scaled_to_double(unsigned long long u, int e2) {
+  if (u == 0ull) return 0.0;
+  const int top = 63 - __clzll((long long)u);  // position of the leading one
+  unsigned long long M;
+  int E = top + e2;
+  if (top <= 52) {
+    M = u << (52 - top);
+  } else {
+    const int sh = top - 52;
+    M = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (M & 1ull))) ++M;
+    if (M >> 53) {
+      M >>= 1;
+      ++E;
+    }
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(E + 1023) << 52) | (M & 0xFFFFFFFFFFFFFull)));
+}
+
+// eta = acc * scale.  pow2 != 0: scale = 2^e2 exactly (the particle count is the cell count times a power of
+// two, the usual PM set-up), converted by integer operations, bit for bit the FP64 result.
 template <class T>
-__global__ void cic_finish(const unsigned long long* __restrict__ acc, T* __restrict__ eta, size_t n, double scale) {
+__global__ void cic_finish(const unsigned long long* __restrict__ acc, T* __restrict__ eta, size_t n, double scale,
+                           int pow2, int e2) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) eta[t] = (T)((double)acc[t] * scale);
+  if (t >= n) return;
+  if (sizeof(T) == 8 && pow2) eta[t] = (T)u64_scaled_to_double(acc[t], e2);
+  else eta[t] = (T)((double)acc[t] * scale);
+}
+
+// Whether scale is an exact power of two 2^e2 (host).
+inline bool exact_pow2(double scale, int* e2) {
+  int e = 0;
+  const double mant = std::frexp(scale, &e);  // scale = mant 2^e, mant in [1/2, 1)
+  if (mant != 0.5) return false;
+  *e2 = e - 1;
+  return *e2 > -960 && *e2 < 960;
 }
 
 // Grid force at every cell (one pass):
@@ -127,9 +164,11 @@ __device__ __forceinline__ float to_f32(T a) {
   else return (float)a;
 }
 
+// The grid force is stored interleaved, one float4 (f_x, f_y, f_z, 0) per cell: the gather then reads each of a
+// particle's eight cells with one 16-byte load instead of three scattered 4-byte ones.
 template <class T, int MODEL>
 __global__ void force_grid(const T* __restrict__ Phi, const T* __restrict__ phi, int lg, float a2, float Cs,
-                           float inv2h, float* __restrict__ fx, float* __restrict__ fy, float* __restrict__ fz) {
+                           float inv2h, float4* __restrict__ f) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t n = (size_t)1 << (3 * lg);
   if (t >= n) return;
@@ -151,9 +190,7 @@ __global__ void force_grid(const T* __restrict__ Phi, const T* __restrict__ phi,
     g1 = fmaf(pref, fdiff<T>(phi[yp], phi[ym]), g1);
     g2 = fmaf(pref, fdiff<T>(phi[zp], phi[zm]), g2);
   }
-  fx[t] = g0 * inv2h;
-  fy[t] = g1 * inv2h;
-  fz[t] = g2 * inv2h;
+  f[t] = make_float4(g0 * inv2h, g1 * inv2h, g2 * inv2h, 0.f);
 }
 
 // The same grid force, streamed: a block takes a tile of 8 x 32 cells in (j, k) through 32 planes in i and keeps
@@ -177,8 +214,7 @@ __device__ __forceinline__ float2 split_pair(T a) {
 template <class T, int MODEL>
 __global__ void __launch_bounds__(kFGTJ * kFGTK) force_grid_st(const T* __restrict__ Phi, const T* __restrict__ phi,
                                                                int lg, float a2, float Cs, float inv2h,
-                                                               float* __restrict__ fx, float* __restrict__ fy,
-                                                               float* __restrict__ fz) {
+                                                               float4* __restrict__ f) {
   __shared__ float2 sP[3][kFGHalo], sF[3][kFGHalo];
   const int N = 1 << lg, m = N - 1, ntk = N / kFGTK, ntj = N / kFGTJ;
   int b = blockIdx.x;
@@ -240,9 +276,7 @@ __global__ void __launch_bounds__(kFGTJ * kFGTK) force_grid_st(const T* __restri
       g2 = fmaf(pref, diff(sF[sc][c + 1], sF[sc][c - 1]), g2);
     }
     const size_t o = cidx(lg, i, j0 + tj, k0 + tk);
-    fx[o] = g0 * inv2h;
-    fy[o] = g1 * inv2h;
-    fz[o] = g2 * inv2h;
+    f[o] = make_float4(g0 * inv2h, g1 * inv2h, g2 * inv2h, 0.f);
     __syncthreads();
   }
 }
@@ -262,8 +296,7 @@ __device__ __forceinline__ void cic_axis_f(float x, int N, int& i0, int& i1, flo
 }
 
 // Per-particle acceleration g = -sum over the 8 CIC cells of W f (FP32).
-__global__ void force_gather(const float* __restrict__ fx, const float* __restrict__ fy,
-                             const float* __restrict__ fz, const float* __restrict__ x, const float* __restrict__ y,
+__global__ void force_gather(const float4* __restrict__ f, const float* __restrict__ x, const float* __restrict__ y,
                              const float* __restrict__ z, long long np, int lg, float* __restrict__ gx,
                              float* __restrict__ gy, float* __restrict__ gz) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -284,9 +317,10 @@ __global__ void force_gather(const float* __restrict__ fx, const float* __restri
       for (int d = 0; d < 2; ++d) {
         const size_t c = cidx(lg, ii[a], jj[b], kk[d]);
         const float w = wab * wk[d];
-        a0 = fmaf(w, __ldg(&fx[c]), a0);
-        a1 = fmaf(w, __ldg(&fy[c]), a1);
-        a2 = fmaf(w, __ldg(&fz[c]), a2);
+        const float4 v = __ldg(&f[c]);
+        a0 = fmaf(w, v.x, a0);
+        a1 = fmaf(w, v.y, a1);
+        a2 = fmaf(w, v.z, a2);
       }
     }
   gx[p] = -a0;
@@ -382,12 +416,14 @@ isis_status isis_cic_deposit(const isis_grid* grid, const float* x, const float*
   ISIS_LAUNCH(KK_CIC_SCATTER, 12.0 * npart + 8.0 * n, st,
               (cic_scatter<<<nblk((size_t)npart, 256), 256, 0, st>>>(x, y, z, (long long)npart, lg, acc)));
   const double scale = (double)n / ((double)npart * kFix);
+  int e2 = 0;
+  const int pow2 = exact_pow2(scale, &e2) ? 1 : 0;
   if (eta_f64)
     ISIS_LAUNCH(KK_CIC_FINISH, 16.0 * n, st,
-                (cic_finish<double><<<nblk(n, 256), 256, 0, st>>>(acc, (double*)eta, n, scale)));
+                (cic_finish<double><<<nblk(n, 256), 256, 0, st>>>(acc, (double*)eta, n, scale, pow2, e2)));
   else
     ISIS_LAUNCH(KK_CIC_FINISH, 12.0 * n, st,
-                (cic_finish<float><<<nblk(n, 256), 256, 0, st>>>(acc, (float*)eta, n, scale)));
+                (cic_finish<float><<<nblk(n, 256), 256, 0, st>>>(acc, (float*)eta, n, scale, pow2, e2)));
   return ISIS_OK;
 }
 
@@ -406,12 +442,14 @@ isis_status isis_cic_deposit_noalloc(const isis_grid* grid, const float* x, cons
   ISIS_LAUNCH(KK_CIC_SCATTER, 12.0 * npart + 8.0 * n, st,
               (cic_scatter<<<nblk((size_t)npart, 256), 256, 0, st>>>(x, y, z, (long long)npart, lg, acc)));
   const double scale = (double)n / ((double)npart * kFix);
+  int e2 = 0;
+  const int pow2 = exact_pow2(scale, &e2) ? 1 : 0;
   if (eta_f64)
     ISIS_LAUNCH(KK_CIC_FINISH, 16.0 * n, st,
-                (cic_finish<double><<<nblk(n, 256), 256, 0, st>>>(acc, (double*)eta, n, scale)));
+                (cic_finish<double><<<nblk(n, 256), 256, 0, st>>>(acc, (double*)eta, n, scale, pow2, e2)));
   else
     ISIS_LAUNCH(KK_CIC_FINISH, 12.0 * n, st,
-                (cic_finish<float><<<nblk(n, 256), 256, 0, st>>>(acc, (float*)eta, n, scale)));
+                (cic_finish<float><<<nblk(n, 256), 256, 0, st>>>(acc, (float*)eta, n, scale, pow2, e2)));
   return ISIS_OK;
 }
 
@@ -438,9 +476,7 @@ isis_status isis_fifth_force(isis_model model, const isis_params* p, const isis_
   const size_t n = (size_t)grid->N * grid->N * grid->N;
   float* fg = get_force_buf(grid->N);
   if (!fg) return ISIS_ENOMEM;
-  float* fx = fg;
-  float* fy = fg + n;
-  float* fz = fg + 2 * n;
+  float4* f4 = reinterpret_cast<float4*>(fg);
   int mcode = phi ? (int)model : 0;
   const double gbytes = (double)n * ((fields_f64 ? 8 : 4) * ((Phi ? 1 : 0) + (phi ? 1 : 0)) + 12);
   const int Ng = grid->N;
@@ -450,11 +486,11 @@ isis_status isis_fifth_force(isis_model model, const isis_params* p, const isis_
     ISIS_LAUNCH(KK_FORCE_GRID, gbytes, st,                                                                     \
                 (force_grid_st<T, MC><<<st_blocks, kFGTJ * kFGTK, 0, st>>>((const T*)Phi, (const T*)phi, lg,    \
                                                                           (float)a2, (float)Cs, (float)inv2h,   \
-                                                                          fx, fy, fz)));                        \
+                                                                          f4)));                                \
   else                                                                                                         \
     ISIS_LAUNCH(KK_FORCE_GRID, gbytes, st,                                                                     \
                 (force_grid<T, MC><<<nblk(n, 256), 256, 0, st>>>((const T*)Phi, (const T*)phi, lg, (float)a2,  \
-                                                                 (float)Cs, (float)inv2h, fx, fy, fz)))
+                                                                 (float)Cs, (float)inv2h, f4)))
   if (fields_f64) {
     if (mcode == 0) ISIS_FGRID(double, 0);
     else if (mcode == ISIS_SYMMETRON) ISIS_FGRID(double, ISIS_SYMMETRON);
@@ -466,8 +502,8 @@ isis_status isis_fifth_force(isis_model model, const isis_params* p, const isis_
   }
 #undef ISIS_FGRID
   ISIS_LAUNCH(KK_FORCE, 24.0 * npart + 12.0 * n, st,
-              (force_gather<<<nblk((size_t)npart, 256), 256, 0, st>>>(fx, fy, fz, x, y, z, (long long)npart, lg, gx,
-                                                                      gy, gz)));
+              (force_gather<<<nblk((size_t)npart, 256), 256, 0, st>>>(f4, x, y, z, (long long)npart, lg, gx, gy,
+                                                                      gz)));
   return ISIS_OK;
 }
 
