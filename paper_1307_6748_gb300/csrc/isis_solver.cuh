@@ -794,8 +794,15 @@ isis_status solve_refine(const SolveArgs& A) {
     Cycler<M, FIELD, float> cy;
     cy.setup(ws, A1, B0, eta0, nullptr);
     double res;
-    s = cy.fine_rms(&res);
-    if (s != ISIS_OK) return s;
+    if (bg_start && ref > 0.0) {
+      // The background field's residual is the reference itself, in closed form: -ref_scale (eta - <eta>) for
+      // Poisson at Phi = 0, -A s chi_bg (eta - 1) for the symmetron at chi_bg (chi_bg^2 = 1 - s), -K1 (eta - 1)
+      // for f(R) and the chameleon at their background (S vanishes there at eta = 1).  No norm pass.
+      res = ref;
+    } else {
+      s = cy.fine_rms(&res);
+      if (s != ISIS_OK) return s;
+    }
     loc.res0 = res;
     if (!(ref > 0.0)) ref = res;
     loc.res_ref = ref;
