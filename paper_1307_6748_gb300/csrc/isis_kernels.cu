@@ -237,7 +237,8 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, F
                                                                        const float2* __restrict__ tab,
                                                                        float* __restrict__ r32,
                                                                        float* __restrict__ B32,
-                                                                       double* __restrict__ part) {
+                                                                       double* __restrict__ part,
+                                                                       double* __restrict__ phi_out, double base) {
   __shared__ float2 stab[64];
   if (threadIdx.x < 64) stab[threadIdx.x] = tab[threadIdx.x];
   __syncthreads();
@@ -310,6 +311,7 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, F
     r32[o1] = -r.y;
     B32[o0] = B.x;
     B32[o1] = B.y;
+    if (phi_out) write_f64_pair(phi_out, q, pc, base, 1);  // u = u_bar + psi
     acc = fmaf(F.hi.x, F.hi.x, acc);
     acc = fmaf(F.hi.y, F.hi.y, acc);
   }

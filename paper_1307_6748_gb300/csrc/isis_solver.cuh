@@ -505,11 +505,28 @@ struct ResFF {
 // Two cells per thread, (k, k+1) with k even, as the lanes of packed FP32x2 float-float arithmetic (ff2):
 // the pair's own values and its i and j neighbours are 16-byte loads, the k neighbours outside the pair two
 // 8-byte loads.  In the red/black output the pair's two cells sit at the same place of the two halves.
+// phi_out (nullptr: none): the carried field written to FP64 as ff_to_f64 writes it, in the same pass.
+__device__ __forceinline__ void write_f64_pair(double* __restrict__ phi, unsigned q, const ff2& v, double base,
+                                               int has_base) {
+  double d0 = ff_to_double_bits(v.hi.x, v.lo.x), d1 = ff_to_double_bits(v.hi.y, v.lo.y);
+  if (has_base) {
+    d0 += base;
+    d1 += base;
+  }
+  if ((reinterpret_cast<uintptr_t>(phi) & 15u) == 0) {  // the caller's array: 8-byte alignment is all it promises
+    reinterpret_cast<double2*>(phi)[q >> 1] = make_double2(d0, d1);
+  } else {
+    phi[q] = d0;
+    phi[q + 1] = d1;
+  }
+}
+
 template <Model M>
 __global__ void __launch_bounds__(kNormThreads) outer_residual_ff(int lg, ResFF c, const double* __restrict__ eta,
                                                                   const float2* __restrict__ pff,
                                                                   float* __restrict__ r32, float* __restrict__ B32,
-                                                                  double* __restrict__ part) {
+                                                                  double* __restrict__ part,
+                                                                  double* __restrict__ phi_out) {
   // 32-bit positions: N <= 1024, so N^3 <= 2^30
   const unsigned np = 1u << (3 * lg - 1), half = np, m = (1u << lg) - 1u;
   const ff2 ih2 = ff2_bc(c.ih2), K = ff2_bc(c.K);
@@ -559,6 +576,7 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_ff(int lg, ResFF 
     r32[o1] = -r.y;
     B32[o0] = pc.hi.x;
     B32[o1] = pc.hi.y;
+    if (phi_out) write_f64_pair(phi_out, q, pc, 0.0, 0);
     acc = fmaf(F.hi.x, F.hi.x, acc);
     acc = fmaf(F.hi.y, F.hi.y, acc);
   }
@@ -585,7 +603,8 @@ __global__ void __launch_bounds__(kNormThreads) outer_residual_fofr_ff(int lg, F
                                                                        const float2* __restrict__ tab,
                                                                        float* __restrict__ r32,
                                                                        float* __restrict__ B32,
-                                                                       double* __restrict__ part);
+                                                                       double* __restrict__ part,
+                                                                       double* __restrict__ phi_out, double base);
 
 // ---------------------------------------------------------------------------
 // Drivers
@@ -922,26 +941,32 @@ isis_status solve_refine(const SolveArgs& A) {
   const double target = A.tol * ref;
   double prev_res = 0.0;
   int prev_k = 0;
+  bool written = false;  // the caller's FP64 field holds the carried field
   for (int outer = 0;; ++outer) {
-    // r = -L(phi) to FP64 accuracy from the carried float-float field, B = its FP32 value, RMS of r
+    // r = -L(phi) to FP64 accuracy from the carried float-float field, B = its FP32 value, RMS of r.  After a
+    // correction the pass also writes the field to the caller's FP64 array: it is the answer whenever this
+    // residual ends the loop (a residual that does not only costs the write).
     float2* carry = reinterpret_cast<float2*>(ws->b64);
+    double* wout = outer > 0 ? phi64 : nullptr;
     if (M == FOFR) {
       float2* E_ff = reinterpret_cast<float2*>(ws->s64);
       ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), 16.0 * n, st,
                   (fofr_exp_ff<<<nblk(n / 2, 256), 256, 0, st>>>(carry, E_ff, n, ws->exptab_ff, ffc.ek)));
-      ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), 32.0 * n, st,
+      ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), (wout ? 40.0 : 32.0) * n, st,
                   (outer_residual_fofr_ff<<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, ffc, eta64, carry, E_ff,
-                                                                                 ws->exptab_ff, r0, B0, ws->part)));
+                                                                                 ws->exptab_ff, r0, B0, ws->part,
+                                                                                 wout, u0)));
     } else {
-      // phi_ff and eta read, r and B written: 24 bytes per cell
-      ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), 24.0 * n, st,
+      // phi_ff and eta read, r and B written: 24 bytes per cell (and the FP64 field, 8 more)
+      ISIS_LAUNCH(kind_tag(KK_OUTER_RESID, (int)M, (int)FIELD), (wout ? 32.0 : 24.0) * n, st,
                   (outer_residual_ff<M><<<kNormBlocks, kNormThreads, 0, st>>>(F64.lg, rff, eta64, carry, r0, B0,
-                                                                              ws->part)));
+                                                                              ws->part, wout)));
     }
     ISIS_LAUNCH(KK_REDUCE, 0.0, st, (reduce_final<<<1, kNormThreads, 0, st>>>(ws->part, kNormBlocks, ws->scal)));
     ISIS_LAUNCH(KK_REDUCE, 0.0, st,
                 (publish_scalars<<<1, 32, 0, st>>>(ws->scal, 1, ws->iflags, 2, ws->host_dev, (int*)(ws->host_dev + 4))));
     ISIS_CK(cudaStreamSynchronize(st));
+    written = wout != nullptr;
     double res = std::sqrt(h[0] / (double)n);
     if (outer > 0 && nh < 128) loc.hist[nh++] = res;
     loc.nhist = nh;
@@ -990,10 +1015,13 @@ isis_status solve_refine(const SolveArgs& A) {
     }
     ISIS_LAUNCH(KK_UPDATE, 20.0 * n, st, (update_ff<<<nblk(n / 4, 256), 256, 0, st>>>(carry, ecur, lg, emean)));
   }
-  // the carried field to the caller: phi = hi + lo (f(R): u = u_bar + psi), in FP64
-  ISIS_LAUNCH(KK_UPDATE, 16.0 * n, st,
-              (ff_to_f64<<<nblk(n / 2, 256), 256, 0, st>>>(reinterpret_cast<const float2*>(ws->b64), phi64, n,
-                                                           M == FOFR ? u0 : 0.0, M == FOFR ? 1 : 0)));
+  // the carried field to the caller: phi = hi + lo (f(R): u = u_bar + psi), in FP64, unless the last residual
+  // pass wrote it
+  if (!written) {
+    ISIS_LAUNCH(KK_UPDATE, 16.0 * n, st,
+                (ff_to_f64<<<nblk(n / 2, 256), 256, 0, st>>>(reinterpret_cast<const float2*>(ws->b64), phi64, n,
+                                                             M == FOFR ? u0 : 0.0, M == FOFR ? 1 : 0)));
+  }
   if (A.info) *A.info = loc;
   return out;
 }
