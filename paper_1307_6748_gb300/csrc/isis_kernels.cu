@@ -128,11 +128,13 @@ __global__ void mean_to_f32(const double* __restrict__ sum, double inv_n, float*
 __global__ void __launch_bounds__(kNormThreads) moments_to_rb(const double* __restrict__ v, float* __restrict__ rb,
                                                               int lg, double* __restrict__ part2,
                                                               double* __restrict__ part1) {
-  // four cells per iteration (two 16-byte loads in flight per thread), fixed assignment: reproducible
+  // four cells per iteration, two iterations unrolled (four 16-byte loads in flight per thread), fixed
+  // assignment: reproducible
   const size_t nq = (size_t)1 << (3 * lg - 2);
   ff s1 = {0.f, 0.f};
   float s2 = 0.f;
   const bool al = (reinterpret_cast<uintptr_t>(v) & 15u) == 0;  // the caller's array: 16-byte loads if aligned
+#pragma unroll 2
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (size_t)gridDim.x * blockDim.x) {
     double2 a, b;
     if (al) {
@@ -162,6 +164,7 @@ __global__ void __launch_bounds__(kNormThreads) sum_f32_partial(const float* __r
   // four values per iteration (one 16-byte load; n a multiple of 4)
   ff s = {0.f, 0.f};
   const size_t n4 = n >> 2;
+#pragma unroll 2
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += (size_t)gridDim.x * blockDim.x) {
     const float4 a = reinterpret_cast<const float4*>(v)[t];
     s = ff_add(s, ff_add(ff_two_sum(a.x, a.y), ff_two_sum(a.z, a.w)));
