@@ -270,10 +270,15 @@ struct Cycler {
                     (resid_restrict<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(L[l], c, C, (T*)ws->x0[l + 1],
                                                                             (T*)ws->sig[l + 1])));
     }
+    bool paired = false;  // FP32 levels of side 4 or more: the paired gather
     if constexpr (sizeof(T) == 4) {
-      ISIS_LAUNCH(tk(KK_SIGMA), sizeof(T) * ncd * (2 + arrays(true)), st,
-                  (sigma_rb2<M, FM><<<nblk(nc / 2, 256), 256, 0, st>>>(C, c, (float*)ws->sig[l + 1])));
-    } else {
+      if (C.N >= 4) {
+        ISIS_LAUNCH(tk(KK_SIGMA), sizeof(T) * ncd * (2 + arrays(true)), st,
+                    (sigma_rb2<M, FM><<<nblk(nc / 2, 256), 256, 0, st>>>(C, c, (float*)ws->sig[l + 1])));
+        paired = true;
+      }
+    }
+    if (!paired) {
       ISIS_LAUNCH(tk(KK_SIGMA), sizeof(T) * ncd * (2 + arrays(true)), st,
                   (coarse_sigma_add<M, FM, T><<<nblk(nc, 256), 256, 0, st>>>(C, c, (T*)ws->sig[l + 1])));
     }
