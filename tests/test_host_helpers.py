@@ -65,3 +65,36 @@ def test_halo_density_recipe_is_high_contrast():
     assert abs(eta.mean() - 1.0) <= 1e-12
     assert eta.max() >= 1e3 and eta.min() < 0.05
     assert (eta > 0).all()
+
+
+class _Ev:
+    """A stand-in for a CUDA event: elapsed_time is the difference of two stamps."""
+
+    def __init__(self, t):
+        self.t = t
+
+    def elapsed_time(self, other):
+        return other.t - self.t
+
+
+def test_copy_times_groups_copies_per_step():
+    """bench.copy_times: the mean copy time per step and the slowest step, per loop and direction; the
+    pipelined loop reads back each model's forces as its own group (two D2H groups per step)."""
+    import bench
+    ev = {"serial": [("h2d", _Ev(0), _Ev(7)), ("d2h", _Ev(0), _Ev(16)), ("h2d", _Ev(0), _Ev(9)),
+                     ("d2h", _Ev(0), _Ev(100))],
+          "pipelined": [("h2d", _Ev(0), _Ev(7)), ("h2d", _Ev(0), _Ev(8)), ("d2h", _Ev(0), _Ev(8)),
+                        ("d2h", _Ev(0), _Ev(9)), ("d2h", _Ev(0), _Ev(50)), ("d2h", _Ev(0), _Ev(8))]}
+    out = bench.copy_times(ev, 2)
+    assert out["serial_h2d"] == {"mean": 8.0, "max_step": 9}
+    assert out["serial_d2h"] == {"mean": 58.0, "max_step": 100}
+    assert out["pipelined_h2d"] == {"mean": 7.5, "max_step": 8}
+    assert out["pipelined_d2h"] == {"mean": 37.5, "max_step": 58}
+
+
+def test_host_buffer_of_no_bytes_is_rejected():
+    """isis.host_empty(0): isis_host_alloc refuses zero bytes before any driver call."""
+    from paper_1307_6748_gb300 import build
+    build.build()
+    with pytest.raises(isis.IsisError):
+        isis.host_empty(0)
