@@ -58,6 +58,8 @@ def parse(argv=None):
     ap.add_argument("--guess", default="background", choices=["net", "background"],
                     help="symmetron initial guess of the timed step: the background field (the faster start on this "
                          "density, see the learned_guess record) or the trained U-Net")
+    ap.add_argument("--no-halo-record", action="store_true",
+                    help="skip the solves on the lognormal-plus-halo density (outside the timed region)")
     ap.add_argument("--no-guess-record", action="store_true",
                     help="skip the learned guess's record (net start against background start)")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1307_6748_gb300", "weights", "unet_symmetron.npz"))
@@ -384,6 +386,42 @@ def learned_guess(args, dev, S, barrier) -> dict:
     return rec
 
 
+def halo_record(args, dev, S, barrier, peak: float) -> dict:
+    """The metric's solves on the lognormal-plus-halo density (sigma 1.5, 32 NFW haloes of 1e13-1e15 Msun/h,
+    c = 5) at the step's grid and box: the symmetron at a = 1.0 and 0.6 (close to symmetry breaking) from its
+    background field, and f(R) from the cell-wise uniform-density solution (ISIS_INIT_LOCAL: from the background
+    the f(R) iterate overshoots without bound inside the haloes), with the step's options, timed after one warm-up
+    with CUDA events, outside the timed region.  solve_frac as in the roofline record."""
+    import torch
+
+    from paper_1307_6748_gb300 import isis, synth
+    eta = synth.nfw_eta(args.N, args.box, 1.5, seed=11).to(device=dev, dtype=torch.float64)
+    phi = torch.empty_like(eta)
+    per_cycle = 6 * 4 * (8.0 / 7.0) * args.N ** 3
+    out = {"density": "lognormal sigma 1.5 (seed 11) plus 32 NFW haloes (seed 2)"}
+    cases = (("symmetron_a1.0", isis.ISIS_SYMMETRON, S.psym, 1.0, args.inner_sym, isis.ISIS_INIT_BACKGROUND),
+             ("symmetron_a0.6", isis.ISIS_SYMMETRON, S.psym, 0.6, args.inner_sym, isis.ISIS_INIT_BACKGROUND),
+             ("fofr", isis.ISIS_FOFR_HS, S.pfr, 1.0, args.inner_fofr, isis.ISIS_INIT_LOCAL))
+    for name, model, par, a, inner, init in cases:
+        o = isis.Opts(prec=isis.ISIS_F32_REFINE64, inner_cycles=inner, init=init,
+                      n_coarsest=args.ncoarse, fmg=args.fmg, nu1=args.nu1, nu2=args.nu2)
+        try:
+            for _ in range(2):
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(S.stream)
+                info = isis.isis_scalar_solve(model, par, S.grid, a, eta, phi, tol=args.tol, opts=o)
+                e1.record(S.stream)
+                barrier()
+            ms = e0.elapsed_time(e1)
+            out[name] = {"ms": ms, "cycles": info.cycles, "outer": info.outer,
+                         "res_rel": info.res_final / info.res_ref,
+                         "solve_frac": per_cycle * info.cycles / (ms * 1e-3 * peak * 1e9)}
+        except isis.IsisError as err:
+            out[name] = {"error": str(err)}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Roofline figures
 # ---------------------------------------------------------------------------
@@ -680,6 +718,9 @@ def main():
     guess_rec = None
     if not args.no_guess_record and os.path.exists(args.weights):
         guess_rec = learned_guess(args, dev, S, barrier)
+    halo_rec = None
+    if not args.no_halo_record:
+        halo_rec = halo_record(args, dev, S, barrier, hbm_peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -698,6 +739,8 @@ def main():
             line["vs_fp64_solver"] = vs_fp64
         if guess_rec is not None:
             line["learned_guess"] = guess_rec
+        if halo_rec is not None:
+            line["halo_density_solves"] = halo_rec
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
